@@ -1,0 +1,284 @@
+"""Oracle: the three-way (generalised) ACA of one admissible block.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Follows Algorithm 1 ("3D ACA") of the paper, with the implementation
+remarks of the same section, in complex128:
+
+  l = 0, k_1 = first frequency, C^(0) = 0
+  repeat
+    l += 1
+    face:   H_l ~ ENTRY(:, :, k_l) - C^(l-1)[:, :, k_l], approximated by
+            partial-pivot ACA (the faces are compressed with ACA, tolerance
+            eps_face = eps3 / 100, "eps = 100 eps_ACA") and recompressed by
+            QR of both factors + SVD of R_U R_V^H (first remark)
+    pivot:  (i_l, j_l) = argmax |H_l[i, j]| over the dense expansion of the
+            low-rank face (last remark: "expanding to the dense block")
+    fiber:  f_l[k] = (ENTRY(i_l, j_l, k) - C^(l-1)[i_l, j_l, k]) / H_l[i_l, j_l]
+    norm:   ||C^(l)||_F^2 by eq. (norm), i.e. the double sum over
+            <H_d, H_d'>_F <f_d, f_d'>, accumulated over the new terms
+    stop when ||H_l||_F ||f_l||_2 <= eps3 ||C^(l)||_F ; the rank is l - 1
+    (the last cross is dropped, as in Algorithm 1), or when every frequency
+    is used (rank l)
+    k_{l+1} = argmax over not-yet-used k of |f_l[k]|
+
+Readings where the paper is silent (all shared with the CUDA path):
+
+* The tensor is the block restricted to the unique frequencies (one of each
+  conjugate pair, Appendix A: only half of the frequencies need to be
+  computed); k_1 = 0 (every block starts with the first frequency).
+* argmax ties: smallest index (row-major for (i, j)).  k_{l+1} excludes
+  frequencies already used (|f_l[k_l]| = 1 would otherwise repeat k_l).
+* Face ACA (Bebendorf's partial pivoting): start with the block's first row;
+  column pivot j = argmax |residual row|; next row = argmax over unused rows
+  of |u|; a row whose residual is exactly zero is marked used and the
+  smallest unused row is tried next; stop when ||u|| ||v|| <= eps_face ||S||_F
+  (||S||_F updated recursively), or at min(M, N) or `max_face_rank` crosses.
+* Recompression truncates singular values sigma_i < eps_face * sigma_1.
+* A zero face (no row with a nonzero residual) at k_l: the paper only says
+  that some frequencies are tested to confirm a zero block.  Up to three more
+  unused frequencies are tested (the last unique one, the middle one, the one
+  of largest |s|); if all faces are zero the block ends with rank l - 1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+class BlockEntries:
+    """ENTRY restricted to one block and the unique frequencies (abstract)."""
+
+    M: int
+    N: int
+    Ku: int
+
+    def row(self, i: int, k: int) -> np.ndarray:
+        raise NotImplementedError
+
+    def col(self, j: int, k: int) -> np.ndarray:
+        raise NotImplementedError
+
+    def fiber(self, i: int, j: int) -> np.ndarray:
+        raise NotImplementedError
+
+
+class BemBlock(BlockEntries):
+    """Collocation entries of a block (rows/cols are ORIGINAL element ids)."""
+
+    def __init__(self, entry_fn, rows: np.ndarray, cols: np.ndarray, s_u: np.ndarray):
+        self.f = entry_fn            # f(I, J, s) -> [n, nk]
+        self.rows = np.asarray(rows)
+        self.cols = np.asarray(cols)
+        self.s = np.asarray(s_u)
+        self.M, self.N, self.Ku = self.rows.size, self.cols.size, self.s.size
+        self.generated = 0
+
+    def row(self, i, k):
+        self.generated += self.N
+        return self.f(np.full(self.N, self.rows[i]), self.cols, self.s[k:k + 1])[:, 0]
+
+    def col(self, j, k):
+        self.generated += self.M
+        return self.f(self.rows, np.full(self.M, self.cols[j]), self.s[k:k + 1])[:, 0]
+
+    def fiber(self, i, j):
+        self.generated += self.Ku
+        return self.f(self.rows[i:i + 1], self.cols[j:j + 1], self.s)[0]
+
+
+class SeparableBlock(BlockEntries):
+    """Synthetic test tensor A[i, j, k] = sum_t a[t, i] b[t, j] c[t, k]."""
+
+    def __init__(self, a: np.ndarray, b: np.ndarray, c: np.ndarray):
+        self.a, self.b, self.c = (np.asarray(x, dtype=np.complex128) for x in (a, b, c))
+        self.M, self.N, self.Ku = self.a.shape[1], self.b.shape[1], self.c.shape[1]
+        self.generated = 0
+
+    def row(self, i, k):
+        self.generated += self.N
+        return (self.a[:, i] * self.c[:, k]) @ self.b
+
+    def col(self, j, k):
+        self.generated += self.M
+        return (self.b[:, j] * self.c[:, k]) @ self.a
+
+    def fiber(self, i, j):
+        self.generated += self.Ku
+        return (self.a[:, i] * self.b[:, j]) @ self.c
+
+    def dense(self) -> np.ndarray:
+        return np.einsum("ti,tj,tk->ijk", self.a, self.b, self.c)
+
+
+def aca2(row_fn, col_fn, M: int, N: int, eps: float, max_rank: int | None = None):
+    """Partial-pivot ACA of a matrix given by residual row/column callbacks.
+
+    Returns U [M, r], V [N, r] with the approximant S = U V^H.
+    """
+    cap = min(M, N) if max_rank is None else min(M, N, max_rank)
+    us: list[np.ndarray] = []
+    vs: list[np.ndarray] = []
+    used = np.zeros(M, dtype=bool)
+    norm2 = 0.0
+    i = 0
+    while len(us) < cap:
+        while True:
+            row = row_fn(i).astype(np.complex128)
+            for u_t, v_t in zip(us, vs):
+                row = row - u_t[i] * np.conj(v_t)
+            used[i] = True
+            mag = row.real * row.real + row.imag * row.imag
+            j = int(np.argmax(mag))
+            if mag[j] > 0.0:
+                break
+            free = np.nonzero(~used)[0]
+            if free.size == 0:
+                return _stack(us, M), _stack(vs, N)
+            i = int(free[0])
+        delta = row[j]
+        v = np.conj(row / delta)
+        u = col_fn(j).astype(np.complex128)
+        for u_t, v_t in zip(us, vs):
+            u = u - u_t * np.conj(v_t[j])
+        cross = 0.0
+        for u_t, v_t in zip(us, vs):
+            cross += 2.0 * (np.vdot(u_t, u) * np.vdot(v, v_t)).real
+        nu2 = float(np.vdot(u, u).real)
+        nv2 = float(np.vdot(v, v).real)
+        norm2 += cross + nu2 * nv2
+        us.append(u)
+        vs.append(v)
+        if np.sqrt(nu2 * nv2) <= eps * np.sqrt(norm2):
+            break
+        free = np.nonzero(~used)[0]
+        if free.size == 0:
+            break
+        mag = u.real * u.real + u.imag * u.imag
+        i = int(free[int(np.argmax(mag[free]))])
+    return _stack(us, M), _stack(vs, N)
+
+
+def _stack(cols: list[np.ndarray], n: int) -> np.ndarray:
+    if not cols:
+        return np.zeros((n, 0), dtype=np.complex128)
+    return np.stack(cols, axis=1)
+
+
+def recompress(U: np.ndarray, V: np.ndarray, eps: float):
+    """U V^H = Q_U (R_U R_V^H) Q_V^H, SVD of the core, truncation at
+    sigma_i < eps sigma_1.  Returns (U' = Q_U X Sigma, V' = Q_V Y)."""
+    if U.shape[1] == 0:
+        return U, V
+    Qu, Ru = np.linalg.qr(U)
+    Qv, Rv = np.linalg.qr(V)
+    X, sig, Yh = np.linalg.svd(Ru @ Rv.conj().T)
+    r = int(np.count_nonzero(sig >= eps * sig[0]))
+    return Qu @ (X[:, :r] * sig[:r]), Qv @ Yh[:r].conj().T
+
+
+class Cross:
+    __slots__ = ("U", "V", "f", "i", "j", "k")
+
+    def __init__(self, U, V, f, i, j, k):
+        self.U, self.V, self.f, self.i, self.j, self.k = U, V, f, i, j, k
+
+    @property
+    def face_rank(self) -> int:
+        return self.U.shape[1]
+
+
+class Result:
+    def __init__(self, crosses, computed, norm2_history, zero_block):
+        self.crosses: list[Cross] = crosses
+        self.computed = computed           # crosses computed incl. the dropped one
+        self.norm2_history = norm2_history # ||C^(l)||_F^2 after each cross (eq. (norm))
+        self.zero_block = zero_block
+
+    @property
+    def rank(self) -> int:
+        return len(self.crosses)
+
+    def dense(self, M: int, N: int, Ku: int) -> np.ndarray:
+        out = np.zeros((M, N, Ku), dtype=np.complex128)
+        for c in self.crosses:
+            out += (c.U @ c.V.conj().T)[:, :, None] * c.f[None, None, :]
+        return out
+
+
+def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
+         s_abs: np.ndarray | None = None, max_face_rank: int | None = None,
+         k1: int = 0) -> Result:
+    """Algorithm 1 on one block (see module docstring for the readings)."""
+    if eps_face is None:
+        eps_face = eps3 / 100.0
+    M, N, Ku = op.M, op.N, op.Ku
+    crosses: list[Cross] = []
+    faces: list[np.ndarray] = []       # dense H_d, for eq. (norm)
+    used = np.zeros(Ku, dtype=bool)
+    norm2 = 0.0
+    hist: list[float] = []
+    k = k1
+    ell = 0
+
+    def face_at(kk: int):
+        def row_fn(i):
+            r = op.row(i, kk)
+            for c in crosses:
+                r = r - c.f[kk] * (c.U[i, :] @ c.V.conj().T)
+            return r
+
+        def col_fn(j):
+            cc = op.col(j, kk)
+            for c in crosses:
+                cc = cc - c.f[kk] * (c.U @ c.V[j, :].conj())
+            return cc
+
+        return aca2(row_fn, col_fn, M, N, eps_face, max_face_rank)
+
+    while True:
+        ell += 1
+        U, V = face_at(k)
+        used[k] = True
+        if U.shape[1] == 0:
+            cands = []
+            for kk in (Ku - 1, Ku // 2,
+                       int(np.argmax(s_abs)) if s_abs is not None else Ku - 1):
+                if not used[kk] and kk not in cands:
+                    cands.append(kk)
+            found = False
+            for kk in cands[:3]:
+                used[kk] = True
+                U, V = face_at(kk)
+                if U.shape[1] > 0:
+                    k = kk
+                    found = True
+                    break
+            if not found:
+                return Result(crosses, ell - 1, hist, zero_block=(ell == 1))
+        U, V = recompress(U, V, eps_face)
+        H = U @ V.conj().T
+        mag = H.real * H.real + H.imag * H.imag
+        flat = int(np.argmax(mag))
+        ip, jp = divmod(flat, N)
+        fib = op.fiber(ip, jp)
+        for c, Hd in zip(crosses, faces):
+            fib = fib - Hd[ip, jp] * c.f
+        f = fib / H[ip, jp]
+        # eq. (norm): add the terms of the double sum that involve cross l
+        new = 0.0
+        for c, Hd in zip(crosses, faces):
+            new += 2.0 * (np.vdot(Hd, H) * np.vdot(c.f, f)).real
+        nH2 = float(np.vdot(H, H).real)
+        nf2 = float(np.vdot(f, f).real)
+        norm2 += new + nH2 * nf2
+        hist.append(norm2)
+        cross = Cross(U, V, f, ip, jp, k)
+        if np.sqrt(nH2 * nf2) <= eps3 * np.sqrt(norm2):
+            return Result(crosses, ell, hist, zero_block=False)
+        crosses.append(cross)
+        faces.append(H)
+        if ell == Ku or used.all():
+            return Result(crosses, ell, hist, zero_block=False)
+        fm = f.real * f.real + f.imag * f.imag
+        fm = np.where(used, -1.0, fm)
+        k = int(np.argmax(fm))

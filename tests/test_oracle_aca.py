@@ -1,0 +1,189 @@
+"""Pins for the oracle's three-way ACA (Algorithm 1), its face ACA and
+recompression, eq. (norm), and the compressed apply (eq. (product))."""
+import numpy as np
+import pytest
+
+from inputs import workloads
+from oracle import aca3, apply as A, freqs, quadrature as Q, tree
+
+
+def _rand(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def test_aca2_exact_on_rank_r_matrix():
+    rng = np.random.default_rng(0)
+    for r in (1, 3, 7):
+        X = _rand(rng, 40, r) @ _rand(rng, r, 33)
+        U, V = aca2_dense(X, 1e-12)
+        assert U.shape[1] <= r + 1
+        assert np.linalg.norm(X - U @ V.conj().T) < 1e-12 * np.linalg.norm(X)
+
+
+def aca2_dense(X, eps):
+    return aca3.aca2(lambda i: X[i, :], lambda j: X[:, j], X.shape[0], X.shape[1], eps)
+
+
+def test_aca2_smooth_kernel_tolerance_and_interpolation():
+    x = np.linspace(0, 1, 60)
+    y = np.linspace(3, 4, 50)
+    X = 1.0 / np.abs(x[:, None] - y[None, :]) * np.exp(-(0.5 + 2j) * np.abs(x[:, None] - y[None, :]))
+    for eps in (1e-4, 1e-8):
+        U, V = aca2_dense(X, eps)
+        err = np.linalg.norm(X - U @ V.conj().T) / np.linalg.norm(X)
+        assert err < 10 * eps
+    # ACA interpolates the selected crosses: rows i_t / columns j_t are exact
+    U, V = aca2_dense(X, 1e-6)
+    S = U @ V.conj().T
+    res = np.abs(X - S)
+    assert np.sum(res.max(axis=1) < 1e-12 * np.abs(X).max()) >= U.shape[1]
+
+
+def test_aca2_zero_rows_are_skipped_and_zero_matrix_gives_rank0():
+    X = np.zeros((10, 8), dtype=complex)
+    U, V = aca2_dense(X, 1e-6)
+    assert U.shape == (10, 0)
+    X[7, 3] = 2.0 + 1.0j
+    U, V = aca2_dense(X, 1e-6)
+    assert U.shape[1] == 1 and np.allclose(U @ V.conj().T, X)
+
+
+def test_recompress_preserves_product_and_truncates():
+    rng = np.random.default_rng(1)
+    U = _rand(rng, 30, 6)
+    V = _rand(rng, 25, 6)
+    U2, V2 = aca3.recompress(U, V, 1e-14)
+    assert np.linalg.norm(U @ V.conj().T - U2 @ V2.conj().T) < 1e-12 * np.linalg.norm(U @ V.conj().T)
+    assert np.allclose(V2.conj().T @ V2, np.eye(V2.shape[1]), atol=1e-12)
+    # a rank-2 product written with 6 columns recompresses to rank 2
+    U = _rand(rng, 30, 2) @ _rand(rng, 2, 6)
+    U2, V2 = aca3.recompress(U, V, 1e-10)
+    assert U2.shape[1] == 2
+
+
+def test_aca3_rank1_separable_exact():
+    rng = np.random.default_rng(2)
+    op = aca3.SeparableBlock(_rand(rng, 1, 20), _rand(rng, 1, 17), _rand(rng, 1, 9))
+    res = aca3.aca3(op, 1e-6)
+    assert res.rank == 1
+    D = op.dense()
+    assert np.linalg.norm(D - res.dense(20, 17, 9)) < 1e-13 * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("R", [2, 3, 5])
+def test_aca3_rank_r_separable_recovered(R):
+    rng = np.random.default_rng(10 + R)
+    # decaying weights keep the cross pivots well separated
+    c = _rand(rng, R, 12) * (0.3 ** np.arange(R))[:, None]
+    op = aca3.SeparableBlock(_rand(rng, R, 22), _rand(rng, R, 19), c)
+    res = aca3.aca3(op, 1e-10)
+    assert res.rank <= R
+    D = op.dense()
+    assert np.linalg.norm(D - res.dense(22, 19, 12)) < 1e-9 * np.linalg.norm(D)
+
+
+def _bem_block(name="cube768", kernel="slp", pick="largest"):
+    w = workloads.get(name)
+    g = Q.Geometry(w.verts, w.tris)
+    T = tree.build(w.verts, w.tris, w.leaf, w.eta)
+    fs = freqs.frequency_set(w.freq)
+    s_u = fs["s"][fs["uniq"]]
+    far = [b for b in range(T.blocks.shape[0]) if T.blocks[b, 4] == 1]
+    sizes = [(T.blocks[b, 1] - T.blocks[b, 0]) * (T.blocks[b, 3] - T.blocks[b, 2]) for b in far]
+    b = far[int(np.argmax(sizes))] if pick == "largest" else far[pick]
+    rb, re, cb, ce, _ = T.blocks[b]
+    ef = lambda I, J, s: Q.entries(g, kernel, I, J, s)
+    op = aca3.BemBlock(ef, T.perm[rb:re], T.perm[cb:ce], s_u)
+    D = Q.dense(g, kernel, s_u, rows=T.perm[rb:re], cols=T.perm[cb:ce])
+    return op, D, s_u
+
+
+def test_aca3_bem_block_tolerance_norm_recursion_and_fiber_interpolation():
+    op, D, s_u = _bem_block()
+    eps3 = 1e-4
+    res = aca3.aca3(op, eps3, s_abs=np.abs(s_u))
+    M, N, Ku = D.shape
+    C = res.dense(M, N, Ku)
+    assert res.rank >= 2
+    # brute force: the approximant meets the tolerance on the whole block
+    assert np.linalg.norm(D - C) <= 10 * eps3 * np.linalg.norm(D)
+    # eq. (norm): the recursive norm equals the dense norm of the approximant
+    assert abs(res.norm2_history[res.rank - 1] - np.linalg.norm(C) ** 2) < 1e-10 * np.linalg.norm(C) ** 2
+    # the fiber at the last kept pivot is reproduced exactly
+    last = res.crosses[-1]
+    assert np.max(np.abs(C[last.i, last.j, :] - D[last.i, last.j, :])) < 1e-10 * np.abs(D).max()
+    # the face at each used frequency is reproduced to the face tolerance
+    for c in res.crosses:
+        assert np.linalg.norm(C[:, :, c.k] - D[:, :, c.k]) < 1e-4 * np.linalg.norm(D[:, :, c.k])
+    # the first frequency is always the first one used
+    assert res.crosses[0].k == 0
+
+
+def test_aca3_dlp_zero_block_has_rank0():
+    """Double-layer blocks whose collocation points all lie in the planes of
+    the column elements vanish identically; they are detected as zero blocks
+    after testing further frequencies, and other blocks are not."""
+    w = workloads.get("lshape3072")
+    g = Q.Geometry(w.verts, w.tris)
+    T = tree.build(w.verts, w.tris, w.leaf, w.eta)
+    fs = freqs.frequency_set(w.freq)
+    s_u = fs["s"][fs["uniq"]]
+    ef = lambda I, J, s: Q.entries(g, "dlp", I, J, s)
+    zero, nonzero = 0, 0
+    for b in range(T.blocks.shape[0]):
+        rb, re, cb, ce, adm = T.blocks[b]
+        if not adm:
+            continue
+        R, Cc = T.perm[rb:re], T.perm[cb:ce]
+        d = np.einsum("ijd,jd->ij", g.centroid[R][:, None, :] - g.v0[Cc][None, :, :], g.normal[Cc])
+        is_zero = bool(np.all(d == 0.0))
+        if (is_zero and zero < 3) or (not is_zero and nonzero < 2):
+            res = aca3.aca3(aca3.BemBlock(ef, R, Cc, s_u), 1e-4, s_abs=np.abs(s_u))
+            assert (res.rank == 0) == is_zero and res.zero_block == is_zero
+            zero += is_zero
+            nonzero += not is_zero
+        if zero == 3 and nonzero == 2:
+            break
+    assert zero == 3 and nonzero == 2
+
+
+def test_compressed_apply_matches_dense_apply():
+    w = workloads.get("cube768")
+    g = Q.Geometry(w.verts, w.tris)
+    T = tree.build(w.verts, w.tris, 32, 1.0)
+    fs = freqs.frequency_set(workloads.bdf2_spec(8, 0.1))
+    s_all, uniq, partner = fs["s"], fs["uniq"], fs["partner"]
+    s_u = s_all[uniq]
+    ef = lambda I, J, s: Q.entries(g, "slp", I, J, s)
+    res = {}
+    for b, (rb, re, cb, ce, adm) in enumerate(T.blocks):
+        if adm:
+            res[b] = aca3.aca3(aca3.BemBlock(ef, T.perm[rb:re], T.perm[cb:ce], s_u), 1e-4,
+                               s_abs=np.abs(s_u))
+    assert len(res) > 0
+    W = workloads.densities(w.E, 8, 3)
+    yc = A.compressed_apply(T, res, ef, s_all, uniq, partner, W)
+    yd = A.dense_apply(ef, w.E, s_all, W)
+    assert np.linalg.norm(yc - yd) <= 10 * 1e-4 * np.linalg.norm(yd)
+    # the far-field part alone also meets the tolerance
+    far_only = A.compressed_apply(T, res, lambda I, J, s: np.zeros((I.size, s.size), complex),
+                                  s_all, uniq, partner, W)
+    yfar = np.zeros(w.E, dtype=complex)
+    for b, (rb, re, cb, ce, adm) in enumerate(T.blocks):
+        if adm:
+            R, Cc = T.perm[rb:re], T.perm[cb:ce]
+            D = Q.dense(g, "slp", s_all, rows=R, cols=Cc)
+            yfar[R] += np.einsum("ijk,jk->i", D, W[Cc, :])
+    assert np.linalg.norm(far_only - yfar) <= 10 * 1e-4 * np.linalg.norm(yfar)
+
+
+def test_expand_fibers_uses_conjugate_partners():
+    K = 8
+    uniq, partner = freqs.bdf2_unique(K)
+    f = np.arange(1, uniq.size + 1) * (1 + 1j)
+    a, b = A.expand_fibers(f, uniq, partner, K)
+    assert np.allclose(a[uniq], f)
+    for u, k in enumerate(uniq):
+        if partner[k] != k:
+            assert b[partner[k]] == np.conj(f[u])
+    assert np.all(a[[k for k in range(K) if k not in uniq]] == 0)
