@@ -1,0 +1,279 @@
+/*
+ * g3aca.h -- C ABI of the GB300 three-way ACA library.
+ *
+ * The library generates and compresses the three-way array
+ *     A[i, j, k] = ENTRY(i, j, s_k)
+ * of Laplace-domain boundary element entries (single layer V, double layer
+ * K) over complex (g)CQ frequencies s_k, block by block with the generalised
+ * (three-way) adaptive cross approximation, and applies the compressed
+ * factors plus the dense near field to densities at all frequencies.
+ *
+ * Paper: "Generalised Adaptive Cross Approximation for Convolution
+ * Quadrature based Boundary Element Formulation" (Haider, Rjasanow, Schanz,
+ * arXiv 2312.11219).  Each entry point names the section, equation or
+ * algorithm that defines its operation.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns g3_status; 0 (G3_OK) is success, negative values
+ *    are errors.  g3_last_error() returns a message for the calling thread's
+ *    most recent error (static storage, valid until the next call on that
+ *    thread).  No function exits, aborts or traps.
+ *  - Handles (g3_ctx, g3_freqs, g3_tree, g3_near, g3_factors) are opaque,
+ *    owned by the library and released with the matching *_free / destroy.
+ *    A handle is used on the device and stream of the context it was created
+ *    with.  Handles are not thread-safe; distinct handles may be used from
+ *    distinct threads.
+ *  - Host arrays passed in are copied (or fully consumed) before return;
+ *    the caller keeps ownership.  Device pointers passed in (W, Y of
+ *    apply_gcq) belong to the caller; the library reads/writes them in
+ *    stream order on the context's stream and never frees them.
+ *  - Complex numbers are interleaved (re, im) pairs; "c128" = 2 doubles,
+ *    "c64" = 2 floats.  Matrices are column-major unless stated otherwise.
+ *  - Element indices at the boundary are ORIGINAL element indices (the row of
+ *    `tris`), not cluster order, unless stated otherwise.
+ *  - Device errors are reported through a device status word that the host
+ *    reads after the launch; they surface as G3_ECUDA, G3_ENOCONV or
+ *    G3_EOVERFLOW.  No kernel spins on a flag written by another block.
+ */
+#ifndef G3ACA_H
+#define G3ACA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define G3ACA_VERSION 1
+
+typedef enum {
+    G3_OK = 0,
+    G3_EINVAL = -1,     /* invalid argument (null handle, bad size, bad enum) */
+    G3_ENOMEM = -2,     /* host or device allocation failed */
+    G3_ECUDA = -3,      /* a CUDA runtime call or a kernel failed */
+    G3_ETIMEOUT = -4,   /* reserved: a bounded device wait ran out */
+    G3_ENOCONV = -5,    /* a face ACA reached its rank cap before its tolerance */
+    G3_EOVERFLOW = -6,  /* the factor pool was too small even after regrowth */
+    G3_EUNSUPPORTED = -7 /* combination not implemented (e.g. DLP + Galerkin) */
+} g3_status;
+
+/* Integral kernel (paper Section 2: single layer eq. (slp), double layer
+ * eq. (dlp); Laplace-domain fundamental solution exp(-s r)/(4 pi r), c = 1). */
+typedef enum {
+    G3_SLP = 0,          /* V: exp(-s r)/(4 pi r)                                  */
+    G3_DLP = 1,          /* K: exp(-s r)(1 + s r)((x - y).n_y)/(4 pi r^3)          */
+    G3_SEPARABLE = 2     /* synthetic sum_t a_t[i] b_t[j] c_t[k] (test tensors)     */
+} g3_kernel;
+
+/* Spatial scheme (paper Section 3, eq. (bie_semi_diri), eq. (bie_semi_indirect)). */
+typedef enum {
+    G3_COLLOC7 = 0,      /* collocation at centroids, 7-point degree-5 rule        */
+    G3_GALERKIN4x4 = 1   /* Galerkin, 4-point x 4-point rule (single layer only)   */
+} g3_scheme;
+
+/* Arithmetic of the path. */
+typedef enum {
+    G3_FP64 = 0,   /* everything in float64; factors and near field complex128       */
+    G3_MIXED = 1   /* float32 entries and face arithmetic, float64 singular entries,
+                      fiber residuals, norms, recompression and frequencies;
+                      factors and near field complex64                                */
+} g3_precision;
+
+typedef enum { G3_C64 = 0, G3_C128 = 1 } g3_dtype;
+typedef enum { G3_DEVICE = 0, G3_HOST = 1 } g3_memory;
+typedef enum {
+    G3_APPLY_SUM = 0,     /* y = sum_{l=1}^{K} A(s_l) w_l              (eq. (product)) */
+    G3_APPLY_PERFREQ = 1  /* Y[:, l] = A(s_l) w_l for every l (check mode)             */
+} g3_apply_mode;
+
+typedef struct g3_ctx g3_ctx;
+typedef struct g3_freqs g3_freqs;
+typedef struct g3_tree g3_tree;
+typedef struct g3_near g3_near;
+typedef struct g3_factors g3_factors;
+
+/* Options of aca3_compress.  Zero-initialise and set what you need;
+ * a NULL pointer means all defaults. */
+typedef struct {
+    int face_rank_max;    /* cap of a face ACA's rank (0 = 48; max 64)                     */
+    int unbatched;        /* 1 = one block per launch sequence, host loop (plain baseline) */
+    int ctas_per_sm;      /* persistent CTAs per SM (0 = from the occupancy calculator)    */
+    int threads;          /* threads per CTA: 128 or 256 (0 = 256)                         */
+    int no_recompress;    /* 1 = keep raw ACA faces (no QR+SVD)                            */
+    int order_by_cost;    /* 1 (default when 0 is given: 1) = longest-first queue order    */
+    const int32_t* k1;    /* optional host array [n_far]: first frequency per block
+                             (unique-set index); NULL = 0 for every block                 */
+    const float* cost;    /* optional host array [n_far]: predicted cost per block used
+                             for the queue order instead of M_b * N_b                      */
+    double pool_factor;   /* initial factor-pool size multiplier (0 = 1.0)                 */
+} g3_opts;
+
+/* Statistics of one compression. */
+typedef struct {
+    int64_t n_far;            /* admissible blocks compressed                             */
+    int64_t entries;          /* ENTRY evaluations done (rows, columns, fibers)           */
+    int64_t crosses;          /* kept crosses, sum of r3 over blocks                     */
+    int64_t crosses_computed; /* crosses computed (incl. the dropped last one per block)  */
+    int64_t face_rank_sum;    /* sum of kept face ranks                                   */
+    int64_t factor_bytes;     /* bytes of kept factors (U, V, f)                          */
+    int64_t dense_bytes;      /* bytes of the same blocks stored densely (Ku freqs)       */
+    int32_t r3_max;           /* largest block rank                                       */
+    int32_t face_rank_max;    /* largest kept face rank                                   */
+    int32_t zero_blocks;      /* blocks detected as zero                                  */
+    int32_t capped_faces;     /* faces whose ACA hit face_rank_max                         */
+    int32_t pool_regrows;     /* times the factor pool had to be enlarged                 */
+    int32_t status_bits;      /* OR of device status flags                                */
+    double ms;                /* device time of the compression (CUDA events)             */
+} g3_stats;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL for the legacy default stream); the library enqueues all its
+ * work on it. */
+g3_status g3_create(int device, void* cuda_stream, g3_ctx** out);
+g3_status g3_set_stream(g3_ctx* ctx, void* cuda_stream);
+g3_status g3_destroy(g3_ctx* ctx);
+const char* g3_last_error(void);
+int g3_version(void);
+/* Number of kernel launches the library has issued on this context. */
+int64_t g3_launch_count(const g3_ctx* ctx);
+/* Name of the kernel that issued the most launches / the i-th kernel name
+ * and its launch count (diagnostics; i >= count returns NULL). */
+const char* g3_kernel_name(const g3_ctx* ctx, int i, int64_t* launches);
+
+/* ---- frequencies (Appendix A; multistep CQ) ------------------------------ */
+
+/* Multistep-CQ frequencies with the BDF2 generating function,
+ *   s_k = delta(zeta_k)/dt, delta(z) = (1 - z) + (1 - z)^2/2,
+ *   zeta_k = lambda exp(2 pi i k / K), k = 0..K-1.
+ * Unique set: k = 0..K/2 (K even); partner(k) = (K - k) mod K.
+ * Computed on the device in float64.  K >= 2 and even, 0 < lambda < 1, dt > 0. */
+g3_status g3_freqs_bdf2(g3_ctx* ctx, int K, double lambda, double dt, g3_freqs** out);
+
+/* gCQ contour points and weights (paper Appendix A) for time steps in
+ * [dt_min, dt_max], N_Q = NQ points:
+ *   q = dt_max/dt_min (implicit-Euler reading), k = (q - sqrt(2q-1))/(q + sqrt(2q-1)),
+ *   sigma_l = -K(k^2) + (l - 1/2) 4K(k^2)/NQ + i K(1-k^2)/2,
+ *   s_l = gamma(sigma_l), omega_l = -4K(k^2) gamma'(sigma_l) / (2 pi i NQ).
+ * Unique set: l = 0..NQ/2-1 (0-based); partner(l) = NQ - 1 - l.
+ * Returns G3_EINVAL for dt_max <= dt_min (q = 1 gives k = 0, the degenerate
+ * constant-step case the paper warns about) or odd NQ. */
+g3_status g3_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, g3_freqs** out);
+
+/* Sizes of a frequency set: K (all) and Ku (unique). */
+g3_status g3_freqs_info(const g3_freqs* f, int* K, int* Ku);
+/* Copy to host: s [2K] (c128, all K), omega [2K] or NULL (gCQ only; zeros for
+ * multistep CQ), uniq [Ku] (full index of each unique frequency) and partner [K]
+ * (full index of the conjugate); any output may be NULL. */
+g3_status g3_freqs_get(const g3_freqs* f, double* s, double* omega, int32_t* uniq, int32_t* partner);
+g3_status g3_freqs_free(g3_freqs* f);
+
+/* ---- cluster tree and block partition (Section 4, eq. (outerProd)) --------- */
+
+/* Build the balanced binary cluster tree and the geometric block partition
+ * of a flat-triangle surface mesh, and upload the element geometry to the
+ * device in cluster order.
+ *   verts [nv*3] float64 (x, y, z per vertex), tris [ne*3] int32 (outward,
+ *   counter-clockwise), leaf >= 1 (clusters with more elements are split),
+ *   eta > 0 (admissibility min(diam) <= eta * dist, dist > 0).
+ * Splitting: longest side of the cluster's vertex box (lowest axis on
+ * ties); stable sort by (centroid[axis], element index); left = first half.
+ * Admissibility in float64 without fused multiply-adds.  The result is
+ * bit-identical on every machine.  Degenerate triangles -> G3_EINVAL. */
+g3_status build_cluster_tree(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne,
+                             int leaf, double eta, g3_tree** out);
+g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near);
+/* Copy to host (any output may be NULL):
+ *   perm [ne]            cluster position -> original element index
+ *   nodes [n_nodes*4]    (begin, end, left, right) per preorder node; -1 = no child
+ *   boxes [n_nodes*6]    (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z)
+ *   blocks [n_blocks*5]  (row_begin, row_end, col_begin, col_end, admissible),
+ *                        cluster-order ranges, depth-first order
+ *   far_index [n_far]    block index of the i-th admissible block */
+g3_status g3_tree_get(const g3_tree* t, int32_t* perm, int32_t* nodes, double* boxes, int32_t* blocks,
+                      int32_t* far_index);
+g3_status g3_tree_free(g3_tree* t);
+
+/* ---- entries (Section 3, eq. (bie_semi_diri) / (bie_semi_indirect)) ------- */
+
+/* ENTRY(rows[n], cols[n], s_{kidx[m]}) for n pairs and nk frequency indices
+ * (indices into the FULL set 0..K-1; frequencies outside the unique set are
+ * evaluated as conj of their partner's entry) -> out [n*nk] c128 row-major
+ * (pair-major), host memory.  Evaluated by the same device routines the
+ * compression uses, in the given precision.  Diagnostic entry point. */
+g3_status g3_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                     g3_precision prec, const int32_t* rows, const int32_t* cols, int n, const int32_t* kidx,
+                     int nk, double* out);
+
+/* ---- near field ---------------------------------------------------------- */
+
+/* Assemble the dense near field: every entry of every non-admissible block
+ * at every unique frequency (self entries in float64).  Storage: complex64
+ * (G3_MIXED) or complex128 (G3_FP64), grouped by row cluster.  The paper
+ * keeps non-admissible blocks dense (last implementation remark, Section 4). */
+g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                        g3_precision prec, g3_near** out);
+g3_status g3_near_info(const g3_near* nf, int64_t* n_entries, int64_t* bytes, double* ms);
+/* Copy the near field of block `block` (index into the tree's block list; must
+ * be non-admissible) to host: out [M_b*N_b*Ku] c128, layout [k][i][j] with i, j
+ * local cluster-order indices. */
+g3_status g3_near_get_block(const g3_near* nf, int block, double* out);
+g3_status g3_near_free(g3_near* nf);
+
+/* ---- compression (Algorithm 1, eq. (norm), Section 4 remarks) -------------- */
+
+/* Compress every admissible block of `t` with the three-way ACA of
+ * Algorithm 1 on the unique frequencies of `f`:
+ *   face H_l by partial-pivot ACA of the residual face at k_l (tolerance
+ *   eps3/100) with QR+SVD recompression; pivot (i_l, j_l) = argmax |H_l| over
+ *   the dense expansion of the low-rank face; fiber f_l from the residual
+ *   fiber; ||C^(l)||_F by eq. (norm); stop when ||H_l|| ||f_l|| <= eps3 ||C^(l)||
+ *   (rank l - 1) or when all unique frequencies are used (rank l);
+ *   k_{l+1} = argmax of |f_l| over unused frequencies.
+ * All blocks run in one persistent launch unless opts->unbatched.
+ * kernel: G3_SLP or G3_DLP.  eps3 in (0, 1). */
+g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                        g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out);
+
+/* Same algorithm on ONE synthetic block A[i,j,k] = sum_{t<R} a[t,i] b[t,j] c[t,k]
+ * (host arrays a [R*M], b [R*N], c [R*Ku], c128, row t contiguous).  Used to
+ * check exact recovery of separable tensors. */
+g3_status aca3_compress_separable(g3_ctx* ctx, const double* a, const double* b, const double* c, int R, int M,
+                                  int N, int Ku, g3_precision prec, double eps3, const g3_opts* opts,
+                                  g3_factors** out);
+
+g3_status g3_factors_stats(const g3_factors* fa, g3_stats* out);
+/* Per admissible block i (in the tree's far order): r3[i] kept crosses. */
+g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3);
+/* Export block i's crosses to host.  Sizes first: call with U = V = fib = NULL
+ * to get r3 and the face ranks in face_ranks [r3] (if non-NULL).  Then:
+ *   U [sum_p M_b r_p] c128, column-major per cross, crosses concatenated;
+ *   V [sum_p N_b r_p] c128, likewise (face_p = U_p V_p^H);
+ *   fib [r3 * Ku] c128; piv [r3*3] int32 (i_l, j_l, k_l) local indices. */
+g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t* face_ranks, double* U, double* V,
+                               double* fib, int32_t* piv);
+g3_status g3_factors_free(g3_factors* fa);
+
+/* ---- application (eq. (product)) ------------------------------------------ */
+
+/* y = sum_{l=1}^{K} A(s_l) w_l with the compressed far field and the dense
+ * near field (near may be NULL: far field only; fa may be NULL: near only).
+ *   W [M*K] complex (dtype), column l = w_l, ORIGINAL element order;
+ *   Y [M] (SUM) or [M*K] (PERFREQ), complex (dtype), overwritten.
+ * mem = G3_DEVICE: W, Y are device pointers (caller-owned).
+ * mem = G3_HOST:   W, Y are host pointers; the library copies W in and Y out
+ *                  on the context's stream and synchronises before return.
+ * Frequencies outside the unique set use A(conj s) = conj A(s). */
+g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
+                    g3_dtype dtype, g3_apply_mode mode, g3_memory mem);
+/* Device time (ms) of the last apply on this context and its algorithmic
+ * bytes (near field, factors, W read once, Y written once). */
+g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* near_ms, int64_t* near_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* G3ACA_H */

@@ -1,0 +1,16 @@
+"""GB300-native three-way ACA for convolution-quadrature boundary elements.
+
+Python binding of the C ABI (include/g3aca.h) of the CUDA library built in
+`lib/libg3aca.so`.  Importing this package loads the library; if it has not
+been built the import fails (there is no CPU fallback).
+
+Entry points (same names as the C ABI):
+  build_cluster_tree, assemble_near, aca3_compress, apply_gcq
+plus frequency sets (g3_freqs_bdf2, g3_freqs_gcq), diagnostic entries
+(g3_entries) and a separable-tensor compression used by the tests.
+"""
+from ._binding import (  # noqa: F401
+    EXPORTED, LIB_PATH, Context, Factors, Freqs, G3Error, Near, Tree, aca3_compress,
+    aca3_compress_separable, apply_gcq, assemble_near, build_cluster_tree, freqs_from_spec,
+    g3_entries, g3_freqs_bdf2, g3_freqs_gcq,
+)

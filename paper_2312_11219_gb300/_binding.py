@@ -1,0 +1,383 @@
+"""ctypes binding of the C ABI in include/g3aca.h.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  The functions keep the C names (build_cluster_tree,
+assemble_near, aca3_compress, apply_gcq); handles are wrapped in small
+classes that free themselves.  PyTorch is used only for device buffers and
+the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libg3aca.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+KERNELS = {"slp": 0, "dlp": 1}
+SCHEMES = {"colloc7": 0, "galerkin4x4": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "G3_OK", -1: "G3_EINVAL", -2: "G3_ENOMEM", -3: "G3_ECUDA", -4: "G3_ETIMEOUT",
+          -5: "G3_ENOCONV", -6: "G3_EOVERFLOW", -7: "G3_EUNSUPPORTED"}
+
+_p = C.c_void_p
+_pp = C.POINTER(C.c_void_p)
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+
+
+class Opts(C.Structure):
+    _fields_ = [("face_rank_max", C.c_int), ("unbatched", C.c_int), ("ctas_per_sm", C.c_int),
+                ("threads", C.c_int), ("no_recompress", C.c_int), ("order_by_cost", C.c_int),
+                ("k1", _i32p), ("cost", C.POINTER(C.c_float)), ("pool_factor", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_far", C.c_int64), ("entries", C.c_int64), ("crosses", C.c_int64),
+                ("crosses_computed", C.c_int64), ("face_rank_sum", C.c_int64), ("factor_bytes", C.c_int64),
+                ("dense_bytes", C.c_int64), ("r3_max", C.c_int32), ("face_rank_max", C.c_int32),
+                ("zero_blocks", C.c_int32), ("capped_faces", C.c_int32), ("pool_regrows", C.c_int32),
+                ("status_bits", C.c_int32), ("ms", C.c_double)]
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_ci = C.c_int
+_sig("g3_create", _ci, _ci, _p, _pp)
+_sig("g3_set_stream", _ci, _p, _p)
+_sig("g3_destroy", _ci, _p)
+_sig("g3_last_error", C.c_char_p)
+_sig("g3_version", _ci)
+_sig("g3_launch_count", C.c_int64, _p)
+_sig("g3_kernel_name", C.c_char_p, _p, _ci, _i64p)
+_sig("g3_freqs_bdf2", _ci, _p, _ci, C.c_double, C.c_double, _pp)
+_sig("g3_freqs_gcq", _ci, _p, _ci, C.c_double, C.c_double, _pp)
+_sig("g3_freqs_info", _ci, _p, C.POINTER(_ci), C.POINTER(_ci))
+_sig("g3_freqs_get", _ci, _p, _dp, _dp, _i32p, _i32p)
+_sig("g3_freqs_free", _ci, _p)
+_sig("build_cluster_tree", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _pp)
+_sig("g3_tree_info", _ci, _p, *(C.POINTER(_ci),) * 5)
+_sig("g3_tree_get", _ci, _p, _i32p, _i32p, _dp, _i32p, _i32p)
+_sig("g3_tree_free", _ci, _p)
+_sig("g3_entries", _ci, _p, _p, _p, _ci, _ci, _ci, _i32p, _i32p, _ci, _i32p, _ci, _dp)
+_sig("assemble_near", _ci, _p, _p, _p, _ci, _ci, _ci, _pp)
+_sig("g3_near_info", _ci, _p, _i64p, _i64p, _dp)
+_sig("g3_near_get_block", _ci, _p, _ci, _dp)
+_sig("g3_near_free", _ci, _p)
+_sig("aca3_compress", _ci, _p, _p, _p, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _pp)
+_sig("aca3_compress_separable", _ci, _p, _dp, _dp, _dp, _ci, _ci, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _pp)
+_sig("g3_factors_stats", _ci, _p, C.POINTER(Stats))
+_sig("g3_factors_ranks", _ci, _p, _i32p)
+_sig("g3_factors_get_block", _ci, _p, _ci, _i32p, _i32p, _dp, _dp, _dp, _i32p)
+_sig("g3_factors_free", _ci, _p)
+_sig("apply_gcq", _ci, _p, _p, _p, _p, _p, _p, _ci, _ci, _ci)
+_sig("g3_apply_last", _ci, _p, _dp, _i64p, _dp, _i64p)
+
+EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
+            "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
+            "build_cluster_tree", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
+            "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_separable",
+            "g3_factors_stats", "g3_factors_ranks", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
+            "g3_apply_last"]
+
+
+class G3Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.g3_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise G3Error(st, where)
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, h, keep=()):
+        self.h = h
+        self._keep = keep   # objects this handle depends on (kept alive)
+
+    def close(self):
+        if self.h and self._free is not None:
+            type(self)._free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context(_Handle):
+    _free = _lib.g3_destroy
+
+    def __init__(self, device: int = 0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = C.c_void_p()
+        _check(_lib.g3_create(device, C.c_void_p(stream), C.byref(h)), "g3_create")
+        super().__init__(h)
+        self.device = device
+
+    def set_stream(self, stream) -> None:
+        _check(_lib.g3_set_stream(self.h, C.c_void_p(stream)), "g3_set_stream")
+
+    def launch_count(self) -> int:
+        return int(_lib.g3_launch_count(self.h))
+
+    def kernel_launches(self) -> dict:
+        out, i = {}, 0
+        n = C.c_int64()
+        while True:
+            name = _lib.g3_kernel_name(self.h, i, C.byref(n))
+            if name is None:
+                return out
+            out[name.decode()] = int(n.value)
+            i += 1
+
+    def last_apply(self) -> dict:
+        ms, nms = C.c_double(), C.c_double()
+        b, nb = C.c_int64(), C.c_int64()
+        _check(_lib.g3_apply_last(self.h, C.byref(ms), C.byref(b), C.byref(nms), C.byref(nb)), "g3_apply_last")
+        return {"ms": ms.value, "bytes": b.value, "near_ms": nms.value, "near_bytes": nb.value}
+
+
+class Freqs(_Handle):
+    _free = _lib.g3_freqs_free
+
+    def info(self) -> tuple[int, int]:
+        K, Ku = C.c_int(), C.c_int()
+        _check(_lib.g3_freqs_info(self.h, C.byref(K), C.byref(Ku)), "g3_freqs_info")
+        return K.value, Ku.value
+
+    def get(self) -> dict:
+        K, Ku = self.info()
+        s = np.zeros(2 * K)
+        w = np.zeros(2 * K)
+        u = np.zeros(Ku, dtype=np.int32)
+        p = np.zeros(K, dtype=np.int32)
+        _check(_lib.g3_freqs_get(self.h, _ptr(s, C.c_double), _ptr(w, C.c_double), _ptr(u, C.c_int32),
+                                 _ptr(p, C.c_int32)), "g3_freqs_get")
+        return {"s": s.view(np.complex128), "omega": w.view(np.complex128), "uniq": u, "partner": p}
+
+
+def g3_freqs_bdf2(ctx: Context, K: int, lam: float, dt: float) -> Freqs:
+    h = C.c_void_p()
+    _check(_lib.g3_freqs_bdf2(ctx.h, K, lam, dt, C.byref(h)), "g3_freqs_bdf2")
+    return Freqs(h, (ctx,))
+
+
+def g3_freqs_gcq(ctx: Context, NQ: int, dt_min: float, dt_max: float) -> Freqs:
+    h = C.c_void_p()
+    _check(_lib.g3_freqs_gcq(ctx.h, NQ, dt_min, dt_max, C.byref(h)), "g3_freqs_gcq")
+    return Freqs(h, (ctx,))
+
+
+def freqs_from_spec(ctx: Context, spec) -> Freqs:
+    if spec.kind == "bdf2":
+        return g3_freqs_bdf2(ctx, spec.K, spec.lam, spec.dt)
+    return g3_freqs_gcq(ctx, spec.K, spec.dt_min, spec.dt_max)
+
+
+class Tree(_Handle):
+    _free = _lib.g3_tree_free
+
+    def info(self) -> dict:
+        v = [C.c_int() for _ in range(5)]
+        _check(_lib.g3_tree_info(self.h, *[C.byref(x) for x in v]), "g3_tree_info")
+        return dict(zip(["ne", "n_nodes", "n_blocks", "n_far", "n_near"], [x.value for x in v]))
+
+    def get(self) -> dict:
+        i = self.info()
+        perm = np.zeros(i["ne"], dtype=np.int32)
+        nodes = np.zeros((i["n_nodes"], 4), dtype=np.int32)
+        boxes = np.zeros((i["n_nodes"], 6))
+        blocks = np.zeros((i["n_blocks"], 5), dtype=np.int32)
+        far = np.zeros(i["n_far"], dtype=np.int32)
+        _check(_lib.g3_tree_get(self.h, _ptr(perm, C.c_int32), _ptr(nodes, C.c_int32), _ptr(boxes, C.c_double),
+                                _ptr(blocks, C.c_int32), _ptr(far, C.c_int32)), "g3_tree_get")
+        return {"perm": perm, "nodes": nodes, "boxes": boxes, "blocks": blocks, "far_index": far}
+
+
+def build_cluster_tree(ctx: Context, verts, tris, leaf: int = 32, eta: float = 1.0) -> Tree:
+    v = _arr(verts, np.float64)
+    t = _arr(tris, np.int32)
+    h = C.c_void_p()
+    _check(_lib.build_cluster_tree(ctx.h, _ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0], leaf,
+                                   eta, C.byref(h)), "build_cluster_tree")
+    return Tree(h, (ctx,))
+
+
+def g3_entries(ctx: Context, tree: Tree, freqs: Freqs, kernel: str, rows, cols, kidx, prec: str = "fp64",
+               scheme: str = "colloc7") -> np.ndarray:
+    r = _arr(rows, np.int32)
+    c = _arr(cols, np.int32)
+    k = _arr(kidx, np.int32)
+    out = np.zeros(2 * r.size * k.size)
+    _check(_lib.g3_entries(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec],
+                           _ptr(r, C.c_int32), _ptr(c, C.c_int32), r.size, _ptr(k, C.c_int32), k.size,
+                           _ptr(out, C.c_double)), "g3_entries")
+    return out.view(np.complex128).reshape(r.size, k.size)
+
+
+class Near(_Handle):
+    _free = _lib.g3_near_free
+
+    def info(self) -> dict:
+        n, b, ms = C.c_int64(), C.c_int64(), C.c_double()
+        _check(_lib.g3_near_info(self.h, C.byref(n), C.byref(b), C.byref(ms)), "g3_near_info")
+        return {"entries": n.value, "bytes": b.value, "ms": ms.value}
+
+    def block(self, b: int, M: int, N: int, Ku: int) -> np.ndarray:
+        out = np.zeros(2 * M * N * Ku)
+        _check(_lib.g3_near_get_block(self.h, b, _ptr(out, C.c_double)), "g3_near_get_block")
+        return out.view(np.complex128).reshape(Ku, M, N)
+
+
+def assemble_near(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", scheme: str = "colloc7",
+                  prec: str = "mixed") -> Near:
+    h = C.c_void_p()
+    _check(_lib.assemble_near(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec],
+                              C.byref(h)), "assemble_near")
+    return Near(h, (ctx, tree, freqs))
+
+
+class Factors(_Handle):
+    _free = _lib.g3_factors_free
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(_lib.g3_factors_stats(self.h, C.byref(s)), "g3_factors_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def ranks(self) -> np.ndarray:
+        n = self.stats()["n_far"]
+        r = np.zeros(n, dtype=np.int32)
+        _check(_lib.g3_factors_ranks(self.h, _ptr(r, C.c_int32)), "g3_factors_ranks")
+        return r
+
+    def block(self, i: int, M: int, N: int, Ku: int) -> dict:
+        r3 = C.c_int32()
+        _check(_lib.g3_factors_get_block(self.h, i, C.byref(r3), None, None, None, None, None), "g3_factors_get_block")
+        n = r3.value
+        fr = np.zeros(max(n, 1), dtype=np.int32)
+        _check(_lib.g3_factors_get_block(self.h, i, C.byref(r3), _ptr(fr, C.c_int32), None, None, None, None),
+               "g3_factors_get_block")
+        fr = fr[:n]
+        U = np.zeros(2 * int(fr.sum()) * M + 2)
+        V = np.zeros(2 * int(fr.sum()) * N + 2)
+        F = np.zeros(2 * n * Ku + 2)
+        P = np.zeros(3 * n + 1, dtype=np.int32)
+        _check(_lib.g3_factors_get_block(self.h, i, C.byref(r3), _ptr(fr, C.c_int32), _ptr(U, C.c_double),
+                                         _ptr(V, C.c_double), _ptr(F, C.c_double), _ptr(P, C.c_int32)),
+               "g3_factors_get_block")
+        Uc = U[:-2].view(np.complex128)
+        Vc = V[:-2].view(np.complex128)
+        us, vs, ou, ov = [], [], 0, 0
+        for r in fr:
+            us.append(Uc[ou:ou + r * M].reshape(r, M).T)
+            vs.append(Vc[ov:ov + r * N].reshape(r, N).T)
+            ou += r * M
+            ov += r * N
+        return {"U": us, "V": vs, "f": F[:-2].view(np.complex128).reshape(n, Ku),
+                "piv": P[:-1].reshape(n, 3), "face_ranks": fr}
+
+
+def _opts(**kw) -> Opts:
+    o = Opts()
+    keep = []
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "k1":
+            a = _arr(v, np.int32)
+            keep.append(a)
+            o.k1 = _ptr(a, C.c_int32)
+        elif k == "cost":
+            a = _arr(v, np.float32)
+            keep.append(a)
+            o.cost = _ptr(a, C.c_float)
+        else:
+            setattr(o, k, v)
+    o._keep = keep
+    return o
+
+
+def aca3_compress(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", scheme: str = "colloc7",
+                  prec: str = "mixed", eps3: float = 1e-4, **opts) -> Factors:
+    o = _opts(**opts)
+    h = C.c_void_p()
+    _check(_lib.aca3_compress(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec], eps3,
+                              C.byref(o), C.byref(h)), "aca3_compress")
+    return Factors(h, (ctx, tree, freqs))
+
+
+def aca3_compress_separable(ctx: Context, a, b, c, prec: str = "fp64", eps3: float = 1e-6, **opts) -> Factors:
+    a = _arr(a, np.complex128)
+    b = _arr(b, np.complex128)
+    c = _arr(c, np.complex128)
+    R, M = a.shape
+    N = b.shape[1]
+    Ku = c.shape[1]
+    o = _opts(**opts)
+    h = C.c_void_p()
+    _check(_lib.aca3_compress_separable(ctx.h, _ptr(a.view(np.float64), C.c_double), _ptr(b.view(np.float64), C.c_double),
+                                        _ptr(c.view(np.float64), C.c_double), R, M, N, Ku, PRECISIONS[prec], eps3,
+                                        C.byref(o), C.byref(h)), "aca3_compress_separable")
+    return Factors(h, (ctx,))
+
+
+def apply_gcq(ctx: Context, tree: Tree, near: Near | None, factors: Factors | None, W, Y=None, mode: str = "sum"):
+    """y = sum_l A(s_l) w_l.  W: torch CUDA tensor (device path) or numpy array
+    (host path: copies inside the call), complex64 or complex128, shape [M, K]
+    with column l = w_l (the call reads W in column-major order)."""
+    mode_i = {"sum": 0, "perfreq": 1}[mode]
+    nh = near.h if near is not None else None
+    fh = factors.h if factors is not None else None
+    if isinstance(W, np.ndarray):
+        dt = 1 if W.dtype == np.complex128 else 0
+        Wc = np.asfortranarray(W)
+        M = W.shape[0]
+        out = np.zeros(M if mode_i == 0 else W.shape, dtype=W.dtype, order="F")
+        _check(_lib.apply_gcq(ctx.h, tree.h, nh, fh, Wc.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p),
+                              dt, mode_i, 1), "apply_gcq")
+        return out
+    import torch
+    if not (W.is_cuda and W.dtype in (torch.complex64, torch.complex128)):
+        raise TypeError("W must be a complex CUDA tensor or a numpy array")
+    dt = 1 if W.dtype == torch.complex128 else 0
+    Wt = W.t().contiguous()          # [K, M]: column l of W contiguous
+    M = W.shape[0]
+    if Y is None:
+        Y = torch.empty(M if mode_i == 0 else (W.shape[1], M), dtype=W.dtype, device=W.device)
+    _check(_lib.apply_gcq(ctx.h, tree.h, nh, fh, C.c_void_p(Wt.data_ptr()), C.c_void_p(Y.data_ptr()), dt, mode_i, 0),
+           "apply_gcq")
+    return Y if mode_i == 0 else Y.t()

@@ -1,0 +1,673 @@
+// C ABI entry points (include/g3aca.h): handle management, argument checks,
+// host<->device staging.  All compute runs in the kernels of g3_prep.cu,
+// g3_aca.cu and g3_apply.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "g3_internal.h"
+
+namespace g3 {
+
+static thread_local char t_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+}
+
+g3_status fail(g3_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+g3_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? G3_ENOMEM : G3_ECUDA;
+}
+
+}  // namespace g3
+
+using namespace g3;
+
+#define G3_CHECK(cond, ...)                                   \
+    do {                                                      \
+        if (!(cond)) return ::g3::fail(G3_EINVAL, __VA_ARGS__); \
+    } while (0)
+
+#define G3_TRY(expr)                       \
+    do {                                   \
+        g3_status st_ = (expr);            \
+        if (st_ != G3_OK) return st_;      \
+    } while (0)
+
+static g3_status use_device(const g3_ctx* ctx) {
+    G3_CUDA(cudaSetDevice(ctx->device));
+    return G3_OK;
+}
+
+extern "C" {
+
+const char* g3_last_error(void) { return g3::t_err; }
+int g3_version(void) { return G3ACA_VERSION; }
+
+g3_status g3_create(int device, void* cuda_stream, g3_ctx** out) {
+    G3_CHECK(out != nullptr, "g3_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    G3_CUDA(cudaGetDeviceCount(&n));
+    G3_CHECK(device >= 0 && device < n, "g3_create: device %d outside [0, %d)", device, n);
+    G3_CUDA(cudaSetDevice(device));
+    g3_ctx* c = new (std::nothrow) g3_ctx();
+    if (!c) return fail(G3_ENOMEM, "g3_create: out of host memory");
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaGetDeviceProperties");
+    }
+    c->n_sm = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    for (auto& ev : c->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            g3_destroy(c);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    e = c->status.alloc(64);
+    if (e != cudaSuccess) {
+        g3_destroy(c);
+        return cuda_fail(e, "status buffer");
+    }
+    g3_status st = gl_table(c);
+    if (st != G3_OK) {
+        g3_destroy(c);
+        return st;
+    }
+    *out = c;
+    return G3_OK;
+}
+
+g3_status g3_set_stream(g3_ctx* ctx, void* cuda_stream) {
+    G3_CHECK(ctx != nullptr, "g3_set_stream: ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return G3_OK;
+}
+
+g3_status g3_destroy(g3_ctx* ctx) {
+    if (!ctx) return G3_OK;
+    cudaSetDevice(ctx->device);
+    for (auto& ev : ctx->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete ctx;
+    return G3_OK;
+}
+
+int64_t g3_launch_count(const g3_ctx* ctx) { return ctx ? ctx->n_launch : 0; }
+
+const char* g3_kernel_name(const g3_ctx* ctx, int i, int64_t* launches) {
+    if (!ctx || i < 0 || i >= (int)ctx->launches.size()) return nullptr;
+    auto it = ctx->launches.begin();
+    std::advance(it, i);
+    if (launches) *launches = it->second;
+    return it->first.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// frequencies
+// ---------------------------------------------------------------------------
+
+static g3_status finish_freqs(g3_ctx* ctx, g3_freqs* f, const std::vector<double>& su_host) {
+    // su_host: unique set as interleaved pairs [2 Ku]
+    G3_CUDA(f->d_sd.alloc((size_t)f->Ku * 2 * sizeof(double)));
+    G3_CUDA(f->d_sf.alloc((size_t)f->Ku * 2 * sizeof(float)));
+    std::vector<float> sf(2 * (size_t)f->Ku);
+    for (size_t i = 0; i < sf.size(); ++i) sf[i] = (float)su_host[i];
+    G3_CUDA(cudaMemcpy(f->d_sd.p, su_host.data(), su_host.size() * sizeof(double), cudaMemcpyHostToDevice));
+    G3_CUDA(cudaMemcpy(f->d_sf.p, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    G3_CUDA(f->d_uniq.alloc(f->uniq.size() * sizeof(int)));
+    G3_CUDA(f->d_partner.alloc(f->partner.size() * sizeof(int)));
+    G3_CUDA(cudaMemcpy(f->d_uniq.p, f->uniq.data(), f->uniq.size() * sizeof(int), cudaMemcpyHostToDevice));
+    G3_CUDA(cudaMemcpy(f->d_partner.p, f->partner.data(), f->partner.size() * sizeof(int), cudaMemcpyHostToDevice));
+    double best = -1;
+    for (int u = 0; u < f->Ku; ++u) {
+        double a = std::hypot(su_host[2 * u], su_host[2 * u + 1]);
+        if (a > best) {
+            best = a;
+            f->k_maxabs = u;
+        }
+    }
+    (void)ctx;
+    return G3_OK;
+}
+
+g3_status g3_freqs_bdf2(g3_ctx* ctx, int K, double lambda, double dt, g3_freqs** out) {
+    G3_CHECK(ctx && out, "g3_freqs_bdf2: NULL argument");
+    *out = nullptr;
+    G3_CHECK(K >= 2 && K % 2 == 0 && K <= 2 * 255, "g3_freqs_bdf2: K = %d must be even in [2, 510]", K);
+    G3_CHECK(lambda > 0 && lambda < 1, "g3_freqs_bdf2: lambda = %g outside (0, 1)", lambda);
+    G3_CHECK(dt > 0 && std::isfinite(dt), "g3_freqs_bdf2: dt = %g must be positive", dt);
+    G3_TRY(use_device(ctx));
+    g3_freqs* f = new (std::nothrow) g3_freqs();
+    if (!f) return fail(G3_ENOMEM, "g3_freqs_bdf2: out of host memory");
+    f->ctx = ctx;
+    f->kind = 0;
+    f->K = K;
+    f->Ku = K / 2 + 1;
+    DevBuf sd, sf;
+    g3_status st = G3_OK;
+    if (sd.alloc((size_t)f->Ku * 2 * sizeof(double)) != cudaSuccess || sf.alloc((size_t)f->Ku * 2 * sizeof(float)) != cudaSuccess)
+        st = fail(G3_ENOMEM, "g3_freqs_bdf2: device allocation");
+    if (st == G3_OK) st = launch_freqs_bdf2(ctx, K, f->Ku, lambda, dt, sd.as<double>(), sf.as<float>());
+    std::vector<double> su(2 * (size_t)f->Ku);
+    if (st == G3_OK) {
+        cudaError_t e = cudaMemcpyAsync(su.data(), sd.p, su.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "g3_freqs_bdf2 copy");
+    }
+    if (st == G3_OK) {
+        f->s.assign(2 * (size_t)K, 0.0);
+        f->omega.assign(2 * (size_t)K, 0.0);
+        f->uniq.resize(f->Ku);
+        f->partner.resize(K);
+        for (int k = 0; k < K; ++k) f->partner[k] = (K - k) % K;
+        for (int u = 0; u < f->Ku; ++u) {
+            f->uniq[u] = u;
+            f->s[2 * u] = su[2 * u];
+            f->s[2 * u + 1] = su[2 * u + 1];
+        }
+        for (int k = f->Ku; k < K; ++k) {
+            f->s[2 * k] = su[2 * (K - k)];
+            f->s[2 * k + 1] = -su[2 * (K - k) + 1];
+        }
+        st = finish_freqs(ctx, f, su);
+    }
+    if (st != G3_OK) {
+        delete f;
+        return st;
+    }
+    *out = f;
+    return G3_OK;
+}
+
+g3_status g3_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, g3_freqs** out) {
+    G3_CHECK(ctx && out, "g3_freqs_gcq: NULL argument");
+    *out = nullptr;
+    G3_CHECK(NQ >= 2 && NQ % 2 == 0 && NQ <= 512, "g3_freqs_gcq: NQ = %d must be even in [2, 512]", NQ);
+    G3_CHECK(dt_min > 0 && std::isfinite(dt_max), "g3_freqs_gcq: dt_min must be positive");
+    G3_CHECK(dt_max > dt_min,
+             "g3_freqs_gcq: dt_max (%g) must exceed dt_min (%g); constant steps give q = 1, k = 0 where the contour "
+             "degenerates",
+             dt_max, dt_min);
+    G3_TRY(use_device(ctx));
+    g3_freqs* f = new (std::nothrow) g3_freqs();
+    if (!f) return fail(G3_ENOMEM, "g3_freqs_gcq: out of host memory");
+    f->ctx = ctx;
+    f->kind = 1;
+    f->K = NQ;
+    f->Ku = NQ / 2;
+    DevBuf ds, dw;
+    g3_status st = G3_OK;
+    if (ds.alloc((size_t)NQ * 2 * sizeof(double)) != cudaSuccess || dw.alloc((size_t)NQ * 2 * sizeof(double)) != cudaSuccess)
+        st = fail(G3_ENOMEM, "g3_freqs_gcq: device allocation");
+    if (st == G3_OK) st = launch_freqs_gcq(ctx, NQ, dt_min, dt_max, ds.as<double>(), dw.as<double>());
+    f->s.assign(2 * (size_t)NQ, 0.0);
+    f->omega.assign(2 * (size_t)NQ, 0.0);
+    if (st == G3_OK) {
+        cudaError_t e = cudaMemcpyAsync(f->s.data(), ds.p, f->s.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(f->omega.data(), dw.p, f->omega.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "g3_freqs_gcq copy");
+    }
+    if (st == G3_OK) {
+        f->uniq.resize(f->Ku);
+        f->partner.resize(NQ);
+        for (int l = 0; l < NQ; ++l) f->partner[l] = NQ - 1 - l;
+        std::vector<double> su(2 * (size_t)f->Ku);
+        for (int u = 0; u < f->Ku; ++u) {
+            f->uniq[u] = u;
+            su[2 * u] = f->s[2 * u];
+            su[2 * u + 1] = f->s[2 * u + 1];
+        }
+        for (double v : f->s)
+            if (!std::isfinite(v)) st = fail(G3_ECUDA, "g3_freqs_gcq: non-finite contour point");
+        if (st == G3_OK) st = finish_freqs(ctx, f, su);
+    }
+    if (st != G3_OK) {
+        delete f;
+        return st;
+    }
+    *out = f;
+    return G3_OK;
+}
+
+g3_status g3_freqs_info(const g3_freqs* f, int* K, int* Ku) {
+    G3_CHECK(f != nullptr, "g3_freqs_info: NULL handle");
+    if (K) *K = f->K;
+    if (Ku) *Ku = f->Ku;
+    return G3_OK;
+}
+
+g3_status g3_freqs_get(const g3_freqs* f, double* s, double* omega, int32_t* uniq, int32_t* partner) {
+    G3_CHECK(f != nullptr, "g3_freqs_get: NULL handle");
+    if (s) std::memcpy(s, f->s.data(), f->s.size() * sizeof(double));
+    if (omega) std::memcpy(omega, f->omega.data(), f->omega.size() * sizeof(double));
+    if (uniq) std::memcpy(uniq, f->uniq.data(), f->uniq.size() * sizeof(int32_t));
+    if (partner) std::memcpy(partner, f->partner.data(), f->partner.size() * sizeof(int32_t));
+    return G3_OK;
+}
+
+g3_status g3_freqs_free(g3_freqs* f) {
+    if (f) {
+        cudaSetDevice(f->ctx->device);
+        delete f;
+    }
+    return G3_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cluster tree
+// ---------------------------------------------------------------------------
+
+g3_status build_cluster_tree(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne, int leaf,
+                             double eta, g3_tree** out) {
+    G3_CHECK(ctx && verts && tris && out, "build_cluster_tree: NULL argument");
+    *out = nullptr;
+    G3_CHECK(nv >= 3 && ne >= 1, "build_cluster_tree: nv = %d, ne = %d", nv, ne);
+    G3_CHECK(leaf >= 1, "build_cluster_tree: leaf = %d must be >= 1", leaf);
+    G3_CHECK(eta > 0 && std::isfinite(eta), "build_cluster_tree: eta = %g must be positive", eta);
+    for (long long i = 0; i < 3LL * nv; ++i)
+        G3_CHECK(std::isfinite(verts[i]), "build_cluster_tree: non-finite vertex coordinate at %lld", i);
+    G3_TRY(use_device(ctx));
+    g3_tree* t = new (std::nothrow) g3_tree();
+    if (!t) return fail(G3_ENOMEM, "build_cluster_tree: out of host memory");
+    t->ctx = ctx;
+    t->ne = ne;
+    t->nv = nv;
+    t->leaf = leaf;
+    t->eta = eta;
+    t->verts.assign(verts, verts + 3 * (size_t)nv);
+    t->tris.assign(tris, tris + 3 * (size_t)ne);
+    g3_status st = build_tree_host(t);
+    if (st == G3_OK) {
+        if (t->d_perm.alloc(ne * sizeof(int)) != cudaSuccess) st = fail(G3_ENOMEM, "build_cluster_tree: perm");
+    }
+    if (st == G3_OK) {
+        cudaError_t e = cudaMemcpyAsync(t->d_perm.p, t->perm.data(), ne * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "build_cluster_tree: perm copy");
+    }
+    if (st == G3_OK) st = launch_geometry(ctx, t);
+    if (st != G3_OK) {
+        delete t;
+        return st;
+    }
+    *out = t;
+    return G3_OK;
+}
+
+g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near) {
+    G3_CHECK(t != nullptr, "g3_tree_info: NULL handle");
+    if (ne) *ne = t->ne;
+    if (n_nodes) *n_nodes = (int)(t->nodes.size() / 4);
+    if (n_blocks) *n_blocks = (int)(t->blocks.size() / 5);
+    if (n_far) *n_far = (int)t->far_index.size();
+    if (n_near) *n_near = (int)t->near_index.size();
+    return G3_OK;
+}
+
+g3_status g3_tree_get(const g3_tree* t, int32_t* perm, int32_t* nodes, double* boxes, int32_t* blocks,
+                      int32_t* far_index) {
+    G3_CHECK(t != nullptr, "g3_tree_get: NULL handle");
+    if (perm) std::memcpy(perm, t->perm.data(), t->perm.size() * sizeof(int32_t));
+    if (nodes) std::memcpy(nodes, t->nodes.data(), t->nodes.size() * sizeof(int32_t));
+    if (boxes) std::memcpy(boxes, t->boxes.data(), t->boxes.size() * sizeof(double));
+    if (blocks) std::memcpy(blocks, t->blocks.data(), t->blocks.size() * sizeof(int32_t));
+    if (far_index) std::memcpy(far_index, t->far_index.data(), t->far_index.size() * sizeof(int32_t));
+    return G3_OK;
+}
+
+g3_status g3_tree_free(g3_tree* t) {
+    if (t) {
+        cudaSetDevice(t->ctx->device);
+        delete t;
+    }
+    return G3_OK;
+}
+
+// ---------------------------------------------------------------------------
+// entries
+// ---------------------------------------------------------------------------
+
+static bool valid_kernel(int k) { return k == G3_SLP || k == G3_DLP; }
+static bool valid_prec(int p) { return p == G3_FP64 || p == G3_MIXED; }
+
+g3_status g3_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                     g3_precision prec, const int32_t* rows, const int32_t* cols, int n, const int32_t* kidx, int nk,
+                     double* out) {
+    G3_CHECK(ctx && t && f && out, "g3_entries: NULL argument");
+    G3_CHECK(n >= 0 && nk >= 0, "g3_entries: negative size");
+    G3_CHECK(n == 0 || (rows && cols), "g3_entries: rows/cols NULL");
+    G3_CHECK(nk == 0 || kidx, "g3_entries: kidx NULL");
+    G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "g3_entries: bad kernel or precision");
+    if (n == 0 || nk == 0) return G3_OK;
+    G3_TRY(use_device(ctx));
+    std::vector<int> inv(t->ne);
+    for (int p = 0; p < t->ne; ++p) inv[t->perm[p]] = p;
+    std::vector<int> r(n), c(n), ku(nk), cj(nk);
+    for (int i = 0; i < n; ++i) {
+        G3_CHECK(rows[i] >= 0 && rows[i] < t->ne && cols[i] >= 0 && cols[i] < t->ne,
+                 "g3_entries: pair %d = (%d, %d) outside [0, %d)", i, rows[i], cols[i], t->ne);
+        r[i] = inv[rows[i]];
+        c[i] = inv[cols[i]];
+    }
+    std::vector<int> upos(f->K, -1);
+    for (int u = 0; u < f->Ku; ++u) upos[f->uniq[u]] = u;
+    for (int m = 0; m < nk; ++m) {
+        G3_CHECK(kidx[m] >= 0 && kidx[m] < f->K, "g3_entries: kidx[%d] = %d outside [0, %d)", m, kidx[m], f->K);
+        if (upos[kidx[m]] >= 0) {
+            ku[m] = upos[kidx[m]];
+            cj[m] = 0;
+        } else {
+            ku[m] = upos[f->partner[kidx[m]]];
+            cj[m] = 1;
+        }
+    }
+    DevBuf dr, dc, dk, dj, dout;
+    G3_CUDA(dr.alloc(n * sizeof(int)));
+    G3_CUDA(dc.alloc(n * sizeof(int)));
+    G3_CUDA(dk.alloc(nk * sizeof(int)));
+    G3_CUDA(dj.alloc(nk * sizeof(int)));
+    G3_CUDA(dout.alloc((size_t)n * nk * 2 * sizeof(double)));
+    G3_CUDA(cudaMemcpyAsync(dr.p, r.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    G3_CUDA(cudaMemcpyAsync(dc.p, c.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    G3_CUDA(cudaMemcpyAsync(dk.p, ku.data(), nk * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    G3_CUDA(cudaMemcpyAsync(dj.p, cj.data(), nk * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    G3_TRY(launch_entries(ctx, t, f, kernel, scheme, prec, dr.as<int>(), dc.as<int>(), n, dk.as<int>(), dj.as<int>(), nk,
+                          dout.as<double>()));
+    G3_CUDA(cudaMemcpyAsync(out, dout.p, (size_t)n * nk * 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    G3_CUDA(cudaStreamSynchronize(ctx->stream));
+    return G3_OK;
+}
+
+// ---------------------------------------------------------------------------
+// near field
+// ---------------------------------------------------------------------------
+
+g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                        g3_precision prec, g3_near** out) {
+    G3_CHECK(ctx && t && f && out, "assemble_near: NULL argument");
+    *out = nullptr;
+    G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "assemble_near: bad kernel or precision");
+    G3_CHECK(scheme == G3_COLLOC7 || scheme == G3_GALERKIN4x4, "assemble_near: bad scheme");
+    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "assemble_near: only G3_COLLOC7 is implemented");
+    G3_TRY(use_device(ctx));
+    g3_near* nf = new (std::nothrow) g3_near();
+    if (!nf) return fail(G3_ENOMEM, "assemble_near: out of host memory");
+    nf->ctx = ctx;
+    nf->tree = t;
+    nf->freqs = f;
+    nf->prec = prec;
+    nf->kernel = kernel;
+    nf->Ku = f->Ku;
+    nf->K = f->K;
+    nf->order = t->near_index;
+    std::stable_sort(nf->order.begin(), nf->order.end(), [t](int a, int b) {
+        const int32_t* x = &t->blocks[5 * (size_t)a];
+        const int32_t* y = &t->blocks[5 * (size_t)b];
+        if (x[0] != y[0]) return x[0] < y[0];
+        return x[2] < y[2];
+    });
+    std::vector<BlockRange> rg;
+    long long off = 0;
+    for (size_t i = 0; i < nf->order.size(); ++i) {
+        const int32_t* x = &t->blocks[5 * (size_t)nf->order[i]];
+        rg.push_back(BlockRange{x[0], x[1], x[2], x[3]});
+        nf->offs.push_back(off);
+        off += (long long)(x[1] - x[0]) * (x[3] - x[2]) * f->Ku;
+        if (i == 0 || x[0] != rg[i - 1].rb) nf->row_start.push_back((int)i);
+    }
+    nf->row_start.push_back((int)nf->order.size());
+    nf->n_entries = off;
+    const size_t esz = prec == G3_MIXED ? 8 : 16;
+    g3_status st = G3_OK;
+    auto chk = [&](cudaError_t e, const char* w) {
+        if (st == G3_OK && e != cudaSuccess) st = cuda_fail(e, w);
+    };
+    chk(nf->data.alloc((size_t)off * esz), "assemble_near: near-field storage");
+    chk(nf->d_ranges.alloc(rg.size() * sizeof(BlockRange)), "assemble_near: ranges");
+    chk(nf->d_offs.alloc(nf->offs.size() * sizeof(long long)), "assemble_near: offsets");
+    chk(nf->d_row_start.alloc(nf->row_start.size() * sizeof(int)), "assemble_near: rows");
+    if (st == G3_OK && !rg.empty()) {
+        chk(cudaMemcpyAsync(nf->d_ranges.p, rg.data(), rg.size() * sizeof(BlockRange), cudaMemcpyHostToDevice, ctx->stream), "copy");
+        chk(cudaMemcpyAsync(nf->d_offs.p, nf->offs.data(), nf->offs.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream), "copy");
+        chk(cudaMemcpyAsync(nf->d_row_start.p, nf->row_start.data(), nf->row_start.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "copy");
+    }
+    if (st == G3_OK) chk(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
+    if (st == G3_OK) st = launch_near(ctx, t, f, nf, kernel, scheme);
+    if (st == G3_OK) chk(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
+    if (st == G3_OK) chk(cudaEventSynchronize(ctx->ev[1]), "assemble_near: kernel");
+    if (st == G3_OK) {
+        float ms = 0;
+        chk(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]), "event time");
+        nf->ms = ms;
+    }
+    if (st != G3_OK) {
+        delete nf;
+        return st;
+    }
+    *out = nf;
+    return G3_OK;
+}
+
+g3_status g3_near_info(const g3_near* nf, int64_t* n_entries, int64_t* bytes, double* ms) {
+    G3_CHECK(nf != nullptr, "g3_near_info: NULL handle");
+    if (n_entries) *n_entries = nf->n_entries;
+    if (bytes) *bytes = nf->n_entries * (nf->prec == G3_MIXED ? 8 : 16);
+    if (ms) *ms = nf->ms;
+    return G3_OK;
+}
+
+g3_status g3_near_get_block(const g3_near* nf, int block, double* out) {
+    G3_CHECK(nf && out, "g3_near_get_block: NULL argument");
+    const g3_tree* t = nf->tree;
+    G3_CHECK(block >= 0 && block < (int)(t->blocks.size() / 5), "g3_near_get_block: block %d out of range", block);
+    auto it = std::find(nf->order.begin(), nf->order.end(), block);
+    G3_CHECK(it != nf->order.end(), "g3_near_get_block: block %d is admissible", block);
+    const size_t pos = it - nf->order.begin();
+    const int32_t* x = &t->blocks[5 * (size_t)block];
+    const size_t n = (size_t)(x[1] - x[0]) * (x[3] - x[2]) * nf->Ku;
+    G3_TRY(use_device(nf->ctx));
+    if (nf->prec == G3_MIXED) {
+        std::vector<float> tmp(2 * n);
+        G3_CUDA(cudaMemcpy(tmp.data(), nf->data.as<float>() + 2 * nf->offs[pos], tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < tmp.size(); ++i) out[i] = tmp[i];
+    } else {
+        G3_CUDA(cudaMemcpy(out, nf->data.as<double>() + 2 * nf->offs[pos], 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return G3_OK;
+}
+
+g3_status g3_near_free(g3_near* nf) {
+    if (nf) {
+        cudaSetDevice(nf->ctx->device);
+        delete nf;
+    }
+    return G3_OK;
+}
+
+// ---------------------------------------------------------------------------
+// compression
+// ---------------------------------------------------------------------------
+
+static g3_opts defaults(const g3_opts* o) {
+    g3_opts d{};
+    if (o) d = *o;
+    return d;
+}
+
+g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                        g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out) {
+    G3_CHECK(ctx && t && f && out, "aca3_compress: NULL argument");
+    *out = nullptr;
+    G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "aca3_compress: bad kernel or precision");
+    G3_CHECK(scheme == G3_COLLOC7 || scheme == G3_GALERKIN4x4, "aca3_compress: bad scheme");
+    G3_CHECK(eps3 > 0 && eps3 < 1, "aca3_compress: eps3 = %g outside (0, 1)", eps3);
+    g3_opts o = defaults(opts);
+    G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress: face_rank_max = %d outside [0, 64]", o.face_rank_max);
+    G3_CHECK(o.threads == 0 || o.threads == 256, "aca3_compress: threads must be 0 or 256");
+    G3_TRY(use_device(ctx));
+    g3_factors* fa = new (std::nothrow) g3_factors();
+    if (!fa) return fail(G3_ENOMEM, "aca3_compress: out of host memory");
+    fa->ctx = ctx;
+    fa->tree = t;
+    fa->freqs = f;
+    fa->prec = prec;
+    fa->kernel = kernel;
+    fa->Ku = f->Ku;
+    fa->K = f->K;
+    g3_status st = run_aca(ctx, t, f, fa, kernel, scheme, eps3, o, nullptr, nullptr, nullptr, 0);
+    if (st != G3_OK) {
+        delete fa;
+        return st;
+    }
+    *out = fa;
+    return G3_OK;
+}
+
+g3_status aca3_compress_separable(g3_ctx* ctx, const double* a, const double* b, const double* c, int R, int M, int N,
+                                  int Ku, g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out) {
+    G3_CHECK(ctx && a && b && c && out, "aca3_compress_separable: NULL argument");
+    *out = nullptr;
+    G3_CHECK(R >= 1 && M >= 1 && N >= 1 && Ku >= 1 && Ku <= 256, "aca3_compress_separable: bad sizes");
+    G3_CHECK(valid_prec(prec), "aca3_compress_separable: bad precision");
+    G3_CHECK(eps3 > 0 && eps3 < 1, "aca3_compress_separable: eps3 = %g outside (0, 1)", eps3);
+    g3_opts o = defaults(opts);
+    G3_TRY(use_device(ctx));
+    g3_factors* fa = new (std::nothrow) g3_factors();
+    if (!fa) return fail(G3_ENOMEM, "aca3_compress_separable: out of host memory");
+    fa->ctx = ctx;
+    fa->prec = prec;
+    fa->kernel = G3_SEPARABLE;
+    fa->Ku = Ku;
+    fa->K = Ku;
+    fa->M_sep = M;
+    fa->N_sep = N;
+    g3_status st = run_aca(ctx, nullptr, nullptr, fa, G3_SEPARABLE, G3_COLLOC7, eps3, o, a, b, c, R);
+    if (st != G3_OK) {
+        delete fa;
+        return st;
+    }
+    *out = fa;
+    return G3_OK;
+}
+
+g3_status g3_factors_stats(const g3_factors* fa, g3_stats* out) {
+    G3_CHECK(fa && out, "g3_factors_stats: NULL argument");
+    *out = fa->stats;
+    return G3_OK;
+}
+
+g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3) {
+    G3_CHECK(fa && r3, "g3_factors_ranks: NULL argument");
+    std::memcpy(r3, fa->r3.data(), fa->r3.size() * sizeof(int32_t));
+    return G3_OK;
+}
+
+g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t* face_ranks, double* U, double* V,
+                               double* fib, int32_t* piv) {
+    G3_CHECK(fa != nullptr, "g3_factors_get_block: NULL handle");
+    G3_CHECK(i >= 0 && i < fa->n_far, "g3_factors_get_block: block %d outside [0, %d)", i, fa->n_far);
+    const int nc = fa->r3[i];
+    if (r3) *r3 = nc;
+    const BlockRange br = fa->ranges[i];
+    const int M = br.re - br.rb, N = br.ce - br.cb, Ku = fa->Ku;
+    G3_TRY(use_device(fa->ctx));
+    size_t ou = 0, ov = 0;
+    for (int p = 0; p < nc; ++p) {
+        const CrossRec& c = fa->rec[(size_t)i * fa->Cmax + p];
+        if (face_ranks) face_ranks[p] = c.r;
+        if (piv) {
+            piv[3 * p] = c.ip;
+            piv[3 * p + 1] = c.jp;
+            piv[3 * p + 2] = c.kp;
+        }
+        const size_t nu = (size_t)c.r * M, nv = (size_t)c.r * N;
+        const size_t tot = nu + nv + Ku;
+        std::vector<double> tmp(2 * tot);
+        if (fa->prec == G3_MIXED) {
+            std::vector<float> tf(2 * tot);
+            G3_CUDA(cudaMemcpy(tf.data(), fa->pool.as<float>() + 2 * c.off, tf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+            for (size_t k = 0; k < tf.size(); ++k) tmp[k] = tf[k];
+        } else {
+            G3_CUDA(cudaMemcpy(tmp.data(), fa->pool.as<double>() + 2 * c.off, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        if (U) std::memcpy(U + 2 * ou, tmp.data(), 2 * nu * sizeof(double));
+        if (V) std::memcpy(V + 2 * ov, tmp.data() + 2 * nu, 2 * nv * sizeof(double));
+        if (fib) std::memcpy(fib + 2 * (size_t)p * Ku, tmp.data() + 2 * (nu + nv), 2 * (size_t)Ku * sizeof(double));
+        ou += nu;
+        ov += nv;
+    }
+    return G3_OK;
+}
+
+g3_status g3_factors_free(g3_factors* fa) {
+    if (fa) {
+        cudaSetDevice(fa->ctx->device);
+        delete fa;
+    }
+    return G3_OK;
+}
+
+// ---------------------------------------------------------------------------
+// apply
+// ---------------------------------------------------------------------------
+
+g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
+                    g3_dtype dtype, g3_apply_mode mode, g3_memory mem) {
+    G3_CHECK(ctx && t && W && Y, "apply_gcq: NULL argument");
+    G3_CHECK(nf || fa, "apply_gcq: near field and factors are both NULL");
+    G3_CHECK(dtype == G3_C64 || dtype == G3_C128, "apply_gcq: bad dtype");
+    G3_CHECK(mode == G3_APPLY_SUM || mode == G3_APPLY_PERFREQ, "apply_gcq: bad mode");
+    G3_CHECK(mem == G3_DEVICE || mem == G3_HOST, "apply_gcq: bad memory kind");
+    G3_CHECK(!nf || nf->tree == t, "apply_gcq: near field built on another tree");
+    G3_CHECK(!fa || fa->tree == t, "apply_gcq: factors built on another tree");
+    G3_TRY(use_device(ctx));
+    const g3_freqs* f = nf ? nf->freqs : fa->freqs;
+    const size_t esz = dtype == G3_C128 ? 16 : 8;
+    const size_t wbytes = (size_t)t->ne * f->K * esz;
+    const size_t ybytes = (size_t)t->ne * (mode == G3_APPLY_SUM ? 1 : f->K) * esz;
+    if (mem == G3_DEVICE) return run_apply(ctx, t, nf, fa, W, Y, dtype, mode);
+    // host buffers: staged through context-owned device buffers (kept for reuse)
+    G3_CUDA(ctx->stage_w.ensure(wbytes));
+    G3_CUDA(ctx->stage_y.ensure(ybytes));
+    G3_CUDA(cudaMemcpyAsync(ctx->stage_w.p, W, wbytes, cudaMemcpyHostToDevice, ctx->stream));
+    G3_TRY(run_apply(ctx, t, nf, fa, ctx->stage_w.p, ctx->stage_y.p, dtype, mode));
+    G3_CUDA(cudaMemcpyAsync(Y, ctx->stage_y.p, ybytes, cudaMemcpyDeviceToHost, ctx->stream));
+    G3_CUDA(cudaStreamSynchronize(ctx->stream));
+    return G3_OK;
+}
+
+g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* near_ms, int64_t* near_bytes) {
+    G3_CHECK(ctx != nullptr, "g3_apply_last: NULL handle");
+    if (ms) *ms = ctx->last_apply_ms;
+    if (bytes) *bytes = ctx->last_apply_bytes;
+    if (near_ms) *near_ms = ctx->last_near_ms;
+    if (near_bytes) *near_bytes = ctx->last_near_bytes;
+    return G3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+// Application of the compressed three-way array to densities at all
+// frequencies (eq. (product)):
+//
+//   y = sum_{l=1}^{K} A(s_l) w_l
+//     = sum_near sum_k [Re A_k (w_k + w_k') + i Im A_k (w_k - w_k')]
+//       + sum_far sum_p [ U_p (V_p^H x_p) + conj(U_p (V_p^H zc_p)) ],
+//   x_p = sum_{k in unique} f_p[k] w_k ,  zc_p = sum_{k paired} f_p[k] conj(w_k'),
+//
+// where k' is the conjugate partner of the unique frequency k
+// (A(conj s) = conj A(s) for real geometry; Appendix A notes that half of the
+// frequencies suffice).  The near field is read once from HBM (the bound of
+// this step); each stored (unique-frequency) entry serves both members of a
+// conjugate pair.
+#include <algorithm>
+#include <vector>
+
+#include "g3_device.cuh"
+
+namespace g3 {
+
+// W (original order, column l = w_l, M x K column-major, complex TI) ->
+// Wf[k][p] = w_{uniq[k]}[perm[p]],  Wc[k][p] = w_{partner(uniq[k])}[perm[p]] or 0
+// (cluster order, frequency-major), and y := 0.
+template <class TI, class T>
+__global__ void k_apply_prep(int E, int K, int Ku, const int* __restrict__ perm, const int* __restrict__ uniq,
+                             const int* __restrict__ partner, const Cx<TI>* __restrict__ W, Cx<T>* __restrict__ Wf,
+                             Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < E) y[idx] = Cx<T>{0, 0};
+    if (idx >= (long long)Ku * E) return;
+    const int k = (int)(idx / E), p = (int)(idx % E);
+    const int e = perm[p];
+    const int l = uniq[k], lp = partner[l];
+    Cx<TI> a = W[(long long)l * E + e];
+    Wf[idx] = Cx<T>{(T)a.x, (T)a.y};
+    if (lp != l) {
+        Cx<TI> b = W[(long long)lp * E + e];
+        Wc[idx] = Cx<T>{(T)b.x, (T)b.y};
+    } else {
+        Wc[idx] = Cx<T>{0, 0};
+    }
+}
+
+// Near field: one CTA per (row cluster, frequency chunk).  For each near block
+// of the row, each thread owns entries e = tid + NT*m of the block and sums
+// Re A (w + w') + i Im A (w - w') over the chunk's frequencies; rows are
+// reduced in shared memory, then added to y.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, const BlockRange* __restrict__ ranges,
+                                                   const long long* __restrict__ offs, const int* __restrict__ row_start,
+                                                   int Ku, int kchunk, int E, const Cx<T>* __restrict__ Wf,
+                                                   const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ysh = reinterpret_cast<T*>(smem_raw);  // [2 * Mrow]
+    const int g = blockIdx.x;
+    const int k0 = blockIdx.y * kchunk, k1 = min(Ku, k0 + kchunk);
+    const int b0 = row_start[g], b1 = row_start[g + 1];
+    const int rb = ranges[b0].rb, Mrow = ranges[b0].re - ranges[b0].rb;
+    for (int i = threadIdx.x; i < 2 * Mrow; i += NT) ysh[i] = 0;
+    __syncthreads();
+    for (int b = b0; b < b1; ++b) {
+        const BlockRange br = ranges[b];
+        const int N = br.ce - br.cb;
+        const int MN = Mrow * N;
+        const Cx<T>* Ab = A + offs[b];
+        for (int e = threadIdx.x; e < MN; e += NT) {
+            const int i = e / N, j = br.cb + e % N;
+            T ax = 0, ay = 0;
+            int k = k0;
+            for (; k + 4 <= k1; k += 4) {
+                Cx<T> a[4], wf[4], wc[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = Ab[(long long)(k + u) * MN + e];
+                    wf[u] = Wf[(long long)(k + u) * E + j];
+                    wc[u] = Wc[(long long)(k + u) * E + j];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    // Re A (wf + wc) + i Im A (wf - wc)
+                    ax += a[u].x * (wf[u].x + wc[u].x) - a[u].y * (wf[u].y - wc[u].y);
+                    ay += a[u].x * (wf[u].y + wc[u].y) + a[u].y * (wf[u].x - wc[u].x);
+                }
+            }
+            for (; k < k1; ++k) {
+                Cx<T> a = Ab[(long long)k * MN + e], wf = Wf[(long long)k * E + j], wc = Wc[(long long)k * E + j];
+                ax += a.x * (wf.x + wc.x) - a.y * (wf.y - wc.y);
+                ay += a.x * (wf.y + wc.y) + a.y * (wf.x - wc.x);
+            }
+            atomicAdd(&ysh[2 * i], ax);
+            atomicAdd(&ysh[2 * i + 1], ay);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < Mrow; i += NT) {
+        atomicAdd(&y[rb + i].x, ysh[2 * i]);
+        atomicAdd(&y[rb + i].y, ysh[2 * i + 1]);
+    }
+}
+
+// Far field: one CTA per admissible block with r3 > 0.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
+                                                  const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
+                                                  const int* __restrict__ list, int Cmax, int Ku, int E,
+                                                  const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
+                                                  Cx<T>* __restrict__ y, int ysmem_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T>* fsh = reinterpret_cast<Cx<T>*>(smem_raw);  // [Ku]
+    Cx<T>* ab = fsh + Ku;                             // [2 * 64]: a[t], b[t]
+    T* ysh = reinterpret_cast<T*>(ab + 128);          // [2 * M] when M <= ysmem_max
+    const int blk = list[blockIdx.x];
+    const BlockRange br = ranges[blk];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const int nc = r3[blk];
+    const bool ysm = M <= ysmem_max;
+    const int lane = threadIdx.x & 31;
+    if (ysm)
+        for (int i = threadIdx.x; i < 2 * M; i += NT) ysh[i] = 0;
+    for (int p = 0; p < nc; ++p) {
+        const CrossRec c = rec[(size_t)blk * Cmax + p];
+        const Cx<T>* U = pool + c.off;
+        const Cx<T>* V = U + (long long)c.r * M;
+        const Cx<T>* F = U + (long long)c.r * (M + N);
+        for (int k = threadIdx.x; k < Ku; k += NT) fsh[k] = F[k];
+        for (int t = threadIdx.x; t < 2 * c.r; t += NT) ab[t] = Cx<T>{0, 0};
+        __syncthreads();
+        const int nj = (N + NT - 1) / NT * NT;
+        for (int j = threadIdx.x; j < nj; j += NT) {
+            Cx<T> x{0, 0}, zc{0, 0};
+            if (j < N) {
+                const int gj = br.cb + j;
+                for (int k = 0; k < Ku; ++k) {
+                    Cx<T> f = fsh[k];
+                    cfma(x, f, Wf[(long long)k * E + gj]);
+                    cfmac(zc, f, Wc[(long long)k * E + gj]);
+                }
+            }
+            for (int t = 0; t < c.r; ++t) {
+                Cx<T> v = j < N ? V[(long long)t * N + j] : Cx<T>{0, 0};
+                Cx<T> pa = cmulc(x, v), pb = cmulc(zc, v);  // conj(v) x, conj(v) zc
+                pa.x = warp_sum(pa.x);
+                pa.y = warp_sum(pa.y);
+                pb.x = warp_sum(pb.x);
+                pb.y = warp_sum(pb.y);
+                if (lane == 0) {
+                    atomicAdd(&ab[t].x, pa.x);
+                    atomicAdd(&ab[t].y, pa.y);
+                    atomicAdd(&ab[c.r + t].x, pb.x);
+                    atomicAdd(&ab[c.r + t].y, pb.y);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < M; i += NT) {
+            Cx<T> s1{0, 0}, s2{0, 0};
+            for (int t = 0; t < c.r; ++t) {
+                Cx<T> u = U[(long long)t * M + i];
+                cfma(s1, u, ab[t]);
+                cfma(s2, u, ab[c.r + t]);
+            }
+            T vx = s1.x + s2.x, vy = s1.y - s2.y;  // U a + conj(U b)
+            if (ysm) {
+                ysh[2 * i] += vx;
+                ysh[2 * i + 1] += vy;
+            } else {
+                atomicAdd(&y[br.rb + i].x, vx);
+                atomicAdd(&y[br.rb + i].y, vy);
+            }
+        }
+        __syncthreads();
+    }
+    if (ysm)
+        for (int i = threadIdx.x; i < M; i += NT) {
+            atomicAdd(&y[br.rb + i].x, ysh[2 * i]);
+            atomicAdd(&y[br.rb + i].y, ysh[2 * i + 1]);
+        }
+}
+
+template <class T, class TO>
+__global__ void k_apply_finish(int E, const int* __restrict__ perm, const Cx<T>* __restrict__ y, Cx<TO>* __restrict__ Y) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= E) return;
+    Cx<T> v = y[p];
+    Y[perm[p]] = Cx<TO>{(TO)v.x, (TO)v.y};
+}
+
+template <class T>
+static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
+                             void* Y, int dtype, const g3_freqs* f) {
+    const int E = t->ne, K = f->K, Ku = f->Ku;
+    const size_t nW = (size_t)Ku * E;
+    const size_t need = (2 * nW + E) * sizeof(Cx<T>) + 256;
+    G3_CUDA(ctx->scratch.ensure(need));
+    Cx<T>* Wf = ctx->scratch.as<Cx<T>>();
+    Cx<T>* Wc = Wf + nW;
+    Cx<T>* y = Wc + nW;
+    cudaEvent_t e0 = ctx->ev[2], e1 = ctx->ev[3], e2 = ctx->ev[4], e3 = ctx->ev[5];
+    G3_CUDA(cudaEventRecord(e0, ctx->stream));
+    {
+        long long tot = (long long)Ku * E;
+        int blocks = (int)((tot + 255) / 256);
+        if (dtype == G3_C128)
+            k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, y);
+        else
+            k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, y);
+        ctx->count("k_apply_prep");
+        G3_CUDA(cudaGetLastError());
+    }
+    G3_CUDA(cudaEventRecord(e1, ctx->stream));
+    if (nf && !nf->order.empty()) {
+        constexpr int NT = 256;
+        const int n_rows = (int)nf->row_start.size() - 1;
+        int ksplit = std::max(1, std::min(Ku, (8 * ctx->n_sm + n_rows - 1) / n_rows));
+        int kchunk = (Ku + ksplit - 1) / ksplit;
+        ksplit = (Ku + kchunk - 1) / kchunk;
+        int mrow = 0;
+        for (int g = 0; g < n_rows; ++g) {
+            const int32_t* r = &t->blocks[5 * (size_t)nf->order[nf->row_start[g]]];
+            mrow = std::max(mrow, r[1] - r[0]);
+        }
+        size_t smem = 2 * (size_t)mrow * sizeof(T);
+        dim3 grid(n_rows, ksplit);
+        k_apply_near<T, NT><<<grid, NT, smem, ctx->stream>>>(nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(),
+                                                             nf->d_offs.as<long long>(), nf->d_row_start.as<int>(), Ku,
+                                                             kchunk, E, Wf, Wc, y);
+        ctx->count("k_apply_near");
+        G3_CUDA(cudaGetLastError());
+    }
+    G3_CUDA(cudaEventRecord(e2, ctx->stream));
+    if (fa && fa->n_far > 0) {
+        std::vector<int> list;
+        for (int b = 0; b < fa->n_far; ++b)
+            if (fa->r3[b] > 0) list.push_back(b);
+        if (!list.empty()) {
+            DevBuf d_list, d_ranges;
+            G3_CUDA(d_list.alloc(list.size() * sizeof(int)));
+            G3_CUDA(d_ranges.alloc(fa->ranges.size() * sizeof(BlockRange)));
+            G3_CUDA(cudaMemcpyAsync(d_list.p, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+            G3_CUDA(cudaMemcpyAsync(d_ranges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+            constexpr int NT = 128;
+            const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
+            int mmax = 0;
+            for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
+            const int ym = std::min(mmax, ysmem_max);
+            size_t smem = (Ku + 128) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+            k_apply_far<T, NT><<<(int)list.size(), NT, smem, ctx->stream>>>(
+                fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges.as<BlockRange>(),
+                d_list.as<int>(), fa->Cmax, Ku, E, Wf, Wc, y, ym);
+            ctx->count("k_apply_far");
+            G3_CUDA(cudaGetLastError());
+            G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
+        }
+    }
+    {
+        int blocks = (E + 255) / 256;
+        if (dtype == G3_C128)
+            k_apply_finish<T, double><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<double>*)Y);
+        else
+            k_apply_finish<T, float><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<float>*)Y);
+        ctx->count("k_apply_finish");
+        G3_CUDA(cudaGetLastError());
+    }
+    G3_CUDA(cudaEventRecord(e3, ctx->stream));
+    G3_CUDA(cudaEventSynchronize(e3));
+    float ms_all = 0, ms_near = 0;
+    G3_CUDA(cudaEventElapsedTime(&ms_all, e0, e3));
+    G3_CUDA(cudaEventElapsedTime(&ms_near, e1, e2));
+    ctx->last_apply_ms = ms_all;
+    ctx->last_near_ms = ms_near;
+    const int64_t in_sz = dtype == G3_C128 ? 16 : 8;
+    int64_t near_bytes = nf ? nf->n_entries * (int64_t)sizeof(Cx<T>) : 0;
+    int64_t far_bytes = fa ? fa->stats.factor_bytes : 0;
+    ctx->last_near_bytes = near_bytes;
+    ctx->last_apply_bytes = near_bytes + far_bytes + (int64_t)E * K * in_sz + (int64_t)E * in_sz;
+    return G3_OK;
+}
+
+g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
+                    int dtype, int mode) {
+    if (mode != G3_APPLY_SUM) return fail(G3_EUNSUPPORTED, "apply_gcq: only G3_APPLY_SUM is implemented");
+    const g3_freqs* f = nf ? nf->freqs : fa->freqs;
+    const int prec = nf ? nf->prec : fa->prec;
+    if (nf && fa && (nf->prec != fa->prec || nf->freqs != fa->freqs))
+        return fail(G3_EINVAL, "apply_gcq: near field and factors differ in precision or frequency set");
+    if (prec == G3_MIXED) return run_apply_t<float>(ctx, t, nf, fa, W, Y, dtype, f);
+    return run_apply_t<double>(ctx, t, nf, fa, W, Y, dtype, f);
+}
+
+}  // namespace g3

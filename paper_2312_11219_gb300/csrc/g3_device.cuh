@@ -1,0 +1,268 @@
+// Device-side math of the three-way ACA path: complex helpers, the
+// Laplace-domain kernel exp(-s r)/(4 pi r) and its normal derivative, the
+// collocation entry (7-point rule) and the float64 singular self term.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "g3_internal.h"
+
+namespace g3 {
+
+#define G3_INV4PI 0.07957747154594767
+
+template <class T>
+struct Cx {
+    T x, y;
+};
+
+template <class T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> cmulc(Cx<T> a, Cx<T> b) {  // a * conj(b)
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> cconj(Cx<T> a) {
+    return {a.x, -a.y};
+}
+template <class T>
+__device__ __forceinline__ T cabs2(Cx<T> a) {
+    return a.x * a.x + a.y * a.y;
+}
+template <class T>
+__device__ __forceinline__ void cfma(Cx<T>& acc, Cx<T> a, Cx<T> b) {  // acc += a * b
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+template <class T>
+__device__ __forceinline__ void cfmac(Cx<T>& acc, Cx<T> a, Cx<T> b) {  // acc += a * conj(b)
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.y, b.x, acc.y);
+    acc.y = fma(-a.x, b.y, acc.y);
+}
+__device__ __forceinline__ Cx<double> cdiv(Cx<double> a, Cx<double> b) {
+    double d = b.x * b.x + b.y * b.y;
+    return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+template <class T, class S>
+__device__ __forceinline__ Cx<T> ccast(Cx<S> a) {
+    return {(T)a.x, (T)a.y};
+}
+
+// exp and sincos in the working precision.  float32: the hardware ex2 / sin /
+// cos approximations after an own Cody-Waite reduction of the phase modulo
+// 2 pi (two-part constant: 6.28125 is exact in 8 bits, the remainder carries
+// the rest), so the approximation sees |t| <= pi.  float64: CUDA's exp and
+// sincos.
+__device__ __forceinline__ float kexp(float x) { return __expf(x); }
+__device__ __forceinline__ double kexp(double x) { return exp(x); }
+__device__ __forceinline__ void ksincos(float t, float* s, float* c) {
+    float n = rintf(t * 0.15915494309189535f);
+    float r = fmaf(-n, 6.28125f, t);
+    r = fmaf(-n, 1.9353071795864769e-3f, r);
+    __sincosf(r, s, c);
+}
+__device__ __forceinline__ void ksincos(double t, double* s, double* c) { sincos(t, s, c); }
+__device__ __forceinline__ float krsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double krsqrt(double x) { return rsqrt(x); }
+
+// ---- geometry access in the working precision ---------------------------------
+// (x_i - c_j) for collocation: centroid difference, float32 via float-float.
+__device__ __forceinline__ void cdiff(const GeomF& g, int i, int j, float d[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float hi = g.ch[k * g.E + i] - g.ch[k * g.E + j];
+        float lo = g.cl[k * g.E + i] - g.cl[k * g.E + j];
+        d[k] = hi + lo;
+    }
+}
+__device__ __forceinline__ void cdiff(const GeomD& g, int i, int j, double d[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = g.c[k * g.E + i] - g.c[k * g.E + j];
+}
+template <class G>
+__device__ __forceinline__ auto qoff(const G& g, int q, int k, int j) {
+    return g.q[(q * 3 + k) * g.E + j];
+}
+template <class G>
+__device__ __forceinline__ auto qwt(const G& g, int q, int j) {
+    return g.w[q * g.E + j];
+}
+template <class G>
+__device__ __forceinline__ auto nrm(const G& g, int k, int j) {
+    return g.n[k * g.E + j];
+}
+
+// ---- collocation pair: geometry part of ENTRY(i, j, .) ---------------------------
+// For i != j the 7 quadrature points give distances r_q and amplitudes
+//   SLP: a_q = w_q / (4 pi r_q)
+//   DLP: a_q = w_q d / (4 pi r_q^3), d = (x_i - c_j) . n_j (plane distance)
+// and ENTRY(s) = sum_q a_q exp(-s r_q)            (SLP)
+//              = sum_q a_q exp(-s r_q) (1 + s r_q) (DLP).
+template <class T>
+struct Pair7 {
+    T r[7];
+    T a[7];
+};
+
+template <int KER, class G, class T>
+__device__ __forceinline__ void pair_setup(const G& g, int i, int j, Pair7<T>& p) {
+    T d[3];
+    cdiff(g, i, j, d);
+    T pd = 0;
+    if (KER == G3_DLP) pd = d[0] * nrm(g, 0, j) + d[1] * nrm(g, 1, j) + d[2] * nrm(g, 2, j);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        T rx = d[0] - qoff(g, q, 0, j);
+        T ry = d[1] - qoff(g, q, 1, j);
+        T rz = d[2] - qoff(g, q, 2, j);
+        T r2 = rx * rx + ry * ry + rz * rz;
+        T ri = krsqrt(r2);
+        p.r[q] = r2 * ri;
+        T w = qwt(g, q, j) * (T)G3_INV4PI;
+        if (KER == G3_DLP)
+            p.a[q] = w * pd * ri * ri * ri;
+        else
+            p.a[q] = w * ri;
+    }
+}
+
+template <int KER, class T>
+__device__ __forceinline__ Cx<T> pair_eval(const Pair7<T>& p, T sre, T sim) {
+    Cx<T> acc{0, 0};
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        T m = p.a[q] * kexp(-sre * p.r[q]);
+        T sn, cs;
+        ksincos(sim * p.r[q], &sn, &cs);
+        // exp(-s r) = m' (cos(sim r) - i sin(sim r))
+        if (KER == G3_DLP) {
+            T fr = (T)1 + sre * p.r[q];
+            T fi = sim * p.r[q];
+            // (fr + i fi)(cs - i sn)
+            acc.x += m * (fr * cs + fi * sn);
+            acc.y += m * (fi * cs - fr * sn);
+        } else {
+            acc.x += m * cs;
+            acc.y -= m * sn;
+        }
+    }
+    return acc;
+}
+
+// ---- float64 singular self entry V[i, i](s) (collocation at the centroid) ------
+// Polar coordinates about x_i over the three sub-triangles (x_i, a, b): with
+// d the distance of x_i to the edge line and phi the angle from the foot of
+// the perpendicular, r runs to rho(phi) = d / cos(phi), and the radial
+// integral is analytic:
+//   int_0^rho exp(-s r)/(4 pi r) r dr = rho g(s rho) / (4 pi),
+//   g(z) = (1 - exp(-z)) / z  (series for |z| < 0.1).
+// The angular integral uses 24-point Gauss-Legendre per edge.
+__device__ __forceinline__ Cx<double> g_expm1_over(Cx<double> z) {
+    double az = sqrt(z.x * z.x + z.y * z.y);
+    if (az < 0.1) {
+        // 1 - z/2 + z^2/6 - z^3/24 + ... = sum_{n>=0} (-z)^n / (n+1)!
+        Cx<double> term{1.0, 0.0}, sum{1.0, 0.0};
+        for (int n = 1; n <= 14; ++n) {
+            term = cmul(term, Cx<double>{-z.x, -z.y});
+            term.x /= (double)(n + 1);
+            term.y /= (double)(n + 1);
+            sum.x += term.x;
+            sum.y += term.y;
+        }
+        return sum;
+    }
+    double e = exp(-z.x), sn, cs;
+    sincos(z.y, &sn, &cs);
+    Cx<double> one_minus{1.0 - e * cs, e * sn};  // 1 - exp(-z)
+    return cdiv(one_minus, z);
+}
+
+__device__ inline Cx<double> slp_self_f64(const GeomD& g, int e, double sre, double sim) {
+    double x[3], v[3][3];
+    for (int k = 0; k < 3; ++k) x[k] = g.c[k * g.E + e];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) v[a][k] = g.v[(a * 3 + k) * g.E + e];
+    Cx<double> tot{0.0, 0.0};
+    for (int ed = 0; ed < 3; ++ed) {
+        const double* A = v[ed];
+        const double* B = v[(ed + 1) % 3];
+        double t[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double L = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        for (int k = 0; k < 3; ++k) t[k] /= L;
+        double t1 = (A[0] - x[0]) * t[0] + (A[1] - x[1]) * t[1] + (A[2] - x[2]) * t[2];
+        double t2 = (B[0] - x[0]) * t[0] + (B[1] - x[1]) * t[1] + (B[2] - x[2]) * t[2];
+        double f[3] = {A[0] - x[0] - t1 * t[0], A[1] - x[1] - t1 * t[1], A[2] - x[2] - t1 * t[2]};
+        double dd = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        double p1 = atan2(t1, dd), p2 = atan2(t2, dd);
+        double hm = 0.5 * (p2 - p1), hp = 0.5 * (p2 + p1);
+        for (int q = 0; q < 24; ++q) {
+            double ph = hm * g.gl[q] + hp;
+            double w = hm * g.gl[24 + q];
+            double rho = dd / cos(ph);
+            Cx<double> gz = g_expm1_over(Cx<double>{sre * rho, sim * rho});
+            tot.x += w * rho * gz.x;
+            tot.y += w * rho * gz.y;
+        }
+    }
+    tot.x *= G3_INV4PI;
+    tot.y *= G3_INV4PI;
+    return tot;
+}
+
+// ---- full collocation entry (any i, j) in working precision ----------------------
+// Self entries (i == j): float64 routine (SLP), 0 (DLP: x_i lies in the plane).
+template <int KER, class T>
+__device__ __forceinline__ Cx<T> colloc_entry(const GeomF& gf, const GeomD& gd, int i, int j, T sre, T sim,
+                                             double sre_d, double sim_d) {
+    if (i == j) {
+        if (KER == G3_DLP) return {0, 0};
+        Cx<double> v = slp_self_f64(gd, i, sre_d, sim_d);
+        return {(T)v.x, (T)v.y};
+    }
+    Pair7<T> p;
+    if constexpr (sizeof(T) == 4)
+        pair_setup<KER>(gf, i, j, p);
+    else
+        pair_setup<KER>(gd, i, j, p);
+    return pair_eval<KER>(p, sre, sim);
+}
+
+// ---- block reductions ------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// argmax with ties to the smallest index; val < 0 means "no candidate"
+struct ArgMax {
+    double v;
+    long long i;
+};
+__device__ __forceinline__ ArgMax amax_better(ArgMax a, ArgMax b) {
+    if (b.v > a.v) return b;
+    if (b.v == a.v && b.i < a.i && b.v >= 0) return b;
+    return a;
+}
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ArgMax b;
+        b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        a = amax_better(a, b);
+    }
+    return a;
+}
+
+}  // namespace g3

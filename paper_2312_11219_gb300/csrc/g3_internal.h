@@ -1,0 +1,218 @@
+// Internal declarations shared by the host C++ and the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/g3aca.h"
+
+namespace g3 {
+
+// ---- error handling -------------------------------------------------------
+
+void set_error(const char* fmt, ...);
+g3_status fail(g3_status st, const char* fmt, ...);
+g3_status cuda_fail(cudaError_t e, const char* what);
+
+#define G3_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return ::g3::cuda_fail(e_, #call);            \
+    } while (0)
+
+// ---- device status bits (written by kernels with atomicOr) ----------------
+enum : unsigned {
+    ST_POOL_OVERFLOW = 1u << 0,   // factor pool exhausted
+    ST_FACE_CAPPED = 1u << 1,     // a face ACA hit its rank cap
+    ST_CHOL_FALLBACK = 1u << 2,   // recompression skipped (Cholesky breakdown)
+    ST_BAD_INDEX = 1u << 3,       // an index check failed (access skipped)
+    ST_JACOBI_NOCONV = 1u << 4,   // Jacobi SVD hit its sweep limit
+};
+
+// ---- owned device buffer ----------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    cudaError_t ensure(size_t n) { return n <= bytes ? cudaSuccess : alloc(n); }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---- geometry views passed to kernels (cluster order, SoA) ------------------
+// float32 view: centroid as an unevaluated float-float sum (hi + lo) so that
+// centroid differences keep float32 relative accuracy; quadrature points as
+// float offsets from the centroid.
+struct GeomF {
+    int E;
+    const float* ch;   // [3][E]
+    const float* cl;   // [3][E]
+    const float* q;    // [7][3][E] 7-point rule offsets  y_q - c
+    const float* w;    // [7][E] weight * area
+    const float* n;    // [3][E] unit normal
+    const float* q4;   // [4][3][E] 4-point (Galerkin) rule offsets
+    const float* w4;   // [4][E]
+};
+struct GeomD {
+    int E;
+    const double* c;   // [3][E]
+    const double* q;   // [7][3][E]
+    const double* w;   // [7][E]
+    const double* n;   // [3][E]
+    const double* v;   // [3 vertices][3 coords][E] absolute vertex coordinates
+    const double* q4;  // [4][3][E]
+    const double* w4;  // [4][E]
+    const double* gl;  // 24-point Gauss-Legendre nodes [24] then weights [24] on [-1, 1]
+};
+
+// synthetic separable tensor sum_t a[t][i] b[t][j] c[t][k] (complex, interleaved)
+template <class T>
+struct SepView {
+    int R, M, N, Ku;
+    const T* a;  // [R][M][2]
+    const T* b;  // [R][N][2]
+    const T* c;  // [R][Ku][2]
+};
+
+struct BlockRange {
+    int rb, re, cb, ce;
+};
+
+// per-cross record written by the compression kernel
+struct CrossRec {
+    long long off;   // pool offset (complex elements) of U (M x r), then V (N x r), then f (Ku)
+    int r;           // face rank
+    int ip, jp, kp;  // pivot (local row, local column, unique-frequency index)
+};
+
+}  // namespace g3
+
+// ---- opaque handle definitions ---------------------------------------------
+
+struct g3_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_sm = 0;
+    size_t smem_optin = 0;
+    std::map<std::string, int64_t> launches;
+    int64_t n_launch = 0;
+    std::vector<std::string> names_cache;
+    g3::DevBuf gl;           // Gauss-Legendre table for self terms
+    g3::DevBuf scratch;      // apply scratch (cluster-order densities, partial y)
+    g3::DevBuf status;       // device status word(s)
+    g3::DevBuf stage_w, stage_y;  // device staging of host W / Y in apply_gcq
+    cudaEvent_t ev[6] = {};
+    double last_apply_ms = 0, last_near_ms = 0;
+    int64_t last_apply_bytes = 0, last_near_bytes = 0;
+    void count(const char* name, int64_t n = 1) {
+        launches[name] += n;
+        n_launch += n;
+    }
+};
+
+struct g3_freqs {
+    g3_ctx* ctx = nullptr;
+    int kind = 0;  // 0 = bdf2, 1 = gcq
+    int K = 0, Ku = 0;
+    std::vector<double> s;      // [2K]
+    std::vector<double> omega;  // [2K]
+    std::vector<int32_t> uniq;  // [Ku]
+    std::vector<int32_t> partner;  // [K]
+    int k_maxabs = 0;           // unique index of the largest |s|
+    g3::DevBuf d_sd;            // [Ku] double2 (unique set)
+    g3::DevBuf d_sf;            // [Ku] float2
+    g3::DevBuf d_uniq, d_partner;
+};
+
+struct g3_tree {
+    g3_ctx* ctx = nullptr;
+    int ne = 0, nv = 0, leaf = 0;
+    double eta = 0;
+    std::vector<double> verts;
+    std::vector<int32_t> tris;
+    std::vector<int32_t> perm;     // cluster position -> element
+    std::vector<int32_t> nodes;    // [n][4]
+    std::vector<double> boxes;     // [n][6]
+    std::vector<int32_t> blocks;   // [nb][5]
+    std::vector<int32_t> far_index, near_index;
+    int max_far_m = 0, max_far_n = 0;
+    // device
+    g3::DevBuf d_perm;             // int32 [ne]
+    g3::DevBuf d_geom_f, d_geom_d; // packed SoA arrays
+    g3::GeomF gf{};
+    g3::GeomD gd{};
+    g3::DevBuf d_far;              // BlockRange [n_far]
+};
+
+struct g3_near {
+    g3_ctx* ctx = nullptr;
+    const g3_tree* tree = nullptr;
+    int prec = 0, kernel = 0, Ku = 0, K = 0;
+    std::vector<int32_t> order;       // near blocks (tree block ids) sorted by (row, col)
+    std::vector<long long> offs;      // entry offset (complex elements) of each sorted block
+    std::vector<int32_t> row_start;   // [n_rows+1] into `order`, grouped by row cluster
+    long long n_entries = 0;
+    double ms = 0;
+    g3::DevBuf data;                  // complex64 or complex128
+    g3::DevBuf d_ranges;              // BlockRange per sorted near block
+    g3::DevBuf d_offs;                // long long per sorted near block
+    g3::DevBuf d_row_start;
+    const g3_freqs* freqs = nullptr;
+    std::vector<int32_t> partner_u;   // unique index -> full index of partner (or -1)
+};
+
+struct g3_factors {
+    g3_ctx* ctx = nullptr;
+    const g3_tree* tree = nullptr;
+    int prec = 0, kernel = 0, Ku = 0, K = 0, n_far = 0, Cmax = 0;
+    int M_sep = 0, N_sep = 0;          // separable mode: one block
+    g3::DevBuf pool;                   // complex (float or double) elements
+    long long pool_cap = 0;            // elements
+    g3::DevBuf d_rec;                  // CrossRec [n_far][Cmax]
+    g3::DevBuf d_r3;                   // int [n_far]
+    std::vector<int32_t> r3;
+    std::vector<g3::CrossRec> rec;     // host copy
+    std::vector<g3::BlockRange> ranges;
+    g3_stats stats{};
+    const g3_freqs* freqs = nullptr;
+};
+
+namespace g3 {
+
+// ---- launchers implemented in the .cu files ----------------------------------
+g3_status launch_freqs_bdf2(g3_ctx* ctx, int K, int Ku, double lam, double dt, double* d_sd, float* d_sf);
+g3_status launch_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, double* d_s, double* d_w);
+g3_status launch_geometry(g3_ctx* ctx, g3_tree* t);
+g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int kernel, int scheme, int prec,
+                         const int* d_rows, const int* d_cols, int n, const int* d_ku, const int* d_conj, int nk,
+                         double* d_out);
+g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf, int kernel, int scheme);
+g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel, int scheme,
+                  double eps3, const g3_opts& o, const void* sep_a, const void* sep_b, const void* sep_c, int sep_R);
+g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
+                    int dtype, int mode);
+g3_status gl_table(g3_ctx* ctx);
+
+// host tree builder (bit-exact specification)
+g3_status build_tree_host(g3_tree* t);
+
+}  // namespace g3

@@ -1,0 +1,392 @@
+// Frequencies, device geometry, diagnostic entries and near-field assembly.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "g3_device.cuh"
+
+namespace g3 {
+
+// ============================================================================
+// Frequencies (float64)
+// ============================================================================
+
+// Multistep CQ with the BDF2 generating function: s_k = delta(zeta_k) / dt,
+// delta(z) = (1 - z) + (1 - z)^2 / 2, zeta_k = lam exp(2 pi i k / K),
+// computed for the unique half k = 0..Ku-1.
+__global__ void k_freqs_bdf2(int K, int Ku, double lam, double dt, double2* sd, float2* sf) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Ku) return;
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)K, &sn, &cs);
+    double omr = 1.0 - lam * cs, omi = -lam * sn;             // 1 - zeta
+    double sqr = omr * omr - omi * omi, sqi = 2.0 * omr * omi;  // (1 - zeta)^2
+    double dr = omr + 0.5 * sqr, di = omi + 0.5 * sqi;
+    sd[k] = make_double2(dr / dt, di / dt);
+    sf[k] = make_float2((float)(dr / dt), (float)(di / dt));
+}
+
+// Complete elliptic integral of the first kind, parameter m: K = pi / (2 AGM(1, sqrt(1 - m))).
+__device__ double ellipk_agm(double m) {
+    double a = 1.0, b = sqrt(1.0 - m);
+    for (int it = 0; it < 40 && fabs(a - b) > 1e-16 * a; ++it) {
+        double an = 0.5 * (a + b);
+        b = sqrt(a * b);
+        a = an;
+    }
+    return 3.141592653589793 / (2.0 * a);
+}
+
+// Jacobi sn, cn, dn of a real argument by the arithmetic-geometric mean and
+// descending Landen recursion (Abramowitz & Stegun 16.4).
+__device__ void jacobi_real(double u, double m, double* sn, double* cn, double* dn) {
+    double a[24], c[24];
+    a[0] = 1.0;
+    double b = sqrt(1.0 - m);
+    c[0] = sqrt(m);
+    int N = 0;
+    while (N < 22 && fabs(c[N]) > 1e-16) {
+        double an = 0.5 * (a[N] + b);
+        double cn1 = 0.5 * (a[N] - b);
+        b = sqrt(a[N] * b);
+        ++N;
+        a[N] = an;
+        c[N] = cn1;
+    }
+    double phi = ldexp(1.0, N) * a[N] * u;
+    double phi_next = phi;
+    for (int n = N; n >= 1; --n) {
+        phi_next = phi;
+        phi = 0.5 * (phi + asin(c[n] * sin(phi) / a[n]));
+    }
+    *sn = sin(phi);
+    *cn = cos(phi);
+    *dn = (N == 0) ? 1.0 : cos(phi) / cos(phi_next - phi);
+}
+
+// gCQ contour (Appendix A) with q = dt_max / dt_min:
+//   s_l = gamma(sigma_l), omega_l = -4 K gamma'(sigma_l) / (2 pi i NQ),
+// sn/cn/dn at complex sigma from the addition formula with Jacobi's
+// imaginary transformation (A&S 16.21.1-3).
+__global__ void k_freqs_gcq(int NQ, double dt_min, double dt_max, double2* s_out, double2* w_out) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= NQ) return;
+    double q = dt_max / dt_min;
+    double r = sqrt(2.0 * q - 1.0);
+    double k = (q - r) / (q + r);
+    double m = k * k;
+    double Kk = ellipk_agm(m), Kp = ellipk_agm(1.0 - m);
+    double x = -Kk + ((double)(l + 1) - 0.5) * 4.0 * Kk / (double)NQ;
+    double y = 0.5 * Kp;
+    double s, c, d, s1, c1, d1;
+    jacobi_real(x, m, &s, &c, &d);
+    jacobi_real(y, 1.0 - m, &s1, &c1, &d1);
+    double den = c1 * c1 + m * s * s * s1 * s1;
+    Cx<double> sn{s * d1 / den, c * d * s1 * c1 / den};
+    Cx<double> cn{c * c1 / den, -s * d * s1 * d1 / den};
+    Cx<double> dn{d * c1 * d1 / den, -m * s * c * s1 / den};
+    double pref = 1.0 / (dt_min * (q - 1.0));
+    double ik = 1.0 / k;
+    Cx<double> num{ik + sn.x, sn.y}, dnm{ik - sn.x, -sn.y};
+    Cx<double> ratio = cdiv(num, dnm);
+    double2 sl = make_double2(pref * (r * ratio.x - 1.0), pref * r * ratio.y);
+    Cx<double> cd = cmul(cn, dn);
+    Cx<double> d2 = cmul(dnm, dnm);
+    Cx<double> gp = cdiv(cd, d2);
+    double fac = pref * r * 2.0 / k;
+    gp.x *= fac;
+    gp.y *= fac;
+    // omega = -4K gp / (2 pi i NQ) = (4K / (2 pi NQ)) * i * gp
+    double wfac = 4.0 * Kk / (2.0 * 3.141592653589793 * (double)NQ);
+    s_out[l] = sl;
+    w_out[l] = make_double2(-wfac * gp.y, wfac * gp.x);
+}
+
+g3_status launch_freqs_bdf2(g3_ctx* ctx, int K, int Ku, double lam, double dt, double* d_sd, float* d_sf) {
+    k_freqs_bdf2<<<(Ku + 127) / 128, 128, 0, ctx->stream>>>(K, Ku, lam, dt, (double2*)d_sd, (float2*)d_sf);
+    ctx->count("k_freqs_bdf2");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+g3_status launch_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, double* d_s, double* d_w) {
+    k_freqs_gcq<<<(NQ + 127) / 128, 128, 0, ctx->stream>>>(NQ, dt_min, dt_max, (double2*)d_s, (double2*)d_w);
+    ctx->count("k_freqs_gcq");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+// ============================================================================
+// Geometry in cluster order
+// ============================================================================
+
+// One thread per cluster position p (element e = perm[p]): centroid
+// ((v0 + v1) + v2) / 3, unit normal and area from the cross product, the
+// 7-point degree-5 rule (Radon; constants from their closed forms) and the
+// 4-point degree-3 conical-product rule (2-point Gauss-Jacobi in u with
+// weight (1 - u), 2-point Gauss-Legendre in v), as offsets from the centroid.
+__global__ void k_geometry(int ne, const double* __restrict__ verts, const int* __restrict__ tris,
+                           const int* __restrict__ perm, GeomF gf, GeomD gd, float* chw, float* clw, float* qw,
+                           float* ww, float* nw, float* q4w, float* w4w, double* cdw, double* qdw, double* wdw,
+                           double* ndw, double* vdw, double* q4dw, double* w4dw) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ne) return;
+    const int E = ne;
+    int e = perm[p];
+    double v[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) v[a][k] = verts[3 * (size_t)tris[3 * e + a] + k];
+    double c[3];
+    for (int k = 0; k < 3; ++k) c[k] = ((v[0][k] + v[1][k]) + v[2][k]) / 3.0;
+    double u[3], w[3];
+    for (int k = 0; k < 3; ++k) {
+        u[k] = v[1][k] - v[0][k];
+        w[k] = v[2][k] - v[0][k];
+    }
+    double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    double n2 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    double area = 0.5 * n2;
+    for (int k = 0; k < 3; ++k) {
+        float hi = (float)c[k];
+        chw[k * E + p] = hi;
+        clw[k * E + p] = (float)(c[k] - (double)hi);
+        cdw[k * E + p] = c[k];
+        double nk = cr[k] / n2;
+        nw[k * E + p] = (float)nk;
+        ndw[k * E + p] = nk;
+        for (int a = 0; a < 3; ++a) vdw[(a * 3 + k) * E + p] = v[a][k];
+    }
+    // 7-point rule
+    const double r15 = sqrt(15.0);
+    const double a1 = (6.0 - r15) / 21.0, b1 = (9.0 + 2.0 * r15) / 21.0;
+    const double a2 = (6.0 + r15) / 21.0, b2 = (9.0 - 2.0 * r15) / 21.0;
+    const double w1 = (155.0 - r15) / 1200.0, w2 = (155.0 + r15) / 1200.0;
+    const double t3 = 1.0 / 3.0;
+    const double L[7][3] = {{t3, t3, t3}, {a1, a1, b1}, {a1, b1, a1}, {b1, a1, a1},
+                            {a2, a2, b2}, {a2, b2, a2}, {b2, a2, a2}};
+    const double W[7] = {9.0 / 40.0, w1, w1, w1, w2, w2, w2};
+    for (int q = 0; q < 7; ++q) {
+        for (int k = 0; k < 3; ++k) {
+            double y = L[q][0] * v[0][k] + L[q][1] * v[1][k] + L[q][2] * v[2][k];
+            double off = y - c[k];
+            qw[(q * 3 + k) * E + p] = (float)off;
+            qdw[(q * 3 + k) * E + p] = off;
+        }
+        ww[q * E + p] = (float)(W[q] * area);
+        wdw[q * E + p] = W[q] * area;
+    }
+    // 4-point conical product rule
+    const double r6 = sqrt(6.0);
+    const double uu[2] = {(4.0 - r6) / 10.0, (4.0 + r6) / 10.0};
+    const double wu[2] = {(9.0 + r6) / 36.0, (9.0 - r6) / 36.0};
+    const double vv[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+    for (int ia = 0; ia < 2; ++ia)
+        for (int ib = 0; ib < 2; ++ib) {
+            int q = ia * 2 + ib;
+            double l1 = uu[ia], l2 = vv[ib] * (1.0 - uu[ia]), l0 = 1.0 - l1 - l2;
+            for (int k = 0; k < 3; ++k) {
+                double y = l0 * v[0][k] + l1 * v[1][k] + l2 * v[2][k];
+                q4w[(q * 3 + k) * E + p] = (float)(y - c[k]);
+                q4dw[(q * 3 + k) * E + p] = y - c[k];
+            }
+            double wq = 2.0 * wu[ia] * 0.5 * area;
+            w4w[q * E + p] = (float)wq;
+            w4dw[q * E + p] = wq;
+        }
+}
+
+g3_status launch_geometry(g3_ctx* ctx, g3_tree* t) {
+    const int E = t->ne;
+    // float arrays: ch 3, cl 3, q 21, w 7, n 3, q4 12, w4 4 = 53 per element
+    const size_t nf = 53;
+    // double arrays: c 3, q 21, w 7, n 3, v 9, q4 12, w4 4 = 59 per element
+    const size_t nd = 59;
+    G3_CUDA(t->d_geom_f.alloc(nf * E * sizeof(float)));
+    G3_CUDA(t->d_geom_d.alloc(nd * E * sizeof(double) + 48 * sizeof(double)));
+    float* F = t->d_geom_f.as<float>();
+    double* D = t->d_geom_d.as<double>();
+    GeomF gf{};
+    gf.E = E;
+    gf.ch = F;
+    gf.cl = F + 3 * (size_t)E;
+    gf.q = F + 6 * (size_t)E;
+    gf.w = F + 27 * (size_t)E;
+    gf.n = F + 34 * (size_t)E;
+    gf.q4 = F + 37 * (size_t)E;
+    gf.w4 = F + 49 * (size_t)E;
+    GeomD gd{};
+    gd.E = E;
+    gd.c = D;
+    gd.q = D + 3 * (size_t)E;
+    gd.w = D + 24 * (size_t)E;
+    gd.n = D + 31 * (size_t)E;
+    gd.v = D + 34 * (size_t)E;
+    gd.q4 = D + 43 * (size_t)E;
+    gd.w4 = D + 55 * (size_t)E;
+    gd.gl = D + 59 * (size_t)E;
+    G3_CUDA(cudaMemcpyAsync((void*)gd.gl, ctx->gl.p, 48 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    DevBuf dv, dt;
+    G3_CUDA(dv.alloc(t->verts.size() * sizeof(double)));
+    G3_CUDA(dt.alloc(t->tris.size() * sizeof(int)));
+    G3_CUDA(cudaMemcpyAsync(dv.p, t->verts.data(), t->verts.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    G3_CUDA(cudaMemcpyAsync(dt.p, t->tris.data(), t->tris.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    k_geometry<<<(E + 127) / 128, 128, 0, ctx->stream>>>(
+        E, dv.as<double>(), dt.as<int>(), t->d_perm.as<int>(), gf, gd, (float*)gf.ch, (float*)gf.cl, (float*)gf.q,
+        (float*)gf.w, (float*)gf.n, (float*)gf.q4, (float*)gf.w4, (double*)gd.c, (double*)gd.q, (double*)gd.w,
+        (double*)gd.n, (double*)gd.v, (double*)gd.q4, (double*)gd.w4);
+    ctx->count("k_geometry");
+    G3_CUDA(cudaGetLastError());
+    G3_CUDA(cudaStreamSynchronize(ctx->stream));  // dv, dt are released on return
+    t->gf = gf;
+    t->gd = gd;
+    return G3_OK;
+}
+
+// 24-point Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on
+// the Legendre recurrence), uploaded once per context.
+g3_status gl_table(g3_ctx* ctx) {
+    const int n = 24;
+    std::vector<double> tab(2 * n);
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            double dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) {
+                tab[i] = x;
+                tab[n + i] = 2.0 / ((1.0 - x * x) * dp * dp);
+                break;
+            }
+        }
+        // recompute the weight at the converged node
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        double dp = n * (x * p1 - p0) / (x * x - 1.0);
+        tab[i] = x;
+        tab[n + i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    G3_CUDA(ctx->gl.alloc(2 * n * sizeof(double)));
+    G3_CUDA(cudaMemcpy(ctx->gl.p, tab.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice));
+    return G3_OK;
+}
+
+// ============================================================================
+// Diagnostic entries
+// ============================================================================
+
+template <int KER, class T>
+__global__ void k_entries(GeomF gf, GeomD gd, const double2* __restrict__ sd, const int* __restrict__ rows,
+                          const int* __restrict__ cols, int n, const int* __restrict__ ku,
+                          const int* __restrict__ conj, int nk, double2* out) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * nk) return;
+    int pr = (int)(idx / nk), m = (int)(idx % nk);
+    int i = rows[pr], j = cols[pr];
+    double2 s = sd[ku[m]];
+    Cx<T> v = colloc_entry<KER, T>(gf, gd, i, j, (T)s.x, (T)s.y, s.x, s.y);
+    double im = conj[m] ? -(double)v.y : (double)v.y;
+    out[idx] = make_double2((double)v.x, im);
+}
+
+g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int kernel, int scheme, int prec,
+                         const int* d_rows, const int* d_cols, int n, const int* d_ku, const int* d_conj, int nk,
+                         double* d_out) {
+    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "g3_entries: only G3_COLLOC7 is implemented");
+    long long tot = (long long)n * nk;
+    int blocks = (int)((tot + 127) / 128);
+    if (tot == 0) return G3_OK;
+    const double2* sd = f->d_sd.as<double2>();
+    double2* out = (double2*)d_out;
+#define G3_ENT(K, T) k_entries<K, T><<<blocks, 128, 0, ctx->stream>>>(t->gf, t->gd, sd, d_rows, d_cols, n, d_ku, d_conj, nk, out)
+    if (kernel == G3_SLP && prec == G3_MIXED) G3_ENT(G3_SLP, float);
+    else if (kernel == G3_SLP) G3_ENT(G3_SLP, double);
+    else if (kernel == G3_DLP && prec == G3_MIXED) G3_ENT(G3_DLP, float);
+    else if (kernel == G3_DLP) G3_ENT(G3_DLP, double);
+    else return fail(G3_EINVAL, "g3_entries: kernel %d not supported", kernel);
+#undef G3_ENT
+    ctx->count("k_entries");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+// ============================================================================
+// Near-field assembly
+// ============================================================================
+
+// One CTA per (near block, chunk of KCH unique frequencies).  Threads run
+// over the M_b * N_b entries of the block; each thread sets up the pair
+// geometry once and evaluates it at the KCH frequencies.  Layout of a block:
+// [k][i][j] (frequency-major), complex, starting at offs[b].
+template <int KER, class T, int KCH>
+__global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2* __restrict__ sd,
+                                              const BlockRange* __restrict__ ranges,
+                                              const long long* __restrict__ offs, int Ku, Cx<T>* __restrict__ out) {
+    const int b = blockIdx.x;
+    const int k0 = blockIdx.y * KCH;
+    const BlockRange br = ranges[b];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const int MN = M * N;
+    const long long base = offs[b];
+    const int kn = min(KCH, Ku - k0);
+    for (int e = threadIdx.x; e < MN; e += blockDim.x) {
+        int i = br.rb + e / N, j = br.cb + e % N;
+        if (i == j) {
+            for (int kk = 0; kk < kn; ++kk) {
+                double2 s = sd[k0 + kk];
+                Cx<T> v{0, 0};
+                if (KER == G3_SLP) {
+                    Cx<double> d = slp_self_f64(gd, i, s.x, s.y);
+                    v = {(T)d.x, (T)d.y};
+                }
+                out[base + (long long)(k0 + kk) * MN + e] = v;
+            }
+            continue;
+        }
+        Pair7<T> p;
+        if constexpr (sizeof(T) == 4)
+            pair_setup<KER>(gf, i, j, p);
+        else
+            pair_setup<KER>(gd, i, j, p);
+        for (int kk = 0; kk < kn; ++kk) {
+            double2 s = sd[k0 + kk];
+            out[base + (long long)(k0 + kk) * MN + e] = pair_eval<KER, T>(p, (T)s.x, (T)s.y);
+        }
+    }
+}
+
+g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf, int kernel, int scheme) {
+    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "assemble_near: only G3_COLLOC7 is implemented");
+    const int nb = (int)nf->order.size();
+    if (nb == 0) return G3_OK;
+    constexpr int KCH = 16;
+    dim3 grid(nb, (f->Ku + KCH - 1) / KCH);
+    const double2* sd = f->d_sd.as<double2>();
+    const BlockRange* rg = nf->d_ranges.as<BlockRange>();
+    const long long* of = nf->d_offs.as<long long>();
+    if (nf->prec == G3_MIXED) {
+        Cx<float>* o = nf->data.as<Cx<float>>();
+        if (kernel == G3_SLP) k_near<G3_SLP, float, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+        else k_near<G3_DLP, float, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+    } else {
+        Cx<double>* o = nf->data.as<Cx<double>>();
+        if (kernel == G3_SLP) k_near<G3_SLP, double, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+        else k_near<G3_DLP, double, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+    }
+    ctx->count("k_near");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+}  // namespace g3

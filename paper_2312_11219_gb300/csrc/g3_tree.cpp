@@ -1,0 +1,198 @@
+// Balanced binary cluster tree and geometric block partition (host, float64).
+//
+// The paper builds the H-matrix on balanced cluster trees with a purely
+// geometric admissibility condition, one block structure shared by every
+// frequency (Section 4, paragraph after eq. (outerProd), and the first
+// implementation remark).  Its concrete rules are not given; this file
+// implements one fixed reading exactly (compiled without FMA contraction so
+// the result is identical on every host):
+//   * cluster box = bounding box of all vertices of the cluster's elements;
+//   * a cluster of n > leaf elements splits along the longest box side (lowest
+//     axis on ties): elements sorted by (centroid[axis], element index),
+//     centroid = ((v0 + v1) + v2) / 3, left child = first floor(n/2);
+//     node ids in preorder;
+//   * (t, s) admissible iff min(diam2(t), diam2(s)) <= eta^2 dist2(t, s) and
+//     dist2 > 0 (squared box diameter / box distance, summed x, y, z);
+//   * partition from (root, root): admissible -> far; two leaves -> near;
+//     two inner nodes -> (LL, LR, RL, RR); else split the inner one.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "g3_internal.h"
+
+namespace g3 {
+namespace {
+
+struct Builder {
+    const std::vector<double>& V;
+    const std::vector<int32_t>& T;
+    int leaf;
+    double eta;
+    std::vector<double> cen;        // [ne][3]
+    std::vector<double> tmin, tmax; // [ne][3]
+    std::vector<int32_t> perm;
+    std::vector<int32_t> nodes;     // begin, end, left, right
+    std::vector<double> boxes;      // lo[3], hi[3]
+    std::vector<int32_t> blocks;
+
+    Builder(const std::vector<double>& v, const std::vector<int32_t>& t, int lf, double e)
+        : V(v), T(t), leaf(lf), eta(e) {}
+
+    void prepare(int ne) {
+        cen.resize(3 * (size_t)ne);
+        tmin.resize(3 * (size_t)ne);
+        tmax.resize(3 * (size_t)ne);
+        for (int e = 0; e < ne; ++e) {
+            const double* a = &V[3 * (size_t)T[3 * e + 0]];
+            const double* b = &V[3 * (size_t)T[3 * e + 1]];
+            const double* c = &V[3 * (size_t)T[3 * e + 2]];
+            for (int d = 0; d < 3; ++d) {
+                double sum = a[d] + b[d];
+                sum = sum + c[d];
+                cen[3 * e + d] = sum / 3.0;
+                tmin[3 * e + d] = std::min(std::min(a[d], b[d]), c[d]);
+                tmax[3 * e + d] = std::max(std::max(a[d], b[d]), c[d]);
+            }
+        }
+    }
+
+    // idx: elements of this node (already in the parent's sorted order)
+    int node(std::vector<int32_t>& idx, int start) {
+        const int nid = (int)(nodes.size() / 4);
+        const int n = (int)idx.size();
+        nodes.insert(nodes.end(), {start, start + n, -1, -1});
+        double lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = tmin[3 * (size_t)idx[0] + d];
+            hi[d] = tmax[3 * (size_t)idx[0] + d];
+        }
+        for (int e : idx)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], tmin[3 * (size_t)e + d]);
+                hi[d] = std::max(hi[d], tmax[3 * (size_t)e + d]);
+            }
+        boxes.insert(boxes.end(), {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]});
+        if (n > leaf) {
+            int axis = 0;
+            double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+            for (int d = 1; d < 3; ++d)
+                if (ext[d] > ext[axis]) axis = d;
+            const double* c = cen.data();
+            std::sort(idx.begin(), idx.end(), [c, axis](int32_t x, int32_t y) {
+                double cx = c[3 * (size_t)x + axis], cy = c[3 * (size_t)y + axis];
+                if (cx < cy) return true;
+                if (cy < cx) return false;
+                return x < y;
+            });
+            const int h = n / 2;
+            std::vector<int32_t> L(idx.begin(), idx.begin() + h), R(idx.begin() + h, idx.end());
+            std::vector<int32_t>().swap(idx);
+            int l = node(L, start);
+            int r = node(R, start + h);
+            nodes[4 * (size_t)nid + 2] = l;
+            nodes[4 * (size_t)nid + 3] = r;
+        } else {
+            perm.insert(perm.end(), idx.begin(), idx.end());
+        }
+        return nid;
+    }
+
+    static double diam2(const double* b) {
+        double dx = b[3] - b[0];
+        double dy = b[4] - b[1];
+        double dz = b[5] - b[2];
+        double a = dx * dx;
+        double bb = dy * dy;
+        double cc = dz * dz;
+        return (a + bb) + cc;
+    }
+    static double dist2(const double* t, const double* s) {
+        double acc = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double g = std::max(0.0, std::max(s[d] - t[3 + d], t[d] - s[3 + d]));
+            double gg = g * g;
+            acc = acc + gg;
+        }
+        return acc;
+    }
+    bool admissible(int t, int s) const {
+        const double* bt = &boxes[6 * (size_t)t];
+        const double* bs = &boxes[6 * (size_t)s];
+        double d2 = dist2(bt, bs);
+        double e2 = eta * eta;
+        double rhs = e2 * d2;
+        return std::min(diam2(bt), diam2(bs)) <= rhs && d2 > 0.0;
+    }
+    void part(int t, int s) {
+        auto N = [&](int id, int k) { return nodes[4 * (size_t)id + k]; };
+        if (admissible(t, s)) {
+            blocks.insert(blocks.end(), {N(t, 0), N(t, 1), N(s, 0), N(s, 1), 1});
+            return;
+        }
+        bool tl = N(t, 2) < 0, sl = N(s, 2) < 0;
+        if (tl && sl) {
+            blocks.insert(blocks.end(), {N(t, 0), N(t, 1), N(s, 0), N(s, 1), 0});
+        } else if (!tl && !sl) {
+            part(N(t, 2), N(s, 2));
+            part(N(t, 2), N(s, 3));
+            part(N(t, 3), N(s, 2));
+            part(N(t, 3), N(s, 3));
+        } else if (tl) {
+            part(t, N(s, 2));
+            part(t, N(s, 3));
+        } else {
+            part(N(t, 2), s);
+            part(N(t, 3), s);
+        }
+    }
+};
+
+}  // namespace
+
+g3_status build_tree_host(g3_tree* t) {
+    const int ne = t->ne;
+    for (int e = 0; e < ne; ++e) {
+        for (int k = 0; k < 3; ++k) {
+            int v = t->tris[3 * (size_t)e + k];
+            if (v < 0 || v >= t->nv) return fail(G3_EINVAL, "tris[%d] references vertex %d outside [0, %d)", e, v, t->nv);
+        }
+        // degenerate triangle check: zero cross product
+        const double* a = &t->verts[3 * (size_t)t->tris[3 * e]];
+        const double* b = &t->verts[3 * (size_t)t->tris[3 * e + 1]];
+        const double* c = &t->verts[3 * (size_t)t->tris[3 * e + 2]];
+        double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        double w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        if (!(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2] > 0.0))
+            return fail(G3_EINVAL, "triangle %d is degenerate", e);
+    }
+    Builder B(t->verts, t->tris, t->leaf, t->eta);
+    B.prepare(ne);
+    std::vector<int32_t> all(ne);
+    std::iota(all.begin(), all.end(), 0);
+    B.perm.reserve(ne);
+    B.node(all, 0);
+    B.part(0, 0);
+    t->perm.swap(B.perm);
+    t->nodes.swap(B.nodes);
+    t->boxes.swap(B.boxes);
+    t->blocks.swap(B.blocks);
+    const int nb = (int)(t->blocks.size() / 5);
+    t->far_index.clear();
+    t->near_index.clear();
+    t->max_far_m = t->max_far_n = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int32_t* r = &t->blocks[5 * (size_t)b];
+        if (r[4]) {
+            t->far_index.push_back(b);
+            t->max_far_m = std::max(t->max_far_m, r[1] - r[0]);
+            t->max_far_n = std::max(t->max_far_n, r[3] - r[2]);
+        } else {
+            t->near_index.push_back(b);
+        }
+    }
+    return G3_OK;
+}
+
+}  // namespace g3
