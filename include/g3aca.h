@@ -107,6 +107,10 @@ typedef struct {
     const float* cost;    /* optional host array [n_far]: predicted cost per block used
                              for the queue order instead of M_b * N_b                      */
     double pool_factor;   /* initial factor-pool size multiplier (0 = 1.0)                 */
+    double eps_face;      /* face ACA / recompression tolerance (0 = eps3/100; in G3_MIXED
+                             not below 1e-5, the relative noise of float32 entries)        */
+    int max_blocks;       /* > 0: compress only the first max_blocks admissible blocks (far
+                             order); the others get rank 0 (bounded timing samples)         */
 } g3_opts;
 
 /* Statistics of one compression. */
@@ -125,6 +129,11 @@ typedef struct {
     int32_t pool_regrows;     /* times the factor pool had to be enlarged                 */
     int32_t status_bits;      /* OR of device status flags                                */
     double ms;                /* device time of the compression (CUDA events)             */
+    int64_t phase_cycles[7];  /* SM cycles summed over CTAs: face ACA, recompression,
+                                 factor formation, pivot search, fiber, eq. (norm), next k  */
+    int32_t ctas;             /* persistent CTAs launched                                 */
+    int32_t recompress_fallbacks; /* faces kept unrecompressed (Cholesky breakdown)       */
+    int32_t blocks_run;       /* blocks compressed (n_far unless opts->max_blocks)        */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */
@@ -247,6 +256,9 @@ g3_status aca3_compress_separable(g3_ctx* ctx, const double* a, const double* b,
 g3_status g3_factors_stats(const g3_factors* fa, g3_stats* out);
 /* Per admissible block i (in the tree's far order): r3[i] kept crosses. */
 g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3);
+/* Per admissible block i: SM clock cycles its compression took (one CTA;
+ * diagnostics and cost labels for scheduling). */
+g3_status g3_factors_block_cycles(const g3_factors* fa, int64_t* cycles);
 /* Export block i's crosses to host.  Sizes first: call with U = V = fib = NULL
  * to get r3 and the face ranks in face_ranks [r3] (if non-NULL).  Then:
  *   U [sum_p M_b r_p] c128, column-major per cross, crosses concatenated;
@@ -271,6 +283,15 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
 /* Device time (ms) of the last apply on this context and its algorithmic
  * bytes (near field, factors, W read once, Y written once). */
 g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* near_ms, int64_t* near_bytes);
+
+/* ---- diagnostics -------------------------------------------------------------- */
+
+/* Throughput of one arithmetic pipe on the context's GPU (no counterpart in
+ * the paper; it measures the denominators of the compression's ALU roofline):
+ * kind 0 = float32 FMA, 1 = rsqrt.approx, 2 = ex2.approx, 3 = sin.approx,
+ * 4 = cos.approx (special-function unit), 5 = float64 FMA.  Writes
+ * operations per second (one FMA = one operation) and the timed ms. */
+g3_status g3_peak(g3_ctx* ctx, int kind, double* ops_per_s, double* ms);
 
 #ifdef __cplusplus
 }

@@ -39,7 +39,8 @@ _i64p = C.POINTER(C.c_int64)
 class Opts(C.Structure):
     _fields_ = [("face_rank_max", C.c_int), ("unbatched", C.c_int), ("ctas_per_sm", C.c_int),
                 ("threads", C.c_int), ("no_recompress", C.c_int), ("order_by_cost", C.c_int),
-                ("k1", _i32p), ("cost", C.POINTER(C.c_float)), ("pool_factor", C.c_double)]
+                ("k1", _i32p), ("cost", C.POINTER(C.c_float)), ("pool_factor", C.c_double),
+                ("eps_face", C.c_double), ("max_blocks", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -47,7 +48,8 @@ class Stats(C.Structure):
                 ("crosses_computed", C.c_int64), ("face_rank_sum", C.c_int64), ("factor_bytes", C.c_int64),
                 ("dense_bytes", C.c_int64), ("r3_max", C.c_int32), ("face_rank_max", C.c_int32),
                 ("zero_blocks", C.c_int32), ("capped_faces", C.c_int32), ("pool_regrows", C.c_int32),
-                ("status_bits", C.c_int32), ("ms", C.c_double)]
+                ("status_bits", C.c_int32), ("ms", C.c_double), ("phase_cycles", C.c_int64 * 7),
+                ("ctas", C.c_int32), ("recompress_fallbacks", C.c_int32), ("blocks_run", C.c_int32)]
 
 
 def _sig(name, res, *args):
@@ -84,16 +86,18 @@ _sig("aca3_compress_separable", _ci, _p, _dp, _dp, _dp, _ci, _ci, _ci, _ci, _ci,
 _sig("g3_factors_stats", _ci, _p, C.POINTER(Stats))
 _sig("g3_factors_ranks", _ci, _p, _i32p)
 _sig("g3_factors_get_block", _ci, _p, _ci, _i32p, _i32p, _dp, _dp, _dp, _i32p)
+_sig("g3_factors_block_cycles", _ci, _p, _i64p)
 _sig("g3_factors_free", _ci, _p)
 _sig("apply_gcq", _ci, _p, _p, _p, _p, _p, _p, _ci, _ci, _ci)
 _sig("g3_apply_last", _ci, _p, _dp, _i64p, _dp, _i64p)
+_sig("g3_peak", _ci, _p, _ci, _dp, _dp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
             "build_cluster_tree", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_separable",
-            "g3_factors_stats", "g3_factors_ranks", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
-            "g3_apply_last"]
+            "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
+            "g3_apply_last", "g3_peak"]
 
 
 class G3Error(RuntimeError):
@@ -162,6 +166,13 @@ class Context(_Handle):
                 return out
             out[name.decode()] = int(n.value)
             i += 1
+
+    def peak(self, kind: str) -> float:
+        """Measured operations/s of one pipe: ffma, rsqrt, ex2, sin, cos, dfma."""
+        k = ["ffma", "rsqrt", "ex2", "sin", "cos", "dfma"].index(kind)
+        ops, ms = C.c_double(), C.c_double()
+        _check(_lib.g3_peak(self.h, k, C.byref(ops), C.byref(ms)), "g3_peak")
+        return ops.value
 
     def last_apply(self) -> dict:
         ms, nms = C.c_double(), C.c_double()
@@ -276,13 +287,22 @@ class Factors(_Handle):
     def stats(self) -> dict:
         s = Stats()
         _check(_lib.g3_factors_stats(self.h, C.byref(s)), "g3_factors_stats")
-        return {f: getattr(s, f) for f, _ in Stats._fields_}
+        out = {f: getattr(s, f) for f, _ in Stats._fields_}
+        out["phase_cycles"] = dict(zip(["face", "recompress", "formation", "pivot", "fiber", "norm", "next_k"],
+                                       list(s.phase_cycles)))
+        return out
 
     def ranks(self) -> np.ndarray:
         n = self.stats()["n_far"]
         r = np.zeros(n, dtype=np.int32)
         _check(_lib.g3_factors_ranks(self.h, _ptr(r, C.c_int32)), "g3_factors_ranks")
         return r
+
+    def block_cycles(self) -> np.ndarray:
+        n = self.stats()["n_far"]
+        c = np.zeros(n, dtype=np.int64)
+        _check(_lib.g3_factors_block_cycles(self.h, _ptr(c, C.c_int64)), "g3_factors_block_cycles")
+        return c
 
     def block(self, i: int, M: int, N: int, Ku: int) -> dict:
         r3 = C.c_int32()

@@ -60,7 +60,9 @@ struct AcaArgs {
     unsigned long long* pool_ctr;
     CrossRec* rec;
     int* r3;
+    long long* blk_cycles;   // [n_far] SM cycles spent on each block
     unsigned long long* counters;  // [0] entries [1] crosses computed [2] zero blocks [3] capped faces
+                                   // [8..14] clock cycles per phase (thread 0 of each CTA)
     unsigned* status;
     char* ws;
     size_t ws_stride;
@@ -79,6 +81,9 @@ struct Ws {
     Cx<double>* TU;
     Cx<double>* TV;
     Cx<double>* fib;      // [Ku]
+    long long* colU;      // [Cmax * RF] flattened column tables (when they exceed shared memory)
+    long long* colV;
+    short* colP;
 };
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -91,9 +96,12 @@ __host__ __device__ inline size_t ws_bytes(int RF, int Mmax, int Nmax, int Cmax,
     add((size_t)RF * Nmax * sizeof(Cx<T>));
     add((size_t)Nmax * sizeof(Cx<T>));
     add((size_t)Mmax);
-    add((size_t)Cmax * RF * sizeof(Cx<T>));
+    add((size_t)(Cmax + 1) * RF * sizeof(Cx<T>));
     for (int i = 0; i < 4; ++i) add((size_t)RF * RF * sizeof(Cx<double>));
     add((size_t)Ku * sizeof(Cx<double>));
+    add((size_t)Cmax * RF * sizeof(long long));
+    add((size_t)Cmax * RF * sizeof(long long));
+    add((size_t)Cmax * RF * sizeof(short));
     return b;
 }
 
@@ -110,12 +118,15 @@ __device__ inline Ws<T> ws_carve(char* base, int RF, int Mmax, int Nmax, int Cma
     w.vw = (Cx<T>*)take((size_t)RF * Nmax * sizeof(Cx<T>));
     w.row = (Cx<T>*)take((size_t)Nmax * sizeof(Cx<T>));
     w.used = (unsigned char*)take((size_t)Mmax);
-    w.pre = (Cx<T>*)take((size_t)Cmax * RF * sizeof(Cx<T>));
+    w.pre = (Cx<T>*)take((size_t)(Cmax + 1) * RF * sizeof(Cx<T>));
     w.RU = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
     w.RV = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
     w.TU = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
     w.TV = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
     w.fib = (Cx<double>*)take((size_t)Ku * sizeof(Cx<double>));
+    w.colU = (long long*)take((size_t)Cmax * RF * sizeof(long long));
+    w.colV = (long long*)take((size_t)Cmax * RF * sizeof(long long));
+    w.colP = (short*)take((size_t)Cmax * RF * sizeof(short));
     return w;
 }
 
@@ -201,15 +212,234 @@ __device__ __forceinline__ const Cx<T>* Fp(const AcaArgs<T>& A, const BlockSh<T>
     return A.pool + S.off[p] + (long long)S.r[p] * (S.M + S.N);
 }
 
+// ---- one quadrature point of a collocation entry --------------------------------------
+template <int KER, class G, class T>
+__device__ __forceinline__ Cx<T> colloc_q(const G& g, int i, int j, int q, T sre, T sim) {
+    T d[3];
+    cdiff(g, i, j, d);
+    T rx = d[0] - qoff(g, q, 0, j), ry = d[1] - qoff(g, q, 1, j), rz = d[2] - qoff(g, q, 2, j);
+    T r2 = rx * rx + ry * ry + rz * rz;
+    T ri = krsqrt(r2);
+    T r = r2 * ri;
+    T wq = qwt(g, q, j) * (T)G3_INV4PI;
+    T amp;
+    if (KER == G3_DLP) {
+        T pd = d[0] * nrm(g, 0, j) + d[1] * nrm(g, 1, j) + d[2] * nrm(g, 2, j);
+        amp = wq * pd * ri * ri * ri;
+    } else {
+        amp = wq * ri;
+    }
+    T m = amp * kexp(-sre * r);
+    T sn, cs;
+    ksincos(sim * r, &sn, &cs);
+    if (KER == G3_DLP) {
+        T fr = (T)1 + sre * r, fi = sim * r;
+        return {m * (fr * cs + fi * sn), m * (fi * cs - fr * sn)};
+    }
+    return {m * cs, -m * sn};
+}
+
+// part `part` of a gang of G threads evaluating ENTRY(gi, gj, k): with G >= 8
+// each of the first 7 parts evaluates one quadrature point; otherwise part 0
+// evaluates the whole entry.  The gang sum is the entry.
+template <int KER, class T>
+__device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, int k, int part, int G) {
+    if constexpr (KER == G3_SEPARABLE) {
+        return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
+    } else {
+        if (G >= 8) {
+            if (part >= 7) return Cx<T>{0, 0};
+            double2 s = A.sd[k];
+            if constexpr (sizeof(T) == 4)
+                return colloc_q<KER>(A.gf, gi, gj, part, (T)s.x, (T)s.y);
+            else
+                return colloc_q<KER>(A.gd, gi, gj, part, (T)s.x, (T)s.y);
+        }
+        return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
+    }
+}
+
+template <class T>
+__device__ __forceinline__ Cx<T> shfl_xor_c(Cx<T> v, int o) {
+    return Cx<T>{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
+
+// gang size: the largest power of two <= 32 with L * G <= 2 NT
+template <int NT>
+__device__ __forceinline__ int gang_size(int L) {
+    int G = 1;
+    while (G < 32 && L * (G * 2) <= 2 * NT) G *= 2;
+    return G;
+}
+
+// Per-face tables of the earlier crosses' columns, flattened over (p, t):
+//   colU[c] / colV[c]  pool offsets of U_p[:, t] / V_p[:, t],  colP[c] = p,
+// and the coefficient vector of the line being evaluated (coef[c], then the
+// current face's m coefficients).  In shared memory when they fit, else in
+// the workspace.
+constexpr int TABMAX = 1024;    // flattened columns kept in shared memory
+constexpr int ROWMAX = 1024;    // row buffer length kept in shared memory
+
+template <class T>
+struct FaceTab {
+    const long long* colU;
+    const long long* colV;
+    const short* colP;
+    Cx<T>* coef;
+    Cx<T>* row;
+    int ncol;   // sum of the earlier crosses' ranks
+};
+
+template <class T>
+__device__ __forceinline__ size_t facetab_smem_bytes() {
+    return 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) + (TABMAX + RF_MAX) * sizeof(Cx<T>) +
+           ROWMAX * sizeof(Cx<T>) + 64;
+}
+
+template <class T, int NT>
+__device__ FaceTab<T> facetab_build(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, unsigned char* arena) {
+    FaceTab<T> F;
+    const int nc = S.ncross;
+    F.ncol = S.pre[nc];
+    const bool sm = F.ncol <= TABMAX;
+    unsigned char* p = arena;
+    long long* cu = sm ? reinterpret_cast<long long*>(p) : w.colU;
+    p += TABMAX * sizeof(long long);
+    long long* cv = sm ? reinterpret_cast<long long*>(p) : w.colV;
+    p += TABMAX * sizeof(long long);
+    short* cp = sm ? reinterpret_cast<short*>(p) : w.colP;
+    p += TABMAX * sizeof(short);
+    p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    F.coef = sm ? reinterpret_cast<Cx<T>*>(p) : w.pre;
+    p += (TABMAX + RF_MAX) * sizeof(Cx<T>);
+    F.row = S.N <= ROWMAX ? reinterpret_cast<Cx<T>*>(p) : w.row;
+    for (int c = threadIdx.x; c < F.ncol; c += NT) {
+        int q = 0;
+        while (S.pre[q + 1] <= c) ++q;
+        const int t = c - S.pre[q];
+        cu[c] = S.off[q] + (long long)t * S.M;
+        cv[c] = S.off[q] + (long long)S.r[q] * S.M + (long long)t * S.N;
+        cp[c] = (short)q;
+    }
+    F.colU = cu;
+    F.colV = cv;
+    F.colP = cp;
+    return F;
+}
+
+// coefficients of a row (f_p[kf] U_p[t][fix], then u_t[fix] of the current face)
+// or of a column (f_p[kf] conj(V_p[t][fix]), then conj(v_t[fix]))
+template <class T, int NT, bool ROW>
+__device__ void line_coeffs(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int fix,
+                            int m) {
+    for (int c = threadIdx.x; c < F.ncol + m; c += NT) {
+        if (c < F.ncol) {
+            const Cx<T> fk = S.fk[F.colP[c]];
+            F.coef[c] = ROW ? cmul(fk, A.pool[F.colU[c] + fix]) : cmul(fk, cconj(A.pool[F.colV[c] + fix]));
+        } else {
+            const int t = c - F.ncol;
+            F.coef[c] = ROW ? w.uw[(size_t)t * A.Mmax + fix] : cconj(w.vw[(size_t)t * A.Nmax + fix]);
+        }
+    }
+}
+
+// Residual of one row (ROW: fixed row `fix`, all columns) or one column (!ROW:
+// fixed column `fix`, all rows) of the face at kf:
+//   ENTRY - sum_p f_p[kf] (U_p V_p^H) - sum_{t<m} u_t v_t^H
+//   ROW:  out[j] = ENTRY(fix, j) - sum_c coef[c] conj(X_c[j]),  X_c = V_p[:, t] | v_t
+//   !ROW: out[i] = ENTRY(i, fix) - sum_c X_c[i] coef[c],        X_c = U_p[:, t] | u_t
+// G threads per output element share the sum (4-way unrolled, independent
+// partial sums) and the quadrature points.  Returns the block-wide argmax of
+// |out|^2 (ROW: over all columns; !ROW: over the rows not yet used).
+template <int KER, class T, int NT, bool ROW>
+__device__ ArgMax residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int fix,
+                                int kf, int m, Cx<T>* out) {
+    const int tid = threadIdx.x;
+    const int M = S.M, N = S.N;
+    const int L = ROW ? N : M;
+    const int G = gang_size<NT>(L);
+    const int per = NT / G;
+    const int part = tid % G;
+    const long long* col = ROW ? F.colV : F.colU;
+    const Cx<T>* cur = ROW ? w.vw : w.uw;
+    const size_t ldc = ROW ? A.Nmax : A.Mmax;
+    const int nt = F.ncol;
+    ArgMax am{-1.0, LLONG_MAX};
+    for (int base = 0; base < L; base += per) {
+        const int v = base + tid / G;
+        Cx<T> acc{0, 0};
+        if (v < L) {
+            const int gi = S.rb + (ROW ? fix : v), gj = S.cb + (ROW ? v : fix);
+            acc = ent_part<KER, T>(A, gi, gj, kf, part, G);
+            Cx<T> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+            int c = part;
+            for (; c + 3 * G < nt; c += 4 * G) {
+                const Cx<T> x0 = A.pool[col[c] + v], x1 = A.pool[col[c + G] + v];
+                const Cx<T> x2 = A.pool[col[c + 2 * G] + v], x3 = A.pool[col[c + 3 * G] + v];
+                if (ROW) {
+                    cfmac(s0, F.coef[c], x0);
+                    cfmac(s1, F.coef[c + G], x1);
+                    cfmac(s2, F.coef[c + 2 * G], x2);
+                    cfmac(s3, F.coef[c + 3 * G], x3);
+                } else {
+                    cfma(s0, x0, F.coef[c]);
+                    cfma(s1, x1, F.coef[c + G]);
+                    cfma(s2, x2, F.coef[c + 2 * G]);
+                    cfma(s3, x3, F.coef[c + 3 * G]);
+                }
+            }
+            for (; c < nt; c += G) {
+                const Cx<T> x0 = A.pool[col[c] + v];
+                if (ROW) cfmac(s0, F.coef[c], x0);
+                else cfma(s0, x0, F.coef[c]);
+            }
+            int t = part;
+            for (; t + G < m; t += 2 * G) {
+                const Cx<T> x0 = cur[(size_t)t * ldc + v], x1 = cur[(size_t)(t + G) * ldc + v];
+                if (ROW) {
+                    cfmac(s1, F.coef[nt + t], x0);
+                    cfmac(s2, F.coef[nt + t + G], x1);
+                } else {
+                    cfma(s1, x0, F.coef[nt + t]);
+                    cfma(s2, x1, F.coef[nt + t + G]);
+                }
+            }
+            for (; t < m; t += G) {
+                const Cx<T> x0 = cur[(size_t)t * ldc + v];
+                if (ROW) cfmac(s3, F.coef[nt + t], x0);
+                else cfma(s3, x0, F.coef[nt + t]);
+            }
+            acc.x -= (s0.x + s1.x) + (s2.x + s3.x);
+            acc.y -= (s0.y + s1.y) + (s2.y + s3.y);
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            Cx<T> y = shfl_xor_c(acc, o);
+            acc.x += y.x;
+            acc.y += y.y;
+        }
+        if (part == 0 && v < L) {
+            out[v] = acc;
+            if (ROW || !w.used[v]) am = amax_better(am, ArgMax{cabs2d(acc), (long long)v});
+        }
+    }
+    if (tid == 0) S.entries += L;
+    return block_argmax<NT>(am, S.am);
+}
+
 // ---- face ACA (partial pivoting) on the residual face at frequency kf -----------------
 // Returns the rank m; columns 0..m-1 of uw / vw hold the crosses (S = U V^H).
 template <int KER, class T, int NT>
-__device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int kf) {
+__device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int kf, unsigned char* arena) {
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N, nc = S.ncross;
     const int cap = min(min(M, N), A.RF);
-    // f_p[kf] of earlier crosses
+    if (kf < 0 || kf >= A.Ku) {  // cannot happen: every caller passes a checked index
+        if (tid == 0) atomicOr(A.status, ST_BAD_INDEX);
+        return 0;
+    }
+    // f_p[kf] of earlier crosses, the column tables, used-row flags
     for (int p = tid; p < nc; p += NT) S.fk[p] = Fp(A, S, p)[kf];
+    const FaceTab<T> F = facetab_build<T, NT>(A, w, S, arena);
     for (int i = tid; i < M; i += NT) w.used[i] = 0;
     __syncthreads();
     double Sn2 = 0.0;
@@ -219,32 +449,9 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     while (m < cap) {
         int jp = -1;
         for (;;) {
-            // residual row irow
-            for (int p = 0; p < nc; ++p) {
-                if (tid < S.r[p]) w.pre[S.pre[p] + tid] = cmul(S.fk[p], Up(A, S, p)[(long long)tid * M + irow]);
-            }
+            line_coeffs<T, NT, true>(A, w, S, F, irow, m);
             __syncthreads();
-            ArgMax am{-1.0, LLONG_MAX};
-            for (int j = tid; j < N; j += NT) {
-                Cx<T> e = ent<KER, T>(A, S.rb + irow, S.cb + j, kf);
-                for (int p = 0; p < nc; ++p) {
-                    const Cx<T>* V = Vp(A, S, p);
-                    const Cx<T>* pr = w.pre + S.pre[p];
-                    const int rp = S.r[p];
-                    Cx<T> acc{0, 0};
-                    for (int t = 0; t < rp; ++t) cfmac(acc, pr[t], V[(long long)t * N + j]);
-                    e.x -= acc.x;
-                    e.y -= acc.y;
-                }
-                Cx<T> acc{0, 0};
-                for (int t = 0; t < m; ++t) cfmac(acc, w.uw[(size_t)t * A.Mmax + irow], w.vw[(size_t)t * A.Nmax + j]);
-                e.x -= acc.x;
-                e.y -= acc.y;
-                w.row[j] = e;
-                am = amax_better(am, ArgMax{(double)cabs2(e), (long long)j});
-            }
-            if (tid == 0) S.entries += N;
-            am = block_argmax<NT>(am, S.am);
+            ArgMax am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row);
             if (tid == 0) w.used[irow] = 1;
             if (am.v > 0.0) {
                 jp = (int)am.i;
@@ -262,65 +469,34 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             irow = (int)un.i;
         }
         if (jp < 0) break;  // no row with a nonzero residual left
-        const Cx<T> delta = w.row[jp];
-        const T dn = (T)1 / cabs2(delta);
+        // v = conj(row / delta), formed in float64 so that a tiny pivot of a
+        // strongly damped face cannot overflow 1 / |delta|^2 in float32
+        const Cx<double> delta = ccast<double>(F.row[jp]);
+        const double dn = 1.0 / (delta.x * delta.x + delta.y * delta.y);
         Cx<T>* vm = w.vw + (size_t)m * A.Nmax;
         for (int j = tid; j < N; j += NT) {
-            Cx<T> q = cmulc(w.row[j], delta);  // row * conj(delta) / |delta|^2 = row / delta
-            vm[j] = Cx<T>{q.x * dn, -q.y * dn};  // conj(row / delta)
+            Cx<double> q = cmulc(ccast<double>(F.row[j]), delta);  // row conj(delta)
+            vm[j] = Cx<T>{(T)(q.x * dn), (T)(-q.y * dn)};           // conj(row / delta)
         }
-        for (int p = 0; p < nc; ++p) {
-            if (tid < S.r[p]) {
-                Cx<T> v = Vp(A, S, p)[(long long)tid * N + jp];
-                w.pre[S.pre[p] + tid] = cmul(S.fk[p], cconj(v));
-            }
-        }
+        line_coeffs<T, NT, false>(A, w, S, F, jp, m);
         __syncthreads();
-        // residual column jp
+        // residual column jp = u_m; the argmax over unused rows of |u_m| is the next row
         Cx<T>* um = w.uw + (size_t)m * A.Mmax;
-        for (int i = tid; i < M; i += NT) {
-            Cx<T> e = ent<KER, T>(A, S.rb + i, S.cb + jp, kf);
-            for (int p = 0; p < nc; ++p) {
-                const Cx<T>* U = Up(A, S, p);
-                const Cx<T>* pr = w.pre + S.pre[p];
-                const int rp = S.r[p];
-                Cx<T> acc{0, 0};
-                for (int t = 0; t < rp; ++t) cfma(acc, U[(long long)t * M + i], pr[t]);
-                e.x -= acc.x;
-                e.y -= acc.y;
-            }
-            Cx<T> acc{0, 0};
-            for (int t = 0; t < m; ++t) cfmac(acc, w.uw[(size_t)t * A.Mmax + i], w.vw[(size_t)t * A.Nmax + jp]);
-            e.x -= acc.x;
-            e.y -= acc.y;
-            um[i] = e;
-        }
-        if (tid == 0) S.entries += M;
-        __syncthreads();
+        ArgMax nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um);
         // recursive Frobenius norm of the face approximant:
         // ||S_m||^2 = ||S_{m-1}||^2 + 2 Re sum_t (u_t^H u_m)(v_m^H v_t) + ||u_m||^2 ||v_m||^2
         const int wid = tid >> 5, lane = tid & 31;
         for (int t = wid; t <= m; t += NT / 32) {
             const Cx<T>* ut = w.uw + (size_t)t * A.Mmax;
             const Cx<T>* vt = w.vw + (size_t)t * A.Nmax;
-            Cx<double> gu{0, 0}, gv{0, 0};
-            for (int i = lane; i < M; i += 32) {
-                Cx<T> a = cmulc(um[i], ut[i]);  // conj(u_t) u_m
-                gu.x += a.x;
-                gu.y += a.y;
-            }
-            for (int j = lane; j < N; j += 32) {
-                Cx<T> a = cmulc(vt[j], vm[j]);  // conj(v_m) v_t
-                gv.x += a.x;
-                gv.y += a.y;
-            }
-            gu.x = warp_sum(gu.x);
-            gu.y = warp_sum(gu.y);
-            gv.x = warp_sum(gv.x);
-            gv.y = warp_sum(gv.y);
+            Cx<T> gu{0, 0}, gv{0, 0};
+            for (int i = lane; i < M; i += 32) cfmac(gu, um[i], ut[i]);  // conj(u_t) u_m
+            for (int j = lane; j < N; j += 32) cfmac(gv, vt[j], vm[j]);  // conj(v_m) v_t
+            double gux = warp_sum((double)gu.x), guy = warp_sum((double)gu.y);
+            double gvx = warp_sum((double)gv.x), gvy = warp_sum((double)gv.y);
             if (lane == 0) {
-                S.gu[t] = gu;
-                S.gv[t] = gv;
+                S.gu[t] = Cx<double>{gux, guy};
+                S.gv[t] = Cx<double>{gvx, gvy};
             }
         }
         __syncthreads();
@@ -334,12 +510,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             converged = true;
             break;
         }
-        // next row: argmax over unused rows of |u_m|
-        ArgMax nx{-1.0, LLONG_MAX};
-        for (int i = tid; i < M; i += NT)
-            if (!w.used[i]) nx = amax_better(nx, ArgMax{(double)cabs2(um[i]), (long long)i});
-        nx = block_argmax<NT>(nx, S.am);
-        if (nx.v < 0.0) break;
+        if (nx.v < 0.0) break;  // every row used
         irow = (int)nx.i;
     }
     if (!converged && m == A.RF && m < min(M, N)) {
@@ -352,98 +523,156 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     return m;
 }
 
-// ---- recompression: Cholesky-QR + one-sided Jacobi SVD ---------------------------------
-// Input uw, vw (r columns).  Output: the rank r' and the transforms
-// T_U (r x r'), T_V (r x r') in shared memory (row-major, stride RF) such that
-// U' = uw T_U, V' = vw T_V, U' V'^H = uw vw^H truncated.  Returns r' or -1 if
-// Cholesky broke down (caller keeps the raw factors).
+// ---- tiled Gram of the face factors: G[a][b] = sum_i conj(X_a[i]) X_b[i], a <= b < r ----
+// Products and the sum over a 32-row chunk in the working precision T, the sum
+// over chunks in float64.  sh: >= 33 * r complex T.
 template <class T, int NT>
-__device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int r, Cx<double>* shB,
-                          Cx<double>* shJ) {
-    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const int M = S.M, N = S.N, RF = A.RF;
-    // Gram matrices (upper triangles): G[a][b] = sum conj(x_a) x_b
+__device__ void gram_upper(const Cx<T>* X, size_t ld, int L, int r, Cx<double>* G, int RF, Cx<T>* sh) {
+    constexpr int QMAX = (RF_MAX * (RF_MAX + 1) / 2 + NT - 1) / NT;
+    const int tid = threadIdx.x;
     const int npair = r * (r + 1) / 2;
-    for (int it = wid; it < 2 * npair; it += NT / 32) {
-        const bool isU = it < npair;
-        int q = isU ? it : it - npair;
-        int a = 0;
-        while (q >= r - a) {
-            q -= r - a;
-            ++a;
+    int pa[QMAX], pb[QMAX];
+    Cx<double> acc[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+        int p = tid + q * NT;
+        acc[q] = Cx<double>{0, 0};
+        pa[q] = -1;
+        pb[q] = 0;
+        if (p < npair) {
+            int a = 0;
+            while (p >= r - a) {
+                p -= r - a;
+                ++a;
+            }
+            pa[q] = a;
+            pb[q] = a + p;
         }
-        const int b = a + q;
-        const Cx<T>* xa = isU ? w.uw + (size_t)a * A.Mmax : w.vw + (size_t)a * A.Nmax;
-        const Cx<T>* xb = isU ? w.uw + (size_t)b * A.Mmax : w.vw + (size_t)b * A.Nmax;
-        const int L = isU ? M : N;
-        Cx<double> g{0, 0};
-        for (int i = lane; i < L; i += 32) {
-            Cx<double> va = ccast<double>(xa[i]), vb = ccast<double>(xb[i]);
-            g.x += va.x * vb.x + va.y * vb.y;
-            g.y += va.x * vb.y - va.y * vb.x;
-        }
-        g.x = warp_sum(g.x);
-        g.y = warp_sum(g.y);
-        if (lane == 0) (isU ? w.RU : w.RV)[a * RF + b] = g;
     }
+    for (int i0 = 0; i0 < L; i0 += 32) {
+        for (int e = tid; e < r * 32; e += NT) {
+            const int c = e >> 5, ii = e & 31;
+            sh[c * 33 + ii] = (i0 + ii < L) ? X[(size_t)c * ld + i0 + ii] : Cx<T>{0, 0};
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            if (pa[q] < 0) continue;
+            const Cx<T>* xa = sh + pa[q] * 33;
+            const Cx<T>* xb = sh + pb[q] * 33;
+            Cx<T> s{0, 0};
+#pragma unroll 8
+            for (int ii = 0; ii < 32; ++ii) cfmac(s, xb[ii], xa[ii]);  // conj(x_a) x_b
+            acc[q].x += (double)s.x;
+            acc[q].y += (double)s.y;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q)
+        if (pa[q] >= 0) G[pa[q] * RF + pb[q]] = acc[q];
+}
+
+// ---- recompression: Cholesky-QR + one-sided Jacobi SVD ---------------------------------
+// Input uw, vw (r columns).  Output: the rank r' and the transforms T_U, T_V
+// (r x r', complex T, row-major with stride *ldT) such that U' = uw T_U,
+// V' = vw T_V.  For any invertible triangular R used consistently,
+// uw T_U T_V^H vw^H = uw vw^H before truncation, so the Gram matrices may be
+// formed in the working precision; the r x r algebra is float64.
+//
+// The four r x r float64 matrices (R_U, R_V, B = C J, J) live in shared memory
+// (stride RS) when r <= RS, else in the global workspace (stride RF).  The
+// back substitution runs in place on the selected columns of B and J.
+// Returns r' or -1 (Cholesky breakdown or a non-finite SVD: the caller keeps
+// the raw factors).
+constexpr int RS = 32;
+
+template <class T>
+__device__ __forceinline__ T jacobi_tol();
+template <>
+__device__ __forceinline__ float jacobi_tol<float>() { return 1e-6f; }
+template <>
+__device__ __forceinline__ double jacobi_tol<double>() { return 1e-12; }
+
+template <class T, int NT>
+__device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int r, Cx<double>* smem,
+                          const Cx<T>** tUo, const Cx<T>** tVo, int* ldTo) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int M = S.M, N = S.N;
+    const bool small = r <= RS;
+    const int ld = small ? RS : A.RF;
+    Cx<double>* RU = small ? smem : w.RU;
+    Cx<double>* RV = small ? smem + RS * RS : w.RV;
+    // B = C J and J in the working precision T (the Jacobi sweeps dominate the
+    // r x r work; float64 is rate-limited on this part)
+    Cx<T>* shB = small ? reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS) : reinterpret_cast<Cx<T>*>(w.TU);
+    Cx<T>* shJ = shB + (small ? RS * RS : A.RF * A.RF);
+    // Gram staging after R_U, R_V
+    Cx<T>* stage = reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS);
+    gram_upper<T, NT>(w.uw, A.Mmax, M, r, RU, ld, stage);
+    gram_upper<T, NT>(w.vw, A.Nmax, N, r, RV, ld, stage);
     if (tid == 0) S.flag = 0;
     __syncthreads();
-    // column scaling and upper Cholesky of the scaled Gram matrices: warp 0 -> U, warp 1 -> V
+    // column scaling and upper Cholesky of the scaled Gram matrices (float64):
+    // warp 0 -> U, warp 1 -> V
     if (wid < 2) {
-        Cx<double>* R = wid == 0 ? w.RU : w.RV;
+        Cx<double>* R = wid == 0 ? RU : RV;
         double* dsc = wid == 0 ? S.dU : S.dV;
-        for (int a = lane; a < r; a += 32) dsc[a] = 1.0 / sqrt(fmax(R[a * RF + a].x, 1e-300));
+        for (int a = lane; a < r; a += 32) dsc[a] = 1.0 / sqrt(fmax(R[a * ld + a].x, 1e-300));
         __syncwarp();
         for (int a = lane; a < r; a += 32)
             for (int b = a; b < r; ++b) {
                 double s = dsc[a] * dsc[b];
-                R[a * RF + b].x *= s;
-                R[a * RF + b].y *= s;
+                R[a * ld + b].x *= s;
+                R[a * ld + b].y *= s;
             }
         __syncwarp();
         for (int k = 0; k < r; ++k) {
-            double dkk = R[k * RF + k].x;
-            for (int i = 0; i < k; ++i) dkk -= R[i * RF + k].x * R[i * RF + k].x + R[i * RF + k].y * R[i * RF + k].y;
+            double dkk = R[k * ld + k].x;
+            for (int i = 0; i < k; ++i) dkk -= cabs2(R[i * ld + k]);
             bool bad = !(dkk > 1e-24);
             if (bad) {
                 if (lane == 0) atomicOr(&S.flag, 1);
                 break;
             }
             double rkk = sqrt(dkk);
+            double irkk = 1.0 / rkk;
             for (int j = k + 1 + lane; j < r; j += 32) {
-                Cx<double> acc = R[k * RF + j];
+                Cx<double> acc = R[k * ld + j];
                 for (int i = 0; i < k; ++i) {
-                    Cx<double> rik = R[i * RF + k], rij = R[i * RF + j];
+                    Cx<double> rik = R[i * ld + k], rij = R[i * ld + j];
                     acc.x -= rik.x * rij.x + rik.y * rij.y;  // conj(R[i][k]) R[i][j]
                     acc.y -= rik.x * rij.y - rik.y * rij.x;
                 }
-                R[k * RF + j] = Cx<double>{acc.x / rkk, acc.y / rkk};
+                R[k * ld + j] = Cx<double>{acc.x * irkk, acc.y * irkk};
             }
             __syncwarp();
-            if (lane == 0) R[k * RF + k] = Cx<double>{rkk, 0.0};
+            if (lane == 0) R[k * ld + k] = Cx<double>{rkk, 0.0};
             __syncwarp();
         }
     }
     __syncthreads();
     if (S.flag) return -1;
     // core C = R_U R_V^H with R_U = Rhat_U diag(1/dU): C[a][b] = sum_{c >= max(a,b)}
-    //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in shB, J = I
+    //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in B, J = I
     for (int e = tid; e < r * r; e += NT) {
         const int a = e % r, b = e / r;
         Cx<double> acc{0, 0};
         for (int c = max(a, b); c < r; ++c) {
-            Cx<double> x = w.RU[a * RF + c], y = w.RV[b * RF + c];
+            Cx<double> x = RU[a * ld + c], y = RV[b * ld + c];
             double s = 1.0 / (S.dU[c] * S.dV[c]);
             acc.x += (x.x * y.x + x.y * y.y) * s;
             acc.y += (x.y * y.x - x.x * y.y) * s;
         }
-        shB[b * RF + a] = acc;
-        shJ[b * RF + a] = Cx<double>{a == b ? 1.0 : 0.0, 0.0};
+        shB[b * ld + a] = ccast<T>(acc);
+        shJ[b * ld + a] = Cx<T>{(T)(a == b ? 1 : 0), (T)0};
     }
     __syncthreads();
-    // one-sided Jacobi (Hestenes) on the columns of C, round-robin pair schedule
+    // one-sided Jacobi (Hestenes) on the columns of C, round-robin pair schedule;
+    // a pair is rotated while |<c_p, c_q>| > tol ||c_p|| ||c_q||
     const int n = (r + 1) & ~1;
-    for (int sweep = 0; sweep < 30; ++sweep) {
+    const T tol = jacobi_tol<T>();
+    for (int sweep = 0; sweep < 16; ++sweep) {
         if (tid == 0) S.rot = 0;
         __syncthreads();
         for (int rho = 0; rho < n - 1; ++rho) {
@@ -457,12 +686,12 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                     q = (rho - pi + (n - 1)) % (n - 1);
                 }
                 if (p >= r || q >= r) continue;
-                Cx<double>* bp = shB + p * RF;
-                Cx<double>* bq = shB + q * RF;
-                double al = 0, be = 0;
-                Cx<double> ga{0, 0};
+                Cx<T>* bp = shB + p * ld;
+                Cx<T>* bq = shB + q * ld;
+                T al = 0, be = 0;
+                Cx<T> ga{0, 0};
                 for (int i = lane; i < r; i += 32) {
-                    Cx<double> x = bp[i], y = bq[i];
+                    Cx<T> x = bp[i], y = bq[i];
                     al += x.x * x.x + x.y * x.y;
                     be += y.x * y.x + y.y * y.y;
                     ga.x += x.x * y.x + x.y * y.y;
@@ -472,26 +701,26 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                 be = warp_sum(be);
                 ga.x = warp_sum(ga.x);
                 ga.y = warp_sum(ga.y);
-                double ag = sqrt(ga.x * ga.x + ga.y * ga.y);
-                if (ag > 1e-15 * sqrt(al * be) && ag > 1e-300) {
-                    double zeta = (be - al) / (2.0 * ag);
-                    double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    Cx<double> ph{ga.x / ag, ga.y / ag};  // e^{i phi}
-                    Cx<double>* jp_ = shJ + p * RF;
-                    Cx<double>* jq_ = shJ + q * RF;
+                T ag = sqrt(ga.x * ga.x + ga.y * ga.y);
+                if (ag > tol * sqrt(al * be) && ag > (T)1e-30) {
+                    T zeta = (be - al) / ((T)2 * ag);
+                    T t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+                    T c = (T)1 / sqrt((T)1 + t * t), s = c * t;
+                    Cx<T> ph{ga.x / ag, ga.y / ag};  // e^{i phi}
+                    Cx<T>* jp_ = shJ + p * ld;
+                    Cx<T>* jq_ = shJ + q * ld;
                     for (int i = lane; i < r; i += 32) {
-                        Cx<double> x = bp[i], y = bq[i];
+                        Cx<T> x = bp[i], y = bq[i];
                         // x' = c x - s e^{-i phi} y ; y' = s e^{i phi} x + c y
-                        Cx<double> ey = cmulc(y, ph), ex = cmul(x, ph);
-                        bp[i] = Cx<double>{c * x.x - s * ey.x, c * x.y - s * ey.y};
-                        bq[i] = Cx<double>{s * ex.x + c * y.x, s * ex.y + c * y.y};
+                        Cx<T> ey = cmulc(y, ph), ex = cmul(x, ph);
+                        bp[i] = Cx<T>{c * x.x - s * ey.x, c * x.y - s * ey.y};
+                        bq[i] = Cx<T>{s * ex.x + c * y.x, s * ex.y + c * y.y};
                         x = jp_[i];
                         y = jq_[i];
                         ey = cmulc(y, ph);
                         ex = cmul(x, ph);
-                        jp_[i] = Cx<double>{c * x.x - s * ey.x, c * x.y - s * ey.y};
-                        jq_[i] = Cx<double>{s * ex.x + c * y.x, s * ex.y + c * y.y};
+                        jp_[i] = Cx<T>{c * x.x - s * ey.x, c * x.y - s * ey.y};
+                        jq_[i] = Cx<T>{s * ex.x + c * y.x, s * ex.y + c * y.y};
                     }
                     if (lane == 0) atomicAdd(&S.rot, 1);
                 }
@@ -501,17 +730,22 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         const int rot = S.rot;
         __syncthreads();
         if (rot == 0) break;
-        if (sweep == 29 && tid == 0) atomicOr(A.status, ST_JACOBI_NOCONV);
+        if (sweep == 15 && tid == 0) atomicOr(A.status, ST_JACOBI_NOCONV);
     }
     // singular values, sort descending, truncation sigma < eps_face * sigma_max
     for (int a = tid; a < r; a += NT) {
         double s2 = 0;
-        for (int i = 0; i < r; ++i) s2 += cabs2(shB[a * RF + i]);
+        for (int i = 0; i < r; ++i) s2 += cabs2d(shB[a * ld + i]);
         S.sig[a] = sqrt(s2);
     }
     __syncthreads();
     double smax = 0;
-    for (int a = 0; a < r; ++a) smax = fmax(smax, S.sig[a]);
+    bool finite = true;
+    for (int a = 0; a < r; ++a) {
+        smax = fmax(smax, S.sig[a]);
+        finite &= (bool)isfinite(S.sig[a]);
+    }
+    if (!finite || !(smax > 0.0)) return -1;
     for (int a = tid; a < r; a += NT) {
         int rank = 0;
         for (int b = 0; b < r; ++b)
@@ -522,39 +756,133 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     __syncthreads();
     int rn = 0;
     while (rn < r && S.sel[rn] >= 0) ++rn;
-    // T_U = diag(dU) RhatU^{-1} B[:, sel] ;  T_V = diag(dV) RhatV^{-1} J[:, sel]   (back substitution)
+    // T_U[:, b] = diag(dU) RhatU^{-1} B[:, sel[b]],  T_V[:, b] = diag(dV) RhatV^{-1} J[:, sel[b]]
+    // (float64 back substitution, in place on the selected columns)
     for (int item = tid; item < 2 * rn; item += NT) {
         const bool isU = item < rn;
         const int b = isU ? item : item - rn;
-        const Cx<double>* R = isU ? w.RU : w.RV;
-        const Cx<double>* rhs = (isU ? shB : shJ) + S.sel[b] * RF;
+        const Cx<double>* R = isU ? RU : RV;
+        Cx<T>* z = (isU ? shB : shJ) + S.sel[b] * ld;
         const double* dsc = isU ? S.dU : S.dV;
-        Cx<double>* Tm = isU ? w.TU : w.TV;
         for (int a = r - 1; a >= 0; --a) {
-            Cx<double> acc = rhs[a];
+            Cx<double> acc = ccast<double>(z[a]);
             for (int c = a + 1; c < r; ++c) {
-                Cx<double> z = Tm[c * RF + b];  // z[c] (unscaled, stored temporarily)
-                Cx<double> rr = R[a * RF + c];
-                acc.x -= rr.x * z.x - rr.y * z.y;
-                acc.y -= rr.x * z.y + rr.y * z.x;
+                Cx<double> rr = R[a * ld + c];
+                Cx<double> zc = ccast<double>(z[c]);
+                acc.x -= rr.x * zc.x - rr.y * zc.y;
+                acc.y -= rr.x * zc.y + rr.y * zc.x;
             }
-            double rd = R[a * RF + a].x;
-            Tm[a * RF + b] = Cx<double>{acc.x / rd, acc.y / rd};
+            double rd = 1.0 / R[a * ld + a].x;
+            z[a] = Cx<T>{(T)(acc.x * rd), (T)(acc.y * rd)};
         }
         for (int a = 0; a < r; ++a) {
-            Tm[a * RF + b].x *= dsc[a];
-            Tm[a * RF + b].y *= dsc[a];
+            z[a].x *= (T)dsc[a];
+            z[a].y *= (T)dsc[a];
         }
     }
     __syncthreads();
-    // move T_U, T_V into shared memory (the Jacobi buffers are free now)
+    // compact T_U, T_V (row-major r x r', complex T) into the R_U / R_V storage (dead now)
+    Cx<T>* tU = reinterpret_cast<Cx<T>*>(RU);
+    Cx<T>* tV = reinterpret_cast<Cx<T>*>(RV);
     for (int e = tid; e < r * rn; e += NT) {
         const int a = e / rn, b = e % rn;
-        shB[a * RF + b] = w.TU[a * RF + b];
-        shJ[a * RF + b] = w.TV[a * RF + b];
+        tU[a * ld + b] = shB[S.sel[b] * ld + a];
+        tV[a * ld + b] = shJ[S.sel[b] * ld + a];
     }
     __syncthreads();
+    *tUo = tU;
+    *tVo = tV;
+    *ldTo = ld;
     return rn;
+}
+
+// ---- eq. (norm) inner products ------------------------------------------------------------
+// hh[d] = <H_l, H_d>_F = sum_{a in cross d, b} (U_d^H U_l)[a][b] conj((V_d^H V_l)[a][b]) for the
+// earlier crosses d < nc, and hself = ||H_l||_F^2 (a over the columns of cross l).
+// Tiled: 32 columns of [U_1 .. U_nc U_l] at a time against all rn columns of U_l,
+// over 32-row chunks staged in shared memory (sh: >= 33 * (32 + RF) complex T).
+template <class T, int NT>
+__device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, const Cx<T>* Vn, int rn,
+                           Cx<T>* sh) {
+    constexpr int QMAX = 32 * RF_MAX / NT;
+    const int tid = threadIdx.x;
+    const int M = S.M, N = S.N, nc = S.ncross;
+    const int na = S.pre[nc] + rn;
+    Cx<T>* sa = sh;             // [32][33]
+    Cx<T>* sb = sh + 32 * 33;   // [rn][33]
+    for (int a0 = 0; a0 < na; a0 += 32) {
+        const int acnt = min(32, na - a0);
+        Cx<T> zu[QMAX], zv[QMAX];
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) zu[q] = zv[q] = Cx<T>{0, 0};
+        for (int pass = 0; pass < 2; ++pass) {  // 0: U (rows M), 1: V (rows N)
+            const int L = pass == 0 ? M : N;
+            for (int i0 = 0; i0 < L; i0 += 32) {
+                for (int e = tid; e < acnt * 32; e += NT) {
+                    const int c = e >> 5, ii = e & 31, col = a0 + c;
+                    Cx<T> v{0, 0};
+                    if (i0 + ii < L) {
+                        const Cx<T>* base;
+                        if (col < S.pre[nc]) {
+                            int d = 0;
+                            while (S.pre[d + 1] <= col) ++d;
+                            const int t = col - S.pre[d];
+                            base = pass == 0 ? A.pool + S.off[d] + (long long)t * M
+                                             : A.pool + S.off[d] + (long long)S.r[d] * M + (long long)t * N;
+                        } else {
+                            const int t = col - S.pre[nc];
+                            base = pass == 0 ? Un + (long long)t * M : Vn + (long long)t * N;
+                        }
+                        v = base[i0 + ii];
+                    }
+                    sa[c * 33 + ii] = v;
+                }
+                for (int e = tid; e < rn * 32; e += NT) {
+                    const int b = e >> 5, ii = e & 31;
+                    const Cx<T>* base = pass == 0 ? Un + (long long)b * M : Vn + (long long)b * N;
+                    sb[b * 33 + ii] = (i0 + ii < L) ? base[i0 + ii] : Cx<T>{0, 0};
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < QMAX; ++q) {
+                    const int o = tid + q * NT;
+                    if (o >= acnt * rn) break;
+                    const int al = o / rn, b = o % rn;
+                    const Cx<T>* xa = sa + al * 33;
+                    const Cx<T>* xb = sb + b * 33;
+                    Cx<T> s{0, 0};
+#pragma unroll 8
+                    for (int ii = 0; ii < 32; ++ii) cfmac(s, xb[ii], xa[ii]);
+                    if (pass == 0) {
+                        zu[q].x += s.x;
+                        zu[q].y += s.y;
+                    } else {
+                        zv[q].x += s.x;
+                        zv[q].y += s.y;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // combine: contribution zu conj(zv) to the cross that owns column a
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            const int o = tid + q * NT;
+            if (o >= acnt * rn) break;
+            const int col = a0 + o / rn;
+            const double px = (double)zu[q].x * zv[q].x + (double)zu[q].y * zv[q].y;
+            const double py = (double)zu[q].y * zv[q].x - (double)zu[q].x * zv[q].y;
+            if (col < S.pre[nc]) {
+                int d = 0;
+                while (S.pre[d + 1] <= col) ++d;
+                atomicAdd(&S.hh[d].x, px);
+                atomicAdd(&S.hh[d].y, py);
+            } else {
+                atomicAdd(&S.hself, px);
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // ---- the persistent kernel ---------------------------------------------------------
@@ -564,8 +892,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
     __shared__ BlockSh<T> S;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const int RF = A.RF;
-    Cx<double>* shB = reinterpret_cast<Cx<double>*>(smem_raw);
-    Cx<double>* shJ = shB + RF * RF;
+    Cx<double>* shB = reinterpret_cast<Cx<double>*>(smem_raw);  // arena base
     const Ws<T> w = ws_carve<T>(A.ws + (size_t)blockIdx.x * A.ws_stride, RF, A.Mmax, A.Nmax, A.Cmax, A.Ku);
     __shared__ int s_q;
     for (int iter = 0;; ++iter) {
@@ -598,6 +925,16 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
         }
         __syncthreads();
         const int M = S.M, N = S.N, Ku = A.Ku;
+        // phase cycle counters: face, recompress, formation, pivot, fiber, norm, next-k
+        long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
+        long long tclk = clock64();
+        auto lap = [&](int i) {
+            if (tid == 0) {
+                long long tn = clock64();
+                ph[i] += tn - tclk;
+                tclk = tn;
+            }
+        };
         bool zero_block = false;
         int computed = 0;
         bool overflow = false;
@@ -608,7 +945,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
         while (!overflow) {
             // ---------------- face at S.k ----------------
             int kf = S.k;
-            int r = face_aca<KER, T, NT>(A, w, S, kf);
+            int r = face_aca<KER, T, NT>(A, w, S, kf, smem_raw);
             if (tid == 0) S.used_k[kf >> 5] |= 1u << (kf & 31);
             __syncthreads();
             if (r == 0) {
@@ -625,7 +962,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                     __syncthreads();
                     if (tid == 0) S.used_k[kk >> 5] |= 1u << (kk & 31);
                     __syncthreads();
-                    r = face_aca<KER, T, NT>(A, w, S, kk);
+                    r = face_aca<KER, T, NT>(A, w, S, kk, smem_raw);
                     if (r > 0) {
                         found = true;
                         kf = kk;
@@ -639,14 +976,22 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 __syncthreads();
             }
             ++computed;
+            lap(0);
             // ---------------- recompression ----------------
             int rn = -1;
+            const Cx<T>* tU = nullptr;
+            const Cx<T>* tV = nullptr;
+            int ldT = 0;
             if (!A.no_recompress) {
-                rn = recompress<T, NT>(A, w, S, r, shB, shJ);
-                if (rn < 0 && tid == 0) atomicOr(A.status, ST_CHOL_FALLBACK);
+                rn = recompress<T, NT>(A, w, S, r, shB, &tU, &tV, &ldT);
+                if (rn < 0 && tid == 0) {
+                    atomicOr(A.status, ST_CHOL_FALLBACK);
+                    atomicAdd(&A.counters[4], 1ull);
+                }
             }
             const bool raw = rn < 0;
             if (raw) rn = r;
+            lap(1);
             // allocate U', V', f in the pool
             if (tid == 0) {
                 long long need = (long long)rn * (M + N) + Ku;
@@ -672,22 +1017,31 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 for (int e = tid; e < rn * M; e += NT) Un[e] = w.uw[(size_t)(e / M) * A.Mmax + e % M];
                 for (int e = tid; e < rn * N; e += NT) Vn[e] = w.vw[(size_t)(e / N) * A.Nmax + e % N];
             } else {
-                for (int i = tid; i < M; i += NT) {
-                    for (int b = 0; b < rn; ++b) {
-                        Cx<double> acc{0, 0};
-                        for (int a = 0; a < r; ++a) cfma(acc, ccast<double>(w.uw[(size_t)a * A.Mmax + i]), shB[a * RF + b]);
-                        Un[(long long)b * M + i] = ccast<T>(acc);
+                // U' = uw T_U, V' = vw T_V in the working precision, 8 output columns per pass
+                for (int e = tid; e < (M + N) * ((rn + 7) / 8); e += NT) {
+                    const int row = e % (M + N), b0 = (e / (M + N)) * 8;
+                    const bool isU = row < M;
+                    const int i = isU ? row : row - M;
+                    const Cx<T>* src = isU ? w.uw + i : w.vw + i;
+                    const size_t ld = isU ? A.Mmax : A.Nmax;
+                    const Cx<T>* Tm = isU ? tU : tV;
+                    Cx<T> acc[8];
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) acc[bb] = Cx<T>{0, 0};
+                    for (int a = 0; a < r; ++a) {
+                        const Cx<T> u = src[(size_t)a * ld];
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) cfma(acc[bb], u, Tm[a * ldT + min(b0 + bb, rn - 1)]);
                     }
-                }
-                for (int j = tid; j < N; j += NT) {
-                    for (int b = 0; b < rn; ++b) {
-                        Cx<double> acc{0, 0};
-                        for (int a = 0; a < r; ++a) cfma(acc, ccast<double>(w.vw[(size_t)a * A.Nmax + j]), shJ[a * RF + b]);
-                        Vn[(long long)b * N + j] = ccast<T>(acc);
-                    }
+                    Cx<T>* dst = isU ? Un + i : Vn + i;
+                    const long long L = isU ? M : N;
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb)
+                        if (b0 + bb < rn) dst[(long long)(b0 + bb) * L] = acc[bb];
                 }
             }
             __syncthreads();
+            lap(2);
             // ---------------- pivot: argmax |U' V'^H| ----------------
             {
                 constexpr int TM = sizeof(T) == 4 ? 64 : 32;
@@ -732,7 +1086,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                                 for (int c = 0; c < RM; ++c) {
                                     int gi = i0 + ty * RM + a, gj = j0 + tx * RM + c;
                                     if (gi < M && gj < N)
-                                        best = amax_better(best, ArgMax{(double)cabs2(acc[a][c]), (long long)gi * N + gj});
+                                        best = amax_better(best, ArgMax{cabs2d(acc[a][c]), (long long)gi * N + gj});
                                 }
                         }
                         __syncthreads();
@@ -740,15 +1094,25 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 }
                 best = block_argmax<NT>(best, S.am);
                 if (tid == 0) {
-                    S.ip = (int)(best.i / N);
-                    S.jp = (int)(best.i % N);
-                    Cx<double> h{0, 0};
-                    for (int b = 0; b < rn; ++b)
-                        cfmac(h, ccast<double>(Un[(long long)b * M + S.ip]), ccast<double>(Vn[(long long)b * N + S.jp]));
-                    S.hpiv = h;
+                    // no finite candidate (a non-finite face): report a vanishing pivot
+                    if (best.v < 0.0 || best.i < 0 || best.i >= (long long)M * N) {
+                        S.ip = 0;
+                        S.jp = 0;
+                        S.hpiv = Cx<double>{0.0, 0.0};
+                        if (best.v >= 0.0) atomicOr(A.status, ST_BAD_INDEX);
+                    } else {
+                        S.ip = (int)(best.i / N);
+                        S.jp = (int)(best.i % N);
+                        Cx<double> h{0, 0};
+                        for (int b = 0; b < rn; ++b)
+                            cfmac(h, ccast<double>(Un[(long long)b * M + S.ip]), ccast<double>(Vn[(long long)b * N + S.jp]));
+                        if (!isfinite(h.x) || !isfinite(h.y)) h = Cx<double>{0.0, 0.0};
+                        S.hpiv = h;
+                    }
                 }
             }
             __syncthreads();
+            lap(3);
             if (S.hpiv.x == 0.0 && S.hpiv.y == 0.0) break;  // vanishing face: nothing to divide by
             // H_p[i_l, j_l] of earlier crosses (float64)
             for (int p = tid; p < S.ncross; p += NT) {
@@ -777,6 +1141,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             }
             if (tid == 0) S.entries += Ku;
             __syncthreads();
+            lap(4);
             // ---------------- eq. (norm) ----------------
             // <f_l, f_d> and ||f_l||^2
             for (int d = wid; d <= nc; d += NT / 32) {
@@ -797,43 +1162,8 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             for (int d = tid; d < nc; d += NT) S.hh[d] = Cx<double>{0, 0};
             if (tid == 0) S.hself = 0.0;
             __syncthreads();
-            // <H_l, H_d> = sum_{a,b} (U_d^H U_l)[a][b] (V_l^H V_d)[b][a]; d = nc gives ||H_l||^2
-            {
-                long long total = 0;
-                for (int d = 0; d <= nc; ++d) total += (long long)(d < nc ? S.r[d] : rn) * rn;
-                for (long long it = wid; it < total; it += NT / 32) {
-                    long long q = it;
-                    int d = 0;
-                    while (true) {
-                        long long sz = (long long)(d < nc ? S.r[d] : rn) * rn;
-                        if (q < sz) break;
-                        q -= sz;
-                        ++d;
-                    }
-                    const int a = (int)(q / rn), b = (int)(q % rn);
-                    const Cx<T>* Ud = d < nc ? Up(A, S, d) : Un;
-                    const Cx<T>* Vd = d < nc ? Vp(A, S, d) : Vn;
-                    const Cx<T>* ua = Ud + (long long)a * M;
-                    const Cx<T>* ub = Un + (long long)b * M;
-                    const Cx<T>* va = Vd + (long long)a * N;
-                    const Cx<T>* vb = Vn + (long long)b * N;
-                    Cx<T> gu{0, 0}, gv{0, 0};
-                    for (int i = lane; i < M; i += 32) cfmac(gu, ub[i], ua[i]);  // conj(U_d[a]) U_l[b]
-                    for (int j = lane; j < N; j += 32) cfmac(gv, va[j], vb[j]);  // conj(V_l[b]) V_d[a]
-                    double gux = warp_sum((double)gu.x), guy = warp_sum((double)gu.y);
-                    double gvx = warp_sum((double)gv.x), gvy = warp_sum((double)gv.y);
-                    if (lane == 0) {
-                        double px = gux * gvx - guy * gvy, py = gux * gvy + guy * gvx;
-                        if (d < nc) {
-                            atomicAdd(&S.hh[d].x, px);
-                            atomicAdd(&S.hh[d].y, py);
-                        } else {
-                            atomicAdd(&S.hself, px);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
+            // <H_l, H_d> and ||H_l||^2 through tiled Gram products
+            norm_grams<T, NT>(A, S, Un, Vn, rn, reinterpret_cast<Cx<T>*>(smem_raw));
             if (tid == 0) {
                 double add = 0.0;
                 for (int d = 0; d < nc; ++d) add += 2.0 * (S.hh[d].x * S.ff[d].x - S.hh[d].y * S.ff[d].y);
@@ -861,20 +1191,25 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 }
             }
             __syncthreads();
+            lap(5);
             if (S.flag) break;
             // next frequency: argmax over unused k of |f_l[k]|
             ArgMax nk{-1.0, LLONG_MAX};
             for (int k = tid; k < Ku; k += NT)
                 if (!((S.used_k[k >> 5] >> (k & 31)) & 1u)) nk = amax_better(nk, ArgMax{cabs2(w.fib[k]), (long long)k});
             nk = block_argmax<NT>(nk, S.am);
+            if (nk.v < 0.0 || nk.i < 0 || nk.i >= Ku) break;  // no finite candidate left
             if (tid == 0) S.k = (int)nk.i;
             __syncthreads();
+            lap(6);
         }
         if (tid == 0) {
             A.r3[blk] = S.ncross;
+            A.blk_cycles[blk] = ph[0] + ph[1] + ph[2] + ph[3] + ph[4] + ph[5] + ph[6];
             atomicAdd(&A.counters[0], (unsigned long long)S.entries);
             atomicAdd(&A.counters[1], (unsigned long long)computed);
             if (zero_block) atomicAdd(&A.counters[2], 1ull);
+            for (int i = 0; i < 7; ++i) atomicAdd(&A.counters[8 + i], (unsigned long long)ph[i]);
         }
         __syncthreads();
     }
@@ -910,6 +1245,9 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
     const bool sep = kernel == G3_SEPARABLE;
     const int Ku = fa->Ku;
     const int RF = o.face_rank_max > 0 ? std::min(o.face_rank_max, RF_MAX) : 48;
+    // face tolerance: eps3 / 100 (eps = 100 eps_ACA); in float32 arithmetic not
+    // below 1e-5, the relative noise level of float32 entries
+    const double eps_face = o.eps_face > 0 ? o.eps_face : (sizeof(T) == 4 ? std::max(eps3 / 100.0, 1e-5) : eps3 / 100.0);
     // block list (far order) and queue
     std::vector<BlockRange> ranges;
     if (sep) {
@@ -935,6 +1273,8 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
     }
     std::vector<int> queue(n_far);
     std::iota(queue.begin(), queue.end(), 0);
+    // optional bounded run: only the first max_blocks blocks of the far order
+    const int n_run = o.max_blocks > 0 ? std::min(n_far, o.max_blocks) : n_far;
     const int order = o.order_by_cost;  // 0 given -> default on
     if (order >= 0) {
         std::vector<double> cost(n_far);
@@ -942,13 +1282,13 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
             double mm = ranges[i].re - ranges[i].rb, nn = ranges[i].ce - ranges[i].cb;
             cost[i] = o.cost ? (double)o.cost[i] : mm * nn;
         }
-        std::stable_sort(queue.begin(), queue.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::stable_sort(queue.begin(), queue.begin() + n_run, [&](int a, int b) { return cost[a] > cost[b]; });
     }
     DevBuf d_ranges, d_queue, d_head, d_k1, d_counters, d_ctr;
     G3_CUDA(d_ranges.alloc(n_far * sizeof(BlockRange)));
     G3_CUDA(d_queue.alloc(n_far * sizeof(int)));
     G3_CUDA(d_head.alloc(sizeof(int)));
-    G3_CUDA(d_counters.alloc(8 * sizeof(unsigned long long)));
+    G3_CUDA(d_counters.alloc(16 * sizeof(unsigned long long)));
     G3_CUDA(d_ctr.alloc(sizeof(unsigned long long)));
     G3_CUDA(cudaMemcpyAsync(d_ranges.p, ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice, ctx->stream));
     G3_CUDA(cudaMemcpyAsync(d_queue.p, queue.data(), n_far * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -977,22 +1317,30 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         sv = SepView<T>{sep_R, fa->M_sep, fa->N_sep, Ku, d_sa.as<T>(), d_sb.as<T>(), d_sc.as<T>()};
     }
     constexpr int NT = 256;
-    // dynamic shared memory: Jacobi matrices (2 RF^2 complex double), reused for
-    // the pivot-search tiles (2 RF TM complex T, TM = 64 float / 32 double)
+    // dynamic shared memory arena, reused phase by phase: the four RS x RS
+    // float64 matrices of the recompression (+ Gram staging), the pivot-search
+    // tiles (2 RF TM complex T, TM = 64 float / 32 double) and the eq. (norm)
+    // staging (33 (32 + RF) complex T)
+    const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
+                                std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>));
     const size_t tile_bytes = 2 * (size_t)RF * (sizeof(T) == 4 ? 64 : 32) * sizeof(Cx<T>);
-    const size_t smem = std::max(2 * (size_t)RF * RF * sizeof(Cx<double>), tile_bytes);
+    const size_t gram_bytes = 33 * (size_t)(32 + RF) * sizeof(Cx<T>);
+    const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
+                             (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
+    const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
     int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 0;
     if (per_sm == 0) {
         if (kernel == G3_SLP) per_sm = occupancy<G3_SLP, T, NT>(smem);
         else if (kernel == G3_DLP) per_sm = occupancy<G3_DLP, T, NT>(smem);
         else per_sm = occupancy<G3_SEPARABLE, T, NT>(smem);
     }
-    int grid = o.unbatched ? 1 : std::min(n_far, ctx->n_sm * per_sm);
+    int grid = o.unbatched ? 1 : std::min(n_run, ctx->n_sm * per_sm);
     const size_t stride = al256(ws_bytes<T>(RF, Mmax, Nmax, Ku, Ku));
     DevBuf d_ws;
     G3_CUDA(d_ws.alloc(stride * grid));
     G3_CUDA(fa->d_rec.alloc((size_t)n_far * Ku * sizeof(CrossRec)));
     G3_CUDA(fa->d_r3.alloc((size_t)n_far * sizeof(int)));
+    G3_CUDA(fa->d_cycles.alloc((size_t)n_far * sizeof(long long)));
     // factor pool: initial estimate, regrown on overflow
     double pf = o.pool_factor > 0 ? o.pool_factor : 1.0;
     long long cap = (long long)(pf * (double)(sumMN * 16 * 12 + (long long)n_far * Ku * 16));
@@ -1004,9 +1352,11 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         G3_CUDA(fa->pool.alloc((size_t)cap * sizeof(Cx<T>)));
         fa->pool_cap = cap;
         G3_CUDA(cudaMemsetAsync(d_head.p, 0, sizeof(int), ctx->stream));
-        G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 8 * sizeof(unsigned long long), ctx->stream));
+        G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 16 * sizeof(unsigned long long), ctx->stream));
         G3_CUDA(cudaMemsetAsync(d_ctr.p, 0, sizeof(unsigned long long), ctx->stream));
         G3_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
+        G3_CUDA(cudaMemsetAsync(fa->d_r3.p, 0, (size_t)n_far * sizeof(int), ctx->stream));
+        G3_CUDA(cudaMemsetAsync(fa->d_cycles.p, 0, (size_t)n_far * sizeof(long long), ctx->stream));
         AcaArgs<T> A{};
         A.gf = t ? t->gf : GeomF{};
         A.gd = t ? t->gd : GeomD{};
@@ -1015,7 +1365,7 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.Ku = Ku;
         A.k_maxabs = f ? f->k_maxabs : Ku - 1;
         A.ranges = d_ranges.as<BlockRange>();
-        A.n_far = n_far;
+        A.n_far = n_run;
         A.queue = d_queue.as<int>();
         A.queue_head = d_head.as<int>();
         A.single = -1;
@@ -1023,13 +1373,14 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.Cmax = Ku;
         A.RF = RF;
         A.eps3 = eps3;
-        A.eps_face = eps3 / 100.0;
+        A.eps_face = eps_face;
         A.no_recompress = o.no_recompress;
         A.pool = fa->pool.as<Cx<T>>();
         A.pool_cap = cap;
         A.pool_ctr = d_ctr.as<unsigned long long>();
         A.rec = fa->d_rec.as<CrossRec>();
         A.r3 = fa->d_r3.as<int>();
+        A.blk_cycles = fa->d_cycles.as<long long>();
         A.counters = d_counters.as<unsigned long long>();
         A.status = ctx->status.as<unsigned>();
         A.ws = d_ws.as<char>();
@@ -1038,7 +1389,7 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.Nmax = Nmax;
         G3_CUDA(cudaEventRecord(e0, ctx->stream));
         g3_status st = G3_OK;
-        const int launches = o.unbatched ? n_far : 1;
+        const int launches = o.unbatched ? n_run : 1;
         for (int l = 0; l < launches && st == G3_OK; ++l) {
             if (o.unbatched) A.single = l;
             if (kernel == G3_SLP) st = launch_aca_t<G3_SLP, T, NT>(ctx, A, grid, smem);
@@ -1060,22 +1411,28 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
             cap = std::max(cap * 2, (long long)(ctr * 5 / 4));
             continue;
         }
-        unsigned long long cnt[8];
+        unsigned long long cnt[16];
         G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
         fa->r3.resize(n_far);
         G3_CUDA(cudaMemcpy(fa->r3.data(), fa->d_r3.p, n_far * sizeof(int), cudaMemcpyDeviceToHost));
+        fa->cycles.resize(n_far);
+        G3_CUDA(cudaMemcpy(fa->cycles.data(), fa->d_cycles.p, n_far * sizeof(long long), cudaMemcpyDeviceToHost));
         fa->rec.resize((size_t)n_far * Ku);
         G3_CUDA(cudaMemcpy(fa->rec.data(), fa->d_rec.p, fa->rec.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
         g3_stats& S = fa->stats;
         S = g3_stats{};
         S.n_far = n_far;
+        S.blocks_run = n_run;
         S.entries = (int64_t)cnt[0];
         S.crosses_computed = (int64_t)cnt[1];
         S.zero_blocks = (int32_t)cnt[2];
         S.capped_faces = (int32_t)cnt[3];
         S.pool_regrows = regrows;
+        S.recompress_fallbacks = (int32_t)cnt[4];
         S.status_bits = (int32_t)status;
         S.ms = ms_total;
+        for (int i = 0; i < 7; ++i) S.phase_cycles[i] = (int64_t)cnt[8 + i];
+        S.ctas = grid;
         for (int b = 0; b < n_far; ++b) {
             const int M = ranges[b].re - ranges[b].rb, N = ranges[b].ce - ranges[b].cb;
             S.crosses += fa->r3[b];

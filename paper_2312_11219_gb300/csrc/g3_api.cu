@@ -442,6 +442,23 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     }
     nf->row_start.push_back((int)nf->order.size());
     nf->n_entries = off;
+    // position of every self entry (p, p): the diagonal leaf block (tau, tau)
+    // is non-admissible (dist = 0), so each element has exactly one
+    std::vector<long long> diag_base(t->ne, -1);
+    std::vector<int> diag_mn(t->ne, 0);
+    for (size_t i = 0; i < rg.size(); ++i) {
+        const BlockRange& r = rg[i];
+        for (int p = std::max(r.rb, r.cb); p < std::min(r.re, r.ce); ++p) {
+            const int N = r.ce - r.cb;
+            diag_base[p] = nf->offs[i] + (long long)(p - r.rb) * N + (p - r.cb);
+            diag_mn[p] = (r.re - r.rb) * N;
+        }
+    }
+    for (int p = 0; p < t->ne; ++p)
+        if (diag_base[p] < 0) {
+            delete nf;
+            return fail(G3_EINVAL, "assemble_near: element %d has no diagonal near block", p);
+        }
     const size_t esz = prec == G3_MIXED ? 8 : 16;
     g3_status st = G3_OK;
     auto chk = [&](cudaError_t e, const char* w) {
@@ -451,6 +468,12 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     chk(nf->d_ranges.alloc(rg.size() * sizeof(BlockRange)), "assemble_near: ranges");
     chk(nf->d_offs.alloc(nf->offs.size() * sizeof(long long)), "assemble_near: offsets");
     chk(nf->d_row_start.alloc(nf->row_start.size() * sizeof(int)), "assemble_near: rows");
+    chk(nf->d_diag_base.alloc(t->ne * sizeof(long long)), "assemble_near: diagonal offsets");
+    chk(nf->d_diag_mn.alloc(t->ne * sizeof(int)), "assemble_near: diagonal sizes");
+    if (st == G3_OK) {
+        chk(cudaMemcpyAsync(nf->d_diag_base.p, diag_base.data(), t->ne * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream), "copy");
+        chk(cudaMemcpyAsync(nf->d_diag_mn.p, diag_mn.data(), t->ne * sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "copy");
+    }
     if (st == G3_OK && !rg.empty()) {
         chk(cudaMemcpyAsync(nf->d_ranges.p, rg.data(), rg.size() * sizeof(BlockRange), cudaMemcpyHostToDevice, ctx->stream), "copy");
         chk(cudaMemcpyAsync(nf->d_offs.p, nf->offs.data(), nf->offs.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream), "copy");
@@ -587,6 +610,12 @@ g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3) {
     return G3_OK;
 }
 
+g3_status g3_factors_block_cycles(const g3_factors* fa, int64_t* cycles) {
+    G3_CHECK(fa && cycles, "g3_factors_block_cycles: NULL argument");
+    for (size_t i = 0; i < fa->cycles.size(); ++i) cycles[i] = (int64_t)fa->cycles[i];
+    return G3_OK;
+}
+
 g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t* face_ranks, double* U, double* V,
                                double* fib, int32_t* piv) {
     G3_CHECK(fa != nullptr, "g3_factors_get_block: NULL handle");
@@ -659,6 +688,13 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
     G3_CUDA(cudaMemcpyAsync(Y, ctx->stage_y.p, ybytes, cudaMemcpyDeviceToHost, ctx->stream));
     G3_CUDA(cudaStreamSynchronize(ctx->stream));
     return G3_OK;
+}
+
+g3_status g3_peak(g3_ctx* ctx, int kind, double* ops_per_s, double* ms) {
+    G3_CHECK(ctx && ops_per_s, "g3_peak: NULL argument");
+    G3_CHECK(kind >= 0 && kind <= 5, "g3_peak: kind %d outside [0, 5]", kind);
+    G3_TRY(use_device(ctx));
+    return run_peak(ctx, kind, ops_per_s, ms);
 }
 
 g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* near_ms, int64_t* near_bytes) {

@@ -34,6 +34,11 @@ template <class T>
 __device__ __forceinline__ T cabs2(Cx<T> a) {
     return a.x * a.x + a.y * a.y;
 }
+// |a|^2 evaluated in float64 (no underflow for tiny float32 values)
+template <class T>
+__device__ __forceinline__ double cabs2d(Cx<T> a) {
+    return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+}
 template <class T>
 __device__ __forceinline__ void cfma(Cx<T>& acc, Cx<T> a, Cx<T> b) {  // acc += a * b
     acc.x = fma(a.x, b.x, acc.x);

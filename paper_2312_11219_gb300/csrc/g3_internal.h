@@ -176,6 +176,8 @@ struct g3_near {
     g3::DevBuf d_ranges;              // BlockRange per sorted near block
     g3::DevBuf d_offs;                // long long per sorted near block
     g3::DevBuf d_row_start;
+    g3::DevBuf d_diag_base;           // long long [ne]: offset of entry (p, p) at k = 0
+    g3::DevBuf d_diag_mn;             // int [ne]: M_b * N_b of the diagonal block of p
     const g3_freqs* freqs = nullptr;
     std::vector<int32_t> partner_u;   // unique index -> full index of partner (or -1)
 };
@@ -189,6 +191,8 @@ struct g3_factors {
     long long pool_cap = 0;            // elements
     g3::DevBuf d_rec;                  // CrossRec [n_far][Cmax]
     g3::DevBuf d_r3;                   // int [n_far]
+    g3::DevBuf d_cycles;               // long long [n_far]
+    std::vector<long long> cycles;     // host copy of the per-block cycle counts
     std::vector<int32_t> r3;
     std::vector<g3::CrossRec> rec;     // host copy
     std::vector<g3::BlockRange> ranges;
@@ -211,6 +215,7 @@ g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* 
 g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
                     int dtype, int mode);
 g3_status gl_table(g3_ctx* ctx);
+g3_status run_peak(g3_ctx* ctx, int kind, double* ops_per_s, double* ms);
 
 // host tree builder (bit-exact specification)
 g3_status build_tree_host(g3_tree* t);

@@ -328,7 +328,8 @@ g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int k
 // One CTA per (near block, chunk of KCH unique frequencies).  Threads run
 // over the M_b * N_b entries of the block; each thread sets up the pair
 // geometry once and evaluates it at the KCH frequencies.  Layout of a block:
-// [k][i][j] (frequency-major), complex, starting at offs[b].
+// [k][i][j] (frequency-major), complex, starting at offs[b].  Self entries
+// (i == j) are left to k_near_self.
 template <int KER, class T, int KCH>
 __global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2* __restrict__ sd,
                                               const BlockRange* __restrict__ ranges,
@@ -342,18 +343,7 @@ __global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2*
     const int kn = min(KCH, Ku - k0);
     for (int e = threadIdx.x; e < MN; e += blockDim.x) {
         int i = br.rb + e / N, j = br.cb + e % N;
-        if (i == j) {
-            for (int kk = 0; kk < kn; ++kk) {
-                double2 s = sd[k0 + kk];
-                Cx<T> v{0, 0};
-                if (KER == G3_SLP) {
-                    Cx<double> d = slp_self_f64(gd, i, s.x, s.y);
-                    v = {(T)d.x, (T)d.y};
-                }
-                out[base + (long long)(k0 + kk) * MN + e] = v;
-            }
-            continue;
-        }
+        if (i == j) continue;
         Pair7<T> p;
         if constexpr (sizeof(T) == 4)
             pair_setup<KER>(gf, i, j, p);
@@ -366,6 +356,25 @@ __global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2*
     }
 }
 
+// Self entries of the near field, float64: one thread per (element p, unique
+// frequency k); the entry (p, p) of the diagonal leaf block sits at
+// diag_base[p] + k * diag_mn[p].
+template <int KER, class T>
+__global__ void k_near_self(GeomD gd, const double2* __restrict__ sd, int E, int Ku,
+                            const long long* __restrict__ diag_base, const int* __restrict__ diag_mn,
+                            Cx<T>* __restrict__ out) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)E * Ku) return;
+    const int p = (int)(idx % E), k = (int)(idx / E);
+    Cx<T> v{0, 0};
+    if (KER == G3_SLP) {
+        double2 s = sd[k];
+        Cx<double> d = slp_self_f64(gd, p, s.x, s.y);
+        v = Cx<T>{(T)d.x, (T)d.y};
+    }
+    out[diag_base[p] + (long long)k * diag_mn[p]] = v;
+}
+
 g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf, int kernel, int scheme) {
     if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "assemble_near: only G3_COLLOC7 is implemented");
     const int nb = (int)nf->order.size();
@@ -375,16 +384,30 @@ g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near*
     const double2* sd = f->d_sd.as<double2>();
     const BlockRange* rg = nf->d_ranges.as<BlockRange>();
     const long long* of = nf->d_offs.as<long long>();
+    const long long* db = nf->d_diag_base.as<long long>();
+    const int* dm = nf->d_diag_mn.as<int>();
+    const int sgrid = (int)(((long long)t->ne * f->Ku + 255) / 256);
     if (nf->prec == G3_MIXED) {
         Cx<float>* o = nf->data.as<Cx<float>>();
-        if (kernel == G3_SLP) k_near<G3_SLP, float, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
-        else k_near<G3_DLP, float, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+        if (kernel == G3_SLP) {
+            k_near<G3_SLP, float, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+            k_near_self<G3_SLP, float><<<sgrid, 256, 0, ctx->stream>>>(t->gd, sd, t->ne, f->Ku, db, dm, o);
+        } else {
+            k_near<G3_DLP, float, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+            k_near_self<G3_DLP, float><<<sgrid, 256, 0, ctx->stream>>>(t->gd, sd, t->ne, f->Ku, db, dm, o);
+        }
     } else {
         Cx<double>* o = nf->data.as<Cx<double>>();
-        if (kernel == G3_SLP) k_near<G3_SLP, double, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
-        else k_near<G3_DLP, double, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+        if (kernel == G3_SLP) {
+            k_near<G3_SLP, double, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+            k_near_self<G3_SLP, double><<<sgrid, 256, 0, ctx->stream>>>(t->gd, sd, t->ne, f->Ku, db, dm, o);
+        } else {
+            k_near<G3_DLP, double, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, sd, rg, of, f->Ku, o);
+            k_near_self<G3_DLP, double><<<sgrid, 256, 0, ctx->stream>>>(t->gd, sd, t->ne, f->Ku, db, dm, o);
+        }
     }
     ctx->count("k_near");
+    ctx->count("k_near_self");
     G3_CUDA(cudaGetLastError());
     return G3_OK;
 }
