@@ -194,6 +194,22 @@ def oracle_sample(name: str, seconds: float, seed: int, cores: int) -> dict:
 # our arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(values: list[float], device=None) -> list[float]:
+    """Element-wise maximum of `values` over all ranks (identity for one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float, steps: int) -> float:
+    """Units processed by all ranks per second, timed by the slowest rank."""
+    return units_per_rank * world / ((ms_max / steps) / 1e3)
+
+
 def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     import numpy as np
     import torch
@@ -265,17 +281,13 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     # end to end through the C ABI with host buffers (mesh in, densities in, y out)
     e_steps = max(1, args.steps // 2)
     erecs, ems = timed(e_steps, host=True)
-    t_max, e_max = ms, ems
-    if world > 1:
-        t = torch.tensor([ms, ems], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max, e_max = float(t[0]), float(t[1])
+    t_max, e_max = max_over_ranks([ms, ems], device=dev)
     if rank != 0:
         return None
     r0 = recs[-1]
     entries = r0["entries_aca"] + r0["entries_near"]
     ms_step = t_max / args.steps
-    value = entries * world / (ms_step / 1e3)
+    value = whole_job_rate(entries, world, t_max, args.steps)
     peaks = _peaks()
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
@@ -326,7 +338,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "storage_ratio": r0["factor_bytes"] / r0["dense_bytes"] if r0["dense_bytes"] else None,
         "crosses": r0["crosses"],
         "gpu_launches": int(launches),
-        "e2e": {"value": entries * world / ((e_max / e_steps) / 1e3), "unit": "entries/s",
+        "e2e": {"value": whole_job_rate(entries, world, e_max, e_steps), "unit": "entries/s",
                 "h2d_bytes_per_step": int(w.verts.nbytes + w.tris.nbytes + len(kernels) * W.nbytes),
                 "d2h_bytes_per_step": int(len(kernels) * w.E * 16)},
         "roofline": {"bound": "alu", "achieved": achieved_sfu / 1e12, "peak": sfu_peak / 1e12,

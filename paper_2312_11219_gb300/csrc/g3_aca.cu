@@ -45,6 +45,7 @@ struct AcaArgs {
     GeomD gd;
     SepView<T> sep;
     const double2* sd;
+    const float2* sf;        // the unique frequencies rounded once to float32
     int Ku, k_maxabs;
     const BlockRange* ranges;
     int n_far;
@@ -149,7 +150,7 @@ struct BlockSh {
     double sig[RF_MAX];
     double dU[RF_MAX], dV[RF_MAX];
     int sel[RF_MAX];
-    ArgMax am[32];
+    ArgMaxT<T> am[32];
     double red[64];
     double norm2;
     double hself;            // ||H_l||^2
@@ -163,22 +164,29 @@ struct BlockSh {
     int ip, jp;
 };
 
-template <int NT>
-__device__ __forceinline__ ArgMax block_argmax(ArgMax a, ArgMax* sh) {
+template <int NT, class V>
+__device__ __forceinline__ ArgMaxT<V> block_argmax(ArgMaxT<V> a, ArgMaxT<V>* sh) {
     a = warp_argmax(a);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) sh[w] = a;
     __syncthreads();
     if (w == 0) {
-        ArgMax b = (l < NT / 32) ? sh[l] : ArgMax{-1.0, LLONG_MAX};
+        ArgMaxT<V> b = (l < NT / 32) ? sh[l] : amax_none<V>();
         b = warp_argmax(b);
         if (l == 0) sh[0] = b;
     }
     __syncthreads();
-    ArgMax r = sh[0];
+    ArgMaxT<V> r = sh[0];
     __syncthreads();
     return r;
 }
+
+template <class T>
+__device__ __forceinline__ T tiny_norm2();
+template <>
+__device__ __forceinline__ float tiny_norm2<float>() { return 1.1754944e-38f; }
+template <>
+__device__ __forceinline__ double tiny_norm2<double>() { return 2.2250738585072014e-308; }
 
 // ---- entry access ----------------------------------------------------------------
 template <int KER, class T>
@@ -193,8 +201,13 @@ __device__ __forceinline__ Cx<T> ent(const AcaArgs<T>& A, int gi, int gj, int k)
         }
         return acc;
     } else {
-        double2 s = A.sd[k];
-        return colloc_entry<KER, T>(A.gf, A.gd, gi, gj, (T)s.x, (T)s.y, s.x, s.y);
+        if constexpr (sizeof(T) == 4) {
+            const float2 s = A.sf[k];
+            return colloc_entry<KER, T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        } else {
+            const double2 s = A.sd[k];
+            return colloc_entry<KER, T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        }
     }
 }
 
@@ -249,11 +262,13 @@ __device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, i
     } else {
         if (G >= 8) {
             if (part >= 7) return Cx<T>{0, 0};
-            double2 s = A.sd[k];
-            if constexpr (sizeof(T) == 4)
-                return colloc_q<KER>(A.gf, gi, gj, part, (T)s.x, (T)s.y);
-            else
-                return colloc_q<KER>(A.gd, gi, gj, part, (T)s.x, (T)s.y);
+            if constexpr (sizeof(T) == 4) {
+                const float2 s = A.sf[k];
+                return colloc_q<KER>(A.gf, gi, gj, part, s.x, s.y);
+            } else {
+                const double2 s = A.sd[k];
+                return colloc_q<KER>(A.gd, gi, gj, part, s.x, s.y);
+            }
         }
         return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
     }
@@ -352,8 +367,8 @@ __device__ void line_coeffs(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, 
 // partial sums) and the quadrature points.  Returns the block-wide argmax of
 // |out|^2 (ROW: over all columns; !ROW: over the rows not yet used).
 template <int KER, class T, int NT, bool ROW>
-__device__ ArgMax residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int fix,
-                                int kf, int m, Cx<T>* out) {
+__device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
+                                    int fix, int kf, int m, Cx<T>* out) {
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N;
     const int L = ROW ? N : M;
@@ -364,7 +379,7 @@ __device__ ArgMax residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>&
     const Cx<T>* cur = ROW ? w.vw : w.uw;
     const size_t ldc = ROW ? A.Nmax : A.Mmax;
     const int nt = F.ncol;
-    ArgMax am{-1.0, LLONG_MAX};
+    ArgMaxT<T> am = amax_none<T>();
     for (int base = 0; base < L; base += per) {
         const int v = base + tid / G;
         Cx<T> acc{0, 0};
@@ -419,7 +434,7 @@ __device__ ArgMax residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>&
         }
         if (part == 0 && v < L) {
             out[v] = acc;
-            if (ROW || !w.used[v]) am = amax_better(am, ArgMax{cabs2d(acc), (long long)v});
+            if (ROW || !w.used[v]) am = amax_better(am, ArgMaxT<T>{cabs2(acc), v});
         }
     }
     if (tid == 0) S.entries += L;
@@ -451,38 +466,44 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
         for (;;) {
             line_coeffs<T, NT, true>(A, w, S, F, irow, m);
             __syncthreads();
-            ArgMax am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row);
+            ArgMaxT<T> am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row);
             if (tid == 0) w.used[irow] = 1;
-            if (am.v > 0.0) {
-                jp = (int)am.i;
+            // a row counts as nonzero when |delta|^2 is a normal number of the
+            // working precision (below that the entries are far under any tolerance)
+            if (am.v > tiny_norm2<T>()) {
+                jp = am.i;
                 break;
             }
             // zero residual row: next unused row in index order
-            ArgMax un{-1.0, LLONG_MAX};
+            ArgMaxT<T> un = amax_none<T>();
             for (int i = tid; i < M; i += NT)
-                if (i != irow && !w.used[i]) un = amax_better(un, ArgMax{0.0, (long long)i});
+                if (i != irow && !w.used[i]) un = amax_better(un, ArgMaxT<T>{(T)0, i});
             un = block_argmax<NT>(un, S.am);
             if (un.v < 0.0) {
                 irow = -1;
                 break;
             }
-            irow = (int)un.i;
+            irow = un.i;
         }
         if (jp < 0) break;  // no row with a nonzero residual left
-        // v = conj(row / delta), formed in float64 so that a tiny pivot of a
-        // strongly damped face cannot overflow 1 / |delta|^2 in float32
-        const Cx<double> delta = ccast<double>(F.row[jp]);
-        const double dn = 1.0 / (delta.x * delta.x + delta.y * delta.y);
+        // v = conj(row / delta) with delta scaled to magnitude ~1 first, so that a
+        // tiny pivot of a strongly damped face cannot overflow 1 / |delta|^2
+        // (|row[j]| <= |delta| since delta is the row's largest entry)
+        const Cx<T> delta = F.row[jp];
+        const T sc = (T)1 / fmax(fabs(delta.x), fabs(delta.y));
+        const Cx<T> ds{delta.x * sc, delta.y * sc};
+        const T dn = (T)1 / cabs2(ds);
         Cx<T>* vm = w.vw + (size_t)m * A.Nmax;
         for (int j = tid; j < N; j += NT) {
-            Cx<double> q = cmulc(ccast<double>(F.row[j]), delta);  // row conj(delta)
-            vm[j] = Cx<T>{(T)(q.x * dn), (T)(-q.y * dn)};           // conj(row / delta)
+            const Cx<T> rj = F.row[j];
+            const Cx<T> q = cmulc(Cx<T>{rj.x * sc, rj.y * sc}, ds);  // (row / s) conj(delta / s)
+            vm[j] = Cx<T>{q.x * dn, -q.y * dn};                      // conj(row / delta)
         }
         line_coeffs<T, NT, false>(A, w, S, F, jp, m);
         __syncthreads();
         // residual column jp = u_m; the argmax over unused rows of |u_m| is the next row
         Cx<T>* um = w.uw + (size_t)m * A.Mmax;
-        ArgMax nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um);
+        ArgMaxT<T> nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um);
         // recursive Frobenius norm of the face approximant:
         // ||S_m||^2 = ||S_{m-1}||^2 + 2 Re sum_t (u_t^H u_m)(v_m^H v_t) + ||u_m||^2 ||v_m||^2
         const int wid = tid >> 5, lane = tid & 31;
@@ -492,11 +513,11 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             Cx<T> gu{0, 0}, gv{0, 0};
             for (int i = lane; i < M; i += 32) cfmac(gu, um[i], ut[i]);  // conj(u_t) u_m
             for (int j = lane; j < N; j += 32) cfmac(gv, vt[j], vm[j]);  // conj(v_m) v_t
-            double gux = warp_sum((double)gu.x), guy = warp_sum((double)gu.y);
-            double gvx = warp_sum((double)gv.x), gvy = warp_sum((double)gv.y);
+            const T gux = warp_sum(gu.x), guy = warp_sum(gu.y);
+            const T gvx = warp_sum(gv.x), gvy = warp_sum(gv.y);
             if (lane == 0) {
-                S.gu[t] = Cx<double>{gux, guy};
-                S.gv[t] = Cx<double>{gvx, gvy};
+                S.gu[t] = Cx<double>{(double)gux, (double)guy};
+                S.gv[t] = Cx<double>{(double)gvx, (double)gvy};
             }
         }
         __syncthreads();
@@ -510,8 +531,8 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             converged = true;
             break;
         }
-        if (nx.v < 0.0) break;  // every row used
-        irow = (int)nx.i;
+        if (nx.v < 0) break;  // every row used
+        irow = nx.i;
     }
     if (!converged && m == A.RF && m < min(M, N)) {
         if (tid == 0) {
@@ -669,11 +690,20 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     }
     __syncthreads();
     // one-sided Jacobi (Hestenes) on the columns of C, round-robin pair schedule;
-    // a pair is rotated while |<c_p, c_q>| > tol ||c_p|| ||c_q||
+    // a pair is rotated while |<c_p, c_q>| > tol ||c_p|| ||c_q||.  Column norms
+    // are recomputed at each sweep start and updated after every rotation
+    // (||c_p'||^2 = ||c_p||^2 - t |g|, ||c_q'||^2 = ||c_q||^2 + t |g|).
     const int n = (r + 1) & ~1;
     const T tol = jacobi_tol<T>();
+    T* cn = reinterpret_cast<T*>(S.sig);  // column norms (S.sig is free until the SVD finishes)
     for (int sweep = 0; sweep < 16; ++sweep) {
         if (tid == 0) S.rot = 0;
+        for (int a = wid; a < r; a += NT / 32) {
+            T s2 = 0;
+            for (int i = lane; i < r; i += 32) s2 += cabs2(shB[a * ld + i]);
+            s2 = warp_sum(s2);
+            if (lane == 0) cn[a] = s2;
+        }
         __syncthreads();
         for (int rho = 0; rho < n - 1; ++rho) {
             for (int pi = wid; pi < n / 2; pi += NT / 32) {
@@ -688,17 +718,13 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                 if (p >= r || q >= r) continue;
                 Cx<T>* bp = shB + p * ld;
                 Cx<T>* bq = shB + q * ld;
-                T al = 0, be = 0;
+                const T al = cn[p], be = cn[q];
                 Cx<T> ga{0, 0};
                 for (int i = lane; i < r; i += 32) {
                     Cx<T> x = bp[i], y = bq[i];
-                    al += x.x * x.x + x.y * x.y;
-                    be += y.x * y.x + y.y * y.y;
                     ga.x += x.x * y.x + x.y * y.y;
                     ga.y += x.x * y.y - x.y * y.x;
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
                 ga.x = warp_sum(ga.x);
                 ga.y = warp_sum(ga.y);
                 T ag = sqrt(ga.x * ga.x + ga.y * ga.y);
@@ -722,7 +748,11 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                         jp_[i] = Cx<T>{c * x.x - s * ey.x, c * x.y - s * ey.y};
                         jq_[i] = Cx<T>{s * ex.x + c * y.x, s * ex.y + c * y.y};
                     }
-                    if (lane == 0) atomicAdd(&S.rot, 1);
+                    if (lane == 0) {
+                        atomicAdd(&S.rot, 1);
+                        cn[p] = al - t * ag;
+                        cn[q] = be + t * ag;
+                    }
                 }
             }
             __syncthreads();
@@ -1051,7 +1081,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 Cx<T>* tu = reinterpret_cast<Cx<T>*>(smem_raw);  // [rn][TM]
                 Cx<T>* tv = tu + (size_t)RF * TM;                // [rn][TN]
                 const int tx = tid % TX, ty = tid / TX;
-                ArgMax best{-1.0, LLONG_MAX};
+                ArgMaxT<T> best = amax_none<T>();
                 for (int i0 = 0; i0 < M; i0 += TM) {
                     for (int j0 = 0; j0 < N; j0 += TN) {
                         for (int e = tid; e < rn * TM; e += NT) {
@@ -1086,7 +1116,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                                 for (int c = 0; c < RM; ++c) {
                                     int gi = i0 + ty * RM + a, gj = j0 + tx * RM + c;
                                     if (gi < M && gj < N)
-                                        best = amax_better(best, ArgMax{cabs2d(acc[a][c]), (long long)gi * N + gj});
+                                        best = amax_better(best, ArgMaxT<T>{cabs2(acc[a][c]), gi * N + gj});
                                 }
                         }
                         __syncthreads();
@@ -1095,11 +1125,11 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 best = block_argmax<NT>(best, S.am);
                 if (tid == 0) {
                     // no finite candidate (a non-finite face): report a vanishing pivot
-                    if (best.v < 0.0 || best.i < 0 || best.i >= (long long)M * N) {
+                    if (best.v < 0 || best.i < 0 || best.i >= M * N) {
                         S.ip = 0;
                         S.jp = 0;
                         S.hpiv = Cx<double>{0.0, 0.0};
-                        if (best.v >= 0.0) atomicOr(A.status, ST_BAD_INDEX);
+                        if (best.v >= 0) atomicOr(A.status, ST_BAD_INDEX);
                     } else {
                         S.ip = (int)(best.i / N);
                         S.jp = (int)(best.i % N);
@@ -1194,12 +1224,12 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             lap(5);
             if (S.flag) break;
             // next frequency: argmax over unused k of |f_l[k]|
-            ArgMax nk{-1.0, LLONG_MAX};
+            ArgMaxT<T> nk = amax_none<T>();
             for (int k = tid; k < Ku; k += NT)
-                if (!((S.used_k[k >> 5] >> (k & 31)) & 1u)) nk = amax_better(nk, ArgMax{cabs2(w.fib[k]), (long long)k});
+                if (!((S.used_k[k >> 5] >> (k & 31)) & 1u)) nk = amax_better(nk, ArgMaxT<T>{(T)cabs2(w.fib[k]), k});
             nk = block_argmax<NT>(nk, S.am);
-            if (nk.v < 0.0 || nk.i < 0 || nk.i >= Ku) break;  // no finite candidate left
-            if (tid == 0) S.k = (int)nk.i;
+            if (nk.v < 0 || nk.i < 0 || nk.i >= Ku) break;  // no finite candidate left
+            if (tid == 0) S.k = nk.i;
             __syncthreads();
             lap(6);
         }
@@ -1362,6 +1392,7 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.gd = t ? t->gd : GeomD{};
         A.sep = sv;
         A.sd = f ? f->d_sd.as<double2>() : nullptr;
+        A.sf = f ? f->d_sf.as<float2>() : nullptr;
         A.Ku = Ku;
         A.k_maxabs = f ? f->k_maxabs : Ku - 1;
         A.ranges = d_ranges.as<BlockRange>();

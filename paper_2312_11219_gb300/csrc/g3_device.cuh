@@ -226,11 +226,10 @@ __device__ inline Cx<double> slp_self_f64(const GeomD& g, int e, double sre, dou
 // ---- full collocation entry (any i, j) in working precision ----------------------
 // Self entries (i == j): float64 routine (SLP), 0 (DLP: x_i lies in the plane).
 template <int KER, class T>
-__device__ __forceinline__ Cx<T> colloc_entry(const GeomF& gf, const GeomD& gd, int i, int j, T sre, T sim,
-                                             double sre_d, double sim_d) {
+__device__ __forceinline__ Cx<T> colloc_entry(const GeomF& gf, const GeomD& gd, int i, int j, T sre, T sim) {
     if (i == j) {
         if (KER == G3_DLP) return {0, 0};
-        Cx<double> v = slp_self_f64(gd, i, sre_d, sim_d);
+        Cx<double> v = slp_self_f64(gd, i, (double)sre, (double)sim);
         return {(T)v.x, (T)v.y};
     }
     Pair7<T> p;
@@ -249,25 +248,34 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// argmax with ties to the smallest index; val < 0 means "no candidate"
-struct ArgMax {
-    double v;
-    long long i;
+// argmax with ties to the smallest index; v < 0 means "no candidate".  The
+// value type is the working precision (float32 compares stay off the float64
+// pipe, which runs at a small fraction of the float32 rate on this part).
+template <class V>
+struct ArgMaxT {
+    V v;
+    int i;
 };
-__device__ __forceinline__ ArgMax amax_better(ArgMax a, ArgMax b) {
+template <class V>
+__device__ __forceinline__ ArgMaxT<V> amax_better(ArgMaxT<V> a, ArgMaxT<V> b) {
     if (b.v > a.v) return b;
     if (b.v == a.v && b.i < a.i && b.v >= 0) return b;
     return a;
 }
-__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+template <class V>
+__device__ __forceinline__ ArgMaxT<V> warp_argmax(ArgMaxT<V> a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        ArgMax b;
+        ArgMaxT<V> b;
         b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
         b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
         a = amax_better(a, b);
     }
     return a;
+}
+template <class V>
+__device__ __forceinline__ ArgMaxT<V> amax_none() {
+    return ArgMaxT<V>{(V)-1, 0x7fffffff};
 }
 
 }  // namespace g3

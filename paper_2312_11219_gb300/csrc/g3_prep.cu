@@ -295,7 +295,13 @@ __global__ void k_entries(GeomF gf, GeomD gd, const double2* __restrict__ sd, co
     int pr = (int)(idx / nk), m = (int)(idx % nk);
     int i = rows[pr], j = cols[pr];
     double2 s = sd[ku[m]];
-    Cx<T> v = colloc_entry<KER, T>(gf, gd, i, j, (T)s.x, (T)s.y, s.x, s.y);
+    Cx<T> v;
+    if (i == j && KER == G3_SLP) {  // self entries: float64 with the float64 frequency
+        Cx<double> d = slp_self_f64(gd, i, s.x, s.y);
+        v = Cx<T>{(T)d.x, (T)d.y};
+    } else {
+        v = colloc_entry<KER, T>(gf, gd, i, j, (T)s.x, (T)s.y);
+    }
     double im = conj[m] ? -(double)v.y : (double)v.y;
     out[idx] = make_double2((double)v.x, im);
 }
