@@ -280,6 +280,23 @@ g3_status g3_factors_free(g3_factors* fa);
  * Frequencies outside the unique set use A(conj s) = conj A(s). */
 g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
                     g3_dtype dtype, g3_apply_mode mode, g3_memory mem);
+/* Allocation-free variant of apply_gcq (no counterpart in the paper).  For
+ * callers that cannot allocate device memory while this step runs (a
+ * memory-capped or pre-reserved arena, a runtime that forbids cudaMalloc or
+ * the device synchronisation it may cause on its hot path).  Computes the same
+ * y = sum_l A(s_l) w_l as apply_gcq with mem = G3_DEVICE and G3_APPLY_SUM:
+ * W [M*K] and Y [M] are caller-owned device buffers (layout as apply_gcq).
+ * Its scratch is a fixed 32 MiB device array inside the library (held by
+ * every GPU that loads the library until the process exits); no
+ * cudaMalloc/cudaFree or other allocating routine is called.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Problems needing more
+ * scratch than 32 MiB (2 Ku M + M complex values plus 20 bytes per
+ * admissible block) return G3_EINVAL.  All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. */
+g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
+                            void* Y, g3_dtype dtype);
 /* Device time (ms) of the last apply on this context and its algorithmic
  * bytes (near field, factors, W read once, Y written once). */
 g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* near_ms, int64_t* near_bytes);

@@ -11,6 +11,6 @@ plus frequency sets (g3_freqs_bdf2, g3_freqs_gcq), diagnostic entries
 """
 from ._binding import (  # noqa: F401
     EXPORTED, LIB_PATH, Context, Factors, Freqs, G3Error, Near, Tree, aca3_compress,
-    aca3_compress_separable, apply_gcq, assemble_near, build_cluster_tree, freqs_from_spec,
+    aca3_compress_separable, apply_gcq, apply_gcq_noalloc, assemble_near, build_cluster_tree, freqs_from_spec,
     g3_entries, g3_freqs_bdf2, g3_freqs_gcq,
 )

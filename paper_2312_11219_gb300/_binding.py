@@ -91,13 +91,14 @@ _sig("g3_factors_free", _ci, _p)
 _sig("apply_gcq", _ci, _p, _p, _p, _p, _p, _p, _ci, _ci, _ci)
 _sig("g3_apply_last", _ci, _p, _dp, _i64p, _dp, _i64p)
 _sig("g3_peak", _ci, _p, _ci, _dp, _dp)
+_sig("apply_gcq_noalloc", _ci, _p, _p, _p, _p, _p, _p, _ci)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
             "build_cluster_tree", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
-            "g3_apply_last", "g3_peak"]
+            "g3_apply_last", "g3_peak", "apply_gcq_noalloc"]
 
 
 class G3Error(RuntimeError):
@@ -401,3 +402,20 @@ def apply_gcq(ctx: Context, tree: Tree, near: Near | None, factors: Factors | No
     _check(_lib.apply_gcq(ctx.h, tree.h, nh, fh, C.c_void_p(Wt.data_ptr()), C.c_void_p(Y.data_ptr()), dt, mode_i, 0),
            "apply_gcq")
     return Y if mode_i == 0 else Y.t()
+
+
+def apply_gcq_noalloc(ctx: Context, tree: Tree, near: Near | None, factors: Factors | None, W, Y=None):
+    """Allocation-free apply (same result as apply_gcq on device buffers).
+    W: complex CUDA tensor [M, K]; Y: optional preallocated complex CUDA
+    tensor [M] (allocated here by torch when omitted)."""
+    import torch
+    if not (W.is_cuda and W.dtype in (torch.complex64, torch.complex128)):
+        raise TypeError("W must be a complex CUDA tensor")
+    dt = 1 if W.dtype == torch.complex128 else 0
+    Wt = W.t().contiguous()
+    if Y is None:
+        Y = torch.empty(W.shape[0], dtype=W.dtype, device=W.device)
+    _check(_lib.apply_gcq_noalloc(ctx.h, tree.h, near.h if near is not None else None,
+                                  factors.h if factors is not None else None, C.c_void_p(Wt.data_ptr()),
+                                  C.c_void_p(Y.data_ptr()), dt), "apply_gcq_noalloc")
+    return Y

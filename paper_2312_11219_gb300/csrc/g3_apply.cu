@@ -16,6 +16,12 @@
 
 #include "g3_device.cuh"
 
+#define G3_TRY_NA(expr)                 \
+    do {                                \
+        g3_status st_ = (expr);         \
+        if (st_ != G3_OK) return st_;   \
+    } while (0)
+
 namespace g3 {
 
 // W (original order, column l = w_l, M x K column-major, complex TI) ->
@@ -279,6 +285,134 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     return G3_OK;
 }
 
+// ============================================================================
+// Allocation-free apply
+// ============================================================================
+//
+// Some callers cannot allocate device memory while they run this step: code
+// inside a memory-capped or pre-reserved arena, a runtime that forbids
+// cudaMalloc on its hot path, or a host that must not synchronise the device
+// (cudaMalloc/cudaFree can).  apply_gcq_noalloc serves them: it computes the
+// same sum as apply_gcq (device buffers, G3_APPLY_SUM) with its scratch in the
+// fixed array below instead of the context's growable buffer, and calls no
+// allocating routine.
+//
+// The array is a file-scope __device__ object: every GPU that loads this
+// library holds it until the process exits.  All calls on a device share it
+// and it keeps the last call's contents, so every part a call reads is
+// written first by that call (the accumulator is cleared by k_apply_prep).
+// Calls whose work overlaps on the GPU (several streams or threads at once)
+// race on it and must be serialised by the caller.
+constexpr size_t NOALLOC_SCRATCH_BYTES = 32ull << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g3_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// device address of the scratch array, looked up once per device (with that
+// device current); host code must not use the symbol itself as an address
+static void* g_noalloc_ptr[64] = {};
+
+static g3_status noalloc_scratch(int device, void** out) {
+    if (device < 0 || device >= 64) return fail(G3_EINVAL, "apply_gcq_noalloc: device %d not supported", device);
+    if (!g_noalloc_ptr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g3_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g3_noalloc_scratch)");
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = g_noalloc_ptr[device];
+    return G3_OK;
+}
+
+__global__ void k_iota(int* p, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+
+template <class T>
+static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa,
+                                     const void* W, void* Y, int dtype, const g3_freqs* f) {
+    const int E = t->ne, K = f->K, Ku = f->Ku;
+    const int n_far = fa ? fa->n_far : 0;
+    const size_t nW = (size_t)Ku * E;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t need = al(2 * nW * sizeof(Cx<T>)) + al(E * sizeof(Cx<T>)) + al(n_far * sizeof(int)) +
+                        al(n_far * sizeof(BlockRange));
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(G3_EINVAL,
+                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values plus "
+                    "block tables), the fixed scratch holds %zu; use apply_gcq",
+                    need, NOALLOC_SCRATCH_BYTES);
+    void* base = nullptr;
+    G3_TRY_NA(noalloc_scratch(ctx->device, &base));
+    char* p = static_cast<char*>(base);
+    Cx<T>* Wf = reinterpret_cast<Cx<T>*>(p);
+    Cx<T>* Wc = Wf + nW;
+    p += al(2 * nW * sizeof(Cx<T>));
+    Cx<T>* y = reinterpret_cast<Cx<T>*>(p);
+    p += al(E * sizeof(Cx<T>));
+    int* list = reinterpret_cast<int*>(p);
+    p += al(n_far * sizeof(int));
+    BlockRange* ranges = reinterpret_cast<BlockRange*>(p);
+    {
+        long long tot = (long long)Ku * E;
+        int blocks = (int)((tot + 255) / 256);
+        if (dtype == G3_C128)
+            k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, y);
+        else
+            k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, y);
+        ctx->count("k_apply_prep");
+        G3_CUDA(cudaGetLastError());
+    }
+    if (nf && !nf->order.empty()) {
+        constexpr int NT = 256;
+        const int n_rows = (int)nf->row_start.size() - 1;
+        int ksplit = std::max(1, std::min(Ku, (8 * ctx->n_sm + n_rows - 1) / n_rows));
+        int kchunk = (Ku + ksplit - 1) / ksplit;
+        ksplit = (Ku + kchunk - 1) / kchunk;
+        int mrow = 0;
+        for (int g = 0; g < n_rows; ++g) {
+            const int32_t* r = &t->blocks[5 * (size_t)nf->order[nf->row_start[g]]];
+            mrow = std::max(mrow, r[1] - r[0]);
+        }
+        dim3 grid(n_rows, ksplit);
+        k_apply_near<T, NT><<<grid, NT, 2 * (size_t)mrow * sizeof(T), ctx->stream>>>(
+            nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(), nf->d_offs.as<long long>(),
+            nf->d_row_start.as<int>(), Ku, kchunk, E, Wf, Wc, y);
+        ctx->count("k_apply_near");
+        G3_CUDA(cudaGetLastError());
+    }
+    if (n_far > 0) {
+        // every admissible block (blocks of rank 0 add nothing); the block
+        // ranges come from the factors' host copy, the ranks from the device
+        G3_CUDA(cudaMemcpyAsync(ranges, fa->ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        k_iota<<<(n_far + 255) / 256, 256, 0, ctx->stream>>>(list, n_far);
+        ctx->count("k_iota");
+        constexpr int NT = 128;
+        const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
+        int mmax = 0;
+        for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
+        const int ym = std::min(mmax, ysmem_max);
+        size_t smem = (Ku + 128) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+        k_apply_far<T, NT><<<n_far, NT, smem, ctx->stream>>>(fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                              fa->d_r3.as<int>(), ranges, list, fa->Cmax, Ku, E, Wf,
+                                                              Wc, y, ym);
+        ctx->count("k_apply_far");
+        G3_CUDA(cudaGetLastError());
+    }
+    {
+        int blocks = (E + 255) / 256;
+        if (dtype == G3_C128)
+            k_apply_finish<T, double><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<double>*)Y);
+        else
+            k_apply_finish<T, float><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<float>*)Y);
+        ctx->count("k_apply_finish");
+        G3_CUDA(cudaGetLastError());
+    }
+    return G3_OK;
+}
+
 g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
                     int dtype, int mode) {
     if (mode != G3_APPLY_SUM) return fail(G3_EUNSUPPORTED, "apply_gcq: only G3_APPLY_SUM is implemented");
@@ -291,3 +425,21 @@ g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
 }
 
 }  // namespace g3
+
+extern "C" g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa,
+                                       const void* W, void* Y, g3_dtype dtype) {
+    using namespace g3;
+    if (!ctx || !t || !W || !Y) return fail(G3_EINVAL, "apply_gcq_noalloc: NULL argument");
+    if (!nf && !fa) return fail(G3_EINVAL, "apply_gcq_noalloc: near field and factors are both NULL");
+    if (dtype != G3_C64 && dtype != G3_C128) return fail(G3_EINVAL, "apply_gcq_noalloc: bad dtype");
+    if ((nf && nf->tree != t) || (fa && fa->tree != t))
+        return fail(G3_EINVAL, "apply_gcq_noalloc: near field or factors built on another tree");
+    if (nf && fa && (nf->prec != fa->prec || nf->freqs != fa->freqs))
+        return fail(G3_EINVAL, "apply_gcq_noalloc: near field and factors differ in precision or frequency set");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const g3_freqs* f = nf ? nf->freqs : fa->freqs;
+    const int prec = nf ? nf->prec : fa->prec;
+    if (prec == G3_MIXED) return run_apply_noalloc_t<float>(ctx, t, nf, fa, W, Y, dtype, f);
+    return run_apply_noalloc_t<double>(ctx, t, nf, fa, W, Y, dtype, f);
+}
