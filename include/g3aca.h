@@ -111,6 +111,12 @@ typedef struct {
                              not below 1e-5, the relative noise of float32 entries)        */
     int max_blocks;       /* > 0: compress only the first max_blocks admissible blocks (far
                              order); the others get rank 0 (bounded timing samples)         */
+    int dense_face_max;   /* blocks with M_b N_b <= this use exact dense faces (no low-rank
+                             face, the paper's "No Lwr" variant); 0 = 48*48, < 0 = never    */
+    int literal_stop;     /* 1 = stop on Algorithm 1's newest-cross test alone; 0 (default)
+                             = confirm each stop on 32 fixed sample entries over all
+                             frequencies (keeps the cross and continues when the sampled
+                             relative residual exceeds eps3)                               */
 } g3_opts;
 
 /* Statistics of one compression. */
@@ -134,6 +140,9 @@ typedef struct {
     int32_t ctas;             /* persistent CTAs launched                                 */
     int32_t recompress_fallbacks; /* faces kept unrecompressed (Cholesky breakdown)       */
     int32_t blocks_run;       /* blocks compressed (n_far unless opts->max_blocks)        */
+    int64_t dense_crosses;    /* kept crosses with a dense face (face_rank_sum excludes them) */
+    double ms_lowrank;        /* device time of the low-rank-face launch (last attempt)   */
+    double ms_dense;          /* device time of the dense-face launch (last attempt)      */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */
@@ -260,7 +269,8 @@ g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3);
  * diagnostics and cost labels for scheduling). */
 g3_status g3_factors_block_cycles(const g3_factors* fa, int64_t* cycles);
 /* Export block i's crosses to host.  Sizes first: call with U = V = fib = NULL
- * to get r3 and the face ranks in face_ranks [r3] (if non-NULL).  Then:
+ * to get r3 and the face ranks in face_ranks [r3] (if non-NULL; a dense face
+ * is exported as U = H (M_b x N_b), V = identity (N_b x N_b), rank N_b).  Then:
  *   U [sum_p M_b r_p] c128, column-major per cross, crosses concatenated;
  *   V [sum_p N_b r_p] c128, likewise (face_p = U_p V_p^H);
  *   fib [r3 * Ku] c128; piv [r3*3] int32 (i_l, j_l, k_l) local indices. */

@@ -39,6 +39,29 @@ Readings where the paper is silent (all shared with the CUDA path):
   that some frequencies are tested to confirm a zero block.  Up to three more
   unused frequencies are tested (the last unique one, the middle one, the one
   of largest |s|); if all faces are zero the block ends with rank l - 1.
+* Dense faces for small blocks: the paper also runs the three-way ACA
+  without low-rank approximation in the faces ("No Lwr", Section 5.1).  For
+  a block with M N <= dense_max the face H_l is the exact residual face
+  ENTRY(:, :, k_l) - C^(l-1)[:, :, k_l] (Algorithm 1 as written) and the
+  pivot is its largest entry; such blocks are where a face of rank r at the
+  face tolerance has r (M + N) >= M N, i.e. the low-rank form is no smaller
+  than the dense one.  A zero face then means an exactly zero residual face.
+* Confirmed stop (sample_check): the stopping test only measures the newest
+  cross.  On double-layer blocks whose rows and columns span two planar
+  faces (entries zero between coplanar elements, [[0, X], [Y, 0]]), the
+  pivots stay in the dominant part and the test passes at a frequency where
+  the approximation is already exact while other frequencies are off by
+  40-50 %.  When the test passes, the residual of the approximant including
+  the newest cross is therefore evaluated at S = 32 fixed sample entries
+  (rows (2s+1) M // 64, columns (2 (11 s mod 32) + 1) N // 64) over all
+  frequencies; if its Frobenius norm exceeds eps3 times that of the sampled
+  data, the newest cross is kept and the next frequency is the unused one
+  with the largest sampled residual.
+* Confirmed face convergence (sample_check): partial pivoting misses a
+  [[0, X], [Y, 0]] face (every visited row and column stays in X).  When the
+  face ACA's test passes, its residual is evaluated at the same 32 sample
+  positions; if (M N / 32) sum |R_s|^2 > eps_face^2 ||S||_F^2 the ACA
+  continues from the row of the largest sampled residual.
 """
 from __future__ import annotations
 
@@ -59,6 +82,9 @@ class BlockEntries:
         raise NotImplementedError
 
     def fiber(self, i: int, j: int) -> np.ndarray:
+        raise NotImplementedError
+
+    def face(self, k: int) -> np.ndarray:
         raise NotImplementedError
 
 
@@ -85,6 +111,12 @@ class BemBlock(BlockEntries):
         self.generated += self.Ku
         return self.f(self.rows[i:i + 1], self.cols[j:j + 1], self.s)[0]
 
+    def face(self, k):
+        self.generated += self.M * self.N
+        I = np.repeat(self.rows, self.N)
+        J = np.tile(self.cols, self.M)
+        return self.f(I, J, self.s[k:k + 1])[:, 0].reshape(self.M, self.N)
+
 
 class SeparableBlock(BlockEntries):
     """Synthetic test tensor A[i, j, k] = sum_t a[t, i] b[t, j] c[t, k]."""
@@ -106,11 +138,25 @@ class SeparableBlock(BlockEntries):
         self.generated += self.Ku
         return (self.a[:, i] * self.b[:, j]) @ self.c
 
+    def face(self, k):
+        self.generated += self.M * self.N
+        return np.einsum("ti,tj,t->ij", self.a, self.b, self.c[:, k])
+
     def dense(self) -> np.ndarray:
         return np.einsum("ti,tj,tk->ijk", self.a, self.b, self.c)
 
 
-def aca2(row_fn, col_fn, M: int, N: int, eps: float, max_rank: int | None = None):
+SAMPLES = 32
+
+
+def sample_entries(M: int, N: int) -> list[tuple[int, int]]:
+    """The fixed residual-check positions of an M x N block."""
+    return [((2 * s + 1) * M // (2 * SAMPLES), (2 * ((11 * s) % SAMPLES) + 1) * N // (2 * SAMPLES))
+            for s in range(SAMPLES)]
+
+
+def aca2(row_fn, col_fn, M: int, N: int, eps: float, max_rank: int | None = None,
+         sample_check: bool = False):
     """Partial-pivot ACA of a matrix given by residual row/column callbacks.
 
     Returns U [M, r], V [N, r] with the approximant S = U V^H.
@@ -149,7 +195,16 @@ def aca2(row_fn, col_fn, M: int, N: int, eps: float, max_rank: int | None = None
         us.append(u)
         vs.append(v)
         if np.sqrt(nu2 * nv2) <= eps * np.sqrt(norm2):
-            break
+            if not sample_check:
+                break
+            pos = sample_entries(M, N)
+            res = np.array([row_fn(a)[b] - sum(u_t[a] * np.conj(v_t[b]) for u_t, v_t in zip(us, vs))
+                            for a, b in pos])
+            mres = res.real * res.real + res.imag * res.imag
+            if (M * N / SAMPLES) * mres.sum() <= eps * eps * norm2:
+                break
+            i = pos[int(np.argmax(mres))][0]
+            continue
         free = np.nonzero(~used)[0]
         if free.size == 0:
             break
@@ -205,10 +260,15 @@ class Result:
         return out
 
 
+DENSE_MAX = 48 * 48
+
+
 def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
          s_abs: np.ndarray | None = None, max_face_rank: int | None = None,
-         k1: int = 0) -> Result:
-    """Algorithm 1 on one block (see module docstring for the readings)."""
+         k1: int = 0, dense_max: int = DENSE_MAX, sample_check: bool = True) -> Result:
+    """Algorithm 1 on one block (see module docstring for the readings).
+    Blocks with M N <= dense_max use exact dense faces (dense_max < 0: never);
+    sample_check confirms each stop on fixed sample entries."""
     if eps_face is None:
         eps_face = eps3 / 100.0
     M, N, Ku = op.M, op.N, op.Ku
@@ -220,7 +280,17 @@ def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
     k = k1
     ell = 0
 
+    dense = M * N <= dense_max
+
     def face_at(kk: int):
+        if dense:
+            H = op.face(kk)
+            for c in crosses:
+                H = H - c.f[kk] * (c.U @ c.V.conj().T)
+            if not np.any(H != 0):
+                return np.zeros((M, 0), complex), np.zeros((N, 0), complex)
+            return H, np.eye(N, dtype=complex)
+
         def row_fn(i):
             r = op.row(i, kk)
             for c in crosses:
@@ -233,7 +303,7 @@ def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
                 cc = cc - c.f[kk] * (c.U @ c.V[j, :].conj())
             return cc
 
-        return aca2(row_fn, col_fn, M, N, eps_face, max_face_rank)
+        return aca2(row_fn, col_fn, M, N, eps_face, max_face_rank, sample_check=sample_check)
 
     while True:
         ell += 1
@@ -255,7 +325,8 @@ def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
                     break
             if not found:
                 return Result(crosses, ell - 1, hist, zero_block=(ell == 1))
-        U, V = recompress(U, V, eps_face)
+        if not dense:
+            U, V = recompress(U, V, eps_face)
         H = U @ V.conj().T
         mag = H.real * H.real + H.imag * H.imag
         flat = int(np.argmax(mag))
@@ -273,12 +344,22 @@ def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
         norm2 += new + nH2 * nf2
         hist.append(norm2)
         cross = Cross(U, V, f, ip, jp, k)
+        resid = None
         if np.sqrt(nH2 * nf2) <= eps3 * np.sqrt(norm2):
-            return Result(crosses, ell, hist, zero_block=False)
+            if not sample_check or used.all():
+                return Result(crosses, ell, hist, zero_block=False)
+            A_s = np.array([op.fiber(i, j) for i, j in sample_entries(M, N)])          # [S, Ku]
+            C_s = np.zeros_like(A_s)
+            for c, Hd in zip(crosses + [cross], faces + [H]):
+                C_s += np.array([Hd[i, j] for i, j in sample_entries(M, N)])[:, None] * c.f[None, :]
+            R_s = A_s - C_s
+            if np.linalg.norm(R_s) <= eps3 * np.linalg.norm(A_s):
+                return Result(crosses, ell, hist, zero_block=False)
+            resid = np.sum(R_s.real ** 2 + R_s.imag ** 2, axis=0)
         crosses.append(cross)
         faces.append(H)
         if ell == Ku or used.all():
             return Result(crosses, ell, hist, zero_block=False)
-        fm = f.real * f.real + f.imag * f.imag
+        fm = f.real * f.real + f.imag * f.imag if resid is None else resid
         fm = np.where(used, -1.0, fm)
         k = int(np.argmax(fm))

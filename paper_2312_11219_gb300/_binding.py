@@ -40,7 +40,8 @@ class Opts(C.Structure):
     _fields_ = [("face_rank_max", C.c_int), ("unbatched", C.c_int), ("ctas_per_sm", C.c_int),
                 ("threads", C.c_int), ("no_recompress", C.c_int), ("order_by_cost", C.c_int),
                 ("k1", _i32p), ("cost", C.POINTER(C.c_float)), ("pool_factor", C.c_double),
-                ("eps_face", C.c_double), ("max_blocks", C.c_int)]
+                ("eps_face", C.c_double), ("max_blocks", C.c_int), ("dense_face_max", C.c_int),
+                ("literal_stop", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -49,7 +50,8 @@ class Stats(C.Structure):
                 ("dense_bytes", C.c_int64), ("r3_max", C.c_int32), ("face_rank_max", C.c_int32),
                 ("zero_blocks", C.c_int32), ("capped_faces", C.c_int32), ("pool_regrows", C.c_int32),
                 ("status_bits", C.c_int32), ("ms", C.c_double), ("phase_cycles", C.c_int64 * 7),
-                ("ctas", C.c_int32), ("recompress_fallbacks", C.c_int32), ("blocks_run", C.c_int32)]
+                ("ctas", C.c_int32), ("recompress_fallbacks", C.c_int32), ("blocks_run", C.c_int32),
+                ("dense_crosses", C.c_int64), ("ms_lowrank", C.c_double), ("ms_dense", C.c_double)]
 
 
 def _sig(name, res, *args):

@@ -37,6 +37,7 @@
 namespace g3 {
 
 constexpr int KU_MAX = 256;   // largest unique-frequency count
+constexpr int SAMPLES = 32;   // sample entries of the convergence checks
 constexpr int RF_MAX = 64;    // largest face rank cap
 
 template <class T>
@@ -54,6 +55,8 @@ struct AcaArgs {
     int single;              // >= 0: CTA 0 processes queue[single] only
     const int* k1;           // [n_far] first frequency per block, or null
     int Cmax, RF;
+    int dense_max;           // blocks with M N <= dense_max use exact dense faces
+    int sample_check;        // confirm each stop on fixed sample entries
     double eps3, eps_face;
     int no_recompress;
     Cx<T>* pool;
@@ -85,6 +88,8 @@ struct Ws {
     long long* colU;      // [Cmax * RF] flattened column tables (when they exceed shared memory)
     long long* colV;
     short* colP;
+    Cx<double>* hs;       // [SAMPLES][Cmax] H_p at the stop-check samples
+    double* rk;           // [Ku] sampled residual per frequency
 };
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -103,6 +108,8 @@ __host__ __device__ inline size_t ws_bytes(int RF, int Mmax, int Nmax, int Cmax,
     add((size_t)Cmax * RF * sizeof(long long));
     add((size_t)Cmax * RF * sizeof(long long));
     add((size_t)Cmax * RF * sizeof(short));
+    add((size_t)32 * Cmax * sizeof(Cx<double>));
+    add((size_t)Ku * sizeof(double));
     return b;
 }
 
@@ -128,6 +135,8 @@ __device__ inline Ws<T> ws_carve(char* base, int RF, int Mmax, int Nmax, int Cma
     w.colU = (long long*)take((size_t)Cmax * RF * sizeof(long long));
     w.colV = (long long*)take((size_t)Cmax * RF * sizeof(long long));
     w.colP = (short*)take((size_t)Cmax * RF * sizeof(short));
+    w.hs = (Cx<double>*)take((size_t)32 * Cmax * sizeof(Cx<double>));
+    w.rk = (double*)take((size_t)Ku * sizeof(double));
     return w;
 }
 
@@ -153,6 +162,9 @@ struct BlockSh {
     ArgMaxT<T> am[32];
     double red[64];
     double norm2;
+    double red2[2];          // sampled residual / data norms of the stop check
+    double samp[SAMPLES];    // |residual|^2 of the face approximant at the samples
+    int stop;
     double hself;            // ||H_l||^2
     double fself;            // ||f_l||^2
     Cx<double> hpiv;
@@ -441,6 +453,34 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
     return block_argmax<NT>(am, S.am);
 }
 
+// ---- sampled residual of the face approximant ------------------------------------------
+// R_s = ENTRY(i_s, j_s, kf) - sum_p f_p[kf] H_p[i_s, j_s] - sum_{t<m} u_t[i_s] conj(v_t[j_s])
+// at the 32 sample positions; one warp per sample, lanes over the flattened
+// columns of the earlier crosses.  Writes |R_s|^2 to S.samp.
+template <int KER, class T, int NT>
+__device__ void face_samples(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int kf,
+                             int m) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int M = S.M, N = S.N;
+    for (int sm = wid; sm < SAMPLES; sm += NT / 32) {
+        const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
+        Cx<T> acc{0, 0};
+        for (int c = lane; c < F.ncol; c += 32) {
+            const Cx<T> h = cmulc(A.pool[F.colU[c] + i], A.pool[F.colV[c] + j]);
+            cfma(acc, S.fk[F.colP[c]], h);
+        }
+        for (int t = lane; t < m; t += 32) cfmac(acc, w.uw[(size_t)t * A.Mmax + i], w.vw[(size_t)t * A.Nmax + j]);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        if (lane == 0) {
+            const Cx<T> e = ent<KER, T>(A, S.rb + i, S.cb + j, kf);
+            S.samp[sm] = cabs2d(Cx<T>{e.x - acc.x, e.y - acc.y});
+        }
+    }
+    if (threadIdx.x == 0) S.entries += SAMPLES;
+    __syncthreads();
+}
+
 // ---- face ACA (partial pivoting) on the residual face at frequency kf -----------------
 // Returns the rank m; columns 0..m-1 of uw / vw hold the crosses (S = U V^H).
 template <int KER, class T, int NT>
@@ -528,8 +568,29 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
         ++m;
         __syncthreads();
         if (sqrt(nu2 * nv2) <= A.eps_face * sqrt(fmax(Sn2, 0.0))) {
-            converged = true;
-            break;
+            if (!A.sample_check) {
+                converged = true;
+                break;
+            }
+            // confirm on the sample entries: partial pivoting can miss a block
+            // of the face that no visited row or column reaches
+            face_samples<KER, T, NT>(A, w, S, F, kf, m);
+            double tot = 0.0, best = -1.0;
+            int bs = 0;
+            for (int sm = 0; sm < SAMPLES; ++sm) {
+                tot += S.samp[sm];
+                if (S.samp[sm] > best) {
+                    best = S.samp[sm];
+                    bs = sm;
+                }
+            }
+            __syncthreads();
+            if ((double)M * (double)N / SAMPLES * tot <= A.eps_face * A.eps_face * fmax(Sn2, 0.0)) {
+                converged = true;
+                break;
+            }
+            irow = (2 * bs + 1) * M / (2 * SAMPLES);
+            continue;
         }
         if (nx.v < 0) break;  // every row used
         irow = nx.i;
@@ -915,8 +976,260 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
     __syncthreads();
 }
 
-// ---- the persistent kernel ---------------------------------------------------------
+// ---- confirmed stop --------------------------------------------------------------------
+// Algorithm 1's test measures only the newest cross.  When it passes, the
+// residual of the approximant with crosses 0..ncl-1 (the newest one included,
+// staged in S.off / S.r) is evaluated at 32 fixed sample entries over all
+// frequencies: rows (2s+1) M / 64, columns (2 (11 s mod 32) + 1) N / 64.
+// Returns true when ||R_samples||_F <= eps3 ||A_samples||_F; otherwise w.rk[k]
+// holds the sampled residual energy per frequency.
+
+template <class T>
+__device__ __forceinline__ const Cx<T>* f_of(const AcaArgs<T>& A, const BlockSh<T>& S, int p) {
+    const long long span = S.r[p] < 0 ? (long long)S.M * S.N : (long long)S.r[p] * (S.M + S.N);
+    return A.pool + S.off[p] + span;
+}
+
 template <int KER, class T, int NT>
+__device__ __noinline__ bool confirm_stop(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int ncl) {
+    const int tid = threadIdx.x, Ku = A.Ku;
+    const int M = S.M, N = S.N;
+    for (int e = tid; e < SAMPLES * ncl; e += NT) {
+        const int sm = e / ncl, p = e % ncl;
+        const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
+        Cx<double> h{0, 0};
+        if (S.r[p] < 0) {
+            h = ccast<double>(A.pool[S.off[p] + i + (long long)j * M]);
+        } else {
+            const Cx<T>* U = A.pool + S.off[p];
+            const Cx<T>* V = U + (long long)S.r[p] * M;
+            for (int t = 0; t < S.r[p]; ++t)
+                cfmac(h, ccast<double>(U[(long long)t * M + i]), ccast<double>(V[(long long)t * N + j]));
+        }
+        w.hs[sm * A.Cmax + p] = h;
+    }
+    if (tid == 0) {
+        S.red2[0] = 0.0;
+        S.red2[1] = 0.0;
+        S.entries += (long long)SAMPLES * Ku;
+    }
+    __syncthreads();
+    for (int k = tid; k < Ku; k += NT) {
+        double rr = 0.0, aa = 0.0;
+        for (int sm = 0; sm < SAMPLES; ++sm) {
+            const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
+            const Cx<double> a = ccast<double>(ent<KER, T>(A, S.rb + i, S.cb + j, k));
+            Cx<double> r = a;
+            for (int p = 0; p < ncl; ++p) {
+                const Cx<double> c = cmul(w.hs[sm * A.Cmax + p], ccast<double>(f_of(A, S, p)[k]));
+                r.x -= c.x;
+                r.y -= c.y;
+            }
+            rr += cabs2(r);
+            aa += cabs2(a);
+        }
+        w.rk[k] = rr;
+        atomicAdd(&S.red2[0], rr);
+        atomicAdd(&S.red2[1], aa);
+    }
+    __syncthreads();
+    const bool ok = S.red2[0] <= A.eps3 * A.eps3 * S.red2[1];
+    __syncthreads();
+    return ok;
+}
+
+// ---- dense-face blocks ---------------------------------------------------------------
+// Algorithm 1 with the exact residual face (no low-rank approximation in the
+// face, the paper's "No Lwr" variant) for blocks with M N <= dense_max.  A
+// cross is stored as H (M x N, column-major) followed by f (Ku) and recorded
+// with r = -1.  Per cross: one parallel pass over the M N face entries (the
+// residual of earlier crosses is nc multiply-adds per entry), a block argmax
+// for the pivot, the fiber, and eq. (norm) through dense inner products.
+template <int KER, class T, int NT>
+__device__ void dense_block(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, bool& zero_block, int& computed,
+                            bool& overflow, long long* ph, long long& tclk) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int M = S.M, N = S.N, MN = M * N, Ku = A.Ku, blk = S.blk;
+    auto lap = [&](int i) {
+        if (tid == 0) {
+            long long tn = clock64();
+            ph[i] += tn - tclk;
+            tclk = tn;
+        }
+    };
+    for (;;) {
+        const int nc = S.ncross;
+        if (tid == 0) {
+            const long long need = (long long)MN + Ku;
+            unsigned long long o = atomicAdd(A.pool_ctr, (unsigned long long)need);
+            if ((long long)o + need > A.pool_cap) {
+                atomicOr(A.status, ST_POOL_OVERFLOW);
+                S.new_off = -1;
+            } else {
+                S.new_off = (long long)o;
+            }
+        }
+        __syncthreads();
+        if (S.new_off < 0) {
+            overflow = true;
+            return;
+        }
+        const long long off = S.new_off;
+        Cx<T>* Hn = A.pool + off;
+        Cx<T>* Fn = Hn + MN;
+        // ---- face: exact residual at S.k, else up to three more frequencies ----
+        int cand[4] = {S.k, Ku - 1, Ku / 2, A.k_maxabs};
+        ArgMaxT<T> am = amax_none<T>();
+        int kf = -1;
+        for (int c = 0; c < 4; ++c) {
+            const int kk = cand[c];
+            bool skip = false;
+            for (int d = 1; d < c; ++d) skip |= (cand[d] == kk);
+            if (c > 0) skip |= ((S.used_k[kk >> 5] >> (kk & 31)) & 1u) != 0;
+            if (skip) continue;
+            for (int p = tid; p < nc; p += NT) S.fk[p] = (A.pool + S.off[p] + MN)[kk];
+            __syncthreads();
+            ArgMaxT<T> a = amax_none<T>();
+            for (int e = tid; e < MN; e += NT) {
+                const int i = e % M, j = e / M;
+                Cx<T> v = ent<KER, T>(A, S.rb + i, S.cb + j, kk);
+                for (int p = 0; p < nc; ++p) {
+                    const Cx<T> h = A.pool[S.off[p] + e];
+                    const Cx<T> x = cmul(S.fk[p], h);
+                    v.x -= x.x;
+                    v.y -= x.y;
+                }
+                Hn[e] = v;
+                a = amax_better(a, ArgMaxT<T>{cabs2(v), i * N + j});
+            }
+            a = block_argmax<NT>(a, S.am);
+            if (tid == 0) {
+                S.entries += MN;
+                S.used_k[kk >> 5] |= 1u << (kk & 31);
+            }
+            __syncthreads();
+            if (a.v > tiny_norm2<T>()) {
+                am = a;
+                kf = kk;
+                break;
+            }
+            if (c == 0 && nc > 0) {
+                // a vanishing residual face after the first cross: nothing left at
+                // this frequency; test the others only to confirm a zero block
+            }
+        }
+        lap(0);
+        if (kf < 0) {
+            zero_block = (nc == 0);
+            return;
+        }
+        if (tid == 0) S.k = kf;
+        ++computed;
+        const int ip = am.i / N, jp = am.i % N;
+        const int ep = ip + jp * M;
+        const Cx<double> hpiv = ccast<double>(Hn[ep]);
+        for (int p = tid; p < nc; p += NT) S.hp[p] = ccast<double>(A.pool[S.off[p] + ep]);
+        __syncthreads();
+        lap(3);
+        // ---- fiber (float64 residual) ----
+        for (int k = tid; k < Ku; k += NT) {
+            Cx<double> e = ccast<double>(ent<KER, T>(A, S.rb + ip, S.cb + jp, k));
+            for (int p = 0; p < nc; ++p) {
+                Cx<double> hf = cmul(S.hp[p], ccast<double>((A.pool + S.off[p] + MN)[k]));
+                e.x -= hf.x;
+                e.y -= hf.y;
+            }
+            Cx<double> fv = cdiv(e, hpiv);
+            w.fib[k] = fv;
+            Fn[k] = ccast<T>(fv);
+        }
+        if (tid == 0) S.entries += Ku;
+        __syncthreads();
+        lap(4);
+        // ---- eq. (norm) with dense faces ----
+        for (int d = wid; d <= nc; d += NT / 32) {
+            Cx<double> ff{0, 0};
+            Cx<T> hh{0, 0};
+            if (d < nc) {
+                const Cx<T>* fd = A.pool + S.off[d] + MN;
+                for (int k = lane; k < Ku; k += 32) cfmac(ff, w.fib[k], ccast<double>(fd[k]));
+                const Cx<T>* Hd = A.pool + S.off[d];
+                for (int e = lane; e < MN; e += 32) cfmac(hh, Hn[e], Hd[e]);
+            } else {
+                for (int k = lane; k < Ku; k += 32) ff.x += cabs2(w.fib[k]);
+                for (int e = lane; e < MN; e += 32) hh.x += cabs2(Hn[e]);
+            }
+            ff.x = warp_sum(ff.x);
+            ff.y = warp_sum(ff.y);
+            const T hx = warp_sum(hh.x), hy = warp_sum(hh.y);
+            if (lane == 0) {
+                if (d < nc) {
+                    S.ff[d] = ff;
+                    S.hh[d] = Cx<double>{(double)hx, (double)hy};
+                } else {
+                    S.fself = ff.x;
+                    S.hself = (double)hx;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double add = 0.0;
+            for (int d = 0; d < nc; ++d) add += 2.0 * (S.hh[d].x * S.ff[d].x - S.hh[d].y * S.ff[d].y);
+            double own = S.hself * S.fself;
+            S.norm2 += add + own;
+            S.stop = sqrt(fmax(own, 0.0)) <= A.eps3 * sqrt(fmax(S.norm2, 0.0));
+            bool all_used = true;
+            for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+            S.flag = all_used;
+            S.off[nc] = off;  // staged for the stop check
+            S.r[nc] = -1;
+        }
+        __syncthreads();
+        bool from_samples = false;
+        if (S.stop && A.sample_check && !S.flag) {
+            from_samples = !confirm_stop<KER, T, NT>(A, w, S, nc + 1);
+        }
+        if (tid == 0) {
+            const bool stop = S.stop && !from_samples;
+            S.flag = 0;
+            if (!stop) {
+                CrossRec cr;
+                cr.off = off;
+                cr.r = -1;
+                cr.ip = ip;
+                cr.jp = jp;
+                cr.kp = S.k;
+                A.rec[(size_t)blk * A.Cmax + nc] = cr;
+                S.off[nc] = off;
+                S.r[nc] = -1;
+                S.ncross = nc + 1;
+                bool all_used = true;
+                for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+                if (S.ncross >= A.Cmax || all_used) S.flag = 1;
+            } else {
+                S.flag = 1;
+            }
+        }
+        __syncthreads();
+        lap(5);
+        if (S.flag) return;
+        ArgMaxT<T> nk = amax_none<T>();
+        for (int k = tid; k < Ku; k += NT)
+            if (!((S.used_k[k >> 5] >> (k & 31)) & 1u))
+                nk = amax_better(nk, ArgMaxT<T>{(T)(from_samples ? w.rk[k] : cabs2(w.fib[k])), k});
+        nk = block_argmax<NT>(nk, S.am);
+        if (nk.v < 0 || nk.i < 0 || nk.i >= Ku) return;
+        if (tid == 0) S.k = nk.i;
+        __syncthreads();
+        lap(6);
+    }
+}
+
+// ---- the persistent kernel ---------------------------------------------------------
+// DENSE selects the block class this launch serves (dense faces or low-rank
+// faces); the two classes run as two persistent launches with their own queues.
+template <int KER, class T, int NT, bool DENSE>
 __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockSh<T> S;
@@ -971,6 +1284,10 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
         if (M > A.Mmax || N > A.Nmax) {  // cannot happen: workspace is sized from the block list
             if (tid == 0) atomicOr(A.status, ST_BAD_INDEX);
             overflow = true;
+        }
+        if (DENSE) {
+            if (!overflow) dense_block<KER, T, NT>(A, w, S, zero_block, computed, overflow, ph, tclk);
+            overflow = true;  // the low-rank loop below is not for this launch
         }
         while (!overflow) {
             // ---------------- face at S.k ----------------
@@ -1199,7 +1516,20 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
                 for (int d = 0; d < nc; ++d) add += 2.0 * (S.hh[d].x * S.ff[d].x - S.hh[d].y * S.ff[d].y);
                 double own = S.hself * S.fself;
                 S.norm2 += add + own;
-                bool stop = sqrt(fmax(own, 0.0)) <= A.eps3 * sqrt(fmax(S.norm2, 0.0));
+                S.stop = sqrt(fmax(own, 0.0)) <= A.eps3 * sqrt(fmax(S.norm2, 0.0));
+                bool all_used = true;
+                for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+                S.flag = all_used;
+                S.off[nc] = off;  // staged for the stop check
+                S.r[nc] = rn;
+            }
+            __syncthreads();
+            bool from_samples = false;
+            if (S.stop && A.sample_check && !S.flag) {
+                from_samples = !confirm_stop<KER, T, NT>(A, w, S, nc + 1);
+            }
+            if (tid == 0) {
+                const bool stop = S.stop && !from_samples;
                 S.flag = 0;
                 if (!stop) {
                     CrossRec cr;
@@ -1226,7 +1556,8 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             // next frequency: argmax over unused k of |f_l[k]|
             ArgMaxT<T> nk = amax_none<T>();
             for (int k = tid; k < Ku; k += NT)
-                if (!((S.used_k[k >> 5] >> (k & 31)) & 1u)) nk = amax_better(nk, ArgMaxT<T>{(T)cabs2(w.fib[k]), k});
+                if (!((S.used_k[k >> 5] >> (k & 31)) & 1u))
+                    nk = amax_better(nk, ArgMaxT<T>{(T)(from_samples ? w.rk[k] : cabs2(w.fib[k])), k});
             nk = block_argmax<NT>(nk, S.am);
             if (nk.v < 0 || nk.i < 0 || nk.i >= Ku) break;  // no finite candidate left
             if (tid == 0) S.k = nk.i;
@@ -1249,23 +1580,38 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
 // host driver
 // ============================================================================
 
-template <int KER, class T, int NT>
+template <int KER, class T, int NT, bool DENSE>
 static g3_status launch_aca_t(g3_ctx* ctx, AcaArgs<T>& A, int grid, size_t smem) {
-    auto kfn = k_aca3<KER, T, NT>;
+    auto kfn = k_aca3<KER, T, NT, DENSE>;
     G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kfn<<<grid, NT, smem, ctx->stream>>>(A);
-    ctx->count(KER == G3_SEPARABLE ? "k_aca3_separable" : "k_aca3");
+    ctx->count(KER == G3_SEPARABLE ? (DENSE ? "k_aca3_dense_separable" : "k_aca3_separable")
+                                   : (DENSE ? "k_aca3_dense" : "k_aca3"));
     G3_CUDA(cudaGetLastError());
     return G3_OK;
 }
 
-template <int KER, class T, int NT>
+template <int KER, class T, int NT, bool DENSE>
 static int occupancy(size_t smem) {
     int nb = 0;
-    auto kfn = k_aca3<KER, T, NT>;
+    auto kfn = k_aca3<KER, T, NT, DENSE>;
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, NT, smem) != cudaSuccess) nb = 1;
     return std::max(nb, 1);
+}
+
+template <class T, int NT, bool DENSE>
+static g3_status launch_kind(g3_ctx* ctx, int kernel, AcaArgs<T>& A, int grid, size_t smem) {
+    if (kernel == G3_SLP) return launch_aca_t<G3_SLP, T, NT, DENSE>(ctx, A, grid, smem);
+    if (kernel == G3_DLP) return launch_aca_t<G3_DLP, T, NT, DENSE>(ctx, A, grid, smem);
+    return launch_aca_t<G3_SEPARABLE, T, NT, DENSE>(ctx, A, grid, smem);
+}
+
+template <class T, int NT, bool DENSE>
+static int occupancy_kind(int kernel, size_t smem) {
+    if (kernel == G3_SLP) return occupancy<G3_SLP, T, NT, DENSE>(smem);
+    if (kernel == G3_DLP) return occupancy<G3_DLP, T, NT, DENSE>(smem);
+    return occupancy<G3_SEPARABLE, T, NT, DENSE>(smem);
 }
 
 template <class T>
@@ -1314,14 +1660,31 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         }
         std::stable_sort(queue.begin(), queue.begin() + n_run, [&](int a, int b) { return cost[a] > cost[b]; });
     }
+    // two block classes, each in cost order: low-rank faces, then dense faces
+    const int dense_max = o.dense_face_max > 0 ? o.dense_face_max : (o.dense_face_max < 0 ? -1 : 48 * 48);
+    std::vector<int> qcat;
+    qcat.reserve(n_run);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int q = 0; q < n_run; ++q) {
+            const BlockRange& r = ranges[queue[q]];
+            const bool dn = (long long)(r.re - r.rb) * (r.ce - r.cb) <= dense_max;
+            if (dn == (pass == 1)) qcat.push_back(queue[q]);
+        }
+    int n_low = 0;
+    for (int q = 0; q < n_run; ++q) {
+        const BlockRange& r = ranges[queue[q]];
+        n_low += !((long long)(r.re - r.rb) * (r.ce - r.cb) <= dense_max);
+    }
+    const int n_dense = n_run - n_low;
     DevBuf d_ranges, d_queue, d_head, d_k1, d_counters, d_ctr;
     G3_CUDA(d_ranges.alloc(n_far * sizeof(BlockRange)));
-    G3_CUDA(d_queue.alloc(n_far * sizeof(int)));
-    G3_CUDA(d_head.alloc(sizeof(int)));
+    G3_CUDA(d_queue.alloc(std::max(n_run, 1) * sizeof(int)));
+    G3_CUDA(d_head.alloc(2 * sizeof(int)));
     G3_CUDA(d_counters.alloc(16 * sizeof(unsigned long long)));
     G3_CUDA(d_ctr.alloc(sizeof(unsigned long long)));
     G3_CUDA(cudaMemcpyAsync(d_ranges.p, ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice, ctx->stream));
-    G3_CUDA(cudaMemcpyAsync(d_queue.p, queue.data(), n_far * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    if (n_run > 0)
+        G3_CUDA(cudaMemcpyAsync(d_queue.p, qcat.data(), n_run * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     if (o.k1) {
         for (int i = 0; i < n_far; ++i)
             if (o.k1[i] < 0 || o.k1[i] >= Ku) return fail(G3_EINVAL, "opts->k1[%d] = %d outside [0, %d)", i, o.k1[i], Ku);
@@ -1358,13 +1721,11 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
     const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
-    int per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 0;
-    if (per_sm == 0) {
-        if (kernel == G3_SLP) per_sm = occupancy<G3_SLP, T, NT>(smem);
-        else if (kernel == G3_DLP) per_sm = occupancy<G3_DLP, T, NT>(smem);
-        else per_sm = occupancy<G3_SEPARABLE, T, NT>(smem);
-    }
-    int grid = o.unbatched ? 1 : std::min(n_run, ctx->n_sm * per_sm);
+    const int per_low = o.ctas_per_sm > 0 ? o.ctas_per_sm : occupancy_kind<T, NT, false>(kernel, smem);
+    const int per_dense = o.ctas_per_sm > 0 ? o.ctas_per_sm : occupancy_kind<T, NT, true>(kernel, smem);
+    const int grid_low = o.unbatched ? 1 : std::max(1, std::min(n_low, ctx->n_sm * per_low));
+    const int grid_dense = o.unbatched ? 1 : std::max(1, std::min(n_dense, ctx->n_sm * per_dense));
+    const int grid = std::max(grid_low, grid_dense);
     const size_t stride = al256(ws_bytes<T>(RF, Mmax, Nmax, Ku, Ku));
     DevBuf d_ws;
     G3_CUDA(d_ws.alloc(stride * grid));
@@ -1373,7 +1734,17 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
     G3_CUDA(fa->d_cycles.alloc((size_t)n_far * sizeof(long long)));
     // factor pool: initial estimate, regrown on overflow
     double pf = o.pool_factor > 0 ? o.pool_factor : 1.0;
-    long long cap = (long long)(pf * (double)(sumMN * 16 * 12 + (long long)n_far * Ku * 16));
+    // pool estimate per block class (elements): low-rank blocks ~256 (M + N),
+    // dense blocks ~12 M N, fibers 24 Ku per block; scaled by what earlier
+    // compressions on this context needed relative to the same estimate
+    double est = 0.0;
+    for (int q = 0; q < n_run; ++q) {
+        const BlockRange& r = ranges[queue[q]];
+        const double m = r.re - r.rb, n = r.ce - r.cb;
+        est += (m * n <= (double)dense_max) ? 12.0 * m * n : 256.0 * (m + n);
+        est += 24.0 * Ku;
+    }
+    long long cap = (long long)(pf * ctx->pool_scale * est);
     cap = std::max(cap, (long long)1 << 16);
     int regrows = 0;
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
@@ -1381,7 +1752,7 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
     for (;;) {
         G3_CUDA(fa->pool.alloc((size_t)cap * sizeof(Cx<T>)));
         fa->pool_cap = cap;
-        G3_CUDA(cudaMemsetAsync(d_head.p, 0, sizeof(int), ctx->stream));
+        G3_CUDA(cudaMemsetAsync(d_head.p, 0, 2 * sizeof(int), ctx->stream));
         G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 16 * sizeof(unsigned long long), ctx->stream));
         G3_CUDA(cudaMemsetAsync(d_ctr.p, 0, sizeof(unsigned long long), ctx->stream));
         G3_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
@@ -1403,6 +1774,8 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.k1 = o.k1 ? d_k1.as<int>() : nullptr;
         A.Cmax = Ku;
         A.RF = RF;
+        A.dense_max = o.dense_face_max > 0 ? o.dense_face_max : (o.dense_face_max < 0 ? -1 : 48 * 48);
+        A.sample_check = o.literal_stop ? 0 : 1;
         A.eps3 = eps3;
         A.eps_face = eps_face;
         A.no_recompress = o.no_recompress;
@@ -1420,12 +1793,21 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.Nmax = Nmax;
         G3_CUDA(cudaEventRecord(e0, ctx->stream));
         g3_status st = G3_OK;
-        const int launches = o.unbatched ? n_run : 1;
-        for (int l = 0; l < launches && st == G3_OK; ++l) {
-            if (o.unbatched) A.single = l;
-            if (kernel == G3_SLP) st = launch_aca_t<G3_SLP, T, NT>(ctx, A, grid, smem);
-            else if (kernel == G3_DLP) st = launch_aca_t<G3_DLP, T, NT>(ctx, A, grid, smem);
-            else st = launch_aca_t<G3_SEPARABLE, T, NT>(ctx, A, grid, smem);
+        for (int cls = 0; cls < 2 && st == G3_OK; ++cls) {
+            if (cls == 1) G3_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
+            const int cnt = cls == 0 ? n_low : n_dense;
+            if (cnt == 0) continue;
+            AcaArgs<T> B = A;
+            B.queue = d_queue.as<int>() + (cls == 0 ? 0 : n_low);
+            B.queue_head = d_head.as<int>() + cls;
+            B.n_far = cnt;
+            const int launches = o.unbatched ? cnt : 1;
+            const int g = cls == 0 ? grid_low : grid_dense;
+            for (int l = 0; l < launches && st == G3_OK; ++l) {
+                if (o.unbatched) B.single = l;
+                st = cls == 0 ? launch_kind<T, NT, false>(ctx, kernel, B, g, smem)
+                              : launch_kind<T, NT, true>(ctx, kernel, B, g, smem);
+            }
         }
         if (st != G3_OK) return st;
         G3_CUDA(cudaEventRecord(e1, ctx->stream));
@@ -1434,14 +1816,16 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         G3_CUDA(cudaMemcpyAsync(&status, ctx->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
         G3_CUDA(cudaMemcpyAsync(&ctr, d_ctr.p, sizeof(ctr), cudaMemcpyDeviceToHost, ctx->stream));
         G3_CUDA(cudaStreamSynchronize(ctx->stream));
-        float ms = 0;
+        float ms = 0, ms_low = 0;
         G3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        G3_CUDA(cudaEventElapsedTime(&ms_low, e0, ctx->ev[2]));
         ms_total += ms;
         if (status & ST_POOL_OVERFLOW) {
             if (++regrows > 6) return fail(G3_EOVERFLOW, "aca3_compress: factor pool overflow after %d regrows", regrows);
             cap = std::max(cap * 2, (long long)(ctr * 5 / 4));
             continue;
         }
+        if (est > 0) ctx->pool_scale = std::max(ctx->pool_scale, 1.15 * (double)ctr / est);
         unsigned long long cnt[16];
         G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
         fa->r3.resize(n_far);
@@ -1462,6 +1846,8 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         S.recompress_fallbacks = (int32_t)cnt[4];
         S.status_bits = (int32_t)status;
         S.ms = ms_total;
+        S.ms_lowrank = ms_low;
+        S.ms_dense = ms - ms_low;
         for (int i = 0; i < 7; ++i) S.phase_cycles[i] = (int64_t)cnt[8 + i];
         S.ctas = grid;
         for (int b = 0; b < n_far; ++b) {
@@ -1471,9 +1857,14 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
             S.dense_bytes += (int64_t)M * N * Ku * (int64_t)sizeof(Cx<T>);
             for (int p = 0; p < fa->r3[b]; ++p) {
                 const CrossRec& c = fa->rec[(size_t)b * Ku + p];
-                S.face_rank_sum += c.r;
-                S.face_rank_max = std::max(S.face_rank_max, c.r);
-                S.factor_bytes += ((int64_t)c.r * (M + N) + Ku) * (int64_t)sizeof(Cx<T>);
+                if (c.r < 0) {  // dense face
+                    S.dense_crosses += 1;
+                    S.factor_bytes += ((int64_t)M * N + Ku) * (int64_t)sizeof(Cx<T>);
+                } else {
+                    S.face_rank_sum += c.r;
+                    S.face_rank_max = std::max(S.face_rank_max, c.r);
+                    S.factor_bytes += ((int64_t)c.r * (M + N) + Ku) * (int64_t)sizeof(Cx<T>);
+                }
             }
         }
         return G3_OK;

@@ -628,14 +628,17 @@ g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t
     size_t ou = 0, ov = 0;
     for (int p = 0; p < nc; ++p) {
         const CrossRec& c = fa->rec[(size_t)i * fa->Cmax + p];
-        if (face_ranks) face_ranks[p] = c.r;
+        const bool dense = c.r < 0;
+        const int rr = dense ? N : c.r;
+        if (face_ranks) face_ranks[p] = rr;
         if (piv) {
             piv[3 * p] = c.ip;
             piv[3 * p + 1] = c.jp;
             piv[3 * p + 2] = c.kp;
         }
-        const size_t nu = (size_t)c.r * M, nv = (size_t)c.r * N;
-        const size_t tot = nu + nv + Ku;
+        const size_t nu = (size_t)rr * M, nv = (size_t)rr * N;
+        // stored: low-rank U, V, f  |  dense H (M x N column-major), f
+        const size_t tot = dense ? (size_t)M * N + Ku : nu + nv + Ku;
         std::vector<double> tmp(2 * tot);
         if (fa->prec == G3_MIXED) {
             std::vector<float> tf(2 * tot);
@@ -644,9 +647,18 @@ g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t
         } else {
             G3_CUDA(cudaMemcpy(tmp.data(), fa->pool.as<double>() + 2 * c.off, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
         }
-        if (U) std::memcpy(U + 2 * ou, tmp.data(), 2 * nu * sizeof(double));
-        if (V) std::memcpy(V + 2 * ov, tmp.data() + 2 * nu, 2 * nv * sizeof(double));
-        if (fib) std::memcpy(fib + 2 * (size_t)p * Ku, tmp.data() + 2 * (nu + nv), 2 * (size_t)Ku * sizeof(double));
+        if (dense) {
+            if (U) std::memcpy(U + 2 * ou, tmp.data(), 2 * nu * sizeof(double));
+            if (V) {
+                std::memset(V + 2 * ov, 0, 2 * nv * sizeof(double));
+                for (int j = 0; j < N; ++j) V[2 * (ov + (size_t)j * N + j)] = 1.0;
+            }
+            if (fib) std::memcpy(fib + 2 * (size_t)p * Ku, tmp.data() + 2 * (size_t)M * N, 2 * (size_t)Ku * sizeof(double));
+        } else {
+            if (U) std::memcpy(U + 2 * ou, tmp.data(), 2 * nu * sizeof(double));
+            if (V) std::memcpy(V + 2 * ov, tmp.data() + 2 * nu, 2 * nv * sizeof(double));
+            if (fib) std::memcpy(fib + 2 * (size_t)p * Ku, tmp.data() + 2 * (nu + nv), 2 * (size_t)Ku * sizeof(double));
+        }
         ou += nu;
         ov += nv;
     }

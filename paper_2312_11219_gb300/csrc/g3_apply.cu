@@ -104,17 +104,21 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
     }
 }
 
-// Far field: one CTA per admissible block with r3 > 0.
+// Far field: one CTA per admissible block.  A low-rank cross (U, V, f) adds
+// U (V^H x) + conj(U (V^H zc)); a dense cross (H, f; r = -1) adds
+// H x + conj(H zc), with x = sum_k f[k] w_k and zc = sum_k f[k] conj(w_k').
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
                                                   const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
                                                   const int* __restrict__ list, int Cmax, int Ku, int E,
                                                   const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
-                                                  Cx<T>* __restrict__ y, int ysmem_max) {
+                                                  Cx<T>* __restrict__ y, int ysmem_max, int dense_n_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T>* fsh = reinterpret_cast<Cx<T>*>(smem_raw);  // [Ku]
     Cx<T>* ab = fsh + Ku;                             // [2 * 64]: a[t], b[t]
-    T* ysh = reinterpret_cast<T*>(ab + 128);          // [2 * M] when M <= ysmem_max
+    Cx<T>* xs = ab + 128;                             // [dense_n_max] x (dense crosses)
+    Cx<T>* zs = xs + dense_n_max;                     // [dense_n_max] zc
+    T* ysh = reinterpret_cast<T*>(zs + dense_n_max);  // [2 * M] when M <= ysmem_max
     const int blk = list[blockIdx.x];
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
@@ -125,6 +129,42 @@ __global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool
         for (int i = threadIdx.x; i < 2 * M; i += NT) ysh[i] = 0;
     for (int p = 0; p < nc; ++p) {
         const CrossRec c = rec[(size_t)blk * Cmax + p];
+        if (c.r < 0) {
+            const Cx<T>* H = pool + c.off;
+            const Cx<T>* F = H + (long long)M * N;
+            for (int k = threadIdx.x; k < Ku; k += NT) fsh[k] = F[k];
+            __syncthreads();
+            for (int j = threadIdx.x; j < N; j += NT) {
+                const int gj = br.cb + j;
+                Cx<T> x{0, 0}, zc{0, 0};
+                for (int k = 0; k < Ku; ++k) {
+                    Cx<T> f = fsh[k];
+                    cfma(x, f, Wf[(long long)k * E + gj]);
+                    cfmac(zc, f, Wc[(long long)k * E + gj]);
+                }
+                xs[j] = x;
+                zs[j] = zc;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < M; i += NT) {
+                Cx<T> s1{0, 0}, s2{0, 0};
+                for (int j = 0; j < N; ++j) {
+                    Cx<T> h = H[i + (long long)j * M];
+                    cfma(s1, h, xs[j]);
+                    cfma(s2, h, zs[j]);
+                }
+                T vx = s1.x + s2.x, vy = s1.y - s2.y;  // H x + conj(H zc)
+                if (ysm) {
+                    ysh[2 * i] += vx;
+                    ysh[2 * i + 1] += vy;
+                } else {
+                    atomicAdd(&y[br.rb + i].x, vx);
+                    atomicAdd(&y[br.rb + i].y, vy);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         const Cx<T>* U = pool + c.off;
         const Cx<T>* V = U + (long long)c.r * M;
         const Cx<T>* F = U + (long long)c.r * (M + N);
@@ -191,6 +231,18 @@ __global__ void k_apply_finish(int E, const int* __restrict__ perm, const Cx<T>*
     Y[perm[p]] = Cx<TO>{(TO)v.x, (TO)v.y};
 }
 
+// largest N_b over blocks holding a dense cross (shared-memory size of k_apply_far)
+static int dense_n_max(const g3_factors* fa) {
+    int n = 0;
+    for (int b = 0; b < fa->n_far; ++b)
+        for (int p = 0; p < fa->r3[b]; ++p)
+            if (fa->rec[(size_t)b * fa->Cmax + p].r < 0) {
+                n = std::max(n, fa->ranges[b].ce - fa->ranges[b].cb);
+                break;
+            }
+    return n;
+}
+
 template <class T>
 static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
                              void* Y, int dtype, const g3_freqs* f) {
@@ -252,10 +304,12 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
             int mmax = 0;
             for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
             const int ym = std::min(mmax, ysmem_max);
-            size_t smem = (Ku + 128) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+            const int dn = dense_n_max(fa);
+            size_t smem = (Ku + 128 + 2 * (size_t)dn) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+            G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_apply_far<T, NT><<<(int)list.size(), NT, smem, ctx->stream>>>(
                 fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges.as<BlockRange>(),
-                d_list.as<int>(), fa->Cmax, Ku, E, Wf, Wc, y, ym);
+                d_list.as<int>(), fa->Cmax, Ku, E, Wf, Wc, y, ym, dn);
             ctx->count("k_apply_far");
             G3_CUDA(cudaGetLastError());
             G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
@@ -394,10 +448,12 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         int mmax = 0;
         for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
         const int ym = std::min(mmax, ysmem_max);
-        size_t smem = (Ku + 128) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+        const int dn = dense_n_max(fa);
+        size_t smem = (Ku + 128 + 2 * (size_t)dn) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+        G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_apply_far<T, NT><<<n_far, NT, smem, ctx->stream>>>(fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
                                                               fa->d_r3.as<int>(), ranges, list, fa->Cmax, Ku, E, Wf,
-                                                              Wc, y, ym);
+                                                              Wc, y, ym, dn);
         ctx->count("k_apply_far");
         G3_CUDA(cudaGetLastError());
     }

@@ -122,6 +122,7 @@ struct g3_ctx {
     g3::DevBuf stage_w, stage_y;  // device staging of host W / Y in apply_gcq
     cudaEvent_t ev[6] = {};
     double last_apply_ms = 0, last_near_ms = 0;
+    double pool_scale = 1.0;  // factor-pool size / estimate needed by earlier compressions
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
     void count(const char* name, int64_t n = 1) {
         launches[name] += n;

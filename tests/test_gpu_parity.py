@@ -177,11 +177,12 @@ def _rand(rng, *shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
 
+@pytest.mark.parametrize("dense", [0, -1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_separable_rank1_exact(g3, ctx, prec):
+def test_separable_rank1_exact(g3, ctx, prec, dense):
     rng = np.random.default_rng(2)
     a, b, c = _rand(rng, 1, 40), _rand(rng, 1, 33), _rand(rng, 1, 17)
-    fa = g3.aca3_compress_separable(ctx, a, b, c, prec=prec, eps3=1e-4)
+    fa = g3.aca3_compress_separable(ctx, a, b, c, prec=prec, eps3=1e-4, dense_face_max=dense)
     st = fa.stats()
     assert fa.ranks()[0] == 1
     blk = fa.block(0, 40, 33, 17)
@@ -192,12 +193,13 @@ def test_separable_rank1_exact(g3, ctx, prec):
     assert st["status_bits"] & 1 == 0
 
 
+@pytest.mark.parametrize("dense", [0, -1])
 @pytest.mark.parametrize("R", [2, 4])
-def test_separable_rank_r_recovered(g3, ctx, R):
+def test_separable_rank_r_recovered(g3, ctx, R, dense):
     rng = np.random.default_rng(10 + R)
     c = _rand(rng, R, 12) * (0.3 ** np.arange(R))[:, None]
     a, b = _rand(rng, R, 22), _rand(rng, R, 19)
-    fa = g3.aca3_compress_separable(ctx, a, b, c, prec="fp64", eps3=1e-10)
+    fa = g3.aca3_compress_separable(ctx, a, b, c, prec="fp64", eps3=1e-10, dense_face_max=dense)
     r3 = fa.ranks()[0]
     assert r3 <= R
     blk = fa.block(0, 22, 19, 12)
@@ -205,7 +207,7 @@ def test_separable_rank_r_recovered(g3, ctx, R):
     A = sum((U @ V.conj().T)[:, :, None] * f[None, None, :] for U, V, f in zip(blk["U"], blk["V"], blk["f"]))
     assert np.linalg.norm(A - D) <= 1e-9 * np.linalg.norm(D)
     # same ranks as the oracle on the same tensor
-    ref = O_aca.aca3(O_aca.SeparableBlock(a, b, c), 1e-10)
+    ref = O_aca.aca3(O_aca.SeparableBlock(a, b, c), 1e-10, dense_max=O_aca.DENSE_MAX if dense == 0 else -1)
     assert ref.rank == r3
 
 
@@ -218,16 +220,18 @@ def _oracle_blocks(w, kernel, eps3):
     return geo, T, fs, su, ef
 
 
+@pytest.mark.parametrize("dense", [0, -1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_compression_cube768_blockwise(g3, ctx, prec):
+def test_compression_cube768_blockwise(g3, ctx, prec, dense):
     w = workloads.get("cube768")
     eps3 = 1e-4
     geo, OT, fs, su, ef = _oracle_blocks(w, "slp", eps3)
     T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
     F = g3.freqs_from_spec(ctx, w.freq)
-    fa = g3.aca3_compress(ctx, T, F, "slp", prec=prec, eps3=eps3)
+    fa = g3.aca3_compress(ctx, T, F, "slp", prec=prec, eps3=eps3, dense_face_max=dense)
     st = fa.stats()
     assert st["status_bits"] & 1 == 0
+    assert (st["dense_crosses"] == st["crosses"]) if dense == 0 else (st["dense_crosses"] == 0)
     r3 = fa.ranks()
     far = [b for b in range(OT.blocks.shape[0]) if OT.blocks[b, 4] == 1]
     assert r3.size == len(far)
@@ -245,7 +249,8 @@ def test_compression_cube768_blockwise(g3, ctx, prec):
             A += (U @ V.conj().T)[:, :, None] * f[None, None, :]
         err = np.linalg.norm(A - D) / np.linalg.norm(D)
         assert err <= 10 * eps3, (i, err)
-        ref = O_aca.aca3(O_aca.BemBlock(ef, OT.perm[rb:re], OT.perm[cb:ce], su), eps3, s_abs=np.abs(su))
+        ref = O_aca.aca3(O_aca.BemBlock(ef, OT.perm[rb:re], OT.perm[cb:ce], su), eps3, s_abs=np.abs(su),
+                         dense_max=O_aca.DENSE_MAX if dense == 0 else -1)
         oranks.append((ref.rank, r3[i]))
         assert abs(ref.rank - r3[i]) <= 2
         # the first frequency is always the first one used
@@ -254,7 +259,8 @@ def test_compression_cube768_blockwise(g3, ctx, prec):
     assert abs(o.mean() - g.mean()) <= 0.1 * o.mean() + 0.5
 
 
-def test_apply_cube768_against_oracle(g3, ctx):
+@pytest.mark.parametrize("dense", [0, -1])
+def test_apply_cube768_against_oracle(g3, ctx, dense):
     import torch
     w = workloads.get("cube768")
     eps3 = 1e-4
@@ -265,7 +271,7 @@ def test_apply_cube768_against_oracle(g3, ctx):
     F = g3.freqs_from_spec(ctx, w.freq)
     for prec in ("fp64", "mixed"):
         nf = g3.assemble_near(ctx, T, F, "slp", prec=prec)
-        fa = g3.aca3_compress(ctx, T, F, "slp", prec=prec, eps3=eps3)
+        fa = g3.aca3_compress(ctx, T, F, "slp", prec=prec, eps3=eps3, dense_face_max=dense)
         Wd = torch.from_numpy(W).to("cuda")
         y = g3.apply_gcq(ctx, T, nf, fa, Wd).cpu().numpy()
         err = np.linalg.norm(y - yd) / np.linalg.norm(yd)

@@ -83,6 +83,7 @@ def test_aca3_rank_r_separable_recovered(R):
 
 
 def _bem_block(name="cube768", kernel="slp", pick="largest"):
+    """The largest admissible block of a workload (or block `pick`)."""
     w = workloads.get(name)
     g = Q.Geometry(w.verts, w.tris)
     T = tree.build(w.verts, w.tris, w.leaf, w.eta)
@@ -98,10 +99,11 @@ def _bem_block(name="cube768", kernel="slp", pick="largest"):
     return op, D, s_u
 
 
-def test_aca3_bem_block_tolerance_norm_recursion_and_fiber_interpolation():
+@pytest.mark.parametrize("dense_max", [aca3.DENSE_MAX, -1])
+def test_aca3_bem_block_tolerance_norm_recursion_and_fiber_interpolation(dense_max):
     op, D, s_u = _bem_block()
     eps3 = 1e-4
-    res = aca3.aca3(op, eps3, s_abs=np.abs(s_u))
+    res = aca3.aca3(op, eps3, s_abs=np.abs(s_u), dense_max=dense_max)
     M, N, Ku = D.shape
     C = res.dense(M, N, Ku)
     assert res.rank >= 2
@@ -147,7 +149,8 @@ def test_aca3_dlp_zero_block_has_rank0():
     assert zero == 3 and nonzero == 2
 
 
-def test_compressed_apply_matches_dense_apply():
+@pytest.mark.parametrize("dense_max", [aca3.DENSE_MAX, -1])
+def test_compressed_apply_matches_dense_apply(dense_max):
     w = workloads.get("cube768")
     g = Q.Geometry(w.verts, w.tris)
     T = tree.build(w.verts, w.tris, 32, 1.0)
@@ -159,7 +162,7 @@ def test_compressed_apply_matches_dense_apply():
     for b, (rb, re, cb, ce, adm) in enumerate(T.blocks):
         if adm:
             res[b] = aca3.aca3(aca3.BemBlock(ef, T.perm[rb:re], T.perm[cb:ce], s_u), 1e-4,
-                               s_abs=np.abs(s_u))
+                               s_abs=np.abs(s_u), dense_max=dense_max)
     assert len(res) > 0
     W = workloads.densities(w.E, 8, 3)
     yc = A.compressed_apply(T, res, ef, s_all, uniq, partner, W)
@@ -187,3 +190,65 @@ def test_expand_fibers_uses_conjugate_partners():
         if partner[k] != k:
             assert b[partner[k]] == np.conj(f[u])
     assert np.all(a[[k for k in range(K) if k not in uniq]] == 0)
+
+
+def test_dense_faces_rank_r_exact_and_match_algorithm1():
+    """Small blocks use the exact residual face (Algorithm 1 as written):
+    rank-R separable tensors are recovered in R crosses, and every face of the
+    approximant at a used frequency equals the data there."""
+    rng = np.random.default_rng(21)
+    R = 3
+    c = _rand(rng, R, 10) * (0.2 ** np.arange(R))[:, None]
+    op = aca3.SeparableBlock(_rand(rng, R, 12), _rand(rng, R, 9), c)
+    res = aca3.aca3(op, 1e-12)             # 12 x 9 <= DENSE_MAX: dense faces
+    assert res.rank <= R
+    D = op.dense()
+    C = res.dense(12, 9, 10)
+    assert np.linalg.norm(D - C) < 1e-12 * np.linalg.norm(D)
+    for x in res.crosses:
+        assert np.max(np.abs(C[:, :, x.k] - D[:, :, x.k])) < 1e-12 * np.abs(D).max()
+    # forcing low-rank faces reaches the same tensor
+    res2 = aca3.aca3(aca3.SeparableBlock(op.a, op.b, op.c), 1e-12, dense_max=-1)
+    assert np.linalg.norm(D - res2.dense(12, 9, 10)) < 1e-10 * np.linalg.norm(D)
+
+
+def test_dense_faces_bem_block_tolerance():
+    op, D, s_u = _bem_block("lshape768")
+    assert op.M * op.N <= aca3.DENSE_MAX
+    res = aca3.aca3(op, 1e-4, s_abs=np.abs(s_u))
+    C = res.dense(*D.shape)
+    assert np.linalg.norm(D - C) <= 10 * 1e-4 * np.linalg.norm(D)
+    # each face at a used frequency is reproduced up to the later crosses' contribution there
+    assert res.crosses[0].k == 0 and res.crosses[0].U.shape == (op.M, op.N)
+
+
+def test_confirmed_stop_fixes_two_plane_dlp_block():
+    """A double-layer block of the L-shape whose rows and columns each span
+    the x = 0 and z = 1 faces ([[0, X], [Y, 0]] coplanarity): partial-pivot
+    face ACA never visits Y and the block ends with ~47 % error (reproduced
+    with sample_check=False); with the sampled confirmation of face
+    convergence and of the stop the block meets the tolerance."""
+    w = workloads.get("lshape12288")
+    g = Q.Geometry(w.verts, w.tris)
+    T = tree.build(w.verts, w.tris, w.leaf, w.eta)
+    fs = freqs.frequency_set(w.freq)
+    s_u = fs["s"][fs["uniq"]]
+    far = np.nonzero(T.blocks[:, 4] == 1)[0]
+    rb, re, cb, ce, _ = T.blocks[far[3660]]
+    R, C = T.perm[rb:re], T.perm[cb:ce]
+    assert {tuple(n) for n in g.normal[R]} == {(-1.0, 0.0, 0.0), (0.0, 0.0, 1.0)}
+    ef = lambda I, J, s: Q.entries(g, "dlp", I, J, s)
+    D = Q.dense(g, "dlp", s_u, rows=R, cols=C)
+    lit = aca3.aca3(aca3.BemBlock(ef, R, C, s_u), 1e-4, s_abs=np.abs(s_u), sample_check=False)
+    assert np.linalg.norm(lit.dense(*D.shape) - D) > 0.1 * np.linalg.norm(D)
+    res = aca3.aca3(aca3.BemBlock(ef, R, C, s_u), 1e-4, s_abs=np.abs(s_u))
+    assert np.linalg.norm(res.dense(*D.shape) - D) <= 10 * 1e-4 * np.linalg.norm(D)
+    # the faces now also cover the Y part: larger face ranks
+    assert sum(c.face_rank for c in res.crosses) > sum(c.face_rank for c in lit.crosses)
+
+
+def test_sample_positions_cover_the_block():
+    pos = aca3.sample_entries(96, 96)
+    assert len(set(pos)) == 32
+    assert len({i for i, _ in pos}) == 32 and len({j for _, j in pos}) == 32
+    assert all(0 <= i < 7 and 0 <= j < 5 for i, j in aca3.sample_entries(7, 5))
