@@ -92,6 +92,11 @@ typedef struct g3_freqs g3_freqs;
 typedef struct g3_tree g3_tree;
 typedef struct g3_near g3_near;
 typedef struct g3_factors g3_factors;
+typedef struct g3_mlp g3_mlp;
+
+/* Block predictor: features per admissible block and parameters. */
+#define G3_MLP_NF 12
+#define G3_MLP_NP 5122
 
 /* Options of aca3_compress.  Zero-initialise and set what you need;
  * a NULL pointer means all defaults. */
@@ -117,6 +122,18 @@ typedef struct {
                              = confirm each stop on 32 fixed sample entries over all
                              frequencies (keeps the cross and continues when the sampled
                              relative residual exceeds eps3)                               */
+    const g3_mlp* mlp;    /* optional block predictor (no counterpart in the paper): its
+                             predictions of every block's rank r3 and first frequency set
+                             the factor-pool size, the queue order and k1.  Algorithm 1's
+                             stopping test still decides every rank.  Ignored (with the
+                             plain defaults) when opts->k1 or opts->cost is given for the
+                             respective use.                                               */
+    int mlp_use;          /* bit mask of the predictor's uses: 1 = queue order, 2 = pool
+                             size, 4 = k1 seeding; 0 = all three                          */
+    double face_floor_scale;  /* G3_MIXED: the face ACA tests stop at the absolute level
+                                 scale * eps_face * ||C^(l-1)||_F / sqrt(Ku) (0 = 1)     */
+    double trunc_floor_scale; /* G3_MIXED: the recompression drops singular values below
+                                 scale * eps_face * ||C^(l-1)||_F / sqrt(Ku) (0 = 1)     */
 } g3_opts;
 
 /* Statistics of one compression. */
@@ -143,6 +160,12 @@ typedef struct {
     int64_t dense_crosses;    /* kept crosses with a dense face (face_rank_sum excludes them) */
     double ms_lowrank;        /* device time of the low-rank-face launch (last attempt)   */
     double ms_dense;          /* device time of the dense-face launch (last attempt)      */
+    int32_t spilled_blocks;   /* blocks rerun from the spill queue after the factor pool
+                                 filled up (their work up to the overflow is repeated)     */
+    int32_t mlp_used;         /* the predictor's uses applied (mask as opts->mlp_use)      */
+    double ms_mlp;            /* device time of the block features + predictor forward     */
+    int64_t face_check_restarts;  /* face ACAs continued after a failed sample check       */
+    int64_t stop_check_overrides; /* 3D stops overruled by the sampled residual check      */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */
@@ -268,6 +291,13 @@ g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3);
 /* Per admissible block i: SM clock cycles its compression took (one CTA;
  * diagnostics and cost labels for scheduling). */
 g3_status g3_factors_block_cycles(const g3_factors* fa, int64_t* cycles);
+/* Per admissible block i: out[10 i + q] = SM cycles of phase q (0 face ACA,
+ * 1 recompression, 2 factor formation, 3 pivot search, 4 fiber, 5 eq. (norm),
+ * 6 next frequency), out[10 i + 7] = face ACA steps (face ranks before
+ * recompression, summed over the block's faces), out[10 i + 8] and
+ * out[10 i + 9] = start and end of the block's (last) compression on the GPU's
+ * global timer (ns).  Diagnostics. */
+g3_status g3_factors_block_phases(const g3_factors* fa, int64_t* out);
 /* Export block i's crosses to host.  Sizes first: call with U = V = fib = NULL
  * to get r3 and the face ranks in face_ranks [r3] (if non-NULL; a dense face
  * is exported as U = H (M_b x N_b), V = identity (N_b x N_b), rank N_b).  Then:
@@ -277,6 +307,73 @@ g3_status g3_factors_block_cycles(const g3_factors* fa, int64_t* cycles);
 g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t* face_ranks, double* U, double* V,
                                double* fib, int32_t* piv);
 g3_status g3_factors_free(g3_factors* fa);
+
+/* ---- block predictor (no counterpart in the paper) -------------------------- */
+
+/* Algorithm 1 starts each block at an arbitrary frequency and learns the
+ * block's rank only as it goes.  A small network, trained on earlier
+ * compressions, predicts both before a compression starts, so that the factor
+ * pool is sized, the queue ordered longest first and k1 chosen up front:
+ *
+ *   x (G3_MLP_NF = 12 features) -> 64 ReLU -> 64 ReLU -> 2 outputs
+ *   y0 = log2(1 + r3),  y1 = k* / Ku  (k* = argmax_k |f_1[k]|, the frequency of
+ *                                      the block's largest pivot entry)
+ *
+ * Parameters (G3_MLP_NP = 5,122 float32, row-major, output index first):
+ *   W1 [64][12], b1 [64], W2 [64][64], b2 [64], W3 [2][64], b3 [2].
+ * Inputs are standardised as (x - mean) * inv_std in float32 and rounded to
+ * bfloat16; weights are used rounded to bfloat16 (float32 master copy);
+ * activations, sums, gradients and Adam are float32.
+ *
+ * Features of an admissible block (tau, sigma), from the vertex bounding boxes
+ * (diam = box diagonal, dist = box distance), the area-weighted normal sums
+ * nA = sum a_i n_i and area-weighted centroids c, and the unique frequencies:
+ *   0 log2 M_b      1 log2 N_b     2 log2(diam_tau / dist)  3 log2(diam_sigma / dist)
+ *   4 log2(dist max|s|)            5 log2(dist min Re s)
+ *   6 log2(1 + max(diam) max|Im s| / (2 pi))                 7 log2 Ku
+ *   8 -log10 eps3   9 kernel (0 SLP, 1 DLP)
+ *   10 |nA_tau . nA_sigma| / (A_tau A_sigma)
+ *   11 |(c_sigma - c_tau) . nA_tau| / (|nA_tau| |c_sigma - c_tau|)  (0: coplanar) */
+typedef struct {
+    int epochs;           /* passes over the samples (0 = 200)                           */
+    int batch;            /* minibatch size (0 = 256); batches are consecutive slices    */
+    double lr;            /* Adam step size (0 = 1e-3)                                   */
+    double beta1, beta2;  /* Adam decay rates (0 = 0.9, 0.999)                           */
+    double adam_eps;      /* Adam epsilon (0 = 1e-8)                                     */
+    uint64_t seed;        /* He-uniform initial weights from splitmix64 (g3_mlp_train)   */
+    int no_graph;         /* 1 = launch each step; 0 = replay one CUDA graph per epoch   */
+} g3_train_opts;
+
+/* New model.  params [G3_MLP_NP] (NULL = He-uniform from seed), mean and
+ * inv_std [G3_MLP_NF] (NULL = 0 and 1).  Host arrays, copied. */
+g3_status g3_mlp_create(g3_ctx* ctx, const float* params, const float* mean, const float* inv_std, uint64_t seed,
+                        g3_mlp** out);
+/* New model trained on n samples: feats [n*12], labels [n*2] (host, row-major).
+ * mean / inv_std come from the samples (inv_std = 1 for a constant feature). */
+g3_status g3_mlp_train(g3_ctx* ctx, const float* feats, const float* labels, int n, const g3_train_opts* opts,
+                       g3_mlp** out);
+/* Further Adam epochs on an existing model (its Adam state continues).
+ * losses: optional host [epochs * ceil(n / batch)], the loss of every step. */
+g3_status g3_mlp_fit(g3_ctx* ctx, g3_mlp* m, const float* feats, const float* labels, int n,
+                     const g3_train_opts* opts, float* losses);
+/* Loss 0.5/n sum |y - t|^2 and its gradient [G3_MLP_NP] at the model's
+ * current weights over n samples (host arrays). */
+g3_status g3_mlp_grad(g3_ctx* ctx, const g3_mlp* m, const float* feats, const float* labels, int n, float* grad,
+                      float* loss);
+/* Outputs out [n*2] for feats [n*12] (host arrays). */
+g3_status g3_mlp_predict(g3_ctx* ctx, const g3_mlp* m, const float* feats, int n, float* out);
+/* Copy out the state (any pointer may be NULL): params, Adam moments m and v
+ * [G3_MLP_NP], Adam step count t, mean and inv_std [G3_MLP_NF]. */
+g3_status g3_mlp_get(const g3_mlp* m, float* params, float* adam_m, float* adam_v, int64_t* t, float* mean,
+                     float* inv_std);
+g3_status g3_mlp_free(g3_mlp* m);
+/* Features [n_far*12] of the admissible blocks of t (far order), computed on
+ * the device. */
+g3_status g3_block_features(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, double eps3,
+                            float* out);
+/* Training labels [n_far*2] (y0, y1 above) of a compression, computed on the
+ * device from its ranks and first fibers. */
+g3_status g3_factors_labels(g3_ctx* ctx, const g3_factors* fa, float* out);
 
 /* ---- application (eq. (product)) ------------------------------------------ */
 

@@ -16,6 +16,9 @@ gradients:
 with the same weight layout as the library: W1 [64, 12], b1 [64], W2 [64, 64],
 b2 [64], W3 [2, 64], b3 [2] (5,122 parameters).  Inputs are standardised
 features (the library applies the stored mean / std before the first layer).
+
+Also here: the Adam update (Kingma & Ba 2015, Algorithm 1), the 12 block
+features and the two training labels, each written from its definition.
 """
 from __future__ import annotations
 
@@ -79,3 +82,82 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
     lsb = (u >> 16) & 1
     u = (u + 0x7FFF + lsb) & 0xFFFF0000
     return u.view(np.float32).astype(np.float64)
+
+
+def standardise(X: np.ndarray, mean: np.ndarray, inv_std: np.ndarray) -> np.ndarray:
+    """(x - mean) * inv_std in float32 (two separately rounded operations), then
+    rounded to bfloat16."""
+    X = np.asarray(X, dtype=np.float32)
+    d = (X - np.asarray(mean, dtype=np.float32)).astype(np.float32)
+    return bf16_round((d * np.asarray(inv_std, dtype=np.float32)).astype(np.float32))
+
+
+def adam_step(theta, m, v, t, g, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step from state (theta, m, v) after t earlier steps:
+    m' = b1 m + (1 - b1) g, v' = b2 v + (1 - b2) g^2,
+    theta' = theta - lr (m' / (1 - b1^(t+1))) / (sqrt(v' / (1 - b2^(t+1))) + eps)."""
+    theta, m, v, g = (np.asarray(a, dtype=np.float64) for a in (theta, m, v, g))
+    m2 = b1 * m + (1.0 - b1) * g
+    v2 = b2 * v + (1.0 - b2) * g * g
+    mh = m2 / (1.0 - b1 ** (t + 1))
+    vh = v2 / (1.0 - b2 ** (t + 1))
+    return theta - lr * mh / (np.sqrt(vh) + eps), m2, v2
+
+
+def _cluster(verts: np.ndarray, tris: np.ndarray, idx) -> dict:
+    T = np.asarray(tris)[np.asarray(idx)]
+    V = np.asarray(verts, dtype=np.float64)
+    p0, p1, p2 = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    cr = np.cross(p1 - p0, p2 - p0)
+    ln = np.linalg.norm(cr, axis=1)
+    area = 0.5 * ln
+    normal = cr / ln[:, None]
+    cent = ((p0 + p1) + p2) / 3.0
+    allv = np.concatenate([p0, p1, p2])
+    A = area.sum()
+    return {"lo": allv.min(0), "hi": allv.max(0), "A": A, "nA": (area[:, None] * normal).sum(0),
+            "c": (area[:, None] * cent).sum(0) / A}
+
+
+def block_features(verts, tris, rows, cols, s_unique, kernel: int, eps3: float) -> np.ndarray:
+    """The 12 features of the block (rows, cols) (original element indices):
+    0 log2 M, 1 log2 N, 2 log2(diam_rows / dist), 3 log2(diam_cols / dist),
+    4 log2(dist max|s|), 5 log2(dist min Re s),
+    6 log2(1 + max(diam) max|Im s| / (2 pi)), 7 log2 Ku, 8 -log10 eps3,
+    9 kernel (0 SLP, 1 DLP), 10 |nA_r . nA_c| / (A_r A_c),
+    11 |(c_c - c_r) . nA_r| / (|nA_r| |c_c - c_r|) (1 when undefined).
+    diam = diagonal of the vertex bounding box, dist = distance of the two
+    boxes, nA = sum of area x unit normal, c = area-weighted centroid."""
+    r = _cluster(verts, tris, rows)
+    c = _cluster(verts, tris, cols)
+    s = np.asarray(s_unique, dtype=np.complex128)
+    gap = np.maximum(0.0, np.maximum(c["lo"] - r["hi"], r["lo"] - c["hi"]))
+    dist = np.sqrt(np.sum(gap ** 2))
+    dr = np.sqrt(np.sum((r["hi"] - r["lo"]) ** 2))
+    dc = np.sqrt(np.sum((c["hi"] - c["lo"]) ** 2))
+    dcen = c["c"] - r["c"]
+    nr = np.linalg.norm(r["nA"])
+    ndc = np.linalg.norm(dcen)
+    f = np.empty(12)
+    f[0] = np.log2(len(rows))
+    f[1] = np.log2(len(cols))
+    f[2] = np.log2(dr / dist)
+    f[3] = np.log2(dc / dist)
+    f[4] = np.log2(dist * np.abs(s).max())
+    f[5] = np.log2(dist * s.real.min())
+    f[6] = np.log2(1.0 + max(dr, dc) * np.abs(s.imag).max() / (2.0 * np.pi))
+    f[7] = np.log2(len(s))
+    f[8] = -np.log10(eps3)
+    f[9] = kernel
+    f[10] = abs(np.dot(r["nA"], c["nA"])) / (r["A"] * c["A"])
+    f[11] = abs(np.dot(dcen, r["nA"])) / (nr * ndc) if nr > 0 and ndc > 0 else 1.0
+    return f
+
+
+def labels(r3: int, f1) -> tuple[float, float]:
+    """(log2(1 + r3), k* / Ku) with k* = argmax_k |f1[k]| (smallest k on ties;
+    0 when r3 = 0), f1 the block's first fiber over the Ku unique frequencies."""
+    f1 = np.asarray(f1)
+    Ku = f1.shape[0]
+    k = int(np.argmax(np.abs(f1))) if r3 > 0 else 0
+    return float(np.log2(1.0 + r3)), k / Ku

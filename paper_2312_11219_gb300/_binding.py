@@ -41,7 +41,13 @@ class Opts(C.Structure):
                 ("threads", C.c_int), ("no_recompress", C.c_int), ("order_by_cost", C.c_int),
                 ("k1", _i32p), ("cost", C.POINTER(C.c_float)), ("pool_factor", C.c_double),
                 ("eps_face", C.c_double), ("max_blocks", C.c_int), ("dense_face_max", C.c_int),
-                ("literal_stop", C.c_int)]
+                ("literal_stop", C.c_int), ("mlp", C.c_void_p), ("mlp_use", C.c_int),
+                ("face_floor_scale", C.c_double), ("trunc_floor_scale", C.c_double)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("adam_eps", C.c_double), ("seed", C.c_uint64), ("no_graph", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -51,7 +57,9 @@ class Stats(C.Structure):
                 ("zero_blocks", C.c_int32), ("capped_faces", C.c_int32), ("pool_regrows", C.c_int32),
                 ("status_bits", C.c_int32), ("ms", C.c_double), ("phase_cycles", C.c_int64 * 7),
                 ("ctas", C.c_int32), ("recompress_fallbacks", C.c_int32), ("blocks_run", C.c_int32),
-                ("dense_crosses", C.c_int64), ("ms_lowrank", C.c_double), ("ms_dense", C.c_double)]
+                ("dense_crosses", C.c_int64), ("ms_lowrank", C.c_double), ("ms_dense", C.c_double),
+                ("spilled_blocks", C.c_int32), ("mlp_used", C.c_int32), ("ms_mlp", C.c_double),
+                ("face_check_restarts", C.c_int64), ("stop_check_overrides", C.c_int64)]
 
 
 def _sig(name, res, *args):
@@ -89,18 +97,33 @@ _sig("g3_factors_stats", _ci, _p, C.POINTER(Stats))
 _sig("g3_factors_ranks", _ci, _p, _i32p)
 _sig("g3_factors_get_block", _ci, _p, _ci, _i32p, _i32p, _dp, _dp, _dp, _i32p)
 _sig("g3_factors_block_cycles", _ci, _p, _i64p)
+_sig("g3_factors_block_phases", _ci, _p, _i64p)
 _sig("g3_factors_free", _ci, _p)
 _sig("apply_gcq", _ci, _p, _p, _p, _p, _p, _p, _ci, _ci, _ci)
 _sig("g3_apply_last", _ci, _p, _dp, _i64p, _dp, _i64p)
 _sig("g3_peak", _ci, _p, _ci, _dp, _dp)
 _sig("apply_gcq_noalloc", _ci, _p, _p, _p, _p, _p, _p, _ci)
+_fp = C.POINTER(C.c_float)
+_sig("g3_mlp_create", _ci, _p, _fp, _fp, _fp, C.c_uint64, _pp)
+_sig("g3_mlp_train", _ci, _p, _fp, _fp, _ci, C.POINTER(TrainOpts), _pp)
+_sig("g3_mlp_fit", _ci, _p, _p, _fp, _fp, _ci, C.POINTER(TrainOpts), _fp)
+_sig("g3_mlp_grad", _ci, _p, _p, _fp, _fp, _ci, _fp, _fp)
+_sig("g3_mlp_predict", _ci, _p, _p, _fp, _ci, _fp)
+_sig("g3_mlp_get", _ci, _p, _fp, _fp, _fp, _i64p, _fp, _fp)
+_sig("g3_mlp_free", _ci, _p)
+_sig("g3_block_features", _ci, _p, _p, _p, _ci, C.c_double, _fp)
+_sig("g3_factors_labels", _ci, _p, _p, _fp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
             "build_cluster_tree", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_separable",
-            "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
-            "g3_apply_last", "g3_peak", "apply_gcq_noalloc"]
+            "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
+            "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
+            "g3_mlp_grad", "g3_mlp_predict", "g3_mlp_get", "g3_mlp_free", "g3_block_features", "g3_factors_labels"]
+
+MLP_NF = 12
+MLP_NP = 5122
 
 
 class G3Error(RuntimeError):
@@ -307,6 +330,15 @@ class Factors(_Handle):
         _check(_lib.g3_factors_block_cycles(self.h, _ptr(c, C.c_int64)), "g3_factors_block_cycles")
         return c
 
+    def block_phases(self) -> np.ndarray:
+        """[n_far, 10]: SM cycles per phase (face, recompress, formation, pivot,
+        fiber, norm, next_k), the block's face ACA steps, and its start and end
+        times (GPU global timer, ns)."""
+        n = self.stats()["n_far"]
+        c = np.zeros((max(n, 1), 10), dtype=np.int64)
+        _check(_lib.g3_factors_block_phases(self.h, _ptr(c, C.c_int64)), "g3_factors_block_phases")
+        return c[:n]
+
     def block(self, i: int, M: int, N: int, Ku: int) -> dict:
         r3 = C.c_int32()
         _check(_lib.g3_factors_get_block(self.h, i, C.byref(r3), None, None, None, None, None), "g3_factors_get_block")
@@ -333,6 +365,96 @@ class Factors(_Handle):
         return {"U": us, "V": vs, "f": F[:-2].view(np.complex128).reshape(n, Ku),
                 "piv": P[:-1].reshape(n, 3), "face_ranks": fr}
 
+    def labels(self) -> np.ndarray:
+        """Predictor training labels [n_far, 2]: log2(1 + r3), k* / Ku."""
+        n = self.stats()["n_far"]
+        out = np.zeros((max(n, 1), 2), dtype=np.float32)
+        _check(_lib.g3_factors_labels(self._keep[0].h, self.h, _ptr(out, C.c_float)), "g3_factors_labels")
+        return out[:n]
+
+
+def _train_opts(**kw) -> TrainOpts:
+    o = TrainOpts()
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _f32(a, shape_tail):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if a.ndim != 2 or a.shape[1] != shape_tail:
+        raise ValueError(f"expected an [n, {shape_tail}] array, got {a.shape}")
+    return a
+
+
+class Mlp(_Handle):
+    """Block rank / first-frequency predictor (12 -> 64 -> 64 -> 2)."""
+    _free = _lib.g3_mlp_free
+
+    def predict(self, feats) -> np.ndarray:
+        X = _f32(feats, MLP_NF)
+        out = np.zeros((max(X.shape[0], 1), 2), dtype=np.float32)
+        _check(_lib.g3_mlp_predict(self._keep[0].h, self.h, _ptr(X, C.c_float), X.shape[0], _ptr(out, C.c_float)),
+               "g3_mlp_predict")
+        return out[:X.shape[0]]
+
+    def grad(self, feats, labels):
+        X, Y = _f32(feats, MLP_NF), _f32(labels, 2)
+        g = np.zeros(MLP_NP, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(_lib.g3_mlp_grad(self._keep[0].h, self.h, _ptr(X, C.c_float), _ptr(Y, C.c_float), X.shape[0],
+                                _ptr(g, C.c_float), _ptr(loss, C.c_float)), "g3_mlp_grad")
+        return g, float(loss[0])
+
+    def fit(self, feats, labels, **opts) -> np.ndarray:
+        X, Y = _f32(feats, MLP_NF), _f32(labels, 2)
+        o = _train_opts(**opts)
+        epochs = o.epochs or 200
+        batch = o.batch or 256
+        losses = np.zeros(epochs * (-(-X.shape[0] // batch)), dtype=np.float32)
+        _check(_lib.g3_mlp_fit(self._keep[0].h, self.h, _ptr(X, C.c_float), _ptr(Y, C.c_float), X.shape[0],
+                               C.byref(o), _ptr(losses, C.c_float)), "g3_mlp_fit")
+        return losses
+
+    def get(self) -> dict:
+        P, m, v = (np.zeros(MLP_NP, dtype=np.float32) for _ in range(3))
+        mean, inv = np.zeros(MLP_NF, dtype=np.float32), np.zeros(MLP_NF, dtype=np.float32)
+        t = C.c_int64()
+        _check(_lib.g3_mlp_get(self.h, _ptr(P, C.c_float), _ptr(m, C.c_float), _ptr(v, C.c_float), C.byref(t),
+                               _ptr(mean, C.c_float), _ptr(inv, C.c_float)), "g3_mlp_get")
+        return {"params": P, "m": m, "v": v, "t": t.value, "mean": mean, "inv_std": inv}
+
+
+def mlp_create(ctx: Context, params=None, mean=None, inv_std=None, seed: int = 0) -> Mlp:
+    keep = [None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float32)) for a in (params, mean, inv_std)]
+    if keep[0] is not None and keep[0].size != MLP_NP:
+        raise ValueError(f"params must have {MLP_NP} values")
+    for a in keep[1:]:
+        if a is not None and a.size != MLP_NF:
+            raise ValueError(f"mean / inv_std must have {MLP_NF} values")
+    ptrs = [None if a is None else _ptr(a, C.c_float) for a in keep]
+    h = C.c_void_p()
+    _check(_lib.g3_mlp_create(ctx.h, *ptrs, seed, C.byref(h)), "g3_mlp_create")
+    return Mlp(h, (ctx,))
+
+
+def mlp_train(ctx: Context, feats, labels, **opts) -> Mlp:
+    X, Y = _f32(feats, MLP_NF), _f32(labels, 2)
+    o = _train_opts(**opts)
+    h = C.c_void_p()
+    _check(_lib.g3_mlp_train(ctx.h, _ptr(X, C.c_float), _ptr(Y, C.c_float), X.shape[0], C.byref(o), C.byref(h)),
+           "g3_mlp_train")
+    return Mlp(h, (ctx,))
+
+
+def block_features(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", eps3: float = 1e-4) -> np.ndarray:
+    n = tree.info()["n_far"]
+    out = np.zeros((max(n, 1), MLP_NF), dtype=np.float32)
+    _check(_lib.g3_block_features(ctx.h, tree.h, freqs.h, KERNELS[kernel], eps3, _ptr(out, C.c_float)),
+           "g3_block_features")
+    return out[:n]
+
 
 def _opts(**kw) -> Opts:
     o = Opts()
@@ -348,6 +470,9 @@ def _opts(**kw) -> Opts:
             a = _arr(v, np.float32)
             keep.append(a)
             o.cost = _ptr(a, C.c_float)
+        elif k == "mlp":
+            keep.append(v)
+            o.mlp = v.h
         else:
             setattr(o, k, v)
     o._keep = keep

@@ -38,6 +38,14 @@ namespace g3 {
 
 constexpr int KU_MAX = 256;   // largest unique-frequency count
 constexpr int SAMPLES = 32;   // sample entries of the convergence checks
+constexpr int NPH = 10;       // per-block diagnostics: 7 phases, steps, start, end
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 constexpr int RF_MAX = 64;    // largest face rank cap
 
 template <class T>
@@ -58,13 +66,19 @@ struct AcaArgs {
     int dense_max;           // blocks with M N <= dense_max use exact dense faces
     int sample_check;        // confirm each stop on fixed sample entries
     double eps3, eps_face;
+    double face_floor;       // absolute floor factor of the face tests (0 = none)
+    double trunc_floor;      // absolute floor factor of the recompression truncation (0 = none)
     int no_recompress;
     Cx<T>* pool;
     long long pool_cap;
     unsigned long long* pool_ctr;
+    int* spill;              // [n_far] blocks that found the pool full
+    int* spill_n;
+    int spill_cap;
     CrossRec* rec;
     int* r3;
-    long long* blk_cycles;   // [n_far] SM cycles spent on each block
+    long long* blk_cycles;   // [n_far][NPH] SM cycles per phase spent on each block, its face ACA
+                             // steps, and its start and end time (global timer, ns)
     unsigned long long* counters;  // [0] entries [1] crosses computed [2] zero blocks [3] capped faces
                                    // [8..14] clock cycles per phase (thread 0 of each CTA)
     unsigned* status;
@@ -170,6 +184,7 @@ struct BlockSh {
     Cx<double> hpiv;
     long long new_off;
     long long entries;
+    int raw;              // face ACA steps of the block (ranks before recompression)
     int flag;
     int rot;
     int rnew;
@@ -501,6 +516,11 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     int m = 0;
     int irow = 0;
     bool converged = false;
+    // absolute floor of the face tests (float32 entries only): a residual face
+    // far below the block's typical face, face_floor ||C^(l-1)||_F / sqrt(Ku),
+    // is resolved to that level rather than relative to its own norm, which
+    // the entries' rounding noise would never let the test reach
+    const double floor2 = A.face_floor * A.face_floor * S.norm2 / (double)A.Ku;
     while (m < cap) {
         int jp = -1;
         for (;;) {
@@ -567,7 +587,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
         Sn2 += cross + nu2 * nv2;
         ++m;
         __syncthreads();
-        if (sqrt(nu2 * nv2) <= A.eps_face * sqrt(fmax(Sn2, 0.0))) {
+        if (nu2 * nv2 <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
             if (!A.sample_check) {
                 converged = true;
                 break;
@@ -585,16 +605,18 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
                 }
             }
             __syncthreads();
-            if ((double)M * (double)N / SAMPLES * tot <= A.eps_face * A.eps_face * fmax(Sn2, 0.0)) {
+            if ((double)M * (double)N / SAMPLES * tot <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
                 converged = true;
                 break;
             }
+            if (tid == 0) atomicAdd(&A.counters[5], 1ull);
             irow = (2 * bs + 1) * M / (2 * SAMPLES);
             continue;
         }
         if (nx.v < 0) break;  // every row used
         irow = nx.i;
     }
+    if (tid == 0) S.raw += m;
     if (!converged && m == A.RF && m < min(M, N)) {
         if (tid == 0) {
             atomicOr(A.status, ST_FACE_CAPPED);
@@ -837,11 +859,13 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         finite &= (bool)isfinite(S.sig[a]);
     }
     if (!finite || !(smax > 0.0)) return -1;
+    // (float32 entries: also below the face tests' absolute floor, keeping sigma_1)
+    const double sfloor = A.trunc_floor * sqrt(S.norm2 / (double)A.Ku);
     for (int a = tid; a < r; a += NT) {
         int rank = 0;
         for (int b = 0; b < r; ++b)
             if (S.sig[b] > S.sig[a] || (S.sig[b] == S.sig[a] && b < a)) ++rank;
-        bool keep = S.sig[a] > 0.0 && S.sig[a] >= A.eps_face * smax;
+        bool keep = S.sig[a] > 0.0 && S.sig[a] >= A.eps_face * smax && (rank == 0 || S.sig[a] >= sfloor);
         S.sel[rank] = keep ? a : -1;
     }
     __syncthreads();
@@ -1189,6 +1213,7 @@ __device__ void dense_block(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, 
         bool from_samples = false;
         if (S.stop && A.sample_check && !S.flag) {
             from_samples = !confirm_stop<KER, T, NT>(A, w, S, nc + 1);
+                if (from_samples && threadIdx.x == 0) atomicAdd(&A.counters[6], 1ull);
         }
         if (tid == 0) {
             const bool stop = S.stop && !from_samples;
@@ -1263,11 +1288,13 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             S.pre[0] = 0;
             S.norm2 = 0.0;
             S.entries = 0;
+            S.raw = 0;
             S.k = A.k1 ? A.k1[blk] : 0;
             for (int i = 0; i < KU_MAX / 32; ++i) S.used_k[i] = 0u;
         }
         __syncthreads();
         const int M = S.M, N = S.N, Ku = A.Ku;
+        const unsigned long long t_start = globaltimer_ns();
         // phase cycle counters: face, recompress, formation, pivot, fiber, norm, next-k
         long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
         long long tclk = clock64();
@@ -1280,13 +1307,13 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
         };
         bool zero_block = false;
         int computed = 0;
-        bool overflow = false;
+        bool overflow = false, spilled = false;
         if (M > A.Mmax || N > A.Nmax) {  // cannot happen: workspace is sized from the block list
             if (tid == 0) atomicOr(A.status, ST_BAD_INDEX);
             overflow = true;
         }
         if (DENSE) {
-            if (!overflow) dense_block<KER, T, NT>(A, w, S, zero_block, computed, overflow, ph, tclk);
+            if (!overflow) dense_block<KER, T, NT>(A, w, S, zero_block, computed, spilled, ph, tclk);
             overflow = true;  // the low-rank loop below is not for this launch
         }
         while (!overflow) {
@@ -1353,7 +1380,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             }
             __syncthreads();
             if (S.new_off < 0) {
-                overflow = true;
+                overflow = spilled = true;
                 break;
             }
             const long long off = S.new_off;
@@ -1527,6 +1554,7 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             bool from_samples = false;
             if (S.stop && A.sample_check && !S.flag) {
                 from_samples = !confirm_stop<KER, T, NT>(A, w, S, nc + 1);
+                if (from_samples && threadIdx.x == 0) atomicAdd(&A.counters[6], 1ull);
             }
             if (tid == 0) {
                 const bool stop = S.stop && !from_samples;
@@ -1565,11 +1593,20 @@ __global__ void __launch_bounds__(NT) k_aca3(AcaArgs<T> A) {
             lap(6);
         }
         if (tid == 0) {
-            A.r3[blk] = S.ncross;
-            A.blk_cycles[blk] = ph[0] + ph[1] + ph[2] + ph[3] + ph[4] + ph[5] + ph[6];
+            // a block that found the pool full goes to the spill queue and is
+            // rerun from its start with a fresh pool segment
+            A.r3[blk] = spilled ? 0 : S.ncross;
+            if (spilled) {
+                const int q = atomicAdd(A.spill_n, 1);
+                if (q < A.spill_cap) A.spill[q] = blk;
+            }
+            for (int i = 0; i < 7; ++i) A.blk_cycles[(size_t)blk * NPH + i] += ph[i];
+            A.blk_cycles[(size_t)blk * NPH + 7] += S.raw;
+            A.blk_cycles[(size_t)blk * NPH + 8] = (long long)t_start;
+            A.blk_cycles[(size_t)blk * NPH + 9] = (long long)globaltimer_ns();
             atomicAdd(&A.counters[0], (unsigned long long)S.entries);
             atomicAdd(&A.counters[1], (unsigned long long)computed);
-            if (zero_block) atomicAdd(&A.counters[2], 1ull);
+            if (zero_block && !spilled) atomicAdd(&A.counters[2], 1ull);
             for (int i = 0; i < 7; ++i) atomicAdd(&A.counters[8 + i], (unsigned long long)ph[i]);
         }
         __syncthreads();
@@ -1647,6 +1684,41 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         Nmax = std::max(Nmax, r.ce - r.cb);
         sumMN += (r.re - r.rb) + (r.ce - r.cb);
     }
+    const int dense_max = o.dense_face_max > 0 ? o.dense_face_max : (o.dense_face_max < 0 ? -1 : 48 * 48);
+    auto is_dense = [&](const BlockRange& r) { return (long long)(r.re - r.rb) * (r.ce - r.cb) <= dense_max; };
+    // block predictor: rank and first frequency of every block before the
+    // compression starts (features and forward pass on the device)
+    int mlp_use = 0;
+    std::vector<double> rhat;
+    std::vector<int> k1_mlp;
+    double ms_mlp = 0;
+    if (o.mlp && !sep) {
+        mlp_use = o.mlp_use ? o.mlp_use : 7;
+        DevBuf d_feat, d_pred;
+        G3_CUDA(d_feat.alloc((size_t)n_far * G3_MLP_NF * sizeof(float)));
+        G3_CUDA(d_pred.alloc((size_t)n_far * 2 * sizeof(float)));
+        G3_CUDA(cudaEventRecord(ctx->ev[3], ctx->stream));
+        g3_status st = mlp_features_dev(ctx, t, f, kernel, eps3, d_feat.as<float>());
+        if (st == G3_OK) st = mlp_forward_dev(ctx, o.mlp, d_feat.as<float>(), n_far, d_pred.as<float>());
+        if (st != G3_OK) return st;
+        G3_CUDA(cudaEventRecord(ctx->ev[4], ctx->stream));
+        std::vector<float> pred((size_t)n_far * 2);
+        G3_CUDA(cudaMemcpyAsync(pred.data(), d_pred.p, pred.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaStreamSynchronize(ctx->stream));
+        float mm = 0;
+        G3_CUDA(cudaEventElapsedTime(&mm, ctx->ev[3], ctx->ev[4]));
+        ms_mlp = mm;
+        rhat.resize(n_far);
+        k1_mlp.resize(n_far);
+        for (int i = 0; i < n_far; ++i) {
+            const double y0 = std::isfinite(pred[2 * i]) ? pred[2 * i] : 0.0;
+            const double y1 = std::isfinite(pred[2 * i + 1]) ? pred[2 * i + 1] : 0.0;
+            rhat[i] = std::min((double)Ku, std::max(0.0, std::exp2(std::min(y0, 16.0)) - 1.0));
+            k1_mlp[i] = (int)std::min<long long>(Ku - 1, std::max<long long>(0, std::llround(y1 * Ku)));
+        }
+        if (o.cost) mlp_use &= ~1;
+        if (o.k1) mlp_use &= ~4;
+    }
     std::vector<int> queue(n_far);
     std::iota(queue.begin(), queue.end(), 0);
     // optional bounded run: only the first max_blocks blocks of the far order
@@ -1656,12 +1728,16 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         std::vector<double> cost(n_far);
         for (int i = 0; i < n_far; ++i) {
             double mm = ranges[i].re - ranges[i].rb, nn = ranges[i].ce - ranges[i].cb;
-            cost[i] = o.cost ? (double)o.cost[i] : mm * nn;
+            if (o.cost)
+                cost[i] = (double)o.cost[i];
+            else if (mlp_use & 1)  // predicted work: crosses x entries per cross
+                cost[i] = (rhat[i] + 1.0) * (is_dense(ranges[i]) ? mm * nn : mm + nn);
+            else
+                cost[i] = mm * nn;
         }
         std::stable_sort(queue.begin(), queue.begin() + n_run, [&](int a, int b) { return cost[a] > cost[b]; });
     }
     // two block classes, each in cost order: low-rank faces, then dense faces
-    const int dense_max = o.dense_face_max > 0 ? o.dense_face_max : (o.dense_face_max < 0 ? -1 : 48 * 48);
     std::vector<int> qcat;
     qcat.reserve(n_run);
     for (int pass = 0; pass < 2; ++pass)
@@ -1676,20 +1752,24 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         n_low += !((long long)(r.re - r.rb) * (r.ce - r.cb) <= dense_max);
     }
     const int n_dense = n_run - n_low;
-    DevBuf d_ranges, d_queue, d_head, d_k1, d_counters, d_ctr;
+    DevBuf d_ranges, d_queue, d_head, d_k1, d_counters, d_ctr, d_spill, d_spill_n;
     G3_CUDA(d_ranges.alloc(n_far * sizeof(BlockRange)));
     G3_CUDA(d_queue.alloc(std::max(n_run, 1) * sizeof(int)));
     G3_CUDA(d_head.alloc(2 * sizeof(int)));
     G3_CUDA(d_counters.alloc(16 * sizeof(unsigned long long)));
     G3_CUDA(d_ctr.alloc(sizeof(unsigned long long)));
+    G3_CUDA(d_spill.alloc(std::max(n_far, 1) * sizeof(int)));
+    G3_CUDA(d_spill_n.alloc(sizeof(int)));
     G3_CUDA(cudaMemcpyAsync(d_ranges.p, ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice, ctx->stream));
     if (n_run > 0)
         G3_CUDA(cudaMemcpyAsync(d_queue.p, qcat.data(), n_run * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    if (o.k1) {
+    const int* k1_host = o.k1 ? o.k1 : ((mlp_use & 4) ? k1_mlp.data() : nullptr);
+    if (k1_host) {
         for (int i = 0; i < n_far; ++i)
-            if (o.k1[i] < 0 || o.k1[i] >= Ku) return fail(G3_EINVAL, "opts->k1[%d] = %d outside [0, %d)", i, o.k1[i], Ku);
+            if (k1_host[i] < 0 || k1_host[i] >= Ku)
+                return fail(G3_EINVAL, "opts->k1[%d] = %d outside [0, %d)", i, k1_host[i], Ku);
         G3_CUDA(d_k1.alloc(n_far * sizeof(int)));
-        G3_CUDA(cudaMemcpyAsync(d_k1.p, o.k1, n_far * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        G3_CUDA(cudaMemcpy(d_k1.p, k1_host, n_far * sizeof(int), cudaMemcpyHostToDevice));
     }
     // separable inputs (converted to T)
     DevBuf d_sa, d_sb, d_sc;
@@ -1731,33 +1811,50 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
     G3_CUDA(d_ws.alloc(stride * grid));
     G3_CUDA(fa->d_rec.alloc((size_t)n_far * Ku * sizeof(CrossRec)));
     G3_CUDA(fa->d_r3.alloc((size_t)n_far * sizeof(int)));
-    G3_CUDA(fa->d_cycles.alloc((size_t)n_far * sizeof(long long)));
-    // factor pool: initial estimate, regrown on overflow
+    G3_CUDA(fa->d_cycles.alloc((size_t)n_far * NPH * sizeof(long long)));
+    // factor pool: initial estimate; blocks that find it full go to a spill
+    // queue and are rerun in a further launch with an enlarged pool
     double pf = o.pool_factor > 0 ? o.pool_factor : 1.0;
-    // pool estimate per block class (elements): low-rank blocks ~256 (M + N),
-    // dense blocks ~12 M N, fibers 24 Ku per block; scaled by what earlier
-    // compressions on this context needed relative to the same estimate
-    double est = 0.0;
-    for (int q = 0; q < n_run; ++q) {
-        const BlockRange& r = ranges[queue[q]];
+    // estimate per block (complex elements).  Plain: low-rank blocks ~256 (M + N),
+    // dense blocks ~12 M N, fibers 24 Ku.  Predicted: ceil(1.25 r3) + 2 crosses of
+    // 16 (M + N) + Ku (low-rank, a typical kept face rank of 16) or M N + Ku.
+    // Each is scaled by what earlier compressions on this context needed
+    // relative to the same estimate.
+    const bool pool_mlp = (mlp_use & 2) != 0;
+    auto block_est = [&](int b) {
+        const BlockRange& r = ranges[b];
         const double m = r.re - r.rb, n = r.ce - r.cb;
-        est += (m * n <= (double)dense_max) ? 12.0 * m * n : 256.0 * (m + n);
-        est += 24.0 * Ku;
-    }
-    long long cap = (long long)(pf * ctx->pool_scale * est);
+        if (pool_mlp) {
+            const double slots = std::ceil(1.25 * rhat[b]) + 2.0;
+            return slots * ((is_dense(r) ? m * n : 16.0 * (m + n)) + Ku);
+        }
+        return (is_dense(r) ? 12.0 * m * n : 256.0 * (m + n)) + 24.0 * Ku;
+    };
+    double& scale = pool_mlp ? ctx->pool_scale_mlp : ctx->pool_scale;
+    double est = 0.0;
+    for (int q = 0; q < n_run; ++q) est += block_est(queue[q]);
+    long long cap = (long long)(pf * scale * est);
     cap = std::max(cap, (long long)1 << 16);
-    int regrows = 0;
+    G3_CUDA(fa->pool.alloc((size_t)cap * sizeof(Cx<T>)));
+    fa->pool_cap = cap;
+    G3_CUDA(cudaMemsetAsync(d_head.p, 0, 2 * sizeof(int), ctx->stream));
+    G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 16 * sizeof(unsigned long long), ctx->stream));
+    G3_CUDA(cudaMemsetAsync(fa->d_r3.p, 0, (size_t)n_far * sizeof(int), ctx->stream));
+    G3_CUDA(cudaMemsetAsync(fa->d_cycles.p, 0, (size_t)n_far * NPH * sizeof(long long), ctx->stream));
+    std::vector<int> qpos(n_far, 0);
+    for (int q = 0; q < n_run; ++q) qpos[qcat[q]] = q;
+    unsigned long long base = 0;  // pool elements in use before this launch round
+    int n_lo = n_low, n_de = n_dense;
+    int regrows = 0, spilled_total = 0;
+    unsigned status_all = 0;
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
-    float ms_total = 0;
+    double ms_total = 0, ms_low_total = 0, ms_dense_total = 0;
+    unsigned long long ctr = 0;
     for (;;) {
-        G3_CUDA(fa->pool.alloc((size_t)cap * sizeof(Cx<T>)));
-        fa->pool_cap = cap;
         G3_CUDA(cudaMemsetAsync(d_head.p, 0, 2 * sizeof(int), ctx->stream));
-        G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 16 * sizeof(unsigned long long), ctx->stream));
-        G3_CUDA(cudaMemsetAsync(d_ctr.p, 0, sizeof(unsigned long long), ctx->stream));
+        G3_CUDA(cudaMemsetAsync(d_spill_n.p, 0, sizeof(int), ctx->stream));
         G3_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
-        G3_CUDA(cudaMemsetAsync(fa->d_r3.p, 0, (size_t)n_far * sizeof(int), ctx->stream));
-        G3_CUDA(cudaMemsetAsync(fa->d_cycles.p, 0, (size_t)n_far * sizeof(long long), ctx->stream));
+        G3_CUDA(cudaMemcpyAsync(d_ctr.p, &base, sizeof(base), cudaMemcpyHostToDevice, ctx->stream));
         AcaArgs<T> A{};
         A.gf = t ? t->gf : GeomF{};
         A.gd = t ? t->gd : GeomD{};
@@ -1767,21 +1864,26 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         A.Ku = Ku;
         A.k_maxabs = f ? f->k_maxabs : Ku - 1;
         A.ranges = d_ranges.as<BlockRange>();
-        A.n_far = n_run;
+        A.n_far = n_far;
         A.queue = d_queue.as<int>();
         A.queue_head = d_head.as<int>();
         A.single = -1;
-        A.k1 = o.k1 ? d_k1.as<int>() : nullptr;
+        A.k1 = k1_host ? d_k1.as<int>() : nullptr;
         A.Cmax = Ku;
         A.RF = RF;
-        A.dense_max = o.dense_face_max > 0 ? o.dense_face_max : (o.dense_face_max < 0 ? -1 : 48 * 48);
+        A.dense_max = dense_max;
         A.sample_check = o.literal_stop ? 0 : 1;
         A.eps3 = eps3;
         A.eps_face = eps_face;
+        A.face_floor = sizeof(T) == 4 ? eps_face * (o.face_floor_scale > 0 ? o.face_floor_scale : 1.0) : 0.0;
+        A.trunc_floor = sizeof(T) == 4 ? eps_face * (o.trunc_floor_scale > 0 ? o.trunc_floor_scale : 1.0) : 0.0;
         A.no_recompress = o.no_recompress;
         A.pool = fa->pool.as<Cx<T>>();
         A.pool_cap = cap;
         A.pool_ctr = d_ctr.as<unsigned long long>();
+        A.spill = d_spill.as<int>();
+        A.spill_n = d_spill_n.as<int>();
+        A.spill_cap = n_far;
         A.rec = fa->d_rec.as<CrossRec>();
         A.r3 = fa->d_r3.as<int>();
         A.blk_cycles = fa->d_cycles.as<long long>();
@@ -1795,14 +1897,14 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         g3_status st = G3_OK;
         for (int cls = 0; cls < 2 && st == G3_OK; ++cls) {
             if (cls == 1) G3_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
-            const int cnt = cls == 0 ? n_low : n_dense;
+            const int cnt = cls == 0 ? n_lo : n_de;
             if (cnt == 0) continue;
             AcaArgs<T> B = A;
-            B.queue = d_queue.as<int>() + (cls == 0 ? 0 : n_low);
+            B.queue = d_queue.as<int>() + (cls == 0 ? 0 : n_lo);
             B.queue_head = d_head.as<int>() + cls;
             B.n_far = cnt;
             const int launches = o.unbatched ? cnt : 1;
-            const int g = cls == 0 ? grid_low : grid_dense;
+            const int g = std::min(cls == 0 ? grid_low : grid_dense, o.unbatched ? 1 : cnt);
             for (int l = 0; l < launches && st == G3_OK; ++l) {
                 if (o.unbatched) B.single = l;
                 st = cls == 0 ? launch_kind<T, NT, false>(ctx, kernel, B, g, smem)
@@ -1812,26 +1914,68 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         if (st != G3_OK) return st;
         G3_CUDA(cudaEventRecord(e1, ctx->stream));
         unsigned status = 0;
-        unsigned long long ctr = 0;
+        int n_spill = 0;
         G3_CUDA(cudaMemcpyAsync(&status, ctx->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
         G3_CUDA(cudaMemcpyAsync(&ctr, d_ctr.p, sizeof(ctr), cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaMemcpyAsync(&n_spill, d_spill_n.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         G3_CUDA(cudaStreamSynchronize(ctx->stream));
         float ms = 0, ms_low = 0;
         G3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         G3_CUDA(cudaEventElapsedTime(&ms_low, e0, ctx->ev[2]));
         ms_total += ms;
-        if (status & ST_POOL_OVERFLOW) {
-            if (++regrows > 6) return fail(G3_EOVERFLOW, "aca3_compress: factor pool overflow after %d regrows", regrows);
-            cap = std::max(cap * 2, (long long)(ctr * 5 / 4));
-            continue;
-        }
-        if (est > 0) ctx->pool_scale = std::max(ctx->pool_scale, 1.15 * (double)ctr / est);
+        ms_low_total += ms_low;
+        ms_dense_total += ms - ms_low;
+        status_all |= status & ~ST_POOL_OVERFLOW;
+        if (!(status & ST_POOL_OVERFLOW)) break;
+        if (++regrows > 8 || n_spill <= 0 || n_spill > n_far)
+            return fail(G3_EOVERFLOW, "aca3_compress: factor pool overflow after %d spill rounds", regrows);
+        spilled_total += n_spill;
+        // spilled blocks, in their original queue order, split by class
+        std::vector<int> sp(n_spill);
+        G3_CUDA(cudaMemcpy(sp.data(), d_spill.p, n_spill * sizeof(int), cudaMemcpyDeviceToHost));
+        std::sort(sp.begin(), sp.end(), [&](int a, int b) { return qpos[a] < qpos[b]; });
+        std::vector<int> nq;
+        nq.reserve(n_spill);
+        double est2 = 0.0;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b : sp)
+                if (is_dense(ranges[b]) == (pass == 1)) {
+                    nq.push_back(b);
+                    est2 += block_est(b);
+                }
+        n_lo = 0;
+        for (int b : sp) n_lo += !is_dense(ranges[b]);
+        n_de = n_spill - n_lo;
+        // enlarged pool: the used part [0, cap) is kept at the same offsets
+        long long add = (long long)(1.5 * scale * est2);
+        add = std::max(add, (long long)(ctr - std::min<unsigned long long>(ctr, (unsigned long long)cap)));
+        add = std::max(add, (long long)1 << 16);
+        DevBuf grown;
+        G3_CUDA(grown.alloc((size_t)(cap + add) * sizeof(Cx<T>)));
+        G3_CUDA(cudaMemcpyAsync(grown.p, fa->pool.p, (size_t)cap * sizeof(Cx<T>), cudaMemcpyDeviceToDevice, ctx->stream));
+        G3_CUDA(cudaStreamSynchronize(ctx->stream));
+        fa->pool.release();
+        fa->pool.p = grown.p;
+        fa->pool.bytes = grown.bytes;
+        grown.p = nullptr;
+        grown.bytes = 0;
+        base = (unsigned long long)cap;
+        cap += add;
+        fa->pool_cap = cap;
+        G3_CUDA(cudaMemcpy(d_queue.p, nq.data(), n_spill * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    {
+        if (est > 0) scale = std::max(scale, 1.15 * (double)ctr / est);
         unsigned long long cnt[16];
         G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
         fa->r3.resize(n_far);
         G3_CUDA(cudaMemcpy(fa->r3.data(), fa->d_r3.p, n_far * sizeof(int), cudaMemcpyDeviceToHost));
-        fa->cycles.resize(n_far);
-        G3_CUDA(cudaMemcpy(fa->cycles.data(), fa->d_cycles.p, n_far * sizeof(long long), cudaMemcpyDeviceToHost));
+        fa->phases.resize((size_t)n_far * NPH);
+        G3_CUDA(cudaMemcpy(fa->phases.data(), fa->d_cycles.p, fa->phases.size() * sizeof(long long),
+                           cudaMemcpyDeviceToHost));
+        fa->cycles.assign(n_far, 0);
+        for (int b = 0; b < n_far; ++b)
+            for (int i = 0; i < 7; ++i) fa->cycles[b] += fa->phases[(size_t)b * NPH + i];
         fa->rec.resize((size_t)n_far * Ku);
         G3_CUDA(cudaMemcpy(fa->rec.data(), fa->d_rec.p, fa->rec.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
         g3_stats& S = fa->stats;
@@ -1844,10 +1988,15 @@ static g3_status run_aca_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_
         S.capped_faces = (int32_t)cnt[3];
         S.pool_regrows = regrows;
         S.recompress_fallbacks = (int32_t)cnt[4];
-        S.status_bits = (int32_t)status;
+        S.status_bits = (int32_t)status_all;
         S.ms = ms_total;
-        S.ms_lowrank = ms_low;
-        S.ms_dense = ms - ms_low;
+        S.ms_lowrank = ms_low_total;
+        S.ms_dense = ms_dense_total;
+        S.spilled_blocks = spilled_total;
+        S.face_check_restarts = (int64_t)cnt[5];
+        S.stop_check_overrides = (int64_t)cnt[6];
+        S.mlp_used = mlp_use;
+        S.ms_mlp = ms_mlp;
         for (int i = 0; i < 7; ++i) S.phase_cycles[i] = (int64_t)cnt[8 + i];
         S.ctas = grid;
         for (int b = 0; b < n_far; ++b) {

@@ -552,6 +552,7 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     g3_opts o = defaults(opts);
     G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress: face_rank_max = %d outside [0, 64]", o.face_rank_max);
     G3_CHECK(o.threads == 0 || o.threads == 256, "aca3_compress: threads must be 0 or 256");
+    G3_CHECK(o.mlp_use >= 0 && o.mlp_use <= 7, "aca3_compress: mlp_use = %d outside [0, 7]", o.mlp_use);
     G3_TRY(use_device(ctx));
     g3_factors* fa = new (std::nothrow) g3_factors();
     if (!fa) return fail(G3_ENOMEM, "aca3_compress: out of host memory");
@@ -613,6 +614,12 @@ g3_status g3_factors_ranks(const g3_factors* fa, int32_t* r3) {
 g3_status g3_factors_block_cycles(const g3_factors* fa, int64_t* cycles) {
     G3_CHECK(fa && cycles, "g3_factors_block_cycles: NULL argument");
     for (size_t i = 0; i < fa->cycles.size(); ++i) cycles[i] = (int64_t)fa->cycles[i];
+    return G3_OK;
+}
+
+g3_status g3_factors_block_phases(const g3_factors* fa, int64_t* out) {
+    G3_CHECK(fa && out, "g3_factors_block_phases: NULL argument");
+    for (size_t i = 0; i < fa->phases.size(); ++i) out[i] = (int64_t)fa->phases[i];
     return G3_OK;
 }
 
@@ -715,6 +722,224 @@ g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* n
     if (bytes) *bytes = ctx->last_apply_bytes;
     if (near_ms) *near_ms = ctx->last_near_ms;
     if (near_bytes) *near_bytes = ctx->last_near_bytes;
+    return G3_OK;
+}
+
+// ---- block predictor ---------------------------------------------------------
+
+static g3_status mlp_alloc(g3_ctx* ctx, const float* params, const float* mean, const float* inv_std, uint64_t seed,
+                           g3_mlp** out) {
+    g3_mlp* m = new (std::nothrow) g3_mlp();
+    if (!m) return fail(G3_ENOMEM, "g3_mlp: out of host memory");
+    std::vector<float> P(G3_MLP_NP), Z(G3_MLP_NP, 0.f);
+    if (params) {
+        for (int i = 0; i < G3_MLP_NP; ++i)
+            if (!std::isfinite(params[i])) {
+                delete m;
+                return fail(G3_EINVAL, "g3_mlp_create: params[%d] is not finite", i);
+            }
+        std::memcpy(P.data(), params, sizeof(float) * G3_MLP_NP);
+    } else {
+        mlp_init_params(seed, P.data());
+    }
+    for (int i = 0; i < G3_MLP_NF; ++i) {
+        m->mean[i] = mean ? mean[i] : 0.f;
+        m->inv_std[i] = inv_std ? inv_std[i] : 1.f;
+    }
+    m->ctx = ctx;
+    auto up = [&](g3::DevBuf& d, const void* src, size_t bytes) -> cudaError_t {
+        cudaError_t e = d.alloc(bytes);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice);
+    };
+    const long long t0 = 0;
+    cudaError_t e;
+    if ((e = up(m->d_params, P.data(), sizeof(float) * G3_MLP_NP)) != cudaSuccess ||
+        (e = up(m->d_m, Z.data(), sizeof(float) * G3_MLP_NP)) != cudaSuccess ||
+        (e = up(m->d_v, Z.data(), sizeof(float) * G3_MLP_NP)) != cudaSuccess ||
+        (e = up(m->d_t, &t0, sizeof(t0))) != cudaSuccess ||
+        (e = up(m->d_mean, m->mean, sizeof(float) * G3_MLP_NF)) != cudaSuccess ||
+        (e = up(m->d_inv_std, m->inv_std, sizeof(float) * G3_MLP_NF)) != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "g3_mlp_create: upload");
+    }
+    *out = m;
+    return G3_OK;
+}
+
+g3_status g3_mlp_create(g3_ctx* ctx, const float* params, const float* mean, const float* inv_std, uint64_t seed,
+                        g3_mlp** out) {
+    G3_CHECK(ctx && out, "g3_mlp_create: NULL argument");
+    *out = nullptr;
+    G3_TRY(use_device(ctx));
+    return mlp_alloc(ctx, params, mean, inv_std, seed, out);
+}
+
+struct TrainCfg {
+    int epochs, batch, graph;
+    double lr, b1, b2, eps;
+    uint64_t seed;
+};
+
+static g3_status train_cfg(const g3_train_opts* o, TrainCfg& c) {
+    g3_train_opts d{};
+    if (o) d = *o;
+    c.epochs = d.epochs > 0 ? d.epochs : 200;
+    c.batch = d.batch > 0 ? d.batch : 256;
+    c.lr = d.lr > 0 ? d.lr : 1e-3;
+    c.b1 = d.beta1 > 0 ? d.beta1 : 0.9;
+    c.b2 = d.beta2 > 0 ? d.beta2 : 0.999;
+    c.eps = d.adam_eps > 0 ? d.adam_eps : 1e-8;
+    c.seed = d.seed;
+    c.graph = d.no_graph ? 0 : 1;
+    G3_CHECK(d.epochs >= 0 && d.batch >= 0, "g3_mlp: negative epochs or batch");
+    G3_CHECK(c.b1 < 1 && c.b2 < 1, "g3_mlp: Adam decay rates must be below 1");
+    return G3_OK;
+}
+
+static g3_status upload_samples(const float* feats, const float* labels, int n, g3::DevBuf& dx, g3::DevBuf& dy) {
+    G3_CUDA(dx.alloc((size_t)n * G3_MLP_NF * sizeof(float)));
+    G3_CUDA(cudaMemcpy(dx.p, feats, (size_t)n * G3_MLP_NF * sizeof(float), cudaMemcpyHostToDevice));
+    if (labels) {
+        G3_CUDA(dy.alloc((size_t)n * 2 * sizeof(float)));
+        G3_CUDA(cudaMemcpy(dy.p, labels, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return G3_OK;
+}
+
+static g3_status fit(g3_ctx* ctx, g3_mlp* m, const float* feats, const float* labels, int n, const TrainCfg& c,
+                     float* losses) {
+    g3::DevBuf dx, dy, dl;
+    G3_TRY(upload_samples(feats, labels, n, dx, dy));
+    const long long nb = ((long long)n + c.batch - 1) / c.batch;
+    G3_CUDA(dl.alloc((size_t)c.epochs * nb * sizeof(float)));
+    G3_TRY(mlp_fit_dev(ctx, m, dx.as<float>(), dy.as<float>(), n, c.epochs, c.batch, c.lr, c.b1, c.b2, c.eps, c.graph,
+                       dl.as<float>()));
+    if (losses) G3_CUDA(cudaMemcpy(losses, dl.p, (size_t)c.epochs * nb * sizeof(float), cudaMemcpyDeviceToHost));
+    return G3_OK;
+}
+
+g3_status g3_mlp_train(g3_ctx* ctx, const float* feats, const float* labels, int n, const g3_train_opts* opts,
+                       g3_mlp** out) {
+    G3_CHECK(ctx && feats && labels && out, "g3_mlp_train: NULL argument");
+    *out = nullptr;
+    G3_CHECK(n >= 1, "g3_mlp_train: n = %d", n);
+    TrainCfg c;
+    G3_TRY(train_cfg(opts, c));
+    G3_TRY(use_device(ctx));
+    // standardisation from the samples (float64 sums on the host)
+    float mean[G3_MLP_NF], inv[G3_MLP_NF];
+    for (int f = 0; f < G3_MLP_NF; ++f) {
+        double s = 0, s2 = 0;
+        for (int i = 0; i < n; ++i) s += feats[(size_t)i * G3_MLP_NF + f];
+        const double mu = s / n;
+        for (int i = 0; i < n; ++i) {
+            const double d = feats[(size_t)i * G3_MLP_NF + f] - mu;
+            s2 += d * d;
+        }
+        const double sd = std::sqrt(s2 / n);
+        G3_CHECK(std::isfinite(mu) && std::isfinite(sd), "g3_mlp_train: feature %d is not finite", f);
+        mean[f] = (float)mu;
+        inv[f] = sd > 1e-6 ? (float)(1.0 / sd) : 1.0f;
+    }
+    g3_mlp* m = nullptr;
+    G3_TRY(mlp_alloc(ctx, nullptr, mean, inv, c.seed, &m));
+    const g3_status st = fit(ctx, m, feats, labels, n, c, nullptr);
+    if (st != G3_OK) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return G3_OK;
+}
+
+g3_status g3_mlp_fit(g3_ctx* ctx, g3_mlp* m, const float* feats, const float* labels, int n,
+                     const g3_train_opts* opts, float* losses) {
+    G3_CHECK(ctx && m && feats && labels, "g3_mlp_fit: NULL argument");
+    G3_CHECK(n >= 1, "g3_mlp_fit: n = %d", n);
+    TrainCfg c;
+    G3_TRY(train_cfg(opts, c));
+    G3_TRY(use_device(ctx));
+    return fit(ctx, m, feats, labels, n, c, losses);
+}
+
+g3_status g3_mlp_grad(g3_ctx* ctx, const g3_mlp* m, const float* feats, const float* labels, int n, float* grad,
+                      float* loss) {
+    G3_CHECK(ctx && m && feats && labels && grad, "g3_mlp_grad: NULL argument");
+    G3_CHECK(n >= 1, "g3_mlp_grad: n = %d", n);
+    G3_TRY(use_device(ctx));
+    g3::DevBuf dx, dy, dg, dl;
+    G3_TRY(upload_samples(feats, labels, n, dx, dy));
+    G3_CUDA(dg.alloc(G3_MLP_NP * sizeof(float)));
+    G3_CUDA(dl.alloc(sizeof(float)));
+    G3_TRY(mlp_grad_dev(ctx, m, dx.as<float>(), dy.as<float>(), n, dg.as<float>(), dl.as<float>()));
+    G3_CUDA(cudaMemcpy(grad, dg.p, G3_MLP_NP * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss) G3_CUDA(cudaMemcpy(loss, dl.p, sizeof(float), cudaMemcpyDeviceToHost));
+    return G3_OK;
+}
+
+g3_status g3_mlp_predict(g3_ctx* ctx, const g3_mlp* m, const float* feats, int n, float* out) {
+    G3_CHECK(ctx && m && feats && out, "g3_mlp_predict: NULL argument");
+    G3_CHECK(n >= 0, "g3_mlp_predict: n = %d", n);
+    if (n == 0) return G3_OK;
+    G3_TRY(use_device(ctx));
+    g3::DevBuf dx, dy, dout;
+    G3_TRY(upload_samples(feats, nullptr, n, dx, dy));
+    G3_CUDA(dout.alloc((size_t)n * 2 * sizeof(float)));
+    G3_TRY(mlp_forward_dev(ctx, m, dx.as<float>(), n, dout.as<float>()));
+    G3_CUDA(cudaMemcpyAsync(out, dout.p, (size_t)n * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    G3_CUDA(cudaStreamSynchronize(ctx->stream));
+    return G3_OK;
+}
+
+g3_status g3_mlp_get(const g3_mlp* m, float* params, float* adam_m, float* adam_v, int64_t* t, float* mean,
+                     float* inv_std) {
+    G3_CHECK(m != nullptr, "g3_mlp_get: NULL handle");
+    G3_TRY(use_device(m->ctx));
+    G3_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    if (params) G3_CUDA(cudaMemcpy(params, m->d_params.p, G3_MLP_NP * sizeof(float), cudaMemcpyDeviceToHost));
+    if (adam_m) G3_CUDA(cudaMemcpy(adam_m, m->d_m.p, G3_MLP_NP * sizeof(float), cudaMemcpyDeviceToHost));
+    if (adam_v) G3_CUDA(cudaMemcpy(adam_v, m->d_v.p, G3_MLP_NP * sizeof(float), cudaMemcpyDeviceToHost));
+    if (t) *t = m->t;
+    if (mean) std::memcpy(mean, m->mean, sizeof(m->mean));
+    if (inv_std) std::memcpy(inv_std, m->inv_std, sizeof(m->inv_std));
+    return G3_OK;
+}
+
+g3_status g3_mlp_free(g3_mlp* m) {
+    if (!m) return G3_OK;
+    if (m->ctx) cudaSetDevice(m->ctx->device);
+    delete m;
+    return G3_OK;
+}
+
+g3_status g3_block_features(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, double eps3,
+                            float* out) {
+    G3_CHECK(ctx && t && f && out, "g3_block_features: NULL argument");
+    G3_CHECK(kernel == G3_SLP || kernel == G3_DLP, "g3_block_features: kernel must be G3_SLP or G3_DLP");
+    G3_CHECK(eps3 > 0 && eps3 < 1, "g3_block_features: eps3 = %g outside (0, 1)", eps3);
+    const int n_far = (int)t->far_index.size();
+    if (n_far == 0) return G3_OK;
+    G3_TRY(use_device(ctx));
+    g3::DevBuf d;
+    G3_CUDA(d.alloc((size_t)n_far * G3_MLP_NF * sizeof(float)));
+    G3_TRY(mlp_features_dev(ctx, t, f, kernel, eps3, d.as<float>()));
+    G3_CUDA(cudaMemcpyAsync(out, d.p, (size_t)n_far * G3_MLP_NF * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    G3_CUDA(cudaStreamSynchronize(ctx->stream));
+    return G3_OK;
+}
+
+g3_status g3_factors_labels(g3_ctx* ctx, const g3_factors* fa, float* out) {
+    G3_CHECK(ctx && fa && out, "g3_factors_labels: NULL argument");
+    if (fa->n_far == 0) return G3_OK;
+    G3_TRY(use_device(ctx));
+    g3::DevBuf dr, d;
+    G3_CUDA(dr.alloc(fa->ranges.size() * sizeof(BlockRange)));
+    G3_CUDA(cudaMemcpy(dr.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange), cudaMemcpyHostToDevice));
+    G3_CUDA(d.alloc((size_t)fa->n_far * 2 * sizeof(float)));
+    G3_TRY(mlp_labels_dev(ctx, fa, dr.as<BlockRange>(), d.as<float>()));
+    G3_CUDA(cudaMemcpyAsync(out, d.p, (size_t)fa->n_far * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    G3_CUDA(cudaStreamSynchronize(ctx->stream));
     return G3_OK;
 }
 

@@ -47,54 +47,67 @@ __global__ void k_apply_prep(int E, int K, int Ku, const int* __restrict__ perm,
     }
 }
 
-// Near field: one CTA per (row cluster, frequency chunk).  For each near block
-// of the row, each thread owns entries e = tid + NT*m of the block and sums
-// Re A (w + w') + i Im A (w - w') over the chunk's frequencies; rows are
-// reduced in shared memory, then added to y.
+// Near field: one CTA per (row cluster, frequency chunk).  Warp w takes the
+// rows i = w, w + NW, ... of every near block of the row cluster; lane j takes
+// column j (near blocks are leaf x leaf, N <= 32 per pass) and sums
+// Re A (w + w') + i Im A (w - w') over the chunk's frequencies, reading the
+// block's entries A[k][i][j] (row-major per frequency) coalesced along j.  A
+// row's sum is reduced across the warp and added to the row in shared memory
+// by lane 0 (each row has one owning warp); the CTA adds its rows to y once.
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, const BlockRange* __restrict__ ranges,
                                                    const long long* __restrict__ offs, const int* __restrict__ row_start,
                                                    int Ku, int kchunk, int E, const Cx<T>* __restrict__ Wf,
                                                    const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NW = NT / 32;
     T* ysh = reinterpret_cast<T*>(smem_raw);  // [2 * Mrow]
     const int g = blockIdx.x;
     const int k0 = blockIdx.y * kchunk, k1 = min(Ku, k0 + kchunk);
     const int b0 = row_start[g], b1 = row_start[g + 1];
     const int rb = ranges[b0].rb, Mrow = ranges[b0].re - ranges[b0].rb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 2 * Mrow; i += NT) ysh[i] = 0;
     __syncthreads();
     for (int b = b0; b < b1; ++b) {
         const BlockRange br = ranges[b];
         const int N = br.ce - br.cb;
-        const int MN = Mrow * N;
+        const long long MN = (long long)Mrow * N;
         const Cx<T>* Ab = A + offs[b];
-        for (int e = threadIdx.x; e < MN; e += NT) {
-            const int i = e / N, j = br.cb + e % N;
+        for (int i = warp; i < Mrow; i += NW) {
             T ax = 0, ay = 0;
-            int k = k0;
-            for (; k + 4 <= k1; k += 4) {
-                Cx<T> a[4], wf[4], wc[4];
+            for (int j = lane; j < N; j += 32) {
+                const Cx<T>* a_p = Ab + (long long)i * N + j;
+                const Cx<T>* wf_p = Wf + br.cb + j;
+                const Cx<T>* wc_p = Wc + br.cb + j;
+                int k = k0;
+                for (; k + 4 <= k1; k += 4) {
+                    Cx<T> a[4], wf[4], wc[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    a[u] = Ab[(long long)(k + u) * MN + e];
-                    wf[u] = Wf[(long long)(k + u) * E + j];
-                    wc[u] = Wc[(long long)(k + u) * E + j];
+                    for (int u = 0; u < 4; ++u) {
+                        a[u] = a_p[(long long)(k + u) * MN];
+                        wf[u] = wf_p[(long long)(k + u) * E];
+                        wc[u] = wc_p[(long long)(k + u) * E];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        // Re A (wf + wc) + i Im A (wf - wc)
+                        ax += a[u].x * (wf[u].x + wc[u].x) - a[u].y * (wf[u].y - wc[u].y);
+                        ay += a[u].x * (wf[u].y + wc[u].y) + a[u].y * (wf[u].x - wc[u].x);
+                    }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    // Re A (wf + wc) + i Im A (wf - wc)
-                    ax += a[u].x * (wf[u].x + wc[u].x) - a[u].y * (wf[u].y - wc[u].y);
-                    ay += a[u].x * (wf[u].y + wc[u].y) + a[u].y * (wf[u].x - wc[u].x);
+                for (; k < k1; ++k) {
+                    const Cx<T> a = a_p[(long long)k * MN], wf = wf_p[(long long)k * E], wc = wc_p[(long long)k * E];
+                    ax += a.x * (wf.x + wc.x) - a.y * (wf.y - wc.y);
+                    ay += a.x * (wf.y + wc.y) + a.y * (wf.x - wc.x);
                 }
             }
-            for (; k < k1; ++k) {
-                Cx<T> a = Ab[(long long)k * MN + e], wf = Wf[(long long)k * E + j], wc = Wc[(long long)k * E + j];
-                ax += a.x * (wf.x + wc.x) - a.y * (wf.y - wc.y);
-                ay += a.x * (wf.y + wc.y) + a.y * (wf.x - wc.x);
+            ax = warp_sum(ax);
+            ay = warp_sum(ay);
+            if (lane == 0) {
+                ysh[2 * i] += ax;
+                ysh[2 * i + 1] += ay;
             }
-            atomicAdd(&ysh[2 * i], ax);
-            atomicAdd(&ysh[2 * i + 1], ay);
         }
     }
     __syncthreads();
@@ -104,108 +117,124 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
     }
 }
 
-// Far field: one CTA per admissible block.  A low-rank cross (U, V, f) adds
-// U (V^H x) + conj(U (V^H zc)); a dense cross (H, f; r = -1) adds
-// H x + conj(H zc), with x = sum_k f[k] w_k and zc = sum_k f[k] conj(w_k').
-template <class T, int NT>
+// Far field: one CTA per admissible block, its crosses in groups of PG.  For a
+// group the CTA forms, in one pass over the block's columns of W (read once per
+// group rather than once per cross),
+//   x_p = sum_k f_p[k] w_k ,  zc_p = sum_k f_p[k] conj(w_k')      (p in the group)
+// and then adds
+//   low-rank cross (U, V):   U_p (V_p^H x_p) + conj(U_p (V_p^H zc_p))
+//   dense cross (H; r = -1): H_p x_p + conj(H_p zc_p)
+// Every factor is read once; the W columns come from L2.
+template <class T, int NT, int PG>
 __global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
                                                   const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
                                                   const int* __restrict__ list, int Cmax, int Ku, int E,
                                                   const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
-                                                  Cx<T>* __restrict__ y, int ysmem_max, int dense_n_max) {
+                                                  Cx<T>* __restrict__ y, int ysmem_max, int dense_n_max, int rmax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T>* fsh = reinterpret_cast<Cx<T>*>(smem_raw);  // [Ku]
-    Cx<T>* ab = fsh + Ku;                             // [2 * 64]: a[t], b[t]
-    Cx<T>* xs = ab + 128;                             // [dense_n_max] x (dense crosses)
-    Cx<T>* zs = xs + dense_n_max;                     // [dense_n_max] zc
-    T* ysh = reinterpret_cast<T*>(zs + dense_n_max);  // [2 * M] when M <= ysmem_max
+    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);   // [PG][Ku] fibers of the group
+    Cx<T>* ab = fg + PG * Ku;                          // [PG][rmax][2]: V^H x, V^H zc
+    Cx<T>* xs = ab + PG * rmax * 2;                    // [PG][dense_n_max] x (dense crosses)
+    Cx<T>* zs = xs + PG * dense_n_max;                 // [PG][dense_n_max] zc
+    T* ysh = reinterpret_cast<T*>(zs + PG * dense_n_max);  // [2 M] when M <= ysmem_max
+    __shared__ CrossRec crs[PG];
     const int blk = list[blockIdx.x];
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
     const int nc = r3[blk];
     const bool ysm = M <= ysmem_max;
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (ysm)
-        for (int i = threadIdx.x; i < 2 * M; i += NT) ysh[i] = 0;
-    for (int p = 0; p < nc; ++p) {
-        const CrossRec c = rec[(size_t)blk * Cmax + p];
-        if (c.r < 0) {
-            const Cx<T>* H = pool + c.off;
-            const Cx<T>* F = H + (long long)M * N;
-            for (int k = threadIdx.x; k < Ku; k += NT) fsh[k] = F[k];
-            __syncthreads();
-            for (int j = threadIdx.x; j < N; j += NT) {
-                const int gj = br.cb + j;
-                Cx<T> x{0, 0}, zc{0, 0};
-                for (int k = 0; k < Ku; ++k) {
-                    Cx<T> f = fsh[k];
-                    cfma(x, f, Wf[(long long)k * E + gj]);
-                    cfmac(zc, f, Wc[(long long)k * E + gj]);
-                }
-                xs[j] = x;
-                zs[j] = zc;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < M; i += NT) {
-                Cx<T> s1{0, 0}, s2{0, 0};
-                for (int j = 0; j < N; ++j) {
-                    Cx<T> h = H[i + (long long)j * M];
-                    cfma(s1, h, xs[j]);
-                    cfma(s2, h, zs[j]);
-                }
-                T vx = s1.x + s2.x, vy = s1.y - s2.y;  // H x + conj(H zc)
-                if (ysm) {
-                    ysh[2 * i] += vx;
-                    ysh[2 * i + 1] += vy;
-                } else {
-                    atomicAdd(&y[br.rb + i].x, vx);
-                    atomicAdd(&y[br.rb + i].y, vy);
-                }
-            }
-            __syncthreads();
-            continue;
-        }
-        const Cx<T>* U = pool + c.off;
-        const Cx<T>* V = U + (long long)c.r * M;
-        const Cx<T>* F = U + (long long)c.r * (M + N);
-        for (int k = threadIdx.x; k < Ku; k += NT) fsh[k] = F[k];
-        for (int t = threadIdx.x; t < 2 * c.r; t += NT) ab[t] = Cx<T>{0, 0};
+        for (int i = tid; i < 2 * M; i += NT) ysh[i] = 0;
+    for (int g0 = 0; g0 < nc; g0 += PG) {
+        const int np = min(PG, nc - g0);
+        __syncthreads();  // the previous group's readers are done
+        if (tid < PG) crs[tid] = tid < np ? rec[(size_t)blk * Cmax + g0 + tid] : CrossRec{0, 0, 0, 0, 0};
         __syncthreads();
-        const int nj = (N + NT - 1) / NT * NT;
-        for (int j = threadIdx.x; j < nj; j += NT) {
-            Cx<T> x{0, 0}, zc{0, 0};
+        for (int e = tid; e < PG * Ku; e += NT) {
+            const int p = e / Ku, k = e - p * Ku;
+            Cx<T> v{0, 0};
+            if (p < np) {
+                const CrossRec c = crs[p];
+                v = pool[c.off + (c.r < 0 ? (long long)M * N : (long long)c.r * (M + N)) + k];
+            }
+            fg[e] = v;
+        }
+        for (int e = tid; e < PG * rmax * 2; e += NT) ab[e] = Cx<T>{0, 0};
+        __syncthreads();
+        for (int jt = 0; jt < N; jt += NT) {
+            const int j = jt + tid;
+            Cx<T> x[PG], z[PG];
+#pragma unroll
+            for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
             if (j < N) {
-                const int gj = br.cb + j;
+                const Cx<T>* wf = Wf + br.cb + j;
+                const Cx<T>* wc = Wc + br.cb + j;
                 for (int k = 0; k < Ku; ++k) {
-                    Cx<T> f = fsh[k];
-                    cfma(x, f, Wf[(long long)k * E + gj]);
-                    cfmac(zc, f, Wc[(long long)k * E + gj]);
+                    const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
+#pragma unroll
+                    for (int p = 0; p < PG; ++p) {
+                        const Cx<T> f = fg[p * Ku + k];
+                        cfma(x[p], f, a);
+                        cfmac(z[p], f, b);
+                    }
                 }
             }
-            for (int t = 0; t < c.r; ++t) {
-                Cx<T> v = j < N ? V[(long long)t * N + j] : Cx<T>{0, 0};
-                Cx<T> pa = cmulc(x, v), pb = cmulc(zc, v);  // conj(v) x, conj(v) zc
-                pa.x = warp_sum(pa.x);
-                pa.y = warp_sum(pa.y);
-                pb.x = warp_sum(pb.x);
-                pb.y = warp_sum(pb.y);
-                if (lane == 0) {
-                    atomicAdd(&ab[t].x, pa.x);
-                    atomicAdd(&ab[t].y, pa.y);
-                    atomicAdd(&ab[c.r + t].x, pb.x);
-                    atomicAdd(&ab[c.r + t].y, pb.y);
+#pragma unroll
+            for (int p = 0; p < PG; ++p) {
+                if (p < np) {
+                    const CrossRec c = crs[p];
+                    if (c.r < 0) {
+                        if (j < N) {
+                            xs[p * dense_n_max + j] = x[p];
+                            zs[p * dense_n_max + j] = z[p];
+                        }
+                    } else {
+                        const Cx<T>* V = pool + c.off + (long long)c.r * M;
+                        for (int t = 0; t < c.r; ++t) {
+                            const Cx<T> v = j < N ? V[(long long)t * N + j] : Cx<T>{0, 0};
+                            Cx<T> pa = cmulc(x[p], v), pb = cmulc(z[p], v);  // conj(v) x, conj(v) zc
+                            pa.x = warp_sum(pa.x);
+                            pa.y = warp_sum(pa.y);
+                            pb.x = warp_sum(pb.x);
+                            pb.y = warp_sum(pb.y);
+                            if (lane == 0) {
+                                Cx<T>* q = ab + (size_t)(p * rmax + t) * 2;
+                                atomicAdd(&q[0].x, pa.x);
+                                atomicAdd(&q[0].y, pa.y);
+                                atomicAdd(&q[1].x, pb.x);
+                                atomicAdd(&q[1].y, pb.y);
+                            }
+                        }
+                    }
                 }
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < M; i += NT) {
-            Cx<T> s1{0, 0}, s2{0, 0};
-            for (int t = 0; t < c.r; ++t) {
-                Cx<T> u = U[(long long)t * M + i];
-                cfma(s1, u, ab[t]);
-                cfma(s2, u, ab[c.r + t]);
+        for (int i = tid; i < M; i += NT) {
+            T vx = 0, vy = 0;
+            for (int p = 0; p < np; ++p) {
+                const CrossRec c = crs[p];
+                Cx<T> s1{0, 0}, s2{0, 0};
+                if (c.r < 0) {
+                    const Cx<T>* H = pool + c.off;
+                    for (int j = 0; j < N; ++j) {
+                        const Cx<T> h = H[i + (long long)j * M];
+                        cfma(s1, h, xs[p * dense_n_max + j]);
+                        cfma(s2, h, zs[p * dense_n_max + j]);
+                    }
+                } else {
+                    const Cx<T>* U = pool + c.off;
+                    const Cx<T>* q = ab + (size_t)p * rmax * 2;
+                    for (int t = 0; t < c.r; ++t) {
+                        const Cx<T> u = U[(long long)t * M + i];
+                        cfma(s1, u, q[2 * t]);
+                        cfma(s2, u, q[2 * t + 1]);
+                    }
+                }
+                vx += s1.x + s2.x;  // s1 + conj(s2)
+                vy += s1.y - s2.y;
             }
-            T vx = s1.x + s2.x, vy = s1.y - s2.y;  // U a + conj(U b)
             if (ysm) {
                 ysh[2 * i] += vx;
                 ysh[2 * i + 1] += vy;
@@ -214,10 +243,10 @@ __global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool
                 atomicAdd(&y[br.rb + i].y, vy);
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (ysm)
-        for (int i = threadIdx.x; i < M; i += NT) {
+        for (int i = tid; i < M; i += NT) {
             atomicAdd(&y[br.rb + i].x, ysh[2 * i]);
             atomicAdd(&y[br.rb + i].y, ysh[2 * i + 1]);
         }
@@ -241,6 +270,56 @@ static int dense_n_max(const g3_factors* fa) {
                 break;
             }
     return n;
+}
+
+// near-field launch: grid (row clusters) x (frequency chunks), at least
+// ~16 CTAs per SM so that the last wave is short
+template <class T>
+static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, int Ku, int E,
+                                   const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y) {
+    constexpr int NT = 256;
+    const int n_rows = (int)nf->row_start.size() - 1;
+    int ksplit = std::max(1, std::min(Ku, (16 * ctx->n_sm + n_rows - 1) / n_rows));
+    int kchunk = (Ku + ksplit - 1) / ksplit;
+    ksplit = (Ku + kchunk - 1) / kchunk;
+    int mrow = 0;
+    for (int g = 0; g < n_rows; ++g) {
+        const int32_t* r = &t->blocks[5 * (size_t)nf->order[nf->row_start[g]]];
+        mrow = std::max(mrow, r[1] - r[0]);
+    }
+    dim3 grid(n_rows, ksplit);
+    k_apply_near<T, NT><<<grid, NT, 2 * (size_t)mrow * sizeof(T), ctx->stream>>>(
+        nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(), nf->d_offs.as<long long>(), nf->d_row_start.as<int>(),
+        Ku, kchunk, E, Wf, Wc, y);
+    ctx->count("k_apply_near");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+// far-field launch over the n blocks in d_list (device), block ranges in d_ranges
+template <class T>
+static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, const int* d_list, int n,
+                                  const BlockRange* d_ranges, int Ku, int E, const Cx<T>* Wf, const Cx<T>* Wc,
+                                  Cx<T>* y) {
+    constexpr int NT = 128;
+    constexpr int PG = sizeof(T) == 4 ? 16 : 4;
+    const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
+    int mmax = 0;
+    for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
+    const int ym = std::min(mmax, ysmem_max);
+    const int dn = dense_n_max(fa);
+    const int rmax = std::max(1, (int)fa->stats.face_rank_max);
+    const size_t smem = ((size_t)PG * Ku + (size_t)PG * rmax * 2 + 2 * (size_t)PG * dn) * sizeof(Cx<T>) +
+                        2 * (size_t)ym * sizeof(T);
+    if (smem > ctx->smem_optin)
+        return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
+    G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_apply_far<T, NT, PG><<<n, NT, smem, ctx->stream>>>(fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                         fa->d_r3.as<int>(), d_ranges, d_list, fa->Cmax, Ku, E, Wf,
+                                                         Wc, y, ym, dn, rmax);
+    ctx->count("k_apply_far");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
 }
 
 template <class T>
@@ -268,25 +347,7 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
         G3_CUDA(cudaGetLastError());
     }
     G3_CUDA(cudaEventRecord(e1, ctx->stream));
-    if (nf && !nf->order.empty()) {
-        constexpr int NT = 256;
-        const int n_rows = (int)nf->row_start.size() - 1;
-        int ksplit = std::max(1, std::min(Ku, (8 * ctx->n_sm + n_rows - 1) / n_rows));
-        int kchunk = (Ku + ksplit - 1) / ksplit;
-        ksplit = (Ku + kchunk - 1) / kchunk;
-        int mrow = 0;
-        for (int g = 0; g < n_rows; ++g) {
-            const int32_t* r = &t->blocks[5 * (size_t)nf->order[nf->row_start[g]]];
-            mrow = std::max(mrow, r[1] - r[0]);
-        }
-        size_t smem = 2 * (size_t)mrow * sizeof(T);
-        dim3 grid(n_rows, ksplit);
-        k_apply_near<T, NT><<<grid, NT, smem, ctx->stream>>>(nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(),
-                                                             nf->d_offs.as<long long>(), nf->d_row_start.as<int>(), Ku,
-                                                             kchunk, E, Wf, Wc, y);
-        ctx->count("k_apply_near");
-        G3_CUDA(cudaGetLastError());
-    }
+    if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
     G3_CUDA(cudaEventRecord(e2, ctx->stream));
     if (fa && fa->n_far > 0) {
         std::vector<int> list;
@@ -299,19 +360,8 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
             G3_CUDA(cudaMemcpyAsync(d_list.p, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
             G3_CUDA(cudaMemcpyAsync(d_ranges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
                                     cudaMemcpyHostToDevice, ctx->stream));
-            constexpr int NT = 128;
-            const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
-            int mmax = 0;
-            for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
-            const int ym = std::min(mmax, ysmem_max);
-            const int dn = dense_n_max(fa);
-            size_t smem = (Ku + 128 + 2 * (size_t)dn) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
-            G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_apply_far<T, NT><<<(int)list.size(), NT, smem, ctx->stream>>>(
-                fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges.as<BlockRange>(),
-                d_list.as<int>(), fa->Cmax, Ku, E, Wf, Wc, y, ym, dn);
-            ctx->count("k_apply_far");
-            G3_CUDA(cudaGetLastError());
+            G3_TRY_NA(launch_apply_far<T>(ctx, fa, d_list.as<int>(), (int)list.size(), d_ranges.as<BlockRange>(), Ku,
+                                          E, Wf, Wc, y));
             G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
         }
     }
@@ -418,24 +468,7 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         ctx->count("k_apply_prep");
         G3_CUDA(cudaGetLastError());
     }
-    if (nf && !nf->order.empty()) {
-        constexpr int NT = 256;
-        const int n_rows = (int)nf->row_start.size() - 1;
-        int ksplit = std::max(1, std::min(Ku, (8 * ctx->n_sm + n_rows - 1) / n_rows));
-        int kchunk = (Ku + ksplit - 1) / ksplit;
-        ksplit = (Ku + kchunk - 1) / kchunk;
-        int mrow = 0;
-        for (int g = 0; g < n_rows; ++g) {
-            const int32_t* r = &t->blocks[5 * (size_t)nf->order[nf->row_start[g]]];
-            mrow = std::max(mrow, r[1] - r[0]);
-        }
-        dim3 grid(n_rows, ksplit);
-        k_apply_near<T, NT><<<grid, NT, 2 * (size_t)mrow * sizeof(T), ctx->stream>>>(
-            nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(), nf->d_offs.as<long long>(),
-            nf->d_row_start.as<int>(), Ku, kchunk, E, Wf, Wc, y);
-        ctx->count("k_apply_near");
-        G3_CUDA(cudaGetLastError());
-    }
+    if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
     if (n_far > 0) {
         // every admissible block (blocks of rank 0 add nothing); the block
         // ranges come from the factors' host copy, the ranks from the device
@@ -443,19 +476,7 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
                                 ctx->stream));
         k_iota<<<(n_far + 255) / 256, 256, 0, ctx->stream>>>(list, n_far);
         ctx->count("k_iota");
-        constexpr int NT = 128;
-        const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
-        int mmax = 0;
-        for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
-        const int ym = std::min(mmax, ysmem_max);
-        const int dn = dense_n_max(fa);
-        size_t smem = (Ku + 128 + 2 * (size_t)dn) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
-        G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_apply_far<T, NT><<<n_far, NT, smem, ctx->stream>>>(fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
-                                                              fa->d_r3.as<int>(), ranges, list, fa->Cmax, Ku, E, Wf,
-                                                              Wc, y, ym, dn);
-        ctx->count("k_apply_far");
-        G3_CUDA(cudaGetLastError());
+        G3_TRY_NA(launch_apply_far<T>(ctx, fa, list, n_far, ranges, Ku, E, Wf, Wc, y));
     }
     {
         int blocks = (E + 255) / 256;

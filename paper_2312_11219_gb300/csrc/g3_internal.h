@@ -123,6 +123,7 @@ struct g3_ctx {
     cudaEvent_t ev[6] = {};
     double last_apply_ms = 0, last_near_ms = 0;
     double pool_scale = 1.0;  // factor-pool size / estimate needed by earlier compressions
+    double pool_scale_mlp = 1.0;  // the same for the predictor-based estimate
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
     void count(const char* name, int64_t n = 1) {
         launches[name] += n;
@@ -161,7 +162,6 @@ struct g3_tree {
     g3::DevBuf d_geom_f, d_geom_d; // packed SoA arrays
     g3::GeomF gf{};
     g3::GeomD gd{};
-    g3::DevBuf d_far;              // BlockRange [n_far]
 };
 
 struct g3_near {
@@ -192,13 +192,23 @@ struct g3_factors {
     long long pool_cap = 0;            // elements
     g3::DevBuf d_rec;                  // CrossRec [n_far][Cmax]
     g3::DevBuf d_r3;                   // int [n_far]
-    g3::DevBuf d_cycles;               // long long [n_far]
-    std::vector<long long> cycles;     // host copy of the per-block cycle counts
+    g3::DevBuf d_cycles;               // long long [n_far][8]
+    std::vector<long long> cycles;     // per-block cycle totals
+    std::vector<long long> phases;     // [n_far][8]: cycles per phase, then face ACA steps
     std::vector<int32_t> r3;
     std::vector<g3::CrossRec> rec;     // host copy
     std::vector<g3::BlockRange> ranges;
     g3_stats stats{};
     const g3_freqs* freqs = nullptr;
+};
+
+struct g3_mlp {
+    g3_ctx* ctx = nullptr;
+    g3::DevBuf d_params, d_m, d_v;     // float [G3_MLP_NP]: master weights, Adam moments
+    g3::DevBuf d_t;                    // long long: Adam steps taken
+    g3::DevBuf d_mean, d_inv_std;      // float [G3_MLP_NF]
+    long long t = 0;                   // host copy of the step count
+    float mean[G3_MLP_NF] = {}, inv_std[G3_MLP_NF] = {};
 };
 
 namespace g3 {
@@ -211,6 +221,14 @@ g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int k
                          const int* d_rows, const int* d_cols, int n, const int* d_ku, const int* d_conj, int nk,
                          double* d_out);
 g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf, int kernel, int scheme);
+g3_status mlp_forward_dev(g3_ctx* ctx, const g3_mlp* net, const float* d_x, long long n, float* d_out);
+g3_status mlp_features_dev(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int kernel, double eps3, float* d_out);
+g3_status mlp_labels_dev(g3_ctx* ctx, const g3_factors* fa, const BlockRange* d_ranges, float* d_out);
+g3_status mlp_grad_dev(g3_ctx* ctx, const g3_mlp* net, const float* d_x, const float* d_y, long long n,
+                       float* d_grad, float* d_loss);
+g3_status mlp_fit_dev(g3_ctx* ctx, g3_mlp* net, const float* d_x, const float* d_y, long long n, int epochs,
+                      int batch, double lr, double b1, double b2, double eps, int use_graph, float* d_loss);
+void mlp_init_params(uint64_t seed, float* P);
 g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel, int scheme,
                   double eps3, const g3_opts& o, const void* sep_a, const void* sep_b, const void* sep_c, int sep_R);
 g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
