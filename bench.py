@@ -118,7 +118,7 @@ def _oracle_setup(name: str):
         from oracle import freqs as O_freqs, quadrature as O_q, tree as O_tree
         w = workloads.get(name)
         geo = O_q.Geometry(w.verts, w.tris)
-        T = O_tree.build(w.verts, w.tris, w.leaf, w.eta)
+        T = O_tree.build(w.verts, w.tris, w.leaf, w.eta, w.max_block)
         fs = O_freqs.frequency_set(w.freq)
         _ORACLE_CACHE[name] = (w, geo, T, fs)
     return _ORACLE_CACHE[name]
@@ -229,7 +229,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     keep = {}
 
     def step(host: bool):
-        T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+        T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
         F = g3.freqs_from_spec(ctx, w.freq)
         rec = {"entries_aca": 0, "entries_near": 0, "aca_ms": 0.0, "near_ms": 0.0, "apply_ms": 0.0,
                "apply_near_ms": 0.0, "apply_bytes": 0, "apply_near_bytes": 0, "factor_bytes": 0,

@@ -104,7 +104,8 @@ typedef struct {
     int face_rank_max;    /* cap of a face ACA's rank (0 = 48; max 64)                     */
     int unbatched;        /* 1 = one block per launch sequence, host loop (plain baseline) */
     int ctas_per_sm;      /* persistent CTAs per SM (0 = from the occupancy calculator)    */
-    int threads;          /* threads per CTA: 128 or 256 (0 = 256)                         */
+    int threads;          /* threads per CTA of the low-rank-face launch: 256 or 512
+                             (512: G3_MIXED only); 0 = 256                               */
     int no_recompress;    /* 1 = keep raw ACA faces (no QR+SVD)                            */
     int order_by_cost;    /* 1 (default when 0 is given: 1) = longest-first queue order    */
     const int32_t* k1;    /* optional host array [n_far]: first frequency per block
@@ -225,6 +226,13 @@ g3_status g3_freqs_free(g3_freqs* f);
  * bit-identical on every machine.  Degenerate triangles -> G3_EINVAL. */
 g3_status build_cluster_tree(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne,
                              int leaf, double eta, g3_tree** out);
+/* The same with a cap on far blocks (no counterpart in the paper; it bounds
+ * the work of the largest block, the tail of the batched compression): an
+ * admissible pair whose larger cluster has more than max_block elements is
+ * split like an inadmissible pair unless both are leaves (children of an
+ * admissible pair are admissible).  max_block = 0: no cap (build_cluster_tree). */
+g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne,
+                                    int leaf, double eta, int max_block, g3_tree** out);
 g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near);
 /* Copy to host (any output may be NULL):
  *   perm [ne]            cluster position -> original element index
@@ -277,6 +285,18 @@ g3_status g3_near_free(g3_near* nf);
  * kernel: G3_SLP or G3_DLP.  eps3 in (0, 1). */
 g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
                         g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out);
+
+/* Algorithm 1 on every admissible block of n_geom meshes in ONE persistent
+ * launch (blocks of all meshes share one longest-first queue and one factor
+ * pool).  trees[j], freqs[j]: mesh j and its frequency set (K may differ per
+ * mesh).  out [n_geom]: one factors handle per mesh, each usable with
+ * apply_gcq on trees[j] and freed separately (the pool is freed with the
+ * last).  Times and counters in each handle's stats are those of the whole
+ * batch; ranks, bytes and per-block data are the mesh's own.  opts->k1,
+ * opts->cost and opts->unbatched are not accepted. */
+g3_status aca3_compress_batch(g3_ctx* ctx, const g3_tree* const* trees, const g3_freqs* const* freqs, int n_geom,
+                              g3_kernel kernel, g3_scheme scheme, g3_precision prec, double eps3, const g3_opts* opts,
+                              g3_factors** out);
 
 /* Same algorithm on ONE synthetic block A[i,j,k] = sum_{t<R} a[t,i] b[t,j] c[t,k]
  * (host arrays a [R*M], b [R*N], c [R*Ku], c128, row t contiguous).  Used to

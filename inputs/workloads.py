@@ -19,7 +19,9 @@ Workloads (all synthetic; the paper's meshes and load data are not used):
                   layer, the gCQ set of ``sphere20480``.
 
 Small variants (``cube48``, ``cube192``, ``lshape768``, ``sphere1280``...) serve
-the tests.
+the tests.  The large workloads cap far blocks at 192 elements per side
+(``max_block``; a scheduling choice that bounds the longest block of the
+persistent launch, not part of the paper's partition).
 """
 from __future__ import annotations
 
@@ -56,6 +58,7 @@ class Workload:
     scheme: str = "colloc7"
     leaf: int = 32
     eta: float = 1.0
+    max_block: int = 0           # cap of the larger side of a far block (0 = the plain partition)
     eps3: float = 1e-4
     density_seed: int = 1
     extra: dict = field(default_factory=dict)
@@ -106,13 +109,13 @@ def get(name: str) -> Workload:
         return Workload(name, v, t, bdf2_spec(32, 0.1), density_seed=1)
     if name == "lshape12288":
         v, t = meshes.lshape(32)
-        return Workload(name, v, t, bdf2_spec(128, 0.02), kernels=("slp", "dlp"), density_seed=2)
+        return Workload(name, v, t, bdf2_spec(128, 0.02), kernels=("slp", "dlp"), density_seed=2, max_block=192)
     if name == "sphere20480":
         v, t = meshes.icosphere(5)
-        return Workload(name, v, t, _gcq_sphere_spec(), scheme="galerkin4x4", density_seed=3)
+        return Workload(name, v, t, _gcq_sphere_spec(), scheme="galerkin4x4", density_seed=3, max_block=192)
     if name == "sphere81920":
         v, t = meshes.icosphere(6)
-        return Workload(name, v, t, _gcq_sphere_spec(), density_seed=5)
+        return Workload(name, v, t, _gcq_sphere_spec(), density_seed=5, max_block=192)
     # small variants for tests
     if name == "cube48":
         v, t = meshes.cube(2)
@@ -154,7 +157,7 @@ def batch64(seed: int = 4, n_geom: int = 64) -> list[Workload]:
         v = meshes.transformed(v, rot, scale, shift)
         K = int(rng.choice([32, 64, 128, 256]))
         h = mean_edge(v, t)
-        out.append(Workload(f"batch64[{g}]", v, t, bdf2_spec(K, 0.7 * h), density_seed=1000 + g))
+        out.append(Workload(f"batch64[{g}]", v, t, bdf2_spec(K, 0.7 * h), density_seed=1000 + g, max_block=192))
     return out
 
 
@@ -168,7 +171,7 @@ def describe(w: Workload) -> dict:
     f = w.freq
     d = {"workload": w.name, "triangles": w.E, "K": f.K, "freqs": f.kind,
          "kernels": list(w.kernels), "scheme": w.scheme, "leaf": w.leaf,
-         "eta": w.eta, "eps3": w.eps3}
+         "eta": w.eta, "max_block": w.max_block, "eps3": w.eps3}
     if f.kind == "bdf2":
         d.update(dt=f.dt, lam=f.lam)
     else:

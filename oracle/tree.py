@@ -24,6 +24,9 @@ bit for bit:
   -> near block; both inner -> the four child pairs (LL, LR, RL, RR);
   otherwise only the inner cluster is split (left child first).
   Blocks are listed in this depth-first order.
+* Optional cap max_block > 0 (not in the paper; it bounds the work of one
+  block): an admissible pair whose larger cluster has more than max_block
+  elements is split like an inadmissible pair, unless both are leaves.
 
 Output blocks are given as cluster-order index ranges
 (row_begin, row_end, col_begin, col_end, admissible).
@@ -75,7 +78,7 @@ def admissible(lo_t, hi_t, lo_s, hi_s, eta: float) -> bool:
     return min(_diam2(lo_t, hi_t), _diam2(lo_s, hi_s)) <= eta * eta * d2 and d2 > 0.0
 
 
-def build(verts: np.ndarray, tris: np.ndarray, leaf: int = 32, eta: float = 1.0) -> Tree:
+def build(verts: np.ndarray, tris: np.ndarray, leaf: int = 32, eta: float = 1.0, max_block: int = 0) -> Tree:
     verts = np.asarray(verts, dtype=np.float64)
     tris = np.asarray(tris, dtype=np.int64)
     v0, v1, v2 = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
@@ -120,13 +123,16 @@ def build(verts: np.ndarray, tris: np.ndarray, leaf: int = 32, eta: float = 1.0)
     blocks: list[tuple[int, int, int, int, int]] = []
 
     def part(t: int, s: int) -> None:
-        if admissible(lo[t], hi[t], lo[s], hi[s], eta):
-            blocks.append((begin[t], end[t], begin[s], end[s], 1))
-            return
         tl, sl = left[t] < 0, left[s] < 0
-        if tl and sl:
+        if admissible(lo[t], hi[t], lo[s], hi[s], eta):
+            big = max(end[t] - begin[t], end[s] - begin[s])
+            if max_block <= 0 or big <= max_block or (tl and sl):
+                blocks.append((begin[t], end[t], begin[s], end[s], 1))
+                return
+        elif tl and sl:
             blocks.append((begin[t], end[t], begin[s], end[s], 0))
-        elif not tl and not sl:
+            return
+        if not tl and not sl:
             part(left[t], left[s])
             part(left[t], right[s])
             part(right[t], left[s])

@@ -83,6 +83,7 @@ _sig("g3_freqs_info", _ci, _p, C.POINTER(_ci), C.POINTER(_ci))
 _sig("g3_freqs_get", _ci, _p, _dp, _dp, _i32p, _i32p)
 _sig("g3_freqs_free", _ci, _p)
 _sig("build_cluster_tree", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _pp)
+_sig("build_cluster_tree_capped", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _ci, _pp)
 _sig("g3_tree_info", _ci, _p, *(C.POINTER(_ci),) * 5)
 _sig("g3_tree_get", _ci, _p, _i32p, _i32p, _dp, _i32p, _i32p)
 _sig("g3_tree_free", _ci, _p)
@@ -92,6 +93,7 @@ _sig("g3_near_info", _ci, _p, _i64p, _i64p, _dp)
 _sig("g3_near_get_block", _ci, _p, _ci, _dp)
 _sig("g3_near_free", _ci, _p)
 _sig("aca3_compress", _ci, _p, _p, _p, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _pp)
+_sig("aca3_compress_batch", _ci, _p, _p, _p, _ci, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _p)
 _sig("aca3_compress_separable", _ci, _p, _dp, _dp, _dp, _ci, _ci, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _pp)
 _sig("g3_factors_stats", _ci, _p, C.POINTER(Stats))
 _sig("g3_factors_ranks", _ci, _p, _i32p)
@@ -116,8 +118,8 @@ _sig("g3_factors_labels", _ci, _p, _p, _fp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
-            "build_cluster_tree", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
-            "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_separable",
+            "build_cluster_tree", "build_cluster_tree_capped", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
+            "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
             "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
             "g3_mlp_grad", "g3_mlp_predict", "g3_mlp_get", "g3_mlp_free", "g3_block_features", "g3_factors_labels"]
@@ -264,12 +266,14 @@ class Tree(_Handle):
         return {"perm": perm, "nodes": nodes, "boxes": boxes, "blocks": blocks, "far_index": far}
 
 
-def build_cluster_tree(ctx: Context, verts, tris, leaf: int = 32, eta: float = 1.0) -> Tree:
+def build_cluster_tree(ctx: Context, verts, tris, leaf: int = 32, eta: float = 1.0, max_block: int = 0) -> Tree:
+    """Cluster tree and block partition; max_block > 0 caps the larger side of
+    a far block (build_cluster_tree_capped)."""
     v = _arr(verts, np.float64)
     t = _arr(tris, np.int32)
     h = C.c_void_p()
-    _check(_lib.build_cluster_tree(ctx.h, _ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0], leaf,
-                                   eta, C.byref(h)), "build_cluster_tree")
+    _check(_lib.build_cluster_tree_capped(ctx.h, _ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0],
+                                          leaf, eta, max_block, C.byref(h)), "build_cluster_tree")
     return Tree(h, (ctx,))
 
 
@@ -486,6 +490,22 @@ def aca3_compress(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", s
     _check(_lib.aca3_compress(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec], eps3,
                               C.byref(o), C.byref(h)), "aca3_compress")
     return Factors(h, (ctx, tree, freqs))
+
+
+def aca3_compress_batch(ctx: Context, trees, freqs, kernel: str = "slp", scheme: str = "colloc7",
+                        prec: str = "mixed", eps3: float = 1e-4, **opts) -> list:
+    """All admissible blocks of several meshes in one persistent launch;
+    returns one Factors per mesh."""
+    n = len(trees)
+    if len(freqs) != n or n == 0:
+        raise ValueError("need one frequency set per tree")
+    th = (C.c_void_p * n)(*[t.h for t in trees])
+    fh = (C.c_void_p * n)(*[f.h for f in freqs])
+    out = (C.c_void_p * n)()
+    o = _opts(**opts)
+    _check(_lib.aca3_compress_batch(ctx.h, th, fh, n, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec], eps3,
+                                    C.byref(o), out), "aca3_compress_batch")
+    return [Factors(C.c_void_p(out[j]), (ctx, trees[j], freqs[j])) for j in range(n)]
 
 
 def aca3_compress_separable(ctx: Context, a, b, c, prec: str = "fp64", eps3: float = 1e-6, **opts) -> Factors:

@@ -22,7 +22,8 @@ LIB = os.path.join(LIBDIR, "libg3aca.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_apply.cu", "g3_api.cu", "g3_probe.cu", "g3_mlp.cu"]
+CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_aca_sep.cu", "g3_apply.cu", "g3_api.cu",
+              "g3_probe.cu", "g3_mlp.cu"]
 CPP_SOURCES = ["g3_tree.cpp"]
 
 
@@ -66,7 +67,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
         objs.append(o)
         jobs.append([cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off",
                      "-I", os.path.join(CUDA_HOME, "include"), *inc, "-c", os.path.join(CSRC, f), "-o", o])
-    with ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 8))) as ex:
         results = list(ex.map(_run, jobs))
     for cmd, rc, out in results:
         if verbose or rc != 0 or ptxas_info:

@@ -1,0 +1,1670 @@
+#pragma once
+// Three-way (generalised) ACA of every admissible block (Algorithm 1) in one
+// persistent launch.
+//
+// Each CTA claims blocks from an atomic queue counter (longest first) and runs
+// Algorithm 1 on the block restricted to the unique frequencies:
+//   face    partial-pivot ACA of the residual face at k_l (eps_face), with the
+//           residual of earlier crosses subtracted row/column-wise;
+//   recomp  Cholesky-QR of both ACA factors (float64, column-scaled Gram
+//           matrices), one-sided Jacobi SVD of the r x r core R_U R_V^H,
+//           truncation sigma_i < eps_face sigma_1 (Section 4, first remark);
+//   pivot   argmax |H_l[i, j]| over the dense expansion of U' V'^H, tiled
+//           through shared memory, ties to the smallest row-major index
+//           (Section 4, last remark);
+//   fiber   f_l[k] = (ENTRY(i_l, j_l, k) - sum_p H_p[i_l, j_l] f_p[k]) / H_l[i_l, j_l]
+//           with the residual in float64;
+//   norm    eq. (norm): ||C^(l)||^2 += 2 Re sum_d <H_l, H_d><f_l, f_d> + ||H_l||^2 ||f_l||^2,
+//           face inner products through Gram products (U_d^H U_l)(V_l^H V_d);
+//   stop    ||H_l|| ||f_l|| <= eps3 ||C^(l)|| -> rank l - 1; all frequencies
+//           used -> rank l; else k_{l+1} = argmax over unused k of |f_l[k]|.
+// Zero faces: up to three more frequencies are tested (last unique, middle,
+// largest |s|) before a block is declared zero (Section 5.1 on DLP zero blocks).
+//
+// Precision: T = float (mixed) evaluates entries and face arithmetic in
+// float32 and stores complex64 factors; T = double does everything in float64.
+// Recompression, fiber residuals and norms are float64 in both.
+//
+// No CTA waits on another: the only inter-CTA communication is the atomic
+// queue counter and the atomic pool allocator.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <numeric>
+#include <vector>
+
+#include "g3_device.cuh"
+
+namespace g3 {
+
+constexpr int KU_MAX = 256;   // largest unique-frequency count
+constexpr int SAMPLES = 32;   // sample entries of the convergence checks
+constexpr int NPH = 10;       // per-block diagnostics: 7 phases, steps, start, end
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr int RF_MAX = 64;    // largest face rank cap
+
+// geometry and frequencies of one mesh of a batched compression
+struct GeoDesc {
+    GeomF gf;
+    GeomD gd;
+    const double2* sd;
+    const float2* sf;
+    int Ku, k_maxabs;
+};
+
+template <class T>
+struct AcaArgs {
+    const GeoDesc* geos;     // batched compression: per-mesh data (null: gf ... k_maxabs below)
+    const int* bgeo;         // [n_far] mesh of each block
+    GeomF gf;
+    GeomD gd;
+    SepView<T> sep;
+    const double2* sd;
+    const float2* sf;        // the unique frequencies rounded once to float32
+    int Ku, k_maxabs;
+    const BlockRange* ranges;
+    int n_far;
+    const int* queue;
+    int* queue_head;
+    int single;              // >= 0: CTA 0 processes queue[single] only
+    const int* k1;           // [n_far] first frequency per block, or null
+    int Cmax, RF;
+    int dense_max;           // blocks with M N <= dense_max use exact dense faces
+    int sample_check;        // confirm each stop on fixed sample entries
+    double eps3, eps_face;
+    double face_floor;       // absolute floor factor of the face tests (0 = none)
+    double trunc_floor;      // absolute floor factor of the recompression truncation (0 = none)
+    int no_recompress;
+    Cx<T>* pool;
+    long long pool_cap;
+    unsigned long long* pool_ctr;
+    int* spill;              // [n_far] blocks that found the pool full
+    int* spill_n;
+    int spill_cap;
+    CrossRec* rec;
+    int* r3;
+    long long* blk_cycles;   // [n_far][NPH] SM cycles per phase spent on each block, its face ACA
+                             // steps, and its start and end time (global timer, ns)
+    unsigned long long* counters;  // [0] entries [1] crosses computed [2] zero blocks [3] capped faces
+                                   // [8..14] clock cycles per phase (thread 0 of each CTA)
+    unsigned* status;
+    char* ws;
+    size_t ws_stride;
+    int Mmax, Nmax;
+};
+
+template <class T>
+struct Ws {
+    Cx<T>* uw;            // [RF][Mmax]
+    Cx<T>* vw;            // [RF][Nmax]
+    Cx<T>* row;           // [Nmax]
+    unsigned char* used;  // [Mmax]
+    Cx<T>* pre;           // [Cmax * RF]
+    Cx<double>* RU;       // [RF][RF]
+    Cx<double>* RV;
+    Cx<double>* TU;
+    Cx<double>* TV;
+    Cx<double>* fib;      // [Ku]
+    long long* colU;      // [Cmax * RF] flattened column tables (when they exceed shared memory)
+    long long* colV;
+    short* colP;
+    Cx<double>* hs;       // [SAMPLES][Cmax] H_p at the stop-check samples
+    double* rk;           // [Ku] sampled residual per frequency
+};
+
+static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <class T>
+__host__ __device__ inline size_t ws_bytes(int RF, int Mmax, int Nmax, int Cmax, int Ku) {
+    size_t b = 0;
+    auto add = [&](size_t n) { b += (n + 255) & ~size_t(255); };
+    add((size_t)RF * Mmax * sizeof(Cx<T>));
+    add((size_t)RF * Nmax * sizeof(Cx<T>));
+    add((size_t)Nmax * sizeof(Cx<T>));
+    add((size_t)Mmax);
+    add((size_t)(Cmax + 1) * RF * sizeof(Cx<T>));
+    for (int i = 0; i < 4; ++i) add((size_t)RF * RF * sizeof(Cx<double>));
+    add((size_t)Ku * sizeof(Cx<double>));
+    add((size_t)Cmax * RF * sizeof(long long));
+    add((size_t)Cmax * RF * sizeof(long long));
+    add((size_t)Cmax * RF * sizeof(short));
+    add((size_t)32 * Cmax * sizeof(Cx<double>));
+    add((size_t)Ku * sizeof(double));
+    return b;
+}
+
+template <class T>
+__device__ inline Ws<T> ws_carve(char* base, int RF, int Mmax, int Nmax, int Cmax, int Ku) {
+    Ws<T> w;
+    size_t o = 0;
+    auto take = [&](size_t n) {
+        char* p = base + o;
+        o += (n + 255) & ~size_t(255);
+        return p;
+    };
+    w.uw = (Cx<T>*)take((size_t)RF * Mmax * sizeof(Cx<T>));
+    w.vw = (Cx<T>*)take((size_t)RF * Nmax * sizeof(Cx<T>));
+    w.row = (Cx<T>*)take((size_t)Nmax * sizeof(Cx<T>));
+    w.used = (unsigned char*)take((size_t)Mmax);
+    w.pre = (Cx<T>*)take((size_t)(Cmax + 1) * RF * sizeof(Cx<T>));
+    w.RU = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
+    w.RV = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
+    w.TU = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
+    w.TV = (Cx<double>*)take((size_t)RF * RF * sizeof(Cx<double>));
+    w.fib = (Cx<double>*)take((size_t)Ku * sizeof(Cx<double>));
+    w.colU = (long long*)take((size_t)Cmax * RF * sizeof(long long));
+    w.colV = (long long*)take((size_t)Cmax * RF * sizeof(long long));
+    w.colP = (short*)take((size_t)Cmax * RF * sizeof(short));
+    w.hs = (Cx<double>*)take((size_t)32 * Cmax * sizeof(Cx<double>));
+    w.rk = (double*)take((size_t)Ku * sizeof(double));
+    return w;
+}
+
+// shared state of the block being processed
+template <class T>
+struct BlockSh {
+    int M, N, rb, cb, blk;
+    int ncross;
+    int k;
+    unsigned used_k[KU_MAX / 32];
+    long long off[KU_MAX];
+    int r[KU_MAX];
+    int pre[KU_MAX + 1];
+    Cx<T> fk[KU_MAX];
+    Cx<double> hp[KU_MAX];   // H_p[i_l, j_l]
+    Cx<double> ff[KU_MAX];   // <f_l, f_d>
+    Cx<double> hh[KU_MAX];   // <H_l, H_d>
+    Cx<double> gu[RF_MAX + 1];
+    Cx<double> gv[RF_MAX + 1];
+    double sig[RF_MAX];
+    double dU[RF_MAX], dV[RF_MAX];
+    int sel[RF_MAX];
+    ArgMaxT<T> am[32];
+    double red[64];
+    double norm2;
+    double red2[2];          // sampled residual / data norms of the stop check
+    double samp[SAMPLES];    // |residual|^2 of the face approximant at the samples
+    int stop;
+    double hself;            // ||H_l||^2
+    double fself;            // ||f_l||^2
+    Cx<double> hpiv;
+    long long new_off;
+    long long entries;
+    int raw;              // face ACA steps of the block (ranks before recompression)
+    int flag;
+    int rot;
+    int rnew;
+    int ip, jp;
+};
+
+template <int NT, class V>
+__device__ __forceinline__ ArgMaxT<V> block_argmax(ArgMaxT<V> a, ArgMaxT<V>* sh) {
+    a = warp_argmax(a);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        ArgMaxT<V> b = (l < NT / 32) ? sh[l] : amax_none<V>();
+        b = warp_argmax(b);
+        if (l == 0) sh[0] = b;
+    }
+    __syncthreads();
+    ArgMaxT<V> r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__device__ __forceinline__ T tiny_norm2();
+template <>
+__device__ __forceinline__ float tiny_norm2<float>() { return 1.1754944e-38f; }
+template <>
+__device__ __forceinline__ double tiny_norm2<double>() { return 2.2250738585072014e-308; }
+
+// ---- entry access ----------------------------------------------------------------
+template <int KER, class T>
+__device__ __forceinline__ Cx<T> ent(const AcaArgs<T>& A, int gi, int gj, int k) {
+    if constexpr (KER == G3_SEPARABLE) {
+        Cx<T> acc{0, 0};
+        for (int t = 0; t < A.sep.R; ++t) {
+            Cx<T> a{A.sep.a[2 * ((size_t)t * A.sep.M + gi)], A.sep.a[2 * ((size_t)t * A.sep.M + gi) + 1]};
+            Cx<T> b{A.sep.b[2 * ((size_t)t * A.sep.N + gj)], A.sep.b[2 * ((size_t)t * A.sep.N + gj) + 1]};
+            Cx<T> c{A.sep.c[2 * ((size_t)t * A.sep.Ku + k)], A.sep.c[2 * ((size_t)t * A.sep.Ku + k) + 1]};
+            cfma(acc, cmul(a, b), c);
+        }
+        return acc;
+    } else {
+        if constexpr (sizeof(T) == 4) {
+            const float2 s = A.sf[k];
+            return colloc_entry<KER, T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        } else {
+            const double2 s = A.sd[k];
+            return colloc_entry<KER, T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        }
+    }
+}
+
+// pool views of cross p
+template <class T>
+__device__ __forceinline__ const Cx<T>* Up(const AcaArgs<T>& A, const BlockSh<T>& S, int p) {
+    return A.pool + S.off[p];
+}
+template <class T>
+__device__ __forceinline__ const Cx<T>* Vp(const AcaArgs<T>& A, const BlockSh<T>& S, int p) {
+    return A.pool + S.off[p] + (long long)S.r[p] * S.M;
+}
+template <class T>
+__device__ __forceinline__ const Cx<T>* Fp(const AcaArgs<T>& A, const BlockSh<T>& S, int p) {
+    return A.pool + S.off[p] + (long long)S.r[p] * (S.M + S.N);
+}
+
+// ---- one quadrature point of a collocation entry --------------------------------------
+template <int KER, class G, class T>
+__device__ __forceinline__ Cx<T> colloc_q(const G& g, int i, int j, int q, T sre, T sim) {
+    T d[3];
+    cdiff(g, i, j, d);
+    T rx = d[0] - qoff(g, q, 0, j), ry = d[1] - qoff(g, q, 1, j), rz = d[2] - qoff(g, q, 2, j);
+    T r2 = rx * rx + ry * ry + rz * rz;
+    T ri = krsqrt(r2);
+    T r = r2 * ri;
+    T wq = qwt(g, q, j) * (T)G3_INV4PI;
+    T amp;
+    if (KER == G3_DLP) {
+        T pd = d[0] * nrm(g, 0, j) + d[1] * nrm(g, 1, j) + d[2] * nrm(g, 2, j);
+        amp = wq * pd * ri * ri * ri;
+    } else {
+        amp = wq * ri;
+    }
+    T m = amp * kexp(-sre * r);
+    T sn, cs;
+    ksincos(sim * r, &sn, &cs);
+    if (KER == G3_DLP) {
+        T fr = (T)1 + sre * r, fi = sim * r;
+        return {m * (fr * cs + fi * sn), m * (fi * cs - fr * sn)};
+    }
+    return {m * cs, -m * sn};
+}
+
+// part `part` of a gang of G threads evaluating ENTRY(gi, gj, k): with G >= 8
+// each of the first 7 parts evaluates one quadrature point; otherwise part 0
+// evaluates the whole entry.  The gang sum is the entry.
+template <int KER, class T>
+__device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, int k, int part, int G) {
+    if constexpr (KER == G3_SEPARABLE) {
+        return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
+    } else {
+        if (G >= 8) {
+            if (part >= 7) return Cx<T>{0, 0};
+            if constexpr (sizeof(T) == 4) {
+                const float2 s = A.sf[k];
+                return colloc_q<KER>(A.gf, gi, gj, part, s.x, s.y);
+            } else {
+                const double2 s = A.sd[k];
+                return colloc_q<KER>(A.gd, gi, gj, part, s.x, s.y);
+            }
+        }
+        return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
+    }
+}
+
+template <class T>
+__device__ __forceinline__ Cx<T> shfl_xor_c(Cx<T> v, int o) {
+    return Cx<T>{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
+
+// gang size: the largest power of two <= 32 with L * G <= 2 NT
+template <int NT>
+__device__ __forceinline__ int gang_size(int L) {
+    int G = 1;
+    while (G < 32 && L * (G * 2) <= 2 * NT) G *= 2;
+    return G;
+}
+
+// Per-face tables of the earlier crosses' columns, flattened over (p, t):
+//   colU[c] / colV[c]  pool offsets of U_p[:, t] / V_p[:, t],  colP[c] = p,
+// and the coefficient vector of the line being evaluated (coef[c], then the
+// current face's m coefficients).  In shared memory when they fit, else in
+// the workspace.
+constexpr int TABMAX = 1024;    // flattened columns kept in shared memory
+constexpr int ROWMAX = 1024;    // row buffer length kept in shared memory
+
+template <class T>
+struct FaceTab {
+    const long long* colU;
+    const long long* colV;
+    const short* colP;
+    Cx<T>* coef;
+    Cx<T>* row;
+    int ncol;   // sum of the earlier crosses' ranks
+};
+
+template <class T>
+__device__ __forceinline__ size_t facetab_smem_bytes() {
+    return 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) + (TABMAX + RF_MAX) * sizeof(Cx<T>) +
+           ROWMAX * sizeof(Cx<T>) + 64;
+}
+
+template <class T, int NT>
+__device__ FaceTab<T> facetab_build(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, unsigned char* arena) {
+    FaceTab<T> F;
+    const int nc = S.ncross;
+    F.ncol = S.pre[nc];
+    const bool sm = F.ncol <= TABMAX;
+    unsigned char* p = arena;
+    long long* cu = sm ? reinterpret_cast<long long*>(p) : w.colU;
+    p += TABMAX * sizeof(long long);
+    long long* cv = sm ? reinterpret_cast<long long*>(p) : w.colV;
+    p += TABMAX * sizeof(long long);
+    short* cp = sm ? reinterpret_cast<short*>(p) : w.colP;
+    p += TABMAX * sizeof(short);
+    p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    F.coef = sm ? reinterpret_cast<Cx<T>*>(p) : w.pre;
+    p += (TABMAX + RF_MAX) * sizeof(Cx<T>);
+    F.row = S.N <= ROWMAX ? reinterpret_cast<Cx<T>*>(p) : w.row;
+    for (int c = threadIdx.x; c < F.ncol; c += NT) {
+        int q = 0;
+        while (S.pre[q + 1] <= c) ++q;
+        const int t = c - S.pre[q];
+        cu[c] = S.off[q] + (long long)t * S.M;
+        cv[c] = S.off[q] + (long long)S.r[q] * S.M + (long long)t * S.N;
+        cp[c] = (short)q;
+    }
+    F.colU = cu;
+    F.colV = cv;
+    F.colP = cp;
+    return F;
+}
+
+// coefficients of a row (f_p[kf] U_p[t][fix], then u_t[fix] of the current face)
+// or of a column (f_p[kf] conj(V_p[t][fix]), then conj(v_t[fix]))
+template <class T, int NT, bool ROW>
+__device__ void line_coeffs(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int fix,
+                            int m) {
+    for (int c = threadIdx.x; c < F.ncol + m; c += NT) {
+        if (c < F.ncol) {
+            const Cx<T> fk = S.fk[F.colP[c]];
+            F.coef[c] = ROW ? cmul(fk, A.pool[F.colU[c] + fix]) : cmul(fk, cconj(A.pool[F.colV[c] + fix]));
+        } else {
+            const int t = c - F.ncol;
+            F.coef[c] = ROW ? w.uw[(size_t)t * A.Mmax + fix] : cconj(w.vw[(size_t)t * A.Nmax + fix]);
+        }
+    }
+}
+
+// Residual of one row (ROW: fixed row `fix`, all columns) or one column (!ROW:
+// fixed column `fix`, all rows) of the face at kf:
+//   ENTRY - sum_p f_p[kf] (U_p V_p^H) - sum_{t<m} u_t v_t^H
+//   ROW:  out[j] = ENTRY(fix, j) - sum_c coef[c] conj(X_c[j]),  X_c = V_p[:, t] | v_t
+//   !ROW: out[i] = ENTRY(i, fix) - sum_c X_c[i] coef[c],        X_c = U_p[:, t] | u_t
+// G threads per output element share the sum (4-way unrolled, independent
+// partial sums) and the quadrature points.  Returns the block-wide argmax of
+// |out|^2 (ROW: over all columns; !ROW: over the rows not yet used).
+template <int KER, class T, int NT, bool ROW>
+__device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
+                                    int fix, int kf, int m, Cx<T>* out) {
+    const int tid = threadIdx.x;
+    const int M = S.M, N = S.N;
+    const int L = ROW ? N : M;
+    const int G = gang_size<NT>(L);
+    const int per = NT / G;
+    const int part = tid % G;
+    const long long* col = ROW ? F.colV : F.colU;
+    const Cx<T>* cur = ROW ? w.vw : w.uw;
+    const size_t ldc = ROW ? A.Nmax : A.Mmax;
+    const int nt = F.ncol;
+    ArgMaxT<T> am = amax_none<T>();
+    for (int base = 0; base < L; base += per) {
+        const int v = base + tid / G;
+        Cx<T> acc{0, 0};
+        if (v < L) {
+            const int gi = S.rb + (ROW ? fix : v), gj = S.cb + (ROW ? v : fix);
+            acc = ent_part<KER, T>(A, gi, gj, kf, part, G);
+            Cx<T> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+            int c = part;
+            for (; c + 3 * G < nt; c += 4 * G) {
+                const Cx<T> x0 = A.pool[col[c] + v], x1 = A.pool[col[c + G] + v];
+                const Cx<T> x2 = A.pool[col[c + 2 * G] + v], x3 = A.pool[col[c + 3 * G] + v];
+                if (ROW) {
+                    cfmac(s0, F.coef[c], x0);
+                    cfmac(s1, F.coef[c + G], x1);
+                    cfmac(s2, F.coef[c + 2 * G], x2);
+                    cfmac(s3, F.coef[c + 3 * G], x3);
+                } else {
+                    cfma(s0, x0, F.coef[c]);
+                    cfma(s1, x1, F.coef[c + G]);
+                    cfma(s2, x2, F.coef[c + 2 * G]);
+                    cfma(s3, x3, F.coef[c + 3 * G]);
+                }
+            }
+            for (; c < nt; c += G) {
+                const Cx<T> x0 = A.pool[col[c] + v];
+                if (ROW) cfmac(s0, F.coef[c], x0);
+                else cfma(s0, x0, F.coef[c]);
+            }
+            int t = part;
+            for (; t + G < m; t += 2 * G) {
+                const Cx<T> x0 = cur[(size_t)t * ldc + v], x1 = cur[(size_t)(t + G) * ldc + v];
+                if (ROW) {
+                    cfmac(s1, F.coef[nt + t], x0);
+                    cfmac(s2, F.coef[nt + t + G], x1);
+                } else {
+                    cfma(s1, x0, F.coef[nt + t]);
+                    cfma(s2, x1, F.coef[nt + t + G]);
+                }
+            }
+            for (; t < m; t += G) {
+                const Cx<T> x0 = cur[(size_t)t * ldc + v];
+                if (ROW) cfmac(s3, F.coef[nt + t], x0);
+                else cfma(s3, x0, F.coef[nt + t]);
+            }
+            acc.x -= (s0.x + s1.x) + (s2.x + s3.x);
+            acc.y -= (s0.y + s1.y) + (s2.y + s3.y);
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            Cx<T> y = shfl_xor_c(acc, o);
+            acc.x += y.x;
+            acc.y += y.y;
+        }
+        if (part == 0 && v < L) {
+            out[v] = acc;
+            if (ROW || !w.used[v]) am = amax_better(am, ArgMaxT<T>{cabs2(acc), v});
+        }
+    }
+    if (tid == 0) S.entries += L;
+    return block_argmax<NT>(am, S.am);
+}
+
+// ---- sampled residual of the face approximant ------------------------------------------
+// R_s = ENTRY(i_s, j_s, kf) - sum_p f_p[kf] H_p[i_s, j_s] - sum_{t<m} u_t[i_s] conj(v_t[j_s])
+// at the 32 sample positions; one warp per sample, lanes over the flattened
+// columns of the earlier crosses.  Writes |R_s|^2 to S.samp.
+template <int KER, class T, int NT>
+__device__ void face_samples(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int kf,
+                             int m) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int M = S.M, N = S.N;
+    for (int sm = wid; sm < SAMPLES; sm += NT / 32) {
+        const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
+        Cx<T> acc{0, 0};
+        for (int c = lane; c < F.ncol; c += 32) {
+            const Cx<T> h = cmulc(A.pool[F.colU[c] + i], A.pool[F.colV[c] + j]);
+            cfma(acc, S.fk[F.colP[c]], h);
+        }
+        for (int t = lane; t < m; t += 32) cfmac(acc, w.uw[(size_t)t * A.Mmax + i], w.vw[(size_t)t * A.Nmax + j]);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        if (lane == 0) {
+            const Cx<T> e = ent<KER, T>(A, S.rb + i, S.cb + j, kf);
+            S.samp[sm] = cabs2d(Cx<T>{e.x - acc.x, e.y - acc.y});
+        }
+    }
+    if (threadIdx.x == 0) S.entries += SAMPLES;
+    __syncthreads();
+}
+
+// ---- face ACA (partial pivoting) on the residual face at frequency kf -----------------
+// Returns the rank m; columns 0..m-1 of uw / vw hold the crosses (S = U V^H).
+template <int KER, class T, int NT>
+__device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int kf, unsigned char* arena) {
+    const int tid = threadIdx.x;
+    const int M = S.M, N = S.N, nc = S.ncross;
+    const int cap = min(min(M, N), A.RF);
+    if (kf < 0 || kf >= A.Ku) {  // cannot happen: every caller passes a checked index
+        if (tid == 0) atomicOr(A.status, ST_BAD_INDEX);
+        return 0;
+    }
+    // f_p[kf] of earlier crosses, the column tables, used-row flags
+    for (int p = tid; p < nc; p += NT) S.fk[p] = Fp(A, S, p)[kf];
+    const FaceTab<T> F = facetab_build<T, NT>(A, w, S, arena);
+    for (int i = tid; i < M; i += NT) w.used[i] = 0;
+    __syncthreads();
+    double Sn2 = 0.0;
+    int m = 0;
+    int irow = 0;
+    bool converged = false;
+    // absolute floor of the face tests (float32 entries only): a residual face
+    // far below the block's typical face, face_floor ||C^(l-1)||_F / sqrt(Ku),
+    // is resolved to that level rather than relative to its own norm, which
+    // the entries' rounding noise would never let the test reach
+    const double floor2 = A.face_floor * A.face_floor * S.norm2 / (double)A.Ku;
+    while (m < cap) {
+        int jp = -1;
+        for (;;) {
+            line_coeffs<T, NT, true>(A, w, S, F, irow, m);
+            __syncthreads();
+            ArgMaxT<T> am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row);
+            if (tid == 0) w.used[irow] = 1;
+            // a row counts as nonzero when |delta|^2 is a normal number of the
+            // working precision (below that the entries are far under any tolerance)
+            if (am.v > tiny_norm2<T>()) {
+                jp = am.i;
+                break;
+            }
+            // zero residual row: next unused row in index order
+            ArgMaxT<T> un = amax_none<T>();
+            for (int i = tid; i < M; i += NT)
+                if (i != irow && !w.used[i]) un = amax_better(un, ArgMaxT<T>{(T)0, i});
+            un = block_argmax<NT>(un, S.am);
+            if (un.v < 0.0) {
+                irow = -1;
+                break;
+            }
+            irow = un.i;
+        }
+        if (jp < 0) break;  // no row with a nonzero residual left
+        // v = conj(row / delta) with delta scaled to magnitude ~1 first, so that a
+        // tiny pivot of a strongly damped face cannot overflow 1 / |delta|^2
+        // (|row[j]| <= |delta| since delta is the row's largest entry)
+        const Cx<T> delta = F.row[jp];
+        const T sc = (T)1 / fmax(fabs(delta.x), fabs(delta.y));
+        const Cx<T> ds{delta.x * sc, delta.y * sc};
+        const T dn = (T)1 / cabs2(ds);
+        Cx<T>* vm = w.vw + (size_t)m * A.Nmax;
+        for (int j = tid; j < N; j += NT) {
+            const Cx<T> rj = F.row[j];
+            const Cx<T> q = cmulc(Cx<T>{rj.x * sc, rj.y * sc}, ds);  // (row / s) conj(delta / s)
+            vm[j] = Cx<T>{q.x * dn, -q.y * dn};                      // conj(row / delta)
+        }
+        line_coeffs<T, NT, false>(A, w, S, F, jp, m);
+        __syncthreads();
+        // residual column jp = u_m; the argmax over unused rows of |u_m| is the next row
+        Cx<T>* um = w.uw + (size_t)m * A.Mmax;
+        ArgMaxT<T> nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um);
+        // recursive Frobenius norm of the face approximant:
+        // ||S_m||^2 = ||S_{m-1}||^2 + 2 Re sum_t (u_t^H u_m)(v_m^H v_t) + ||u_m||^2 ||v_m||^2
+        const int wid = tid >> 5, lane = tid & 31;
+        for (int t = wid; t <= m; t += NT / 32) {
+            const Cx<T>* ut = w.uw + (size_t)t * A.Mmax;
+            const Cx<T>* vt = w.vw + (size_t)t * A.Nmax;
+            Cx<T> gu{0, 0}, gv{0, 0};
+            for (int i = lane; i < M; i += 32) cfmac(gu, um[i], ut[i]);  // conj(u_t) u_m
+            for (int j = lane; j < N; j += 32) cfmac(gv, vt[j], vm[j]);  // conj(v_m) v_t
+            const T gux = warp_sum(gu.x), guy = warp_sum(gu.y);
+            const T gvx = warp_sum(gv.x), gvy = warp_sum(gv.y);
+            if (lane == 0) {
+                S.gu[t] = Cx<double>{(double)gux, (double)guy};
+                S.gv[t] = Cx<double>{(double)gvx, (double)gvy};
+            }
+        }
+        __syncthreads();
+        double cross = 0.0;
+        for (int t = 0; t < m; ++t) cross += 2.0 * (S.gu[t].x * S.gv[t].x - S.gu[t].y * S.gv[t].y);
+        const double nu2 = S.gu[m].x, nv2 = S.gv[m].x;
+        Sn2 += cross + nu2 * nv2;
+        ++m;
+        __syncthreads();
+        if (nu2 * nv2 <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
+            if (!A.sample_check) {
+                converged = true;
+                break;
+            }
+            // confirm on the sample entries: partial pivoting can miss a block
+            // of the face that no visited row or column reaches
+            face_samples<KER, T, NT>(A, w, S, F, kf, m);
+            double tot = 0.0, best = -1.0;
+            int bs = 0;
+            for (int sm = 0; sm < SAMPLES; ++sm) {
+                tot += S.samp[sm];
+                if (S.samp[sm] > best) {
+                    best = S.samp[sm];
+                    bs = sm;
+                }
+            }
+            __syncthreads();
+            if ((double)M * (double)N / SAMPLES * tot <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
+                converged = true;
+                break;
+            }
+            if (tid == 0) atomicAdd(&A.counters[5], 1ull);
+            irow = (2 * bs + 1) * M / (2 * SAMPLES);
+            continue;
+        }
+        if (nx.v < 0) break;  // every row used
+        irow = nx.i;
+    }
+    if (tid == 0) S.raw += m;
+    if (!converged && m == A.RF && m < min(M, N)) {
+        if (tid == 0) {
+            atomicOr(A.status, ST_FACE_CAPPED);
+            atomicAdd(&A.counters[3], 1ull);
+        }
+    }
+    __syncthreads();
+    return m;
+}
+
+// ---- tiled Gram of the face factors: G[a][b] = sum_i conj(X_a[i]) X_b[i], a <= b < r ----
+// Products and the sum over a 32-row chunk in the working precision T, the sum
+// over chunks in float64.  sh: >= 33 * r complex T.
+template <class T, int NT>
+__device__ void gram_upper(const Cx<T>* X, size_t ld, int L, int r, Cx<double>* G, int RF, Cx<T>* sh) {
+    constexpr int QMAX = (RF_MAX * (RF_MAX + 1) / 2 + NT - 1) / NT;
+    const int tid = threadIdx.x;
+    const int npair = r * (r + 1) / 2;
+    int pa[QMAX], pb[QMAX];
+    Cx<double> acc[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+        int p = tid + q * NT;
+        acc[q] = Cx<double>{0, 0};
+        pa[q] = -1;
+        pb[q] = 0;
+        if (p < npair) {
+            int a = 0;
+            while (p >= r - a) {
+                p -= r - a;
+                ++a;
+            }
+            pa[q] = a;
+            pb[q] = a + p;
+        }
+    }
+    for (int i0 = 0; i0 < L; i0 += 32) {
+        for (int e = tid; e < r * 32; e += NT) {
+            const int c = e >> 5, ii = e & 31;
+            sh[c * 33 + ii] = (i0 + ii < L) ? X[(size_t)c * ld + i0 + ii] : Cx<T>{0, 0};
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            if (pa[q] < 0) continue;
+            const Cx<T>* xa = sh + pa[q] * 33;
+            const Cx<T>* xb = sh + pb[q] * 33;
+            Cx<T> s{0, 0};
+#pragma unroll 8
+            for (int ii = 0; ii < 32; ++ii) cfmac(s, xb[ii], xa[ii]);  // conj(x_a) x_b
+            acc[q].x += (double)s.x;
+            acc[q].y += (double)s.y;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q)
+        if (pa[q] >= 0) G[pa[q] * RF + pb[q]] = acc[q];
+}
+
+// ---- recompression: Cholesky-QR + one-sided Jacobi SVD ---------------------------------
+// Input uw, vw (r columns).  Output: the rank r' and the transforms T_U, T_V
+// (r x r', complex T, row-major with stride *ldT) such that U' = uw T_U,
+// V' = vw T_V.  For any invertible triangular R used consistently,
+// uw T_U T_V^H vw^H = uw vw^H before truncation, so the Gram matrices may be
+// formed in the working precision; the r x r algebra is float64.
+//
+// The four r x r float64 matrices (R_U, R_V, B = C J, J) live in shared memory
+// (stride RS) when r <= RS, else in the global workspace (stride RF).  The
+// back substitution runs in place on the selected columns of B and J.
+// Returns r' or -1 (Cholesky breakdown or a non-finite SVD: the caller keeps
+// the raw factors).
+constexpr int RS = 32;
+
+template <class T>
+__device__ __forceinline__ T jacobi_tol();
+template <>
+__device__ __forceinline__ float jacobi_tol<float>() { return 1e-6f; }
+template <>
+__device__ __forceinline__ double jacobi_tol<double>() { return 1e-12; }
+
+template <class T, int NT>
+__device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int r, Cx<double>* smem,
+                          const Cx<T>** tUo, const Cx<T>** tVo, int* ldTo) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int M = S.M, N = S.N;
+    const bool small = r <= RS;
+    const int ld = small ? RS : A.RF;
+    Cx<double>* RU = small ? smem : w.RU;
+    Cx<double>* RV = small ? smem + RS * RS : w.RV;
+    // B = C J and J in the working precision T (the Jacobi sweeps dominate the
+    // r x r work; float64 is rate-limited on this part)
+    Cx<T>* shB = small ? reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS) : reinterpret_cast<Cx<T>*>(w.TU);
+    Cx<T>* shJ = shB + (small ? RS * RS : A.RF * A.RF);
+    // Gram staging after R_U, R_V
+    Cx<T>* stage = reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS);
+    gram_upper<T, NT>(w.uw, A.Mmax, M, r, RU, ld, stage);
+    gram_upper<T, NT>(w.vw, A.Nmax, N, r, RV, ld, stage);
+    if (tid == 0) S.flag = 0;
+    __syncthreads();
+    // column scaling and upper Cholesky of the scaled Gram matrices (float64):
+    // warp 0 -> U, warp 1 -> V
+    if (wid < 2) {
+        Cx<double>* R = wid == 0 ? RU : RV;
+        double* dsc = wid == 0 ? S.dU : S.dV;
+        for (int a = lane; a < r; a += 32) dsc[a] = 1.0 / sqrt(fmax(R[a * ld + a].x, 1e-300));
+        __syncwarp();
+        for (int a = lane; a < r; a += 32)
+            for (int b = a; b < r; ++b) {
+                double s = dsc[a] * dsc[b];
+                R[a * ld + b].x *= s;
+                R[a * ld + b].y *= s;
+            }
+        __syncwarp();
+        for (int k = 0; k < r; ++k) {
+            double dkk = R[k * ld + k].x;
+            for (int i = 0; i < k; ++i) dkk -= cabs2(R[i * ld + k]);
+            bool bad = !(dkk > 1e-24);
+            if (bad) {
+                if (lane == 0) atomicOr(&S.flag, 1);
+                break;
+            }
+            double rkk = sqrt(dkk);
+            double irkk = 1.0 / rkk;
+            for (int j = k + 1 + lane; j < r; j += 32) {
+                Cx<double> acc = R[k * ld + j];
+                for (int i = 0; i < k; ++i) {
+                    Cx<double> rik = R[i * ld + k], rij = R[i * ld + j];
+                    acc.x -= rik.x * rij.x + rik.y * rij.y;  // conj(R[i][k]) R[i][j]
+                    acc.y -= rik.x * rij.y - rik.y * rij.x;
+                }
+                R[k * ld + j] = Cx<double>{acc.x * irkk, acc.y * irkk};
+            }
+            __syncwarp();
+            if (lane == 0) R[k * ld + k] = Cx<double>{rkk, 0.0};
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (S.flag) return -1;
+    // core C = R_U R_V^H with R_U = Rhat_U diag(1/dU): C[a][b] = sum_{c >= max(a,b)}
+    //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in B, J = I
+    for (int e = tid; e < r * r; e += NT) {
+        const int a = e % r, b = e / r;
+        Cx<double> acc{0, 0};
+        for (int c = max(a, b); c < r; ++c) {
+            Cx<double> x = RU[a * ld + c], y = RV[b * ld + c];
+            double s = 1.0 / (S.dU[c] * S.dV[c]);
+            acc.x += (x.x * y.x + x.y * y.y) * s;
+            acc.y += (x.y * y.x - x.x * y.y) * s;
+        }
+        shB[b * ld + a] = ccast<T>(acc);
+        shJ[b * ld + a] = Cx<T>{(T)(a == b ? 1 : 0), (T)0};
+    }
+    __syncthreads();
+    // one-sided Jacobi (Hestenes) on the columns of C, round-robin pair schedule;
+    // a pair is rotated while |<c_p, c_q>| > tol ||c_p|| ||c_q||.  Column norms
+    // are recomputed at each sweep start and updated after every rotation
+    // (||c_p'||^2 = ||c_p||^2 - t |g|, ||c_q'||^2 = ||c_q||^2 + t |g|).
+    const int n = (r + 1) & ~1;
+    const T tol = jacobi_tol<T>();
+    T* cn = reinterpret_cast<T*>(S.sig);  // column norms (S.sig is free until the SVD finishes)
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        if (tid == 0) S.rot = 0;
+        for (int a = wid; a < r; a += NT / 32) {
+            T s2 = 0;
+            for (int i = lane; i < r; i += 32) s2 += cabs2(shB[a * ld + i]);
+            s2 = warp_sum(s2);
+            if (lane == 0) cn[a] = s2;
+        }
+        __syncthreads();
+        for (int rho = 0; rho < n - 1; ++rho) {
+            for (int pi = wid; pi < n / 2; pi += NT / 32) {
+                int p, q;
+                if (pi == 0) {
+                    p = rho;
+                    q = n - 1;
+                } else {
+                    p = (rho + pi) % (n - 1);
+                    q = (rho - pi + (n - 1)) % (n - 1);
+                }
+                if (p >= r || q >= r) continue;
+                Cx<T>* bp = shB + p * ld;
+                Cx<T>* bq = shB + q * ld;
+                const T al = cn[p], be = cn[q];
+                Cx<T> ga{0, 0};
+                for (int i = lane; i < r; i += 32) {
+                    Cx<T> x = bp[i], y = bq[i];
+                    ga.x += x.x * y.x + x.y * y.y;
+                    ga.y += x.x * y.y - x.y * y.x;
+                }
+                ga.x = warp_sum(ga.x);
+                ga.y = warp_sum(ga.y);
+                T ag = sqrt(ga.x * ga.x + ga.y * ga.y);
+                if (ag > tol * sqrt(al * be) && ag > (T)1e-30) {
+                    T zeta = (be - al) / ((T)2 * ag);
+                    T t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+                    T c = (T)1 / sqrt((T)1 + t * t), s = c * t;
+                    Cx<T> ph{ga.x / ag, ga.y / ag};  // e^{i phi}
+                    Cx<T>* jp_ = shJ + p * ld;
+                    Cx<T>* jq_ = shJ + q * ld;
+                    for (int i = lane; i < r; i += 32) {
+                        Cx<T> x = bp[i], y = bq[i];
+                        // x' = c x - s e^{-i phi} y ; y' = s e^{i phi} x + c y
+                        Cx<T> ey = cmulc(y, ph), ex = cmul(x, ph);
+                        bp[i] = Cx<T>{c * x.x - s * ey.x, c * x.y - s * ey.y};
+                        bq[i] = Cx<T>{s * ex.x + c * y.x, s * ex.y + c * y.y};
+                        x = jp_[i];
+                        y = jq_[i];
+                        ey = cmulc(y, ph);
+                        ex = cmul(x, ph);
+                        jp_[i] = Cx<T>{c * x.x - s * ey.x, c * x.y - s * ey.y};
+                        jq_[i] = Cx<T>{s * ex.x + c * y.x, s * ex.y + c * y.y};
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&S.rot, 1);
+                        cn[p] = al - t * ag;
+                        cn[q] = be + t * ag;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const int rot = S.rot;
+        __syncthreads();
+        if (rot == 0) break;
+        if (sweep == 15 && tid == 0) atomicOr(A.status, ST_JACOBI_NOCONV);
+    }
+    // singular values, sort descending, truncation sigma < eps_face * sigma_max
+    for (int a = tid; a < r; a += NT) {
+        double s2 = 0;
+        for (int i = 0; i < r; ++i) s2 += cabs2d(shB[a * ld + i]);
+        S.sig[a] = sqrt(s2);
+    }
+    __syncthreads();
+    double smax = 0;
+    bool finite = true;
+    for (int a = 0; a < r; ++a) {
+        smax = fmax(smax, S.sig[a]);
+        finite &= (bool)isfinite(S.sig[a]);
+    }
+    if (!finite || !(smax > 0.0)) return -1;
+    // (float32 entries: also below the face tests' absolute floor, keeping sigma_1)
+    const double sfloor = A.trunc_floor * sqrt(S.norm2 / (double)A.Ku);
+    for (int a = tid; a < r; a += NT) {
+        int rank = 0;
+        for (int b = 0; b < r; ++b)
+            if (S.sig[b] > S.sig[a] || (S.sig[b] == S.sig[a] && b < a)) ++rank;
+        bool keep = S.sig[a] > 0.0 && S.sig[a] >= A.eps_face * smax && (rank == 0 || S.sig[a] >= sfloor);
+        S.sel[rank] = keep ? a : -1;
+    }
+    __syncthreads();
+    int rn = 0;
+    while (rn < r && S.sel[rn] >= 0) ++rn;
+    // T_U[:, b] = diag(dU) RhatU^{-1} B[:, sel[b]],  T_V[:, b] = diag(dV) RhatV^{-1} J[:, sel[b]]
+    // (float64 back substitution, in place on the selected columns)
+    for (int item = tid; item < 2 * rn; item += NT) {
+        const bool isU = item < rn;
+        const int b = isU ? item : item - rn;
+        const Cx<double>* R = isU ? RU : RV;
+        Cx<T>* z = (isU ? shB : shJ) + S.sel[b] * ld;
+        const double* dsc = isU ? S.dU : S.dV;
+        for (int a = r - 1; a >= 0; --a) {
+            Cx<double> acc = ccast<double>(z[a]);
+            for (int c = a + 1; c < r; ++c) {
+                Cx<double> rr = R[a * ld + c];
+                Cx<double> zc = ccast<double>(z[c]);
+                acc.x -= rr.x * zc.x - rr.y * zc.y;
+                acc.y -= rr.x * zc.y + rr.y * zc.x;
+            }
+            double rd = 1.0 / R[a * ld + a].x;
+            z[a] = Cx<T>{(T)(acc.x * rd), (T)(acc.y * rd)};
+        }
+        for (int a = 0; a < r; ++a) {
+            z[a].x *= (T)dsc[a];
+            z[a].y *= (T)dsc[a];
+        }
+    }
+    __syncthreads();
+    // compact T_U, T_V (row-major r x r', complex T) into the R_U / R_V storage (dead now)
+    Cx<T>* tU = reinterpret_cast<Cx<T>*>(RU);
+    Cx<T>* tV = reinterpret_cast<Cx<T>*>(RV);
+    for (int e = tid; e < r * rn; e += NT) {
+        const int a = e / rn, b = e % rn;
+        tU[a * ld + b] = shB[S.sel[b] * ld + a];
+        tV[a * ld + b] = shJ[S.sel[b] * ld + a];
+    }
+    __syncthreads();
+    *tUo = tU;
+    *tVo = tV;
+    *ldTo = ld;
+    return rn;
+}
+
+// ---- eq. (norm) inner products ------------------------------------------------------------
+// hh[d] = <H_l, H_d>_F = sum_{a in cross d, b} (U_d^H U_l)[a][b] conj((V_d^H V_l)[a][b]) for the
+// earlier crosses d < nc, and hself = ||H_l||_F^2 (a over the columns of cross l).
+// Tiled: 32 columns of [U_1 .. U_nc U_l] at a time against all rn columns of U_l,
+// over 32-row chunks staged in shared memory (sh: >= 33 * (32 + RF) complex T).
+template <class T, int NT>
+__device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, const Cx<T>* Vn, int rn,
+                           Cx<T>* sh) {
+    constexpr int QMAX = 32 * RF_MAX / NT;
+    const int tid = threadIdx.x;
+    const int M = S.M, N = S.N, nc = S.ncross;
+    const int na = S.pre[nc] + rn;
+    Cx<T>* sa = sh;             // [32][33]
+    Cx<T>* sb = sh + 32 * 33;   // [rn][33]
+    for (int a0 = 0; a0 < na; a0 += 32) {
+        const int acnt = min(32, na - a0);
+        Cx<T> zu[QMAX], zv[QMAX];
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) zu[q] = zv[q] = Cx<T>{0, 0};
+        for (int pass = 0; pass < 2; ++pass) {  // 0: U (rows M), 1: V (rows N)
+            const int L = pass == 0 ? M : N;
+            for (int i0 = 0; i0 < L; i0 += 32) {
+                for (int e = tid; e < acnt * 32; e += NT) {
+                    const int c = e >> 5, ii = e & 31, col = a0 + c;
+                    Cx<T> v{0, 0};
+                    if (i0 + ii < L) {
+                        const Cx<T>* base;
+                        if (col < S.pre[nc]) {
+                            int d = 0;
+                            while (S.pre[d + 1] <= col) ++d;
+                            const int t = col - S.pre[d];
+                            base = pass == 0 ? A.pool + S.off[d] + (long long)t * M
+                                             : A.pool + S.off[d] + (long long)S.r[d] * M + (long long)t * N;
+                        } else {
+                            const int t = col - S.pre[nc];
+                            base = pass == 0 ? Un + (long long)t * M : Vn + (long long)t * N;
+                        }
+                        v = base[i0 + ii];
+                    }
+                    sa[c * 33 + ii] = v;
+                }
+                for (int e = tid; e < rn * 32; e += NT) {
+                    const int b = e >> 5, ii = e & 31;
+                    const Cx<T>* base = pass == 0 ? Un + (long long)b * M : Vn + (long long)b * N;
+                    sb[b * 33 + ii] = (i0 + ii < L) ? base[i0 + ii] : Cx<T>{0, 0};
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < QMAX; ++q) {
+                    const int o = tid + q * NT;
+                    if (o >= acnt * rn) break;
+                    const int al = o / rn, b = o % rn;
+                    const Cx<T>* xa = sa + al * 33;
+                    const Cx<T>* xb = sb + b * 33;
+                    Cx<T> s{0, 0};
+#pragma unroll 8
+                    for (int ii = 0; ii < 32; ++ii) cfmac(s, xb[ii], xa[ii]);
+                    if (pass == 0) {
+                        zu[q].x += s.x;
+                        zu[q].y += s.y;
+                    } else {
+                        zv[q].x += s.x;
+                        zv[q].y += s.y;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // combine: contribution zu conj(zv) to the cross that owns column a
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            const int o = tid + q * NT;
+            if (o >= acnt * rn) break;
+            const int col = a0 + o / rn;
+            const double px = (double)zu[q].x * zv[q].x + (double)zu[q].y * zv[q].y;
+            const double py = (double)zu[q].y * zv[q].x - (double)zu[q].x * zv[q].y;
+            if (col < S.pre[nc]) {
+                int d = 0;
+                while (S.pre[d + 1] <= col) ++d;
+                atomicAdd(&S.hh[d].x, px);
+                atomicAdd(&S.hh[d].y, py);
+            } else {
+                atomicAdd(&S.hself, px);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---- confirmed stop --------------------------------------------------------------------
+// Algorithm 1's test measures only the newest cross.  When it passes, the
+// residual of the approximant with crosses 0..ncl-1 (the newest one included,
+// staged in S.off / S.r) is evaluated at 32 fixed sample entries over all
+// frequencies: rows (2s+1) M / 64, columns (2 (11 s mod 32) + 1) N / 64.
+// Returns true when ||R_samples||_F <= eps3 ||A_samples||_F; otherwise w.rk[k]
+// holds the sampled residual energy per frequency.
+
+template <class T>
+__device__ __forceinline__ const Cx<T>* f_of(const AcaArgs<T>& A, const BlockSh<T>& S, int p) {
+    const long long span = S.r[p] < 0 ? (long long)S.M * S.N : (long long)S.r[p] * (S.M + S.N);
+    return A.pool + S.off[p] + span;
+}
+
+template <int KER, class T, int NT>
+__device__ __noinline__ bool confirm_stop(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int ncl) {
+    const int tid = threadIdx.x, Ku = A.Ku;
+    const int M = S.M, N = S.N;
+    for (int e = tid; e < SAMPLES * ncl; e += NT) {
+        const int sm = e / ncl, p = e % ncl;
+        const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
+        Cx<double> h{0, 0};
+        if (S.r[p] < 0) {
+            h = ccast<double>(A.pool[S.off[p] + i + (long long)j * M]);
+        } else {
+            const Cx<T>* U = A.pool + S.off[p];
+            const Cx<T>* V = U + (long long)S.r[p] * M;
+            for (int t = 0; t < S.r[p]; ++t)
+                cfmac(h, ccast<double>(U[(long long)t * M + i]), ccast<double>(V[(long long)t * N + j]));
+        }
+        w.hs[sm * A.Cmax + p] = h;
+    }
+    if (tid == 0) {
+        S.red2[0] = 0.0;
+        S.red2[1] = 0.0;
+        S.entries += (long long)SAMPLES * Ku;
+    }
+    __syncthreads();
+    for (int k = tid; k < Ku; k += NT) {
+        double rr = 0.0, aa = 0.0;
+        for (int sm = 0; sm < SAMPLES; ++sm) {
+            const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
+            const Cx<double> a = ccast<double>(ent<KER, T>(A, S.rb + i, S.cb + j, k));
+            Cx<double> r = a;
+            for (int p = 0; p < ncl; ++p) {
+                const Cx<double> c = cmul(w.hs[sm * A.Cmax + p], ccast<double>(f_of(A, S, p)[k]));
+                r.x -= c.x;
+                r.y -= c.y;
+            }
+            rr += cabs2(r);
+            aa += cabs2(a);
+        }
+        w.rk[k] = rr;
+        atomicAdd(&S.red2[0], rr);
+        atomicAdd(&S.red2[1], aa);
+    }
+    __syncthreads();
+    const bool ok = S.red2[0] <= A.eps3 * A.eps3 * S.red2[1];
+    __syncthreads();
+    return ok;
+}
+
+// ---- dense-face blocks ---------------------------------------------------------------
+// Algorithm 1 with the exact residual face (no low-rank approximation in the
+// face, the paper's "No Lwr" variant) for blocks with M N <= dense_max.  A
+// cross is stored as H (M x N, column-major) followed by f (Ku) and recorded
+// with r = -1.  Per cross: one parallel pass over the M N face entries (the
+// residual of earlier crosses is nc multiply-adds per entry), a block argmax
+// for the pivot, the fiber, and eq. (norm) through dense inner products.
+template <int KER, class T, int NT>
+__device__ void dense_block(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, bool& zero_block, int& computed,
+                            bool& overflow, long long* ph, long long& tclk) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int M = S.M, N = S.N, MN = M * N, Ku = A.Ku, blk = S.blk;
+    auto lap = [&](int i) {
+        if (tid == 0) {
+            long long tn = clock64();
+            ph[i] += tn - tclk;
+            tclk = tn;
+        }
+    };
+    for (;;) {
+        const int nc = S.ncross;
+        if (tid == 0) {
+            const long long need = (long long)MN + Ku;
+            unsigned long long o = atomicAdd(A.pool_ctr, (unsigned long long)need);
+            if ((long long)o + need > A.pool_cap) {
+                atomicOr(A.status, ST_POOL_OVERFLOW);
+                S.new_off = -1;
+            } else {
+                S.new_off = (long long)o;
+            }
+        }
+        __syncthreads();
+        if (S.new_off < 0) {
+            overflow = true;
+            return;
+        }
+        const long long off = S.new_off;
+        Cx<T>* Hn = A.pool + off;
+        Cx<T>* Fn = Hn + MN;
+        // ---- face: exact residual at S.k, else up to three more frequencies ----
+        int cand[4] = {S.k, Ku - 1, Ku / 2, A.k_maxabs};
+        ArgMaxT<T> am = amax_none<T>();
+        int kf = -1;
+        for (int c = 0; c < 4; ++c) {
+            const int kk = cand[c];
+            bool skip = false;
+            for (int d = 1; d < c; ++d) skip |= (cand[d] == kk);
+            if (c > 0) skip |= ((S.used_k[kk >> 5] >> (kk & 31)) & 1u) != 0;
+            if (skip) continue;
+            for (int p = tid; p < nc; p += NT) S.fk[p] = (A.pool + S.off[p] + MN)[kk];
+            __syncthreads();
+            ArgMaxT<T> a = amax_none<T>();
+            for (int e = tid; e < MN; e += NT) {
+                const int i = e % M, j = e / M;
+                Cx<T> v = ent<KER, T>(A, S.rb + i, S.cb + j, kk);
+                for (int p = 0; p < nc; ++p) {
+                    const Cx<T> h = A.pool[S.off[p] + e];
+                    const Cx<T> x = cmul(S.fk[p], h);
+                    v.x -= x.x;
+                    v.y -= x.y;
+                }
+                Hn[e] = v;
+                a = amax_better(a, ArgMaxT<T>{cabs2(v), i * N + j});
+            }
+            a = block_argmax<NT>(a, S.am);
+            if (tid == 0) {
+                S.entries += MN;
+                S.used_k[kk >> 5] |= 1u << (kk & 31);
+            }
+            __syncthreads();
+            if (a.v > tiny_norm2<T>()) {
+                am = a;
+                kf = kk;
+                break;
+            }
+            if (c == 0 && nc > 0) {
+                // a vanishing residual face after the first cross: nothing left at
+                // this frequency; test the others only to confirm a zero block
+            }
+        }
+        lap(0);
+        if (kf < 0) {
+            zero_block = (nc == 0);
+            return;
+        }
+        if (tid == 0) S.k = kf;
+        ++computed;
+        const int ip = am.i / N, jp = am.i % N;
+        const int ep = ip + jp * M;
+        const Cx<double> hpiv = ccast<double>(Hn[ep]);
+        for (int p = tid; p < nc; p += NT) S.hp[p] = ccast<double>(A.pool[S.off[p] + ep]);
+        __syncthreads();
+        lap(3);
+        // ---- fiber (float64 residual) ----
+        for (int k = tid; k < Ku; k += NT) {
+            Cx<double> e = ccast<double>(ent<KER, T>(A, S.rb + ip, S.cb + jp, k));
+            for (int p = 0; p < nc; ++p) {
+                Cx<double> hf = cmul(S.hp[p], ccast<double>((A.pool + S.off[p] + MN)[k]));
+                e.x -= hf.x;
+                e.y -= hf.y;
+            }
+            Cx<double> fv = cdiv(e, hpiv);
+            w.fib[k] = fv;
+            Fn[k] = ccast<T>(fv);
+        }
+        if (tid == 0) S.entries += Ku;
+        __syncthreads();
+        lap(4);
+        // ---- eq. (norm) with dense faces ----
+        for (int d = wid; d <= nc; d += NT / 32) {
+            Cx<double> ff{0, 0};
+            Cx<T> hh{0, 0};
+            if (d < nc) {
+                const Cx<T>* fd = A.pool + S.off[d] + MN;
+                for (int k = lane; k < Ku; k += 32) cfmac(ff, w.fib[k], ccast<double>(fd[k]));
+                const Cx<T>* Hd = A.pool + S.off[d];
+                for (int e = lane; e < MN; e += 32) cfmac(hh, Hn[e], Hd[e]);
+            } else {
+                for (int k = lane; k < Ku; k += 32) ff.x += cabs2(w.fib[k]);
+                for (int e = lane; e < MN; e += 32) hh.x += cabs2(Hn[e]);
+            }
+            ff.x = warp_sum(ff.x);
+            ff.y = warp_sum(ff.y);
+            const T hx = warp_sum(hh.x), hy = warp_sum(hh.y);
+            if (lane == 0) {
+                if (d < nc) {
+                    S.ff[d] = ff;
+                    S.hh[d] = Cx<double>{(double)hx, (double)hy};
+                } else {
+                    S.fself = ff.x;
+                    S.hself = (double)hx;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double add = 0.0;
+            for (int d = 0; d < nc; ++d) add += 2.0 * (S.hh[d].x * S.ff[d].x - S.hh[d].y * S.ff[d].y);
+            double own = S.hself * S.fself;
+            S.norm2 += add + own;
+            S.stop = sqrt(fmax(own, 0.0)) <= A.eps3 * sqrt(fmax(S.norm2, 0.0));
+            bool all_used = true;
+            for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+            S.flag = all_used;
+            S.off[nc] = off;  // staged for the stop check
+            S.r[nc] = -1;
+        }
+        __syncthreads();
+        bool from_samples = false;
+        if (S.stop && A.sample_check && !S.flag) {
+            from_samples = !confirm_stop<KER, T, NT>(A, w, S, nc + 1);
+                if (from_samples && threadIdx.x == 0) atomicAdd(&A.counters[6], 1ull);
+        }
+        if (tid == 0) {
+            const bool stop = S.stop && !from_samples;
+            S.flag = 0;
+            if (!stop) {
+                CrossRec cr;
+                cr.off = off;
+                cr.r = -1;
+                cr.ip = ip;
+                cr.jp = jp;
+                cr.kp = S.k;
+                A.rec[(size_t)blk * A.Cmax + nc] = cr;
+                S.off[nc] = off;
+                S.r[nc] = -1;
+                S.ncross = nc + 1;
+                bool all_used = true;
+                for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+                if (S.ncross >= A.Cmax || all_used) S.flag = 1;
+            } else {
+                S.flag = 1;
+            }
+        }
+        __syncthreads();
+        lap(5);
+        if (S.flag) return;
+        ArgMaxT<T> nk = amax_none<T>();
+        for (int k = tid; k < Ku; k += NT)
+            if (!((S.used_k[k >> 5] >> (k & 31)) & 1u))
+                nk = amax_better(nk, ArgMaxT<T>{(T)(from_samples ? w.rk[k] : cabs2(w.fib[k])), k});
+        nk = block_argmax<NT>(nk, S.am);
+        if (nk.v < 0 || nk.i < 0 || nk.i >= Ku) return;
+        if (tid == 0) S.k = nk.i;
+        __syncthreads();
+        lap(6);
+    }
+}
+
+// ---- the persistent kernel ---------------------------------------------------------
+// DENSE selects the block class this launch serves (dense faces or low-rank
+// faces); the two classes run as two persistent launches with their own queues.
+template <int KER, class T, int NT, bool DENSE>
+__global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockSh<T> S;
+    // the arguments of the block being processed: P, with the geometry and
+    // frequencies of the block's own mesh in a batched compression
+    __shared__ AcaArgs<T> Ash;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int RF = P.RF;
+    Cx<double>* shB = reinterpret_cast<Cx<double>*>(smem_raw);  // arena base
+    const Ws<T> w = ws_carve<T>(P.ws + (size_t)blockIdx.x * P.ws_stride, RF, P.Mmax, P.Nmax, P.Cmax, P.Ku);
+    __shared__ int s_q;
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) {
+            if (P.single >= 0)
+                s_q = (iter == 0 && blockIdx.x == 0) ? P.single : -1;
+            else {
+                int q = atomicAdd(P.queue_head, 1);
+                s_q = q < P.n_far ? q : -1;
+            }
+        }
+        __syncthreads();
+        const int qi = s_q;
+        __syncthreads();
+        if (qi < 0) break;
+        const int blk = P.queue[qi];
+        if (tid == 0) {
+            Ash = P;
+            if (P.geos) {
+                const GeoDesc g = P.geos[P.bgeo[blk]];
+                Ash.gf = g.gf;
+                Ash.gd = g.gd;
+                Ash.sd = g.sd;
+                Ash.sf = g.sf;
+                Ash.Ku = g.Ku;
+                Ash.k_maxabs = g.k_maxabs;
+            }
+        }
+        __syncthreads();
+        const AcaArgs<T>& A = Ash;
+        if (tid == 0) {
+            BlockRange br = A.ranges[blk];
+            S.rb = br.rb;
+            S.cb = br.cb;
+            S.M = br.re - br.rb;
+            S.N = br.ce - br.cb;
+            S.blk = blk;
+            S.ncross = 0;
+            S.pre[0] = 0;
+            S.norm2 = 0.0;
+            S.entries = 0;
+            S.raw = 0;
+            S.k = A.k1 ? A.k1[blk] : 0;
+            for (int i = 0; i < KU_MAX / 32; ++i) S.used_k[i] = 0u;
+        }
+        __syncthreads();
+        const int M = S.M, N = S.N, Ku = A.Ku;
+        const unsigned long long t_start = globaltimer_ns();
+        // phase cycle counters: face, recompress, formation, pivot, fiber, norm, next-k
+        long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
+        long long tclk = clock64();
+        auto lap = [&](int i) {
+            if (tid == 0) {
+                long long tn = clock64();
+                ph[i] += tn - tclk;
+                tclk = tn;
+            }
+        };
+        bool zero_block = false;
+        int computed = 0;
+        bool overflow = false, spilled = false;
+        if (M > A.Mmax || N > A.Nmax) {  // cannot happen: workspace is sized from the block list
+            if (tid == 0) atomicOr(A.status, ST_BAD_INDEX);
+            overflow = true;
+        }
+        if (DENSE) {
+            if (!overflow) dense_block<KER, T, NT>(A, w, S, zero_block, computed, spilled, ph, tclk);
+            overflow = true;  // the low-rank loop below is not for this launch
+        }
+        while (!overflow) {
+            // ---------------- face at S.k ----------------
+            int kf = S.k;
+            int r = face_aca<KER, T, NT>(A, w, S, kf, smem_raw);
+            if (tid == 0) S.used_k[kf >> 5] |= 1u << (kf & 31);
+            __syncthreads();
+            if (r == 0) {
+                // zero face: test up to three more unused frequencies
+                int cand[3] = {Ku - 1, Ku / 2, A.k_maxabs};
+                bool found = false;
+                int tested = 0;
+                for (int c = 0; c < 3 && !found; ++c) {
+                    int kk = cand[c];
+                    bool dup = false;
+                    for (int d = 0; d < c; ++d) dup |= (cand[d] == kk);
+                    if (dup || (S.used_k[kk >> 5] >> (kk & 31)) & 1u) continue;
+                    ++tested;
+                    __syncthreads();
+                    if (tid == 0) S.used_k[kk >> 5] |= 1u << (kk & 31);
+                    __syncthreads();
+                    r = face_aca<KER, T, NT>(A, w, S, kk, smem_raw);
+                    if (r > 0) {
+                        found = true;
+                        kf = kk;
+                    }
+                }
+                if (!found) {
+                    zero_block = (S.ncross == 0);
+                    break;
+                }
+                if (tid == 0) S.k = kf;
+                __syncthreads();
+            }
+            ++computed;
+            lap(0);
+            // ---------------- recompression ----------------
+            int rn = -1;
+            const Cx<T>* tU = nullptr;
+            const Cx<T>* tV = nullptr;
+            int ldT = 0;
+            if (!A.no_recompress) {
+                rn = recompress<T, NT>(A, w, S, r, shB, &tU, &tV, &ldT);
+                if (rn < 0 && tid == 0) {
+                    atomicOr(A.status, ST_CHOL_FALLBACK);
+                    atomicAdd(&A.counters[4], 1ull);
+                }
+            }
+            const bool raw = rn < 0;
+            if (raw) rn = r;
+            lap(1);
+            // allocate U', V', f in the pool
+            if (tid == 0) {
+                long long need = (long long)rn * (M + N) + Ku;
+                unsigned long long o = atomicAdd(A.pool_ctr, (unsigned long long)need);
+                if ((long long)o + need > A.pool_cap) {
+                    atomicOr(A.status, ST_POOL_OVERFLOW);
+                    S.new_off = -1;
+                } else {
+                    S.new_off = (long long)o;
+                }
+                S.rnew = rn;
+            }
+            __syncthreads();
+            if (S.new_off < 0) {
+                overflow = spilled = true;
+                break;
+            }
+            const long long off = S.new_off;
+            Cx<T>* Un = A.pool + off;
+            Cx<T>* Vn = A.pool + off + (long long)rn * M;
+            Cx<T>* Fn = A.pool + off + (long long)rn * (M + N);
+            if (raw) {
+                for (int e = tid; e < rn * M; e += NT) Un[e] = w.uw[(size_t)(e / M) * A.Mmax + e % M];
+                for (int e = tid; e < rn * N; e += NT) Vn[e] = w.vw[(size_t)(e / N) * A.Nmax + e % N];
+            } else {
+                // U' = uw T_U, V' = vw T_V in the working precision, 8 output columns per pass
+                for (int e = tid; e < (M + N) * ((rn + 7) / 8); e += NT) {
+                    const int row = e % (M + N), b0 = (e / (M + N)) * 8;
+                    const bool isU = row < M;
+                    const int i = isU ? row : row - M;
+                    const Cx<T>* src = isU ? w.uw + i : w.vw + i;
+                    const size_t ld = isU ? A.Mmax : A.Nmax;
+                    const Cx<T>* Tm = isU ? tU : tV;
+                    Cx<T> acc[8];
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) acc[bb] = Cx<T>{0, 0};
+                    for (int a = 0; a < r; ++a) {
+                        const Cx<T> u = src[(size_t)a * ld];
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) cfma(acc[bb], u, Tm[a * ldT + min(b0 + bb, rn - 1)]);
+                    }
+                    Cx<T>* dst = isU ? Un + i : Vn + i;
+                    const long long L = isU ? M : N;
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb)
+                        if (b0 + bb < rn) dst[(long long)(b0 + bb) * L] = acc[bb];
+                }
+            }
+            __syncthreads();
+            lap(2);
+            // ---------------- pivot: argmax |U' V'^H| ----------------
+            {
+                constexpr int TM = sizeof(T) == 4 ? 64 : 32;
+                constexpr int TN = TM;
+                constexpr int RM = TM * TN / NT >= 16 ? 4 : 2;  // micro-tile edge
+                constexpr int TX = TN / RM;                     // threads along j
+                Cx<T>* tu = reinterpret_cast<Cx<T>*>(smem_raw);  // [rn][TM]
+                Cx<T>* tv = tu + (size_t)RF * TM;                // [rn][TN]
+                const int tx = tid % TX, ty = tid / TX;
+                ArgMaxT<T> best = amax_none<T>();
+                for (int i0 = 0; i0 < M; i0 += TM) {
+                    for (int j0 = 0; j0 < N; j0 += TN) {
+                        for (int e = tid; e < rn * TM; e += NT) {
+                            int b = e / TM, ii = e % TM;
+                            tu[b * TM + ii] = (i0 + ii < M) ? Un[(long long)b * M + i0 + ii] : Cx<T>{0, 0};
+                        }
+                        for (int e = tid; e < rn * TN; e += NT) {
+                            int b = e / TN, jj = e % TN;
+                            tv[b * TN + jj] = (j0 + jj < N) ? Vn[(long long)b * N + j0 + jj] : Cx<T>{0, 0};
+                        }
+                        __syncthreads();
+                        if (ty * RM < TM) {
+                            Cx<T> acc[RM][RM];
+#pragma unroll
+                            for (int a = 0; a < RM; ++a)
+#pragma unroll
+                                for (int c = 0; c < RM; ++c) acc[a][c] = Cx<T>{0, 0};
+                            for (int b = 0; b < rn; ++b) {
+                                Cx<T> uu[RM], vv[RM];
+#pragma unroll
+                                for (int a = 0; a < RM; ++a) uu[a] = tu[b * TM + ty * RM + a];
+#pragma unroll
+                                for (int c = 0; c < RM; ++c) vv[c] = tv[b * TN + tx * RM + c];
+#pragma unroll
+                                for (int a = 0; a < RM; ++a)
+#pragma unroll
+                                    for (int c = 0; c < RM; ++c) cfmac(acc[a][c], uu[a], vv[c]);
+                            }
+#pragma unroll
+                            for (int a = 0; a < RM; ++a)
+#pragma unroll
+                                for (int c = 0; c < RM; ++c) {
+                                    int gi = i0 + ty * RM + a, gj = j0 + tx * RM + c;
+                                    if (gi < M && gj < N)
+                                        best = amax_better(best, ArgMaxT<T>{cabs2(acc[a][c]), gi * N + gj});
+                                }
+                        }
+                        __syncthreads();
+                    }
+                }
+                best = block_argmax<NT>(best, S.am);
+                if (tid == 0) {
+                    // no finite candidate (a non-finite face): report a vanishing pivot
+                    if (best.v < 0 || best.i < 0 || best.i >= M * N) {
+                        S.ip = 0;
+                        S.jp = 0;
+                        S.hpiv = Cx<double>{0.0, 0.0};
+                        if (best.v >= 0) atomicOr(A.status, ST_BAD_INDEX);
+                    } else {
+                        S.ip = (int)(best.i / N);
+                        S.jp = (int)(best.i % N);
+                        Cx<double> h{0, 0};
+                        for (int b = 0; b < rn; ++b)
+                            cfmac(h, ccast<double>(Un[(long long)b * M + S.ip]), ccast<double>(Vn[(long long)b * N + S.jp]));
+                        if (!isfinite(h.x) || !isfinite(h.y)) h = Cx<double>{0.0, 0.0};
+                        S.hpiv = h;
+                    }
+                }
+            }
+            __syncthreads();
+            lap(3);
+            if (S.hpiv.x == 0.0 && S.hpiv.y == 0.0) break;  // vanishing face: nothing to divide by
+            // H_p[i_l, j_l] of earlier crosses (float64)
+            for (int p = tid; p < S.ncross; p += NT) {
+                const Cx<T>* U = Up(A, S, p);
+                const Cx<T>* V = Vp(A, S, p);
+                Cx<double> h{0, 0};
+                for (int t = 0; t < S.r[p]; ++t)
+                    cfmac(h, ccast<double>(U[(long long)t * M + S.ip]), ccast<double>(V[(long long)t * N + S.jp]));
+                S.hp[p] = h;
+            }
+            __syncthreads();
+            // ---------------- fiber (float64 residual) ----------------
+            const int ip = S.ip, jp = S.jp, nc = S.ncross;
+            const Cx<double> hpiv = S.hpiv;
+            for (int k = tid; k < Ku; k += NT) {
+                Cx<double> e = ccast<double>(ent<KER, T>(A, S.rb + ip, S.cb + jp, k));
+                for (int p = 0; p < nc; ++p) {
+                    Cx<double> fp = ccast<double>(Fp(A, S, p)[k]);
+                    Cx<double> hf = cmul(S.hp[p], fp);
+                    e.x -= hf.x;
+                    e.y -= hf.y;
+                }
+                Cx<double> fv = cdiv(e, hpiv);
+                w.fib[k] = fv;
+                Fn[k] = ccast<T>(fv);
+            }
+            if (tid == 0) S.entries += Ku;
+            __syncthreads();
+            lap(4);
+            // ---------------- eq. (norm) ----------------
+            // <f_l, f_d> and ||f_l||^2
+            for (int d = wid; d <= nc; d += NT / 32) {
+                Cx<double> acc{0, 0};
+                if (d < nc) {
+                    const Cx<T>* fd = Fp(A, S, d);
+                    for (int k = lane; k < Ku; k += 32) cfmac(acc, w.fib[k], ccast<double>(fd[k]));
+                } else {
+                    for (int k = lane; k < Ku; k += 32) acc.x += cabs2(w.fib[k]);
+                }
+                acc.x = warp_sum(acc.x);
+                acc.y = warp_sum(acc.y);
+                if (lane == 0) {
+                    if (d < nc) S.ff[d] = acc;
+                    else S.fself = acc.x;
+                }
+            }
+            for (int d = tid; d < nc; d += NT) S.hh[d] = Cx<double>{0, 0};
+            if (tid == 0) S.hself = 0.0;
+            __syncthreads();
+            // <H_l, H_d> and ||H_l||^2 through tiled Gram products
+            norm_grams<T, NT>(A, S, Un, Vn, rn, reinterpret_cast<Cx<T>*>(smem_raw));
+            if (tid == 0) {
+                double add = 0.0;
+                for (int d = 0; d < nc; ++d) add += 2.0 * (S.hh[d].x * S.ff[d].x - S.hh[d].y * S.ff[d].y);
+                double own = S.hself * S.fself;
+                S.norm2 += add + own;
+                S.stop = sqrt(fmax(own, 0.0)) <= A.eps3 * sqrt(fmax(S.norm2, 0.0));
+                bool all_used = true;
+                for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+                S.flag = all_used;
+                S.off[nc] = off;  // staged for the stop check
+                S.r[nc] = rn;
+            }
+            __syncthreads();
+            bool from_samples = false;
+            if (S.stop && A.sample_check && !S.flag) {
+                from_samples = !confirm_stop<KER, T, NT>(A, w, S, nc + 1);
+                if (from_samples && threadIdx.x == 0) atomicAdd(&A.counters[6], 1ull);
+            }
+            if (tid == 0) {
+                const bool stop = S.stop && !from_samples;
+                S.flag = 0;
+                if (!stop) {
+                    CrossRec cr;
+                    cr.off = off;
+                    cr.r = rn;
+                    cr.ip = ip;
+                    cr.jp = jp;
+                    cr.kp = S.k;
+                    A.rec[(size_t)blk * A.Cmax + nc] = cr;
+                    S.off[nc] = off;
+                    S.r[nc] = rn;
+                    S.pre[nc + 1] = S.pre[nc] + rn;
+                    S.ncross = nc + 1;
+                    bool all_used = true;
+                    for (int k = 0; k < Ku; ++k) all_used &= (S.used_k[k >> 5] >> (k & 31)) & 1u;
+                    if (S.ncross >= A.Cmax || all_used) S.flag = 1;
+                } else {
+                    S.flag = 1;
+                }
+            }
+            __syncthreads();
+            lap(5);
+            if (S.flag) break;
+            // next frequency: argmax over unused k of |f_l[k]|
+            ArgMaxT<T> nk = amax_none<T>();
+            for (int k = tid; k < Ku; k += NT)
+                if (!((S.used_k[k >> 5] >> (k & 31)) & 1u))
+                    nk = amax_better(nk, ArgMaxT<T>{(T)(from_samples ? w.rk[k] : cabs2(w.fib[k])), k});
+            nk = block_argmax<NT>(nk, S.am);
+            if (nk.v < 0 || nk.i < 0 || nk.i >= Ku) break;  // no finite candidate left
+            if (tid == 0) S.k = nk.i;
+            __syncthreads();
+            lap(6);
+        }
+        if (tid == 0) {
+            // a block that found the pool full goes to the spill queue and is
+            // rerun from its start with a fresh pool segment
+            A.r3[blk] = spilled ? 0 : S.ncross;
+            if (spilled) {
+                const int q = atomicAdd(A.spill_n, 1);
+                if (q < A.spill_cap) A.spill[q] = blk;
+            }
+            for (int i = 0; i < 7; ++i) A.blk_cycles[(size_t)blk * NPH + i] += ph[i];
+            A.blk_cycles[(size_t)blk * NPH + 7] += S.raw;
+            A.blk_cycles[(size_t)blk * NPH + 8] = (long long)t_start;
+            A.blk_cycles[(size_t)blk * NPH + 9] = (long long)globaltimer_ns();
+            atomicAdd(&A.counters[0], (unsigned long long)S.entries);
+            atomicAdd(&A.counters[1], (unsigned long long)computed);
+            if (zero_block && !spilled) atomicAdd(&A.counters[2], 1ull);
+            for (int i = 0; i < 7; ++i) atomicAdd(&A.counters[8 + i], (unsigned long long)ph[i]);
+        }
+        __syncthreads();
+    }
+}
+
+// ============================================================================
+// launch helpers (instantiated once per kernel kind, in g3_aca_slp.cu,
+// g3_aca_dlp.cu and g3_aca_sep.cu, so that the kinds compile in parallel)
+// ============================================================================
+
+template <int KER, class T, int NT, bool DENSE>
+g3_status launch_aca_t(g3_ctx* ctx, AcaArgs<T>& A, int grid, size_t smem) {
+    auto kfn = k_aca3<KER, T, NT, DENSE>;
+    G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kfn<<<grid, NT, smem, ctx->stream>>>(A);
+    ctx->count(KER == G3_SEPARABLE ? (DENSE ? "k_aca3_dense_separable" : "k_aca3_separable")
+                                   : (DENSE ? "k_aca3_dense" : "k_aca3"));
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+template <int KER, class T, int NT, bool DENSE>
+int occupancy(size_t smem) {
+    int nb = 0;
+    auto kfn = k_aca3<KER, T, NT, DENSE>;
+    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, NT, smem) != cudaSuccess) nb = 1;
+    return std::max(nb, 1);
+}
+
+}  // namespace g3

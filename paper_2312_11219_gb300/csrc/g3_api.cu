@@ -285,10 +285,16 @@ g3_status g3_freqs_free(g3_freqs* f) {
 
 g3_status build_cluster_tree(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne, int leaf,
                              double eta, g3_tree** out) {
+    return build_cluster_tree_capped(ctx, verts, nv, tris, ne, leaf, eta, 0, out);
+}
+
+g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne, int leaf,
+                                    double eta, int max_block, g3_tree** out) {
     G3_CHECK(ctx && verts && tris && out, "build_cluster_tree: NULL argument");
     *out = nullptr;
     G3_CHECK(nv >= 3 && ne >= 1, "build_cluster_tree: nv = %d, ne = %d", nv, ne);
     G3_CHECK(leaf >= 1, "build_cluster_tree: leaf = %d must be >= 1", leaf);
+    G3_CHECK(max_block >= 0, "build_cluster_tree: max_block = %d must be >= 0", max_block);
     G3_CHECK(eta > 0 && std::isfinite(eta), "build_cluster_tree: eta = %g must be positive", eta);
     for (long long i = 0; i < 3LL * nv; ++i)
         G3_CHECK(std::isfinite(verts[i]), "build_cluster_tree: non-finite vertex coordinate at %lld", i);
@@ -299,6 +305,7 @@ g3_status build_cluster_tree(g3_ctx* ctx, const double* verts, int nv, const int
     t->ne = ne;
     t->nv = nv;
     t->leaf = leaf;
+    t->max_block = max_block;
     t->eta = eta;
     t->verts.assign(verts, verts + 3 * (size_t)nv);
     t->tris.assign(tris, tris + 3 * (size_t)ne);
@@ -450,7 +457,7 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
         const BlockRange& r = rg[i];
         for (int p = std::max(r.rb, r.cb); p < std::min(r.re, r.ce); ++p) {
             const int N = r.ce - r.cb;
-            diag_base[p] = nf->offs[i] + (long long)(p - r.rb) * N + (p - r.cb);
+            diag_base[p] = nf->offs[i] + (long long)(p - r.cb) * (r.re - r.rb) + (p - r.rb);  // [k][j][i]
             diag_mn[p] = (r.re - r.rb) * N;
         }
     }
@@ -512,15 +519,25 @@ g3_status g3_near_get_block(const g3_near* nf, int block, double* out) {
     G3_CHECK(it != nf->order.end(), "g3_near_get_block: block %d is admissible", block);
     const size_t pos = it - nf->order.begin();
     const int32_t* x = &t->blocks[5 * (size_t)block];
-    const size_t n = (size_t)(x[1] - x[0]) * (x[3] - x[2]) * nf->Ku;
+    const size_t M = x[1] - x[0], N = x[3] - x[2];
+    const size_t n = M * N * nf->Ku;
     G3_TRY(use_device(nf->ctx));
+    std::vector<double> tmp(2 * n);
     if (nf->prec == G3_MIXED) {
-        std::vector<float> tmp(2 * n);
-        G3_CUDA(cudaMemcpy(tmp.data(), nf->data.as<float>() + 2 * nf->offs[pos], tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < tmp.size(); ++i) out[i] = tmp[i];
+        std::vector<float> tf(2 * n);
+        G3_CUDA(cudaMemcpy(tf.data(), nf->data.as<float>() + 2 * nf->offs[pos], tf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < tf.size(); ++i) tmp[i] = tf[i];
     } else {
-        G3_CUDA(cudaMemcpy(out, nf->data.as<double>() + 2 * nf->offs[pos], 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
+        G3_CUDA(cudaMemcpy(tmp.data(), nf->data.as<double>() + 2 * nf->offs[pos], 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
     }
+    // device layout [k][j][i] -> exported [k][i][j]
+    for (size_t k = 0; k < (size_t)nf->Ku; ++k)
+        for (size_t i = 0; i < M; ++i)
+            for (size_t j = 0; j < N; ++j) {
+                const size_t src = k * M * N + j * M + i, dst = k * M * N + i * N + j;
+                out[2 * dst] = tmp[2 * src];
+                out[2 * dst + 1] = tmp[2 * src + 1];
+            }
     return G3_OK;
 }
 
@@ -551,7 +568,8 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     G3_CHECK(eps3 > 0 && eps3 < 1, "aca3_compress: eps3 = %g outside (0, 1)", eps3);
     g3_opts o = defaults(opts);
     G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress: face_rank_max = %d outside [0, 64]", o.face_rank_max);
-    G3_CHECK(o.threads == 0 || o.threads == 256, "aca3_compress: threads must be 0 or 256");
+    G3_CHECK(o.threads == 0 || o.threads == 256 || o.threads == 512,
+             "aca3_compress: threads must be 0, 256 or 512");
     G3_CHECK(o.mlp_use >= 0 && o.mlp_use <= 7, "aca3_compress: mlp_use = %d outside [0, 7]", o.mlp_use);
     G3_TRY(use_device(ctx));
     g3_factors* fa = new (std::nothrow) g3_factors();
@@ -569,6 +587,52 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
         return st;
     }
     *out = fa;
+    return G3_OK;
+}
+
+g3_status aca3_compress_batch(g3_ctx* ctx, const g3_tree* const* trees, const g3_freqs* const* freqs, int n_geom,
+                              g3_kernel kernel, g3_scheme scheme, g3_precision prec, double eps3, const g3_opts* opts,
+                              g3_factors** out) {
+    G3_CHECK(ctx && trees && freqs && out, "aca3_compress_batch: NULL argument");
+    G3_CHECK(n_geom >= 1, "aca3_compress_batch: n_geom = %d", n_geom);
+    for (int j = 0; j < n_geom; ++j) {
+        out[j] = nullptr;
+        G3_CHECK(trees[j] && freqs[j], "aca3_compress_batch: NULL tree or frequencies for mesh %d", j);
+    }
+    G3_CHECK(kernel == G3_SLP || kernel == G3_DLP, "aca3_compress_batch: kernel must be G3_SLP or G3_DLP");
+    G3_CHECK(valid_prec(prec), "aca3_compress_batch: bad precision");
+    G3_CHECK(scheme == G3_COLLOC7 || scheme == G3_GALERKIN4x4, "aca3_compress_batch: bad scheme");
+    G3_CHECK(eps3 > 0 && eps3 < 1, "aca3_compress_batch: eps3 = %g outside (0, 1)", eps3);
+    g3_opts o = defaults(opts);
+    G3_CHECK(o.k1 == nullptr && o.cost == nullptr, "aca3_compress_batch: opts->k1 and opts->cost are per mesh; not accepted");
+    G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress_batch: face_rank_max = %d outside [0, 64]",
+             o.face_rank_max);
+    G3_CHECK(o.threads == 0 || o.threads == 256 || o.threads == 512, "aca3_compress_batch: threads must be 0, 256 or 512");
+    G3_CHECK(o.mlp_use >= 0 && o.mlp_use <= 7, "aca3_compress_batch: mlp_use = %d outside [0, 7]", o.mlp_use);
+    G3_CHECK(!o.unbatched, "aca3_compress_batch: unbatched is not accepted");
+    G3_TRY(use_device(ctx));
+    std::vector<g3_factors*> fas(n_geom, nullptr);
+    for (int j = 0; j < n_geom; ++j) {
+        g3_factors* fa = new (std::nothrow) g3_factors();
+        if (!fa) {
+            for (auto* x : fas) delete x;
+            return fail(G3_ENOMEM, "aca3_compress_batch: out of host memory");
+        }
+        fa->ctx = ctx;
+        fa->tree = trees[j];
+        fa->freqs = freqs[j];
+        fa->prec = prec;
+        fa->kernel = kernel;
+        fa->Ku = freqs[j]->Ku;
+        fa->K = freqs[j]->K;
+        fas[j] = fa;
+    }
+    g3_status st = run_aca_batch(ctx, trees, freqs, n_geom, fas.data(), kernel, scheme, eps3, o);
+    if (st != G3_OK) {
+        for (auto* x : fas) delete x;
+        return st;
+    }
+    for (int j = 0; j < n_geom; ++j) out[j] = fas[j];
     return G3_OK;
 }
 
@@ -649,10 +713,10 @@ g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t
         std::vector<double> tmp(2 * tot);
         if (fa->prec == G3_MIXED) {
             std::vector<float> tf(2 * tot);
-            G3_CUDA(cudaMemcpy(tf.data(), fa->pool.as<float>() + 2 * c.off, tf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+            G3_CUDA(cudaMemcpy(tf.data(), fa->pool->as<float>() + 2 * c.off, tf.size() * sizeof(float), cudaMemcpyDeviceToHost));
             for (size_t k = 0; k < tf.size(); ++k) tmp[k] = tf[k];
         } else {
-            G3_CUDA(cudaMemcpy(tmp.data(), fa->pool.as<double>() + 2 * c.off, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            G3_CUDA(cudaMemcpy(tmp.data(), fa->pool->as<double>() + 2 * c.off, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
         }
         if (dense) {
             if (U) std::memcpy(U + 2 * ou, tmp.data(), 2 * nu * sizeof(double));

@@ -47,13 +47,13 @@ __global__ void k_apply_prep(int E, int K, int Ku, const int* __restrict__ perm,
     }
 }
 
-// Near field: one CTA per (row cluster, frequency chunk).  Warp w takes the
-// rows i = w, w + NW, ... of every near block of the row cluster; lane j takes
-// column j (near blocks are leaf x leaf, N <= 32 per pass) and sums
-// Re A (w + w') + i Im A (w - w') over the chunk's frequencies, reading the
-// block's entries A[k][i][j] (row-major per frequency) coalesced along j.  A
-// row's sum is reduced across the warp and added to the row in shared memory
-// by lane 0 (each row has one owning warp); the CTA adds its rows to y once.
+// Near field: one CTA per (row cluster, frequency chunk).  The work units are
+// the (near block, frequency) pairs of the row cluster and chunk, dealt to the
+// warps in turn.  For a unit, lane i holds row i of the block (blocks are
+// stored [k][j][i], so the column j of all rows is one coalesced load) and
+// sums Re A (w + w') + i Im A (w - w') over the block's columns, with w_j and
+// w'_j read as broadcasts.  Each warp keeps its row sums in its own slice of
+// shared memory; the CTA adds the warps' sums to y once.
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, const BlockRange* __restrict__ ranges,
                                                    const long long* __restrict__ offs, const int* __restrict__ row_start,
@@ -61,59 +61,60 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
                                                    const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NW = NT / 32;
-    T* ysh = reinterpret_cast<T*>(smem_raw);  // [2 * Mrow]
     const int g = blockIdx.x;
-    const int k0 = blockIdx.y * kchunk, k1 = min(Ku, k0 + kchunk);
+    const int k0 = blockIdx.y * kchunk, k1 = min(Ku, k0 + kchunk), nk = k1 - k0;
     const int b0 = row_start[g], b1 = row_start[g + 1];
     const int rb = ranges[b0].rb, Mrow = ranges[b0].re - ranges[b0].rb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 2 * Mrow; i += NT) ysh[i] = 0;
+    T* ysw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * Mrow;  // [NW][2 * Mrow]
+    for (int i = threadIdx.x; i < NW * 2 * Mrow; i += NT) reinterpret_cast<T*>(smem_raw)[i] = 0;
     __syncthreads();
-    for (int b = b0; b < b1; ++b) {
+    const int units = (b1 - b0) * nk;
+    for (int u = warp; u < units; u += NW) {
+        const int b = b0 + u / nk, k = k0 + u % nk;
         const BlockRange br = ranges[b];
         const int N = br.ce - br.cb;
-        const long long MN = (long long)Mrow * N;
-        const Cx<T>* Ab = A + offs[b];
-        for (int i = warp; i < Mrow; i += NW) {
+        const Cx<T>* Ak = A + offs[b] + (long long)k * Mrow * N;
+        const Cx<T>* wf = Wf + (long long)k * E + br.cb;
+        const Cx<T>* wc = Wc + (long long)k * E + br.cb;
+        for (int i0 = 0; i0 < Mrow; i0 += 32) {
+            const int i = i0 + lane;
+            const bool act = i < Mrow;
             T ax = 0, ay = 0;
-            for (int j = lane; j < N; j += 32) {
-                const Cx<T>* a_p = Ab + (long long)i * N + j;
-                const Cx<T>* wf_p = Wf + br.cb + j;
-                const Cx<T>* wc_p = Wc + br.cb + j;
-                int k = k0;
-                for (; k + 4 <= k1; k += 4) {
-                    Cx<T> a[4], wf[4], wc[4];
+            int j = 0;
+            for (; j + 8 <= N; j += 8) {
+                Cx<T> a[8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        a[u] = a_p[(long long)(k + u) * MN];
-                        wf[u] = wf_p[(long long)(k + u) * E];
-                        wc[u] = wc_p[(long long)(k + u) * E];
-                    }
+                for (int q = 0; q < 8; ++q) a[q] = act ? Ak[(long long)(j + q) * Mrow + i] : Cx<T>{0, 0};
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        // Re A (wf + wc) + i Im A (wf - wc)
-                        ax += a[u].x * (wf[u].x + wc[u].x) - a[u].y * (wf[u].y - wc[u].y);
-                        ay += a[u].x * (wf[u].y + wc[u].y) + a[u].y * (wf[u].x - wc[u].x);
-                    }
-                }
-                for (; k < k1; ++k) {
-                    const Cx<T> a = a_p[(long long)k * MN], wf = wf_p[(long long)k * E], wc = wc_p[(long long)k * E];
-                    ax += a.x * (wf.x + wc.x) - a.y * (wf.y - wc.y);
-                    ay += a.x * (wf.y + wc.y) + a.y * (wf.x - wc.x);
+                for (int q = 0; q < 8; ++q) {
+                    const Cx<T> f = wf[j + q], c = wc[j + q];
+                    ax += a[q].x * (f.x + c.x) - a[q].y * (f.y - c.y);
+                    ay += a[q].x * (f.y + c.y) + a[q].y * (f.x - c.x);
                 }
             }
-            ax = warp_sum(ax);
-            ay = warp_sum(ay);
-            if (lane == 0) {
-                ysh[2 * i] += ax;
-                ysh[2 * i + 1] += ay;
+            for (; j < N; ++j) {
+                const Cx<T> a = act ? Ak[(long long)j * Mrow + i] : Cx<T>{0, 0};
+                const Cx<T> f = wf[j], c = wc[j];
+                ax += a.x * (f.x + c.x) - a.y * (f.y - c.y);
+                ay += a.x * (f.y + c.y) + a.y * (f.x - c.x);
+            }
+            if (act) {
+                ysw[2 * i] += ax;
+                ysw[2 * i + 1] += ay;
             }
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < Mrow; i += NT) {
-        atomicAdd(&y[rb + i].x, ysh[2 * i]);
-        atomicAdd(&y[rb + i].y, ysh[2 * i + 1]);
+        T sx = 0, sy = 0;
+        for (int w = 0; w < NW; ++w) {
+            const T* yw = reinterpret_cast<const T*>(smem_raw) + (size_t)w * 2 * Mrow;
+            sx += yw[2 * i];
+            sy += yw[2 * i + 1];
+        }
+        atomicAdd(&y[rb + i].x, sx);
+        atomicAdd(&y[rb + i].y, sy);
     }
 }
 
@@ -272,8 +273,8 @@ static int dense_n_max(const g3_factors* fa) {
     return n;
 }
 
-// near-field launch: grid (row clusters) x (frequency chunks), at least
-// ~16 CTAs per SM so that the last wave is short
+// near-field launch: grid (row clusters) x (frequency chunks), about 16 CTAs
+// per SM so that the last wave is short
 template <class T>
 static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, int Ku, int E,
                                    const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y) {
@@ -288,7 +289,7 @@ static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near*
         mrow = std::max(mrow, r[1] - r[0]);
     }
     dim3 grid(n_rows, ksplit);
-    k_apply_near<T, NT><<<grid, NT, 2 * (size_t)mrow * sizeof(T), ctx->stream>>>(
+    k_apply_near<T, NT><<<grid, NT, (NT / 32) * 2 * (size_t)mrow * sizeof(T), ctx->stream>>>(
         nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(), nf->d_offs.as<long long>(), nf->d_row_start.as<int>(),
         Ku, kchunk, E, Wf, Wc, y);
     ctx->count("k_apply_near");
@@ -314,7 +315,7 @@ static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, const int* 
     if (smem > ctx->smem_optin)
         return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
     G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_apply_far<T, NT, PG><<<n, NT, smem, ctx->stream>>>(fa->pool.as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+    k_apply_far<T, NT, PG><<<n, NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
                                                          fa->d_r3.as<int>(), d_ranges, d_list, fa->Cmax, Ku, E, Wf,
                                                          Wc, y, ym, dn, rmax);
     ctx->count("k_apply_far");

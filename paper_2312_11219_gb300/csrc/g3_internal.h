@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -148,6 +149,7 @@ struct g3_freqs {
 struct g3_tree {
     g3_ctx* ctx = nullptr;
     int ne = 0, nv = 0, leaf = 0;
+    int max_block = 0;             // cap of the larger side of a far block (0 = none)
     double eta = 0;
     std::vector<double> verts;
     std::vector<int32_t> tris;
@@ -188,7 +190,8 @@ struct g3_factors {
     const g3_tree* tree = nullptr;
     int prec = 0, kernel = 0, Ku = 0, K = 0, n_far = 0, Cmax = 0;
     int M_sep = 0, N_sep = 0;          // separable mode: one block
-    g3::DevBuf pool;                   // complex (float or double) elements
+    std::shared_ptr<g3::DevBuf> pool = std::make_shared<g3::DevBuf>();  // complex elements; shared by
+                                                                          // the meshes of a batch
     long long pool_cap = 0;            // elements
     g3::DevBuf d_rec;                  // CrossRec [n_far][Cmax]
     g3::DevBuf d_r3;                   // int [n_far]
@@ -229,6 +232,8 @@ g3_status mlp_grad_dev(g3_ctx* ctx, const g3_mlp* net, const float* d_x, const f
 g3_status mlp_fit_dev(g3_ctx* ctx, g3_mlp* net, const float* d_x, const float* d_y, long long n, int epochs,
                       int batch, double lr, double b1, double b2, double eps, int use_graph, float* d_loss);
 void mlp_init_params(uint64_t seed, float* P);
+g3_status run_aca_batch(g3_ctx* ctx, const g3_tree* const* trees, const g3_freqs* const* freqs, int n,
+                        g3_factors* const* fas, int kernel, int scheme, double eps3, const g3_opts& o);
 g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel, int scheme,
                   double eps3, const g3_opts& o, const void* sep_a, const void* sep_b, const void* sep_c, int sep_R);
 g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,

@@ -382,14 +382,14 @@ template <class T>
 __global__ void __launch_bounds__(256) k_mlp_labels(const CrossRec* __restrict__ rec, const int* __restrict__ r3,
                                                       const BlockRange* __restrict__ ranges,
                                                       const Cx<T>* __restrict__ pool, int n_far, int Ku,
-                                                      float* __restrict__ out) {
+                                                      int Cmax, float* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= n_far) return;
     const int r = r3[b];
     int kstar = 0;
     if (r > 0) {
-        const CrossRec c = rec[(size_t)b * Ku];
+        const CrossRec c = rec[(size_t)b * Cmax];
         const BlockRange br = ranges[b];
         const long long M = br.re - br.rb, N = br.ce - br.cb;
         const Cx<T>* f = pool + c.off + (c.r < 0 ? M * N : (long long)c.r * (M + N));
@@ -452,10 +452,10 @@ g3_status mlp_labels_dev(g3_ctx* ctx, const g3_factors* fa, const BlockRange* d_
     const int grid = (fa->n_far + 7) / 8;
     if (fa->prec == G3_MIXED)
         k_mlp_labels<float><<<grid, 256, 0, ctx->stream>>>(fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges,
-                                                            fa->pool.as<Cx<float>>(), fa->n_far, fa->Ku, d_out);
+                                                            fa->pool->as<Cx<float>>(), fa->n_far, fa->Ku, fa->Cmax, d_out);
     else
         k_mlp_labels<double><<<grid, 256, 0, ctx->stream>>>(fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges,
-                                                             fa->pool.as<Cx<double>>(), fa->n_far, fa->Ku, d_out);
+                                                             fa->pool->as<Cx<double>>(), fa->n_far, fa->Ku, fa->Cmax, d_out);
     ctx->count("k_mlp_labels");
     G3_CUDA(cudaGetLastError());
     return G3_OK;

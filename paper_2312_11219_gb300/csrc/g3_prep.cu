@@ -334,8 +334,9 @@ g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int k
 // One CTA per (near block, chunk of KCH unique frequencies).  Threads run
 // over the M_b * N_b entries of the block; each thread sets up the pair
 // geometry once and evaluates it at the KCH frequencies.  Layout of a block:
-// [k][i][j] (frequency-major), complex, starting at offs[b].  Self entries
-// (i == j) are left to k_near_self.
+// [k][j][i] (frequency-major, column-major per frequency: the apply reads a
+// column of rows with one coalesced load), complex, starting at offs[b].
+// Self entries (i == j) are left to k_near_self.
 template <int KER, class T, int KCH>
 __global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2* __restrict__ sd,
                                               const BlockRange* __restrict__ ranges,
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2*
     const long long base = offs[b];
     const int kn = min(KCH, Ku - k0);
     for (int e = threadIdx.x; e < MN; e += blockDim.x) {
-        int i = br.rb + e / N, j = br.cb + e % N;
+        int i = br.rb + e % M, j = br.cb + e / M;
         if (i == j) continue;
         Pair7<T> p;
         if constexpr (sizeof(T) == 4)

@@ -14,7 +14,12 @@
 //   * (t, s) admissible iff min(diam2(t), diam2(s)) <= eta^2 dist2(t, s) and
 //     dist2 > 0 (squared box diameter / box distance, summed x, y, z);
 //   * partition from (root, root): admissible -> far; two leaves -> near;
-//     two inner nodes -> (LL, LR, RL, RR); else split the inner one.
+//     two inner nodes -> (LL, LR, RL, RR); else split the inner one;
+//   * optional cap max_block > 0: an admissible pair whose larger cluster has
+//     more than max_block elements is split by the same rule as an
+//     inadmissible one (children of an admissible pair stay admissible: their
+//     boxes shrink and their distance grows), so no far block exceeds the cap
+//     unless both clusters are leaves.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -29,6 +34,7 @@ struct Builder {
     const std::vector<int32_t>& T;
     int leaf;
     double eta;
+    int max_block = 0;
     std::vector<double> cen;        // [ne][3]
     std::vector<double> tmin, tmax; // [ne][3]
     std::vector<int32_t> perm;
@@ -126,14 +132,18 @@ struct Builder {
     }
     void part(int t, int s) {
         auto N = [&](int id, int k) { return nodes[4 * (size_t)id + k]; };
+        bool tl = N(t, 2) < 0, sl = N(s, 2) < 0;
         if (admissible(t, s)) {
-            blocks.insert(blocks.end(), {N(t, 0), N(t, 1), N(s, 0), N(s, 1), 1});
+            const int big = std::max(N(t, 1) - N(t, 0), N(s, 1) - N(s, 0));
+            if (max_block <= 0 || big <= max_block || (tl && sl)) {
+                blocks.insert(blocks.end(), {N(t, 0), N(t, 1), N(s, 0), N(s, 1), 1});
+                return;
+            }
+        } else if (tl && sl) {
+            blocks.insert(blocks.end(), {N(t, 0), N(t, 1), N(s, 0), N(s, 1), 0});
             return;
         }
-        bool tl = N(t, 2) < 0, sl = N(s, 2) < 0;
-        if (tl && sl) {
-            blocks.insert(blocks.end(), {N(t, 0), N(t, 1), N(s, 0), N(s, 1), 0});
-        } else if (!tl && !sl) {
+        if (!tl && !sl) {
             part(N(t, 2), N(s, 2));
             part(N(t, 2), N(s, 3));
             part(N(t, 3), N(s, 2));
@@ -168,6 +178,7 @@ g3_status build_tree_host(g3_tree* t) {
             return fail(G3_EINVAL, "triangle %d is degenerate", e);
     }
     Builder B(t->verts, t->tris, t->leaf, t->eta);
+    B.max_block = t->max_block;
     B.prepare(ne);
     std::vector<int32_t> all(ne);
     std::iota(all.begin(), all.end(), 0);

@@ -24,10 +24,10 @@ def setup(g3):
     import torch
     ctx = g3.Context(0)
     w = workloads.get("lshape12288")
-    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
     F = g3.freqs_from_spec(ctx, w.freq)
     geo = O_q.Geometry(w.verts, w.tris)
-    OT = O_tree.build(w.verts, w.tris, w.leaf, w.eta)
+    OT = O_tree.build(w.verts, w.tris, w.leaf, w.eta, w.max_block)
     fs = O_freqs.frequency_set(w.freq)
     W = workloads.densities(w.E, w.freq.K, w.density_seed)
     out = {}

@@ -76,6 +76,16 @@ def test_tree_bit_exact(g3, ctx, name):
     assert np.array_equal(got["boxes"][:, :3], ref.lo) and np.array_equal(got["boxes"][:, 3:], ref.hi)
 
 
+@pytest.mark.parametrize("name,cap", [("cube768", 96), ("lshape12288", 384), ("lshape12288", 192)])
+def test_tree_capped_bit_exact(g3, ctx, name, cap):
+    w = workloads.get(name)
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=cap)
+    got = T.get()
+    ref = O_tree.build(w.verts, w.tris, w.leaf, w.eta, cap)
+    assert np.array_equal(got["perm"], ref.perm)
+    assert np.array_equal(got["blocks"], ref.blocks)
+
+
 def test_tree_batch_geometries_bit_exact(g3, ctx):
     for w in workloads.batch64(n_geom=6):
         T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)

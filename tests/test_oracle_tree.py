@@ -7,8 +7,8 @@ from inputs import meshes, workloads
 from oracle import tree
 
 
-def _check(verts, tris, leaf, eta):
-    T = tree.build(verts, tris, leaf, eta)
+def _check(verts, tris, leaf, eta, max_block=0):
+    T = tree.build(verts, tris, leaf, eta, max_block)
     E = tris.shape[0]
     assert np.array_equal(np.sort(T.perm), np.arange(E))
     # every (i, j) covered exactly once
@@ -74,3 +74,27 @@ def test_tree_is_deterministic_and_preorder():
     for n in range(a.begin.size):
         if a.left[n] >= 0:
             assert a.left[n] == n + 1
+
+
+@pytest.mark.parametrize("cap", [48, 96, 192])
+def test_far_block_cap(cap):
+    """With a cap, the partition is still an exact cover with admissible far
+    blocks; no far block's larger side exceeds the cap; the near blocks are
+    unchanged; and every capped far block lies inside one far block of the
+    uncapped partition."""
+    w = workloads.get("lshape3072")
+    plain = tree.build(w.verts, w.tris, w.leaf, w.eta)
+    T = _check(w.verts, w.tris, w.leaf, w.eta, cap)
+    far = T.blocks[T.blocks[:, 4] == 1]
+    assert np.max(np.maximum(far[:, 1] - far[:, 0], far[:, 3] - far[:, 2])) <= cap
+    assert np.array_equal(plain.blocks[plain.blocks[:, 4] == 0], T.blocks[T.blocks[:, 4] == 0])
+    pf = plain.blocks[plain.blocks[:, 4] == 1]
+    for rb, re, cb, ce, _ in far:
+        inside = (pf[:, 0] <= rb) & (re <= pf[:, 1]) & (pf[:, 2] <= cb) & (ce <= pf[:, 3])
+        assert inside.sum() == 1
+    # a cap below the largest block adds blocks; one at or above it changes nothing
+    big = int(np.max(np.maximum(pf[:, 1] - pf[:, 0], pf[:, 3] - pf[:, 2])))
+    if cap < big:
+        assert far.shape[0] > pf.shape[0]
+    else:
+        assert np.array_equal(T.blocks, plain.blocks)
