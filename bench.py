@@ -210,6 +210,33 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float, steps: int)
     return units_per_rank * world / ((ms_max / steps) / 1e3)
 
 
+def train_predictor(g3, ctx, kernels, prec):
+    """Block predictor trained on the compressions of cube768 and lshape3072
+    (features and labels from the library, training on the GPU)."""
+    import time
+
+    import numpy as np
+
+    from inputs import workloads
+    X, Y = [], []
+    for name in ("cube768", "lshape3072"):
+        w = workloads.get(name)
+        T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
+        F = g3.freqs_from_spec(ctx, w.freq)
+        for ker in kernels:
+            fa = g3.aca3_compress(ctx, T, F, ker, prec=prec, eps3=w.eps3)
+            X.append(g3.block_features(ctx, T, F, ker, w.eps3))
+            Y.append(fa.labels())
+    X, Y = np.concatenate(X), np.concatenate(Y)
+    t0 = time.perf_counter()
+    net = g3.mlp_train(ctx, X, Y, epochs=150, batch=256, seed=1)
+    secs = time.perf_counter() - t0
+    p = net.predict(X)
+    return net, {"samples": int(X.shape[0]), "epochs": 150, "seconds": secs,
+                 "mae_log2_r3": float(np.abs(p[:, 0] - Y[:, 0]).mean()),
+                 "data": "cube768 + lshape3072 compressions"}
+
+
 def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     import numpy as np
     import torch
@@ -228,7 +255,13 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     prec = args.precision
     keep = {}
 
-    def step(host: bool):
+    # the learned part: a predictor trained (untimed, like any model) on the
+    # compressions of two smaller meshes, used by every timed compression
+    net, train_info = None, None
+    if args.mlp_use:
+        net, train_info = train_predictor(g3, ctx, kernels, prec)
+
+    def step(host: bool, mlp=None, mlp_use=0):
         T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
         F = g3.freqs_from_spec(ctx, w.freq)
         rec = {"entries_aca": 0, "entries_near": 0, "aca_ms": 0.0, "near_ms": 0.0, "apply_ms": 0.0,
@@ -236,7 +269,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                "dense_bytes": 0, "crosses": 0, "stats": {}}
         for ker in kernels:
             nf = g3.assemble_near(ctx, T, F, ker, prec=prec)
-            fa = g3.aca3_compress(ctx, T, F, ker, prec=prec, eps3=w.eps3)
+            fa = g3.aca3_compress(ctx, T, F, ker, prec=prec, eps3=w.eps3, mlp=mlp, mlp_use=mlp_use)
             y = g3.apply_gcq(ctx, T, nf, fa, W if host else Wd)
             st = fa.stats()
             ni = nf.info()
@@ -265,7 +298,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(n):
-            recs.append(step(host))
+            recs.append(step(host, net, args.mlp_use))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
@@ -273,7 +306,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         return recs, e0.elapsed_time(e1)
 
     for _ in range(args.warmup):
-        step(False)
+        step(False, net, args.mlp_use)
     launches0 = ctx.launch_count()
     with Clocks(local_rank) as clk:
         recs, ms = timed(args.steps, host=False)
@@ -302,6 +335,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     near_ms = sum(r["apply_near_ms"] for r in recs) / len(recs)
     apply_gbs = r0["apply_bytes"] / (apply_ms / 1e3) / 1e9
     near_gbs = r0["apply_near_bytes"] / (near_ms / 1e3) / 1e9
+    # far part of the apply (everything but the near-field stream: factors,
+    # W read once, y written once)
+    far_gbs = (r0["apply_bytes"] - r0["apply_near_bytes"]) / ((apply_ms - near_ms) / 1e3) / 1e9
     # plain baseline: float64, one block per launch (host loop), on a bounded
     # sample of the first admissible blocks of the single layer
     T, F, nf, fa, y = keep[kernels[0]]
@@ -310,6 +346,17 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     ours_sample = g3.aca3_compress(ctx, T, F, kernels[0], prec=prec, eps3=w.eps3,
                                    max_blocks=args.plain_blocks).stats()
     plain_eps = plain["entries"] / (plain["ms"] / 1e3)
+    # what the predictor gains: the same compression without it, and with
+    # queue order + pool size only (one step each, after the timed region)
+    learned = None
+    if net is not None:
+        ab = {}
+        for label, (m, u) in {"none": (None, 0), "order_pool": (net, 3), "all": (net, 7)}.items():
+            r = step(False, m, u)
+            ab[label] = {"aca_ms": r["aca_ms"], "crosses": r["crosses"], "factor_bytes": r["factor_bytes"],
+                         "spilled_blocks": sum(st["spilled_blocks"] for st in r["stats"].values()),
+                         "pool_regrows": sum(st["pool_regrows"] for st in r["stats"].values())}
+        learned = {"mlp_use": args.mlp_use, "training": train_info, "ab": ab}
     aca_eps = sum(r["entries_aca"] for r in recs) / (sum(r["aca_ms"] for r in recs) / 1e3)
     out = {
         "metric": METRIC,
@@ -331,6 +378,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                    "parallelism": f"independent replicas x{world}"},
         "apply_gbs": apply_gbs,
         "near_apply_gbs": near_gbs,
+        "far_apply_gbs": far_gbs,
         "entries_per_step": entries,
         "entries_aca": r0["entries_aca"],
         "entries_near": r0["entries_near"],
@@ -357,6 +405,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                                f"block per launch vs the mixed-precision persistent launch over all blocks"},
         "clocks": clk.summary(),
         "peaks_source": peaks["source"],
+        "learned": learned,
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(args.workload, args.cpu_seconds, 7, os.cpu_count() or 1)
@@ -397,6 +446,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mlp-use", type=int, default=7,
+                    help="predictor uses in the timed compressions (1 order, 2 pool, 4 k1; 0 = no predictor)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
