@@ -261,6 +261,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     if args.mlp_use:
         net, train_info = train_predictor(g3, ctx, kernels, prec)
 
+    # launch shape per operator from the autotuner (untimed; cached in the context)
+    tune = {}
+    if not args.no_autotune:
+        T0 = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
+        F0 = g3.freqs_from_spec(ctx, w.freq)
+        for ker in kernels:
+            tune[ker] = g3.autotune(ctx, T0, F0, ker, scheme=w.scheme, prec=prec, eps3=w.eps3)
+        del T0, F0
+
     def step(host: bool, mlp=None, mlp_use=0):
         T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
         F = g3.freqs_from_spec(ctx, w.freq)
@@ -268,8 +277,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                "apply_near_ms": 0.0, "apply_bytes": 0, "apply_near_bytes": 0, "factor_bytes": 0,
                "dense_bytes": 0, "crosses": 0, "stats": {}}
         for ker in kernels:
-            nf = g3.assemble_near(ctx, T, F, ker, prec=prec)
-            fa = g3.aca3_compress(ctx, T, F, ker, prec=prec, eps3=w.eps3, mlp=mlp, mlp_use=mlp_use)
+            nf = g3.assemble_near(ctx, T, F, ker, scheme=w.scheme, prec=prec)
+            shape = {k: tune[ker][k] for k in ("threads", "dense_face_max")} if ker in tune else {}
+            fa = g3.aca3_compress(ctx, T, F, ker, scheme=w.scheme, prec=prec, eps3=w.eps3, mlp=mlp, mlp_use=mlp_use,
+                                  **shape)
             y = g3.apply_gcq(ctx, T, nf, fa, W if host else Wd)
             st = fa.stats()
             ni = nf.info()
@@ -406,6 +417,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "clocks": clk.summary(),
         "peaks_source": peaks["source"],
         "learned": learned,
+        "autotune": tune or None,
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(args.workload, args.cpu_seconds, 7, os.cpu_count() or 1)
@@ -446,7 +458,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mlp-use", type=int, default=7,
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--mlp-use", type=int, default=3,
                     help="predictor uses in the timed compressions (1 order, 2 pool, 4 k1; 0 = no predictor)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

@@ -286,6 +286,17 @@ g3_status g3_near_free(g3_near* nf);
 g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
                         g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out);
 
+/* Autotuner of the compression's launch shape (no counterpart in the paper).
+ * Times aca3_compress on (t, f) for each candidate -- threads per CTA of the
+ * low-rank launch 256 or 512 (512: G3_MIXED only) and the dense-face
+ * threshold M_b N_b <= 24^2, 48^2 or 64^2 -- and writes the fastest into
+ * opts->threads and opts->dense_face_max (the other fields of *opts are used
+ * as given).  The choice is cached in ctx by (K_u bucket, largest far-block
+ * bucket, kernel, scheme, precision) and reused without timing.  best_ms
+ * (may be NULL): the fastest time, 0 on a cache hit. */
+g3_status g3_autotune(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                      g3_precision prec, double eps3, g3_opts* opts, double* best_ms);
+
 /* Algorithm 1 on every admissible block of n_geom meshes in ONE persistent
  * launch (blocks of all meshes share one longest-first queue and one factor
  * pool).  trees[j], freqs[j]: mesh j and its frequency set (K may differ per

@@ -132,6 +132,9 @@ def get(name: str) -> Workload:
     if name == "sphere1280":
         v, t = meshes.icosphere(3)
         return Workload(name, v, t, _gcq_sphere_spec(), density_seed=15)
+    if name == "sphere1280g":
+        v, t = meshes.icosphere(3)
+        return Workload(name, v, t, gcq_spec(64, 0.005, 0.015), scheme="galerkin4x4", density_seed=17)
     if name == "sphere320g":
         v, t = meshes.icosphere(2)
         return Workload(name, v, t, gcq_spec(64, 0.005, 0.015), scheme="galerkin4x4", density_seed=16)

@@ -93,6 +93,7 @@ _sig("g3_near_info", _ci, _p, _i64p, _i64p, _dp)
 _sig("g3_near_get_block", _ci, _p, _ci, _dp)
 _sig("g3_near_free", _ci, _p)
 _sig("aca3_compress", _ci, _p, _p, _p, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _pp)
+_sig("g3_autotune", _ci, _p, _p, _p, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _dp)
 _sig("aca3_compress_batch", _ci, _p, _p, _p, _ci, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _p)
 _sig("aca3_compress_separable", _ci, _p, _dp, _dp, _dp, _ci, _ci, _ci, _ci, _ci, C.c_double, C.POINTER(Opts), _pp)
 _sig("g3_factors_stats", _ci, _p, C.POINTER(Stats))
@@ -119,7 +120,7 @@ _sig("g3_factors_labels", _ci, _p, _p, _fp)
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
             "build_cluster_tree", "build_cluster_tree_capped", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
-            "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "aca3_compress_separable",
+            "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
             "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
             "g3_mlp_grad", "g3_mlp_predict", "g3_mlp_get", "g3_mlp_free", "g3_block_features", "g3_factors_labels"]
@@ -490,6 +491,17 @@ def aca3_compress(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", s
     _check(_lib.aca3_compress(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec], eps3,
                               C.byref(o), C.byref(h)), "aca3_compress")
     return Factors(h, (ctx, tree, freqs))
+
+
+def autotune(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", scheme: str = "colloc7",
+             prec: str = "mixed", eps3: float = 1e-4, **opts) -> dict:
+    """Fastest launch shape of aca3_compress on this problem (cached per
+    problem class in the context): {"threads", "dense_face_max", "ms"}."""
+    o = _opts(**opts)
+    ms = C.c_double()
+    _check(_lib.g3_autotune(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec], eps3,
+                            C.byref(o), C.byref(ms)), "g3_autotune")
+    return {"threads": o.threads, "dense_face_max": o.dense_face_max, "ms": ms.value}
 
 
 def aca3_compress_batch(ctx: Context, trees, freqs, kernel: str = "slp", scheme: str = "colloc7",

@@ -22,7 +22,8 @@ LIB = os.path.join(LIBDIR, "libg3aca.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_aca_sep.cu", "g3_apply.cu", "g3_api.cu",
+CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_aca_sep.cu", "g3_aca_gal.cu", "g3_apply.cu",
+              "g3_api.cu",
               "g3_probe.cu", "g3_mlp.cu"]
 CPP_SOURCES = ["g3_tree.cpp"]
 

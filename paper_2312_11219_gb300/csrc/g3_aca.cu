@@ -16,11 +16,13 @@ namespace g3 {
 G3_ACA_EXTERN_KIND(G3_SLP)
 G3_ACA_EXTERN_KIND(G3_DLP)
 G3_ACA_EXTERN_KIND(G3_SEPARABLE)
+G3_ACA_EXTERN_KIND(G3_GAL_SLP)
 
 template <class T, int NT, bool DENSE>
 static g3_status launch_kind(g3_ctx* ctx, int kernel, AcaArgs<T>& A, int grid, size_t smem) {
     if (kernel == G3_SLP) return launch_aca_t<G3_SLP, T, NT, DENSE>(ctx, A, grid, smem);
     if (kernel == G3_DLP) return launch_aca_t<G3_DLP, T, NT, DENSE>(ctx, A, grid, smem);
+    if (kernel == G3_GAL_SLP) return launch_aca_t<G3_GAL_SLP, T, NT, DENSE>(ctx, A, grid, smem);
     return launch_aca_t<G3_SEPARABLE, T, NT, DENSE>(ctx, A, grid, smem);
 }
 
@@ -28,6 +30,7 @@ template <class T, int NT, bool DENSE>
 static int occupancy_kind(int kernel, size_t smem) {
     if (kernel == G3_SLP) return occupancy<G3_SLP, T, NT, DENSE>(smem);
     if (kernel == G3_DLP) return occupancy<G3_DLP, T, NT, DENSE>(smem);
+    if (kernel == G3_GAL_SLP) return occupancy<G3_GAL_SLP, T, NT, DENSE>(smem);
     return occupancy<G3_SEPARABLE, T, NT, DENSE>(smem);
 }
 
@@ -483,8 +486,9 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
 
 g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel, int scheme,
                   double eps3, const g3_opts& o, const void* sep_a, const void* sep_b, const void* sep_c, int sep_R) {
-    if (scheme != G3_COLLOC7 && kernel != G3_SEPARABLE)
-        return fail(G3_EUNSUPPORTED, "aca3_compress: only G3_COLLOC7 is implemented");
+    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+        return fail(G3_EUNSUPPORTED, "aca3_compress: the Galerkin scheme is implemented for G3_SLP");
+    if (scheme == G3_GALERKIN4x4) kernel = G3_GAL_SLP;
     if (fa->Ku > KU_MAX) return fail(G3_EINVAL, "aca3_compress: %d unique frequencies exceed %d", fa->Ku, KU_MAX);
     std::vector<AcaJob> jobs(1);
     jobs[0].t = t;
@@ -496,7 +500,9 @@ g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* 
 
 g3_status run_aca_batch(g3_ctx* ctx, const g3_tree* const* trees, const g3_freqs* const* freqs, int n,
                         g3_factors* const* fas, int kernel, int scheme, double eps3, const g3_opts& o) {
-    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "aca3_compress_batch: only G3_COLLOC7 is implemented");
+    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+        return fail(G3_EUNSUPPORTED, "aca3_compress_batch: the Galerkin scheme is implemented for G3_SLP");
+    if (scheme == G3_GALERKIN4x4) kernel = G3_GAL_SLP;
     std::vector<AcaJob> jobs(n);
     for (int j = 0; j < n; ++j) {
         if (fas[j]->Ku > KU_MAX)

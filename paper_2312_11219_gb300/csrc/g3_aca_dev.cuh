@@ -239,6 +239,15 @@ __device__ __forceinline__ Cx<T> ent(const AcaArgs<T>& A, int gi, int gj, int k)
             cfma(acc, cmul(a, b), c);
         }
         return acc;
+    } else if constexpr (KER == G3_GAL_SLP) {
+        // admissible blocks never hold pairs with a common vertex
+        if constexpr (sizeof(T) == 4) {
+            const float2 s = A.sf[k];
+            return gal_regular<T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        } else {
+            const double2 s = A.sd[k];
+            return gal_regular<T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        }
     } else {
         if constexpr (sizeof(T) == 4) {
             const float2 s = A.sf[k];
@@ -298,6 +307,29 @@ template <int KER, class T>
 __device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, int k, int part, int G) {
     if constexpr (KER == G3_SEPARABLE) {
         return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
+    } else if constexpr (KER == G3_GAL_SLP) {
+        // 16 terms dealt round-robin to the gang's parts
+        Cx<T> acc{0, 0};
+        T sre, sim;
+        if constexpr (sizeof(T) == 4) {
+            const float2 s = A.sf[k];
+            sre = s.x;
+            sim = s.y;
+        } else {
+            const double2 s = A.sd[k];
+            sre = s.x;
+            sim = s.y;
+        }
+        for (int t = part; t < 16; t += G) {
+            Cx<T> v;
+            if constexpr (sizeof(T) == 4)
+                v = gal_q(A.gf, gi, gj, t, sre, sim);
+            else
+                v = gal_q(A.gd, gi, gj, t, sre, sim);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        return acc;
     } else {
         if (G >= 8) {
             if (part >= 7) return Cx<T>{0, 0};
@@ -1652,7 +1684,8 @@ g3_status launch_aca_t(g3_ctx* ctx, AcaArgs<T>& A, int grid, size_t smem) {
     auto kfn = k_aca3<KER, T, NT, DENSE>;
     G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kfn<<<grid, NT, smem, ctx->stream>>>(A);
-    ctx->count(KER == G3_SEPARABLE ? (DENSE ? "k_aca3_dense_separable" : "k_aca3_separable")
+    ctx->count(KER == G3_SEPARABLE   ? (DENSE ? "k_aca3_dense_separable" : "k_aca3_separable")
+               : KER == G3_GAL_SLP ? (DENSE ? "k_aca3_dense_galerkin" : "k_aca3_galerkin")
                                    : (DENSE ? "k_aca3_dense" : "k_aca3"));
     G3_CUDA(cudaGetLastError());
     return G3_OK;

@@ -317,6 +317,14 @@ g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, co
         cudaError_t e = cudaMemcpyAsync(t->d_perm.p, t->perm.data(), ne * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "build_cluster_tree: perm copy");
     }
+    if (st == G3_OK) {  // vertex ids in cluster order (Galerkin adjacency)
+        std::vector<int> tv(3 * (size_t)ne);
+        for (int p = 0; p < ne; ++p)
+            for (int k = 0; k < 3; ++k) tv[3 * (size_t)p + k] = t->tris[3 * (size_t)t->perm[p] + k];
+        cudaError_t e = t->d_tv.alloc(tv.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(t->d_tv.p, tv.data(), tv.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "build_cluster_tree: vertex ids");
+    }
     if (st == G3_OK) st = launch_geometry(ctx, t);
     if (st != G3_OK) {
         delete t;
@@ -420,7 +428,8 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     *out = nullptr;
     G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "assemble_near: bad kernel or precision");
     G3_CHECK(scheme == G3_COLLOC7 || scheme == G3_GALERKIN4x4, "assemble_near: bad scheme");
-    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "assemble_near: only G3_COLLOC7 is implemented");
+    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+        return fail(G3_EUNSUPPORTED, "assemble_near: the Galerkin scheme is implemented for G3_SLP");
     G3_TRY(use_device(ctx));
     g3_near* nf = new (std::nothrow) g3_near();
     if (!nf) return fail(G3_ENOMEM, "assemble_near: out of host memory");
@@ -431,6 +440,7 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     nf->kernel = kernel;
     nf->Ku = f->Ku;
     nf->K = f->K;
+    nf->scheme = scheme;
     nf->order = t->near_index;
     std::stable_sort(nf->order.begin(), nf->order.end(), [t](int a, int b) {
         const int32_t* x = &t->blocks[5 * (size_t)a];
@@ -466,11 +476,40 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
             delete nf;
             return fail(G3_EINVAL, "assemble_near: element %d has no diagonal near block", p);
         }
+    // Galerkin: the pairs with a common vertex (Sauter-Schwab); they all lie
+    // in near blocks (a far block's clusters have disjoint boxes)
+    std::vector<SsPair> ss;
+    if (scheme == G3_GALERKIN4x4) {
+        std::vector<int> tv(3 * (size_t)t->ne);
+        for (int p = 0; p < t->ne; ++p)
+            for (int k = 0; k < 3; ++k) tv[3 * (size_t)p + k] = t->tris[3 * (size_t)t->perm[p] + k];
+        for (size_t b = 0; b < rg.size(); ++b) {
+            const BlockRange& r = rg[b];
+            const int M = r.re - r.rb, N = r.ce - r.cb;
+            for (int j = r.cb; j < r.ce; ++j)
+                for (int i = r.rb; i < r.re; ++i) {
+                    SsPair q{};
+                    q.cas = ss_classify(&tv[3 * (size_t)i], &tv[3 * (size_t)j], i == j, q.px, q.py);
+                    if (q.cas == SS_REGULAR) continue;
+                    q.i = i;
+                    q.j = j;
+                    q.stride = M * N;
+                    q.off = nf->offs[b] + (long long)(j - r.cb) * M + (i - r.rb);  // [k][j][i]
+                    ss.push_back(q);
+                }
+        }
+        nf->n_ss = (int)ss.size();
+    }
     const size_t esz = prec == G3_MIXED ? 8 : 16;
     g3_status st = G3_OK;
     auto chk = [&](cudaError_t e, const char* w) {
         if (st == G3_OK && e != cudaSuccess) st = cuda_fail(e, w);
     };
+    if (!ss.empty()) {
+        chk(nf->d_ss.alloc(ss.size() * sizeof(SsPair)), "assemble_near: singular pairs");
+        if (st == G3_OK)
+            chk(cudaMemcpy(nf->d_ss.p, ss.data(), ss.size() * sizeof(SsPair), cudaMemcpyHostToDevice), "copy");
+    }
     chk(nf->data.alloc((size_t)off * esz), "assemble_near: near-field storage");
     chk(nf->d_ranges.alloc(rg.size() * sizeof(BlockRange)), "assemble_near: ranges");
     chk(nf->d_offs.alloc(nf->offs.size() * sizeof(long long)), "assemble_near: offsets");
@@ -587,6 +626,55 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
         return st;
     }
     *out = fa;
+    return G3_OK;
+}
+
+static int log2_ceil(int x) {
+    int b = 0;
+    while ((1 << b) < x) ++b;
+    return b;
+}
+
+g3_status g3_autotune(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
+                      g3_precision prec, double eps3, g3_opts* opts, double* best_ms) {
+    G3_CHECK(ctx && t && f && opts, "g3_autotune: NULL argument");
+    G3_CHECK(kernel == G3_SLP || kernel == G3_DLP, "g3_autotune: kernel must be G3_SLP or G3_DLP");
+    G3_CHECK(valid_prec(prec), "g3_autotune: bad precision");
+    G3_CHECK(eps3 > 0 && eps3 < 1, "g3_autotune: eps3 = %g outside (0, 1)", eps3);
+    const int side = std::max(t->max_far_m, t->max_far_n);
+    const long long key = (((long long)log2_ceil(f->Ku) * 32 + log2_ceil(std::max(side, 1))) * 8 + kernel) * 8 +
+                          scheme * 2 + prec;
+    if (best_ms) *best_ms = 0.0;
+    auto hit = ctx->tune_cache.find(key);
+    if (hit != ctx->tune_cache.end()) {
+        opts->threads = hit->second.first;
+        opts->dense_face_max = hit->second.second;
+        return G3_OK;
+    }
+    G3_TRY(use_device(ctx));
+    const int threads[2] = {256, 512};
+    const int dmax[3] = {24 * 24, 48 * 48, 64 * 64};
+    double best = -1.0;
+    int bt = 256, bd = 48 * 48;
+    for (int a = 0; a < (prec == G3_MIXED ? 2 : 1); ++a)
+        for (int b = 0; b < 3; ++b) {
+            g3_opts o = *opts;
+            o.threads = threads[a];
+            o.dense_face_max = dmax[b];
+            g3_factors* fa = nullptr;
+            G3_TRY(aca3_compress(ctx, t, f, kernel, scheme, prec, eps3, &o, &fa));
+            const double ms = fa->stats.ms;
+            g3_factors_free(fa);
+            if (best < 0 || ms < best) {
+                best = ms;
+                bt = threads[a];
+                bd = dmax[b];
+            }
+        }
+    ctx->tune_cache[key] = {bt, bd};
+    opts->threads = bt;
+    opts->dense_face_max = bd;
+    if (best_ms) *best_ms = best;
     return G3_OK;
 }
 

@@ -253,6 +253,97 @@ __global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool
         }
 }
 
+// Far field, blocks with dense faces (small blocks): one warp per block, no
+// block-wide barrier.  Crosses in groups of PG: the group's fibers are staged
+// in the warp's slice of shared memory; lane j forms x_p[j] = sum_k f_p[k] w_k[j]
+// and zc_p[j] = sum_k f_p[k] conj(w_k'[j]) for the group in one pass over W;
+// lane i then adds sum_p (H_p x_p)[i] + conj((H_p zc_p)[i]) for its rows.
+template <class T, int NW, int PG, int MQ>
+__global__ void __launch_bounds__(NW * 32) k_apply_far_dense(const Cx<T>* __restrict__ pool,
+                                                            const CrossRec* __restrict__ rec,
+                                                            const int* __restrict__ r3,
+                                                            const BlockRange* __restrict__ ranges,
+                                                            const int* __restrict__ list, int n, int Cmax, int Ku,
+                                                            int E, const Cx<T>* __restrict__ Wf,
+                                                            const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y,
+                                                            int nmax) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * NW + warp;
+    if (bi >= n) return;  // the whole warp: no block-wide synchronisation below
+    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * (PG * Ku + 2 * PG * nmax);
+    Cx<T>* xs = fg + PG * Ku;
+    Cx<T>* zs = xs + PG * nmax;
+    const int blk = list[bi];
+    const BlockRange br = ranges[blk];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const int nc = r3[blk];
+    Cx<T> acc[MQ];
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) acc[q] = Cx<T>{0, 0};
+    for (int g0 = 0; g0 < nc; g0 += PG) {
+        const int np = min(PG, nc - g0);
+        for (int e = lane; e < PG * Ku; e += 32) {
+            const int p = e / Ku, k = e - p * Ku;
+            Cx<T> v{0, 0};
+            if (p < np) v = pool[rec[(size_t)blk * Cmax + g0 + p].off + (long long)M * N + k];
+            fg[e] = v;
+        }
+        __syncwarp();
+        for (int j0 = 0; j0 < N; j0 += 32) {
+            const int j = j0 + lane;
+            Cx<T> x[PG], z[PG];
+#pragma unroll
+            for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
+            if (j < N) {
+                const Cx<T>* wf = Wf + br.cb + j;
+                const Cx<T>* wc = Wc + br.cb + j;
+                for (int k = 0; k < Ku; ++k) {
+                    const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
+#pragma unroll
+                    for (int p = 0; p < PG; ++p) {
+                        const Cx<T> f = fg[p * Ku + k];
+                        cfma(x[p], f, a);
+                        cfmac(z[p], f, b);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < PG; ++p) {
+                    xs[p * nmax + j] = x[p];
+                    zs[p * nmax + j] = z[p];
+                }
+            }
+        }
+        __syncwarp();
+        for (int p = 0; p < np; ++p) {
+            const Cx<T>* H = pool + rec[(size_t)blk * Cmax + g0 + p].off;
+#pragma unroll
+            for (int q = 0; q < MQ; ++q) {
+                const int i = lane + 32 * q;
+                if (i < M) {
+                    Cx<T> s1{0, 0}, s2{0, 0};
+                    for (int j = 0; j < N; ++j) {
+                        const Cx<T> h = H[i + (long long)j * M];
+                        cfma(s1, h, xs[p * nmax + j]);
+                        cfma(s2, h, zs[p * nmax + j]);
+                    }
+                    acc[q].x += s1.x + s2.x;  // s1 + conj(s2)
+                    acc[q].y += s1.y - s2.y;
+                }
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int i = lane + 32 * q;
+        if (i < M) {
+            atomicAdd(&y[br.rb + i].x, acc[q].x);
+            atomicAdd(&y[br.rb + i].y, acc[q].y);
+        }
+    }
+}
+
 template <class T, class TO>
 __global__ void k_apply_finish(int E, const int* __restrict__ perm, const Cx<T>* __restrict__ y, Cx<TO>* __restrict__ Y) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,17 +352,6 @@ __global__ void k_apply_finish(int E, const int* __restrict__ perm, const Cx<T>*
     Y[perm[p]] = Cx<TO>{(TO)v.x, (TO)v.y};
 }
 
-// largest N_b over blocks holding a dense cross (shared-memory size of k_apply_far)
-static int dense_n_max(const g3_factors* fa) {
-    int n = 0;
-    for (int b = 0; b < fa->n_far; ++b)
-        for (int p = 0; p < fa->r3[b]; ++p)
-            if (fa->rec[(size_t)b * fa->Cmax + p].r < 0) {
-                n = std::max(n, fa->ranges[b].ce - fa->ranges[b].cb);
-                break;
-            }
-    return n;
-}
 
 // near-field launch: grid (row clusters) x (frequency chunks), about 16 CTAs
 // per SM so that the last wave is short
@@ -297,29 +377,67 @@ static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near*
     return G3_OK;
 }
 
-// far-field launch over the n blocks in d_list (device), block ranges in d_ranges
+// far-field launches: the blocks with dense faces (all crosses of a block
+// are of one kind) by the warp-per-block kernel, the others by the
+// CTA-per-block kernel.  d_list: device space for n_far ints (filled here);
+// d_ranges: the block ranges on the device.
 template <class T>
-static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, const int* d_list, int n,
-                                  const BlockRange* d_ranges, int Ku, int E, const Cx<T>* Wf, const Cx<T>* Wc,
-                                  Cx<T>* y) {
-    constexpr int NT = 128;
-    constexpr int PG = sizeof(T) == 4 ? 16 : 4;
-    const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
-    int mmax = 0;
-    for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
-    const int ym = std::min(mmax, ysmem_max);
-    const int dn = dense_n_max(fa);
-    const int rmax = std::max(1, (int)fa->stats.face_rank_max);
-    const size_t smem = ((size_t)PG * Ku + (size_t)PG * rmax * 2 + 2 * (size_t)PG * dn) * sizeof(Cx<T>) +
-                        2 * (size_t)ym * sizeof(T);
-    if (smem > ctx->smem_optin)
-        return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
-    G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_apply_far<T, NT, PG><<<n, NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
-                                                         fa->d_r3.as<int>(), d_ranges, d_list, fa->Cmax, Ku, E, Wf,
-                                                         Wc, y, ym, dn, rmax);
-    ctx->count("k_apply_far");
-    G3_CUDA(cudaGetLastError());
+static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, int* d_list, const BlockRange* d_ranges, int Ku,
+                                  int E, const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y) {
+    std::vector<int> lst;
+    lst.reserve(fa->n_far);
+    int mmax_dense = 0, nmax_dense = 0;
+    for (int b = 0; b < fa->n_far; ++b)
+        if (fa->r3[b] > 0 && fa->rec[(size_t)b * fa->Cmax].r < 0) {
+            lst.push_back(b);
+            mmax_dense = std::max(mmax_dense, fa->ranges[b].re - fa->ranges[b].rb);
+            nmax_dense = std::max(nmax_dense, fa->ranges[b].ce - fa->ranges[b].cb);
+        }
+    const int n_dense = (int)lst.size();
+    for (int b = 0; b < fa->n_far; ++b)
+        if (fa->r3[b] > 0 && fa->rec[(size_t)b * fa->Cmax].r >= 0) lst.push_back(b);
+    const int n_low = (int)lst.size() - n_dense;
+    if (lst.empty()) return G3_OK;
+    G3_CUDA(cudaMemcpyAsync(d_list, lst.data(), lst.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    if (n_dense > 0) {
+        constexpr int NW = 8, PGW = 4;
+        const size_t smem = (size_t)NW * (PGW * Ku + 2 * PGW * nmax_dense) * sizeof(Cx<T>);
+        if (smem > ctx->smem_optin || mmax_dense > 96)
+            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks of %d x %d exceed the apply kernel's limits",
+                        mmax_dense, nmax_dense);
+        const int grid = (n_dense + NW - 1) / NW;
+        if (mmax_dense <= 32) {
+            G3_CUDA(cudaFuncSetAttribute(k_apply_far_dense<T, NW, PGW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_apply_far_dense<T, NW, PGW, 1><<<grid, NW * 32, smem, ctx->stream>>>(
+                fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges, d_list, n_dense,
+                fa->Cmax, Ku, E, Wf, Wc, y, nmax_dense);
+        } else {
+            G3_CUDA(cudaFuncSetAttribute(k_apply_far_dense<T, NW, PGW, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_apply_far_dense<T, NW, PGW, 3><<<grid, NW * 32, smem, ctx->stream>>>(
+                fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges, d_list, n_dense,
+                fa->Cmax, Ku, E, Wf, Wc, y, nmax_dense);
+        }
+        ctx->count("k_apply_far_dense");
+        G3_CUDA(cudaGetLastError());
+    }
+    if (n_low > 0) {
+        constexpr int NT = 128;
+        constexpr int PG = sizeof(T) == 4 ? 16 : 4;
+        const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
+        int mmax = 0;
+        for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
+        const int ym = std::min(mmax, ysmem_max);
+        const int rmax = std::max(1, (int)fa->stats.face_rank_max);
+        const size_t smem = ((size_t)PG * Ku + (size_t)PG * rmax * 2) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+        if (smem > ctx->smem_optin)
+            return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
+        G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_apply_far<T, NT, PG><<<n_low, NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                                 fa->d_r3.as<int>(), d_ranges, d_list + n_dense,
+                                                                 fa->Cmax, Ku, E, Wf, Wc, y, ym, 0, rmax);
+        ctx->count("k_apply_far");
+        G3_CUDA(cudaGetLastError());
+    }
     return G3_OK;
 }
 
@@ -351,20 +469,13 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
     G3_CUDA(cudaEventRecord(e2, ctx->stream));
     if (fa && fa->n_far > 0) {
-        std::vector<int> list;
-        for (int b = 0; b < fa->n_far; ++b)
-            if (fa->r3[b] > 0) list.push_back(b);
-        if (!list.empty()) {
-            DevBuf d_list, d_ranges;
-            G3_CUDA(d_list.alloc(list.size() * sizeof(int)));
-            G3_CUDA(d_ranges.alloc(fa->ranges.size() * sizeof(BlockRange)));
-            G3_CUDA(cudaMemcpyAsync(d_list.p, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-            G3_CUDA(cudaMemcpyAsync(d_ranges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
-                                    cudaMemcpyHostToDevice, ctx->stream));
-            G3_TRY_NA(launch_apply_far<T>(ctx, fa, d_list.as<int>(), (int)list.size(), d_ranges.as<BlockRange>(), Ku,
-                                          E, Wf, Wc, y));
-            G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
-        }
+        DevBuf d_list, d_ranges;
+        G3_CUDA(d_list.alloc(fa->n_far * sizeof(int)));
+        G3_CUDA(d_ranges.alloc(fa->ranges.size() * sizeof(BlockRange)));
+        G3_CUDA(cudaMemcpyAsync(d_ranges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
+                                cudaMemcpyHostToDevice, ctx->stream));
+        G3_TRY_NA(launch_apply_far<T>(ctx, fa, d_list.as<int>(), d_ranges.as<BlockRange>(), Ku, E, Wf, Wc, y));
+        G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
     }
     {
         int blocks = (E + 255) / 256;
@@ -427,10 +538,6 @@ static g3_status noalloc_scratch(int device, void** out) {
     return G3_OK;
 }
 
-__global__ void k_iota(int* p, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = i;
-}
 
 template <class T>
 static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa,
@@ -475,9 +582,7 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         // ranges come from the factors' host copy, the ranks from the device
         G3_CUDA(cudaMemcpyAsync(ranges, fa->ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice,
                                 ctx->stream));
-        k_iota<<<(n_far + 255) / 256, 256, 0, ctx->stream>>>(list, n_far);
-        ctx->count("k_iota");
-        G3_TRY_NA(launch_apply_far<T>(ctx, fa, list, n_far, ranges, Ku, E, Wf, Wc, y));
+        G3_TRY_NA(launch_apply_far<T>(ctx, fa, list, ranges, Ku, E, Wf, Wc, y));
     }
     {
         int blocks = (E + 255) / 256;

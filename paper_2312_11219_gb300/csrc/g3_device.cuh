@@ -240,6 +240,168 @@ __device__ __forceinline__ Cx<T> colloc_entry(const GeomF& gf, const GeomD& gd, 
     return pair_eval<KER>(p, sre, sim);
 }
 
+// ---- Galerkin single layer, piecewise-constant elements ---------------------------
+// V[i, j](s) = int_{tau_i} int_{tau_j} exp(-s |x - y|) / (4 pi |x - y|) dy dx.
+// Pairs without a common vertex: the 4-point conical-product rule on both
+// triangles (16 kernel evaluations), points as offsets from the centroids
+// (centroid difference in float-float for float32).
+template <class G>
+__device__ __forceinline__ auto q4off(const G& g, int q, int k, int e) {
+    return g.q4[(q * 3 + k) * g.E + e];
+}
+template <class G>
+__device__ __forceinline__ auto q4wt(const G& g, int q, int e) {
+    return g.w4[q * g.E + e];
+}
+
+template <class T>
+struct Pair16 {
+    T r[16];
+    T a[16];
+};
+
+template <class G, class T>
+__device__ __forceinline__ void gal_setup(const G& g, int i, int j, Pair16<T>& p) {
+    T d[3];
+    cdiff(g, i, j, d);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const T xa0 = d[0] + q4off(g, a, 0, i), xa1 = d[1] + q4off(g, a, 1, i), xa2 = d[2] + q4off(g, a, 2, i);
+        const T wa = q4wt(g, a, i) * (T)G3_INV4PI;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const T rx = xa0 - q4off(g, b, 0, j), ry = xa1 - q4off(g, b, 1, j), rz = xa2 - q4off(g, b, 2, j);
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            const T ri = krsqrt(r2);
+            p.r[a * 4 + b] = r2 * ri;
+            p.a[a * 4 + b] = wa * q4wt(g, b, j) * ri;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ Cx<T> gal_eval(const Pair16<T>& p, T sre, T sim) {
+    Cx<T> acc{0, 0};
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const T m = p.a[q] * kexp(-sre * p.r[q]);
+        T sn, cs;
+        ksincos(sim * p.r[q], &sn, &cs);
+        acc.x += m * cs;
+        acc.y -= m * sn;
+    }
+    return acc;
+}
+
+// one of the 16 terms (t = 4 a + b)
+template <class G, class T>
+__device__ __forceinline__ Cx<T> gal_q(const G& g, int i, int j, int t, T sre, T sim) {
+    T d[3];
+    cdiff(g, i, j, d);
+    const int a = t >> 2, b = t & 3;
+    const T rx = d[0] + q4off(g, a, 0, i) - q4off(g, b, 0, j);
+    const T ry = d[1] + q4off(g, a, 1, i) - q4off(g, b, 1, j);
+    const T rz = d[2] + q4off(g, a, 2, i) - q4off(g, b, 2, j);
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    const T ri = krsqrt(r2);
+    const T r = r2 * ri;
+    const T m = q4wt(g, a, i) * q4wt(g, b, j) * (T)G3_INV4PI * ri * kexp(-sre * r);
+    T sn, cs;
+    ksincos(sim * r, &sn, &cs);
+    return {m * cs, -m * sn};
+}
+
+template <class T>
+__device__ __forceinline__ Cx<T> gal_regular(const GeomF& gf, const GeomD& gd, int i, int j, T sre, T sim) {
+    Pair16<T> p;
+    if constexpr (sizeof(T) == 4)
+        gal_setup(gf, i, j, p);
+    else
+        gal_setup(gd, i, j, p);
+    return gal_eval(p, sre, sim);
+}
+
+// Pairs with a common vertex, a common edge or identical panels: the
+// Sauter-Schwab transformations (Sauter and Schwab, Boundary Element Methods,
+// Section 5.2).  Reference triangle {0 <= x2 <= x1 <= 1}; panel map
+// chi(x1, x2) = P0 + x1 (P1 - P0) + x2 (P2 - P1), Jacobian 2 |tau|.  The
+// vertices of both panels are ordered with the shared ones first (same order;
+// a common edge is x2 = 0 of both maps).  The integrand at (xi, e1, e2, e3) in
+// [0, 1]^4 carries the factor returned below; its 1/r singularity is cancelled.
+// Regions: identical 6, common edge 5, common vertex 2.
+__host__ __device__ inline int ss_regions(int cas) { return cas == SS_IDENTICAL ? 6 : (cas == SS_EDGE ? 5 : 2); }
+
+__device__ inline double ss_map(int cas, int m, double xi, double e1, double e2, double e3, double xh[2],
+                                double yh[2]) {
+    if (cas == SS_IDENTICAL) {
+        const double f = xi * xi * xi * e1 * e1 * e2;
+        switch (m) {
+            case 0: xh[0] = xi; xh[1] = xi * (1 - e1 + e1 * e2); yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * (1 - e1); break;
+            case 1: yh[0] = xi; yh[1] = xi * (1 - e1 + e1 * e2); xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * (1 - e1); break;
+            case 2: xh[0] = xi; xh[1] = xi * e1 * (1 - e2 + e2 * e3); yh[0] = xi * (1 - e1 * e2); yh[1] = xi * e1 * (1 - e2); break;
+            case 3: yh[0] = xi; yh[1] = xi * e1 * (1 - e2 + e2 * e3); xh[0] = xi * (1 - e1 * e2); xh[1] = xi * e1 * (1 - e2); break;
+            case 4: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * (1 - e2 * e3); yh[0] = xi; yh[1] = xi * e1 * (1 - e2); break;
+            default: yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * e1 * (1 - e2 * e3); xh[0] = xi; xh[1] = xi * e1 * (1 - e2); break;
+        }
+        return f;
+    }
+    if (cas == SS_EDGE) {
+        const double f1 = xi * xi * xi * e1 * e1;
+        switch (m) {
+            case 0: xh[0] = xi; xh[1] = xi * e1 * e3; yh[0] = xi * (1 - e1 * e2); yh[1] = xi * e1 * (1 - e2); return f1;
+            case 1: xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * e1 * e2 * (1 - e3); break;
+            case 2: xh[0] = xi * (1 - e1 * e2); xh[1] = xi * e1 * (1 - e2); yh[0] = xi; yh[1] = xi * e1 * e2 * e3; break;
+            case 3: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * e2 * (1 - e3); yh[0] = xi; yh[1] = xi * e1; break;
+            default: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * (1 - e2 * e3); yh[0] = xi; yh[1] = xi * e1 * e2; break;
+        }
+        return f1 * e2;
+    }
+    // common vertex
+    if (m == 0) {
+        xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * e2; yh[1] = xi * e2 * e3;
+    } else {
+        yh[0] = xi; yh[1] = xi * e1; xh[0] = xi * e2; xh[1] = xi * e2 * e3;
+    }
+    return xi * xi * xi * e2;
+}
+
+// geometry of one Sauter-Schwab point: r = |chi_x(xh) - chi_y(yh)| and the
+// weight w = (Gauss weight) (region factor) (2|tau_x|)(2|tau_y|) / (4 pi r),
+// all float64 (the two points can be very close)
+struct SsPanels {
+    double P[3][3], Q[3][3];   // vertices of tau_x and tau_y in the Sauter-Schwab order
+    double jac;                // (2 |tau_x|)(2 |tau_y|) / (4 pi)
+};
+
+__device__ inline void ss_panels(const GeomD& g, int i, int j, const int8_t* px, const int8_t* py, SsPanels& S) {
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            S.P[a][k] = g.v[(px[a] * 3 + k) * g.E + i];
+            S.Q[a][k] = g.v[(py[a] * 3 + k) * g.E + j];
+        }
+    auto area2 = [](const double V[3][3]) {
+        double u[3] = {V[1][0] - V[0][0], V[1][1] - V[0][1], V[1][2] - V[0][2]};
+        double w[3] = {V[2][0] - V[0][0], V[2][1] - V[0][1], V[2][2] - V[0][2]};
+        double c0 = u[1] * w[2] - u[2] * w[1], c1 = u[2] * w[0] - u[0] * w[2], c2 = u[0] * w[1] - u[1] * w[0];
+        return sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    };
+    S.jac = area2(S.P) * area2(S.Q) * G3_INV4PI;
+}
+
+__device__ inline void ss_point(const SsPanels& S, int cas, int m, const double g4[4], double gw, double& r,
+                                double& w) {
+    double xh[2], yh[2];
+    const double f = ss_map(cas, m, g4[0], g4[1], g4[2], g4[3], xh, yh);
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double x = S.P[0][k] + xh[0] * (S.P[1][k] - S.P[0][k]) + xh[1] * (S.P[2][k] - S.P[1][k]);
+        const double y = S.Q[0][k] + yh[0] * (S.Q[1][k] - S.Q[0][k]) + yh[1] * (S.Q[2][k] - S.Q[1][k]);
+        d2 += (x - y) * (x - y);
+    }
+    r = sqrt(d2);
+    w = r > 0.0 ? gw * f * S.jac / r : 0.0;
+}
+
 // ---- block reductions ------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -85,6 +85,74 @@ struct GeomD {
     const double* gl;  // 24-point Gauss-Legendre nodes [24] then weights [24] on [-1, 1]
 };
 
+#ifdef __CUDACC__
+#define G3_HD __host__ __device__
+#else
+#define G3_HD
+#endif
+
+// internal kernel kind of the Galerkin single layer (the C ABI passes G3_SLP
+// with G3_GALERKIN4x4)
+constexpr int G3_GAL_SLP = 3;
+
+// Galerkin pairs with a common vertex: classification and vertex order for
+// the Sauter-Schwab rules (shared vertices first, in the same order in both
+// panels; a common edge keeps the orientation it has in the first panel)
+enum : int { SS_REGULAR = 0, SS_VERTEX = 1, SS_EDGE = 2, SS_IDENTICAL = 3 };
+
+G3_HD inline int ss_classify(const int* a, const int* b, bool same, int8_t px[3], int8_t py[3]) {
+    if (same) {
+        for (int k = 0; k < 3; ++k) px[k] = py[k] = (int8_t)k;
+        return SS_IDENTICAL;
+    }
+    int ia[3], ib[3], nc = 0;
+    for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y)
+            if (a[x] == b[y]) {
+                ia[nc] = x;
+                ib[nc] = y;
+                ++nc;
+            }
+    if (nc == 0) return SS_REGULAR;
+    if (nc == 1) {
+        px[0] = (int8_t)ia[0];
+        py[0] = (int8_t)ib[0];
+        for (int k = 0, u = 1, v = 1; k < 3; ++k) {
+            if (k != ia[0]) px[u++] = (int8_t)k;
+            if (k != ib[0]) py[v++] = (int8_t)k;
+        }
+        return SS_VERTEX;
+    }
+    if (nc == 2) {
+        int e0 = 0, e1 = 1;
+        if ((ia[0] + 1) % 3 != ia[1]) {
+            e0 = 1;
+            e1 = 0;
+        }
+        px[0] = (int8_t)ia[e0];
+        px[1] = (int8_t)ia[e1];
+        px[2] = (int8_t)(3 - ia[0] - ia[1]);
+        py[0] = (int8_t)ib[e0];
+        py[1] = (int8_t)ib[e1];
+        py[2] = (int8_t)(3 - ib[0] - ib[1]);
+        return SS_EDGE;
+    }
+    for (int k = 0; k < 3; ++k) {  // three common vertices: the same triangle
+        px[k] = (int8_t)k;
+        py[k] = (int8_t)ib[k];
+    }
+    return SS_IDENTICAL;
+}
+
+// one Galerkin near-field pair for the Sauter-Schwab kernel
+struct SsPair {
+    int i, j;          // cluster positions of tau_x, tau_y
+    int cas;           // SS_VERTEX, SS_EDGE or SS_IDENTICAL
+    int stride;        // M_b N_b: distance between frequencies in the block
+    long long off;     // near-field offset of the entry at the first frequency
+    int8_t px[3], py[3];
+};
+
 // synthetic separable tensor sum_t a[t][i] b[t][j] c[t][k] (complex, interleaved)
 template <class T>
 struct SepView {
@@ -125,6 +193,7 @@ struct g3_ctx {
     double last_apply_ms = 0, last_near_ms = 0;
     double pool_scale = 1.0;  // factor-pool size / estimate needed by earlier compressions
     double pool_scale_mlp = 1.0;  // the same for the predictor-based estimate
+    std::map<long long, std::pair<int, int>> tune_cache;  // autotuner: key -> (threads, dense_face_max)
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
     void count(const char* name, int64_t n = 1) {
         launches[name] += n;
@@ -161,6 +230,7 @@ struct g3_tree {
     int max_far_m = 0, max_far_n = 0;
     // device
     g3::DevBuf d_perm;             // int32 [ne]
+    g3::DevBuf d_tv;               // int32 [ne][3]: vertex ids of the element at each cluster position
     g3::DevBuf d_geom_f, d_geom_d; // packed SoA arrays
     g3::GeomF gf{};
     g3::GeomD gd{};
@@ -181,6 +251,9 @@ struct g3_near {
     g3::DevBuf d_row_start;
     g3::DevBuf d_diag_base;           // long long [ne]: offset of entry (p, p) at k = 0
     g3::DevBuf d_diag_mn;             // int [ne]: M_b * N_b of the diagonal block of p
+    g3::DevBuf d_ss;                  // SsPair [n_ss] (Galerkin)
+    int n_ss = 0;
+    int scheme = 0;
     const g3_freqs* freqs = nullptr;
     std::vector<int32_t> partner_u;   // unique index -> full index of partner (or -1)
 };

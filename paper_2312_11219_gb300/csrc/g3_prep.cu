@@ -243,6 +243,36 @@ g3_status launch_geometry(g3_ctx* ctx, g3_tree* t) {
     return G3_OK;
 }
 
+// n-point Gauss-Legendre nodes and weights on [0, 1] (Newton iteration on the
+// Legendre recurrence)
+static void gauss_legendre01(int n, double* x01, double* w01) {
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        x01[i] = 0.5 * (x + 1.0);
+        w01[i] = 1.0 / ((1.0 - x * x) * dp * dp);  // (2 / ((1 - x^2) P'^2)) / 2
+    }
+}
+
 // 24-point Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on
 // the Legendre recurrence), uploaded once per context.
 g3_status gl_table(g3_ctx* ctx) {
@@ -286,17 +316,52 @@ g3_status gl_table(g3_ctx* ctx) {
 // Diagnostic entries
 // ============================================================================
 
+// Gauss-Legendre rule of the Sauter-Schwab quadrature (n = SS_N per coordinate)
+constexpr int SS_N = 6;
+struct SsRule {
+    double x[SS_N], w[SS_N];
+};
+
 template <int KER, class T>
-__global__ void k_entries(GeomF gf, GeomD gd, const double2* __restrict__ sd, const int* __restrict__ rows,
-                          const int* __restrict__ cols, int n, const int* __restrict__ ku,
-                          const int* __restrict__ conj, int nk, double2* out) {
+__global__ void k_entries(GeomF gf, GeomD gd, const int* __restrict__ tv, SsRule gr, const double2* __restrict__ sd,
+                          const int* __restrict__ rows, const int* __restrict__ cols, int n,
+                          const int* __restrict__ ku, const int* __restrict__ conj, int nk, double2* out) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)n * nk) return;
     int pr = (int)(idx / nk), m = (int)(idx % nk);
     int i = rows[pr], j = cols[pr];
     double2 s = sd[ku[m]];
     Cx<T> v;
-    if (i == j && KER == G3_SLP) {  // self entries: float64 with the float64 frequency
+    if constexpr (KER == G3_GAL_SLP) {
+        int8_t px[3], py[3];
+        const int cas = ss_classify(tv + 3 * (size_t)i, tv + 3 * (size_t)j, i == j, px, py);
+        if (cas == 0) {
+            v = gal_regular<T>(gf, gd, i, j, (T)s.x, (T)s.y);
+        } else {  // Sauter-Schwab, one thread (diagnostic path)
+            SsPanels P;
+            ss_panels(gd, i, j, px, py, P);
+            Cx<T> acc{0, 0};
+            const int nr = ss_regions(cas);
+            for (int q = 0; q < SS_N * SS_N * SS_N * SS_N * nr; ++q) {
+                const int mreg = q / (SS_N * SS_N * SS_N * SS_N);
+                int rem = q % (SS_N * SS_N * SS_N * SS_N);
+                double g4[4], gw = 1.0;
+                for (int a = 3; a >= 0; --a) {
+                    g4[a] = gr.x[rem % SS_N];
+                    gw *= gr.w[rem % SS_N];
+                    rem /= SS_N;
+                }
+                double r, w;
+                ss_point(P, cas, mreg, g4, gw, r, w);
+                const T mm = (T)w * kexp(-(T)s.x * (T)r);
+                T sn, cs;
+                ksincos((T)s.y * (T)r, &sn, &cs);
+                acc.x += mm * cs;
+                acc.y -= mm * sn;
+            }
+            v = acc;
+        }
+    } else if (i == j && KER == G3_SLP) {  // self entries: float64 with the float64 frequency
         Cx<double> d = slp_self_f64(gd, i, s.x, s.y);
         v = Cx<T>{(T)d.x, (T)d.y};
     } else {
@@ -309,14 +374,21 @@ __global__ void k_entries(GeomF gf, GeomD gd, const double2* __restrict__ sd, co
 g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int kernel, int scheme, int prec,
                          const int* d_rows, const int* d_cols, int n, const int* d_ku, const int* d_conj, int nk,
                          double* d_out) {
-    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "g3_entries: only G3_COLLOC7 is implemented");
+    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+        return fail(G3_EUNSUPPORTED, "g3_entries: the Galerkin scheme is implemented for G3_SLP");
     long long tot = (long long)n * nk;
     int blocks = (int)((tot + 127) / 128);
     if (tot == 0) return G3_OK;
     const double2* sd = f->d_sd.as<double2>();
     double2* out = (double2*)d_out;
-#define G3_ENT(K, T) k_entries<K, T><<<blocks, 128, 0, ctx->stream>>>(t->gf, t->gd, sd, d_rows, d_cols, n, d_ku, d_conj, nk, out)
-    if (kernel == G3_SLP && prec == G3_MIXED) G3_ENT(G3_SLP, float);
+    SsRule gr;
+    gauss_legendre01(SS_N, gr.x, gr.w);
+    const int* tv = t->d_tv.as<int>();
+#define G3_ENT(K, T) \
+    k_entries<K, T><<<blocks, 128, 0, ctx->stream>>>(t->gf, t->gd, tv, gr, sd, d_rows, d_cols, n, d_ku, d_conj, nk, out)
+    if (scheme == G3_GALERKIN4x4 && prec == G3_MIXED) G3_ENT(G3_GAL_SLP, float);
+    else if (scheme == G3_GALERKIN4x4) G3_ENT(G3_GAL_SLP, double);
+    else if (kernel == G3_SLP && prec == G3_MIXED) G3_ENT(G3_SLP, float);
     else if (kernel == G3_SLP) G3_ENT(G3_SLP, double);
     else if (kernel == G3_DLP && prec == G3_MIXED) G3_ENT(G3_DLP, float);
     else if (kernel == G3_DLP) G3_ENT(G3_DLP, double);
@@ -351,15 +423,94 @@ __global__ void __launch_bounds__(256) k_near(GeomF gf, GeomD gd, const double2*
     for (int e = threadIdx.x; e < MN; e += blockDim.x) {
         int i = br.rb + e % M, j = br.cb + e / M;
         if (i == j) continue;
-        Pair7<T> p;
-        if constexpr (sizeof(T) == 4)
-            pair_setup<KER>(gf, i, j, p);
-        else
-            pair_setup<KER>(gd, i, j, p);
-        for (int kk = 0; kk < kn; ++kk) {
-            double2 s = sd[k0 + kk];
-            out[base + (long long)(k0 + kk) * MN + e] = pair_eval<KER, T>(p, (T)s.x, (T)s.y);
+        if constexpr (KER == G3_GAL_SLP) {
+            // regular rule for every off-diagonal pair; pairs with a common
+            // vertex are overwritten by k_near_ss
+            Pair16<T> p;
+            if constexpr (sizeof(T) == 4)
+                gal_setup(gf, i, j, p);
+            else
+                gal_setup(gd, i, j, p);
+            for (int kk = 0; kk < kn; ++kk) {
+                double2 s = sd[k0 + kk];
+                out[base + (long long)(k0 + kk) * MN + e] = gal_eval<T>(p, (T)s.x, (T)s.y);
+            }
+        } else {
+            Pair7<T> p;
+            if constexpr (sizeof(T) == 4)
+                pair_setup<KER>(gf, i, j, p);
+            else
+                pair_setup<KER>(gd, i, j, p);
+            for (int kk = 0; kk < kn; ++kk) {
+                double2 s = sd[k0 + kk];
+                out[base + (long long)(k0 + kk) * MN + e] = pair_eval<KER, T>(p, (T)s.x, (T)s.y);
+            }
         }
+    }
+}
+
+// Galerkin near-field entries of pairs with a common vertex, a common edge or
+// identical panels (Sauter-Schwab, SS_N^4 Gauss points per region): one CTA
+// per pair.  The points' distances and weights are formed once in float64
+// and kept in shared memory (as T); each frequency is then a sum over them
+// (exp and sincos in T) reduced across the CTA.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPair* __restrict__ pairs,
+                                                 const double2* __restrict__ sd, int Ku, Cx<T>* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* rs = reinterpret_cast<T*>(smem_raw);
+    const SsPair pr = pairs[blockIdx.x];
+    const int nq = SS_N * SS_N * SS_N * SS_N;
+    const int npts = nq * ss_regions(pr.cas);
+    T* ws = rs + npts;
+    __shared__ SsPanels P;
+    __shared__ T red[2][NT / 32];
+    if (threadIdx.x == 0) ss_panels(gd, pr.i, pr.j, pr.px, pr.py, P);
+    __syncthreads();
+    for (int q = threadIdx.x; q < npts; q += NT) {
+        const int mreg = q / nq;
+        int rem = q % nq;
+        double g4[4], gw = 1.0;
+        for (int a = 3; a >= 0; --a) {
+            g4[a] = gr.x[rem % SS_N];
+            gw *= gr.w[rem % SS_N];
+            rem /= SS_N;
+        }
+        double r, w;
+        ss_point(P, pr.cas, mreg, g4, gw, r, w);
+        rs[q] = (T)r;
+        ws[q] = (T)w;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < Ku; ++k) {
+        const double2 s = sd[k];
+        const T sre = (T)s.x, sim = (T)s.y;
+        T ax = 0, ay = 0;
+        for (int q = threadIdx.x; q < npts; q += NT) {
+            const T r = rs[q];
+            const T m = ws[q] * kexp(-sre * r);
+            T sn, cs;
+            ksincos(sim * r, &sn, &cs);
+            ax += m * cs;
+            ay -= m * sn;
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        if (lane == 0) {
+            red[0][wid] = ax;
+            red[1][wid] = ay;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T sx = 0, sy = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                sx += red[0][w];
+                sy += red[1][w];
+            }
+            out[pr.off + (long long)k * pr.stride] = Cx<T>{sx, sy};
+        }
+        __syncthreads();
     }
 }
 
@@ -382,10 +533,41 @@ __global__ void k_near_self(GeomD gd, const double2* __restrict__ sd, int E, int
     out[diag_base[p] + (long long)k * diag_mn[p]] = v;
 }
 
+// Galerkin: near-field pairs with a common vertex (the list of SsPair records
+// built on the host) by k_near_ss, after the regular rule for all pairs
+template <class T>
+static g3_status launch_near_galerkin(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf) {
+    const int nb = (int)nf->order.size();
+    constexpr int KCH = 16;
+    dim3 grid(nb, (f->Ku + KCH - 1) / KCH);
+    Cx<T>* o = reinterpret_cast<Cx<T>*>(nf->data.p);
+    k_near<G3_GAL_SLP, T, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, f->d_sd.as<double2>(),
+                                                               nf->d_ranges.as<BlockRange>(),
+                                                               nf->d_offs.as<long long>(), f->Ku, o);
+    ctx->count("k_near");
+    G3_CUDA(cudaGetLastError());
+    if (nf->n_ss > 0) {
+        SsRule gr;
+        gauss_legendre01(SS_N, gr.x, gr.w);
+        constexpr int NT = 256;
+        const size_t smem = 2 * (size_t)SS_N * SS_N * SS_N * SS_N * 6 * sizeof(T);
+        G3_CUDA(cudaFuncSetAttribute(k_near_ss<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_near_ss<T, NT><<<nf->n_ss, NT, smem, ctx->stream>>>(t->gd, gr, nf->d_ss.as<SsPair>(),
+                                                              f->d_sd.as<double2>(), f->Ku, o);
+        ctx->count("k_near_ss");
+        G3_CUDA(cudaGetLastError());
+    }
+    return G3_OK;
+}
+
 g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf, int kernel, int scheme) {
-    if (scheme != G3_COLLOC7) return fail(G3_EUNSUPPORTED, "assemble_near: only G3_COLLOC7 is implemented");
     const int nb = (int)nf->order.size();
     if (nb == 0) return G3_OK;
+    if (scheme == G3_GALERKIN4x4) {
+        if (kernel != G3_SLP) return fail(G3_EUNSUPPORTED, "assemble_near: the Galerkin scheme is implemented for G3_SLP");
+        return nf->prec == G3_MIXED ? launch_near_galerkin<float>(ctx, t, f, nf)
+                                    : launch_near_galerkin<double>(ctx, t, f, nf);
+    }
     constexpr int KCH = 16;
     dim3 grid(nb, (f->Ku + KCH - 1) / KCH);
     const double2* sd = f->d_sd.as<double2>();
