@@ -167,6 +167,10 @@ typedef struct {
     double ms_mlp;            /* device time of the block features + predictor forward     */
     int64_t face_check_restarts;  /* face ACAs continued after a failed sample check       */
     int64_t stop_check_overrides; /* 3D stops overruled by the sampled residual check      */
+    int64_t sub_cycles[10];   /* SM cycles of sub-steps (thread 0 of each CTA, diagnostics):
+                                 recompression Gram, Cholesky, core, Jacobi SVD, rest;
+                                 face ACA table set-up, residual rows, residual columns,
+                                 approximant norm, sample checks                           */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */
@@ -429,10 +433,10 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
  * cudaMalloc/cudaFree or other allocating routine is called.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture.  Problems needing more
- * scratch than 32 MiB (2 Ku M + M complex values plus 20 bytes per
- * admissible block) return G3_EINVAL.  All calls share the array: calls whose
- * work overlaps on the GPU (other streams, other threads) race and must be
- * serialised by the caller. */
+ * scratch than 32 MiB (2 Ku M + M complex values, 16 bytes per admissible
+ * block and 4 bytes per far-field work item) return G3_EINVAL.  All calls
+ * share the array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
 g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
                             void* Y, g3_dtype dtype);
 /* Device time (ms) of the last apply on this context and its algorithmic

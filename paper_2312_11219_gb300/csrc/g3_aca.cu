@@ -166,7 +166,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     G3_CUDA(d_ranges.alloc(n_far * sizeof(BlockRange)));
     G3_CUDA(d_queue.alloc(std::max(n_run, 1) * sizeof(int)));
     G3_CUDA(d_head.alloc(2 * sizeof(int)));
-    G3_CUDA(d_counters.alloc(16 * sizeof(unsigned long long)));
+    G3_CUDA(d_counters.alloc(32 * sizeof(unsigned long long)));
     G3_CUDA(d_ctr.alloc(sizeof(unsigned long long)));
     G3_CUDA(d_spill.alloc(std::max(n_far, 1) * sizeof(int)));
     G3_CUDA(d_spill_n.alloc(sizeof(int)));
@@ -214,11 +214,11 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     // dynamic shared memory arena, reused phase by phase: the four RS x RS
     // float64 matrices of the recompression (+ Gram staging), the pivot-search
     // tiles (2 RF TM complex T, TM = 64 float / 32 double) and the eq. (norm)
-    // staging (33 (32 + RF) complex T)
+    // staging ((NORM_RC + 1) (32 + RF) complex T)
     const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
                                 std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>));
     const size_t tile_bytes = 2 * (size_t)RF * (sizeof(T) == 4 ? 64 : 32) * sizeof(Cx<T>);
-    const size_t gram_bytes = 33 * (size_t)(32 + RF) * sizeof(Cx<T>);
+    const size_t gram_bytes = (NORM_RC<T> + 1) * (size_t)(32 + RF) * sizeof(Cx<T>);
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
     const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
@@ -268,10 +268,15 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     for (int q = 0; q < n_run; ++q) est += block_est(queue[q]);
     long long cap = (long long)(pf * scale * est);
     cap = std::max(cap, (long long)1 << 16);
+    // never ask for more than 85 % of the free device memory: an estimate
+    // above it is served by spill rounds instead
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b > 0)
+        cap = std::min(cap, std::max((long long)1 << 16, (long long)(0.85 * (double)free_b / sizeof(Cx<T>))));
     auto pool = std::make_shared<DevBuf>();
     G3_CUDA(pool->alloc((size_t)cap * sizeof(Cx<T>)));
     G3_CUDA(cudaMemsetAsync(d_head.p, 0, 2 * sizeof(int), ctx->stream));
-    G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 16 * sizeof(unsigned long long), ctx->stream));
+    G3_CUDA(cudaMemsetAsync(d_counters.p, 0, 32 * sizeof(unsigned long long), ctx->stream));
     G3_CUDA(cudaMemsetAsync(g_r3.p, 0, (size_t)n_far * sizeof(int), ctx->stream));
     G3_CUDA(cudaMemsetAsync(g_cyc.p, 0, (size_t)n_far * NPH * sizeof(long long), ctx->stream));
     std::vector<int> qpos(n_far, 0);
@@ -392,6 +397,13 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         long long add = (long long)(1.5 * scale * est2);
         add = std::max(add, (long long)(ctr - std::min<unsigned long long>(ctr, (unsigned long long)cap)));
         add = std::max(add, (long long)1 << 16);
+        // the enlarged pool and the copy of the old one must fit together
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const long long room = (long long)(0.9 * (double)free_b / sizeof(Cx<T>)) - cap;
+            if (room < (long long)1 << 16)
+                return fail(G3_ENOMEM, "aca3_compress: the factors need more than the free device memory");
+            add = std::min(add, room);
+        }
         DevBuf grown;
         G3_CUDA(grown.alloc((size_t)(cap + add) * sizeof(Cx<T>)));
         G3_CUDA(cudaMemcpyAsync(grown.p, pool->p, (size_t)cap * sizeof(Cx<T>), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -402,7 +414,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         G3_CUDA(cudaMemcpy(d_queue.p, nq.data(), n_spill * sizeof(int), cudaMemcpyHostToDevice));
     }
     if (est > 0) scale = std::max(scale, 1.15 * (double)ctr / est);
-    unsigned long long cnt[16];
+    unsigned long long cnt[32];
     G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
     std::vector<int32_t> r3(n_far);
     G3_CUDA(cudaMemcpy(r3.data(), g_r3.p, n_far * sizeof(int), cudaMemcpyDeviceToHost));
@@ -461,6 +473,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         S.mlp_used = mlp_use;
         S.ms_mlp = ms_mlp;
         for (int i = 0; i < 7; ++i) S.phase_cycles[i] = (int64_t)cnt[8 + i];
+        for (int i = 0; i < 10; ++i) S.sub_cycles[i] = (int64_t)cnt[16 + i];
         S.ctas = grid;
         for (int b = 0; b < J.n; ++b) {
             const BlockRange& rg = fa->ranges[b];

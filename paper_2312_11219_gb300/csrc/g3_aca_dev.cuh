@@ -40,6 +40,20 @@ namespace g3 {
 constexpr int KU_MAX = 256;   // largest unique-frequency count
 constexpr int SAMPLES = 32;   // sample entries of the convergence checks
 constexpr int NPH = 10;       // per-block diagnostics: 7 phases, steps, start, end
+constexpr int NSUB = 10;      // sub-step cycle counters (diagnostics)
+// rows staged per pass of the eq. (norm) Gram products
+template <class T>
+constexpr int NORM_RC = sizeof(T) == 4 ? 64 : 32;
+
+// sub-step timing by thread 0: adds the cycles since *t0 to slot i
+template <class T>
+__device__ __forceinline__ void sublap(T& S, int i, long long& t0) {
+    if (threadIdx.x == 0) {
+        const long long t = clock64();
+        S.sub[i] += t - t0;
+        t0 = t;
+    }
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -185,6 +199,8 @@ struct BlockSh {
     double sig[RF_MAX];
     double dU[RF_MAX], dV[RF_MAX];
     int sel[RF_MAX];
+    int piv;                 // pivoted QR of the core: pivot column of the step
+    float rkk;               // and its norm
     ArgMaxT<T> am[32];
     double red[64];
     double norm2;
@@ -197,6 +213,8 @@ struct BlockSh {
     long long new_off;
     long long entries;
     int raw;              // face ACA steps of the block (ranks before recompression)
+    long long sub[NSUB];  // SM cycles of sub-steps (thread 0): recompression Gram, Cholesky,
+                          // core, Jacobi, rest; face table, rows, columns, norm, samples
     int flag;
     int rot;
     int rnew;
@@ -553,6 +571,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     }
     // f_p[kf] of earlier crosses, the column tables, used-row flags
     for (int p = tid; p < nc; p += NT) S.fk[p] = Fp(A, S, p)[kf];
+    long long tf = clock64();
     const FaceTab<T> F = facetab_build<T, NT>(A, w, S, arena);
     for (int i = tid; i < M; i += NT) w.used[i] = 0;
     __syncthreads();
@@ -568,6 +587,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     while (m < cap) {
         int jp = -1;
         for (;;) {
+            sublap(S, 5, tf);
             line_coeffs<T, NT, true>(A, w, S, F, irow, m);
             __syncthreads();
             ArgMaxT<T> am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row);
@@ -607,7 +627,9 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
         __syncthreads();
         // residual column jp = u_m; the argmax over unused rows of |u_m| is the next row
         Cx<T>* um = w.uw + (size_t)m * A.Mmax;
+        sublap(S, 6, tf);
         ArgMaxT<T> nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um);
+        sublap(S, 7, tf);
         // recursive Frobenius norm of the face approximant:
         // ||S_m||^2 = ||S_{m-1}||^2 + 2 Re sum_t (u_t^H u_m)(v_m^H v_t) + ||u_m||^2 ||v_m||^2
         const int wid = tid >> 5, lane = tid & 31;
@@ -631,6 +653,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
         Sn2 += cross + nu2 * nv2;
         ++m;
         __syncthreads();
+        sublap(S, 8, tf);
         if (nu2 * nv2 <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
             if (!A.sample_check) {
                 converged = true;
@@ -639,6 +662,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             // confirm on the sample entries: partial pivoting can miss a block
             // of the face that no visited row or column reaches
             face_samples<KER, T, NT>(A, w, S, F, kf, m);
+            sublap(S, 9, tf);
             double tot = 0.0, best = -1.0;
             int bs = 0;
             for (int sm = 0; sm < SAMPLES; ++sm) {
@@ -738,84 +762,17 @@ constexpr int RS = 32;
 template <class T>
 __device__ __forceinline__ T jacobi_tol();
 template <>
-__device__ __forceinline__ float jacobi_tol<float>() { return 1e-6f; }
+__device__ __forceinline__ float jacobi_tol<float>() { return 1e-3f; }
 template <>
 __device__ __forceinline__ double jacobi_tol<double>() { return 1e-12; }
 
+// One-sided Jacobi SVD (Hestenes) of the r x r core C (columns of B, J = I on
+// entry): B <- C J with orthogonal columns, J unitary; singular values = column
+// norms of B; sel[] lists the kept columns in descending order.  Returns the
+// kept rank or -1 (non-finite).
 template <class T, int NT>
-__device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int r, Cx<double>* smem,
-                          const Cx<T>** tUo, const Cx<T>** tVo, int* ldTo) {
+__device__ int jacobi_core(const AcaArgs<T>& A, BlockSh<T>& S, Cx<T>* shB, Cx<T>* shJ, int ld, int r) {
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const int M = S.M, N = S.N;
-    const bool small = r <= RS;
-    const int ld = small ? RS : A.RF;
-    Cx<double>* RU = small ? smem : w.RU;
-    Cx<double>* RV = small ? smem + RS * RS : w.RV;
-    // B = C J and J in the working precision T (the Jacobi sweeps dominate the
-    // r x r work; float64 is rate-limited on this part)
-    Cx<T>* shB = small ? reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS) : reinterpret_cast<Cx<T>*>(w.TU);
-    Cx<T>* shJ = shB + (small ? RS * RS : A.RF * A.RF);
-    // Gram staging after R_U, R_V
-    Cx<T>* stage = reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS);
-    gram_upper<T, NT>(w.uw, A.Mmax, M, r, RU, ld, stage);
-    gram_upper<T, NT>(w.vw, A.Nmax, N, r, RV, ld, stage);
-    if (tid == 0) S.flag = 0;
-    __syncthreads();
-    // column scaling and upper Cholesky of the scaled Gram matrices (float64):
-    // warp 0 -> U, warp 1 -> V
-    if (wid < 2) {
-        Cx<double>* R = wid == 0 ? RU : RV;
-        double* dsc = wid == 0 ? S.dU : S.dV;
-        for (int a = lane; a < r; a += 32) dsc[a] = 1.0 / sqrt(fmax(R[a * ld + a].x, 1e-300));
-        __syncwarp();
-        for (int a = lane; a < r; a += 32)
-            for (int b = a; b < r; ++b) {
-                double s = dsc[a] * dsc[b];
-                R[a * ld + b].x *= s;
-                R[a * ld + b].y *= s;
-            }
-        __syncwarp();
-        for (int k = 0; k < r; ++k) {
-            double dkk = R[k * ld + k].x;
-            for (int i = 0; i < k; ++i) dkk -= cabs2(R[i * ld + k]);
-            bool bad = !(dkk > 1e-24);
-            if (bad) {
-                if (lane == 0) atomicOr(&S.flag, 1);
-                break;
-            }
-            double rkk = sqrt(dkk);
-            double irkk = 1.0 / rkk;
-            for (int j = k + 1 + lane; j < r; j += 32) {
-                Cx<double> acc = R[k * ld + j];
-                for (int i = 0; i < k; ++i) {
-                    Cx<double> rik = R[i * ld + k], rij = R[i * ld + j];
-                    acc.x -= rik.x * rij.x + rik.y * rij.y;  // conj(R[i][k]) R[i][j]
-                    acc.y -= rik.x * rij.y - rik.y * rij.x;
-                }
-                R[k * ld + j] = Cx<double>{acc.x * irkk, acc.y * irkk};
-            }
-            __syncwarp();
-            if (lane == 0) R[k * ld + k] = Cx<double>{rkk, 0.0};
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    if (S.flag) return -1;
-    // core C = R_U R_V^H with R_U = Rhat_U diag(1/dU): C[a][b] = sum_{c >= max(a,b)}
-    //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in B, J = I
-    for (int e = tid; e < r * r; e += NT) {
-        const int a = e % r, b = e / r;
-        Cx<double> acc{0, 0};
-        for (int c = max(a, b); c < r; ++c) {
-            Cx<double> x = RU[a * ld + c], y = RV[b * ld + c];
-            double s = 1.0 / (S.dU[c] * S.dV[c]);
-            acc.x += (x.x * y.x + x.y * y.y) * s;
-            acc.y += (x.y * y.x - x.x * y.y) * s;
-        }
-        shB[b * ld + a] = ccast<T>(acc);
-        shJ[b * ld + a] = Cx<T>{(T)(a == b ? 1 : 0), (T)0};
-    }
-    __syncthreads();
     // one-sided Jacobi (Hestenes) on the columns of C, round-robin pair schedule;
     // a pair is rotated while |<c_p, c_q>| > tol ||c_p|| ||c_q||.  Column norms
     // are recomputed at each sweep start and updated after every rotation
@@ -889,6 +846,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         if (rot == 0) break;
         if (sweep == 15 && tid == 0) atomicOr(A.status, ST_JACOBI_NOCONV);
     }
+
     // singular values, sort descending, truncation sigma < eps_face * sigma_max
     for (int a = tid; a < r; a += NT) {
         double s2 = 0;
@@ -915,6 +873,200 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     __syncthreads();
     int rn = 0;
     while (rn < r && S.sel[rn] >= 0) ++rn;
+    return rn;
+}
+
+// Column-pivoted QR of the r x r core C (columns of B) by modified
+// Gram-Schmidt (see the caller).  On return B[:, sel[k]] = q_k and
+// J[:, sel[k]] = (Pi R^H)[:, k] in the original column order, k < rank.
+template <class T, int NT>
+__device__ int cpqr_core(const AcaArgs<T>& A, BlockSh<T>& S, Cx<T>* shB, Cx<T>* shJ, int ld, int r) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    constexpr int NW = NT / 32;
+    T* cn = reinterpret_cast<T*>(S.sig);     // squared column norms, -1 once used
+    for (int c = wid; c < r; c += NW) {
+        T s2 = 0;
+        for (int i = lane; i < r; i += 32) s2 += cabs2(shB[c * ld + i]);
+        s2 = warp_sum(s2);
+        if (lane == 0) cn[c] = s2;
+    }
+    for (int e = tid; e < r * r; e += NT) shJ[(e / r) * ld + (e % r)] = Cx<T>{0, 0};
+    __syncthreads();
+    const double sfloor = A.trunc_floor * sqrt(S.norm2 / (double)A.Ku);
+    float r00 = 0.f;
+    int k = 0;
+    for (; k < r; ++k) {
+        if (wid == 0) {
+            ArgMaxT<T> best = amax_none<T>();
+            for (int c = lane; c < r; c += 32)
+                if (cn[c] >= (T)0) best = amax_better(best, ArgMaxT<T>{cn[c], c});
+            best = warp_argmax(best);
+            const int pv = best.i;
+            T s2 = 0;
+            if (best.v >= (T)0 && pv >= 0 && pv < r)
+                for (int i = lane; i < r; i += 32) s2 += cabs2(shB[pv * ld + i]);
+            s2 = warp_sum(s2);
+            if (lane == 0) {
+                S.piv = (best.v >= (T)0 && pv >= 0 && pv < r) ? pv : -1;
+                S.rkk = sqrt(s2);
+                if (S.piv >= 0) cn[pv] = (T)-1;
+            }
+        }
+        __syncthreads();
+        const int pv = S.piv;
+        const float rkk = S.rkk;
+        if (k == 0) r00 = rkk;
+        if (pv < 0 || !(rkk > 0.f) || !isfinite(rkk) || rkk < (float)A.eps_face * r00 ||
+            (k > 0 && (double)rkk < sfloor))
+            break;
+        const T inv = (T)1 / (T)rkk;
+        const Cx<T>* q = shB + pv * ld;
+        if (tid == 0) {
+            S.sel[k] = pv;
+            shJ[pv * ld + pv] = Cx<T>{(T)rkk, (T)0};
+        }
+        for (int j = wid; j < r; j += NW) {
+            if (!(cn[j] >= (T)0)) continue;  // used (or the pivot)
+            Cx<T>* cj = shB + j * ld;
+            Cx<T> g{0, 0};
+            for (int i = lane; i < r; i += 32) cfmac(g, cj[i], q[i]);  // conj(q) c_j, q unscaled
+            g.x = warp_sum(g.x) * inv;
+            g.y = warp_sum(g.y) * inv;
+            for (int i = lane; i < r; i += 32) {
+                const Cx<T> qi{q[i].x * inv, q[i].y * inv};
+                cj[i].x -= qi.x * g.x - qi.y * g.y;
+                cj[i].y -= qi.x * g.y + qi.y * g.x;
+            }
+            if (lane == 0) {
+                shJ[pv * ld + j] = Cx<T>{g.x, -g.y};  // conj(R[k][j])
+                cn[j] = fmax(cn[j] - cabs2(g), (T)0);
+            }
+        }
+        __syncthreads();
+    }
+    // scale the pivot columns to q (their norms rkk sit on J's diagonal)
+    for (int e = tid; e < k * r; e += NT) {
+        const int b = e / r, i = e - b * r;
+        const int pv = S.sel[b];
+        const T inv = (T)1 / shJ[pv * ld + pv].x;
+        shB[pv * ld + i].x *= inv;
+        shB[pv * ld + i].y *= inv;
+    }
+    __syncthreads();
+    return k;
+}
+
+template <class T, int NT>
+__device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int r, Cx<double>* smem,
+                          const Cx<T>** tUo, const Cx<T>** tVo, int* ldTo) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int M = S.M, N = S.N;
+    const bool small = r <= RS;
+    const int ld = small ? RS : A.RF;
+    Cx<double>* RU = small ? smem : w.RU;
+    Cx<double>* RV = small ? smem + RS * RS : w.RV;
+    // B = C J and J in the working precision T (the Jacobi sweeps dominate the
+    // r x r work; float64 is rate-limited on this part)
+    Cx<T>* shB = small ? reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS) : reinterpret_cast<Cx<T>*>(w.TU);
+    Cx<T>* shJ = shB + (small ? RS * RS : A.RF * A.RF);
+    // Gram staging after R_U, R_V
+    Cx<T>* stage = reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS);
+    long long tc = clock64();
+    gram_upper<T, NT>(w.uw, A.Mmax, M, r, RU, ld, stage);
+    gram_upper<T, NT>(w.vw, A.Nmax, N, r, RV, ld, stage);
+    if (tid == 0) S.flag = 0;
+    __syncthreads();
+    sublap(S, 0, tc);
+    // column scaling and upper Cholesky of the scaled Gram matrices (float64),
+    // both matrices at once by all threads, right-looking: step k scales row k
+    // by 1 / sqrt(R[k][k]) and then updates the trailing block
+    // R[i][j] -= conj(R[k][i]) R[k][j] (k < i <= j)
+    for (int e = tid; e < 2 * r; e += NT) {
+        const int mtx = e / r, a = e - mtx * r;
+        const Cx<double>* R = mtx == 0 ? RU : RV;
+        (mtx == 0 ? S.dU : S.dV)[a] = 1.0 / sqrt(fmax(R[a * ld + a].x, 1e-300));
+    }
+    __syncthreads();
+    for (int e = tid; e < 2 * r * r; e += NT) {
+        const int mtx = e / (r * r), q = e - mtx * r * r, a = q / r, b = q - a * r;
+        if (b < a) continue;
+        Cx<double>* R = mtx == 0 ? RU : RV;
+        const double* dsc = mtx == 0 ? S.dU : S.dV;
+        const double sc = dsc[a] * dsc[b];
+        R[a * ld + b].x *= sc;
+        R[a * ld + b].y *= sc;
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        const int tail = r - k - 1;
+        // row k of both matrices (the diagonal itself is written after the sync)
+        for (int e = tid; e < 2 * tail; e += NT) {
+            const int mtx = e / tail, j = k + 1 + (e - mtx * tail);
+            Cx<double>* R = mtx == 0 ? RU : RV;
+            const double dkk = R[k * ld + k].x;
+            if (!(dkk > 1e-24)) {
+                S.flag = 1;
+                continue;
+            }
+            const double irkk = 1.0 / sqrt(dkk);
+            R[k * ld + j].x *= irkk;
+            R[k * ld + j].y *= irkk;
+        }
+        if (tid < 2 && !(((tid == 0 ? RU : RV)[k * ld + k].x) > 1e-24)) S.flag = 1;
+        __syncthreads();
+        // trailing update and the diagonal entry of step k
+        for (int e = tid; e < 2 * tail * tail; e += NT) {
+            const int mtx = e / (tail * tail), q = e - mtx * tail * tail;
+            const int i = k + 1 + q / tail, j = k + 1 + (q - (q / tail) * tail);
+            if (j < i) continue;
+            Cx<double>* R = mtx == 0 ? RU : RV;
+            const Cx<double> rki = R[k * ld + i], rkj = R[k * ld + j];
+            R[i * ld + j].x -= rki.x * rkj.x + rki.y * rkj.y;  // conj(R[k][i]) R[k][j]
+            R[i * ld + j].y -= rki.x * rkj.y - rki.y * rkj.x;
+        }
+        if (tid < 2) {
+            Cx<double>* R = tid == 0 ? RU : RV;
+            R[k * ld + k] = Cx<double>{sqrt(fmax(R[k * ld + k].x, 0.0)), 0.0};
+        }
+        __syncthreads();
+    }
+    sublap(S, 1, tc);
+    if (S.flag) return -1;
+    // core C = R_U R_V^H with R_U = Rhat_U diag(1/dU): C[a][b] = sum_{c >= max(a,b)}
+    //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in B, J = I
+    for (int e = tid; e < r * r; e += NT) {
+        const int a = e % r, b = e / r;
+        Cx<double> acc{0, 0};
+        for (int c = max(a, b); c < r; ++c) {
+            Cx<double> x = RU[a * ld + c], y = RV[b * ld + c];
+            double s = 1.0 / (S.dU[c] * S.dV[c]);
+            acc.x += (x.x * y.x + x.y * y.y) * s;
+            acc.y += (x.y * y.x - x.x * y.y) * s;
+        }
+        shB[b * ld + a] = ccast<T>(acc);
+        shJ[b * ld + a] = Cx<T>{(T)(a == b ? 1 : 0), (T)0};
+    }
+    __syncthreads();
+    sublap(S, 2, tc);
+    int rn = 0;
+    if constexpr (sizeof(T) == 4) {
+        // float32: column-pivoted QR of C by modified Gram-Schmidt, C Pi = Q R,
+        // stopped when the largest remaining column norm falls below the
+        // truncation threshold; dropping the remaining columns removes exactly
+        // their norms (||R_22||_F), as truncating the SVD removes its dropped
+        // singular values.  Step k (two barriers): warp 0 picks the unused
+        // column of largest (downdated) norm and recomputes its norm exactly;
+        // then every other unused column j is orthogonalised against it by a
+        // warp (g = q^H c_j, c_j -= q g) and J[:, pivot][j] = conj(g), which
+        // builds Pi R^H column by column.  The pivot columns are scaled to q
+        // at the end; sel[k] = pivot of step k.
+        rn = cpqr_core<T, NT>(A, S, shB, shJ, ld, r);
+        if (rn < 0) return -1;
+    } else {
+        rn = jacobi_core<T, NT>(A, S, shB, shJ, ld, r);
+        if (rn < 0) return -1;
+    }
+    sublap(S, 3, tc);
     // T_U[:, b] = diag(dU) RhatU^{-1} B[:, sel[b]],  T_V[:, b] = diag(dV) RhatV^{-1} J[:, sel[b]]
     // (float64 back substitution, in place on the selected columns)
     for (int item = tid; item < 2 * rn; item += NT) {
@@ -949,6 +1101,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         tV[a * ld + b] = shJ[S.sel[b] * ld + a];
     }
     __syncthreads();
+    sublap(S, 4, tc);
     *tUo = tU;
     *tVo = tV;
     *ldTo = ld;
@@ -959,16 +1112,17 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
 // hh[d] = <H_l, H_d>_F = sum_{a in cross d, b} (U_d^H U_l)[a][b] conj((V_d^H V_l)[a][b]) for the
 // earlier crosses d < nc, and hself = ||H_l||_F^2 (a over the columns of cross l).
 // Tiled: 32 columns of [U_1 .. U_nc U_l] at a time against all rn columns of U_l,
-// over 32-row chunks staged in shared memory (sh: >= 33 * (32 + RF) complex T).
+// over NORM_RC-row chunks staged in shared memory (sh: >= (NORM_RC + 1) (32 + RF) complex T).
 template <class T, int NT>
 __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, const Cx<T>* Vn, int rn,
                            Cx<T>* sh) {
     constexpr int QMAX = 32 * RF_MAX / NT;
+    constexpr int RC = NORM_RC<T>;  // rows staged per pass (fewer barriers per column chunk)
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N, nc = S.ncross;
     const int na = S.pre[nc] + rn;
-    Cx<T>* sa = sh;             // [32][33]
-    Cx<T>* sb = sh + 32 * 33;   // [rn][33]
+    Cx<T>* sa = sh;                  // [32][RC + 1]
+    Cx<T>* sb = sh + 32 * (RC + 1);  // [rn][RC + 1]
     for (int a0 = 0; a0 < na; a0 += 32) {
         const int acnt = min(32, na - a0);
         Cx<T> zu[QMAX], zv[QMAX];
@@ -976,9 +1130,9 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
         for (int q = 0; q < QMAX; ++q) zu[q] = zv[q] = Cx<T>{0, 0};
         for (int pass = 0; pass < 2; ++pass) {  // 0: U (rows M), 1: V (rows N)
             const int L = pass == 0 ? M : N;
-            for (int i0 = 0; i0 < L; i0 += 32) {
-                for (int e = tid; e < acnt * 32; e += NT) {
-                    const int c = e >> 5, ii = e & 31, col = a0 + c;
+            for (int i0 = 0; i0 < L; i0 += RC) {
+                for (int e = tid; e < acnt * RC; e += NT) {
+                    const int c = e / RC, ii = e - c * RC, col = a0 + c;
                     Cx<T> v{0, 0};
                     if (i0 + ii < L) {
                         const Cx<T>* base;
@@ -994,12 +1148,12 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
                         }
                         v = base[i0 + ii];
                     }
-                    sa[c * 33 + ii] = v;
+                    sa[c * (RC + 1) + ii] = v;
                 }
-                for (int e = tid; e < rn * 32; e += NT) {
-                    const int b = e >> 5, ii = e & 31;
+                for (int e = tid; e < rn * RC; e += NT) {
+                    const int b = e / RC, ii = e - b * RC;
                     const Cx<T>* base = pass == 0 ? Un + (long long)b * M : Vn + (long long)b * N;
-                    sb[b * 33 + ii] = (i0 + ii < L) ? base[i0 + ii] : Cx<T>{0, 0};
+                    sb[b * (RC + 1) + ii] = (i0 + ii < L) ? base[i0 + ii] : Cx<T>{0, 0};
                 }
                 __syncthreads();
 #pragma unroll
@@ -1007,11 +1161,11 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
                     const int o = tid + q * NT;
                     if (o >= acnt * rn) break;
                     const int al = o / rn, b = o % rn;
-                    const Cx<T>* xa = sa + al * 33;
-                    const Cx<T>* xb = sb + b * 33;
+                    const Cx<T>* xa = sa + al * (RC + 1);
+                    const Cx<T>* xb = sb + b * (RC + 1);
                     Cx<T> s{0, 0};
 #pragma unroll 8
-                    for (int ii = 0; ii < 32; ++ii) cfmac(s, xb[ii], xa[ii]);
+                    for (int ii = 0; ii < RC; ++ii) cfmac(s, xb[ii], xa[ii]);
                     if (pass == 0) {
                         zu[q].x += s.x;
                         zu[q].y += s.y;
@@ -1350,6 +1504,7 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
             S.norm2 = 0.0;
             S.entries = 0;
             S.raw = 0;
+            for (int i = 0; i < NSUB; ++i) S.sub[i] = 0;
             S.k = A.k1 ? A.k1[blk] : 0;
             for (int i = 0; i < KU_MAX / 32; ++i) S.used_k[i] = 0u;
         }
@@ -1669,6 +1824,7 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
             atomicAdd(&A.counters[1], (unsigned long long)computed);
             if (zero_block && !spilled) atomicAdd(&A.counters[2], 1ull);
             for (int i = 0; i < 7; ++i) atomicAdd(&A.counters[8 + i], (unsigned long long)ph[i]);
+            for (int i = 0; i < NSUB; ++i) atomicAdd(&A.counters[16 + i], (unsigned long long)S.sub[i]);
         }
         __syncthreads();
     }

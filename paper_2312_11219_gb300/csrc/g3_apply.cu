@@ -118,162 +118,150 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
     }
 }
 
-// Far field: one CTA per admissible block, its crosses in groups of PG.  For a
-// group the CTA forms, in one pass over the block's columns of W (read once per
-// group rather than once per cross),
-//   x_p = sum_k f_p[k] w_k ,  zc_p = sum_k f_p[k] conj(w_k')      (p in the group)
-// and then adds
-//   low-rank cross (U, V):   U_p (V_p^H x_p) + conj(U_p (V_p^H zc_p))
-//   dense cross (H; r = -1): H_p x_p + conj(H_p zc_p)
-// Every factor is read once; the W columns come from L2.
+// Far field, blocks with low-rank faces, in two phases over work items of
+// one block and a group of up to PG crosses (ab: the group's V^H x and
+// V^H zc, 2 r_p complex values per cross, from ab_base on):
+//   phase 1, item (block, group, column tile of NT):
+//     x_p[j] = sum_k f_p[k] w_k[j], zc_p[j] = sum_k f_p[k] conj(w_k'[j]) for the
+//     tile's columns (W read once per group and tile), then the tile's part
+//     of a_p = V_p^H x_p and b_p = V_p^H zc_p, added to ab;
+//   phase 2, item (block, group): y += U_p a_p + conj(U_p b_p).
+// Each factor is read once; the many small items keep the SMs busy.
 template <class T, int NT, int PG>
-__global__ void __launch_bounds__(NT) k_apply_far(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
-                                                  const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
-                                                  const int* __restrict__ list, int Cmax, int Ku, int E,
-                                                  const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
-                                                  Cx<T>* __restrict__ y, int ysmem_max, int dense_n_max, int rmax) {
+__global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
+                                               const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
+                                               const int4* __restrict__ items, int Cmax, int Ku, int E,
+                                               const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
+                                               Cx<T>* __restrict__ ab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);   // [PG][Ku] fibers of the group
-    Cx<T>* ab = fg + PG * Ku;                          // [PG][rmax][2]: V^H x, V^H zc
-    Cx<T>* xs = ab + PG * rmax * 2;                    // [PG][dense_n_max] x (dense crosses)
-    Cx<T>* zs = xs + PG * dense_n_max;                 // [PG][dense_n_max] zc
-    T* ysh = reinterpret_cast<T*>(zs + PG * dense_n_max);  // [2 M] when M <= ysmem_max
+    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);  // [PG][Ku]
+    Cx<T>* acc = fg + PG * Ku;                        // [2 * sum r_p] partial a_p, b_p
     __shared__ CrossRec crs[PG];
-    const int blk = list[blockIdx.x];
+    __shared__ int offs[PG + 1];
+    const int4 it = items[blockIdx.x];  // block, group, column tile, a/b offset
+    const int blk = it.x, g0 = it.y * PG, jt = it.z;
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
-    const int nc = r3[blk];
-    const bool ysm = M <= ysmem_max;
+    const int np = min(PG, r3[blk] - g0);
     const int tid = threadIdx.x, lane = tid & 31;
-    if (ysm)
-        for (int i = tid; i < 2 * M; i += NT) ysh[i] = 0;
-    for (int g0 = 0; g0 < nc; g0 += PG) {
-        const int np = min(PG, nc - g0);
-        __syncthreads();  // the previous group's readers are done
-        if (tid < PG) crs[tid] = tid < np ? rec[(size_t)blk * Cmax + g0 + tid] : CrossRec{0, 0, 0, 0, 0};
-        __syncthreads();
-        for (int e = tid; e < PG * Ku; e += NT) {
-            const int p = e / Ku, k = e - p * Ku;
-            Cx<T> v{0, 0};
-            if (p < np) {
-                const CrossRec c = crs[p];
-                v = pool[c.off + (c.r < 0 ? (long long)M * N : (long long)c.r * (M + N)) + k];
-            }
-            fg[e] = v;
-        }
-        for (int e = tid; e < PG * rmax * 2; e += NT) ab[e] = Cx<T>{0, 0};
-        __syncthreads();
-        for (int jt = 0; jt < N; jt += NT) {
-            const int j = jt + tid;
-            Cx<T> x[PG], z[PG];
+    if (tid < PG) crs[tid] = tid < np ? rec[(size_t)blk * Cmax + g0 + tid] : CrossRec{0, 0, 0, 0, 0};
+    __syncthreads();
+    if (tid == 0) {
+        offs[0] = 0;
+        for (int p = 0; p < PG; ++p) offs[p + 1] = offs[p] + (p < np ? 2 * crs[p].r : 0);
+    }
+    for (int e = tid; e < PG * Ku; e += NT) {
+        const int p = e / Ku, k = e - p * Ku;
+        Cx<T> v{0, 0};
+        if (p < np) v = pool[crs[p].off + (long long)crs[p].r * (M + N) + k];
+        fg[e] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < offs[PG]; e += NT) acc[e] = Cx<T>{0, 0};
+    const int j = jt * NT + tid;
+    Cx<T> x[PG], z[PG];
 #pragma unroll
-            for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
-            if (j < N) {
-                const Cx<T>* wf = Wf + br.cb + j;
-                const Cx<T>* wc = Wc + br.cb + j;
-                for (int k = 0; k < Ku; ++k) {
-                    const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
-#pragma unroll
-                    for (int p = 0; p < PG; ++p) {
-                        const Cx<T> f = fg[p * Ku + k];
-                        cfma(x[p], f, a);
-                        cfmac(z[p], f, b);
-                    }
-                }
-            }
+    for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
+    if (j < N) {
+        const Cx<T>* wf = Wf + br.cb + j;
+        const Cx<T>* wc = Wc + br.cb + j;
+#pragma unroll 4
+        for (int k = 0; k < Ku; ++k) {
+            const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
 #pragma unroll
             for (int p = 0; p < PG; ++p) {
-                if (p < np) {
-                    const CrossRec c = crs[p];
-                    if (c.r < 0) {
-                        if (j < N) {
-                            xs[p * dense_n_max + j] = x[p];
-                            zs[p * dense_n_max + j] = z[p];
-                        }
-                    } else {
-                        const Cx<T>* V = pool + c.off + (long long)c.r * M;
-                        for (int t = 0; t < c.r; ++t) {
-                            const Cx<T> v = j < N ? V[(long long)t * N + j] : Cx<T>{0, 0};
-                            Cx<T> pa = cmulc(x[p], v), pb = cmulc(z[p], v);  // conj(v) x, conj(v) zc
-                            pa.x = warp_sum(pa.x);
-                            pa.y = warp_sum(pa.y);
-                            pb.x = warp_sum(pb.x);
-                            pb.y = warp_sum(pb.y);
-                            if (lane == 0) {
-                                Cx<T>* q = ab + (size_t)(p * rmax + t) * 2;
-                                atomicAdd(&q[0].x, pa.x);
-                                atomicAdd(&q[0].y, pa.y);
-                                atomicAdd(&q[1].x, pb.x);
-                                atomicAdd(&q[1].y, pb.y);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < M; i += NT) {
-            T vx = 0, vy = 0;
-            for (int p = 0; p < np; ++p) {
-                const CrossRec c = crs[p];
-                Cx<T> s1{0, 0}, s2{0, 0};
-                if (c.r < 0) {
-                    const Cx<T>* H = pool + c.off;
-                    for (int j = 0; j < N; ++j) {
-                        const Cx<T> h = H[i + (long long)j * M];
-                        cfma(s1, h, xs[p * dense_n_max + j]);
-                        cfma(s2, h, zs[p * dense_n_max + j]);
-                    }
-                } else {
-                    const Cx<T>* U = pool + c.off;
-                    const Cx<T>* q = ab + (size_t)p * rmax * 2;
-                    for (int t = 0; t < c.r; ++t) {
-                        const Cx<T> u = U[(long long)t * M + i];
-                        cfma(s1, u, q[2 * t]);
-                        cfma(s2, u, q[2 * t + 1]);
-                    }
-                }
-                vx += s1.x + s2.x;  // s1 + conj(s2)
-                vy += s1.y - s2.y;
-            }
-            if (ysm) {
-                ysh[2 * i] += vx;
-                ysh[2 * i + 1] += vy;
-            } else {
-                atomicAdd(&y[br.rb + i].x, vx);
-                atomicAdd(&y[br.rb + i].y, vy);
+                const Cx<T> f = fg[p * Ku + k];
+                cfma(x[p], f, a);
+                cfmac(z[p], f, b);
             }
         }
     }
     __syncthreads();
-    if (ysm)
-        for (int i = tid; i < M; i += NT) {
-            atomicAdd(&y[br.rb + i].x, ysh[2 * i]);
-            atomicAdd(&y[br.rb + i].y, ysh[2 * i + 1]);
+#pragma unroll
+    for (int p = 0; p < PG; ++p) {
+        if (p < np) {
+            const int r = crs[p].r;
+            const Cx<T>* V = pool + crs[p].off + (long long)r * M;
+            for (int t = 0; t < r; ++t) {
+                const Cx<T> v = j < N ? V[(long long)t * N + j] : Cx<T>{0, 0};
+                Cx<T> pa = cmulc(x[p], v), pb = cmulc(z[p], v);  // conj(v) x, conj(v) zc
+                pa.x = warp_sum(pa.x);
+                pa.y = warp_sum(pa.y);
+                pb.x = warp_sum(pb.x);
+                pb.y = warp_sum(pb.y);
+                if (lane == 0) {
+                    Cx<T>* q = acc + offs[p] + 2 * t;
+                    atomicAdd(&q[0].x, pa.x);
+                    atomicAdd(&q[0].y, pa.y);
+                    atomicAdd(&q[1].x, pb.x);
+                    atomicAdd(&q[1].y, pb.y);
+                }
+            }
         }
+    }
+    __syncthreads();
+    for (int e = tid; e < offs[PG]; e += NT) {
+        atomicAdd(&ab[it.w + e].x, acc[e].x);
+        atomicAdd(&ab[it.w + e].y, acc[e].y);
+    }
+}
+
+template <class T, int NT, int PG>
+__global__ void __launch_bounds__(NT) k_far_uy(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
+                                               const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
+                                               const int4* __restrict__ items, int Cmax,
+                                               const Cx<T>* __restrict__ ab, Cx<T>* __restrict__ y) {
+    __shared__ CrossRec crs[PG];
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, g0 = it.y * PG;
+    const BlockRange br = ranges[blk];
+    const int M = br.re - br.rb;
+    const int np = min(PG, r3[blk] - g0);
+    if (threadIdx.x < PG && threadIdx.x < np) crs[threadIdx.x] = rec[(size_t)blk * Cmax + g0 + threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += NT) {
+        T vx = 0, vy = 0;
+        int o = it.w;
+        for (int p = 0; p < np; ++p) {
+            const int r = crs[p].r;
+            const Cx<T>* U = pool + crs[p].off;
+            Cx<T> s1{0, 0}, s2{0, 0};
+#pragma unroll 4
+            for (int t = 0; t < r; ++t) {
+                const Cx<T> u = U[(long long)t * M + i];
+                cfma(s1, u, ab[o + 2 * t]);
+                cfma(s2, u, ab[o + 2 * t + 1]);
+            }
+            o += 2 * r;
+            vx += s1.x + s2.x;  // U a + conj(U b)
+            vy += s1.y - s2.y;
+        }
+        atomicAdd(&y[br.rb + i].x, vx);
+        atomicAdd(&y[br.rb + i].y, vy);
+    }
 }
 
 // Far field, blocks with dense faces (small blocks): one warp per block, no
 // block-wide barrier.  Crosses in groups of PG: the group's fibers are staged
-// in the warp's slice of shared memory; lane j forms x_p[j] = sum_k f_p[k] w_k[j]
-// and zc_p[j] = sum_k f_p[k] conj(w_k'[j]) for the group in one pass over W;
-// lane i then adds sum_p (H_p x_p)[i] + conj((H_p zc_p)[i]) for its rows.
+// in the warp's slice of shared memory; for each chunk of 32 columns, lane j
+// forms x_p[j] = sum_k f_p[k] w_k[j] and zc_p[j] = sum_k f_p[k] conj(w_k'[j])
+// for the group in one pass over W, and lane i then adds
+// sum_p (H_p x_p)[i] + conj((H_p zc_p)[i]) over the chunk for its rows.
 template <class T, int NW, int PG, int MQ>
-__global__ void __launch_bounds__(NW * 32) k_apply_far_dense(const Cx<T>* __restrict__ pool,
-                                                            const CrossRec* __restrict__ rec,
-                                                            const int* __restrict__ r3,
-                                                            const BlockRange* __restrict__ ranges,
-                                                            const int* __restrict__ list, int n, int Cmax, int Ku,
-                                                            int E, const Cx<T>* __restrict__ Wf,
-                                                            const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y,
-                                                            int nmax) {
+__global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __restrict__ pool,
+                                                               const CrossRec* __restrict__ rec,
+                                                               const int* __restrict__ r3,
+                                                               const BlockRange* __restrict__ ranges,
+                                                               const int* __restrict__ list, int n, int Cmax, int Ku,
+                                                               int E, const Cx<T>* __restrict__ Wf,
+                                                               const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * NW + warp;
     if (bi >= n) return;  // the whole warp: no block-wide synchronisation below
-    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * (PG * Ku + 2 * PG * nmax);
+    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * (PG * Ku + 2 * PG * 32);
     Cx<T>* xs = fg + PG * Ku;
-    Cx<T>* zs = xs + PG * nmax;
+    Cx<T>* zs = xs + PG * 32;
     const int blk = list[bi];
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
@@ -283,6 +271,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply_far_dense(const Cx<T>* __rest
     for (int q = 0; q < MQ; ++q) acc[q] = Cx<T>{0, 0};
     for (int g0 = 0; g0 < nc; g0 += PG) {
         const int np = min(PG, nc - g0);
+        __syncwarp();
         for (int e = lane; e < PG * Ku; e += 32) {
             const int p = e / Ku, k = e - p * Ku;
             Cx<T> v{0, 0};
@@ -298,6 +287,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply_far_dense(const Cx<T>* __rest
             if (j < N) {
                 const Cx<T>* wf = Wf + br.cb + j;
                 const Cx<T>* wc = Wc + br.cb + j;
+#pragma unroll 4
                 for (int k = 0; k < Ku; ++k) {
                     const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
 #pragma unroll
@@ -307,32 +297,34 @@ __global__ void __launch_bounds__(NW * 32) k_apply_far_dense(const Cx<T>* __rest
                         cfmac(z[p], f, b);
                     }
                 }
-#pragma unroll
-                for (int p = 0; p < PG; ++p) {
-                    xs[p * nmax + j] = x[p];
-                    zs[p * nmax + j] = z[p];
-                }
             }
-        }
-        __syncwarp();
-        for (int p = 0; p < np; ++p) {
-            const Cx<T>* H = pool + rec[(size_t)blk * Cmax + g0 + p].off;
 #pragma unroll
-            for (int q = 0; q < MQ; ++q) {
-                const int i = lane + 32 * q;
-                if (i < M) {
-                    Cx<T> s1{0, 0}, s2{0, 0};
-                    for (int j = 0; j < N; ++j) {
-                        const Cx<T> h = H[i + (long long)j * M];
-                        cfma(s1, h, xs[p * nmax + j]);
-                        cfma(s2, h, zs[p * nmax + j]);
+            for (int p = 0; p < PG; ++p) {
+                xs[p * 32 + lane] = x[p];
+                zs[p * 32 + lane] = z[p];
+            }
+            __syncwarp();
+            const int jn = min(32, N - j0);
+            for (int p = 0; p < np; ++p) {
+                const Cx<T>* H = pool + rec[(size_t)blk * Cmax + g0 + p].off + (long long)j0 * M;
+#pragma unroll
+                for (int q = 0; q < MQ; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i < M) {
+                        Cx<T> s1{0, 0}, s2{0, 0};
+#pragma unroll 8
+                        for (int jj = 0; jj < jn; ++jj) {
+                            const Cx<T> h = H[i + (long long)jj * M];
+                            cfma(s1, h, xs[p * 32 + jj]);
+                            cfma(s2, h, zs[p * 32 + jj]);
+                        }
+                        acc[q].x += s1.x + s2.x;  // s1 + conj(s2)
+                        acc[q].y += s1.y - s2.y;
                     }
-                    acc[q].x += s1.x + s2.x;  // s1 + conj(s2)
-                    acc[q].y += s1.y - s2.y;
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < MQ; ++q) {
@@ -377,65 +369,117 @@ static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near*
     return G3_OK;
 }
 
-// far-field launches: the blocks with dense faces (all crosses of a block
-// are of one kind) by the warp-per-block kernel, the others by the
-// CTA-per-block kernel.  d_list: device space for n_far ints (filled here);
-// d_ranges: the block ranges on the device.
+// Far-field work lists (host, cached in the factors): the dense-face blocks
+// (one warp each), padded to a multiple of 4 ints, then the phase-1 items
+// (block, group of FAR_PG crosses, column tile of FAR_NT, offset of the
+// group in the a/b buffer) and the phase-2 items (block, group, 0, offset).
+constexpr int FAR_PG = 4;
+constexpr int FAR_NT = 128;
+
+static void far_plan(const g3_factors* fa) {
+    if (fa->plan_ready) return;
+    std::vector<int>& L = fa->plan;
+    L.clear();
+    std::vector<int> p1, p2;
+    long long ab = 0;
+    for (int b = 0; b < fa->n_far; ++b) {
+        const int r = fa->r3[b];
+        if (r <= 0) continue;
+        if (fa->rec[(size_t)b * fa->Cmax].r < 0) {
+            L.push_back(b);
+            continue;
+        }
+        const int N = fa->ranges[b].ce - fa->ranges[b].cb;
+        for (int g = 0; g * FAR_PG < r; ++g) {
+            const long long base = ab;
+            for (int p = g * FAR_PG; p < std::min(r, (g + 1) * FAR_PG); ++p)
+                ab += 2 * fa->rec[(size_t)b * fa->Cmax + p].r;
+            for (int jt = 0; jt * FAR_NT < N; ++jt) p1.insert(p1.end(), {b, g, jt, (int)base});
+            p2.insert(p2.end(), {b, g, 0, (int)base});
+        }
+    }
+    fa->plan_nd = (int)L.size();
+    fa->plan_n1 = (int)p1.size() / 4;
+    fa->plan_n2 = (int)p2.size() / 4;
+    fa->plan_ab = ab;
+    while (L.size() % 4) L.push_back(0);  // int4 alignment of the item arrays
+    L.insert(L.end(), p1.begin(), p1.end());
+    L.insert(L.end(), p2.begin(), p2.end());
+    fa->plan_ready = true;
+}
+
+// ints of the far work lists and complex values of the a/b buffer
+static int far_list_len(const g3_factors* fa) {
+    far_plan(fa);
+    return (int)fa->plan.size();
+}
+static long long far_ab_len(const g3_factors* fa) {
+    far_plan(fa);
+    return fa->plan_ab;
+}
+
+// far-field launches; d_list: device space for far_list_len(fa) ints,
+// d_ab: for far_ab_len(fa) complex values (cleared here); d_ranges: the
+// block ranges on the device
 template <class T>
-static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, int* d_list, const BlockRange* d_ranges, int Ku,
-                                  int E, const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y) {
-    std::vector<int> lst;
-    lst.reserve(fa->n_far);
-    int mmax_dense = 0, nmax_dense = 0;
-    for (int b = 0; b < fa->n_far; ++b)
-        if (fa->r3[b] > 0 && fa->rec[(size_t)b * fa->Cmax].r < 0) {
-            lst.push_back(b);
-            mmax_dense = std::max(mmax_dense, fa->ranges[b].re - fa->ranges[b].rb);
-            nmax_dense = std::max(nmax_dense, fa->ranges[b].ce - fa->ranges[b].cb);
+static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, int* d_list, Cx<T>* d_ab,
+                                  const BlockRange* d_ranges, int Ku, int E, const Cx<T>* Wf, const Cx<T>* Wc,
+                                  Cx<T>* y) {
+    far_plan(fa);
+    if (fa->plan.empty()) return G3_OK;
+    if (fa->plan_ab >= (1LL << 31)) return fail(G3_EUNSUPPORTED, "apply_gcq: the far-field a/b buffer exceeds 2^31");
+    const int nd = fa->plan_nd, n1 = fa->plan_n1, n2 = fa->plan_n2;
+    G3_CUDA(cudaMemcpyAsync(d_list, fa->plan.data(), fa->plan.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    if (nd > 0) {
+        int mmax_dense = 0;
+        for (int q = 0; q < nd; ++q) {
+            const BlockRange& r = fa->ranges[fa->plan[q]];
+            mmax_dense = std::max(mmax_dense, r.re - r.rb);
         }
-    const int n_dense = (int)lst.size();
-    for (int b = 0; b < fa->n_far; ++b)
-        if (fa->r3[b] > 0 && fa->rec[(size_t)b * fa->Cmax].r >= 0) lst.push_back(b);
-    const int n_low = (int)lst.size() - n_dense;
-    if (lst.empty()) return G3_OK;
-    G3_CUDA(cudaMemcpyAsync(d_list, lst.data(), lst.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    if (n_dense > 0) {
         constexpr int NW = 8, PGW = 4;
-        const size_t smem = (size_t)NW * (PGW * Ku + 2 * PGW * nmax_dense) * sizeof(Cx<T>);
+        const size_t smem = (size_t)NW * (PGW * Ku + 2 * PGW * 32) * sizeof(Cx<T>);
         if (smem > ctx->smem_optin || mmax_dense > 96)
-            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks of %d x %d exceed the apply kernel's limits",
-                        mmax_dense, nmax_dense);
-        const int grid = (n_dense + NW - 1) / NW;
-        if (mmax_dense <= 32) {
-            G3_CUDA(cudaFuncSetAttribute(k_apply_far_dense<T, NW, PGW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_apply_far_dense<T, NW, PGW, 1><<<grid, NW * 32, smem, ctx->stream>>>(
-                fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges, d_list, n_dense,
-                fa->Cmax, Ku, E, Wf, Wc, y, nmax_dense);
-        } else {
-            G3_CUDA(cudaFuncSetAttribute(k_apply_far_dense<T, NW, PGW, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_apply_far_dense<T, NW, PGW, 3><<<grid, NW * 32, smem, ctx->stream>>>(
-                fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(), d_ranges, d_list, n_dense,
-                fa->Cmax, Ku, E, Wf, Wc, y, nmax_dense);
-        }
+            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks with %d rows exceed the apply kernel's limit",
+                        mmax_dense);
+        const int grid = (nd + NW - 1) / NW;
+        auto go = [&](auto kfn) -> g3_status {
+            G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kfn<<<grid, NW * 32, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                      fa->d_r3.as<int>(), d_ranges, d_list, nd, fa->Cmax, Ku, E,
+                                                      Wf, Wc, y);
+            return G3_OK;
+        };
+        g3_status st;
+        if (mmax_dense <= 32)
+            st = go(k_apply_far_dense<T, NW, PGW, 1>);
+        else if (mmax_dense <= 64)
+            st = go(k_apply_far_dense<T, NW, PGW, 2>);
+        else
+            st = go(k_apply_far_dense<T, NW, PGW, 3>);
+        if (st != G3_OK) return st;
         ctx->count("k_apply_far_dense");
         G3_CUDA(cudaGetLastError());
     }
-    if (n_low > 0) {
-        constexpr int NT = 128;
-        constexpr int PG = sizeof(T) == 4 ? 16 : 4;
-        const int ysmem_max = sizeof(T) == 4 ? 4096 : 2048;
-        int mmax = 0;
-        for (auto& r : fa->ranges) mmax = std::max(mmax, r.re - r.rb);
-        const int ym = std::min(mmax, ysmem_max);
+    if (n1 > 0) {
+        G3_CUDA(cudaMemsetAsync(d_ab, 0, (size_t)fa->plan_ab * sizeof(Cx<T>), ctx->stream));
         const int rmax = std::max(1, (int)fa->stats.face_rank_max);
-        const size_t smem = ((size_t)PG * Ku + (size_t)PG * rmax * 2) * sizeof(Cx<T>) + 2 * (size_t)ym * sizeof(T);
+        const size_t smem = ((size_t)FAR_PG * Ku + 2 * (size_t)FAR_PG * rmax) * sizeof(Cx<T>);
         if (smem > ctx->smem_optin)
             return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
-        G3_CUDA(cudaFuncSetAttribute(k_apply_far<T, NT, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_apply_far<T, NT, PG><<<n_low, NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
-                                                                 fa->d_r3.as<int>(), d_ranges, d_list + n_dense,
-                                                                 fa->Cmax, Ku, E, Wf, Wc, y, ym, 0, rmax);
-        ctx->count("k_apply_far");
+        const int4* it1 = reinterpret_cast<const int4*>(d_list + (nd + 3) / 4 * 4);
+        const int4* it2 = it1 + n1;
+        G3_CUDA(cudaFuncSetAttribute(k_far_vx<T, FAR_NT, FAR_PG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        k_far_vx<T, FAR_NT, FAR_PG><<<n1, FAR_NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(),
+                                                                        fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(),
+                                                                        d_ranges, it1, fa->Cmax, Ku, E, Wf, Wc, d_ab);
+        ctx->count("k_far_vx");
+        G3_CUDA(cudaGetLastError());
+        k_far_uy<T, FAR_NT, FAR_PG><<<n2, FAR_NT, 0, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                                     fa->d_r3.as<int>(), d_ranges, it2, fa->Cmax,
+                                                                     d_ab, y);
+        ctx->count("k_far_uy");
         G3_CUDA(cudaGetLastError());
     }
     return G3_OK;
@@ -469,12 +513,14 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
     G3_CUDA(cudaEventRecord(e2, ctx->stream));
     if (fa && fa->n_far > 0) {
-        DevBuf d_list, d_ranges;
-        G3_CUDA(d_list.alloc(fa->n_far * sizeof(int)));
+        DevBuf d_list, d_ranges, d_ab;
+        G3_CUDA(d_list.alloc(std::max(1, far_list_len(fa)) * sizeof(int)));
+        G3_CUDA(d_ab.alloc(std::max(1LL, far_ab_len(fa)) * sizeof(Cx<T>)));
         G3_CUDA(d_ranges.alloc(fa->ranges.size() * sizeof(BlockRange)));
         G3_CUDA(cudaMemcpyAsync(d_ranges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
                                 cudaMemcpyHostToDevice, ctx->stream));
-        G3_TRY_NA(launch_apply_far<T>(ctx, fa, d_list.as<int>(), d_ranges.as<BlockRange>(), Ku, E, Wf, Wc, y));
+        G3_TRY_NA(launch_apply_far<T>(ctx, fa, d_list.as<int>(), d_ab.as<Cx<T>>(), d_ranges.as<BlockRange>(), Ku, E,
+                                      Wf, Wc, y));
         G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
     }
     {
@@ -546,12 +592,14 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
     const int n_far = fa ? fa->n_far : 0;
     const size_t nW = (size_t)Ku * E;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t need = al(2 * nW * sizeof(Cx<T>)) + al(E * sizeof(Cx<T>)) + al(n_far * sizeof(int)) +
-                        al(n_far * sizeof(BlockRange));
+    const int n_list = fa ? far_list_len(fa) : 0;
+    const long long n_ab = fa ? far_ab_len(fa) : 0;
+    const size_t need = al(2 * nW * sizeof(Cx<T>)) + al(E * sizeof(Cx<T>)) + al(n_list * sizeof(int)) +
+                        al(n_far * sizeof(BlockRange)) + al(n_ab * sizeof(Cx<T>));
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(G3_EINVAL,
-                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values plus "
-                    "block tables), the fixed scratch holds %zu; use apply_gcq",
+                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values, "
+                    "block tables and far-field work lists), the fixed scratch holds %zu; use apply_gcq",
                     need, NOALLOC_SCRATCH_BYTES);
     void* base = nullptr;
     G3_TRY_NA(noalloc_scratch(ctx->device, &base));
@@ -562,8 +610,10 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
     Cx<T>* y = reinterpret_cast<Cx<T>*>(p);
     p += al(E * sizeof(Cx<T>));
     int* list = reinterpret_cast<int*>(p);
-    p += al(n_far * sizeof(int));
+    p += al(n_list * sizeof(int));
     BlockRange* ranges = reinterpret_cast<BlockRange*>(p);
+    p += al(n_far * sizeof(BlockRange));
+    Cx<T>* abuf = reinterpret_cast<Cx<T>*>(p);
     {
         long long tot = (long long)Ku * E;
         int blocks = (int)((tot + 255) / 256);
@@ -582,7 +632,7 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         // ranges come from the factors' host copy, the ranks from the device
         G3_CUDA(cudaMemcpyAsync(ranges, fa->ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice,
                                 ctx->stream));
-        G3_TRY_NA(launch_apply_far<T>(ctx, fa, list, ranges, Ku, E, Wf, Wc, y));
+        G3_TRY_NA(launch_apply_far<T>(ctx, fa, list, abuf, ranges, Ku, E, Wf, Wc, y));
     }
     {
         int blocks = (E + 255) / 256;

@@ -275,6 +275,11 @@ struct g3_factors {
     std::vector<g3::CrossRec> rec;     // host copy
     std::vector<g3::BlockRange> ranges;
     g3_stats stats{};
+    // far-field apply work lists (built on the first apply)
+    mutable bool plan_ready = false;
+    mutable std::vector<int> plan;
+    mutable int plan_nd = 0, plan_n1 = 0, plan_n2 = 0;
+    mutable long long plan_ab = 0;
     const g3_freqs* freqs = nullptr;
 };
 
