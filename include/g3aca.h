@@ -433,8 +433,8 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
  * cudaMalloc/cudaFree or other allocating routine is called.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture.  Problems needing more
- * scratch than 32 MiB (2 Ku M + M complex values, 16 bytes per admissible
- * block and 4 bytes per far-field work item) return G3_EINVAL.  All calls
+ * scratch than 32 MiB (2 Ku M + M complex values and 2 per face rank of the
+ * low-rank far field) return G3_EINVAL.  All calls
  * share the array: calls whose work overlaps on the GPU (other streams,
  * other threads) race and must be serialised by the caller. */
 g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,

@@ -414,6 +414,20 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         G3_CUDA(cudaMemcpy(d_queue.p, nq.data(), n_spill * sizeof(int), cudaMemcpyHostToDevice));
     }
     if (est > 0) scale = std::max(scale, 1.15 * (double)ctr / est);
+    // give back what the estimate over-reserved: a pool much larger than its
+    // use is moved into an exact-size buffer (its offsets stay valid)
+    if (ctr > 0 && (double)cap > 1.25 * (double)ctr && ((long long)cap - (long long)ctr) * (long long)sizeof(Cx<T>) > (256LL << 20)) {
+        DevBuf exact;
+        if (exact.alloc((size_t)ctr * sizeof(Cx<T>)) == cudaSuccess) {
+            G3_CUDA(cudaMemcpyAsync(exact.p, pool->p, (size_t)ctr * sizeof(Cx<T>), cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+            G3_CUDA(cudaStreamSynchronize(ctx->stream));
+            take(*pool, exact);
+            cap = (long long)ctr;
+        } else {
+            cudaGetLastError();  // keep the large pool
+        }
+    }
     unsigned long long cnt[32];
     G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
     std::vector<int32_t> r3(n_far);
@@ -493,6 +507,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
                 }
             }
         }
+        const g3_status pst = far_plan_build(fa);
+        if (pst != G3_OK) return pst;
     }
     return G3_OK;
 }

@@ -369,24 +369,26 @@ static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near*
     return G3_OK;
 }
 
-// Far-field work lists (host, cached in the factors): the dense-face blocks
-// (one warp each), padded to a multiple of 4 ints, then the phase-1 items
-// (block, group of FAR_PG crosses, column tile of FAR_NT, offset of the
-// group in the a/b buffer) and the phase-2 items (block, group, 0, offset).
+// Far-field work lists, built on the host when the compression ends and
+// uploaded with the block ranges: the dense-face blocks (one warp each),
+// padded to a multiple of 4 ints, then the phase-1 items (block, group of
+// FAR_PG crosses, column tile of FAR_NT, offset of the group in the a/b
+// buffer) and the phase-2 items (block, group, 0, offset).
 constexpr int FAR_PG = 4;
 constexpr int FAR_NT = 128;
 
-static void far_plan(const g3_factors* fa) {
-    if (fa->plan_ready) return;
+g3_status far_plan_build(g3_factors* fa) {
     std::vector<int>& L = fa->plan;
     L.clear();
     std::vector<int> p1, p2;
     long long ab = 0;
+    int mmax = 0;
     for (int b = 0; b < fa->n_far; ++b) {
         const int r = fa->r3[b];
         if (r <= 0) continue;
         if (fa->rec[(size_t)b * fa->Cmax].r < 0) {
             L.push_back(b);
+            mmax = std::max(mmax, fa->ranges[b].re - fa->ranges[b].rb);
             continue;
         }
         const int N = fa->ranges[b].ce - fa->ranges[b].cb;
@@ -398,45 +400,37 @@ static void far_plan(const g3_factors* fa) {
             p2.insert(p2.end(), {b, g, 0, (int)base});
         }
     }
+    if (ab >= (1LL << 31)) return fail(G3_EUNSUPPORTED, "aca3_compress: the far-field a/b buffer exceeds 2^31");
     fa->plan_nd = (int)L.size();
     fa->plan_n1 = (int)p1.size() / 4;
     fa->plan_n2 = (int)p2.size() / 4;
     fa->plan_ab = ab;
+    fa->plan_mmax_dense = mmax;
     while (L.size() % 4) L.push_back(0);  // int4 alignment of the item arrays
     L.insert(L.end(), p1.begin(), p1.end());
     L.insert(L.end(), p2.begin(), p2.end());
+    G3_CUDA(fa->d_plan.alloc(std::max<size_t>(1, L.size()) * sizeof(int)));
+    if (!L.empty()) G3_CUDA(cudaMemcpy(fa->d_plan.p, L.data(), L.size() * sizeof(int), cudaMemcpyHostToDevice));
+    G3_CUDA(fa->d_franges.alloc(std::max<size_t>(1, fa->ranges.size()) * sizeof(BlockRange)));
+    if (!fa->ranges.empty())
+        G3_CUDA(cudaMemcpy(fa->d_franges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
+                           cudaMemcpyHostToDevice));
     fa->plan_ready = true;
+    return G3_OK;
 }
 
-// ints of the far work lists and complex values of the a/b buffer
-static int far_list_len(const g3_factors* fa) {
-    far_plan(fa);
-    return (int)fa->plan.size();
-}
-static long long far_ab_len(const g3_factors* fa) {
-    far_plan(fa);
-    return fa->plan_ab;
-}
-
-// far-field launches; d_list: device space for far_list_len(fa) ints,
-// d_ab: for far_ab_len(fa) complex values (cleared here); d_ranges: the
-// block ranges on the device
+// far-field launches over the factors' device work lists; d_ab: space for
+// fa->plan_ab complex values (cleared here)
 template <class T>
-static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, int* d_list, Cx<T>* d_ab,
-                                  const BlockRange* d_ranges, int Ku, int E, const Cx<T>* Wf, const Cx<T>* Wc,
-                                  Cx<T>* y) {
-    far_plan(fa);
+static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, Cx<T>* d_ab, int Ku, int E, const Cx<T>* Wf,
+                                  const Cx<T>* Wc, Cx<T>* y) {
+    if (!fa->plan_ready) return fail(G3_EINVAL, "apply_gcq: factors without far-field work lists");
     if (fa->plan.empty()) return G3_OK;
-    if (fa->plan_ab >= (1LL << 31)) return fail(G3_EUNSUPPORTED, "apply_gcq: the far-field a/b buffer exceeds 2^31");
     const int nd = fa->plan_nd, n1 = fa->plan_n1, n2 = fa->plan_n2;
-    G3_CUDA(cudaMemcpyAsync(d_list, fa->plan.data(), fa->plan.size() * sizeof(int), cudaMemcpyHostToDevice,
-                            ctx->stream));
+    const int* d_list = fa->d_plan.as<int>();
+    const BlockRange* d_ranges = fa->d_franges.as<BlockRange>();
     if (nd > 0) {
-        int mmax_dense = 0;
-        for (int q = 0; q < nd; ++q) {
-            const BlockRange& r = fa->ranges[fa->plan[q]];
-            mmax_dense = std::max(mmax_dense, r.re - r.rb);
-        }
+        const int mmax_dense = fa->plan_mmax_dense;
         constexpr int NW = 8, PGW = 4;
         const size_t smem = (size_t)NW * (PGW * Ku + 2 * PGW * 32) * sizeof(Cx<T>);
         if (smem > ctx->smem_optin || mmax_dense > 96)
@@ -490,11 +484,13 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
                              void* Y, int dtype, const g3_freqs* f) {
     const int E = t->ne, K = f->K, Ku = f->Ku;
     const size_t nW = (size_t)Ku * E;
-    const size_t need = (2 * nW + E) * sizeof(Cx<T>) + 256;
+    const long long n_ab = fa ? fa->plan_ab : 0;
+    const size_t need = (2 * nW + E + (size_t)n_ab) * sizeof(Cx<T>) + 256;
     G3_CUDA(ctx->scratch.ensure(need));
     Cx<T>* Wf = ctx->scratch.as<Cx<T>>();
     Cx<T>* Wc = Wf + nW;
     Cx<T>* y = Wc + nW;
+    Cx<T>* abuf = reinterpret_cast<Cx<T>*>((reinterpret_cast<uintptr_t>(y + E) + 255) & ~uintptr_t(255));
     cudaEvent_t e0 = ctx->ev[2], e1 = ctx->ev[3], e2 = ctx->ev[4], e3 = ctx->ev[5];
     G3_CUDA(cudaEventRecord(e0, ctx->stream));
     {
@@ -512,17 +508,7 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     G3_CUDA(cudaEventRecord(e1, ctx->stream));
     if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
     G3_CUDA(cudaEventRecord(e2, ctx->stream));
-    if (fa && fa->n_far > 0) {
-        DevBuf d_list, d_ranges, d_ab;
-        G3_CUDA(d_list.alloc(std::max(1, far_list_len(fa)) * sizeof(int)));
-        G3_CUDA(d_ab.alloc(std::max(1LL, far_ab_len(fa)) * sizeof(Cx<T>)));
-        G3_CUDA(d_ranges.alloc(fa->ranges.size() * sizeof(BlockRange)));
-        G3_CUDA(cudaMemcpyAsync(d_ranges.p, fa->ranges.data(), fa->ranges.size() * sizeof(BlockRange),
-                                cudaMemcpyHostToDevice, ctx->stream));
-        G3_TRY_NA(launch_apply_far<T>(ctx, fa, d_list.as<int>(), d_ab.as<Cx<T>>(), d_ranges.as<BlockRange>(), Ku, E,
-                                      Wf, Wc, y));
-        G3_CUDA(cudaStreamSynchronize(ctx->stream));  // list buffers are released on return
-    }
+    if (fa && fa->n_far > 0) G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
     {
         int blocks = (E + 255) / 256;
         if (dtype == G3_C128)
@@ -592,14 +578,12 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
     const int n_far = fa ? fa->n_far : 0;
     const size_t nW = (size_t)Ku * E;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const int n_list = fa ? far_list_len(fa) : 0;
-    const long long n_ab = fa ? far_ab_len(fa) : 0;
-    const size_t need = al(2 * nW * sizeof(Cx<T>)) + al(E * sizeof(Cx<T>)) + al(n_list * sizeof(int)) +
-                        al(n_far * sizeof(BlockRange)) + al(n_ab * sizeof(Cx<T>));
+    const long long n_ab = fa ? fa->plan_ab : 0;
+    const size_t need = al(2 * nW * sizeof(Cx<T>)) + al(E * sizeof(Cx<T>)) + al(n_ab * sizeof(Cx<T>));
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(G3_EINVAL,
-                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values, "
-                    "block tables and far-field work lists), the fixed scratch holds %zu; use apply_gcq",
+                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values and "
+                    "2 per far-field face rank), the fixed scratch holds %zu; use apply_gcq",
                     need, NOALLOC_SCRATCH_BYTES);
     void* base = nullptr;
     G3_TRY_NA(noalloc_scratch(ctx->device, &base));
@@ -609,10 +593,6 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
     p += al(2 * nW * sizeof(Cx<T>));
     Cx<T>* y = reinterpret_cast<Cx<T>*>(p);
     p += al(E * sizeof(Cx<T>));
-    int* list = reinterpret_cast<int*>(p);
-    p += al(n_list * sizeof(int));
-    BlockRange* ranges = reinterpret_cast<BlockRange*>(p);
-    p += al(n_far * sizeof(BlockRange));
     Cx<T>* abuf = reinterpret_cast<Cx<T>*>(p);
     {
         long long tot = (long long)Ku * E;
@@ -627,13 +607,7 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         G3_CUDA(cudaGetLastError());
     }
     if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
-    if (n_far > 0) {
-        // every admissible block (blocks of rank 0 add nothing); the block
-        // ranges come from the factors' host copy, the ranks from the device
-        G3_CUDA(cudaMemcpyAsync(ranges, fa->ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice,
-                                ctx->stream));
-        G3_TRY_NA(launch_apply_far<T>(ctx, fa, list, abuf, ranges, Ku, E, Wf, Wc, y));
-    }
+    if (n_far > 0) G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
     {
         int blocks = (E + 255) / 256;
         if (dtype == G3_C128)

@@ -275,11 +275,15 @@ struct g3_factors {
     std::vector<g3::CrossRec> rec;     // host copy
     std::vector<g3::BlockRange> ranges;
     g3_stats stats{};
-    // far-field apply work lists (built on the first apply)
-    mutable bool plan_ready = false;
-    mutable std::vector<int> plan;
-    mutable int plan_nd = 0, plan_n1 = 0, plan_n2 = 0;
-    mutable long long plan_ab = 0;
+    // far-field apply work lists, built when the compression ends and kept
+    // on the device with the factors (the apply does no host work for them)
+    bool plan_ready = false;
+    std::vector<int> plan;             // host copy
+    int plan_nd = 0, plan_n1 = 0, plan_n2 = 0;
+    int plan_mmax_dense = 0;           // most rows of a dense-face block
+    long long plan_ab = 0;             // complex values of the a/b buffer
+    g3::DevBuf d_plan;                 // int [plan.size()]
+    g3::DevBuf d_franges;              // BlockRange [n_far]
     const g3_freqs* freqs = nullptr;
 };
 
@@ -298,6 +302,7 @@ namespace g3 {
 g3_status launch_freqs_bdf2(g3_ctx* ctx, int K, int Ku, double lam, double dt, double* d_sd, float* d_sf);
 g3_status launch_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, double* d_s, double* d_w);
 g3_status launch_geometry(g3_ctx* ctx, g3_tree* t);
+g3_status far_plan_build(g3_factors* fa);
 g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int kernel, int scheme, int prec,
                          const int* d_rows, const int* d_cols, int n, const int* d_ku, const int* d_conj, int nk,
                          double* d_out);
