@@ -104,8 +104,8 @@ typedef struct {
     int face_rank_max;    /* cap of a face ACA's rank (0 = 48; max 64)                     */
     int unbatched;        /* 1 = one block per launch sequence, host loop (plain baseline) */
     int ctas_per_sm;      /* persistent CTAs per SM (0 = from the occupancy calculator)    */
-    int threads;          /* threads per CTA of the low-rank-face launch: 256 or 512
-                             (512: G3_MIXED only); 0 = 256                               */
+    int threads;          /* threads per CTA of the low-rank-face launch: 128, 256 or
+                             512 (128 and 512: G3_MIXED only); 0 = 256                   */
     int no_recompress;    /* 1 = keep raw ACA faces (no QR+SVD)                            */
     int order_by_cost;    /* 1 (default when 0 is given: 1) = longest-first queue order    */
     const int32_t* k1;    /* optional host array [n_far]: first frequency per block
@@ -292,7 +292,7 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
 
 /* Autotuner of the compression's launch shape (no counterpart in the paper).
  * Times aca3_compress on (t, f) for each candidate -- threads per CTA of the
- * low-rank launch 256 or 512 (512: G3_MIXED only) and the dense-face
+ * low-rank launch 128, 256 or 512 (128, 512: G3_MIXED only) and the dense-face
  * threshold M_b N_b <= 24^2, 48^2 or 64^2 -- and writes the fastest into
  * opts->threads and opts->dense_face_max (the other fields of *opts are used
  * as given).  The choice is cached in ctx by (K_u bucket, largest far-block

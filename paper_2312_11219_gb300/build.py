@@ -25,6 +25,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_aca_sep.cu", "g3_aca_gal.cu", "g3_apply.cu",
               "g3_api.cu",
               "g3_probe.cu", "g3_mlp.cu"]
+# the compression-kernel instantiations of each kernel kind are compiled in
+# this many parts (-DG3_ACA_PART=0..), one nvcc process each
+ACA_PARTS = {"g3_aca_slp.cu": 3, "g3_aca_dlp.cu": 3, "g3_aca_sep.cu": 3, "g3_aca_gal.cu": 3}
 CPP_SOURCES = ["g3_tree.cpp"]
 
 
@@ -55,19 +58,24 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
     jobs = []
     objs = []
     for f in CU_SOURCES:
-        o = os.path.join(OBJDIR, f.replace(".cu", ".o"))
-        objs.append(o)
-        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-               "--expt-relaxed-constexpr", *inc, "-c", os.path.join(CSRC, f), "-o", o]
-        if ptxas_info:
-            cmd.insert(1, "-Xptxas=-v")
-        jobs.append(cmd)
+        parts = ACA_PARTS.get(f, 0)
+        for part in range(max(parts, 1)):
+            o = os.path.join(OBJDIR, f.replace(".cu", f"_{part}.o" if parts else ".o"))
+            objs.append(o)
+            cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "--expt-relaxed-constexpr", *inc, "-c", os.path.join(CSRC, f), "-o", o]
+            if parts:
+                cmd.insert(1, f"-DG3_ACA_PART={part}")
+            if ptxas_info:
+                cmd.insert(1, "-Xptxas=-v")
+            jobs.append(cmd)
     cxx = shutil.which("g++") or "g++"
     for f in CPP_SOURCES:
         o = os.path.join(OBJDIR, f.replace(".cpp", ".o"))
         objs.append(o)
         jobs.append([cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off",
                      "-I", os.path.join(CUDA_HOME, "include"), *inc, "-c", os.path.join(CSRC, f), "-o", o])
+    jobs.sort(key=lambda c: not any(a.startswith("-DG3_ACA_PART") for a in c))  # longest first
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 8))) as ex:
         results = list(ex.map(_run, jobs))
     for cmd, rc, out in results:

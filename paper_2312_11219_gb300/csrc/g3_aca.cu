@@ -10,6 +10,7 @@ namespace g3 {
 #define G3_ACA_EXTERN_KIND(KER)              \
     G3_ACA_EXTERN(KER, float, 256, false)    \
     G3_ACA_EXTERN(KER, float, 256, true)     \
+    G3_ACA_EXTERN(KER, float, 128, false)    \
     G3_ACA_EXTERN(KER, float, 512, false)    \
     G3_ACA_EXTERN(KER, double, 256, false)   \
     G3_ACA_EXTERN(KER, double, 256, true)
@@ -214,21 +215,24 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     // dynamic shared memory arena, reused phase by phase: the four RS x RS
     // float64 matrices of the recompression (+ Gram staging), the pivot-search
     // tiles (2 RF TM complex T, TM = 64 float / 32 double) and the eq. (norm)
-    // staging ((NORM_RC + 1) (32 + RF) complex T)
+    // staging ((NORM_RC + 1) (32 + RF) + 32 RF complex T)
     const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
                                 std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>));
     const size_t tile_bytes = 2 * (size_t)RF * (sizeof(T) == 4 ? 64 : 32) * sizeof(Cx<T>);
-    const size_t gram_bytes = (NORM_RC<T> + 1) * (size_t)(32 + RF) * sizeof(Cx<T>);
+    const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>);
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
     const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
-    // low-rank class: 256 or 512 threads per CTA (float32 path); more threads
-    // shorten each block, which matters for the largest blocks at the end
-    const int nt_low = (sizeof(T) == 4 && o.threads == 512) ? 512 : NT;
+    // low-rank class: 128, 256 or 512 threads per CTA (float32 path); more
+    // threads shorten each block, which matters for the largest blocks at the
+    // end, fewer keep more blocks in flight per SM
+    const int nt_low = (sizeof(T) == 4 && (o.threads == 128 || o.threads == 512)) ? o.threads : NT;
     int per_low = o.ctas_per_sm;
     if (per_low <= 0) {
         if constexpr (sizeof(T) == 4)
-            per_low = nt_low == 512 ? occupancy_kind<T, 512, false>(kernel, smem) : occupancy_kind<T, NT, false>(kernel, smem);
+            per_low = nt_low == 512   ? occupancy_kind<T, 512, false>(kernel, smem)
+                      : nt_low == 128 ? occupancy_kind<T, 128, false>(kernel, smem)
+                                      : occupancy_kind<T, NT, false>(kernel, smem);
         else
             per_low = occupancy_kind<T, NT, false>(kernel, smem);
     }
@@ -352,8 +356,9 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
                 if (cls == 1)
                     st = launch_kind<T, NT, true>(ctx, kernel, B, g, smem);
                 else if constexpr (sizeof(T) == 4)
-                    st = nt_low == 512 ? launch_kind<T, 512, false>(ctx, kernel, B, g, smem)
-                                       : launch_kind<T, NT, false>(ctx, kernel, B, g, smem);
+                    st = nt_low == 512   ? launch_kind<T, 512, false>(ctx, kernel, B, g, smem)
+                         : nt_low == 128 ? launch_kind<T, 128, false>(ctx, kernel, B, g, smem)
+                                         : launch_kind<T, NT, false>(ctx, kernel, B, g, smem);
                 else
                     st = launch_kind<T, NT, false>(ctx, kernel, B, g, smem);
             }

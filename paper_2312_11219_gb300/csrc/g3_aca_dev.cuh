@@ -198,6 +198,10 @@ struct BlockSh {
     Cx<double> gv[RF_MAX + 1];
     double sig[RF_MAX];
     double dU[RF_MAX], dV[RF_MAX];
+    double rdU[RF_MAX], rdV[RF_MAX];  // 1 / diagonal of the Cholesky factors
+    double fsn2;             // ||S_m||_F^2 of the face approximant (recursive)
+    int fconv;               // face test passed (written by warp 0)
+    int fbs;                 // sample of the largest residual
     int sel[RF_MAX];
     int piv;                 // pivoted QR of the core: pivot column of the step
     float rkk;               // and its norm
@@ -318,9 +322,10 @@ __device__ __forceinline__ Cx<T> colloc_q(const G& g, int i, int j, int q, T sre
     return {m * cs, -m * sn};
 }
 
-// part `part` of a gang of G threads evaluating ENTRY(gi, gj, k): with G >= 8
-// each of the first 7 parts evaluates one quadrature point; otherwise part 0
-// evaluates the whole entry.  The gang sum is the entry.
+// part `part` of a gang of G threads evaluating ENTRY(gi, gj, k): the
+// quadrature points (terms) are dealt round-robin to the parts, so that no
+// part idles while another evaluates the whole entry.  The gang sum is the
+// entry (admissible blocks hold no self entries).
 template <int KER, class T>
 __device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, int k, int part, int G) {
     if constexpr (KER == G3_SEPARABLE) {
@@ -349,17 +354,29 @@ __device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, i
         }
         return acc;
     } else {
-        if (G >= 8) {
-            if (part >= 7) return Cx<T>{0, 0};
-            if constexpr (sizeof(T) == 4) {
-                const float2 s = A.sf[k];
-                return colloc_q<KER>(A.gf, gi, gj, part, s.x, s.y);
-            } else {
-                const double2 s = A.sd[k];
-                return colloc_q<KER>(A.gd, gi, gj, part, s.x, s.y);
-            }
+        // the 7 quadrature points dealt round-robin to the gang's parts
+        if (G == 1) return ent<KER, T>(A, gi, gj, k);
+        T sre, sim;
+        if constexpr (sizeof(T) == 4) {
+            const float2 s = A.sf[k];
+            sre = s.x;
+            sim = s.y;
+        } else {
+            const double2 s = A.sd[k];
+            sre = s.x;
+            sim = s.y;
         }
-        return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
+        Cx<T> acc{0, 0};
+        for (int q = part; q < 7; q += G) {
+            Cx<T> v;
+            if constexpr (sizeof(T) == 4)
+                v = colloc_q<KER>(A.gf, gi, gj, q, sre, sim);
+            else
+                v = colloc_q<KER>(A.gd, gi, gj, q, sre, sim);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        return acc;
     }
 }
 
@@ -575,7 +592,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     const FaceTab<T> F = facetab_build<T, NT>(A, w, S, arena);
     for (int i = tid; i < M; i += NT) w.used[i] = 0;
     __syncthreads();
-    double Sn2 = 0.0;
+    if (tid == 0) S.fsn2 = 0.0;
     int m = 0;
     int irow = 0;
     bool converged = false;
@@ -647,14 +664,23 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             }
         }
         __syncthreads();
-        double cross = 0.0;
-        for (int t = 0; t < m; ++t) cross += 2.0 * (S.gu[t].x * S.gv[t].x - S.gu[t].y * S.gv[t].y);
-        const double nu2 = S.gu[m].x, nv2 = S.gv[m].x;
-        Sn2 += cross + nu2 * nv2;
+        // the float64 scalars of the test on warp 0 only (float64 runs at a
+        // small fraction of the float32 rate on this part)
+        if (wid == 0) {
+            double cross = 0.0;
+            for (int t = lane; t < m; t += 32) cross += 2.0 * (S.gu[t].x * S.gv[t].x - S.gu[t].y * S.gv[t].y);
+            cross = warp_sum(cross);
+            if (lane == 0) {
+                const double nu2 = S.gu[m].x, nv2 = S.gv[m].x;
+                const double sn2 = S.fsn2 + cross + nu2 * nv2;
+                S.fsn2 = sn2;
+                S.fconv = nu2 * nv2 <= fmax(A.eps_face * A.eps_face * fmax(sn2, 0.0), floor2);
+            }
+        }
         ++m;
         __syncthreads();
         sublap(S, 8, tf);
-        if (nu2 * nv2 <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
+        if (S.fconv) {
             if (!A.sample_check) {
                 converged = true;
                 break;
@@ -663,22 +689,30 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             // of the face that no visited row or column reaches
             face_samples<KER, T, NT>(A, w, S, F, kf, m);
             sublap(S, 9, tf);
-            double tot = 0.0, best = -1.0;
-            int bs = 0;
-            for (int sm = 0; sm < SAMPLES; ++sm) {
-                tot += S.samp[sm];
-                if (S.samp[sm] > best) {
-                    best = S.samp[sm];
-                    bs = sm;
+            static_assert(SAMPLES == 32, "one sample per lane");
+            if (wid == 0) {
+                const double sv = S.samp[lane];
+                const double tot = warp_sum(sv);
+                ArgMaxT<T> b{(T)sv, lane};
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ArgMaxT<T> y{__shfl_xor_sync(0xffffffffu, b.v, o), __shfl_xor_sync(0xffffffffu, b.i, o)};
+                    b = amax_better(b, y);
+                }
+                if (lane == 0) {
+                    S.fconv = (double)M * (double)N / SAMPLES * tot <=
+                              fmax(A.eps_face * A.eps_face * fmax(S.fsn2, 0.0), floor2);
+                    S.fbs = b.i;
                 }
             }
             __syncthreads();
-            if ((double)M * (double)N / SAMPLES * tot <= fmax(A.eps_face * A.eps_face * fmax(Sn2, 0.0), floor2)) {
+            if (S.fconv) {
                 converged = true;
                 break;
             }
             if (tid == 0) atomicAdd(&A.counters[5], 1ull);
-            irow = (2 * bs + 1) * M / (2 * SAMPLES);
+            irow = (2 * S.fbs + 1) * M / (2 * SAMPLES);
+            __syncthreads();  // S.fbs is rewritten by the next test
             continue;
         }
         if (nx.v < 0) break;  // every row used
@@ -984,7 +1018,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     for (int e = tid; e < 2 * r; e += NT) {
         const int mtx = e / r, a = e - mtx * r;
         const Cx<double>* R = mtx == 0 ? RU : RV;
-        (mtx == 0 ? S.dU : S.dV)[a] = 1.0 / sqrt(fmax(R[a * ld + a].x, 1e-300));
+        (mtx == 0 ? S.dU : S.dV)[a] = rsqrt(fmax(R[a * ld + a].x, 1e-300));
     }
     __syncthreads();
     for (int e = tid; e < 2 * r * r; e += NT) {
@@ -1008,7 +1042,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                 S.flag = 1;
                 continue;
             }
-            const double irkk = 1.0 / sqrt(dkk);
+            const double irkk = rsqrt(dkk);
             R[k * ld + j].x *= irkk;
             R[k * ld + j].y *= irkk;
         }
@@ -1026,7 +1060,10 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         }
         if (tid < 2) {
             Cx<double>* R = tid == 0 ? RU : RV;
-            R[k * ld + k] = Cx<double>{sqrt(fmax(R[k * ld + k].x, 0.0)), 0.0};
+            const double dkk = R[k * ld + k].x;
+            const double irkk = dkk > 0.0 ? rsqrt(dkk) : 0.0;
+            R[k * ld + k] = Cx<double>{dkk * irkk, 0.0};  // sqrt(dkk)
+            (tid == 0 ? S.rdU : S.rdV)[k] = irkk;          // its reciprocal
         }
         __syncthreads();
     }
@@ -1034,12 +1071,15 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     if (S.flag) return -1;
     // core C = R_U R_V^H with R_U = Rhat_U diag(1/dU): C[a][b] = sum_{c >= max(a,b)}
     //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in B, J = I
+    double* isc = S.sig;  // 1 / (dU[c] dV[c]); S.sig is free until the core is factored
+    for (int c = tid; c < r; c += NT) isc[c] = 1.0 / (S.dU[c] * S.dV[c]);
+    __syncthreads();
     for (int e = tid; e < r * r; e += NT) {
         const int a = e % r, b = e / r;
         Cx<double> acc{0, 0};
         for (int c = max(a, b); c < r; ++c) {
             Cx<double> x = RU[a * ld + c], y = RV[b * ld + c];
-            double s = 1.0 / (S.dU[c] * S.dV[c]);
+            const double s = isc[c];
             acc.x += (x.x * y.x + x.y * y.y) * s;
             acc.y += (x.y * y.x - x.x * y.y) * s;
         }
@@ -1075,6 +1115,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         const Cx<double>* R = isU ? RU : RV;
         Cx<T>* z = (isU ? shB : shJ) + S.sel[b] * ld;
         const double* dsc = isU ? S.dU : S.dV;
+        const double* rdg = isU ? S.rdU : S.rdV;
         for (int a = r - 1; a >= 0; --a) {
             Cx<double> acc = ccast<double>(z[a]);
             for (int c = a + 1; c < r; ++c) {
@@ -1083,7 +1124,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                 acc.x -= rr.x * zc.x - rr.y * zc.y;
                 acc.y -= rr.x * zc.y + rr.y * zc.x;
             }
-            double rd = 1.0 / R[a * ld + a].x;
+            const double rd = rdg[a];
             z[a] = Cx<T>{(T)(acc.x * rd), (T)(acc.y * rd)};
         }
         for (int a = 0; a < r; ++a) {
@@ -1112,7 +1153,12 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
 // hh[d] = <H_l, H_d>_F = sum_{a in cross d, b} (U_d^H U_l)[a][b] conj((V_d^H V_l)[a][b]) for the
 // earlier crosses d < nc, and hself = ||H_l||_F^2 (a over the columns of cross l).
 // Tiled: 32 columns of [U_1 .. U_nc U_l] at a time against all rn columns of U_l,
-// over NORM_RC-row chunks staged in shared memory (sh: >= (NORM_RC + 1) (32 + RF) complex T).
+// over NORM_RC-row chunks staged in shared memory; the products per (column,
+// b) go to a shared buffer and one warp per cross sums its own (sh: >=
+// (NORM_RC + 1) (32 + RF) + 32 RF complex T).  With recompressed factors one of
+// U, V has orthonormal columns, so the products have the scale of the face
+// values and are formed in the working precision; the sums over crosses are
+// float64.
 template <class T, int NT>
 __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, const Cx<T>* Vn, int rn,
                            Cx<T>* sh) {
@@ -1178,24 +1224,41 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
             }
         }
         // combine: contribution zu conj(zv) to the cross that owns column a
+        Cx<T>* pr = sb + rn * (RC + 1);  // [acnt][rn]
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
             const int o = tid + q * NT;
             if (o >= acnt * rn) break;
-            const int col = a0 + o / rn;
-            const double px = (double)zu[q].x * zv[q].x + (double)zu[q].y * zv[q].y;
-            const double py = (double)zu[q].y * zv[q].x - (double)zu[q].x * zv[q].y;
-            if (col < S.pre[nc]) {
-                int d = 0;
-                while (S.pre[d + 1] <= col) ++d;
-                atomicAdd(&S.hh[d].x, px);
-                atomicAdd(&S.hh[d].y, py);
-            } else {
-                atomicAdd(&S.hself, px);
+            pr[o] = Cx<T>{zu[q].x * zv[q].x + zu[q].y * zv[q].y, zu[q].y * zv[q].x - zu[q].x * zv[q].y};
+        }
+        __syncthreads();
+        // owners of the chunk's columns: crosses d_lo.. (d = nc: the new cross)
+        int d_lo = 0;
+        while (d_lo < nc && S.pre[d_lo + 1] <= a0) ++d_lo;
+        for (int d = d_lo + (tid >> 5); d <= nc; d += NT / 32) {
+            const int lane = tid & 31;
+            const int c_lo = max(a0, S.pre[d]);
+            const int c_hi = min(a0 + acnt, d < nc ? S.pre[d + 1] : na);
+            if (c_lo >= c_hi) continue;
+            T sx = 0, sy = 0;
+            for (int e = lane; e < (c_hi - c_lo) * rn; e += 32) {
+                const Cx<T> v = pr[(c_lo - a0) * rn + e];
+                sx += v.x;
+                sy += v.y;
+            }
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            if (lane == 0) {
+                if (d < nc) {
+                    S.hh[d].x += (double)sx;
+                    S.hh[d].y += (double)sy;
+                } else {
+                    S.hself += (double)sx;
+                }
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // ---- confirmed stop --------------------------------------------------------------------
@@ -1216,19 +1279,21 @@ template <int KER, class T, int NT>
 __device__ __noinline__ bool confirm_stop(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int ncl) {
     const int tid = threadIdx.x, Ku = A.Ku;
     const int M = S.M, N = S.N;
+    // H_p at the samples and the residuals in the working precision (values
+    // of the face's scale); the squared norms summed in float64
+    Cx<T>* hs = reinterpret_cast<Cx<T>*>(w.hs);
     for (int e = tid; e < SAMPLES * ncl; e += NT) {
         const int sm = e / ncl, p = e % ncl;
         const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
-        Cx<double> h{0, 0};
+        Cx<T> h{0, 0};
         if (S.r[p] < 0) {
-            h = ccast<double>(A.pool[S.off[p] + i + (long long)j * M]);
+            h = A.pool[S.off[p] + i + (long long)j * M];
         } else {
             const Cx<T>* U = A.pool + S.off[p];
             const Cx<T>* V = U + (long long)S.r[p] * M;
-            for (int t = 0; t < S.r[p]; ++t)
-                cfmac(h, ccast<double>(U[(long long)t * M + i]), ccast<double>(V[(long long)t * N + j]));
+            for (int t = 0; t < S.r[p]; ++t) cfmac(h, U[(long long)t * M + i], V[(long long)t * N + j]);
         }
-        w.hs[sm * A.Cmax + p] = h;
+        hs[sm * A.Cmax + p] = h;
     }
     if (tid == 0) {
         S.red2[0] = 0.0;
@@ -1236,23 +1301,30 @@ __device__ __noinline__ bool confirm_stop(const AcaArgs<T>& A, const Ws<T>& w, B
         S.entries += (long long)SAMPLES * Ku;
     }
     __syncthreads();
+    double rr_t = 0.0, aa_t = 0.0;
     for (int k = tid; k < Ku; k += NT) {
         double rr = 0.0, aa = 0.0;
         for (int sm = 0; sm < SAMPLES; ++sm) {
             const int i = (2 * sm + 1) * M / (2 * SAMPLES), j = (2 * ((11 * sm) % SAMPLES) + 1) * N / (2 * SAMPLES);
-            const Cx<double> a = ccast<double>(ent<KER, T>(A, S.rb + i, S.cb + j, k));
-            Cx<double> r = a;
+            const Cx<T> a = ent<KER, T>(A, S.rb + i, S.cb + j, k);
+            Cx<T> r = a;
             for (int p = 0; p < ncl; ++p) {
-                const Cx<double> c = cmul(w.hs[sm * A.Cmax + p], ccast<double>(f_of(A, S, p)[k]));
+                const Cx<T> c = cmul(hs[sm * A.Cmax + p], f_of(A, S, p)[k]);
                 r.x -= c.x;
                 r.y -= c.y;
             }
-            rr += cabs2(r);
-            aa += cabs2(a);
+            rr += cabs2d(r);
+            aa += cabs2d(a);
         }
         w.rk[k] = rr;
-        atomicAdd(&S.red2[0], rr);
-        atomicAdd(&S.red2[1], aa);
+        rr_t += rr;
+        aa_t += aa;
+    }
+    rr_t = warp_sum(rr_t);
+    aa_t = warp_sum(aa_t);
+    if ((tid & 31) == 0) {
+        atomicAdd(&S.red2[0], rr_t);
+        atomicAdd(&S.red2[1], aa_t);
     }
     __syncthreads();
     const bool ok = S.red2[0] <= A.eps3 * A.eps3 * S.red2[1];
@@ -1452,8 +1524,13 @@ __device__ void dense_block(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, 
 // ---- the persistent kernel ---------------------------------------------------------
 // DENSE selects the block class this launch serves (dense faces or low-rank
 // faces); the two classes run as two persistent launches with their own queues.
+// resident CTAs per SM the register allocation is sized for: 128 registers
+// a thread at 128 threads (4 CTAs), 256 (2 CTAs) and 512 (1 CTA)
+template <int NT>
+constexpr int aca_min_ctas() { return NT <= 128 ? 4 : (NT <= 256 ? 2 : 1); }
+
 template <int KER, class T, int NT, bool DENSE>
-__global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
+__global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3(const AcaArgs<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockSh<T> S;
     // the arguments of the block being processed: P, with the geometry and
@@ -1637,10 +1714,10 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
                 constexpr int TM = sizeof(T) == 4 ? 64 : 32;
                 constexpr int TN = TM;
                 constexpr int RM = TM * TN / NT >= 16 ? 4 : 2;  // micro-tile edge
-                constexpr int TX = TN / RM;                     // threads along j
+                constexpr int TX = TN / RM;                     // micro-tiles along j
+                constexpr int NMT = (TM / RM) * TX;             // micro-tiles per tile
                 Cx<T>* tu = reinterpret_cast<Cx<T>*>(smem_raw);  // [rn][TM]
                 Cx<T>* tv = tu + (size_t)RF * TM;                // [rn][TN]
-                const int tx = tid % TX, ty = tid / TX;
                 ArgMaxT<T> best = amax_none<T>();
                 for (int i0 = 0; i0 < M; i0 += TM) {
                     for (int j0 = 0; j0 < N; j0 += TN) {
@@ -1653,7 +1730,8 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
                             tv[b * TN + jj] = (j0 + jj < N) ? Vn[(long long)b * N + j0 + jj] : Cx<T>{0, 0};
                         }
                         __syncthreads();
-                        if (ty * RM < TM) {
+                        for (int mt = tid; mt < NMT; mt += NT) {
+                            const int tx = mt % TX, ty = mt / TX;
                             Cx<T> acc[RM][RM];
 #pragma unroll
                             for (int a = 0; a < RM; ++a)
@@ -1693,9 +1771,9 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
                     } else {
                         S.ip = (int)(best.i / N);
                         S.jp = (int)(best.i % N);
-                        Cx<double> h{0, 0};
-                        for (int b = 0; b < rn; ++b)
-                            cfmac(h, ccast<double>(Un[(long long)b * M + S.ip]), ccast<double>(Vn[(long long)b * N + S.jp]));
+                        Cx<T> hw{0, 0};
+                        for (int b = 0; b < rn; ++b) cfmac(hw, Un[(long long)b * M + S.ip], Vn[(long long)b * N + S.jp]);
+                        Cx<double> h = ccast<double>(hw);
                         if (!isfinite(h.x) || !isfinite(h.y)) h = Cx<double>{0.0, 0.0};
                         S.hpiv = h;
                     }
@@ -1704,14 +1782,13 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
             __syncthreads();
             lap(3);
             if (S.hpiv.x == 0.0 && S.hpiv.y == 0.0) break;  // vanishing face: nothing to divide by
-            // H_p[i_l, j_l] of earlier crosses (float64)
+            // H_p[i_l, j_l] of earlier crosses (values of the face's scale: working precision)
             for (int p = tid; p < S.ncross; p += NT) {
                 const Cx<T>* U = Up(A, S, p);
                 const Cx<T>* V = Vp(A, S, p);
-                Cx<double> h{0, 0};
-                for (int t = 0; t < S.r[p]; ++t)
-                    cfmac(h, ccast<double>(U[(long long)t * M + S.ip]), ccast<double>(V[(long long)t * N + S.jp]));
-                S.hp[p] = h;
+                Cx<T> h{0, 0};
+                for (int t = 0; t < S.r[p]; ++t) cfmac(h, U[(long long)t * M + S.ip], V[(long long)t * N + S.jp]);
+                S.hp[p] = ccast<double>(h);
             }
             __syncthreads();
             // ---------------- fiber (float64 residual) ----------------
@@ -1734,19 +1811,20 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
             lap(4);
             // ---------------- eq. (norm) ----------------
             // <f_l, f_d> and ||f_l||^2
+            // (the fibers are normalised by their pivot entry: working precision)
             for (int d = wid; d <= nc; d += NT / 32) {
-                Cx<double> acc{0, 0};
+                Cx<T> acc{0, 0};
                 if (d < nc) {
                     const Cx<T>* fd = Fp(A, S, d);
-                    for (int k = lane; k < Ku; k += 32) cfmac(acc, w.fib[k], ccast<double>(fd[k]));
+                    for (int k = lane; k < Ku; k += 32) cfmac(acc, Fn[k], fd[k]);
                 } else {
-                    for (int k = lane; k < Ku; k += 32) acc.x += cabs2(w.fib[k]);
+                    for (int k = lane; k < Ku; k += 32) acc.x += cabs2(Fn[k]);
                 }
                 acc.x = warp_sum(acc.x);
                 acc.y = warp_sum(acc.y);
                 if (lane == 0) {
-                    if (d < nc) S.ff[d] = acc;
-                    else S.fself = acc.x;
+                    if (d < nc) S.ff[d] = ccast<double>(acc);
+                    else S.fself = (double)acc.x;
                 }
             }
             for (int d = tid; d < nc; d += NT) S.hh[d] = Cx<double>{0, 0};
@@ -1801,7 +1879,7 @@ __global__ void __launch_bounds__(NT) k_aca3(const AcaArgs<T> P) {
             ArgMaxT<T> nk = amax_none<T>();
             for (int k = tid; k < Ku; k += NT)
                 if (!((S.used_k[k >> 5] >> (k & 31)) & 1u))
-                    nk = amax_better(nk, ArgMaxT<T>{(T)(from_samples ? w.rk[k] : cabs2(w.fib[k])), k});
+                    nk = amax_better(nk, ArgMaxT<T>{from_samples ? (T)w.rk[k] : cabs2(Fn[k]), k});
             nk = block_argmax<NT>(nk, S.am);
             if (nk.v < 0 || nk.i < 0 || nk.i >= Ku) break;  // no finite candidate left
             if (tid == 0) S.k = nk.i;

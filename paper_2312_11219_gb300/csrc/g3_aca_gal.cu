@@ -9,10 +9,18 @@ namespace g3 {
     template g3_status launch_aca_t<G3_GAL_SLP, T, NT, DENSE>(g3_ctx*, AcaArgs<T>&, int, size_t);        \
     template int occupancy<G3_GAL_SLP, T, NT, DENSE>(size_t);
 
+// compiled in three parts (G3_ACA_PART = 0, 1, 2) by separate compiler processes
+#if !defined(G3_ACA_PART) || G3_ACA_PART == 0
 G3_ACA_INST(float, 256, false)
+G3_ACA_INST(float, 128, false)
+#endif
+#if !defined(G3_ACA_PART) || G3_ACA_PART == 1
 G3_ACA_INST(float, 256, true)
 G3_ACA_INST(float, 512, false)
+#endif
+#if !defined(G3_ACA_PART) || G3_ACA_PART == 2
 G3_ACA_INST(double, 256, false)
 G3_ACA_INST(double, 256, true)
+#endif
 
 }  // namespace g3

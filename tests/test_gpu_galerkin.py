@@ -124,7 +124,7 @@ def test_autotune_picks_and_caches_a_launch_shape(g3, ctx):
     T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
     F = g3.freqs_from_spec(ctx, w.freq)
     first = g3.autotune(ctx, T, F, "slp", prec="mixed", eps3=w.eps3)
-    assert first["threads"] in (256, 512) and first["dense_face_max"] in (24 * 24, 48 * 48, 64 * 64)
+    assert first["threads"] in (128, 256, 512) and first["dense_face_max"] in (24 * 24, 48 * 48, 64 * 64)
     assert first["ms"] > 0
     again = g3.autotune(ctx, T, F, "slp", prec="mixed", eps3=w.eps3)
     assert again == {**first, "ms": 0.0}            # served from the context's cache

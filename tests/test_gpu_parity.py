@@ -269,6 +269,45 @@ def test_compression_cube768_blockwise(g3, ctx, prec, dense):
     assert abs(o.mean() - g.mean()) <= 0.1 * o.mean() + 0.5
 
 
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_compression_launch_shapes(g3, ctx, threads):
+    """Every CTA size of the low-rank launch computes Algorithm 1: blocks
+    within 10 eps3 of the oracle's dense blocks, and every cross's pivot the
+    largest entry of its face approximant H_l (the pivot step of Algorithm 1),
+    checked on blocks that span several 64-row tiles of the pivot search."""
+    w = workloads.get("lshape3072")
+    eps3 = 1e-4
+    geo, OT, fs, su, ef = _oracle_blocks(w, "slp", eps3)
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+    F = g3.freqs_from_spec(ctx, w.freq)
+    fa = g3.aca3_compress(ctx, T, F, "slp", prec="mixed", eps3=eps3, dense_face_max=-1, threads=threads)
+    st = fa.stats()
+    assert st["status_bits"] & 1 == 0 and st["dense_crosses"] == 0
+    far = [b for b in range(OT.blocks.shape[0]) if OT.blocks[b, 4] == 1]
+    rows = np.array([OT.blocks[b, 1] - OT.blocks[b, 0] for b in far])
+    cols = np.array([OT.blocks[b, 3] - OT.blocks[b, 2] for b in far])
+    big = np.flatnonzero((rows > 64) & (rows * cols <= 256 * 256))
+    assert big.size > 0
+    rng = np.random.default_rng(11)
+    order = np.argsort(-(rows * cols)[big], kind="stable")
+    check = sorted(set(big[order[:3]].tolist()) | set(rng.choice(big, min(3, big.size), replace=False).tolist()))
+    n_piv = 0
+    for i in check:
+        rb, re, cb, ce, _ = OT.blocks[far[i]]
+        M, N = re - rb, ce - cb
+        blk = fa.block(i, M, N, su.size)
+        for U, V, piv in zip(blk["U"], blk["V"], blk["piv"]):
+            H = np.abs(U @ V.conj().T)
+            assert H[piv[0], piv[1]] >= (1 - 1e-3) * H.max(), (i, piv, H.max())
+            n_piv += 1
+        D = O_q.dense(geo, "slp", su, rows=OT.perm[rb:re], cols=OT.perm[cb:ce])
+        A = np.zeros_like(D)
+        for U, V, f in zip(blk["U"], blk["V"], blk["f"]):
+            A += (U @ V.conj().T)[:, :, None] * f[None, None, :]
+        assert np.linalg.norm(A - D) <= 10 * eps3 * np.linalg.norm(D), i
+    assert n_piv > 0
+
+
 @pytest.mark.parametrize("dense", [0, -1])
 def test_apply_cube768_against_oracle(g3, ctx, dense):
     import torch
