@@ -167,10 +167,11 @@ typedef struct {
     double ms_mlp;            /* device time of the block features + predictor forward     */
     int64_t face_check_restarts;  /* face ACAs continued after a failed sample check       */
     int64_t stop_check_overrides; /* 3D stops overruled by the sampled residual check      */
-    int64_t sub_cycles[10];   /* SM cycles of sub-steps (thread 0 of each CTA, diagnostics):
-                                 recompression Gram, Cholesky, core, Jacobi SVD, rest;
-                                 face ACA table set-up, residual rows, residual columns,
-                                 approximant norm, sample checks                           */
+    int64_t sub_cycles[12];   /* SM cycles of sub-steps (thread 0 of each CTA, diagnostics):
+                                 recompression Gram, Cholesky, core, core factorisation,
+                                 rest; face ACA table set-up, residual rows, residual
+                                 columns, approximant norm, sample checks; of the residual
+                                 rows and columns: the entries; 0 (reserved)              */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */

@@ -213,11 +213,13 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     }
     constexpr int NT = 256;
     // dynamic shared memory arena, reused phase by phase: the four RS x RS
-    // float64 matrices of the recompression (+ Gram staging), the pivot-search
+    // matrices of the recompression (+ Gram staging; float32: + the working-
+    // precision copies of the two Cholesky factors), the pivot-search
     // tiles (2 RF TM complex T, TM = 64 float / 32 double) and the eq. (norm)
     // staging ((NORM_RC + 1) (32 + RF) + 32 RF complex T)
     const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
-                                std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>));
+                                std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>)) +
+                                (sizeof(T) == 4 ? 2 * (size_t)RS * RS * sizeof(Cx<T>) : 0);
     const size_t tile_bytes = 2 * (size_t)RF * (sizeof(T) == 4 ? 64 : 32) * sizeof(Cx<T>);
     const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>);
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
@@ -492,7 +494,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         S.mlp_used = mlp_use;
         S.ms_mlp = ms_mlp;
         for (int i = 0; i < 7; ++i) S.phase_cycles[i] = (int64_t)cnt[8 + i];
-        for (int i = 0; i < 10; ++i) S.sub_cycles[i] = (int64_t)cnt[16 + i];
+        for (int i = 0; i < NSUB; ++i) S.sub_cycles[i] = (int64_t)cnt[16 + i];
         S.ctas = grid;
         for (int b = 0; b < J.n; ++b) {
             const BlockRange& rg = fa->ranges[b];

@@ -40,7 +40,7 @@ namespace g3 {
 constexpr int KU_MAX = 256;   // largest unique-frequency count
 constexpr int SAMPLES = 32;   // sample entries of the convergence checks
 constexpr int NPH = 10;       // per-block diagnostics: 7 phases, steps, start, end
-constexpr int NSUB = 10;      // sub-step cycle counters (diagnostics)
+constexpr int NSUB = 11;      // sub-step cycle counters (diagnostics)
 // rows staged per pass of the eq. (norm) Gram products
 template <class T>
 constexpr int NORM_RC = sizeof(T) == 4 ? 64 : 32;
@@ -199,6 +199,8 @@ struct BlockSh {
     double sig[RF_MAX];
     double dU[RF_MAX], dV[RF_MAX];
     double rdU[RF_MAX], rdV[RF_MAX];  // 1 / diagonal of the Cholesky factors
+    T tdU[RF_MAX], tdV[RF_MAX];       // dU, dV and rdU, rdV in the working precision
+    T trdU[RF_MAX], trdV[RF_MAX];
     double fsn2;             // ||S_m||_F^2 of the face approximant (recursive)
     int fconv;               // face test passed (written by warp 0)
     int fbs;                 // sample of the largest residual
@@ -491,9 +493,23 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
         Cx<T> acc{0, 0};
         if (v < L) {
             const int gi = S.rb + (ROW ? fix : v), gj = S.cb + (ROW ? v : fix);
+            const long long te = tid == 0 ? clock64() : 0;
             acc = ent_part<KER, T>(A, gi, gj, kf, part, G);
+            if (tid == 0) S.sub[10] += clock64() - te;
             Cx<T> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
             int c = part;
+            // 8 loads in flight per thread (the sums wait on memory, not on arithmetic)
+            for (; c + 7 * G < nt; c += 8 * G) {
+                Cx<T> x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = A.pool[col[c + u * G] + v];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    Cx<T>& acc_u = (u & 3) == 0 ? s0 : (u & 3) == 1 ? s1 : (u & 3) == 2 ? s2 : s3;
+                    if (ROW) cfmac(acc_u, F.coef[c + u * G], x[u]);
+                    else cfma(acc_u, x[u], F.coef[c + u * G]);
+                }
+            }
             for (; c + 3 * G < nt; c += 4 * G) {
                 const Cx<T> x0 = A.pool[col[c] + v], x1 = A.pool[col[c + G] + v];
                 const Cx<T> x2 = A.pool[col[c + 2 * G] + v], x3 = A.pool[col[c + 3 * G] + v];
@@ -1069,6 +1085,28 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     }
     sublap(S, 1, tc);
     if (S.flag) return -1;
+    // working-precision copies of Rhat_U, Rhat_V (upper triangles) and of the
+    // scalings for the back substitution (float32: after the two r x r float64
+    // matrices and B, J in shared memory, or in the workspace's T_V block)
+    Cx<T>* RUf = small ? reinterpret_cast<Cx<T>*>(smem + 2 * RS * RS) + 2 * RS * RS : reinterpret_cast<Cx<T>*>(w.TV);
+    Cx<T>* RVf = RUf + (small ? RS * RS : A.RF * A.RF);
+    if constexpr (sizeof(T) == 4) {
+        for (int e = tid; e < 2 * r * r; e += NT) {
+            const int mtx = e / (r * r), q = e - mtx * r * r, a = q / r, c = q - a * r;
+            if (c < a) continue;
+            (mtx == 0 ? RUf : RVf)[a * ld + c] = ccast<T>((mtx == 0 ? RU : RV)[a * ld + c]);
+        }
+        for (int e = tid; e < 2 * r; e += NT) {
+            const int a = e < r ? e : e - r;
+            if (e < r) {
+                S.tdU[a] = (T)S.dU[a];
+                S.trdU[a] = (T)S.rdU[a];
+            } else {
+                S.tdV[a] = (T)S.dV[a];
+                S.trdV[a] = (T)S.rdV[a];
+            }
+        }
+    }
     // core C = R_U R_V^H with R_U = Rhat_U diag(1/dU): C[a][b] = sum_{c >= max(a,b)}
     //   RhatU[a][c] conj(RhatV[b][c]) / (dU[c] dV[c]); stored column-major in B, J = I
     double* isc = S.sig;  // 1 / (dU[c] dV[c]); S.sig is free until the core is factored
@@ -1108,7 +1146,33 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
     }
     sublap(S, 3, tc);
     // T_U[:, b] = diag(dU) RhatU^{-1} B[:, sel[b]],  T_V[:, b] = diag(dV) RhatV^{-1} J[:, sel[b]]
-    // (float64 back substitution, in place on the selected columns)
+    // in place on the selected columns.  float32: in the working precision (the
+    // columns of B and J are held in it already, so the solve's forward error
+    // is of the order cond(Rhat) u either way); float64: in float64.
+    if constexpr (sizeof(T) == 4) {
+        for (int item = tid; item < 2 * rn; item += NT) {
+            const bool isU = item < rn;
+            const int b = isU ? item : item - rn;
+            const Cx<T>* R = isU ? RUf : RVf;
+            Cx<T>* z = (isU ? shB : shJ) + S.sel[b] * ld;
+            const T* dsc = isU ? S.tdU : S.tdV;
+            const T* rdg = isU ? S.trdU : S.trdV;
+            for (int a = r - 1; a >= 0; --a) {
+                Cx<T> acc = z[a];
+                for (int c = a + 1; c < r; ++c) {
+                    const Cx<T> rr = R[a * ld + c], zc = z[c];
+                    acc.x -= rr.x * zc.x - rr.y * zc.y;
+                    acc.y -= rr.x * zc.y + rr.y * zc.x;
+                }
+                const T rd = rdg[a];
+                z[a] = Cx<T>{acc.x * rd, acc.y * rd};
+            }
+            for (int a = 0; a < r; ++a) {
+                z[a].x *= dsc[a];
+                z[a].y *= dsc[a];
+            }
+        }
+    } else
     for (int item = tid; item < 2 * rn; item += NT) {
         const bool isU = item < rn;
         const int b = isU ? item : item - rn;
