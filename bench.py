@@ -347,7 +347,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     apply_gbs = r0["apply_bytes"] / (apply_ms / 1e3) / 1e9
     near_gbs = r0["apply_near_bytes"] / (near_ms / 1e3) / 1e9
     # far part of the apply (everything but the near-field stream: factors,
-    # W read once, y written once)
+    # W read once, y written once); the near field runs on a second stream
+    # next to the far-field kernels, so this is the far part's share of the
+    # apply's wall time
     far_gbs = (r0["apply_bytes"] - r0["apply_near_bytes"]) / ((apply_ms - near_ms) / 1e3) / 1e9
     # plain baseline: float64, one block per launch (host loop), on a bounded
     # sample of the first admissible blocks of the single layer

@@ -227,6 +227,10 @@ struct BlockSh {
     int ip, jp;
 };
 
+// sh: NT / 32 + 1 slots; the result goes to its own slot, so two barriers
+// suffice (the next call writes the per-warp slots only after every thread
+// has passed this call's second barrier, and the result slot only after its
+// own first one)
 template <int NT, class V>
 __device__ __forceinline__ ArgMaxT<V> block_argmax(ArgMaxT<V> a, ArgMaxT<V>* sh) {
     a = warp_argmax(a);
@@ -236,12 +240,10 @@ __device__ __forceinline__ ArgMaxT<V> block_argmax(ArgMaxT<V> a, ArgMaxT<V>* sh)
     if (w == 0) {
         ArgMaxT<V> b = (l < NT / 32) ? sh[l] : amax_none<V>();
         b = warp_argmax(b);
-        if (l == 0) sh[0] = b;
+        if (l == 0) sh[NT / 32] = b;
     }
     __syncthreads();
-    ArgMaxT<V> r = sh[0];
-    __syncthreads();
-    return r;
+    return sh[NT / 32];
 }
 
 template <class T>

@@ -87,6 +87,20 @@ g3_status g3_create(int device, void* cuda_stream, g3_ctx** out) {
             return cuda_fail(e, "cudaEventCreate");
         }
     }
+    for (auto& ev : c->ev_side) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            g3_destroy(c);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g3_destroy(c);
+        return cuda_fail(e, "side stream / events");
+    }
     e = c->status.alloc(64);
     if (e != cudaSuccess) {
         g3_destroy(c);
@@ -112,6 +126,11 @@ g3_status g3_destroy(g3_ctx* ctx) {
     cudaSetDevice(ctx->device);
     for (auto& ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto& ev : ctx->ev_side)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
     return G3_OK;
 }

@@ -123,8 +123,11 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
 // V^H zc, 2 r_p complex values per cross, from ab_base on):
 //   phase 1, item (block, group, column tile of NT):
 //     x_p[j] = sum_k f_p[k] w_k[j], zc_p[j] = sum_k f_p[k] conj(w_k'[j]) for the
-//     tile's columns (W read once per group and tile), then the tile's part
-//     of a_p = V_p^H x_p and b_p = V_p^H zc_p, added to ab;
+//     tile's columns (thread j; W read once per group and tile), kept in
+//     shared memory; then one warp per (p, t) forms the tile's part of
+//     a_p[t] = V_p[:, t]^H x_p and b_p[t] = V_p[:, t]^H zc_p (lanes over the
+//     columns, coalesced reads of V, one warp reduction per pair) and adds it
+//     to ab;
 //   phase 2, item (block, group): y += U_p a_p + conj(U_p b_p).
 // Each factor is read once; the many small items keep the SMs busy.
 template <class T, int NT, int PG>
@@ -135,20 +138,21 @@ __global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, c
                                                Cx<T>* __restrict__ ab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);  // [PG][Ku]
-    Cx<T>* acc = fg + PG * Ku;                        // [2 * sum r_p] partial a_p, b_p
+    Cx<T>* xs = fg + PG * Ku;                         // [PG][NT] x_p of the tile
+    Cx<T>* zs = xs + PG * NT;                         // [PG][NT] zc_p of the tile
     __shared__ CrossRec crs[PG];
-    __shared__ int offs[PG + 1];
+    __shared__ int pre[PG + 1];  // prefix sums of the ranks
     const int4 it = items[blockIdx.x];  // block, group, column tile, a/b offset
     const int blk = it.x, g0 = it.y * PG, jt = it.z;
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
     const int np = min(PG, r3[blk] - g0);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < PG) crs[tid] = tid < np ? rec[(size_t)blk * Cmax + g0 + tid] : CrossRec{0, 0, 0, 0, 0};
     __syncthreads();
     if (tid == 0) {
-        offs[0] = 0;
-        for (int p = 0; p < PG; ++p) offs[p + 1] = offs[p] + (p < np ? 2 * crs[p].r : 0);
+        pre[0] = 0;
+        for (int p = 0; p < PG; ++p) pre[p + 1] = pre[p] + (p < np ? crs[p].r : 0);
     }
     for (int e = tid; e < PG * Ku; e += NT) {
         const int p = e / Ku, k = e - p * Ku;
@@ -157,52 +161,58 @@ __global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, c
         fg[e] = v;
     }
     __syncthreads();
-    for (int e = tid; e < offs[PG]; e += NT) acc[e] = Cx<T>{0, 0};
-    const int j = jt * NT + tid;
-    Cx<T> x[PG], z[PG];
+    const int j0 = jt * NT, jn = min(NT, N - j0);
+    {
+        const int j = j0 + tid;
+        Cx<T> x[PG], z[PG];
 #pragma unroll
-    for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
-    if (j < N) {
-        const Cx<T>* wf = Wf + br.cb + j;
-        const Cx<T>* wc = Wc + br.cb + j;
+        for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
+        if (tid < jn) {
+            const Cx<T>* wf = Wf + br.cb + j;
+            const Cx<T>* wc = Wc + br.cb + j;
 #pragma unroll 4
-        for (int k = 0; k < Ku; ++k) {
-            const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
+            for (int k = 0; k < Ku; ++k) {
+                const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
 #pragma unroll
-            for (int p = 0; p < PG; ++p) {
-                const Cx<T> f = fg[p * Ku + k];
-                cfma(x[p], f, a);
-                cfmac(z[p], f, b);
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PG; ++p) {
-        if (p < np) {
-            const int r = crs[p].r;
-            const Cx<T>* V = pool + crs[p].off + (long long)r * M;
-            for (int t = 0; t < r; ++t) {
-                const Cx<T> v = j < N ? V[(long long)t * N + j] : Cx<T>{0, 0};
-                Cx<T> pa = cmulc(x[p], v), pb = cmulc(z[p], v);  // conj(v) x, conj(v) zc
-                pa.x = warp_sum(pa.x);
-                pa.y = warp_sum(pa.y);
-                pb.x = warp_sum(pb.x);
-                pb.y = warp_sum(pb.y);
-                if (lane == 0) {
-                    Cx<T>* q = acc + offs[p] + 2 * t;
-                    atomicAdd(&q[0].x, pa.x);
-                    atomicAdd(&q[0].y, pa.y);
-                    atomicAdd(&q[1].x, pb.x);
-                    atomicAdd(&q[1].y, pb.y);
+                for (int p = 0; p < PG; ++p) {
+                    const Cx<T> f = fg[p * Ku + k];
+                    cfma(x[p], f, a);
+                    cfmac(z[p], f, b);
                 }
             }
         }
+#pragma unroll
+        for (int p = 0; p < PG; ++p) {
+            xs[p * NT + tid] = x[p];
+            zs[p * NT + tid] = z[p];
+        }
     }
     __syncthreads();
-    for (int e = tid; e < offs[PG]; e += NT) {
-        atomicAdd(&ab[it.w + e].x, acc[e].x);
-        atomicAdd(&ab[it.w + e].y, acc[e].y);
+    const int npt = pre[PG];
+    for (int q = warp; q < npt; q += NT / 32) {
+        int p = 0;
+        while (pre[p + 1] <= q) ++p;
+        const int t = q - pre[p];
+        const Cx<T>* V = pool + crs[p].off + (long long)crs[p].r * M + (long long)t * N + j0;
+        const Cx<T>* xp = xs + p * NT;
+        const Cx<T>* zp = zs + p * NT;
+        Cx<T> pa{0, 0}, pb{0, 0};
+        for (int jj = lane; jj < jn; jj += 32) {
+            const Cx<T> v = V[jj];
+            cfmac(pa, xp[jj], v);  // conj(v) x
+            cfmac(pb, zp[jj], v);  // conj(v) zc
+        }
+        pa.x = warp_sum(pa.x);
+        pa.y = warp_sum(pa.y);
+        pb.x = warp_sum(pb.x);
+        pb.y = warp_sum(pb.y);
+        if (lane == 0) {
+            Cx<T>* o = ab + it.w + 2 * (pre[p] + t);
+            atomicAdd(&o[0].x, pa.x);
+            atomicAdd(&o[0].y, pa.y);
+            atomicAdd(&o[1].x, pb.x);
+            atomicAdd(&o[1].y, pb.y);
+        }
     }
 }
 
@@ -348,8 +358,8 @@ __global__ void k_apply_finish(int E, const int* __restrict__ perm, const Cx<T>*
 // near-field launch: grid (row clusters) x (frequency chunks), about 16 CTAs
 // per SM so that the last wave is short
 template <class T>
-static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, int Ku, int E,
-                                   const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y) {
+static g3_status launch_apply_near(g3_ctx* ctx, cudaStream_t stream, const g3_tree* t, const g3_near* nf, int Ku,
+                                   int E, const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y) {
     constexpr int NT = 256;
     const int n_rows = (int)nf->row_start.size() - 1;
     int ksplit = std::max(1, std::min(Ku, (16 * ctx->n_sm + n_rows - 1) / n_rows));
@@ -361,7 +371,7 @@ static g3_status launch_apply_near(g3_ctx* ctx, const g3_tree* t, const g3_near*
         mrow = std::max(mrow, r[1] - r[0]);
     }
     dim3 grid(n_rows, ksplit);
-    k_apply_near<T, NT><<<grid, NT, (NT / 32) * 2 * (size_t)mrow * sizeof(T), ctx->stream>>>(
+    k_apply_near<T, NT><<<grid, NT, (NT / 32) * 2 * (size_t)mrow * sizeof(T), stream>>>(
         nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(), nf->d_offs.as<long long>(), nf->d_row_start.as<int>(),
         Ku, kchunk, E, Wf, Wc, y);
     ctx->count("k_apply_near");
@@ -457,8 +467,7 @@ static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, Cx<T>* d_ab
     }
     if (n1 > 0) {
         G3_CUDA(cudaMemsetAsync(d_ab, 0, (size_t)fa->plan_ab * sizeof(Cx<T>), ctx->stream));
-        const int rmax = std::max(1, (int)fa->stats.face_rank_max);
-        const size_t smem = ((size_t)FAR_PG * Ku + 2 * (size_t)FAR_PG * rmax) * sizeof(Cx<T>);
+        const size_t smem = ((size_t)FAR_PG * Ku + 2 * (size_t)FAR_PG * FAR_NT) * sizeof(Cx<T>);
         if (smem > ctx->smem_optin)
             return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
         const int4* it1 = reinterpret_cast<const int4*>(d_list + (nd + 3) / 4 * 4);
@@ -479,6 +488,35 @@ static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, Cx<T>* d_ab
     return G3_OK;
 }
 
+// Near field and far field of one apply.  With both present the near field
+// (an HBM stream) runs on the context's side stream next to the far-field
+// kernels (bound by latency and L2 traffic rather than HBM), forked from and
+// joined back into the main stream; both add into y atomically.  ev_side
+// brackets the near field (its device time).
+template <class T>
+static g3_status apply_near_far(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, int Ku,
+                                int E, const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y, Cx<T>* abuf) {
+    const bool has_near = nf && !nf->order.empty(), has_far = fa && fa->n_far > 0;
+    if (has_near && has_far) {
+        G3_CUDA(cudaEventRecord(ctx->fork, ctx->stream));
+        G3_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+        G3_CUDA(cudaEventRecord(ctx->ev_side[0], ctx->side));
+        G3_TRY_NA(launch_apply_near<T>(ctx, ctx->side, t, nf, Ku, E, Wf, Wc, y));
+        G3_CUDA(cudaEventRecord(ctx->ev_side[1], ctx->side));
+        G3_CUDA(cudaEventRecord(ctx->join, ctx->side));
+        G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
+        G3_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->join, 0));
+        return G3_OK;
+    }
+    if (has_near) {
+        G3_CUDA(cudaEventRecord(ctx->ev_side[0], ctx->stream));
+        G3_TRY_NA(launch_apply_near<T>(ctx, ctx->stream, t, nf, Ku, E, Wf, Wc, y));
+        G3_CUDA(cudaEventRecord(ctx->ev_side[1], ctx->stream));
+    }
+    if (has_far) G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
+    return G3_OK;
+}
+
 template <class T>
 static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
                              void* Y, int dtype, const g3_freqs* f) {
@@ -491,7 +529,7 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     Cx<T>* Wc = Wf + nW;
     Cx<T>* y = Wc + nW;
     Cx<T>* abuf = reinterpret_cast<Cx<T>*>((reinterpret_cast<uintptr_t>(y + E) + 255) & ~uintptr_t(255));
-    cudaEvent_t e0 = ctx->ev[2], e1 = ctx->ev[3], e2 = ctx->ev[4], e3 = ctx->ev[5];
+    cudaEvent_t e0 = ctx->ev[2], e3 = ctx->ev[5];
     G3_CUDA(cudaEventRecord(e0, ctx->stream));
     {
         long long tot = (long long)Ku * E;
@@ -505,10 +543,7 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
         ctx->count("k_apply_prep");
         G3_CUDA(cudaGetLastError());
     }
-    G3_CUDA(cudaEventRecord(e1, ctx->stream));
-    if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
-    G3_CUDA(cudaEventRecord(e2, ctx->stream));
-    if (fa && fa->n_far > 0) G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
+    G3_TRY_NA(apply_near_far<T>(ctx, t, nf, fa, Ku, E, Wf, Wc, y, abuf));
     {
         int blocks = (E + 255) / 256;
         if (dtype == G3_C128)
@@ -522,7 +557,7 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     G3_CUDA(cudaEventSynchronize(e3));
     float ms_all = 0, ms_near = 0;
     G3_CUDA(cudaEventElapsedTime(&ms_all, e0, e3));
-    G3_CUDA(cudaEventElapsedTime(&ms_near, e1, e2));
+    if (nf && !nf->order.empty()) G3_CUDA(cudaEventElapsedTime(&ms_near, ctx->ev_side[0], ctx->ev_side[1]));
     ctx->last_apply_ms = ms_all;
     ctx->last_near_ms = ms_near;
     const int64_t in_sz = dtype == G3_C128 ? 16 : 8;
@@ -606,8 +641,7 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         ctx->count("k_apply_prep");
         G3_CUDA(cudaGetLastError());
     }
-    if (nf && !nf->order.empty()) G3_TRY_NA(launch_apply_near<T>(ctx, t, nf, Ku, E, Wf, Wc, y));
-    if (n_far > 0) G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
+    G3_TRY_NA(apply_near_far<T>(ctx, t, nf, n_far > 0 ? fa : nullptr, Ku, E, Wf, Wc, y, abuf));
     {
         int blocks = (E + 255) / 256;
         if (dtype == G3_C128)

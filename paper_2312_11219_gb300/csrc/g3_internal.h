@@ -190,6 +190,11 @@ struct g3_ctx {
     g3::DevBuf status;       // device status word(s)
     g3::DevBuf stage_w, stage_y;  // device staging of host W / Y in apply_gcq
     cudaEvent_t ev[6] = {};
+    // a second stream on which the apply runs its near field next to the far
+    // field (fork / join through events; ev_side times the near field there)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t ev_side[2] = {};
     double last_apply_ms = 0, last_near_ms = 0;
     double pool_scale = 1.0;  // factor-pool size / estimate needed by earlier compressions
     double pool_scale_mlp = 1.0;  // the same for the predictor-based estimate
