@@ -672,8 +672,13 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             const Cx<T>* ut = w.uw + (size_t)t * A.Mmax;
             const Cx<T>* vt = w.vw + (size_t)t * A.Nmax;
             Cx<T> gu{0, 0}, gv{0, 0};
-            for (int i = lane; i < M; i += 32) cfmac(gu, um[i], ut[i]);  // conj(u_t) u_m
-            for (int j = lane; j < N; j += 32) cfmac(gv, vt[j], vm[j]);  // conj(v_m) v_t
+            // both sums in one loop, unrolled: their loads are in flight together
+            const int L = max(M, N);
+#pragma unroll 4
+            for (int i = lane; i < L; i += 32) {
+                if (i < M) cfmac(gu, um[i], ut[i]);  // conj(u_t) u_m
+                if (i < N) cfmac(gv, vt[i], vm[i]);  // conj(v_m) v_t
+            }
             const T gux = warp_sum(gu.x), guy = warp_sum(gu.y);
             const T gvx = warp_sum(gv.x), gvy = warp_sum(gv.y);
             if (lane == 0) {
@@ -795,6 +800,16 @@ __device__ void gram_upper(const Cx<T>* X, size_t ld, int L, int r, Cx<double>* 
 #pragma unroll
     for (int q = 0; q < QMAX; ++q)
         if (pa[q] >= 0) G[pa[q] * RF + pb[q]] = acc[q];
+}
+
+// 1 / sqrt(x) in float64 for the Cholesky pivots of the column-scaled Gram
+// matrices (x in (1e-24, 1], inside the float32 range): a float32 estimate
+// refined by one Newton-Raphson step for the inverse square root,
+// y <- y (3 - x y^2) / 2, which squares its relative error (~1e-7 -> ~1e-14)
+// at the cost of a few float64 operations.
+__device__ __forceinline__ double rsqrt_pivot(double x) {
+    const double y = (double)rsqrtf((float)x);
+    return y * (1.5 - 0.5 * x * y * y);
 }
 
 // ---- recompression: Cholesky-QR + one-sided Jacobi SVD ---------------------------------
@@ -1060,7 +1075,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
                 S.flag = 1;
                 continue;
             }
-            const double irkk = rsqrt(dkk);
+            const double irkk = rsqrt_pivot(dkk);
             R[k * ld + j].x *= irkk;
             R[k * ld + j].y *= irkk;
         }
@@ -1079,7 +1094,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         if (tid < 2) {
             Cx<double>* R = tid == 0 ? RU : RV;
             const double dkk = R[k * ld + k].x;
-            const double irkk = dkk > 0.0 ? rsqrt(dkk) : 0.0;
+            const double irkk = dkk > 1e-24 ? rsqrt_pivot(dkk) : 0.0;
             R[k * ld + k] = Cx<double>{dkk * irkk, 0.0};  // sqrt(dkk)
             (tid == 0 ? S.rdU : S.rdV)[k] = irkk;          // its reciprocal
         }
