@@ -448,6 +448,35 @@ def run_reference(args) -> dict:
             "gpu_launches": 0}
 
 
+def run_profile_case(args) -> dict:
+    """One small invocation for a profiler (no timing loop, no baselines): the
+    workload's tree and frequencies, one compression of `--profile-case`'s
+    operator (256 threads, dense faces up to 48^2), then the near field and two
+    applies.  Launch order: the compression's low-rank launch, its dense-face
+    launch, the near-field assembly, then per apply k_apply_prep,
+    k_apply_near, k_apply_far_dense, k_far_vx, k_far_uy, k_apply_finish."""
+    import torch
+    import paper_2312_11219_gb300 as g3
+    from inputs import workloads
+    w = workloads.get(args.workload)
+    ker = args.profile_case
+    ctx = g3.Context(0)
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
+    F = g3.freqs_from_spec(ctx, w.freq)
+    fa = g3.aca3_compress(ctx, T, F, ker, scheme=w.scheme, prec=args.precision, eps3=w.eps3, threads=256,
+                          dense_face_max=48 * 48)
+    nf = g3.assemble_near(ctx, T, F, ker, scheme=w.scheme, prec=args.precision)
+    dt = torch.complex64 if args.precision == "mixed" else torch.complex128
+    Wd = torch.from_numpy(workloads.densities(w.E, w.freq.K, w.density_seed)).to("cuda", dt)
+    for _ in range(2):
+        g3.apply_gcq(ctx, T, nf, fa, Wd)
+    torch.cuda.synchronize()
+    st, la = fa.stats(), ctx.last_apply()
+    return {"profile_case": ker, "workload": args.workload, "aca_ms": st["ms"], "aca_lowrank_ms": st["ms_lowrank"],
+            "crosses": st["crosses"], "entries": st["entries"], "n_far": st["n_far"], "apply_ms": la["ms"],
+            "apply_bytes": la["bytes"], "near_ms": la["near_ms"], "near_bytes": la["near_bytes"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,7 +492,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--mlp-use", type=int, default=3,
                     help="predictor uses in the timed compressions (1 order, 2 pool, 4 k1; 0 = no predictor)")
+    ap.add_argument("--profile-case", default=None, choices=["slp", "dlp"],
+                    help="run one compression and two applies of --workload for a profiler, then exit")
     args = ap.parse_args()
+    if args.profile_case:
+        print(json.dumps(run_profile_case(args)), flush=True)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

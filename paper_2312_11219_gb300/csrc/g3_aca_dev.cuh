@@ -504,7 +504,7 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
             for (; c + 7 * G < nt; c += 8 * G) {
                 Cx<T> x[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) x[u] = A.pool[col[c + u * G] + v];
+                for (int u = 0; u < 8; ++u) x[u] = ldcx(A.pool + col[c + u * G] + v);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     Cx<T>& acc_u = (u & 3) == 0 ? s0 : (u & 3) == 1 ? s1 : (u & 3) == 2 ? s2 : s3;
@@ -513,8 +513,8 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
                 }
             }
             for (; c + 3 * G < nt; c += 4 * G) {
-                const Cx<T> x0 = A.pool[col[c] + v], x1 = A.pool[col[c + G] + v];
-                const Cx<T> x2 = A.pool[col[c + 2 * G] + v], x3 = A.pool[col[c + 3 * G] + v];
+                const Cx<T> x0 = ldcx(A.pool + col[c] + v), x1 = ldcx(A.pool + col[c + G] + v);
+                const Cx<T> x2 = ldcx(A.pool + col[c + 2 * G] + v), x3 = ldcx(A.pool + col[c + 3 * G] + v);
                 if (ROW) {
                     cfmac(s0, F.coef[c], x0);
                     cfmac(s1, F.coef[c + G], x1);
@@ -528,13 +528,13 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
                 }
             }
             for (; c < nt; c += G) {
-                const Cx<T> x0 = A.pool[col[c] + v];
+                const Cx<T> x0 = ldcx(A.pool + col[c] + v);
                 if (ROW) cfmac(s0, F.coef[c], x0);
                 else cfma(s0, x0, F.coef[c]);
             }
             int t = part;
             for (; t + G < m; t += 2 * G) {
-                const Cx<T> x0 = cur[(size_t)t * ldc + v], x1 = cur[(size_t)(t + G) * ldc + v];
+                const Cx<T> x0 = ldcx(cur + (size_t)t * ldc + v), x1 = ldcx(cur + (size_t)(t + G) * ldc + v);
                 if (ROW) {
                     cfmac(s1, F.coef[nt + t], x0);
                     cfmac(s2, F.coef[nt + t + G], x1);
@@ -544,7 +544,7 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
                 }
             }
             for (; t < m; t += G) {
-                const Cx<T> x0 = cur[(size_t)t * ldc + v];
+                const Cx<T> x0 = ldcx(cur + (size_t)t * ldc + v);
                 if (ROW) cfmac(s3, F.coef[nt + t], x0);
                 else cfma(s3, x0, F.coef[nt + t]);
             }
@@ -676,8 +676,8 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             const int L = max(M, N);
 #pragma unroll 4
             for (int i = lane; i < L; i += 32) {
-                if (i < M) cfmac(gu, um[i], ut[i]);  // conj(u_t) u_m
-                if (i < N) cfmac(gv, vt[i], vm[i]);  // conj(v_m) v_t
+                if (i < M) cfmac(gu, ldcx(um + i), ldcx(ut + i));  // conj(u_t) u_m
+                if (i < N) cfmac(gv, ldcx(vt + i), ldcx(vm + i));  // conj(v_m) v_t
             }
             const T gux = warp_sum(gu.x), guy = warp_sum(gu.y);
             const T gvx = warp_sum(gv.x), gvy = warp_sum(gv.y);
@@ -781,7 +781,7 @@ __device__ void gram_upper(const Cx<T>* X, size_t ld, int L, int r, Cx<double>* 
     for (int i0 = 0; i0 < L; i0 += 32) {
         for (int e = tid; e < r * 32; e += NT) {
             const int c = e >> 5, ii = e & 31;
-            sh[c * 33 + ii] = (i0 + ii < L) ? X[(size_t)c * ld + i0 + ii] : Cx<T>{0, 0};
+            sh[c * 33 + ii] = (i0 + ii < L) ? ldcx(X + (size_t)c * ld + i0 + ii) : Cx<T>{0, 0};
         }
         __syncthreads();
 #pragma unroll
@@ -1273,14 +1273,14 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
                             const int t = col - S.pre[nc];
                             base = pass == 0 ? Un + (long long)t * M : Vn + (long long)t * N;
                         }
-                        v = base[i0 + ii];
+                        v = ldcx(base + i0 + ii);
                     }
                     sa[c * (RC + 1) + ii] = v;
                 }
                 for (int e = tid; e < rn * RC; e += NT) {
                     const int b = e / RC, ii = e - b * RC;
                     const Cx<T>* base = pass == 0 ? Un + (long long)b * M : Vn + (long long)b * N;
-                    sb[b * (RC + 1) + ii] = (i0 + ii < L) ? base[i0 + ii] : Cx<T>{0, 0};
+                    sb[b * (RC + 1) + ii] = (i0 + ii < L) ? ldcx(base + i0 + ii) : Cx<T>{0, 0};
                 }
                 __syncthreads();
 #pragma unroll
@@ -1804,11 +1804,11 @@ __global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3(const AcaArgs<T
                     for (int j0 = 0; j0 < N; j0 += TN) {
                         for (int e = tid; e < rn * TM; e += NT) {
                             int b = e / TM, ii = e % TM;
-                            tu[b * TM + ii] = (i0 + ii < M) ? Un[(long long)b * M + i0 + ii] : Cx<T>{0, 0};
+                            tu[b * TM + ii] = (i0 + ii < M) ? ldcx(Un + (long long)b * M + i0 + ii) : Cx<T>{0, 0};
                         }
                         for (int e = tid; e < rn * TN; e += NT) {
                             int b = e / TN, jj = e % TN;
-                            tv[b * TN + jj] = (j0 + jj < N) ? Vn[(long long)b * N + j0 + jj] : Cx<T>{0, 0};
+                            tv[b * TN + jj] = (j0 + jj < N) ? ldcx(Vn + (long long)b * N + j0 + jj) : Cx<T>{0, 0};
                         }
                         __syncthreads();
                         for (int mt = tid; mt < NMT; mt += NT) {

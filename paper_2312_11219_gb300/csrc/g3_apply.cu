@@ -85,17 +85,17 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
             for (; j + 8 <= N; j += 8) {
                 Cx<T> a[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) a[q] = act ? Ak[(long long)(j + q) * Mrow + i] : Cx<T>{0, 0};
+                for (int q = 0; q < 8; ++q) a[q] = act ? ldcx(Ak + (long long)(j + q) * Mrow + i) : Cx<T>{0, 0};
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const Cx<T> f = wf[j + q], c = wc[j + q];
+                    const Cx<T> f = ldcx(wf + j + q), c = ldcx(wc + j + q);
                     ax += a[q].x * (f.x + c.x) - a[q].y * (f.y - c.y);
                     ay += a[q].x * (f.y + c.y) + a[q].y * (f.x - c.x);
                 }
             }
             for (; j < N; ++j) {
-                const Cx<T> a = act ? Ak[(long long)j * Mrow + i] : Cx<T>{0, 0};
-                const Cx<T> f = wf[j], c = wc[j];
+                const Cx<T> a = act ? ldcx(Ak + (long long)j * Mrow + i) : Cx<T>{0, 0};
+                const Cx<T> f = ldcx(wf + j), c = ldcx(wc + j);
                 ax += a.x * (f.x + c.x) - a.y * (f.y - c.y);
                 ay += a.x * (f.y + c.y) + a.y * (f.x - c.x);
             }
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, c
     for (int e = tid; e < PG * Ku; e += NT) {
         const int p = e / Ku, k = e - p * Ku;
         Cx<T> v{0, 0};
-        if (p < np) v = pool[crs[p].off + (long long)crs[p].r * (M + N) + k];
+        if (p < np) v = ldcx(pool + crs[p].off + (long long)crs[p].r * (M + N) + k);
         fg[e] = v;
     }
     __syncthreads();
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, c
             const Cx<T>* wc = Wc + br.cb + j;
 #pragma unroll 4
             for (int k = 0; k < Ku; ++k) {
-                const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
+                const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
 #pragma unroll
                 for (int p = 0; p < PG; ++p) {
                     const Cx<T> f = fg[p * Ku + k];
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, c
         const Cx<T>* zp = zs + p * NT;
         Cx<T> pa{0, 0}, pb{0, 0};
         for (int jj = lane; jj < jn; jj += 32) {
-            const Cx<T> v = V[jj];
+            const Cx<T> v = ldcx(V + jj);
             cfmac(pa, xp[jj], v);  // conj(v) x
             cfmac(pb, zp[jj], v);  // conj(v) zc
         }
@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(NT) k_far_uy(const Cx<T>* __restrict__ pool, c
             Cx<T> s1{0, 0}, s2{0, 0};
 #pragma unroll 4
             for (int t = 0; t < r; ++t) {
-                const Cx<T> u = U[(long long)t * M + i];
-                cfma(s1, u, ab[o + 2 * t]);
-                cfma(s2, u, ab[o + 2 * t + 1]);
+                const Cx<T> u = ldcx(U + (long long)t * M + i);
+                cfma(s1, u, ldcx(ab + o + 2 * t));
+                cfma(s2, u, ldcx(ab + o + 2 * t + 1));
             }
             o += 2 * r;
             vx += s1.x + s2.x;  // U a + conj(U b)
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __r
         for (int e = lane; e < PG * Ku; e += 32) {
             const int p = e / Ku, k = e - p * Ku;
             Cx<T> v{0, 0};
-            if (p < np) v = pool[rec[(size_t)blk * Cmax + g0 + p].off + (long long)M * N + k];
+            if (p < np) v = ldcx(pool + rec[(size_t)blk * Cmax + g0 + p].off + (long long)M * N + k);
             fg[e] = v;
         }
         __syncwarp();
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __r
                 const Cx<T>* wc = Wc + br.cb + j;
 #pragma unroll 4
                 for (int k = 0; k < Ku; ++k) {
-                    const Cx<T> a = wf[(long long)k * E], b = wc[(long long)k * E];
+                    const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
 #pragma unroll
                     for (int p = 0; p < PG; ++p) {
                         const Cx<T> f = fg[p * Ku + k];
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __r
                         Cx<T> s1{0, 0}, s2{0, 0};
 #pragma unroll 8
                         for (int jj = 0; jj < jn; ++jj) {
-                            const Cx<T> h = H[i + (long long)jj * M];
+                            const Cx<T> h = ldcx(H + i + (long long)jj * M);
                             cfma(s1, h, xs[p * 32 + jj]);
                             cfma(s2, h, zs[p * 32 + jj]);
                         }

@@ -18,6 +18,23 @@ struct Cx {
     T x, y;
 };
 
+// One load of a complex element of global memory as a single 64-bit (float)
+// or 128-bit (double) access.  Cx<T> has the alignment of T, so a plain
+// dereference becomes two accesses; every device buffer of complex values
+// here (factor pool, workspace, apply scratch, near field) starts at a
+// cudaMalloc'd base and is indexed in whole elements, so its elements are
+// aligned to their size.
+template <class T>
+__device__ __forceinline__ Cx<T> ldcx(const Cx<T>* p) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        return {v.x, v.y};
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        return {v.x, v.y};
+    }
+}
+
 template <class T>
 __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
