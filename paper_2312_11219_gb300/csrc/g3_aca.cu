@@ -269,8 +269,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         }
         return (is_dense(r) ? 12.0 * m * n : 256.0 * (m + n)) + 24.0 * ku;
     };
-    auto scale_it = ctx->pool_scale.emplace((kernel * 2 + (int)(sizeof(T) == 4)) * 2 + (int)pool_mlp, 1.0).first;
-    double& scale = scale_it->second;
+    double& scale = pool_mlp ? ctx->pool_scale_mlp : ctx->pool_scale;
     double est = 0.0;
     for (int q = 0; q < n_run; ++q) est += block_est(queue[q]);
     long long cap = (long long)(pf * scale * est);
@@ -422,11 +421,9 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         G3_CUDA(cudaMemcpy(d_queue.p, nq.data(), n_spill * sizeof(int), cudaMemcpyHostToDevice));
     }
     if (est > 0) scale = std::max(scale, 1.15 * (double)ctr / est);
-    // give back what the estimate over-reserved: a pool more than twice its
-    // use and over-reserved by more than 1 GiB is moved into an exact-size
-    // buffer (its offsets stay valid); smaller excess is kept, the copy would
-    // cost more than the memory is worth
-    if (ctr > 0 && (double)cap > 2.0 * (double)ctr && ((long long)cap - (long long)ctr) * (long long)sizeof(Cx<T>) > (1LL << 30)) {
+    // give back what the estimate over-reserved: a pool much larger than its
+    // use is moved into an exact-size buffer (its offsets stay valid)
+    if (ctr > 0 && (double)cap > 1.25 * (double)ctr && ((long long)cap - (long long)ctr) * (long long)sizeof(Cx<T>) > (256LL << 20)) {
         DevBuf exact;
         if (exact.alloc((size_t)ctr * sizeof(Cx<T>)) == cudaSuccess) {
             G3_CUDA(cudaMemcpyAsync(exact.p, pool->p, (size_t)ctr * sizeof(Cx<T>), cudaMemcpyDeviceToDevice,
@@ -444,11 +441,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     G3_CUDA(cudaMemcpy(r3.data(), g_r3.p, n_far * sizeof(int), cudaMemcpyDeviceToHost));
     std::vector<long long> phases((size_t)n_far * NPH);
     G3_CUDA(cudaMemcpy(phases.data(), g_cyc.p, phases.size() * sizeof(long long), cudaMemcpyDeviceToHost));
-    // cross records: straight into the factors' host copy for a single mesh
-    std::vector<CrossRec> rec;
-    std::vector<CrossRec>& rec_all = batched ? rec : jobs[0].fa->rec;
-    rec_all.resize((size_t)n_far * Cmax);
-    G3_CUDA(cudaMemcpy(rec_all.data(), g_rec.p, rec_all.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
+    std::vector<CrossRec> rec((size_t)n_far * Cmax);
+    G3_CUDA(cudaMemcpy(rec.data(), g_rec.p, rec.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
     // per mesh: device slices (the whole buffers for a single mesh), host
     // copies and statistics; the pool is shared
     for (int j = 0; j < n_jobs; ++j) {
@@ -478,8 +472,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         fa->cycles.assign(J.n, 0);
         for (int b = 0; b < J.n; ++b)
             for (int i = 0; i < 7; ++i) fa->cycles[b] += fa->phases[(size_t)b * NPH + i];
-        if (batched)
-            fa->rec.assign(rec.begin() + (size_t)J.first * Cmax, rec.begin() + (size_t)(J.first + J.n) * Cmax);
+        fa->rec.assign(rec.begin() + (size_t)J.first * Cmax, rec.begin() + (size_t)(J.first + J.n) * Cmax);
         // batch-wide counters and times (a batched compression is one launch)
         g3_stats& S = fa->stats;
         S = g3_stats{};

@@ -196,9 +196,8 @@ struct g3_ctx {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaEvent_t ev_side[2] = {};
     double last_apply_ms = 0, last_near_ms = 0;
-    // factor-pool size / estimate needed by earlier compressions, per problem
-    // class (kernel, precision, predictor-based estimate or not)
-    std::map<int, double> pool_scale;
+    double pool_scale = 1.0;  // factor-pool size / estimate needed by earlier compressions
+    double pool_scale_mlp = 1.0;  // the same for the predictor-based estimate
     std::map<long long, std::pair<int, int>> tune_cache;  // autotuner: key -> (threads, dense_face_max)
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
     void count(const char* name, int64_t n = 1) {
