@@ -473,9 +473,10 @@ __device__ void line_coeffs(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, 
 //   ENTRY - sum_p f_p[kf] (U_p V_p^H) - sum_{t<m} u_t v_t^H
 //   ROW:  out[j] = ENTRY(fix, j) - sum_c coef[c] conj(X_c[j]),  X_c = V_p[:, t] | v_t
 //   !ROW: out[i] = ENTRY(i, fix) - sum_c X_c[i] coef[c],        X_c = U_p[:, t] | u_t
-// G threads per output element share the sum (4-way unrolled, independent
-// partial sums) and the quadrature points.  Returns the block-wide argmax of
-// |out|^2 (ROW: over all columns; !ROW: over the rows not yet used).
+// G threads per output element share the sum (eight loads in flight, four
+// independent partial sums) and the quadrature points.  Returns the
+// block-wide argmax of |out|^2 (ROW: over all columns; !ROW: over the rows
+// not yet used).
 template <int KER, class T, int NT, bool ROW>
 __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
                                     int fix, int kf, int m, Cx<T>* out) {
