@@ -131,3 +131,24 @@ def test_bench_reduction_over_two_gloo_ranks():
     for rank, vals, rate in res:
         assert vals == [20.0, 100.0]               # max over ranks
         assert rate == pytest.approx(1000.0 * 2 / (10.0 / 1e3))   # whole job over the slowest rank
+
+
+def test_reference_arm_json_contract():
+    """`bench.py --impl reference` (the oracle on the host cores): one JSON
+    line with the contract's keys, the oracle as its cpu_baseline and an e2e
+    object that moves no host-device bytes."""
+    import json
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--ref-seconds", "1"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "gpu_launches"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["config"]["workload"] == "lshape12288"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"] and line["gpu_launches"] == 0
