@@ -58,7 +58,11 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}_{os.getpid()}.csv")
+        # raw samples: G3_CLOCKS_DIR if set, else the temporary directory (the
+        # JSON line carries their summary)
+        import tempfile
+        self.path = os.path.join(os.environ.get("G3_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 f"clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
