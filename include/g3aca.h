@@ -420,7 +420,10 @@ g3_status g3_factors_labels(g3_ctx* ctx, const g3_factors* fa, float* out);
  * mem = G3_DEVICE: W, Y are device pointers (caller-owned).
  * mem = G3_HOST:   W, Y are host pointers; the library copies W in and Y out
  *                  on the context's stream and synchronises before return.
- * Frequencies outside the unique set use A(conj s) = conj A(s). */
+ * Frequencies outside the unique set use A(conj s) = conj A(s).
+ * With both parts present the near field runs on a second stream owned by
+ * the context, forked from and joined back into the context's stream, so
+ * work the caller orders after this call on that stream sees y complete. */
 g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
                     g3_dtype dtype, g3_apply_mode mode, g3_memory mem);
 /* Allocation-free variant of apply_gcq (no counterpart in the paper).  For
