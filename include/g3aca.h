@@ -84,7 +84,9 @@ typedef enum { G3_C64 = 0, G3_C128 = 1 } g3_dtype;
 typedef enum { G3_DEVICE = 0, G3_HOST = 1 } g3_memory;
 typedef enum {
     G3_APPLY_SUM = 0,     /* y = sum_{l=1}^{K} A(s_l) w_l              (eq. (product)) */
-    G3_APPLY_PERFREQ = 1  /* Y[:, l] = A(s_l) w_l for every l (check mode)             */
+    G3_APPLY_PERFREQ = 1  /* Y[:, l] = A(s_l) w_l for every l: the terms of eq. (product)
+                             before the sum over l (a per-frequency check of the
+                             compressed operator; not tuned for speed)                 */
 } g3_apply_mode;
 
 typedef struct g3_ctx g3_ctx;
@@ -208,6 +210,19 @@ g3_status g3_freqs_bdf2(g3_ctx* ctx, int K, double lambda, double dt, g3_freqs**
  * Returns G3_EINVAL for dt_max <= dt_min (q = 1 gives k = 0, the degenerate
  * constant-step case the paper warns about) or odd NQ. */
 g3_status g3_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, g3_freqs** out);
+
+/* A frequency set given by the caller (any rule: another CQ generating
+ * function, a Runge-Kutta gCQ, a measured set).  s_re_im [2K] holds
+ * interleaved (Re s_l, Im s_l), l = 0..K-1, copied on entry; 1 <= K <= 512,
+ * every Re s_l > 0 and finite (G3_EINVAL otherwise).  The set keeps the
+ * caller's order.  Conjugate pairing (Appendix A: a real operator gives
+ * A(conj s) = conj A(s), so half of a conjugate-closed set suffices): for
+ * l in increasing order, an unpaired l is unique and is paired with the
+ * first unpaired l' > l with |s_l' - conj(s_l)| <= 1e-12 |s_l|; a frequency
+ * with |Im s_l| <= 1e-12 |s_l|, or without such a partner, is its own
+ * partner.  At most 256 unique frequencies (G3_EINVAL beyond).  omega is
+ * zero (g3_freqs_get). */
+g3_status g3_freqs_from_array(g3_ctx* ctx, const double* s_re_im, int K, g3_freqs** out);
 
 /* Sizes of a frequency set: K (all) and Ku (unique). */
 g3_status g3_freqs_info(const g3_freqs* f, int* K, int* Ku);
@@ -421,9 +436,14 @@ g3_status g3_factors_labels(g3_ctx* ctx, const g3_factors* fa, float* out);
  * mem = G3_HOST:   W, Y are host pointers; the library copies W in and Y out
  *                  on the context's stream and synchronises before return.
  * Frequencies outside the unique set use A(conj s) = conj A(s).
- * With both parts present the near field runs on a second stream owned by
- * the context, forked from and joined back into the context's stream, so
- * work the caller orders after this call on that stream sees y complete. */
+ * G3_APPLY_SUM: with both parts present the near field runs on a second
+ * stream owned by the context, forked from and joined back into the
+ * context's stream, so work the caller orders after this call on that stream
+ * sees y complete.  G3_APPLY_PERFREQ runs on the context's stream only; its
+ * scratch holds 4 Ku M complex values (context-owned, grown on demand), and
+ * face ranks above 64 return G3_EUNSUPPORTED.  The call synchronises the
+ * context's stream before it returns (the device time is recorded for
+ * g3_apply_last). */
 g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
                     g3_dtype dtype, g3_apply_mode mode, g3_memory mem);
 /* Allocation-free variant of apply_gcq (no counterpart in the paper).  For
@@ -435,8 +455,11 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
  * Its scratch is a fixed 32 MiB device array inside the library (held by
  * every GPU that loads the library until the process exits); no
  * cudaMalloc/cudaFree or other allocating routine is called.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Problems needing more
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process; under lazy module loading (the CUDA
+ * default) that lookup also loads the module and so reserves the 32 MiB
+ * then.  Make that first call before any stream capture, and do not call
+ * after cudaDeviceReset (the kept address would be stale).  Problems needing more
  * scratch than 32 MiB (2 Ku M + M complex values and 2 per face rank of the
  * low-rank far field) return G3_EINVAL.  All calls
  * share the array: calls whose work overlaps on the GPU (other streams,

@@ -10,6 +10,8 @@ The operation (eq. (product), the right-hand side of eq.
 * `dense_apply` evaluates it from the definition: every entry at every one
   of the K frequencies (the conjugate symmetry is not used), optionally only
   for a subset of rows.
+* `dense_apply_perfreq` returns the terms of that sum one by one,
+  Y[:, l] = A(s_l) w_l (the per-frequency check mode), from the definition.
 * `compressed_apply` evaluates it with the compressed representation: for
   far blocks A(s_k) ~ sum_p H_p f_p[k] on the unique frequencies and the
   complex conjugate on their partners (A(conj s) = conj A(s) for real
@@ -34,6 +36,19 @@ def dense_apply(entry_fn, E: int, s_all: np.ndarray, W: np.ndarray, rows=None,
             acc += np.sum(A * W[cols, :])
         y[n] = acc
     return y
+
+
+def dense_apply_perfreq(entry_fn, E: int, s_all: np.ndarray, W: np.ndarray, rows=None,
+                        col_chunk: int = 2048) -> np.ndarray:
+    """Y[rows, l] = A(s_l)[rows, :] W[:, l] for every l  (ORIGINAL element order)."""
+    rows = np.arange(E) if rows is None else np.asarray(rows)
+    Y = np.zeros((rows.size, s_all.size), dtype=np.complex128)
+    for n, i in enumerate(rows):
+        for c0 in range(0, E, col_chunk):
+            cols = np.arange(c0, min(E, c0 + col_chunk))
+            A = entry_fn(np.full(cols.size, i), cols, s_all)       # [nc, K]
+            Y[n] += np.sum(A * W[cols, :], axis=0)
+    return Y
 
 
 def expand_fibers(f_u: np.ndarray, uniq: np.ndarray, partner: np.ndarray, K: int):

@@ -24,6 +24,11 @@ real-argument sn, cn, dn and K(m).
 The unique set used by the compression is: BDF2, k = 0..K/2 (k = 0 and
 K/2 are self-conjugate); gCQ, l = 1..N_Q/2 (no self-conjugate points for even
 N_Q).  `partner[k]` is the index of conj(s_k) in the full set.
+
+A set given as an array (any rule) is paired by `pair_conjugates`: a real
+operator has A(conj s) = conj A(s) (Appendix A: half of a conjugate-closed
+set suffices), so each frequency whose conjugate is also in the set needs
+only one of the two.
 """
 from __future__ import annotations
 
@@ -102,3 +107,29 @@ def frequency_set(spec) -> dict:
     else:
         raise ValueError(spec.kind)
     return {"s": s, "omega": w, "uniq": uniq, "partner": partner}
+
+
+def pair_conjugates(s: np.ndarray, tol: float = 1e-12) -> tuple[np.ndarray, np.ndarray]:
+    """Unique indices and conjugate partners of an arbitrary frequency array.
+
+    Scanning l = 0, 1, ...: an l not yet paired is unique; if Im s_l is not
+    zero (|Im s_l| > tol |s_l|) it is paired with the first not-yet-paired
+    l' > l whose s_l' is conj(s_l) within tol |s_l|.  Real frequencies and
+    complex ones without a conjugate in the set are their own partners.
+    """
+    s = np.asarray(s, dtype=np.complex128)
+    K = s.size
+    partner = np.full(K, -1, dtype=np.int64)
+    uniq = []
+    for l in range(K):
+        if partner[l] >= 0:
+            continue
+        uniq.append(l)
+        partner[l] = l
+        if abs(s[l].imag) <= tol * abs(s[l]):
+            continue
+        for m in range(l + 1, K):
+            if partner[m] < 0 and abs(s[m] - np.conj(s[l])) <= tol * abs(s[l]):
+                partner[l], partner[m] = m, l
+                break
+    return np.asarray(uniq, dtype=np.int64), partner

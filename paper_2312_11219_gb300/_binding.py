@@ -80,6 +80,7 @@ _sig("g3_launch_count", C.c_int64, _p)
 _sig("g3_kernel_name", C.c_char_p, _p, _ci, _i64p)
 _sig("g3_freqs_bdf2", _ci, _p, _ci, C.c_double, C.c_double, _pp)
 _sig("g3_freqs_gcq", _ci, _p, _ci, C.c_double, C.c_double, _pp)
+_sig("g3_freqs_from_array", _ci, _p, _dp, _ci, _pp)
 _sig("g3_freqs_info", _ci, _p, C.POINTER(_ci), C.POINTER(_ci))
 _sig("g3_freqs_get", _ci, _p, _dp, _dp, _i32p, _i32p)
 _sig("g3_freqs_free", _ci, _p)
@@ -119,7 +120,7 @@ _sig("g3_block_features", _ci, _p, _p, _p, _ci, C.c_double, _fp)
 _sig("g3_factors_labels", _ci, _p, _p, _fp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
-            "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
+            "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_from_array", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
             "build_cluster_tree", "build_cluster_tree_capped", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
@@ -239,6 +240,15 @@ def g3_freqs_bdf2(ctx: Context, K: int, lam: float, dt: float) -> Freqs:
 def g3_freqs_gcq(ctx: Context, NQ: int, dt_min: float, dt_max: float) -> Freqs:
     h = C.c_void_p()
     _check(_lib.g3_freqs_gcq(ctx.h, NQ, dt_min, dt_max, C.byref(h)), "g3_freqs_gcq")
+    return Freqs(h, (ctx,))
+
+
+def g3_freqs_from_array(ctx: Context, s) -> Freqs:
+    """Frequency set from a complex array (conjugate pairs detected)."""
+    a = np.ascontiguousarray(np.asarray(s, dtype=np.complex128))
+    h = C.c_void_p()
+    _check(_lib.g3_freqs_from_array(ctx.h, _ptr(a.view(np.float64), C.c_double), a.size, C.byref(h)),
+           "g3_freqs_from_array")
     return Freqs(h, (ctx,))
 
 
@@ -567,18 +577,23 @@ def apply_gcq(ctx: Context, tree: Tree, near: Near | None, factors: Factors | No
     return Y if mode_i == 0 else Y.t()
 
 
-def apply_gcq_noalloc(ctx: Context, tree: Tree, near: Near | None, factors: Factors | None, W, Y=None):
+def apply_gcq_noalloc(ctx: Context, tree: Tree, near: Near | None, factors: Factors | None, W, Y):
     """Allocation-free apply (same result as apply_gcq on device buffers).
-    W: complex CUDA tensor [M, K]; Y: optional preallocated complex CUDA
-    tensor [M] (allocated here by torch when omitted)."""
+
+    W: complex CUDA tensor [M, K] whose columns are contiguous in memory (the
+    transpose of a contiguous [K, M] tensor, e.g. ``Wt.t()``); Y: preallocated
+    complex CUDA tensor [M] of W's dtype.  Neither this wrapper nor the
+    library allocates device memory; both read and write in order on the
+    context's stream."""
     import torch
     if not (W.is_cuda and W.dtype in (torch.complex64, torch.complex128)):
         raise TypeError("W must be a complex CUDA tensor")
+    if W.dim() != 2 or not W.t().is_contiguous():
+        raise ValueError("W must be [M, K] with contiguous columns (pass Wt.t() of a contiguous [K, M] tensor)")
+    if Y is None or not (Y.is_cuda and Y.dtype == W.dtype and Y.is_contiguous() and Y.numel() == W.shape[0]):
+        raise ValueError("Y must be a preallocated contiguous CUDA tensor [M] of W's dtype")
     dt = 1 if W.dtype == torch.complex128 else 0
-    Wt = W.t().contiguous()
-    if Y is None:
-        Y = torch.empty(W.shape[0], dtype=W.dtype, device=W.device)
     _check(_lib.apply_gcq_noalloc(ctx.h, tree.h, near.h if near is not None else None,
-                                  factors.h if factors is not None else None, C.c_void_p(Wt.data_ptr()),
+                                  factors.h if factors is not None else None, C.c_void_p(W.data_ptr()),
                                   C.c_void_p(Y.data_ptr()), dt), "apply_gcq_noalloc")
     return Y

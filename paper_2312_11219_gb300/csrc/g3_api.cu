@@ -274,6 +274,66 @@ g3_status g3_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, g3_fre
     return G3_OK;
 }
 
+// Frequencies given by the caller.  Conjugate pairing: l' pairs with l < l'
+// when |s_l' - conj(s_l)| <= 1e-12 |s_l| (the first unpaired such l' in index
+// order); a frequency with |Im s| <= 1e-12 |s| is its own partner (A(s) is
+// real there), as is a complex frequency without a conjugate in the set.
+// The unique set is the lower index of each pair plus the self-partnered
+// frequencies, in increasing index order.
+g3_status g3_freqs_from_array(g3_ctx* ctx, const double* s_re_im, int K, g3_freqs** out) {
+    G3_CHECK(ctx && s_re_im && out, "g3_freqs_from_array: NULL argument");
+    *out = nullptr;
+    G3_CHECK(K >= 1 && K <= 512, "g3_freqs_from_array: K = %d outside [1, 512]", K);
+    for (int l = 0; l < 2 * K; ++l)
+        G3_CHECK(std::isfinite(s_re_im[l]), "g3_freqs_from_array: s[%d] is not finite", l / 2);
+    for (int l = 0; l < K; ++l)
+        G3_CHECK(s_re_im[2 * l] > 0.0, "g3_freqs_from_array: Re s[%d] = %g must be positive (the kernel "
+                 "exp(-s r) / (4 pi r) of a damped problem)", l, s_re_im[2 * l]);
+    std::vector<int32_t> partner(K, -1), uniq;
+    const double tol = 1e-12;
+    for (int l = 0; l < K; ++l) {
+        if (partner[l] >= 0) continue;
+        const double re = s_re_im[2 * l], im = s_re_im[2 * l + 1];
+        const double mag = std::hypot(re, im);
+        uniq.push_back(l);
+        partner[l] = l;
+        if (std::fabs(im) <= tol * mag) continue;
+        for (int m = l + 1; m < K; ++m) {
+            if (partner[m] >= 0) continue;
+            if (std::hypot(s_re_im[2 * m] - re, s_re_im[2 * m + 1] + im) <= tol * mag) {
+                partner[l] = m;
+                partner[m] = l;
+                break;
+            }
+        }
+    }
+    G3_CHECK((int)uniq.size() <= 256, "g3_freqs_from_array: %d unique frequencies, at most 256 are supported",
+             (int)uniq.size());
+    G3_TRY(use_device(ctx));
+    g3_freqs* f = new (std::nothrow) g3_freqs();
+    if (!f) return fail(G3_ENOMEM, "g3_freqs_from_array: out of host memory");
+    f->ctx = ctx;
+    f->kind = 2;
+    f->K = K;
+    f->Ku = (int)uniq.size();
+    f->s.assign(s_re_im, s_re_im + 2 * (size_t)K);
+    f->omega.assign(2 * (size_t)K, 0.0);
+    f->uniq = uniq;
+    f->partner = partner;
+    std::vector<double> su(2 * (size_t)f->Ku);
+    for (int u = 0; u < f->Ku; ++u) {
+        su[2 * u] = s_re_im[2 * uniq[u]];
+        su[2 * u + 1] = s_re_im[2 * uniq[u] + 1];
+    }
+    g3_status st = finish_freqs(ctx, f, su);
+    if (st != G3_OK) {
+        delete f;
+        return st;
+    }
+    *out = f;
+    return G3_OK;
+}
+
 g3_status g3_freqs_info(const g3_freqs* f, int* K, int* Ku) {
     G3_CHECK(f != nullptr, "g3_freqs_info: NULL handle");
     if (K) *K = f->K;

@@ -24,6 +24,10 @@
 
 namespace g3 {
 
+// largest face rank the per-frequency apply keeps in shared memory (the
+// compression caps face ranks at 64)
+constexpr int RF_TS = 64;
+
 // W (original order, column l = w_l, M x K column-major, complex TI) ->
 // Wf[k][p] = w_{uniq[k]}[perm[p]],  Wc[k][p] = w_{partner(uniq[k])}[perm[p]] or 0
 // (cluster order, frequency-major), and y := 0.
@@ -569,6 +573,280 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
 }
 
 // ============================================================================
+// Per-frequency apply (G3_APPLY_PERFREQ): Y[:, l] = A(s_l) w_l for every l
+// ============================================================================
+//
+// The terms of eq. (product) before the sum over l, one column per frequency
+// (a check of the compressed operator at each frequency).  With the unique
+// frequencies k and their partners k' (A(s_k') = conj A(s_k)):
+//   Y[:, k]  = A(s_k) w_k               = sum_far sum_p f_p[k] H_p w_k + near,
+//   Y[:, k'] = conj(A(s_k) conj(w_k'))  (the same operator on conj(w_k')).
+// So every unique frequency k has two right-hand sides, x_k = w_k and
+// x_{Ku + k} = conj(w_k') (zero without a partner), and two outputs
+// yf[k] and yc[k] in cluster order; Y[:, k'] = conj(yc[k]).  Scratch:
+// Wf, Wc (from k_apply_prep, Wc unconjugated), yf, yc: 4 Ku E values.
+
+// near field: one CTA per (near block, frequency chunk); warp per frequency,
+// lane per row; both right-hand sides in one pass over the stored entries
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_pf_near(const Cx<T>* __restrict__ A, const BlockRange* __restrict__ ranges,
+                                                const long long* __restrict__ offs, int Ku, int kchunk, int E,
+                                                const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
+                                                Cx<T>* __restrict__ yf, Cx<T>* __restrict__ yc) {
+    const int b = blockIdx.x;
+    const int k0 = blockIdx.y * kchunk, k1 = min(Ku, k0 + kchunk);
+    const BlockRange br = ranges[b];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = k0 + warp; k < k1; k += NT / 32) {
+        const Cx<T>* Ak = A + offs[b] + (long long)k * M * N;
+        const Cx<T>* wf = Wf + (long long)k * E + br.cb;
+        const Cx<T>* wc = Wc + (long long)k * E + br.cb;
+        for (int i = lane; i < M; i += 32) {
+            Cx<T> s1{0, 0}, s2{0, 0};
+            for (int j = 0; j < N; ++j) {
+                const Cx<T> a = ldcx(Ak + (long long)j * M + i);
+                cfma(s1, a, ldcx(wf + j));
+                cfmac(s2, a, ldcx(wc + j));  // A conj(w')
+            }
+            atomicAdd(&yf[(long long)k * E + br.rb + i].x, s1.x);
+            atomicAdd(&yf[(long long)k * E + br.rb + i].y, s1.y);
+            atomicAdd(&yc[(long long)k * E + br.rb + i].x, s2.x);
+            atomicAdd(&yc[(long long)k * E + br.rb + i].y, s2.y);
+        }
+    }
+}
+
+// far field: one CTA per item (block, 32 right-hand sides c0.., 128 rows
+// i0..).  Right-hand side c < Ku is w_c, c >= Ku is conj(w'_{c-Ku}); its
+// fiber coefficient is f_p[c mod Ku].  Per cross p of the block:
+//   low-rank face:  t[q][c] = V_p[:, q]^H x_c   (q < r_p, the block's columns
+//                   of x_c staged 64 at a time), then z[i][c] += f_p[c] U_p[i, :] t[:, c];
+//   dense face:     z[i][c] += f_p[c] H_p[i, :] x_c.
+// Thread (i = tid / 32 + 8 m, c = tid % 32) keeps 16 outputs in registers;
+// the CTA adds them to yf / yc once.
+constexpr int PF_NT = 256, PF_NC = 32, PF_NI = 128, PF_JC = 64;
+
+template <class T>
+__global__ void __launch_bounds__(PF_NT) k_pf_far(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
+                                                  const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
+                                                  const int4* __restrict__ items, int Cmax, int Ku, int E,
+                                                  const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
+                                                  Cx<T>* __restrict__ yf, Cx<T>* __restrict__ yc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // xs [PF_JC][PF_NC + 1], ts [RF_TS][PF_NC + 1] (dynamic: above 48 KB in float64)
+    auto xs = reinterpret_cast<Cx<T>(*)[PF_NC + 1]>(smem_raw);
+    auto ts = reinterpret_cast<Cx<T>(*)[PF_NC + 1]>(smem_raw + (size_t)PF_JC * (PF_NC + 1) * sizeof(Cx<T>));
+    __shared__ Cx<T> fs[PF_NC];
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, c0 = it.y, i0 = it.z;
+    const BlockRange br = ranges[blk];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const int tid = threadIdx.x, cl = tid & 31, il = tid >> 5;
+    const int nrhs = 2 * Ku;
+    Cx<T> z[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) z[m] = Cx<T>{0, 0};
+    // stage x_c[j0 .. j0 + PF_JC) for the 32 right-hand sides
+    auto stage = [&](int j0) {
+        for (int e = tid; e < PF_JC * PF_NC; e += PF_NT) {
+            const int c = e / PF_JC, jj = e - c * PF_JC;
+            const int gc = c0 + c, j = j0 + jj;
+            Cx<T> v{0, 0};
+            if (gc < nrhs && j < N) {
+                if (gc < Ku) v = ldcx(Wf + (long long)gc * E + br.cb + j);
+                else v = cconj(ldcx(Wc + (long long)(gc - Ku) * E + br.cb + j));
+            }
+            xs[jj][c] = v;
+        }
+    };
+    const int nc = r3[blk];
+    for (int p = 0; p < nc; ++p) {
+        const CrossRec cr = rec[(size_t)blk * Cmax + p];
+        const bool dense = cr.r < 0;
+        const Cx<T>* fb = pool + cr.off + (dense ? (long long)M * N : (long long)cr.r * (M + N));
+        __syncthreads();  // previous cross done with xs / ts / fs
+        if (tid < PF_NC) {
+            const int gc = c0 + tid;
+            fs[tid] = gc < nrhs ? ldcx(fb + (gc < Ku ? gc : gc - Ku)) : Cx<T>{0, 0};
+        }
+        if (dense) {
+            const Cx<T>* H = pool + cr.off;
+            Cx<T> acc[16];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) acc[m] = Cx<T>{0, 0};
+            for (int j0 = 0; j0 < N; j0 += PF_JC) {
+                __syncthreads();
+                stage(j0);
+                __syncthreads();
+                const int jn = min(PF_JC, N - j0);
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    const int i = i0 + il + 8 * m;
+                    if (i < M)
+                        for (int jj = 0; jj < jn; ++jj) cfma(acc[m], ldcx(H + (long long)(j0 + jj) * M + i), xs[jj][cl]);
+                }
+            }
+            __syncthreads();
+            const Cx<T> f = fs[cl];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) cfma(z[m], f, acc[m]);
+            continue;
+        }
+        const int r = cr.r;
+        const Cx<T>* U = pool + cr.off;
+        const Cx<T>* V = U + (long long)r * M;
+        // t[q][c] = V_p[:, q]^H x_c; thread (q = il + 8 m, c = cl)
+        Cx<T> t[RF_TS / 8];
+#pragma unroll
+        for (int m = 0; m < RF_TS / 8; ++m) t[m] = Cx<T>{0, 0};
+        for (int j0 = 0; j0 < N; j0 += PF_JC) {
+            __syncthreads();
+            stage(j0);
+            __syncthreads();
+            const int jn = min(PF_JC, N - j0);
+#pragma unroll
+            for (int m = 0; m < RF_TS / 8; ++m) {
+                const int q = il + 8 * m;
+                if (q < r)
+                    for (int jj = 0; jj < jn; ++jj) cfmac(t[m], xs[jj][cl], ldcx(V + (long long)q * N + j0 + jj));
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < RF_TS / 8; ++m) {
+            const int q = il + 8 * m;
+            if (q < r) ts[q][cl] = t[m];
+        }
+        __syncthreads();
+        const Cx<T> f = fs[cl];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int i = i0 + il + 8 * m;
+            if (i < M) {
+                Cx<T> s{0, 0};
+                for (int q = 0; q < r; ++q) cfma(s, ldcx(U + (long long)q * M + i), ts[q][cl]);
+                cfma(z[m], f, s);
+            }
+        }
+    }
+    const int gc = c0 + cl;
+    if (gc >= nrhs) return;
+    Cx<T>* out = gc < Ku ? yf + (long long)gc * E : yc + (long long)(gc - Ku) * E;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int i = i0 + il + 8 * m;
+        if (i < M) {
+            atomicAdd(&out[br.rb + i].x, z[m].x);
+            atomicAdd(&out[br.rb + i].y, z[m].y);
+        }
+    }
+}
+
+// Y[perm p, uniq k] = yf[k][p];  Y[perm p, partner] = conj(yc[k][p]) (column-major M x K)
+template <class T, class TO>
+__global__ void k_pf_finish(int E, int Ku, const int* __restrict__ perm, const int* __restrict__ uniq,
+                            const int* __restrict__ partner, const Cx<T>* __restrict__ yf,
+                            const Cx<T>* __restrict__ yc, Cx<TO>* __restrict__ Y) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)Ku * E) return;
+    const int k = (int)(idx / E), p = (int)(idx % E);
+    const int l = uniq[k], lp = partner[l];
+    const Cx<T> a = yf[idx];
+    Y[(long long)l * E + perm[p]] = Cx<TO>{(TO)a.x, (TO)a.y};
+    if (lp != l) {
+        const Cx<T> b = yc[idx];
+        Y[(long long)lp * E + perm[p]] = Cx<TO>{(TO)b.x, (TO)-b.y};
+    }
+}
+
+template <class T>
+static g3_status run_apply_perfreq_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa,
+                                     const void* W, void* Y, int dtype, const g3_freqs* f) {
+    const int E = t->ne, K = f->K, Ku = f->Ku;
+    const size_t nW = (size_t)Ku * E;
+    // work items of the far field: (block, right-hand-side chunk, row chunk)
+    std::vector<int> items;
+    if (fa) {
+        for (int b = 0; b < fa->n_far; ++b) {
+            if (fa->r3[b] <= 0) continue;
+            const int M = fa->ranges[b].re - fa->ranges[b].rb;
+            for (int c0 = 0; c0 < 2 * Ku; c0 += PF_NC)
+                for (int i0 = 0; i0 < M; i0 += PF_NI) items.insert(items.end(), {b, c0, i0, 0});
+            for (int p = 0; p < fa->r3[b]; ++p)
+                if (fa->rec[(size_t)b * fa->Cmax + p].r > RF_TS)
+                    return fail(G3_EUNSUPPORTED, "apply_gcq: face rank %d above %d in the per-frequency apply",
+                                fa->rec[(size_t)b * fa->Cmax + p].r, RF_TS);
+        }
+    }
+    const size_t n_items = items.size() / 4;
+    const size_t need = 4 * nW * sizeof(Cx<T>) + (n_items + 1) * sizeof(int4) + 512;
+    G3_CUDA(ctx->scratch.ensure(need));
+    Cx<T>* Wf = ctx->scratch.as<Cx<T>>();
+    Cx<T>* Wc = Wf + nW;
+    Cx<T>* yf = Wc + nW;
+    Cx<T>* yc = yf + nW;
+    int4* d_items = reinterpret_cast<int4*>((reinterpret_cast<uintptr_t>(yc + nW) + 255) & ~uintptr_t(255));
+    cudaEvent_t e0 = ctx->ev[2], e3 = ctx->ev[5];
+    G3_CUDA(cudaEventRecord(e0, ctx->stream));
+    if (n_items)
+        G3_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                ctx->stream));
+    G3_CUDA(cudaMemsetAsync(yf, 0, 2 * nW * sizeof(Cx<T>), ctx->stream));
+    {
+        const int blocks = (int)((nW + 255) / 256);
+        // k_apply_prep also clears its y argument: point it at yf (cleared anyway)
+        if (dtype == G3_C128)
+            k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, yf);
+        else
+            k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, yf);
+        ctx->count("k_apply_prep");
+        G3_CUDA(cudaGetLastError());
+    }
+    if (nf && !nf->order.empty()) {
+        constexpr int NT = 256, KC = 16;
+        dim3 grid((unsigned)nf->order.size(), (Ku + KC - 1) / KC);
+        k_pf_near<T, NT><<<grid, NT, 0, ctx->stream>>>(nf->data.as<Cx<T>>(), nf->d_ranges.as<BlockRange>(),
+                                                       nf->d_offs.as<long long>(), Ku, KC, E, Wf, Wc, yf, yc);
+        ctx->count("k_pf_near");
+        G3_CUDA(cudaGetLastError());
+    }
+    if (n_items) {
+        if (!fa->plan_ready) return fail(G3_EINVAL, "apply_gcq: factors without block ranges on the device");
+        const size_t smem = (size_t)(PF_JC + RF_TS) * (PF_NC + 1) * sizeof(Cx<T>);
+        G3_CUDA(cudaFuncSetAttribute(k_pf_far<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_pf_far<T><<<(unsigned)n_items, PF_NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                                  fa->d_r3.as<int>(), fa->d_franges.as<BlockRange>(),
+                                                                  d_items, fa->Cmax, Ku, E, Wf, Wc, yf, yc);
+        ctx->count("k_pf_far");
+        G3_CUDA(cudaGetLastError());
+    }
+    {
+        const int blocks = (int)((nW + 255) / 256);
+        if (dtype == G3_C128)
+            k_pf_finish<T, double><<<blocks, 256, 0, ctx->stream>>>(E, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                  f->d_partner.as<int>(), yf, yc, (Cx<double>*)Y);
+        else
+            k_pf_finish<T, float><<<blocks, 256, 0, ctx->stream>>>(E, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
+                                                                 f->d_partner.as<int>(), yf, yc, (Cx<float>*)Y);
+        ctx->count("k_pf_finish");
+        G3_CUDA(cudaGetLastError());
+    }
+    G3_CUDA(cudaEventRecord(e3, ctx->stream));
+    G3_CUDA(cudaEventSynchronize(e3));
+    float ms_all = 0;
+    G3_CUDA(cudaEventElapsedTime(&ms_all, e0, e3));
+    ctx->last_apply_ms = ms_all;
+    ctx->last_near_ms = 0;
+    const int64_t in_sz = dtype == G3_C128 ? 16 : 8;
+    const int64_t near_bytes = nf ? nf->n_entries * (int64_t)sizeof(Cx<T>) : 0;
+    ctx->last_near_bytes = near_bytes;
+    ctx->last_apply_bytes = near_bytes + (fa ? fa->stats.factor_bytes : 0) + 2 * (int64_t)E * K * in_sz;
+    return G3_OK;
+}
+
+// ============================================================================
 // Allocation-free apply
 // ============================================================================
 //
@@ -656,11 +934,14 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
 
 g3_status run_apply(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W, void* Y,
                     int dtype, int mode) {
-    if (mode != G3_APPLY_SUM) return fail(G3_EUNSUPPORTED, "apply_gcq: only G3_APPLY_SUM is implemented");
     const g3_freqs* f = nf ? nf->freqs : fa->freqs;
     const int prec = nf ? nf->prec : fa->prec;
     if (nf && fa && (nf->prec != fa->prec || nf->freqs != fa->freqs))
         return fail(G3_EINVAL, "apply_gcq: near field and factors differ in precision or frequency set");
+    if (mode == G3_APPLY_PERFREQ) {
+        if (prec == G3_MIXED) return run_apply_perfreq_t<float>(ctx, t, nf, fa, W, Y, dtype, f);
+        return run_apply_perfreq_t<double>(ctx, t, nf, fa, W, Y, dtype, f);
+    }
     if (prec == G3_MIXED) return run_apply_t<float>(ctx, t, nf, fa, W, Y, dtype, f);
     return run_apply_t<double>(ctx, t, nf, fa, W, Y, dtype, f);
 }

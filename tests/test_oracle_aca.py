@@ -252,3 +252,109 @@ def test_sample_positions_cover_the_block():
     assert len(set(pos)) == 32
     assert len({i for i, _ in pos}) == 32 and len({j for _, j in pos}) == 32
     assert all(0 <= i < 7 and 0 <= j < 5 for i, j in aca3.sample_entries(7, 5))
+
+
+# ---------------------------------------------------------------- next frequency and the literal stop
+
+def _staircase_tensor(scale3: float = 1.0):
+    """Rank-3 tensor sum_t a_t (x) b_t (x) c_t whose three terms live on
+    disjoint column ranges (columns 3t..3t+2 of a 12 x 9 block; the a_t are
+    dense, so every row of a face meets every term; Ku = 10) and whose fibers
+    are built so that Algorithm 1's frequency sequence follows from the
+    definitions alone (the fiber at a pivot in column range t is term t's):
+
+      c_0: c_0[0] = 1 (the only term at k = 0), largest other entry at k = 3
+           (0.9), second largest at k = 5 (0.8);
+      c_1: c_1[0] = 0, c_1[3] = 1 (the only term left at k = 3), largest
+           entry off {0, 3} at k = 7 (0.7), small at k = 5;
+      c_2: c_2[0] = c_2[3] = 0, c_2[7] = scale3 (the only term left at k = 7).
+
+    Face 1 (k = 0) is term 0 alone, so f_1 = c_0 / c_0[0] and C^(1) is term 0
+    exactly; the argmax over unused k of |f_1| is k = 3 (k = 0 itself has
+    |f_1| = 1 > 0.9 and must be excluded).  Face 2 (k = 3) is term 1 alone,
+    f_2 = c_1 / c_1[3], next k = 7 (taking |f_1| instead of |f_2| would give
+    k = 5).  Face 3 (k = 7) is term 2 alone and C^(3) equals the tensor."""
+    rng = np.random.default_rng(77)
+    M, N, Ku = 12, 9, 10
+    a = np.zeros((3, M), complex)
+    b = np.zeros((3, N), complex)
+    for t in range(3):
+        a[t] = _rand(rng, M)
+        b[t, 3 * t:3 * t + 3] = _rand(rng, 3)
+
+    def fiber(mags):
+        return np.asarray(mags) * np.exp(2j * np.pi * rng.random(Ku))
+
+    c = np.zeros((3, Ku), complex)
+    c[0] = fiber([1.0, 0.3, 0.2, 0.9, 0.4, 0.8, 0.1, 0.35, 0.25, 0.15])
+    c[0, 0] = 1.0
+    c[1] = fiber([0.0, 0.2, 0.3, 1.0, 0.25, 0.05, 0.4, 0.7, 0.1, 0.45])
+    c[2] = fiber([0.0, 0.5, 0.3, 0.0, 0.2, 0.4, 0.1, 1.0, 0.45, 0.35]) * scale3
+    return a, b, c
+
+
+@pytest.mark.parametrize("dense_max", [aca3.DENSE_MAX, -1])
+@pytest.mark.parametrize("sample_check", [True, False])
+def test_next_frequency_rule_sequence(dense_max, sample_check):
+    """Algorithm 1's k_{l+1} = argmax over unused k of |f_l[k]| on a tensor
+    whose frequency sequence is known in advance (0, 3, 7)."""
+    a, b, c = _staircase_tensor()
+    op = aca3.SeparableBlock(a, b, c)
+    res = aca3.aca3(op, 1e-4, dense_max=dense_max, sample_check=sample_check)
+    assert [x.k for x in res.crosses] == [0, 3, 7]
+    # each cross carries one term: its pivot lies in that term's column range
+    for t, x in enumerate(res.crosses):
+        assert 3 * t <= x.j < 3 * t + 3
+        assert np.allclose(x.f, c[t] / c[t, x.k], rtol=0, atol=1e-13)
+    D = op.dense()
+    assert np.linalg.norm(D - res.dense(12, 9, 10)) < 1e-13 * np.linalg.norm(D)
+    # a fourth face is zero up to rounding: it is either detected as zero or
+    # computed from rounding noise and dropped by the stopping test
+    assert res.rank == 3 and res.computed in (3, 4)
+
+
+@pytest.mark.parametrize("dense_max", [aca3.DENSE_MAX, -1])
+def test_literal_stop_drops_the_last_cross(dense_max):
+    """Algorithm 1 as written: the cross that meets the stopping test is
+    computed and discarded (r = l - 1).  With the third term at 1e-6 of the
+    others, cross 3 meets ||H_3|| ||f_3|| <= eps3 ||C^(3)|| for eps3 = 1e-4;
+    the returned approximant is terms 0 and 1, off by exactly the third term."""
+    a, b, c = _staircase_tensor(scale3=1e-6)
+    op = aca3.SeparableBlock(a, b, c)
+    D = op.dense()
+    third = np.einsum("i,j,k->ijk", a[2], b[2], c[2])
+    for sample_check in (False, True):
+        res = aca3.aca3(aca3.SeparableBlock(a, b, c), 1e-4, dense_max=dense_max, sample_check=sample_check)
+        assert res.computed == 3 and res.rank == 2 == res.computed - 1
+        assert [x.k for x in res.crosses] == [0, 3]
+        R = D - res.dense(12, 9, 10)
+        assert np.linalg.norm(R - third) < 1e-13 * np.linalg.norm(D)
+        assert np.linalg.norm(R) <= 1e-4 * np.linalg.norm(D)
+
+
+def test_literal_stop_bem_block_meets_tolerance():
+    """On the largest single-layer block of the cube the literal test is
+    valid: rank = crosses computed - 1 and the approximant meets the
+    tolerance against the dense block."""
+    op, D, s_u = _bem_block()
+    eps3 = 1e-4
+    res = aca3.aca3(op, eps3, s_abs=np.abs(s_u), dense_max=-1, sample_check=False)
+    assert res.rank == res.computed - 1 and res.rank >= 2
+    C = res.dense(*D.shape)
+    assert np.linalg.norm(D - C) <= 10 * eps3 * np.linalg.norm(D)
+
+
+def test_perfreq_dense_apply_terms():
+    """Y[:, l] = A(s_l) w_l: each column is the dense matrix at s_l times w_l,
+    and the columns sum to the SUM-mode apply of eq. (product)."""
+    w = workloads.get("cube48")
+    g = Q.Geometry(w.verts, w.tris)
+    s_all = freqs.bdf2(6, 0.1, (1e-8) ** (1.0 / 12))
+    W = workloads.densities(w.E, 6, 5)
+    ef = lambda I, J, s: Q.entries(g, "slp", I, J, s)
+    Y = A.dense_apply_perfreq(ef, w.E, s_all, W)
+    D = Q.dense(g, "slp", s_all)
+    for l in range(6):
+        assert np.allclose(Y[:, l], D[:, :, l] @ W[:, l], rtol=1e-13, atol=0)
+    y = A.dense_apply(ef, w.E, s_all, W)
+    assert np.allclose(Y.sum(axis=1), y, rtol=1e-13, atol=0)

@@ -100,3 +100,42 @@ def test_jacobi_complex_identities():
 def test_gcq_constant_steps_rejected():
     with pytest.raises(ValueError):
         freqs.gcq(64, 0.01, 0.01)
+
+
+# ---------------------------------------------------------------- conjugate pairing of a given set
+
+def test_pair_conjugates_reproduces_the_closed_form_pairings():
+    """The closed-form sets are conjugate-closed; pairing them by value gives
+    the index rules of the multistep CQ (k <-> K - k) and the gCQ
+    (l <-> N_Q + 1 - l)."""
+    for K in (8, 32, 128):
+        s = freqs.bdf2(K, 0.1, (1e-8) ** (1.0 / (2 * K)))
+        u, p = freqs.pair_conjugates(s)
+        u0, p0 = freqs.bdf2_unique(K)
+        assert np.array_equal(u, u0) and np.array_equal(p, p0)
+    s, _ = freqs.gcq(64, 0.005, 0.015)
+    u, p = freqs.pair_conjugates(s)
+    u0, p0 = freqs.gcq_unique(64)
+    assert np.array_equal(u, u0) and np.array_equal(p, p0)
+
+
+def test_pair_conjugates_arbitrary_order_and_unpaired():
+    rng = np.random.default_rng(3)
+    s = freqs.bdf2(16, 0.05, (1e-8) ** (1.0 / 32))
+    order = rng.permutation(16)
+    t = np.r_[s[order], 2.0 + 3.0j, 5.0]        # one complex frequency without partner, one real
+    u, p = freqs.pair_conjugates(t)
+    K = t.size
+    assert np.array_equal(p[p], np.arange(K))                  # an involution
+    paired = p != np.arange(K)
+    assert np.allclose(t[p][paired], np.conj(t[paired]))       # partner = conjugate
+    # self-partners: the real frequencies (BDF2 k = 0, K/2 and the extra 5) and the unpaired 2 + 3i
+    assert np.sum(~paired) == 4 and np.all(np.abs(t[~paired].imag[:-2]) < 1e-12 * np.abs(t[~paired][:-2]))
+    assert np.all(np.diff(u) > 0)                              # increasing
+    covered = np.zeros(K, bool)
+    covered[u] = True
+    covered[p[u]] = True
+    assert covered.all() and u.size == 9 + 2                   # 9 unique BDF2 (two real) + the two extras
+    assert p[16] == 16 and p[17] == 17
+    for l in u:                                                # the lower index of each pair is unique
+        assert p[l] >= l

@@ -33,18 +33,27 @@ def test_noalloc_matches_apply_on_two_calls(g3, ctx, name, kernel, prec, tol):
     nf = g3.assemble_near(ctx, T, F, kernel, prec=prec)
     fa = g3.aca3_compress(ctx, T, F, kernel, prec=prec, eps3=w.eps3)
     dt = torch.complex64 if prec == "mixed" else torch.complex128
+    y = torch.empty(w.E, dtype=dt, device="cuda")
     for call, seed in enumerate((w.density_seed, w.density_seed + 1)):
-        W = torch.from_numpy(workloads.densities(w.E, w.freq.K, seed)).to("cuda", dt)
+        # W [M, K] with contiguous columns, as the allocation-free call wants it
+        W = torch.from_numpy(workloads.densities(w.E, w.freq.K, seed).T.copy()).to("cuda", dt).t()
         y_ref = g3.apply_gcq(ctx, T, nf, fa, W)
-        y = g3.apply_gcq_noalloc(ctx, T, nf, fa, W)
         torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        g3.apply_gcq_noalloc(ctx, T, nf, fa, W, y)
+        torch.cuda.synchronize()
+        if call == 1:
+            # the second call allocates nothing: neither the device nor torch's allocator moves
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
         err = float((y - y_ref).abs().max() / y_ref.abs().max())
         assert err <= tol, (call, err)
     # near field alone and far field alone
-    W = torch.from_numpy(workloads.densities(w.E, w.freq.K, 99)).to("cuda", dt)
+    W = torch.from_numpy(workloads.densities(w.E, w.freq.K, 99).T.copy()).to("cuda", dt).t()
     for a, b in ((nf, None), (None, fa)):
         y_ref = g3.apply_gcq(ctx, T, a, b, W)
-        y = g3.apply_gcq_noalloc(ctx, T, a, b, W)
+        g3.apply_gcq_noalloc(ctx, T, a, b, W, y)
         torch.cuda.synchronize()
         assert float((y - y_ref).abs().max() / y_ref.abs().max()) <= tol
 
@@ -57,7 +66,8 @@ def test_noalloc_rejects_problems_beyond_its_scratch(g3, ctx):
     T = g3.build_cluster_tree(ctx, v, t, 32, 1.0)
     F = g3.freqs_from_spec(ctx, spec)
     fa = g3.aca3_compress(ctx, T, F, "slp", prec="fp64", eps3=1e-4, max_blocks=1)
-    W = torch.zeros((t.shape[0], 128), dtype=torch.complex128, device="cuda")
+    W = torch.zeros((128, t.shape[0]), dtype=torch.complex128, device="cuda").t()
+    Y = torch.empty(t.shape[0], dtype=torch.complex128, device="cuda")
     with pytest.raises(g3.G3Error) as e:
-        g3.apply_gcq_noalloc(ctx, T, None, fa, W)
+        g3.apply_gcq_noalloc(ctx, T, None, fa, W, Y)
     assert "EINVAL" in str(e.value) and "scratch" in str(e.value)
