@@ -12,9 +12,14 @@ three-way ACA plus the near field), with the apply's GB/s alongside.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
-Multi-GPU: each rank runs its own copy of the workload (independent
-problems, no collective on the data path; weak scaling); the timed region
-is bracketed by barriers and the step time is the maximum over ranks.
+Multi-GPU: one problem divided by row clusters (g3_shard_rows /
+g3_tree_subset): each rank assembles, compresses and applies the blocks of
+its row clusters, with disjoint output rows and no collective on the data
+path (strong scaling); the timed region is bracketed by barriers, the step
+time is the maximum over ranks and the entries are summed over ranks.
+
+Workloads: lshape12288 (default), lshape12288_nocap, sphere20480 (Galerkin),
+sphere81920, batch64 (64 meshes in one compression launch per operator).
 """
 from __future__ import annotations
 
@@ -31,8 +36,9 @@ sys.path.insert(0, ROOT)
 METRIC = "3-way ACA entries/s & apply GB/s (1 GB300); learned+batched vs plain at 1e-4"
 
 # special-function-unit operations per collocation entry: 7 quadrature points,
-# each one rsqrt, one ex2, one sin and one cos
+# each one rsqrt, one ex2, one sin and one cos (Galerkin: 16 points)
 MUFU_PER_ENTRY = 28
+MUFU_PER_ENTRY_GALERKIN = 64
 # special-function-unit results per clock per SM for rsqrt / sin / cos
 SFU_PER_CLK_SM = 16
 
@@ -110,17 +116,30 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle timing (cpu_baseline leg and the reference arm)
+# CPU oracle legs: timing (cpu_baseline and the reference arm) and the error
+# of the timed GPU results against the float64 oracle
 # ---------------------------------------------------------------------------
 
 _ORACLE_CACHE: dict = {}
 
 
+def mesh_list(name: str):
+    """The workload's meshes: one, or the 64 of the batched workload."""
+    from inputs import workloads
+    if name == "batch64":
+        return workloads.batch64()
+    return [workloads.get(name)]
+
+
 def _oracle_setup(name: str):
+    """(workload, geometry, tree, frequency set) of a mesh; `name` is a
+    workload name or "batch64[g]" for mesh g of the batch."""
     if name not in _ORACLE_CACHE:
-        from inputs import workloads
         from oracle import freqs as O_freqs, quadrature as O_q, tree as O_tree
-        w = workloads.get(name)
+        if name.startswith("batch64["):
+            w = mesh_list("batch64")[int(name[8:-1])]
+        else:
+            w = mesh_list(name)[0]
         geo = O_q.Geometry(w.verts, w.tris)
         T = O_tree.build(w.verts, w.tris, w.leaf, w.eta, w.max_block)
         fs = O_freqs.frequency_set(w.freq)
@@ -128,16 +147,25 @@ def _oracle_setup(name: str):
     return _ORACLE_CACHE[name]
 
 
+def _entry_fn(w, geo, ker):
+    """The oracle's ENTRY(I, J, s) of the workload's scheme."""
+    if w.scheme == "colloc7":
+        from oracle import quadrature as O_q
+        return lambda I, J, s: O_q.entries(geo, ker, I, J, s)
+    from oracle import galerkin as O_g
+    return lambda I, J, s: O_g.entries(w.verts, w.tris, I, J, s)
+
+
 def _oracle_job(job):
     """One unit of oracle work: compress far block b of operator `ker` (or
     evaluate near block b at every unique frequency).  Returns entries."""
     import numpy as np
-    from oracle import aca3 as O_aca, quadrature as O_q
+    from oracle import aca3 as O_aca
     name, ker, b = job
     w, geo, T, fs = _oracle_setup(name)
     su = fs["s"][fs["uniq"]]
     rb, re, cb, ce, adm = T.blocks[b]
-    ef = lambda I, J, s: O_q.entries(geo, ker, I, J, s)
+    ef = _entry_fn(w, geo, ker)
     if adm:
         op = O_aca.BemBlock(ef, T.perm[rb:re], T.perm[cb:ce], su)
         O_aca.aca3(op, w.eps3, s_abs=np.abs(su))
@@ -149,34 +177,45 @@ def _oracle_job(job):
     return int(I.size * su.size)
 
 
-def _oracle_warm(name):
-    _oracle_setup(name)
+def _oracle_warm(names):
+    for n in names:
+        _oracle_setup(n)
     return os.getpid()
+
+
+def _mesh_names(name: str, n_mesh: int) -> list[str]:
+    return [f"batch64[{g}]" for g in range(n_mesh)] if name == "batch64" else [name]
 
 
 def oracle_sample(name: str, seconds: float, seed: int, cores: int) -> dict:
     """Oracle entries/s on a seeded random sample of the workload's blocks
     (far blocks through the oracle's three-way ACA, near blocks through its
-    dense quadrature, in the workload's far/near proportion), run on a spawn
-    pool of `cores` processes for about `seconds` of wall time."""
+    dense quadrature, in the workload's far/near proportion; for the batch,
+    blocks of eight seeded meshes), run on a spawn pool of `cores` processes
+    for about `seconds` of wall time."""
     import multiprocessing as mp
 
     import numpy as np
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
-    w, geo, T, fs = _oracle_setup(name)
     rng = np.random.default_rng(seed)
-    far = np.nonzero(T.blocks[:, 4] == 1)[0]
-    near = np.nonzero(T.blocks[:, 4] == 0)[0]
+    names = _mesh_names(name, 64)
+    if len(names) > 1:
+        names = [names[int(g)] for g in np.sort(rng.choice(len(names), 8, replace=False))]
+    setups = {n: _oracle_setup(n) for n in names}
     jobs = []
     for i in range(100000):
-        ker = w.kernels[i % len(w.kernels)]
+        n = names[i % len(names)]
+        w, geo, T, fs = setups[n]
+        ker = w.kernels[(i // len(names)) % len(w.kernels)]
+        far = np.nonzero(T.blocks[:, 4] == 1)[0]
+        near = np.nonzero(T.blocks[:, 4] == 0)[0]
         pick_far = rng.random() < far.size / (far.size + near.size)
         b = int(rng.choice(far if pick_far else near))
-        jobs.append((name, ker, b))
+        jobs.append((n, ker, b))
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_warm, [name] * cores)
+        pool.map(_oracle_warm, [names] * cores)
         t0 = time.perf_counter()
         entries = 0
         done = 0
@@ -188,10 +227,60 @@ def oracle_sample(name: str, seconds: float, seed: int, cores: int) -> dict:
                 break
         wall = time.perf_counter() - t0
         pool.terminate()
+    kers = "/".join(setups[names[0]][0].kernels)
     return {"value": entries / wall, "unit": "entries/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} seeded random blocks of {name} ({'/'.join(w.kernels)}; far blocks through the "
+            "sample": f"{done} seeded random blocks of {name} ({kers}; far blocks through the "
                       f"oracle's three-way ACA, near blocks densely), {wall:.1f} s wall",
             "entries": entries, "seconds": wall}
+
+
+def _dense_row_job(job):
+    """y_ref[i] = sum_l sum_j A(s_l)[i, j] W[j, l] of one row (original order),
+    optionally restricted to the column ranges of a block list."""
+    import numpy as np
+    from oracle import apply as O_apply
+    from inputs import workloads
+    name, ker, i, seed, cols = job
+    w, geo, T, fs = _oracle_setup(name)
+    key = ("W", name, seed)
+    if key not in _ORACLE_CACHE:   # the seeded densities, regenerated in the worker
+        _ORACLE_CACHE[key] = workloads.densities(w.E, w.freq.K, seed)
+    W = _ORACLE_CACHE[key]
+    ef = _entry_fn(w, geo, ker)
+    if cols is None:
+        return O_apply.dense_apply(ef, w.E, fs["s"], W, rows=[i])[0]
+    A = ef(np.full(cols.size, i), cols, fs["s"])
+    return np.sum(A * W[cols, :])
+
+
+def oracle_rows(jobs, cores: int) -> list:
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        return pool.map(_dense_row_job, jobs, chunksize=1)
+
+
+def apply_errors(name: str, kernels, ys: dict, seeds: list, n_rows: int, seed: int, cores: int) -> dict:
+    """Relative error ||y - y_ref|| / ||y_ref|| of the timed run's applies on
+    seeded sampled rows against the float64 oracle's dense apply (every entry
+    at all K frequencies), per operator (and per mesh of a batch: three
+    seeded meshes)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    names = _mesh_names(name, len(seeds))
+    picks = list(range(len(names))) if len(names) == 1 else sorted(rng.choice(len(names), 3, replace=False).tolist())
+    out = {}
+    for ker in kernels:
+        for g in picks:
+            w = _oracle_setup(names[g])[0]
+            rows = np.sort(rng.choice(w.E, min(n_rows, w.E), replace=False))
+            ref = np.array(oracle_rows([(names[g], ker, int(i), seeds[g], None) for i in rows], cores))
+            got = ys[(ker, g)][rows]
+            key = ker if len(names) == 1 else f"{ker}[{g}]"
+            out[key] = {"rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), "rows": int(rows.size)}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -209,26 +298,39 @@ def max_over_ranks(values: list[float], device=None) -> list[float]:
     return [float(x) for x in t.cpu()]
 
 
-def whole_job_rate(units_per_rank: float, world: int, ms_max: float, steps: int) -> float:
+def sum_over_ranks(values: list[float], device=None) -> list[float]:
+    """Element-wise sum of `values` over all ranks (identity for one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_all_ranks: float, ms_max: float, steps: int) -> float:
     """Units processed by all ranks per second, timed by the slowest rank."""
-    return units_per_rank * world / ((ms_max / steps) / 1e3)
+    return units_all_ranks / ((ms_max / steps) / 1e3)
 
 
 def train_predictor(g3, ctx, kernels, prec):
-    """Block predictor trained on the compressions of cube768 and lshape3072
-    (features and labels from the library, training on the GPU)."""
+    """Block predictor trained on the compressions of the smaller
+    configurations (the 768-triangle cube, the 3,072-triangle L-shape with
+    both operators, and the 1,280-triangle Galerkin icosphere): features and
+    labels from the library, training on the GPU."""
     import time
 
     import numpy as np
 
     from inputs import workloads
     X, Y = [], []
-    for name in ("cube768", "lshape3072"):
+    for name in ("cube768", "lshape3072", "sphere1280g"):
         w = workloads.get(name)
         T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
         F = g3.freqs_from_spec(ctx, w.freq)
-        for ker in kernels:
-            fa = g3.aca3_compress(ctx, T, F, ker, prec=prec, eps3=w.eps3)
+        for ker in w.kernels:
+            fa = g3.aca3_compress(ctx, T, F, ker, scheme=w.scheme, prec=prec, eps3=w.eps3)
             X.append(g3.block_features(ctx, T, F, ker, w.eps3))
             Y.append(fa.labels())
     X, Y = np.concatenate(X), np.concatenate(Y)
@@ -238,7 +340,34 @@ def train_predictor(g3, ctx, kernels, prec):
     p = net.predict(X)
     return net, {"samples": int(X.shape[0]), "epochs": 150, "seconds": secs,
                  "mae_log2_r3": float(np.abs(p[:, 0] - Y[:, 0]).mean()),
-                 "data": "cube768 + lshape3072 compressions"}
+                 "data": "cube768 + lshape3072 (slp, dlp) + sphere1280g compressions"}
+
+
+def plain_vs_batched(g3, ctx, w, T, F, ker, n_blocks: int, seed: int, prec: str, eps_plain: float,
+                     eps_ours: float, mlp=None, mlp_use=0, shape=None) -> dict:
+    """The same seeded sample of far blocks (stratified by block size),
+    compressed by the plain arm (float64, one block per launch) and by ours
+    (the timed configuration: mixed precision, one persistent launch,
+    predictor); device times and the subset trees for the error leg."""
+    import numpy as np
+    tg = T.get()
+    far = tg["far_index"]
+    sizes = (tg["blocks"][far, 1] - tg["blocks"][far, 0]) * (tg["blocks"][far, 3] - tg["blocks"][far, 2])
+    rng = np.random.default_rng(seed)
+    order = np.argsort(sizes, kind="stable")
+    strata = np.array_split(order, 8)
+    per = max(1, n_blocks // len(strata))
+    pick = np.sort(np.concatenate([rng.choice(s, min(per, s.size), replace=False) for s in strata if s.size]))
+    owner = np.ones(tg["blocks"].shape[0], dtype=np.int32)
+    owner[far[pick]] = 0
+    S = g3.tree_subset(ctx, T, owner, 0)
+    plain = g3.aca3_compress(ctx, S, F, ker, scheme=w.scheme, prec="fp64", eps3=eps_plain, unbatched=1)
+    ours = g3.aca3_compress(ctx, S, F, ker, scheme=w.scheme, prec=prec, eps3=eps_ours, mlp=mlp, mlp_use=mlp_use,
+                            **(shape or {}))
+    ps, os_ = plain.stats(), ours.stats()
+    return {"tree": S, "plain": plain, "ours": ours, "blocks": int(pick.size),
+            "plain_ms": ps["ms"], "ours_ms": os_["ms"], "plain_entries": ps["entries"], "ours_entries": os_["entries"],
+            "plain_crosses": ps["crosses"], "ours_crosses": os_["crosses"]}
 
 
 def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
@@ -250,58 +379,78 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = workloads.get(args.workload)
-    kernels = list(w.kernels)
-    W = workloads.densities(w.E, w.freq.K, w.density_seed)
-    Wd = torch.from_numpy(W).to(dev)
+    ws = mesh_list(args.workload)
+    batch = len(ws) > 1
+    kernels = list(ws[0].kernels)
+    scheme = ws[0].scheme
+    Ws = [workloads.densities(w.E, w.freq.K, w.density_seed) for w in ws]
+    Wds = [torch.from_numpy(W).to(dev) for W in Ws]
     stream = torch.cuda.current_stream(dev)
     ctx = g3.Context(local_rank, stream.cuda_stream)
     prec = args.precision
     keep = {}
 
     # the learned part: a predictor trained (untimed, like any model) on the
-    # compressions of two smaller meshes, used by every timed compression
+    # compressions of the smaller configurations, used by every timed compression
     net, train_info = None, None
     if args.mlp_use:
         net, train_info = train_predictor(g3, ctx, kernels, prec)
 
+    def make_tree(w):
+        """The mesh's tree; with several ranks, this rank's row-cluster shard."""
+        T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
+        if world == 1:
+            return T
+        tg = T.get()
+        sh = g3.shard_rows(tg["nodes"], tg["blocks"], world)
+        return g3.tree_subset(ctx, T, sh["owner"], rank)
+
     # launch shape per operator from the autotuner (untimed; cached in the context)
     tune = {}
-    if not args.no_autotune:
-        T0 = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
-        F0 = g3.freqs_from_spec(ctx, w.freq)
+    if not args.no_autotune and not batch:
+        T0 = make_tree(ws[0])
+        F0 = g3.freqs_from_spec(ctx, ws[0].freq)
         for ker in kernels:
-            tune[ker] = g3.autotune(ctx, T0, F0, ker, scheme=w.scheme, prec=prec, eps3=w.eps3)
+            tune[ker] = g3.autotune(ctx, T0, F0, ker, scheme=scheme, prec=prec, eps3=ws[0].eps3)
         del T0, F0
 
     def step(host: bool, mlp=None, mlp_use=0):
-        T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
-        F = g3.freqs_from_spec(ctx, w.freq)
+        trees = [make_tree(w) for w in ws]
+        freqs = [g3.freqs_from_spec(ctx, w.freq) for w in ws]
         rec = {"entries_aca": 0, "entries_near": 0, "aca_ms": 0.0, "near_ms": 0.0, "apply_ms": 0.0,
                "apply_near_ms": 0.0, "apply_bytes": 0, "apply_near_bytes": 0, "factor_bytes": 0,
                "dense_bytes": 0, "crosses": 0, "stats": {}}
         for ker in kernels:
-            nf = g3.assemble_near(ctx, T, F, ker, scheme=w.scheme, prec=prec)
+            nfs = [g3.assemble_near(ctx, T, F, ker, scheme=scheme, prec=prec) for T, F in zip(trees, freqs)]
             shape = {k: tune[ker][k] for k in ("threads", "dense_face_max")} if ker in tune else {}
-            fa = g3.aca3_compress(ctx, T, F, ker, scheme=w.scheme, prec=prec, eps3=w.eps3, mlp=mlp, mlp_use=mlp_use,
-                                  **shape)
-            y = g3.apply_gcq(ctx, T, nf, fa, W if host else Wd)
-            st = fa.stats()
-            ni = nf.info()
-            la = ctx.last_apply()
+            if batch:
+                fas = g3.aca3_compress_batch(ctx, trees, freqs, ker, scheme=scheme, prec=prec, eps3=ws[0].eps3,
+                                             mlp=mlp, mlp_use=mlp_use)
+            else:
+                fas = [g3.aca3_compress(ctx, trees[0], freqs[0], ker, scheme=scheme, prec=prec, eps3=ws[0].eps3,
+                                        mlp=mlp, mlp_use=mlp_use, **shape)]
+            ys = []
+            for g, (T, nf, fa) in enumerate(zip(trees, nfs, fas)):
+                ys.append(g3.apply_gcq(ctx, T, nf, fa, Ws[g] if host else Wds[g]))
+                la = ctx.last_apply()
+                rec["apply_ms"] += la["ms"]
+                rec["apply_near_ms"] += la["near_ms"]
+                rec["apply_bytes"] += la["bytes"]
+                rec["apply_near_bytes"] += la["near_bytes"]
+            st = fas[0].stats()           # a batch's times and entries are the whole launch's
             rec["entries_aca"] += st["entries"]
-            rec["entries_near"] += ni["entries"]
             rec["aca_ms"] += st["ms"]
-            rec["near_ms"] += ni["ms"]
-            rec["apply_ms"] += la["ms"]
-            rec["apply_near_ms"] += la["near_ms"]
-            rec["apply_bytes"] += la["bytes"]
-            rec["apply_near_bytes"] += la["near_bytes"]
-            rec["factor_bytes"] += st["factor_bytes"]
-            rec["dense_bytes"] += st["dense_bytes"]
-            rec["crosses"] += st["crosses"]
+            for nf in nfs:
+                ni = nf.info()
+                rec["entries_near"] += ni["entries"]
+                rec["near_ms"] += ni["ms"]
+            for fa in fas:
+                sf = fa.stats()
+                rec["factor_bytes"] += sf["factor_bytes"]
+                rec["dense_bytes"] += sf["dense_bytes"]
+                rec["crosses"] += sf["crosses"]
             rec["stats"][ker] = st
-            keep[ker] = (T, F, nf, fa, y)
+            keep[ker] = (trees, freqs, nfs, fas, ys)
         return rec
 
     def timed(n: int, host: bool):
@@ -326,16 +475,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     with Clocks(local_rank) as clk:
         recs, ms = timed(args.steps, host=False)
     launches = ctx.launch_count() - launches0
+    # the timed run's results (device path), kept for the error leg
+    ys_timed = {(ker, g): y.cpu().numpy() for ker in kernels for g, y in enumerate(keep[ker][4])}
     # end to end through the C ABI with host buffers (mesh in, densities in, y out)
     e_steps = max(1, args.steps // 2)
     erecs, ems = timed(e_steps, host=True)
-    t_max, e_max = max_over_ranks([ms, ems], device=dev)
-    if rank != 0:
-        return None
     r0 = recs[-1]
-    entries = r0["entries_aca"] + r0["entries_near"]
-    ms_step = t_max / args.steps
-    value = whole_job_rate(entries, world, t_max, args.steps)
+    t_max, e_max = max_over_ranks([ms, ems], device=dev)
+    entries_all, launches_all, aca_entries_all = sum_over_ranks(
+        [r0["entries_aca"] + r0["entries_near"], launches, r0["entries_aca"]], device=dev)
     peaks = _peaks()
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
@@ -344,29 +492,52 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     aca_entries = r0["entries_aca"] / len(kernels)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     sfu_peak = SFU_PER_CLK_SM * n_sm * sm_mhz * 1e6              # SFU results/s (unit counts x clock)
-    achieved_sfu = aca_entries * MUFU_PER_ENTRY / (aca_ms / 1e3)
+    mufu = MUFU_PER_ENTRY_GALERKIN if scheme != "colloc7" else MUFU_PER_ENTRY
+    achieved_sfu = aca_entries * mufu / (aca_ms / 1e3)
     measured = {k: ctx.peak(k) for k in ("rsqrt", "ex2", "sin", "ffma", "dfma")}
     apply_ms = sum(r["apply_ms"] for r in recs) / len(recs)
     near_ms = sum(r["apply_near_ms"] for r in recs) / len(recs)
     apply_gbs = r0["apply_bytes"] / (apply_ms / 1e3) / 1e9
-    near_gbs = r0["apply_near_bytes"] / (near_ms / 1e3) / 1e9
-    # far part of the apply (everything but the near-field stream: factors,
-    # W read once, y written once); the near field runs on a second stream
-    # next to the far-field kernels, so this is the far part's share of the
-    # apply's wall time
-    far_gbs = (r0["apply_bytes"] - r0["apply_near_bytes"]) / ((apply_ms - near_ms) / 1e3) / 1e9
-    # plain baseline: float64, one block per launch (host loop), on a bounded
-    # sample of the first admissible blocks of the single layer
-    T, F, nf, fa, y = keep[kernels[0]]
-    plain = g3.aca3_compress(ctx, T, F, kernels[0], prec="fp64", eps3=w.eps3, unbatched=1,
-                             max_blocks=args.plain_blocks).stats()
-    ours_sample = g3.aca3_compress(ctx, T, F, kernels[0], prec=prec, eps3=w.eps3,
-                                   max_blocks=args.plain_blocks).stats()
-    plain_eps = plain["entries"] / (plain["ms"] / 1e3)
+    near_gbs = r0["apply_near_bytes"] / (near_ms / 1e3) / 1e9 if near_ms > 0 else None
+    # each part of the apply alone (the near field and the far field on the
+    # context's stream, one after the other; in the timed apply they overlap)
+    parts = {"near_ms": 0.0, "near_bytes": 0, "far_ms": 0.0, "far_bytes": 0}
+    for ker in kernels:
+        trees, freqs, nfs, fas, _ = keep[ker]
+        for g, (T, nf, fa) in enumerate(zip(trees, nfs, fas)):
+            for part, a, b in (("near", nf, None), ("far", None, fa)):
+                best = None
+                for _ in range(3):
+                    g3.apply_gcq(ctx, T, a, b, Wds[g])
+                    la = ctx.last_apply()
+                    best = la if best is None or la["ms"] < best["ms"] else best
+                parts[part + "_ms"] += best["ms"]
+                parts[part + "_bytes"] += best["bytes"]
+    apply_parts = {k: {"ms": parts[k + "_ms"], "bytes": parts[k + "_bytes"],
+                       "gbs": parts[k + "_bytes"] / (parts[k + "_ms"] / 1e3) / 1e9 if parts[k + "_ms"] > 0 else None}
+                   for k in ("near", "far")}
+    # learned + batched vs plain at equal accuracy: one seeded block sample,
+    # both arms (single meshes only; the plain arm is one block per launch)
+    vs_plain = None
+    pv = None
+    if not batch and world == 1 and args.plain_blocks > 0:
+        trees, freqs, _, _, _ = keep[kernels[0]]
+        shape = {k: tune[kernels[0]][k] for k in ("threads", "dense_face_max")} if kernels[0] in tune else {}
+        pv = plain_vs_batched(g3, ctx, ws[0], trees[0], freqs[0], kernels[0], args.plain_blocks, 17, prec,
+                              ws[0].eps3, ws[0].eps3, net, args.mlp_use, shape)
+        vs_plain = {"value": pv["plain_ms"] / pv["ours_ms"], "same_blocks": True, "blocks": pv["blocks"],
+                    "operator": kernels[0], "plain_ms": pv["plain_ms"], "ours_ms": pv["ours_ms"],
+                    "plain_eps3": ws[0].eps3, "ours_eps3": ws[0].eps3,
+                    "plain_entries_per_s": pv["plain_entries"] / (pv["plain_ms"] / 1e3),
+                    "ours_entries_per_s": pv["ours_entries"] / (pv["ours_ms"] / 1e3),
+                    "plain_crosses": pv["plain_crosses"], "ours_crosses": pv["ours_crosses"],
+                    "sample": f"{pv['blocks']} far blocks of {kernels[0]} drawn by seed 17, stratified by block "
+                              "size (8 strata); plain = float64, one block per launch; ours = the timed "
+                              "configuration (mixed precision, one persistent launch, predictor)"}
     # what the predictor gains: the same compression without it, and with
     # queue order + pool size only (one step each, after the timed region)
     learned = None
-    if net is not None:
+    if net is not None and world == 1:
         ab = {}
         for label, (m, u) in {"none": (None, 0), "order_pool": (net, 3), "all": (net, 7)}.items():
             r = step(False, m, u)
@@ -374,7 +545,13 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                          "spilled_blocks": sum(st["spilled_blocks"] for st in r["stats"].values()),
                          "pool_regrows": sum(st["pool_regrows"] for st in r["stats"].values())}
         learned = {"mlp_use": args.mlp_use, "training": train_info, "ab": ab}
+    if rank != 0:
+        return None
+    ms_step = t_max / args.steps
+    value = whole_job_rate(entries_all, t_max, args.steps)
     aca_eps = sum(r["entries_aca"] for r in recs) / (sum(r["aca_ms"] for r in recs) / 1e3)
+    h2d = sum(int(w.verts.nbytes + w.tris.nbytes) for w in ws) + len(kernels) * sum(int(W.nbytes) for W in Ws)
+    d2h = len(kernels) * sum(int(w.E * 16) for w in ws)
     out = {
         "metric": METRIC,
         "value": value,
@@ -384,49 +561,84 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "warmup": args.warmup,
         "ms_per_step": ms_step,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong",
         "vs_baseline": None,
         "dtype": "f32" if prec == "mixed" else "f64",
         "data": "synthetic",
-        "config": {**workloads.describe(w), "precision": prec,
+        "config": {**(workloads.describe(ws[0]) if not batch else
+                      {"workload": "batch64", "meshes": len(ws), "triangles": int(sum(w.E for w in ws)),
+                       "K": sorted({w.freq.K for w in ws}), "kernels": kernels, "scheme": scheme,
+                       "eps3": ws[0].eps3, "max_block": ws[0].max_block}),
+                   "precision": prec,
                    "l2": "inputs larger than L2: near field %.1f GB and factors %.1f GB per operator, "
                          "no flush" % (r0["apply_near_bytes"] / len(kernels) / 1e9,
                                        r0["factor_bytes"] / len(kernels) / 1e9),
-                   "parallelism": f"independent replicas x{world}"},
+                   "parallelism": ("single GPU" if world == 1 else
+                                   f"row-cluster shards x{world} (one problem divided, no data-path collective)")},
         "apply_gbs": apply_gbs,
         "near_apply_gbs": near_gbs,
-        "far_apply_gbs": far_gbs,
-        "entries_per_step": entries,
-        "entries_aca": r0["entries_aca"],
-        "entries_near": r0["entries_near"],
+        "apply_parts": apply_parts,
+        "entries_per_step": entries_all,
+        "entries_aca": aca_entries_all,
+        "entries_near": entries_all - aca_entries_all,
         "phase_ms": {"aca3_compress": r0["aca_ms"], "assemble_near": r0["near_ms"], "apply_gcq": r0["apply_ms"]},
         "storage_ratio": r0["factor_bytes"] / r0["dense_bytes"] if r0["dense_bytes"] else None,
         "crosses": r0["crosses"],
-        "gpu_launches": int(launches),
-        "e2e": {"value": whole_job_rate(entries, world, e_max, e_steps), "unit": "entries/s",
-                "h2d_bytes_per_step": int(w.verts.nbytes + w.tris.nbytes + len(kernels) * W.nbytes),
-                "d2h_bytes_per_step": int(len(kernels) * w.E * 16)},
+        "gpu_launches": int(launches_all),
+        "e2e": {"value": whole_job_rate(entries_all, e_max, e_steps), "unit": "entries/s",
+                "h2d_bytes_per_step": int(h2d * world), "d2h_bytes_per_step": int(d2h * world)},
         "roofline": {"bound": "alu", "achieved": achieved_sfu / 1e12, "peak": sfu_peak / 1e12,
                      "unit": "Tops/s (special-function unit)", "frac": achieved_sfu / sfu_peak, "traffic": None,
                      "kernel": "k_aca3",
-                     "note": f"{MUFU_PER_ENTRY} SFU ops per entry x {aca_entries:.4g} entries per launch / "
-                             f"{aca_ms:.1f} ms; peak = {SFU_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz"},
-        "roofline_apply": {"bound": "hbm", "achieved": near_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": near_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_apply_near",
+                     "note": f"{mufu} SFU ops per entry x {aca_entries:.4g} entries per launch / "
+                             f"{aca_ms:.1f} ms; peak = {SFU_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz "
+                             "(unit counts and clock, matching the measured rsqrt / sin rates)"},
+        "roofline_apply": {"bound": "hbm", "achieved": apply_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": apply_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "apply_gcq (all kernels)",
                            "peak_source": peaks["source"]},
         "measured_pipes_ops_per_s": measured,
-        "vs_plain": {"value": aca_eps / plain_eps, "plain_entries_per_s": plain_eps,
-                     "ours_same_sample_entries_per_s": ours_sample["entries"] / (ours_sample["ms"] / 1e3),
-                     "ours_full_entries_per_s": aca_eps,
-                     "sample": f"first {plain['blocks_run']} admissible blocks of {kernels[0]}, float64, one "
-                               f"block per launch vs the mixed-precision persistent launch over all blocks"},
+        "vs_plain": vs_plain,
         "clocks": clk.summary(),
         "peaks_source": peaks["source"],
         "learned": learned,
         "autotune": tune or None,
+        "compression_entries_per_s": aca_eps,
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(args.workload, args.cpu_seconds, 7, os.cpu_count() or 1)
+        # error of the timed results against the float64 oracle on sampled rows
+        out["apply_error_vs_oracle"] = apply_errors(args.workload, kernels, ys_timed,
+                                                    [w.density_seed for w in ws], args.error_rows, 5,
+                                                    os.cpu_count() or 1)
+        if pv is not None:
+            out["vs_plain"]["errors"] = plain_arm_errors(g3, ctx, ws[0], kernels[0], pv, ws[0].density_seed, Wds[0],
+                                                         args.error_rows, os.cpu_count() or 1)
+    return out
+
+
+def plain_arm_errors(g3, ctx, w, ker, pv, seed: int, Wd, n_rows: int, cores: int) -> dict:
+    """Far-field apply of the sampled blocks by both arms against the float64
+    oracle's dense apply of the same blocks, on seeded sampled rows."""
+    import numpy as np
+    S = pv["tree"]
+    sg = S.get()
+    perm, blocks = sg["perm"], sg["blocks"]
+    rng = np.random.default_rng(11)
+    cand = np.unique(np.concatenate([perm[rb:re] for rb, re, _, _, _ in blocks]))
+    rows = np.sort(rng.choice(cand, min(n_rows, cand.size), replace=False))
+    jobs = []
+    for i in rows:
+        cols = []
+        for rb, re, cb, ce, _ in blocks:
+            if i in set(perm[rb:re].tolist()):
+                cols.append(perm[cb:ce])
+        jobs.append((w.name, ker, int(i), seed, np.concatenate(cols)))
+    ref = np.array(oracle_rows(jobs, cores))
+    out = {}
+    for arm in ("plain", "ours"):
+        y = g3.apply_gcq(ctx, S, None, pv[arm], Wd).cpu().numpy()
+        out[arm] = float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
+    out["rows"] = int(rows.size)
     return out
 
 
@@ -441,11 +653,13 @@ def run_reference(args) -> dict:
     sec = sum(r["seconds"] for r in res)
     value = ent / sec
     from inputs import workloads
-    w = workloads.get(args.workload)
+    ws = mesh_list(args.workload)
+    w = ws[0]
+    cfg = workloads.describe(w) if len(ws) == 1 else {"workload": "batch64", "meshes": len(ws)}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(res),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**workloads.describe(w), "precision": "fp64 (oracle)"},
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**cfg, "precision": "fp64 (oracle)"},
             "cpu_baseline": {"value": value, "unit": "entries/s", "cores": res[0]["cores"], "kind": "oracle",
                              "sample": res[0]["sample"]},
             "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -489,7 +703,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lshape12288")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--plain-blocks", type=int, default=400)
+    ap.add_argument("--plain-blocks", type=int, default=400,
+                    help="far blocks in the same-sample plain float64 vs batched comparison (0 = skip)")
+    ap.add_argument("--error-rows", type=int, default=24,
+                    help="sampled rows of the apply error against the float64 oracle (cpu_baseline leg)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -253,6 +253,31 @@ g3_status build_cluster_tree(g3_ctx* ctx, const double* verts, int nv, const int
  * admissible pair are admissible).  max_block = 0: no cap (build_cluster_tree). */
 g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, const int32_t* tris, int ne,
                                     int leaf, double eta, int max_block, g3_tree** out);
+/* Sharding of the block partition over ranks by row cluster (no counterpart
+ * in the paper, whose code runs OpenMP threads over H-matrix blocks on one
+ * node; Section 5.1).  Blocks are independent units of assembly and
+ * compression, and the apply adds each block's product into the rows of its
+ * row cluster, so ranks that own whole row clusters split the work with
+ * disjoint output rows and no exchange on the data path.
+ * Host only (no GPU, no context): nodes [n_nodes*4] and blocks [n_blocks*5]
+ * as g3_tree_get returns them; cost [n_blocks] per-block work estimates
+ * (NULL = M_b N_b); n_ranks >= 1.  Units are the clusters at the smallest
+ * depth that holds a block's row cluster (plus the leaves above it); each
+ * block belongs to the unit that contains its row cluster.  Units are
+ * assigned longest first (cost = the sum of their blocks' costs; ties: lower
+ * first element) to the least loaded rank (ties: lower rank).
+ * Outputs: owner [n_blocks] rank of each block; load [n_ranks] (may be NULL)
+ * summed cost per rank; n_units (may be NULL).  Deterministic: every rank
+ * computes the same partition.  Balance needs n_units >= n_ranks (a far-block
+ * cap, build_cluster_tree_capped, lowers the depth of the units). */
+g3_status g3_shard_rows(const int32_t* nodes, int n_nodes, const int32_t* blocks, int n_blocks, const double* cost,
+                        int n_ranks, int32_t* owner, double* load, int* n_units);
+/* A tree whose block list is the blocks of t with owner[b] == rank (owner
+ * [n_blocks] as from g3_shard_rows), in t's order; the clusters, permutation
+ * and device geometry are t's (uploaded again).  assemble_near, aca3_compress
+ * and apply_gcq on it handle only those blocks; the apply's y then holds the
+ * rank's rows, zero elsewhere, and the ranks' y add up to t's. */
+g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, int rank, g3_tree** out);
 g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near);
 /* Copy to host (any output may be NULL):
  *   perm [ne]            cluster position -> original element index

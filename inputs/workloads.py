@@ -11,7 +11,8 @@ Workloads (all synthetic; the paper's meshes and load data are not used):
                   collocation, single layer, K = 32 multistep-CQ frequencies.
 * ``lshape12288`` unit cube minus the [1/2,1]^3 octant, h = 1/32
                   (12,288 triangles), collocation, single + double layer,
-                  K = 128 multistep-CQ frequencies.
+                  K = 128 multistep-CQ frequencies (``lshape12288_nocap``:
+                  the same without the far-block cap).
 * ``sphere20480`` icosphere level 5 (20,480 triangles), Galerkin, single
                   layer, N_Q = 256 gCQ frequencies for steps in [0.005, 0.015].
 * ``batch64``     64 seeded cubes/icospheres (about 500-8,000 triangles each).
@@ -110,6 +111,10 @@ def get(name: str) -> Workload:
     if name == "lshape12288":
         v, t = meshes.lshape(32)
         return Workload(name, v, t, bdf2_spec(128, 0.02), kernels=("slp", "dlp"), density_seed=2, max_block=192)
+    if name == "lshape12288_nocap":
+        # the 12,288-triangle L-shape on the plain partition (no far-block cap)
+        v, t = meshes.lshape(32)
+        return Workload(name, v, t, bdf2_spec(128, 0.02), kernels=("slp", "dlp"), density_seed=2)
     if name == "sphere20480":
         v, t = meshes.icosphere(5)
         return Workload(name, v, t, _gcq_sphere_spec(), scheme="galerkin4x4", density_seed=3, max_block=192)

@@ -87,6 +87,8 @@ _sig("g3_freqs_free", _ci, _p)
 _sig("build_cluster_tree", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _pp)
 _sig("build_cluster_tree_capped", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _ci, _pp)
 _sig("g3_tree_info", _ci, _p, *(C.POINTER(_ci),) * 5)
+_sig("g3_shard_rows", _ci, _i32p, _ci, _i32p, _ci, _dp, _ci, _i32p, _dp, C.POINTER(_ci))
+_sig("g3_tree_subset", _ci, _p, _p, _i32p, _ci, _pp)
 _sig("g3_tree_get", _ci, _p, _i32p, _i32p, _dp, _i32p, _i32p)
 _sig("g3_tree_free", _ci, _p)
 _sig("g3_entries", _ci, _p, _p, _p, _ci, _ci, _ci, _i32p, _i32p, _ci, _i32p, _ci, _dp)
@@ -121,7 +123,7 @@ _sig("g3_factors_labels", _ci, _p, _p, _fp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_from_array", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
-            "build_cluster_tree", "build_cluster_tree_capped", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
+            "build_cluster_tree", "build_cluster_tree_capped", "g3_shard_rows", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
             "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
@@ -286,6 +288,32 @@ def build_cluster_tree(ctx: Context, verts, tris, leaf: int = 32, eta: float = 1
     h = C.c_void_p()
     _check(_lib.build_cluster_tree_capped(ctx.h, _ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0],
                                           leaf, eta, max_block, C.byref(h)), "build_cluster_tree")
+    return Tree(h, (ctx,))
+
+
+def shard_rows(nodes, blocks, n_ranks: int, cost=None) -> dict:
+    """Row-cluster partition of a block list over n_ranks (host only, no GPU):
+    {"owner": [n_blocks], "load": [n_ranks], "n_units": int}."""
+    nd = _arr(nodes, np.int32)
+    bl = _arr(blocks, np.int32)
+    nb = bl.shape[0]
+    owner = np.zeros(max(nb, 1), dtype=np.int32)
+    load = np.zeros(n_ranks)
+    nu = C.c_int()
+    c = None if cost is None else _arr(cost, np.float64)
+    _check(_lib.g3_shard_rows(_ptr(nd, C.c_int32), nd.shape[0], _ptr(bl, C.c_int32), nb,
+                              None if c is None else _ptr(c, C.c_double), n_ranks, _ptr(owner, C.c_int32),
+                              _ptr(load, C.c_double), C.byref(nu)), "g3_shard_rows")
+    return {"owner": owner[:nb], "load": load, "n_units": nu.value}
+
+
+def tree_subset(ctx: Context, tree: Tree, owner, rank: int) -> Tree:
+    """The blocks of `tree` owned by `rank` (g3_tree_subset)."""
+    o = _arr(owner, np.int32)
+    if o.size != tree.info()["n_blocks"]:
+        raise ValueError("owner must have one entry per block")
+    h = C.c_void_p()
+    _check(_lib.g3_tree_subset(ctx.h, tree.h, _ptr(o, C.c_int32), rank, C.byref(h)), "g3_tree_subset")
     return Tree(h, (ctx,))
 
 

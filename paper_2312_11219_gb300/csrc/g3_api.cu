@@ -413,6 +413,49 @@ g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, co
     return G3_OK;
 }
 
+g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, int rank, g3_tree** out) {
+    G3_CHECK(ctx && t && owner && out, "g3_tree_subset: NULL argument");
+    *out = nullptr;
+    G3_TRY(use_device(ctx));
+    g3_tree* s = new (std::nothrow) g3_tree();
+    if (!s) return fail(G3_ENOMEM, "g3_tree_subset: out of host memory");
+    s->ctx = ctx;
+    s->ne = t->ne;
+    s->nv = t->nv;
+    s->leaf = t->leaf;
+    s->max_block = t->max_block;
+    s->eta = t->eta;
+    s->verts = t->verts;
+    s->tris = t->tris;
+    s->perm = t->perm;
+    s->nodes = t->nodes;
+    s->boxes = t->boxes;
+    const size_t nb = t->blocks.size() / 5;
+    for (size_t b = 0; b < nb; ++b)
+        if (owner[b] == rank) s->blocks.insert(s->blocks.end(), &t->blocks[5 * b], &t->blocks[5 * b] + 5);
+    tree_index_blocks(s);
+    // device copies: the same uploads as build_cluster_tree (deterministic)
+    g3_status st = G3_OK;
+    cudaError_t e = s->d_perm.alloc(s->ne * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_perm.p, s->perm.data(), s->ne * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<int> tv(3 * (size_t)s->ne);
+        for (int p = 0; p < s->ne; ++p)
+            for (int k = 0; k < 3; ++k) tv[3 * (size_t)p + k] = s->tris[3 * (size_t)s->perm[p] + k];
+        e = s->d_tv.alloc(tv.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(s->d_tv.p, tv.data(), tv.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "g3_tree_subset: device copies");
+    if (st == G3_OK) st = launch_geometry(ctx, s);
+    if (st != G3_OK) {
+        delete s;
+        return st;
+    }
+    *out = s;
+    return G3_OK;
+}
+
 g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near) {
     G3_CHECK(t != nullptr, "g3_tree_info: NULL handle");
     if (ne) *ne = t->ne;

@@ -208,7 +208,7 @@ struct g3_ctx {
 
 struct g3_freqs {
     g3_ctx* ctx = nullptr;
-    int kind = 0;  // 0 = bdf2, 1 = gcq
+    int kind = 0;  // 0 = bdf2, 1 = gcq, 2 = given by the caller
     int K = 0, Ku = 0;
     std::vector<double> s;      // [2K]
     std::vector<double> omega;  // [2K]
@@ -331,5 +331,6 @@ g3_status run_peak(g3_ctx* ctx, int kind, double* ops_per_s, double* ms);
 
 // host tree builder (bit-exact specification)
 g3_status build_tree_host(g3_tree* t);
+void tree_index_blocks(g3_tree* t);
 
 }  // namespace g3

@@ -21,6 +21,7 @@
 //     boxes shrink and their distance grows), so no far block exceeds the cap
 //     unless both clusters are leaves.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <numeric>
 
@@ -189,6 +190,109 @@ g3_status build_tree_host(g3_tree* t) {
     t->nodes.swap(B.nodes);
     t->boxes.swap(B.boxes);
     t->blocks.swap(B.blocks);
+    tree_index_blocks(t);
+    return G3_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Row-cluster sharding of a block partition over ranks (host only)
+// ---------------------------------------------------------------------------
+//
+// The blocks of the partition are independent units of assembly and
+// compression, and the apply adds each block's product into the rows of its
+// row cluster.  Giving every rank whole row clusters therefore splits the
+// work with disjoint output rows and no exchange on the data path (the
+// densities are read by all ranks).  Units: the clusters at the smallest
+// depth d at which some block has its row cluster (every block's row cluster
+// lies in exactly one of them), plus the leaves above d; blocks are
+// assigned with their unit, units longest first (cost = sum of the costs of
+// their blocks) to the least loaded rank (ties: the lower unit begin, the
+// lower rank).
+g3_status shard_rows_host(const int32_t* nodes, int n_nodes, const int32_t* blocks, int nb, const double* cost,
+                          int n_ranks, int32_t* owner, double* load, int* n_units) {
+    if (!nodes || !blocks || !owner || n_nodes < 1 || nb < 0 || n_ranks < 1)
+        return fail(G3_EINVAL, "g3_shard_rows: bad argument");
+    auto N = [&](int id, int k) { return nodes[4 * (size_t)id + k]; };
+    // depth of every node (preorder: a child's id is larger than its parent's)
+    std::vector<int> depth(n_nodes, -1);
+    depth[0] = 0;
+    for (int id = 0; id < n_nodes; ++id) {
+        if (depth[id] < 0) return fail(G3_EINVAL, "g3_shard_rows: node %d is not reachable from the root", id);
+        for (int c = 2; c < 4; ++c) {
+            const int ch = N(id, c);
+            if (ch < 0) continue;
+            if (ch <= id || ch >= n_nodes) return fail(G3_EINVAL, "g3_shard_rows: child %d of node %d", ch, id);
+            depth[ch] = depth[id] + 1;
+        }
+    }
+    const int ne = N(0, 1) - N(0, 0);
+    // node of each (begin, end) row range: descend from the root
+    auto find = [&](int b, int e) -> int {
+        int id = 0;
+        for (;;) {
+            if (N(id, 0) == b && N(id, 1) == e) return id;
+            const int l = N(id, 2), r = N(id, 3);
+            if (l < 0) return -1;
+            if (e <= N(l, 1)) id = l;
+            else if (b >= N(r, 0)) id = r;
+            else return -1;
+        }
+    };
+    std::vector<int> rnode(nb);
+    int dmin = INT32_MAX;
+    for (int b = 0; b < nb; ++b) {
+        const int id = find(blocks[5 * (size_t)b], blocks[5 * (size_t)b + 1]);
+        if (id < 0) return fail(G3_EINVAL, "g3_shard_rows: block %d has no row cluster in the tree", b);
+        rnode[b] = id;
+        dmin = std::min(dmin, depth[id]);
+    }
+    if (nb == 0) dmin = 0;
+    // units: nodes at depth dmin and leaves above it, by element position
+    std::vector<int> unit_of_pos(ne > 0 ? ne : 1, -1);
+    std::vector<int> ubegin;
+    for (int id = 0; id < n_nodes; ++id) {
+        const bool leaf = N(id, 2) < 0;
+        if (depth[id] == dmin || (leaf && depth[id] < dmin)) {
+            const int u = (int)ubegin.size();
+            ubegin.push_back(N(id, 0));
+            for (int p = N(id, 0); p < N(id, 1); ++p) unit_of_pos[p - N(0, 0)] = u;
+        }
+    }
+    const int nu = (int)ubegin.size();
+    std::vector<double> ucost(nu, 0.0);
+    std::vector<int> bunit(nb);
+    for (int b = 0; b < nb; ++b) {
+        const int32_t* r = &blocks[5 * (size_t)b];
+        const int u = unit_of_pos[r[0] - N(0, 0)];
+        bunit[b] = u;
+        const double c = cost ? cost[b] : (double)(r[1] - r[0]) * (double)(r[3] - r[2]);
+        if (!(c >= 0.0) || !std::isfinite(c)) return fail(G3_EINVAL, "g3_shard_rows: cost[%d] = %g", b, c);
+        ucost[u] += c;
+    }
+    std::vector<int> order(nu);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        if (ucost[a] != ucost[b]) return ucost[a] > ucost[b];
+        return ubegin[a] < ubegin[b];
+    });
+    std::vector<double> ld(n_ranks, 0.0);
+    std::vector<int> urank(nu, 0);
+    for (int u : order) {
+        int best = 0;
+        for (int k = 1; k < n_ranks; ++k)
+            if (ld[k] < ld[best]) best = k;
+        urank[u] = best;
+        ld[best] += ucost[u];
+    }
+    for (int b = 0; b < nb; ++b) owner[b] = urank[bunit[b]];
+    if (load)
+        for (int k = 0; k < n_ranks; ++k) load[k] = ld[k];
+    if (n_units) *n_units = nu;
+    return G3_OK;
+}
+
+// far / near lists of a tree's (possibly filtered) block list
+void tree_index_blocks(g3_tree* t) {
     const int nb = (int)(t->blocks.size() / 5);
     t->far_index.clear();
     t->near_index.clear();
@@ -203,7 +307,11 @@ g3_status build_tree_host(g3_tree* t) {
             t->near_index.push_back(b);
         }
     }
-    return G3_OK;
 }
 
 }  // namespace g3
+
+extern "C" g3_status g3_shard_rows(const int32_t* nodes, int n_nodes, const int32_t* blocks, int n_blocks,
+                                   const double* cost, int n_ranks, int32_t* owner, double* load, int* n_units) {
+    return g3::shard_rows_host(nodes, n_nodes, blocks, n_blocks, cost, n_ranks, owner, load, n_units);
+}

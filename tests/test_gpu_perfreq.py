@@ -3,7 +3,8 @@ sets given as arrays (g3_freqs_from_array), through the C ABI.
 
 * g3_freqs_from_array pairs conjugates exactly as the oracle's
   pair_conjugates (bit-exact unique set and partners) and, fed the values of
-  a closed-form set, reproduces its compression and apply bit for bit.
+  a closed-form set, reproduces its ranks exactly and its apply up to the
+  order of float32 atomic sums.
 * PERFREQ: Y[:, l] = A(s_l) w_l for every l against the oracle's dense
   per-frequency apply, per column <= 1e-4 relative (the far field is
   compressed to eps3 = 1e-4); the columns sum to the SUM-mode result.
@@ -59,7 +60,8 @@ def test_from_array_reproduces_closed_form_set(g3, ctx):
         fa = g3.aca3_compress(ctx, T, FF, "slp", prec="mixed", eps3=w.eps3)
         ys.append((fa.ranks(), g3.apply_gcq(ctx, T, nf, fa, Wd).cpu().numpy()))
     assert np.array_equal(ys[0][0], ys[1][0])
-    assert np.array_equal(ys[0][1], ys[1][1])
+    # same factors; the apply's float32 atomic sums may add in another order
+    assert np.linalg.norm(ys[0][1] - ys[1][1]) <= 1e-6 * np.linalg.norm(ys[0][1])
 
 
 @pytest.mark.parametrize("dense", [0, -1])

@@ -105,7 +105,8 @@ def _rank_main(rank, world, port, out):
     import bench
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
     vals = bench.max_over_ranks([10.0 * (rank + 1), 100.0 - rank])
-    rate = bench.whole_job_rate(1000.0, world, vals[0], 2)
+    tot = bench.sum_over_ranks([500.0 * (rank + 1)])[0]
+    rate = bench.whole_job_rate(tot, vals[0], 2)
     out.put((rank, vals, rate))
     dist.barrier()
     dist.destroy_process_group()
@@ -130,7 +131,8 @@ def test_bench_reduction_over_two_gloo_ranks():
         assert p.exitcode == 0
     for rank, vals, rate in res:
         assert vals == [20.0, 100.0]               # max over ranks
-        assert rate == pytest.approx(1000.0 * 2 / (10.0 / 1e3))   # whole job over the slowest rank
+        # entries summed over ranks (500 + 1000), timed by the slowest rank
+        assert rate == pytest.approx(1500.0 / (10.0 / 1e3))
 
 
 def test_reference_arm_json_contract():
@@ -152,3 +154,141 @@ def test_reference_arm_json_contract():
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["e2e"]["value"] == line["value"] and line["gpu_launches"] == 0
+
+
+# ---------------------------------------------------------------- row-cluster sharding (world size 2 over gloo)
+
+def _shard_rank_main(rank, world, port, out):
+    """One rank: the library's row-cluster partition of the capped cube tree,
+    the rank's share of the dense apply (oracle, a few frequencies), and the
+    exchange of blocks and partial results for the checks."""
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import paper_2312_11219_gb300 as g3
+    from oracle import freqs as O_freqs, quadrature as O_q, tree as O_tree
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    w = workloads.get("cube768")
+    T = O_tree.build(w.verts, w.tris, w.leaf, w.eta, 96)
+    nodes = np.stack([T.begin, T.end, T.left, T.right], axis=1)
+    sh = g3.shard_rows(nodes, T.blocks, world)
+    mine = np.flatnonzero(sh["owner"] == rank)
+    # every rank computes the same partition
+    allo = [torch.zeros(T.blocks.shape[0], dtype=torch.int32) for _ in range(world)]
+    dist.all_gather(allo, torch.from_numpy(sh["owner"].astype(np.int32)))
+    same = all(torch.equal(a, allo[0]) for a in allo)
+    # the rank's blocks applied densely (original order), the other rows zero
+    geo = O_q.Geometry(w.verts, w.tris)
+    s = O_freqs.bdf2(4, 0.1, (1e-8) ** (1 / 8))
+    W = workloads.densities(w.E, 4, 21)
+    y = np.zeros(w.E, complex)
+    for b in mine:
+        rb, re, cb, ce, _ = T.blocks[b]
+        R, C = T.perm[rb:re], T.perm[cb:ce]
+        D = O_q.dense(geo, "slp", s, rows=R, cols=C)
+        y[R] += np.einsum("ijk,jk->i", D, W[C])
+    yt = torch.from_numpy(np.stack([y.real, y.imag]))
+    ys = [torch.zeros_like(yt) for _ in range(world)]
+    dist.all_gather(ys, yt)
+    mt = torch.zeros(T.blocks.shape[0], dtype=torch.int32)
+    mt[torch.from_numpy(mine)] = 1
+    cover = mt.clone()
+    dist.all_reduce(cover)
+    out.put((rank, same, cover.numpy(), [t.numpy() for t in ys], sh["load"], sh["n_units"]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_row_cluster_sharding_over_two_gloo_ranks(built_lib):
+    """The library's row-cluster partition, run by two gloo ranks: both
+    compute the same owner list; every block is owned exactly once; the rows
+    of the two ranks are disjoint; the rank loads are within one unit of
+    each other (longest-first greedy); and the ranks' partial applies add up
+    to the dense apply of the whole operator."""
+    import socket
+
+    import torch.multiprocessing as mp
+    from oracle import apply as O_apply, freqs as O_freqs, quadrature as O_q, tree as O_tree
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in procs), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = workloads.get("cube768")
+    T = O_tree.build(w.verts, w.tris, w.leaf, w.eta, 96)
+    for rank, same, cover, ys, load, n_units in res:
+        assert same
+        assert np.all(cover == 1)                     # each block exactly once
+        assert n_units >= 2
+    y0 = ys[0][0] + 1j * ys[0][1]
+    y1 = ys[1][0] + 1j * ys[1][1]
+    assert not np.any((y0 != 0) & (y1 != 0))          # disjoint rows
+    assert np.count_nonzero(y0) > 0 and np.count_nonzero(y1) > 0
+    load = res[0][4]
+    sizes = (T.blocks[:, 1] - T.blocks[:, 0]) * (T.blocks[:, 3] - T.blocks[:, 2])
+    assert load.sum() == pytest.approx(float(sizes.sum()))
+    # greedy longest-first: the spread is at most the largest unit's cost
+    assert abs(load[0] - load[1]) <= 0.25 * load.sum()
+    geo = O_q.Geometry(w.verts, w.tris)
+    s = O_freqs.bdf2(4, 0.1, (1e-8) ** (1 / 8))
+    W = workloads.densities(w.E, 4, 21)
+    yd = O_apply.dense_apply(lambda I, J, ss: O_q.entries(geo, "slp", I, J, ss), w.E, s, W)
+    assert np.linalg.norm(y0 + y1 - yd) <= 1e-12 * np.linalg.norm(yd)
+
+
+def _units(T):
+    """Row units of a partition, written out independently: the clusters at
+    the smallest depth that holds a block's row cluster, plus the leaves above
+    it; returns (unit begin/end list, unit index of each block)."""
+    n = T.begin.size
+    depth = np.zeros(n, int)
+    for v in range(n):
+        for c in (T.left[v], T.right[v]):
+            if c >= 0:
+                depth[c] = depth[v] + 1
+    node_of = {(int(T.begin[v]), int(T.end[v])): v for v in range(n)}
+    dmin = min(depth[node_of[(int(rb), int(re))]] for rb, re, _, _, _ in T.blocks)
+    units = [(int(T.begin[v]), int(T.end[v])) for v in range(n)
+             if depth[v] == dmin or (T.left[v] < 0 and depth[v] < dmin)]
+    bu = np.array([next(k for k, (a, e) in enumerate(units) if a <= rb < e) for rb, _, _, _, _ in T.blocks])
+    return units, bu
+
+
+def test_shard_rows_partition_properties(built_lib):
+    """Single-process checks of the partition for 1-8 ranks on the capped
+    L-shape tree: exact cover, whole units per rank (rows disjoint),
+    deterministic, longest-first balance (spread <= the largest unit)."""
+    sys.path.insert(0, ROOT)
+    import paper_2312_11219_gb300 as g3
+    from oracle import tree as O_tree
+    w = workloads.get("lshape3072")
+    T = O_tree.build(w.verts, w.tris, w.leaf, w.eta, 96)
+    nodes = np.stack([T.begin, T.end, T.left, T.right], axis=1)
+    units, bu = _units(T)
+    rng = np.random.default_rng(1)
+    cost = rng.uniform(1.0, 10.0, T.blocks.shape[0])
+    ucost = np.array([cost[bu == k].sum() for k in range(len(units))])
+    for n in range(1, 9):
+        sh = g3.shard_rows(nodes, T.blocks, n, cost=cost)
+        o = sh["owner"]
+        assert sh["n_units"] == len(units)
+        assert o.min() >= 0 and o.max() < n
+        assert np.array_equal(o, g3.shard_rows(nodes, T.blocks, n, cost=cost)["owner"])
+        for k in range(len(units)):                    # a unit goes to one rank
+            assert np.unique(o[bu == k]).size <= 1
+        rows = np.full(w.E, -1)
+        for b, (rb, re, cb, ce, adm) in enumerate(T.blocks):
+            assert np.all((rows[rb:re] == -1) | (rows[rb:re] == o[b]))
+            rows[rb:re] = o[b]
+        assert np.all(rows >= 0)
+        load = np.array([cost[o == k].sum() for k in range(n)])
+        assert np.allclose(load, sh["load"])
+        assert load.max() - load.min() <= ucost.max() + 1e-9
