@@ -425,6 +425,7 @@ g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, in
     s->leaf = t->leaf;
     s->max_block = t->max_block;
     s->eta = t->eta;
+    s->subset = true;
     s->verts = t->verts;
     s->tris = t->tris;
     s->perm = t->perm;
@@ -594,7 +595,7 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
         }
     }
     for (int p = 0; p < t->ne; ++p)
-        if (diag_base[p] < 0) {
+        if (diag_base[p] < 0 && !t->subset) {  // (a rank's subset holds only its rows' diagonal blocks)
             delete nf;
             return fail(G3_EINVAL, "assemble_near: element %d has no diagonal near block", p);
         }

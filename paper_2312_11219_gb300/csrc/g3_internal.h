@@ -224,6 +224,7 @@ struct g3_tree {
     g3_ctx* ctx = nullptr;
     int ne = 0, nv = 0, leaf = 0;
     int max_block = 0;             // cap of the larger side of a far block (0 = none)
+    bool subset = false;           // a rank's share of another tree's blocks (g3_tree_subset)
     double eta = 0;
     std::vector<double> verts;
     std::vector<int32_t> tris;

@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPai
 
 // Self entries of the near field, float64: one thread per (element p, unique
 // frequency k); the entry (p, p) of the diagonal leaf block sits at
-// diag_base[p] + k * diag_mn[p].
+// diag_base[p] + k * diag_mn[p] (diag_base[p] < 0: not in this tree's blocks).
 template <int KER, class T>
 __global__ void k_near_self(GeomD gd, const double2* __restrict__ sd, int E, int Ku,
                             const long long* __restrict__ diag_base, const int* __restrict__ diag_mn,
@@ -524,6 +524,7 @@ __global__ void k_near_self(GeomD gd, const double2* __restrict__ sd, int E, int
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)E * Ku) return;
     const int p = (int)(idx % E), k = (int)(idx / E);
+    if (diag_base[p] < 0) return;  // the diagonal block belongs to another rank's subset
     Cx<T> v{0, 0};
     if (KER == G3_SLP) {
         double2 s = sd[k];
