@@ -535,7 +535,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                               "size (8 strata); plain = float64, one block per launch; ours = the timed "
                               "configuration (mixed precision, one persistent launch, predictor)"}
     # what the predictor gains: the same compression without it, and with
-    # queue order + pool size only (one step each, after the timed region)
+    # queue order + pool size only (one step each, after the timed region);
+    # and the first compression on a fresh context (no pool size learned from
+    # earlier compressions yet), with the plain estimate and the predictor's
     learned = None
     if net is not None and world == 1:
         ab = {}
@@ -544,7 +546,33 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
             ab[label] = {"aca_ms": r["aca_ms"], "crosses": r["crosses"], "factor_bytes": r["factor_bytes"],
                          "spilled_blocks": sum(st["spilled_blocks"] for st in r["stats"].values()),
                          "pool_regrows": sum(st["pool_regrows"] for st in r["stats"].values())}
-        learned = {"mlp_use": args.mlp_use, "training": train_info, "ab": ab}
+        fresh = {}
+        for label, (m, u) in {"plain_estimate": (None, 0), "predicted_pool": (net, 2)}.items():
+            c2 = g3.Context(local_rank, stream.cuda_stream)
+            T2 = g3.build_cluster_tree(c2, ws[0].verts, ws[0].tris, ws[0].leaf, ws[0].eta, max_block=ws[0].max_block)
+            F2 = g3.freqs_from_spec(c2, ws[0].freq)
+            tot = {"aca_ms": 0.0, "spilled_blocks": 0, "pool_regrows": 0}
+            for ker in kernels:
+                st2 = g3.aca3_compress(c2, T2, F2, ker, scheme=scheme, prec=prec, eps3=ws[0].eps3, mlp=m,
+                                       mlp_use=u).stats()
+                tot["aca_ms"] += st2["ms"]
+                tot["spilled_blocks"] += st2["spilled_blocks"]
+                tot["pool_regrows"] += st2["pool_regrows"]
+            fresh[label] = tot
+            del T2, F2, c2
+        learned = {"mlp_use": args.mlp_use, "training": train_info, "ab": ab, "fresh_context": fresh}
+    # the pivot estimate of eq. (index) against the dense expansion (single
+    # layer, collocation; the double layer keeps the dense expansion)
+    pivot_ab = None
+    if world == 1 and not batch and "slp" in kernels and scheme == "colloc7":
+        trees, freqs, _, _, _ = keep["slp"]
+        shape = {k: tune["slp"][k] for k in ("threads", "dense_face_max")} if "slp" in tune else {}
+        pivot_ab = {}
+        for label, pi in (("dense_expansion", 0), ("eq_index", 1)):
+            stp = g3.aca3_compress(ctx, trees[0], freqs[0], "slp", scheme=scheme, prec=prec, eps3=ws[0].eps3, mlp=net,
+                                   mlp_use=args.mlp_use, pivot_index=pi, **shape).stats()
+            pivot_ab[label] = {"aca_ms": stp["ms"], "crosses": stp["crosses"], "entries": stp["entries"],
+                               "factor_bytes": stp["factor_bytes"]}
     if rank != 0:
         return None
     ms_step = t_max / args.steps
@@ -601,6 +629,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "clocks": clk.summary(),
         "peaks_source": peaks["source"],
         "learned": learned,
+        "pivot_index_ab": pivot_ab,
         "autotune": tune or None,
         "compression_entries_per_s": aca_eps,
     }

@@ -106,8 +106,8 @@ typedef struct {
     int face_rank_max;    /* cap of a face ACA's rank (0 = 48; max 64)                     */
     int unbatched;        /* 1 = one block per launch sequence, host loop (plain baseline) */
     int ctas_per_sm;      /* persistent CTAs per SM (0 = from the occupancy calculator)    */
-    int threads;          /* threads per CTA of the low-rank-face launch: 128, 256 or
-                             512 (128 and 512: G3_MIXED only); 0 = 256                   */
+    int threads;          /* threads per CTA of the low-rank-face launch: 128, 256, 384 or
+                             512 (all but 256: G3_MIXED only); 0 = 256                    */
     int no_recompress;    /* 1 = keep raw ACA faces (no QR+SVD)                            */
     int order_by_cost;    /* 1 (default when 0 is given: 1) = longest-first queue order    */
     const int32_t* k1;    /* optional host array [n_far]: first frequency per block
@@ -137,6 +137,14 @@ typedef struct {
                                  scale * eps_face * ||C^(l-1)||_F / sqrt(Ku) (0 = 1)     */
     double trunc_floor_scale; /* G3_MIXED: the recompression drops singular values below
                                  scale * eps_face * ||C^(l-1)||_F / sqrt(Ku) (0 = 1)     */
+    int pivot_index;      /* 1 = pivot of each low-rank face by the estimate of eq. (index)
+                             (Section 4, last implementation remark): the row
+                             i = argmax_i sum_b |U'[i,b]| ||V'[:,b]|| of the recompressed
+                             factors (the paper's sum_k |u_ik sigma_k|), then the largest
+                             entry of row i, j = argmax_j |(U' V'^H)[i,j]|; O((M + N) r)
+                             instead of the dense expansion's O(M N r).  Single layer
+                             only: G3_DLP keeps the dense expansion, the paper's
+                             fallback.  0 (default) = dense expansion                   */
 } g3_opts;
 
 /* Statistics of one compression. */
@@ -333,7 +341,7 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
 
 /* Autotuner of the compression's launch shape (no counterpart in the paper).
  * Times aca3_compress on (t, f) for each candidate -- threads per CTA of the
- * low-rank launch 128, 256 or 512 (128, 512: G3_MIXED only) and the dense-face
+ * low-rank launch 128, 256, 384 or 512 (all but 256: G3_MIXED only) and the dense-face
  * threshold M_b N_b <= 24^2, 48^2 or 64^2 -- and writes the fastest into
  * opts->threads and opts->dense_face_max (the other fields of *opts are used
  * as given).  The choice is cached in ctx by (K_u bucket, largest far-block
@@ -485,8 +493,8 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
  * default) that lookup also loads the module and so reserves the 32 MiB
  * then.  Make that first call before any stream capture, and do not call
  * after cudaDeviceReset (the kept address would be stale).  Problems needing more
- * scratch than 32 MiB (2 Ku M + M complex values and 2 per face rank of the
- * low-rank far field) return G3_EINVAL.  All calls
+ * scratch than 32 MiB (2 Ku M + M complex values, each part rounded up to
+ * 256 bytes) return G3_EINVAL.  All calls
  * share the array: calls whose work overlaps on the GPU (other streams,
  * other threads) race and must be serialised by the caller. */
 g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,

@@ -13,7 +13,9 @@ remarks of the same section, in complex128:
             eps_face = eps3 / 100, "eps = 100 eps_ACA") and recompressed by
             QR of both factors + SVD of R_U R_V^H (first remark)
     pivot:  (i_l, j_l) = argmax |H_l[i, j]| over the dense expansion of the
-            low-rank face (last remark: "expanding to the dense block")
+            low-rank face (last remark: "expanding to the dense block"), or
+            optionally the cheaper estimate of eq. (index) from the
+            recompressed factors
     fiber:  f_l[k] = (ENTRY(i_l, j_l, k) - C^(l-1)[i_l, j_l, k]) / H_l[i_l, j_l]
     norm:   ||C^(l)||_F^2 by eq. (norm), i.e. the double sum over
             <H_d, H_d'>_F <f_d, f_d'>, accumulated over the new terms
@@ -263,12 +265,35 @@ class Result:
 DENSE_MAX = 48 * 48
 
 
+def index_pivot(U: np.ndarray, V: np.ndarray) -> tuple[int, int]:
+    """Pivot estimate of eq. (index) (Section 4, last implementation remark)
+    for a recompressed face U V^H with orthonormal columns in V and U = (u_k
+    sigma_k): the row i = argmax_i sum_k |u_ik sigma_k| bounds the entries of
+    row i.  Written for any factor pair as i = argmax_i sum_k |U_ik| ||V_:k||
+    (the same numbers when V has orthonormal columns).  The column is then
+    found "the analogous way" in that row: j = argmax_j |(U V^H)[i, j]|, the
+    largest entry of the selected row (O(N r), like the row estimate's
+    O(M r)); ties -> smallest index.  (Choosing j by the independent column
+    bound sum_k ||U_:k|| |V_jk| can pair a large row with a large column whose
+    common entry vanishes, e.g. on block-diagonal faces, and the fiber
+    division then blows up.)"""
+    cv = np.linalg.norm(V, axis=0)
+    i = int(np.argmax(np.abs(U) @ cv))
+    row = U[i, :] @ V.conj().T
+    j = int(np.argmax(row.real * row.real + row.imag * row.imag))
+    return i, j
+
+
 def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
          s_abs: np.ndarray | None = None, max_face_rank: int | None = None,
-         k1: int = 0, dense_max: int = DENSE_MAX, sample_check: bool = True) -> Result:
+         k1: int = 0, dense_max: int = DENSE_MAX, sample_check: bool = True,
+         pivot: str = "dense") -> Result:
     """Algorithm 1 on one block (see module docstring for the readings).
     Blocks with M N <= dense_max use exact dense faces (dense_max < 0: never);
-    sample_check confirms each stop on fixed sample entries."""
+    sample_check confirms each stop on fixed sample entries.  pivot = "dense":
+    the largest entry of the face's dense expansion (the variant of all the
+    paper's results); "index": the estimate of eq. (index) on low-rank faces
+    (dense faces keep their exact largest entry)."""
     if eps_face is None:
         eps_face = eps3 / 100.0
     M, N, Ku = op.M, op.N, op.Ku
@@ -328,9 +353,12 @@ def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
         if not dense:
             U, V = recompress(U, V, eps_face)
         H = U @ V.conj().T
-        mag = H.real * H.real + H.imag * H.imag
-        flat = int(np.argmax(mag))
-        ip, jp = divmod(flat, N)
+        if pivot == "index" and not dense:
+            ip, jp = index_pivot(U, V)
+        else:
+            mag = H.real * H.real + H.imag * H.imag
+            flat = int(np.argmax(mag))
+            ip, jp = divmod(flat, N)
         fib = op.fiber(ip, jp)
         for c, Hd in zip(crosses, faces):
             fib = fib - Hd[ip, jp] * c.f

@@ -27,7 +27,7 @@ CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_a
               "g3_probe.cu", "g3_mlp.cu"]
 # the compression-kernel instantiations of each kernel kind are compiled in
 # this many parts (-DG3_ACA_PART=0..), one nvcc process each
-ACA_PARTS = {"g3_aca_slp.cu": 3, "g3_aca_dlp.cu": 3, "g3_aca_sep.cu": 3, "g3_aca_gal.cu": 3}
+ACA_PARTS = {"g3_aca_slp.cu": 4, "g3_aca_dlp.cu": 4, "g3_aca_sep.cu": 4, "g3_aca_gal.cu": 4}
 CPP_SOURCES = ["g3_tree.cpp"]
 
 

@@ -12,6 +12,7 @@ namespace g3 {
     G3_ACA_EXTERN(KER, float, 256, true)     \
     G3_ACA_EXTERN(KER, float, 128, false)    \
     G3_ACA_EXTERN(KER, float, 512, false)    \
+    G3_ACA_EXTERN(KER, float, 384, false)    \
     G3_ACA_EXTERN(KER, double, 256, false)   \
     G3_ACA_EXTERN(KER, double, 256, true)
 G3_ACA_EXTERN_KIND(G3_SLP)
@@ -225,14 +226,16 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
     const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
-    // low-rank class: 128, 256 or 512 threads per CTA (float32 path); more
+    // low-rank class: 128, 256, 384 or 512 threads per CTA (float32 path); more
     // threads shorten each block, which matters for the largest blocks at the
     // end, fewer keep more blocks in flight per SM
-    const int nt_low = (sizeof(T) == 4 && (o.threads == 128 || o.threads == 512)) ? o.threads : NT;
+    const int nt_low = (sizeof(T) == 4 && (o.threads == 128 || o.threads == 384 || o.threads == 512)) ? o.threads
+                                                                                                         : NT;
     int per_low = o.ctas_per_sm;
     if (per_low <= 0) {
         if constexpr (sizeof(T) == 4)
             per_low = nt_low == 512   ? occupancy_kind<T, 512, false>(kernel, smem)
+                      : nt_low == 384 ? occupancy_kind<T, 384, false>(kernel, smem)
                       : nt_low == 128 ? occupancy_kind<T, 128, false>(kernel, smem)
                                       : occupancy_kind<T, NT, false>(kernel, smem);
         else
@@ -321,6 +324,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         A.RF = RF;
         A.dense_max = dense_max;
         A.sample_check = o.literal_stop ? 0 : 1;
+        A.pivot_index = o.pivot_index;
         A.eps3 = eps3;
         A.eps_face = eps_face;
         A.face_floor = sizeof(T) == 4 ? eps_face * (o.face_floor_scale > 0 ? o.face_floor_scale : 1.0) : 0.0;
@@ -359,6 +363,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
                     st = launch_kind<T, NT, true>(ctx, kernel, B, g, smem);
                 else if constexpr (sizeof(T) == 4)
                     st = nt_low == 512   ? launch_kind<T, 512, false>(ctx, kernel, B, g, smem)
+                         : nt_low == 384 ? launch_kind<T, 384, false>(ctx, kernel, B, g, smem)
                          : nt_low == 128 ? launch_kind<T, 128, false>(ctx, kernel, B, g, smem)
                                          : launch_kind<T, NT, false>(ctx, kernel, B, g, smem);
                 else

@@ -6,12 +6,17 @@
 // Algorithm 1 on the block restricted to the unique frequencies:
 //   face    partial-pivot ACA of the residual face at k_l (eps_face), with the
 //           residual of earlier crosses subtracted row/column-wise;
-//   recomp  Cholesky-QR of both ACA factors (float64, column-scaled Gram
-//           matrices), one-sided Jacobi SVD of the r x r core R_U R_V^H,
-//           truncation sigma_i < eps_face sigma_1 (Section 4, first remark);
+//   recomp  Cholesky-QR of both ACA factors (float64 Cholesky of column-scaled
+//           Gram matrices), then the r x r core R_U R_V^H is factored: float64
+//           (T = double) by a one-sided Jacobi SVD truncated at
+//           sigma_i < eps_face sigma_1, float32 (T = float) by a column-pivoted
+//           QR stopped when the largest remaining column norm falls below the
+//           same threshold (Section 4, second implementation remark);
 //   pivot   argmax |H_l[i, j]| over the dense expansion of U' V'^H, tiled
 //           through shared memory, ties to the smallest row-major index
-//           (Section 4, last remark);
+//           (Section 4, last remark), or optionally (single layer) the
+//           row of eq. (index) from the factors and the largest entry of
+//           that row;
 //   fiber   f_l[k] = (ENTRY(i_l, j_l, k) - sum_p H_p[i_l, j_l] f_p[k]) / H_l[i_l, j_l]
 //           with the residual in float64;
 //   norm    eq. (norm): ||C^(l)||^2 += 2 Re sum_d <H_l, H_d><f_l, f_d> + ||H_l||^2 ||f_l||^2,
@@ -23,7 +28,10 @@
 //
 // Precision: T = float (mixed) evaluates entries and face arithmetic in
 // float32 and stores complex64 factors; T = double does everything in float64.
-// Recompression, fiber residuals and norms are float64 in both.
+// In both, the fiber residuals, the Cholesky factors of the recompression,
+// the sums over crosses of eq. (norm) and ||C^(l)|| are float64; with
+// T = float the Gram products, the core factorisation and the back
+// substitution of the recompression are float32.
 //
 // No CTA waits on another: the only inter-CTA communication is the atomic
 // queue counter and the atomic pool allocator.
@@ -91,6 +99,7 @@ struct AcaArgs {
     int Cmax, RF;
     int dense_max;           // blocks with M N <= dense_max use exact dense faces
     int sample_check;        // confirm each stop on fixed sample entries
+    int pivot_index;         // single layer: pivot of low-rank faces by eq. (index)
     double eps3, eps_face;
     double face_floor;       // absolute floor factor of the face tests (0 = none)
     double trunc_floor;      // absolute floor factor of the recompression truncation (0 = none)
@@ -199,6 +208,7 @@ struct BlockSh {
     double sig[RF_MAX];
     double dU[RF_MAX], dV[RF_MAX];
     double rdU[RF_MAX], rdV[RF_MAX];  // 1 / diagonal of the Cholesky factors
+    T cnV[RF_MAX];                    // column norms of V' (pivot of eq. (index))
     T tdU[RF_MAX], tdV[RF_MAX];       // dU, dV and rdU, rdV in the working precision
     T trdU[RF_MAX], trdV[RF_MAX];
     double fsn2;             // ||S_m||_F^2 of the face approximant (recursive)
@@ -1244,7 +1254,7 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
 template <class T, int NT>
 __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, const Cx<T>* Vn, int rn,
                            Cx<T>* sh) {
-    constexpr int QMAX = 32 * RF_MAX / NT;
+    constexpr int QMAX = (32 * RF_MAX + NT - 1) / NT;
     constexpr int RC = NORM_RC<T>;  // rows staged per pass (fewer barriers per column chunk)
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N, nc = S.ncross;
@@ -1607,9 +1617,10 @@ __device__ void dense_block(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, 
 // DENSE selects the block class this launch serves (dense faces or low-rank
 // faces); the two classes run as two persistent launches with their own queues.
 // resident CTAs per SM the register allocation is sized for: 128 registers
-// a thread at 128 threads (4 CTAs), 256 (2 CTAs) and 512 (1 CTA)
+// a thread at 128 threads (4 CTAs), 256 (2 CTAs) and 512 (1 CTA); 384
+// threads keep 2 CTAs (80 registers a thread, 24 warps per SM)
 template <int NT>
-constexpr int aca_min_ctas() { return NT <= 128 ? 4 : (NT <= 256 ? 2 : 1); }
+constexpr int aca_min_ctas() { return NT <= 128 ? 4 : (NT <= 384 ? 2 : 1); }
 
 template <int KER, class T, int NT, bool DENSE>
 __global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3(const AcaArgs<T> P) {
@@ -1792,7 +1803,56 @@ __global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3(const AcaArgs<T
             __syncthreads();
             lap(2);
             // ---------------- pivot: argmax |U' V'^H| ----------------
-            {
+            if (KER != G3_DLP && A.pivot_index) {
+                // the estimate of eq. (index) (Section 4, last remark): the row
+                // i = argmax_i sum_b |U'[i, b]| ||V'[:, b]|| (for U' = U Sigma and
+                // orthonormal V' the paper's sum_k |u_ik sigma_k|, a bound on the
+                // entries of row i), then the column found in that row: j =
+                // argmax_j |(U' V'^H)[i, j]|, O((M + N) r) instead of the dense
+                // expansion's O(M N r); ties to the smallest index.  The double
+                // layer keeps the dense expansion, as the paper does.
+                for (int b = wid; b < rn; b += NT / 32) {
+                    const Cx<T>* col = Vn + (long long)b * N;
+                    T s2 = 0;
+                    for (int i = lane; i < N; i += 32) s2 += cabs2(ldcx(col + i));
+                    s2 = warp_sum(s2);
+                    if (lane == 0) S.cnV[b] = sqrt(s2);
+                }
+                __syncthreads();
+                ArgMaxT<T> bi = amax_none<T>();
+                for (int i = tid; i < M; i += NT) {
+                    T sc = 0;
+                    for (int b = 0; b < rn; ++b) sc += sqrt(cabs2(ldcx(Un + (long long)b * M + i))) * S.cnV[b];
+                    bi = amax_better(bi, ArgMaxT<T>{sc, i});
+                }
+                bi = block_argmax<NT>(bi, S.am);
+                const int ir = (bi.v >= 0 && bi.i >= 0 && bi.i < M) ? bi.i : 0;
+                // row ir of the face: U'[ir, :] (r values, one broadcast load each)
+                for (int b = tid; b < rn; b += NT) S.fk[b] = Un[(long long)b * M + ir];
+                __syncthreads();
+                ArgMaxT<T> bj = amax_none<T>();
+                for (int j = tid; j < N; j += NT) {
+                    Cx<T> h{0, 0};
+                    for (int b = 0; b < rn; ++b) cfmac(h, S.fk[b], ldcx(Vn + (long long)b * N + j));
+                    bj = amax_better(bj, ArgMaxT<T>{cabs2(h), j});
+                }
+                bj = block_argmax<NT>(bj, S.am);
+                if (tid == 0) {
+                    if (bi.v < 0 || bj.v < 0 || bi.i < 0 || bi.i >= M || bj.i < 0 || bj.i >= N) {
+                        S.ip = 0;
+                        S.jp = 0;
+                        S.hpiv = Cx<double>{0.0, 0.0};
+                    } else {
+                        S.ip = bi.i;
+                        S.jp = bj.i;
+                        Cx<T> hw{0, 0};
+                        for (int b = 0; b < rn; ++b) cfmac(hw, Un[(long long)b * M + S.ip], Vn[(long long)b * N + S.jp]);
+                        Cx<double> h = ccast<double>(hw);
+                        if (!isfinite(h.x) || !isfinite(h.y)) h = Cx<double>{0.0, 0.0};
+                        S.hpiv = h;
+                    }
+                }
+            } else {
                 constexpr int TM = sizeof(T) == 4 ? 64 : 32;
                 constexpr int TN = TM;
                 constexpr int RM = TM * TN / NT >= 16 ? 4 : 2;  // micro-tile edge

@@ -9,7 +9,7 @@ namespace g3 {
     template g3_status launch_aca_t<G3_GAL_SLP, T, NT, DENSE>(g3_ctx*, AcaArgs<T>&, int, size_t);        \
     template int occupancy<G3_GAL_SLP, T, NT, DENSE>(size_t);
 
-// compiled in three parts (G3_ACA_PART = 0, 1, 2) by separate compiler processes
+// compiled in four parts (G3_ACA_PART = 0, 1, 2, 3) by separate compiler processes
 #if !defined(G3_ACA_PART) || G3_ACA_PART == 0
 G3_ACA_INST(float, 256, false)
 G3_ACA_INST(float, 128, false)
@@ -21,6 +21,9 @@ G3_ACA_INST(float, 512, false)
 #if !defined(G3_ACA_PART) || G3_ACA_PART == 2
 G3_ACA_INST(double, 256, false)
 G3_ACA_INST(double, 256, true)
+#endif
+#if !defined(G3_ACA_PART) || G3_ACA_PART == 3
+G3_ACA_INST(float, 384, false)
 #endif
 
 }  // namespace g3

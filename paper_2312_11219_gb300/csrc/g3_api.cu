@@ -730,8 +730,8 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     G3_CHECK(eps3 > 0 && eps3 < 1, "aca3_compress: eps3 = %g outside (0, 1)", eps3);
     g3_opts o = defaults(opts);
     G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress: face_rank_max = %d outside [0, 64]", o.face_rank_max);
-    G3_CHECK(o.threads == 0 || o.threads == 128 || o.threads == 256 || o.threads == 512,
-             "aca3_compress: threads must be 0, 128, 256 or 512");
+    G3_CHECK(o.threads == 0 || o.threads == 128 || o.threads == 256 || o.threads == 384 || o.threads == 512,
+             "aca3_compress: threads must be 0, 128, 256, 384 or 512");
     G3_CHECK(o.mlp_use >= 0 && o.mlp_use <= 7, "aca3_compress: mlp_use = %d outside [0, 7]", o.mlp_use);
     G3_TRY(use_device(ctx));
     g3_factors* fa = new (std::nothrow) g3_factors();
@@ -775,11 +775,11 @@ g3_status g3_autotune(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kerne
         return G3_OK;
     }
     G3_TRY(use_device(ctx));
-    const int threads[3] = {256, 128, 512};
+    const int threads[4] = {256, 384, 128, 512};
     const int dmax[3] = {24 * 24, 48 * 48, 64 * 64};
     double best = -1.0;
     int bt = 256, bd = 48 * 48;
-    for (int a = 0; a < (prec == G3_MIXED ? 3 : 1); ++a)
+    for (int a = 0; a < (prec == G3_MIXED ? 4 : 1); ++a)
         for (int b = 0; b < 3; ++b) {
             g3_opts o = *opts;
             o.threads = threads[a];
@@ -818,8 +818,8 @@ g3_status aca3_compress_batch(g3_ctx* ctx, const g3_tree* const* trees, const g3
     G3_CHECK(o.k1 == nullptr && o.cost == nullptr, "aca3_compress_batch: opts->k1 and opts->cost are per mesh; not accepted");
     G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress_batch: face_rank_max = %d outside [0, 64]",
              o.face_rank_max);
-    G3_CHECK(o.threads == 0 || o.threads == 128 || o.threads == 256 || o.threads == 512,
-             "aca3_compress_batch: threads must be 0, 128, 256 or 512");
+    G3_CHECK(o.threads == 0 || o.threads == 128 || o.threads == 256 || o.threads == 384 || o.threads == 512,
+             "aca3_compress_batch: threads must be 0, 128, 256, 384 or 512");
     G3_CHECK(o.mlp_use >= 0 && o.mlp_use <= 7, "aca3_compress_batch: mlp_use = %d outside [0, 7]", o.mlp_use);
     G3_CHECK(!o.unbatched, "aca3_compress_batch: unbatched is not accepted");
     G3_TRY(use_device(ctx));

@@ -122,32 +122,40 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
     }
 }
 
-// Far field, blocks with low-rank faces, in two phases over work items of
-// one block and a group of up to PG crosses (ab: the group's V^H x and
-// V^H zc, 2 r_p complex values per cross, from ab_base on):
-//   phase 1, item (block, group, column tile of NT):
-//     x_p[j] = sum_k f_p[k] w_k[j], zc_p[j] = sum_k f_p[k] conj(w_k'[j]) for the
-//     tile's columns (thread j; W read once per group and tile), kept in
-//     shared memory; then one warp per (p, t) forms the tile's part of
-//     a_p[t] = V_p[:, t]^H x_p and b_p[t] = V_p[:, t]^H zc_p (lanes over the
-//     columns, coalesced reads of V, one warp reduction per pair) and adds it
-//     to ab;
-//   phase 2, item (block, group): y += U_p a_p + conj(U_p b_p).
-// Each factor is read once; the many small items keep the SMs busy.
-template <class T, int NT, int PG>
-__global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
+// Far field, blocks with low-rank faces: one CTA per work item (block, group
+// of PG crosses), every factor read once from HBM and every item complete in
+// itself (no second pass, no global scratch):
+//   1. x_p[j] = sum_k f_p[k] w_k[j], zc_p[j] = sum_k f_p[k] conj(w_k'[j]) for
+//      the group's crosses and a chunk of the block's columns (the fibers in
+//      shared memory, W read from L2; TPC threads per column, each with
+//      PG / TPC crosses);
+//   2. a_p[t] += V_p[:, t]^H x_p, b_p[t] += V_p[:, t]^H zc_p over the chunk
+//      (one warp per (p, t) pair, two pairs at a time, lanes over the
+//      columns), the sums kept in shared memory;
+//   3. y[i] += sum_p U_p[i, :] a_p + conj(U_p[i, :] b_p) (TPR threads per row
+//      splitting the pairs, lanes over rows, one atomic add per row and part).
+// x formation is N K_u complex multiply-adds per cross, the same order of
+// work per byte as the HBM stream of the factors; grouping PG crosses lets
+// each W value serve PG crosses.
+template <class T, int NT, int PG, int TPC>
+__global__ void __launch_bounds__(NT) k_far_lr(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
                                                const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
                                                const int4* __restrict__ items, int Cmax, int Ku, int E,
                                                const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
-                                               Cx<T>* __restrict__ ab) {
+                                               Cx<T>* __restrict__ y) {
+    constexpr int NC = NT / TPC;    // columns per chunk
+    constexpr int PPT = PG / TPC;   // crosses per thread in phase 1
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);  // [PG][Ku]
-    Cx<T>* xs = fg + PG * Ku;                         // [PG][NT] x_p of the tile
-    Cx<T>* zs = xs + PG * NT;                         // [PG][NT] zc_p of the tile
+    Cx<T>* xs = fg + PG * Ku;                         // [PG][NC]
+    Cx<T>* zs = xs + PG * NC;                         // [PG][NC]
+    Cx<T>* ab = zs + PG * NC;                         // [2][sum of ranks] a, then b
     __shared__ CrossRec crs[PG];
-    __shared__ int pre[PG + 1];  // prefix sums of the ranks
-    const int4 it = items[blockIdx.x];  // block, group, column tile, a/b offset
-    const int blk = it.x, g0 = it.y * PG, jt = it.z;
+    __shared__ int pre[PG + 1];
+    __shared__ int pof[PG * RF_TS];                   // cross of each flattened pair
+    const int4 it = items[blockIdx.x];
+    const int blk = it.x, g0 = it.y * PG;
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
     const int np = min(PG, r3[blk] - g0);
@@ -160,193 +168,244 @@ __global__ void __launch_bounds__(NT) k_far_vx(const Cx<T>* __restrict__ pool, c
     }
     for (int e = tid; e < PG * Ku; e += NT) {
         const int p = e / Ku, k = e - p * Ku;
-        Cx<T> v{0, 0};
-        if (p < np) v = ldcx(pool + crs[p].off + (long long)crs[p].r * (M + N) + k);
-        fg[e] = v;
-    }
-    __syncthreads();
-    const int j0 = jt * NT, jn = min(NT, N - j0);
-    {
-        const int j = j0 + tid;
-        Cx<T> x[PG], z[PG];
-#pragma unroll
-        for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
-        if (tid < jn) {
-            const Cx<T>* wf = Wf + br.cb + j;
-            const Cx<T>* wc = Wc + br.cb + j;
-#pragma unroll 4
-            for (int k = 0; k < Ku; ++k) {
-                const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
-#pragma unroll
-                for (int p = 0; p < PG; ++p) {
-                    const Cx<T> f = fg[p * Ku + k];
-                    cfma(x[p], f, a);
-                    cfmac(z[p], f, b);
-                }
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < PG; ++p) {
-            xs[p * NT + tid] = x[p];
-            zs[p * NT + tid] = z[p];
-        }
+        fg[e] = p < np ? ldcx(pool + crs[p].off + (long long)crs[p].r * (M + N) + k) : Cx<T>{0, 0};
     }
     __syncthreads();
     const int npt = pre[PG];
-    for (int q = warp; q < npt; q += NT / 32) {
+    for (int q = tid; q < npt; q += NT) {
         int p = 0;
         while (pre[p + 1] <= q) ++p;
-        const int t = q - pre[p];
-        const Cx<T>* V = pool + crs[p].off + (long long)crs[p].r * M + (long long)t * N + j0;
-        const Cx<T>* xp = xs + p * NT;
-        const Cx<T>* zp = zs + p * NT;
-        Cx<T> pa{0, 0}, pb{0, 0};
-        for (int jj = lane; jj < jn; jj += 32) {
-            const Cx<T> v = ldcx(V + jj);
-            cfmac(pa, xp[jj], v);  // conj(v) x
-            cfmac(pb, zp[jj], v);  // conj(v) zc
-        }
-        pa.x = warp_sum(pa.x);
-        pa.y = warp_sum(pa.y);
-        pb.x = warp_sum(pb.x);
-        pb.y = warp_sum(pb.y);
-        if (lane == 0) {
-            Cx<T>* o = ab + it.w + 2 * (pre[p] + t);
-            atomicAdd(&o[0].x, pa.x);
-            atomicAdd(&o[0].y, pa.y);
-            atomicAdd(&o[1].x, pb.x);
-            atomicAdd(&o[1].y, pb.y);
-        }
+        pof[q] = p;
+        ab[q] = Cx<T>{0, 0};
+        ab[npt + q] = Cx<T>{0, 0};
     }
-}
-
-template <class T, int NT, int PG>
-__global__ void __launch_bounds__(NT) k_far_uy(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
-                                               const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
-                                               const int4* __restrict__ items, int Cmax,
-                                               const Cx<T>* __restrict__ ab, Cx<T>* __restrict__ y) {
-    __shared__ CrossRec crs[PG];
-    const int4 it = items[blockIdx.x];
-    const int blk = it.x, g0 = it.y * PG;
-    const BlockRange br = ranges[blk];
-    const int M = br.re - br.rb;
-    const int np = min(PG, r3[blk] - g0);
-    if (threadIdx.x < PG && threadIdx.x < np) crs[threadIdx.x] = rec[(size_t)blk * Cmax + g0 + threadIdx.x];
-    __syncthreads();
-    for (int i = threadIdx.x; i < M; i += NT) {
-        T vx = 0, vy = 0;
-        int o = it.w;
-        for (int p = 0; p < np; ++p) {
-            const int r = crs[p].r;
-            const Cx<T>* U = pool + crs[p].off;
-            Cx<T> s1{0, 0}, s2{0, 0};
-#pragma unroll 4
-            for (int t = 0; t < r; ++t) {
-                const Cx<T> u = ldcx(U + (long long)t * M + i);
-                cfma(s1, u, ldcx(ab + o + 2 * t));
-                cfma(s2, u, ldcx(ab + o + 2 * t + 1));
-            }
-            o += 2 * r;
-            vx += s1.x + s2.x;  // U a + conj(U b)
-            vy += s1.y - s2.y;
-        }
-        atomicAdd(&y[br.rb + i].x, vx);
-        atomicAdd(&y[br.rb + i].y, vy);
-    }
-}
-
-// Far field, blocks with dense faces (small blocks): one warp per block, no
-// block-wide barrier.  Crosses in groups of PG: the group's fibers are staged
-// in the warp's slice of shared memory; for each chunk of 32 columns, lane j
-// forms x_p[j] = sum_k f_p[k] w_k[j] and zc_p[j] = sum_k f_p[k] conj(w_k'[j])
-// for the group in one pass over W, and lane i then adds
-// sum_p (H_p x_p)[i] + conj((H_p zc_p)[i]) over the chunk for its rows.
-template <class T, int NW, int PG, int MQ>
-__global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __restrict__ pool,
-                                                               const CrossRec* __restrict__ rec,
-                                                               const int* __restrict__ r3,
-                                                               const BlockRange* __restrict__ ranges,
-                                                               const int* __restrict__ list, int n, int Cmax, int Ku,
-                                                               int E, const Cx<T>* __restrict__ Wf,
-                                                               const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = blockIdx.x * NW + warp;
-    if (bi >= n) return;  // the whole warp: no block-wide synchronisation below
-    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * (PG * Ku + 2 * PG * 32);
-    Cx<T>* xs = fg + PG * Ku;
-    Cx<T>* zs = xs + PG * 32;
-    const int blk = list[bi];
-    const BlockRange br = ranges[blk];
-    const int M = br.re - br.rb, N = br.ce - br.cb;
-    const int nc = r3[blk];
-    Cx<T> acc[MQ];
+    for (int c0 = 0; c0 < N; c0 += NC) {
+        const int jn = min(NC, N - c0);
+        // ---- 1. x_p, zc_p for the chunk ----
+        {
+            const int jl = tid % NC, h = tid / NC;   // column, part of the group
+            Cx<T> x[PPT], z[PPT];
 #pragma unroll
-    for (int q = 0; q < MQ; ++q) acc[q] = Cx<T>{0, 0};
-    for (int g0 = 0; g0 < nc; g0 += PG) {
-        const int np = min(PG, nc - g0);
-        __syncwarp();
-        for (int e = lane; e < PG * Ku; e += 32) {
-            const int p = e / Ku, k = e - p * Ku;
-            Cx<T> v{0, 0};
-            if (p < np) v = ldcx(pool + rec[(size_t)blk * Cmax + g0 + p].off + (long long)M * N + k);
-            fg[e] = v;
-        }
-        __syncwarp();
-        for (int j0 = 0; j0 < N; j0 += 32) {
-            const int j = j0 + lane;
-            Cx<T> x[PG], z[PG];
-#pragma unroll
-            for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
-            if (j < N) {
-                const Cx<T>* wf = Wf + br.cb + j;
-                const Cx<T>* wc = Wc + br.cb + j;
+            for (int u = 0; u < PPT; ++u) x[u] = z[u] = Cx<T>{0, 0};
+            if (jl < jn) {
+                const Cx<T>* wf = Wf + br.cb + c0 + jl;
+                const Cx<T>* wc = Wc + br.cb + c0 + jl;
+                const Cx<T>* f0 = fg + h * PPT * Ku;
 #pragma unroll 4
                 for (int k = 0; k < Ku; ++k) {
                     const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
 #pragma unroll
-                    for (int p = 0; p < PG; ++p) {
-                        const Cx<T> f = fg[p * Ku + k];
-                        cfma(x[p], f, a);
-                        cfmac(z[p], f, b);
+                    for (int u = 0; u < PPT; ++u) {
+                        const Cx<T> f = f0[u * Ku + k];
+                        cfma(x[u], f, a);
+                        cfmac(z[u], f, b);
                     }
                 }
             }
 #pragma unroll
-            for (int p = 0; p < PG; ++p) {
-                xs[p * 32 + lane] = x[p];
-                zs[p * 32 + lane] = z[p];
+            for (int u = 0; u < PPT; ++u) {
+                xs[(h * PPT + u) * NC + jl] = x[u];
+                zs[(h * PPT + u) * NC + jl] = z[u];
             }
-            __syncwarp();
-            const int jn = min(32, N - j0);
-            for (int p = 0; p < np; ++p) {
-                const Cx<T>* H = pool + rec[(size_t)blk * Cmax + g0 + p].off + (long long)j0 * M;
-#pragma unroll
-                for (int q = 0; q < MQ; ++q) {
-                    const int i = lane + 32 * q;
-                    if (i < M) {
-                        Cx<T> s1{0, 0}, s2{0, 0};
+        }
+        __syncthreads();
+        // ---- 2. a_p[t] += V_p[:, t]^H x_p, b_p[t] += V_p[:, t]^H zc_p ----
+        for (int q0 = warp * 2; q0 < npt; q0 += 2 * NW) {
+            const int q1 = q0 + 1 < npt ? q0 + 1 : -1;
+            const int p0 = pof[q0], p1 = q1 >= 0 ? pof[q1] : p0;
+            const Cx<T>* V0 = pool + crs[p0].off + (long long)crs[p0].r * M + (long long)(q0 - pre[p0]) * N + c0;
+            const Cx<T>* V1 = q1 >= 0 ? pool + crs[p1].off + (long long)crs[p1].r * M + (long long)(q1 - pre[p1]) * N + c0
+                                      : V0;
+            const Cx<T>* x0 = xs + p0 * NC;
+            const Cx<T>* z0 = zs + p0 * NC;
+            const Cx<T>* x1 = xs + p1 * NC;
+            const Cx<T>* z1 = zs + p1 * NC;
+            Cx<T> a0{0, 0}, b0{0, 0}, a1{0, 0}, b1{0, 0};
+#pragma unroll 4
+            for (int jj = lane; jj < jn; jj += 32) {
+                const Cx<T> v0 = ldcx(V0 + jj), v1 = ldcx(V1 + jj);
+                cfmac(a0, x0[jj], v0);  // conj(v) x
+                cfmac(b0, z0[jj], v0);
+                cfmac(a1, x1[jj], v1);
+                cfmac(b1, z1[jj], v1);
+            }
+            a0.x = warp_sum(a0.x);
+            a0.y = warp_sum(a0.y);
+            b0.x = warp_sum(b0.x);
+            b0.y = warp_sum(b0.y);
+            a1.x = warp_sum(a1.x);
+            a1.y = warp_sum(a1.y);
+            b1.x = warp_sum(b1.x);
+            b1.y = warp_sum(b1.y);
+            if (lane == 0) {
+                ab[q0].x += a0.x;
+                ab[q0].y += a0.y;
+                ab[npt + q0].x += b0.x;
+                ab[npt + q0].y += b0.y;
+                if (q1 >= 0) {
+                    ab[q1].x += a1.x;
+                    ab[q1].y += a1.y;
+                    ab[npt + q1].x += b1.x;
+                    ab[npt + q1].y += b1.y;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- 3. y += U a + conj(U b): TPR threads per row split the pairs ----
+    const int tpr = M <= NT / 4 ? 4 : (M <= NT / 2 ? 2 : 1);
+    const int rows = NT / tpr;
+    const int h = tid / rows, il = tid - h * rows;
+    for (int i0 = 0; i0 < M; i0 += rows) {
+        const int i = i0 + il;
+        if (i >= M) continue;
+        Cx<T> s1{0, 0}, s2{0, 0};
+        for (int p = 0; p < np; ++p) {
+            const Cx<T>* U = pool + crs[p].off + i;
+            const int r = crs[p].r;
+            const Cx<T>* av = ab + pre[p];
+            const Cx<T>* bv = ab + npt + pre[p];
 #pragma unroll 8
-                        for (int jj = 0; jj < jn; ++jj) {
-                            const Cx<T> h = ldcx(H + i + (long long)jj * M);
-                            cfma(s1, h, xs[p * 32 + jj]);
-                            cfma(s2, h, zs[p * 32 + jj]);
+            for (int t = h; t < r; t += tpr) {
+                const Cx<T> u = ldcx(U + (long long)t * M);
+                cfma(s1, u, av[t]);
+                cfma(s2, u, bv[t]);
+            }
+        }
+        atomicAdd(&y[br.rb + i].x, s1.x + s2.x);  // U a + conj(U b)
+        atomicAdd(&y[br.rb + i].y, s1.y - s2.y);
+    }
+}
+
+// Far field, blocks with dense faces (the small blocks, M N <= the
+// compression's dense-face threshold): one CTA per block streams the block's
+// faces H_p (M x N, column-major, contiguous per cross) from HBM, in chunks of
+// DCH crosses:
+//   1. the chunk's fibers to shared memory;
+//   2. x_p[j] = sum_k f_p[k] w_k[j], zc_p[j] = sum_k f_p[k] conj(w_k'[j])
+//      (TPC threads per column, W from L2), to shared memory;
+//   3. y[i] += sum_p sum_j H_p[i, j] x_p[j] + conj(H_p[i, j] zc_p[j]): thread
+//      (i, q) takes row i and every TPR-th column of the chunk's faces (for a
+//      fixed column the warp's rows are consecutive: coalesced), eight loads
+//      in flight;
+//   4. the TPR partial sums of a row are added in shared memory and the CTA
+//      adds y once per row.
+constexpr int DCH = 8;
+
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, 3) k_far_dense(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
+                                                  const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
+                                                  const int* __restrict__ list, int Cmax, int Ku, int E,
+                                                  const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
+                                                  Cx<T>* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int blk = list[blockIdx.x];
+    const BlockRange br = ranges[blk];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);  // [DCH][Ku]
+    Cx<T>* xs = fg + DCH * Ku;                        // [DCH][N]
+    Cx<T>* zs = xs + DCH * N;                         // [DCH][N]
+    Cx<T>* red = zs + DCH * N;                        // [NT] partial row sums
+    __shared__ long long offs[DCH];
+    const int tid = threadIdx.x;
+    const int nc = r3[blk];
+    const long long MN = (long long)M * N;
+    // phase 3 layout: TPR threads per row
+    const int tpr = max(1, min(NT / M, 32));
+    const int i = tid % M, q = tid / M;
+    const bool row_active = M <= NT ? q < tpr : tid < M;
+    Cx<T> s1{0, 0}, s2{0, 0};
+    // phase 2 layout: TPC threads per column, each with DCH / TPC crosses
+    const int tpc = N >= NT ? 1 : (N * 2 > NT ? 1 : (N * 4 > NT ? 2 : (N * 8 > NT ? 4 : 8)));
+    for (int c0 = 0; c0 < nc; c0 += DCH) {
+        const int np = min(DCH, nc - c0);
+        __syncthreads();  // the previous chunk is done with fg, xs, zs
+        if (tid < DCH) offs[tid] = tid < np ? rec[(size_t)blk * Cmax + c0 + tid].off : 0;
+        __syncthreads();
+        for (int e = tid; e < DCH * Ku; e += NT) {
+            const int p = e / Ku, k = e - p * Ku;
+            fg[e] = p < np ? ldcx(pool + offs[p] + MN + k) : Cx<T>{0, 0};
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < N; j0 += NT / tpc) {
+            const int jl = tid / tpc, h = tid - jl * tpc;
+            const int j = j0 + jl;
+            if (j < N) {
+                const int pp = DCH / tpc;   // crosses of this thread: h * pp ...
+                Cx<T> x[DCH], z[DCH];
+#pragma unroll
+                for (int u = 0; u < DCH; ++u) x[u] = z[u] = Cx<T>{0, 0};
+                const Cx<T>* wf = Wf + br.cb + j;
+                const Cx<T>* wc = Wc + br.cb + j;
+#pragma unroll 2
+                for (int k = 0; k < Ku; ++k) {
+                    const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
+#pragma unroll
+                    for (int u = 0; u < DCH; ++u) {
+                        if (u < pp) {
+                            const Cx<T> f = fg[(h * pp + u) * Ku + k];
+                            cfma(x[u], f, a);
+                            cfmac(z[u], f, b);
                         }
-                        acc[q].x += s1.x + s2.x;  // s1 + conj(s2)
-                        acc[q].y += s1.y - s2.y;
                     }
                 }
+#pragma unroll
+                for (int u = 0; u < DCH; ++u)
+                    if (u < pp) {
+                        xs[(h * pp + u) * N + j] = x[u];
+                        zs[(h * pp + u) * N + j] = z[u];
+                    }
             }
-            __syncwarp();
+        }
+        __syncthreads();
+        // phase 3: stream the chunk's faces
+        for (int i0 = 0; i0 < M; i0 += NT) {  // rows beyond NT (M > NT): one thread per row, more passes
+            const int ii = M <= NT ? i : i0 + tid;
+            const bool act = M <= NT ? row_active : ii < M;
+            const int step = M <= NT ? tpr : 1;
+            const int cstart = M <= NT ? q : 0;
+            if (act) {
+                Cx<T> t1{0, 0}, t2{0, 0};
+                const int ncol = np * N;
+                // flattened (cross, column) index c = p N + j, advanced without division
+                int p = cstart / N, j = cstart - (cstart / N) * N;
+#pragma unroll 8
+                for (int c = cstart; c < ncol; c += step) {
+                    const Cx<T> hv = ldcx(pool + offs[p] + (long long)j * M + ii);
+                    cfma(t1, hv, xs[p * N + j]);
+                    cfma(t2, hv, zs[p * N + j]);
+                    j += step;
+                    while (j >= N) {
+                        j -= N;
+                        ++p;
+                    }
+                }
+                if (M <= NT) {
+                    s1.x += t1.x;
+                    s1.y += t1.y;
+                    s2.x += t2.x;
+                    s2.y += t2.y;
+                } else {
+                    atomicAdd(&y[br.rb + ii].x, t1.x + t2.x);
+                    atomicAdd(&y[br.rb + ii].y, t1.y - t2.y);
+                }
+            }
+            if (M <= NT) break;
         }
     }
-#pragma unroll
-    for (int q = 0; q < MQ; ++q) {
-        const int i = lane + 32 * q;
-        if (i < M) {
-            atomicAdd(&y[br.rb + i].x, acc[q].x);
-            atomicAdd(&y[br.rb + i].y, acc[q].y);
+    if (M > NT) return;
+    // phase 4: rows' partial sums (s1 + conj(s2)) added over the TPR threads of a row
+    red[tid] = row_active ? Cx<T>{s1.x + s2.x, s1.y - s2.y} : Cx<T>{0, 0};
+    __syncthreads();
+    if (tid < M) {
+        Cx<T> acc{0, 0};
+        for (int qq = 0; qq < tpr; ++qq) {
+            const Cx<T> v = red[qq * M + tid];
+            acc.x += v.x;
+            acc.y += v.y;
         }
+        atomicAdd(&y[br.rb + tid].x, acc.x);
+        atomicAdd(&y[br.rb + tid].y, acc.y);
     }
 }
 
@@ -384,45 +443,63 @@ static g3_status launch_apply_near(g3_ctx* ctx, cudaStream_t stream, const g3_tr
 }
 
 // Far-field work lists, built on the host when the compression ends and
-// uploaded with the block ranges: the dense-face blocks (one warp each),
-// padded to a multiple of 4 ints, then the phase-1 items (block, group of
-// FAR_PG crosses, column tile of FAR_NT, offset of the group in the a/b
-// buffer) and the phase-2 items (block, group, 0, offset).
-constexpr int FAR_PG = 4;
-constexpr int FAR_NT = 128;
+// uploaded with the block ranges: the dense-face blocks (one CTA each,
+// longest first), padded to a multiple of 4 ints, then the low-rank items (block, group of
+// FAR_PG crosses) of blocks with at most FAR_NT / 2 columns (two threads per
+// column in the x formation), then those of wider blocks; each list longest
+// first (HBM bytes of the group's factors).
+constexpr int FAR_PG = 8;
+constexpr int FAR_NT = 256;
 
 g3_status far_plan_build(g3_factors* fa) {
     std::vector<int>& L = fa->plan;
     L.clear();
-    std::vector<int> p1, p2;
-    long long ab = 0;
-    int mmax = 0;
+    struct Item {
+        long long cost;
+        int b, g;
+    };
+    std::vector<Item> narrow, wide, dense;
+    int mmax = 0, nmax = 0;
     for (int b = 0; b < fa->n_far; ++b) {
         const int r = fa->r3[b];
         if (r <= 0) continue;
         if (fa->rec[(size_t)b * fa->Cmax].r < 0) {
-            L.push_back(b);
-            mmax = std::max(mmax, fa->ranges[b].re - fa->ranges[b].rb);
+            const int M = fa->ranges[b].re - fa->ranges[b].rb, N = fa->ranges[b].ce - fa->ranges[b].cb;
+            dense.push_back(Item{(long long)r * M * N, b, 0});
+            mmax = std::max(mmax, M);
+            nmax = std::max(nmax, N);
             continue;
         }
+        const int M = fa->ranges[b].re - fa->ranges[b].rb;
         const int N = fa->ranges[b].ce - fa->ranges[b].cb;
+        for (int p = 0; p < r; ++p)
+            if (fa->rec[(size_t)b * fa->Cmax + p].r > RF_TS)
+                return fail(G3_EUNSUPPORTED, "aca3_compress: face rank %d above the apply's limit %d",
+                            fa->rec[(size_t)b * fa->Cmax + p].r, RF_TS);
         for (int g = 0; g * FAR_PG < r; ++g) {
-            const long long base = ab;
+            long long c = 0;
             for (int p = g * FAR_PG; p < std::min(r, (g + 1) * FAR_PG); ++p)
-                ab += 2 * fa->rec[(size_t)b * fa->Cmax + p].r;
-            for (int jt = 0; jt * FAR_NT < N; ++jt) p1.insert(p1.end(), {b, g, jt, (int)base});
-            p2.insert(p2.end(), {b, g, 0, (int)base});
+                c += (long long)fa->rec[(size_t)b * fa->Cmax + p].r * (M + N) + fa->Ku;
+            (N <= FAR_NT / 2 ? narrow : wide).push_back(Item{c, b, g});
         }
     }
-    if (ab >= (1LL << 31)) return fail(G3_EUNSUPPORTED, "aca3_compress: the far-field a/b buffer exceeds 2^31");
+    auto by_cost = [](const Item& x, const Item& y) {
+        if (x.cost != y.cost) return x.cost > y.cost;
+        return x.b != y.b ? x.b < y.b : x.g < y.g;
+    };
+    std::sort(narrow.begin(), narrow.end(), by_cost);
+    std::sort(wide.begin(), wide.end(), by_cost);
+    std::sort(dense.begin(), dense.end(), by_cost);
+    for (const Item& it : dense) L.push_back(it.b);
     fa->plan_nd = (int)L.size();
-    fa->plan_n1 = (int)p1.size() / 4;
-    fa->plan_n2 = (int)p2.size() / 4;
-    fa->plan_ab = ab;
+    fa->plan_nmax_dense = nmax;
+    fa->plan_n1 = (int)narrow.size();
+    fa->plan_n2 = (int)wide.size();
+    fa->plan_ab = 0;
     fa->plan_mmax_dense = mmax;
     while (L.size() % 4) L.push_back(0);  // int4 alignment of the item arrays
-    L.insert(L.end(), p1.begin(), p1.end());
-    L.insert(L.end(), p2.begin(), p2.end());
+    for (const Item& it : narrow) L.insert(L.end(), {it.b, it.g, 0, 0});
+    for (const Item& it : wide) L.insert(L.end(), {it.b, it.g, 0, 0});
     G3_CUDA(fa->d_plan.alloc(std::max<size_t>(1, L.size()) * sizeof(int)));
     if (!L.empty()) G3_CUDA(cudaMemcpy(fa->d_plan.p, L.data(), L.size() * sizeof(int), cudaMemcpyHostToDevice));
     G3_CUDA(fa->d_franges.alloc(std::max<size_t>(1, fa->ranges.size()) * sizeof(BlockRange)));
@@ -433,62 +510,48 @@ g3_status far_plan_build(g3_factors* fa) {
     return G3_OK;
 }
 
-// far-field launches over the factors' device work lists; d_ab: space for
-// fa->plan_ab complex values (cleared here)
+// far-field launches over the factors' device work lists (d_ab: unused,
+// kept for the scratch layout of the callers)
 template <class T>
 static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, Cx<T>* d_ab, int Ku, int E, const Cx<T>* Wf,
                                   const Cx<T>* Wc, Cx<T>* y) {
+    (void)d_ab;
     if (!fa->plan_ready) return fail(G3_EINVAL, "apply_gcq: factors without far-field work lists");
     if (fa->plan.empty()) return G3_OK;
     const int nd = fa->plan_nd, n1 = fa->plan_n1, n2 = fa->plan_n2;
     const int* d_list = fa->d_plan.as<int>();
     const BlockRange* d_ranges = fa->d_franges.as<BlockRange>();
     if (nd > 0) {
-        const int mmax_dense = fa->plan_mmax_dense;
-        constexpr int NW = 8, PGW = 4;
-        const size_t smem = (size_t)NW * (PGW * Ku + 2 * PGW * 32) * sizeof(Cx<T>);
-        if (smem > ctx->smem_optin || mmax_dense > 96)
-            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks with %d rows exceed the apply kernel's limit",
-                        mmax_dense);
-        const int grid = (nd + NW - 1) / NW;
-        auto go = [&](auto kfn) -> g3_status {
-            G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kfn<<<grid, NW * 32, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
-                                                      fa->d_r3.as<int>(), d_ranges, d_list, nd, fa->Cmax, Ku, E,
-                                                      Wf, Wc, y);
-            return G3_OK;
-        };
-        g3_status st;
-        if (mmax_dense <= 32)
-            st = go(k_apply_far_dense<T, NW, PGW, 1>);
-        else if (mmax_dense <= 64)
-            st = go(k_apply_far_dense<T, NW, PGW, 2>);
-        else
-            st = go(k_apply_far_dense<T, NW, PGW, 3>);
-        if (st != G3_OK) return st;
-        ctx->count("k_apply_far_dense");
+        // dense-face blocks: one CTA per block; shared memory for the chunk's
+        // fibers, x and zc of the widest block, and the row partial sums
+        const int nmax = fa->plan_nmax_dense;
+        const size_t smem = ((size_t)DCH * Ku + 2 * (size_t)DCH * nmax + FAR_NT) * sizeof(Cx<T>);
+        if (smem > ctx->smem_optin)
+            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks with %d columns exceed the apply kernel's "
+                        "shared memory", nmax);
+        G3_CUDA(cudaFuncSetAttribute(k_far_dense<T, FAR_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_far_dense<T, FAR_NT><<<nd, FAR_NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                                 fa->d_r3.as<int>(), d_ranges, d_list, fa->Cmax, Ku, E,
+                                                                 Wf, Wc, y);
+        ctx->count("k_far_dense");
         G3_CUDA(cudaGetLastError());
     }
-    if (n1 > 0) {
-        G3_CUDA(cudaMemsetAsync(d_ab, 0, (size_t)fa->plan_ab * sizeof(Cx<T>), ctx->stream));
-        const size_t smem = ((size_t)FAR_PG * Ku + 2 * (size_t)FAR_PG * FAR_NT) * sizeof(Cx<T>);
+    const int4* it1 = reinterpret_cast<const int4*>(d_list + (nd + 3) / 4 * 4);
+    const int4* it2 = it1 + n1;
+    auto far_lr = [&](auto kfn, int n, const int4* items, int nc) -> g3_status {
+        if (n <= 0) return G3_OK;
+        const size_t smem = ((size_t)FAR_PG * Ku + 2 * (size_t)FAR_PG * nc + 2 * (size_t)FAR_PG * RF_TS) * sizeof(Cx<T>);
         if (smem > ctx->smem_optin)
             return fail(G3_EUNSUPPORTED, "apply_gcq: far-field kernel needs %zu bytes of shared memory", smem);
-        const int4* it1 = reinterpret_cast<const int4*>(d_list + (nd + 3) / 4 * 4);
-        const int4* it2 = it1 + n1;
-        G3_CUDA(cudaFuncSetAttribute(k_far_vx<T, FAR_NT, FAR_PG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        k_far_vx<T, FAR_NT, FAR_PG><<<n1, FAR_NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(),
-                                                                        fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(),
-                                                                        d_ranges, it1, fa->Cmax, Ku, E, Wf, Wc, d_ab);
-        ctx->count("k_far_vx");
+        G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kfn<<<n, FAR_NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(), fa->d_r3.as<int>(),
+                                              d_ranges, items, fa->Cmax, Ku, E, Wf, Wc, y);
+        ctx->count("k_far_lr");
         G3_CUDA(cudaGetLastError());
-        k_far_uy<T, FAR_NT, FAR_PG><<<n2, FAR_NT, 0, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
-                                                                     fa->d_r3.as<int>(), d_ranges, it2, fa->Cmax,
-                                                                     d_ab, y);
-        ctx->count("k_far_uy");
-        G3_CUDA(cudaGetLastError());
-    }
+        return G3_OK;
+    };
+    G3_TRY_NA(far_lr(k_far_lr<T, FAR_NT, FAR_PG, 2>, n1, it1, FAR_NT / 2));
+    G3_TRY_NA(far_lr(k_far_lr<T, FAR_NT, FAR_PG, 1>, n2, it2, FAR_NT));
     return G3_OK;
 }
 
@@ -895,8 +958,8 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
     const size_t need = al(2 * nW * sizeof(Cx<T>)) + al(E * sizeof(Cx<T>)) + al(n_ab * sizeof(Cx<T>));
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(G3_EINVAL,
-                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values and "
-                    "2 per far-field face rank), the fixed scratch holds %zu; use apply_gcq",
+                    "apply_gcq_noalloc: this problem needs %zu bytes of scratch (2 Ku E + E complex values), "
+                    "the fixed scratch holds %zu; use apply_gcq",
                     need, NOALLOC_SCRATCH_BYTES);
     void* base = nullptr;
     G3_TRY_NA(noalloc_scratch(ctx->device, &base));

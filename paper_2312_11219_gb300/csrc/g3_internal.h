@@ -287,6 +287,7 @@ struct g3_factors {
     std::vector<int> plan;             // host copy
     int plan_nd = 0, plan_n1 = 0, plan_n2 = 0;
     int plan_mmax_dense = 0;           // most rows of a dense-face block
+    int plan_nmax_dense = 0;           // most columns of a dense-face block
     long long plan_ab = 0;             // complex values of the a/b buffer
     g3::DevBuf d_plan;                 // int [plan.size()]
     g3::DevBuf d_franges;              // BlockRange [n_far]

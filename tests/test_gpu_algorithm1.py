@@ -126,3 +126,61 @@ def test_plain_fp64_unbatched_matches_oracle(g3, ctx):
     # the persistent launch computes the same ranks block for block
     fb = g3.aca3_compress(ctx, T, F, "slp", prec="fp64", eps3=w.eps3, dense_face_max=-1)
     assert np.array_equal(fa.ranks(), fb.ranks())
+
+
+# ---------------------------------------------------------------- pivot estimate of eq. (index)
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_index_pivot_rank1_separable(g3, ctx, prec):
+    """On a rank-1 tensor the estimate of eq. (index) picks the largest entry
+    of the face, (argmax |a|, argmax |b|), and the tensor is recovered."""
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((1, 60)) + 1j * rng.standard_normal((1, 60))
+    b = rng.standard_normal((1, 50)) + 1j * rng.standard_normal((1, 50))
+    c = rng.standard_normal((1, 9)) + 1j * rng.standard_normal((1, 9))
+    fa = g3.aca3_compress_separable(ctx, a, b, c, prec=prec, eps3=1e-4, dense_face_max=-1, pivot_index=1)
+    blk = fa.block(0, 60, 50, 9)
+    assert fa.ranks()[0] == 1
+    assert blk["piv"][0, 0] == int(np.argmax(np.abs(a[0]))) and blk["piv"][0, 1] == int(np.argmax(np.abs(b[0])))
+    D = np.einsum("ti,tj,tk->ijk", a, b, c)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.linalg.norm(_approximant(blk) - D) <= tol * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_index_pivot_blockwise_single_layer(g3, ctx, prec):
+    """Algorithm 1 with the pivot of eq. (index) on the single layer of the
+    3,072-triangle L-shape (low-rank faces everywhere): blocks within 10 eps3 of
+    the dense oracle blocks, ranks within 2 of the oracle run with the same
+    pivot rule."""
+    w = workloads.get("lshape3072")
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+    F = g3.freqs_from_spec(ctx, w.freq)
+    fa = g3.aca3_compress(ctx, T, F, "slp", prec=prec, eps3=w.eps3, dense_face_max=-1, pivot_index=1)
+    assert fa.stats()["status_bits"] & 1 == 0
+    geo, OT, su, ef, far = _blocks(w, "slp")
+    r3 = fa.ranks()
+    sizes = [(OT.blocks[b, 1] - OT.blocks[b, 0]) * (OT.blocks[b, 3] - OT.blocks[b, 2]) for b in far]
+    rng = np.random.default_rng(8)
+    check = sorted(set(rng.choice(len(far), 8, replace=False).tolist()) | {int(np.argmax(sizes))})
+    for i in check:
+        rb, re, cb, ce, _ = OT.blocks[far[i]]
+        M, N = re - rb, ce - cb
+        D = O_q.dense(geo, "slp", su, rows=OT.perm[rb:re], cols=OT.perm[cb:ce])
+        blk = fa.block(i, M, N, su.size)
+        assert np.linalg.norm(_approximant(blk) - D) <= 10 * w.eps3 * np.linalg.norm(D), i
+        ref = O_aca.aca3(O_aca.BemBlock(ef, OT.perm[rb:re], OT.perm[cb:ce], su), w.eps3, s_abs=np.abs(su),
+                         dense_max=-1, pivot="index")
+        assert abs(ref.rank - r3[i]) <= 2, (i, ref.rank, r3[i])
+
+
+def test_index_pivot_double_layer_keeps_dense_expansion(g3, ctx):
+    """The double layer falls back to the dense expansion (the paper's
+    remark): the option changes nothing there."""
+    w = workloads.get("lshape768")
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+    F = g3.freqs_from_spec(ctx, w.freq)
+    f0 = g3.aca3_compress(ctx, T, F, "dlp", prec="fp64", eps3=1e-4, dense_face_max=-1)
+    f1 = g3.aca3_compress(ctx, T, F, "dlp", prec="fp64", eps3=1e-4, dense_face_max=-1, pivot_index=1)
+    assert np.array_equal(f0.ranks(), f1.ranks())
+    assert f0.stats()["entries"] == f1.stats()["entries"]
