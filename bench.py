@@ -561,6 +561,33 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
             fresh[label] = tot
             del T2, F2, c2
         learned = {"mlp_use": args.mlp_use, "training": train_info, "ab": ab, "fresh_context": fresh}
+    # the time-stepping consumer (g3_gcq_history) with the gCQ set of the graded
+    # steps (N_Q = 256) on at least 131,072 elements: an HBM stream of X (read
+    # and written) and W (written), 24 bytes per element and frequency (complex64)
+    gcq_hist = None
+    if world == 1 and not batch:
+        st_ = workloads.graded_steps(64)
+        Fg = g3.g3_freqs_gcq(ctx, 256, float(st_.min()), float(st_.max()))
+        E0 = max(ws[0].E, 131072)   # X and W of 268 MB each: larger than L2
+        Xg = torch.zeros((256, E0), dtype=torch.complex64, device=dev).t()
+        Wg = torch.empty((256, E0), dtype=torch.complex64, device=dev).t()
+        thg = torch.ones(E0, dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            g3.gcq_history(ctx, Fg, Xg, thg, float(st_[0]), float(st_[1]), Wg)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for r in range(reps):
+            g3.gcq_history(ctx, Fg, Xg, thg, float(st_[r % 64]), float(st_[(r + 1) % 64]), Wg)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_h = e0.elapsed_time(e1) / reps
+        byt = E0 * 256 * 24
+        gcq_hist = {"ms": ms_h, "bytes": byt, "gbs": byt / (ms_h / 1e3) / 1e9,
+                    "frac_hbm": byt / (ms_h / 1e3) / 1e9 / _peaks()["hbm_gbs"],
+                    "note": f"{E0} elements x 256 gCQ frequencies, complex64 (X and W larger than L2), "
+                            f"mean of {reps} launches"}
     # the pivot estimate of eq. (index) against the dense expansion (single
     # layer, collocation; the double layer keeps the dense expansion)
     pivot_ab = None
@@ -630,6 +657,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "peaks_source": peaks["source"],
         "learned": learned,
         "pivot_index_ab": pivot_ab,
+        "gcq_history": gcq_hist,
         "autotune": tune or None,
         "compression_entries_per_s": aca_eps,
     }

@@ -499,6 +499,22 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
  * other threads) race and must be serialised by the caller. */
 g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
                             void* Y, g3_dtype dtype);
+/* The gCQ time-stepping consumer of the apply (eq. (gCQ_xn) and the weight
+ * vectors of eq. (gcq_formula)), implicit-Euler reading (one stage,
+ * A = b = 1).  For every frequency l of f (all K) and element i < M:
+ *   X[:, l] <- (X[:, l] + dt_prev theta) / (1 - dt_prev s_l)   (x_{n-1} from x_{n-2})
+ *   W[:, l]  = -omega_l X[:, l] / (1 - dt_next s_l)             (weights for apply_gcq)
+ * where dt_prev = dt_{n-1} (the step of theta = theta_{n-1}) and dt_next =
+ * dt_n.  The sign: the contour integral of eq. (conv_discrete) runs so that
+ * the pole of (1 - dt_n s)^{-1} gives +V((dt_n A)^{-1}); omega_l
+ * (g3_freqs_gcq) is normalised the other way round.  apply_gcq(W) then
+ * returns the history sum of eq. (gcq_formula).  X, W [M*K] complex (dtype)
+ * column-major device buffers (column l = frequency l, caller's element
+ * order), X updated in place (start from zeros: x_0 = 0); theta [M] complex
+ * device buffer, or NULL for zero.  f must carry contour weights (a gCQ set;
+ * G3_EINVAL otherwise).  Runs on the context's stream, no synchronisation. */
+g3_status g3_gcq_history(g3_ctx* ctx, const g3_freqs* f, int M, void* X, const void* theta, double dt_prev,
+                         double dt_next, void* W, g3_dtype dtype);
 /* Device time (ms) of the last apply on this context and its algorithmic
  * bytes (near field, factors, W read once, Y written once). */
 g3_status g3_apply_last(const g3_ctx* ctx, double* ms, int64_t* bytes, double* near_ms, int64_t* near_bytes);

@@ -16,4 +16,6 @@ Modules
   aca3        the three-way ACA of Algorithm 1 with face ACA and
               QR+SVD recompression
   apply       dense and compressed application (eq. (product))
+  gcq         the time-stepping consumer: history update and weights
+              (eq. (gCQ_xn), eq. (gcq_formula)), implicit-Euler reading
 """

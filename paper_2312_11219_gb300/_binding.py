@@ -110,6 +110,7 @@ _sig("apply_gcq", _ci, _p, _p, _p, _p, _p, _p, _ci, _ci, _ci)
 _sig("g3_apply_last", _ci, _p, _dp, _i64p, _dp, _i64p)
 _sig("g3_peak", _ci, _p, _ci, _dp, _dp)
 _sig("apply_gcq_noalloc", _ci, _p, _p, _p, _p, _p, _p, _ci)
+_sig("g3_gcq_history", _ci, _p, _p, _ci, _p, _p, C.c_double, C.c_double, _p, _ci)
 _fp = C.POINTER(C.c_float)
 _sig("g3_mlp_create", _ci, _p, _fp, _fp, _fp, C.c_uint64, _pp)
 _sig("g3_mlp_train", _ci, _p, _fp, _fp, _ci, C.POINTER(TrainOpts), _pp)
@@ -126,7 +127,7 @@ EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_ver
             "build_cluster_tree", "build_cluster_tree_capped", "g3_shard_rows", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
-            "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
+            "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_gcq_history", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
             "g3_mlp_grad", "g3_mlp_predict", "g3_mlp_get", "g3_mlp_free", "g3_block_features", "g3_factors_labels"]
 
 MLP_NF = 12
@@ -625,3 +626,24 @@ def apply_gcq_noalloc(ctx: Context, tree: Tree, near: Near | None, factors: Fact
                                   factors.h if factors is not None else None, C.c_void_p(W.data_ptr()),
                                   C.c_void_p(Y.data_ptr()), dt), "apply_gcq_noalloc")
     return Y
+
+
+def gcq_history(ctx: Context, freqs: Freqs, X, theta, dt_prev: float, dt_next: float, W=None):
+    """One gCQ history step (g3_gcq_history): X [M, K] complex CUDA tensor with
+    contiguous columns (updated in place), theta [M] (or None), returns
+    W [M, K] (the weights for apply_gcq) in X's layout."""
+    import torch
+    if not (X.is_cuda and X.dtype in (torch.complex64, torch.complex128)) or not X.t().is_contiguous():
+        raise ValueError("X must be a complex CUDA tensor [M, K] with contiguous columns")
+    M = X.shape[0]
+    if W is None:
+        W = torch.empty((X.shape[1], M), dtype=X.dtype, device=X.device).t()
+    th = None
+    if theta is not None:
+        if not (theta.is_cuda and theta.dtype == X.dtype and theta.is_contiguous() and theta.numel() == M):
+            raise ValueError("theta must be a contiguous CUDA tensor [M] of X's dtype")
+        th = C.c_void_p(theta.data_ptr())
+    dt = 1 if X.dtype == torch.complex128 else 0
+    _check(_lib.g3_gcq_history(ctx.h, freqs.h, M, C.c_void_p(X.data_ptr()), th, dt_prev, dt_next,
+                               C.c_void_p(W.data_ptr()), dt), "g3_gcq_history")
+    return W

@@ -150,7 +150,11 @@ const char* g3_kernel_name(const g3_ctx* ctx, int i, int64_t* launches) {
 // ---------------------------------------------------------------------------
 
 static g3_status finish_freqs(g3_ctx* ctx, g3_freqs* f, const std::vector<double>& su_host) {
-    // su_host: unique set as interleaved pairs [2 Ku]
+    // su_host: unique set as interleaved pairs [2 Ku]; f->s, f->omega: the full set
+    G3_CUDA(f->d_s_all.alloc((size_t)f->K * 2 * sizeof(double)));
+    G3_CUDA(f->d_w_all.alloc((size_t)f->K * 2 * sizeof(double)));
+    G3_CUDA(cudaMemcpy(f->d_s_all.p, f->s.data(), (size_t)f->K * 2 * sizeof(double), cudaMemcpyHostToDevice));
+    G3_CUDA(cudaMemcpy(f->d_w_all.p, f->omega.data(), (size_t)f->K * 2 * sizeof(double), cudaMemcpyHostToDevice));
     G3_CUDA(f->d_sd.alloc((size_t)f->Ku * 2 * sizeof(double)));
     G3_CUDA(f->d_sf.alloc((size_t)f->Ku * 2 * sizeof(float)));
     std::vector<float> sf(2 * (size_t)f->Ku);

@@ -277,135 +277,98 @@ __global__ void __launch_bounds__(NT) k_far_lr(const Cx<T>* __restrict__ pool, c
     }
 }
 
-// Far field, blocks with dense faces (the small blocks, M N <= the
-// compression's dense-face threshold): one CTA per block streams the block's
-// faces H_p (M x N, column-major, contiguous per cross) from HBM, in chunks of
-// DCH crosses:
-//   1. the chunk's fibers to shared memory;
-//   2. x_p[j] = sum_k f_p[k] w_k[j], zc_p[j] = sum_k f_p[k] conj(w_k'[j])
-//      (TPC threads per column, W from L2), to shared memory;
-//   3. y[i] += sum_p sum_j H_p[i, j] x_p[j] + conj(H_p[i, j] zc_p[j]): thread
-//      (i, q) takes row i and every TPR-th column of the chunk's faces (for a
-//      fixed column the warp's rows are consecutive: coalesced), eight loads
-//      in flight;
-//   4. the TPR partial sums of a row are added in shared memory and the CTA
-//      adds y once per row.
-constexpr int DCH = 8;
-
-template <class T, int NT>
-__global__ void __launch_bounds__(NT, 3) k_far_dense(const Cx<T>* __restrict__ pool, const CrossRec* __restrict__ rec,
-                                                  const int* __restrict__ r3, const BlockRange* __restrict__ ranges,
-                                                  const int* __restrict__ list, int Cmax, int Ku, int E,
-                                                  const Cx<T>* __restrict__ Wf, const Cx<T>* __restrict__ Wc,
-                                                  Cx<T>* __restrict__ y) {
+// Far field, blocks with dense faces (small blocks): one warp per block, no
+// block-wide barrier.  Crosses in groups of PG: the group's fibers are staged
+// in the warp's slice of shared memory; for each chunk of 32 columns, lane j
+// forms x_p[j] = sum_k f_p[k] w_k[j] and zc_p[j] = sum_k f_p[k] conj(w_k'[j])
+// for the group in one pass over W, and lane i then adds
+// sum_p (H_p x_p)[i] + conj((H_p zc_p)[i]) over the chunk for its rows.
+template <class T, int NW, int PG, int MQ>
+__global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __restrict__ pool,
+                                                               const CrossRec* __restrict__ rec,
+                                                               const int* __restrict__ r3,
+                                                               const BlockRange* __restrict__ ranges,
+                                                               const int* __restrict__ list, int n, int Cmax, int Ku,
+                                                               int E, const Cx<T>* __restrict__ Wf,
+                                                               const Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int blk = list[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * NW + warp;
+    if (bi >= n) return;  // the whole warp: no block-wide synchronisation below
+    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * (PG * Ku + 2 * PG * 32);
+    Cx<T>* xs = fg + PG * Ku;
+    Cx<T>* zs = xs + PG * 32;
+    const int blk = list[bi];
     const BlockRange br = ranges[blk];
     const int M = br.re - br.rb, N = br.ce - br.cb;
-    Cx<T>* fg = reinterpret_cast<Cx<T>*>(smem_raw);  // [DCH][Ku]
-    Cx<T>* xs = fg + DCH * Ku;                        // [DCH][N]
-    Cx<T>* zs = xs + DCH * N;                         // [DCH][N]
-    Cx<T>* red = zs + DCH * N;                        // [NT] partial row sums
-    __shared__ long long offs[DCH];
-    const int tid = threadIdx.x;
     const int nc = r3[blk];
-    const long long MN = (long long)M * N;
-    // phase 3 layout: TPR threads per row
-    const int tpr = max(1, min(NT / M, 32));
-    const int i = tid % M, q = tid / M;
-    const bool row_active = M <= NT ? q < tpr : tid < M;
-    Cx<T> s1{0, 0}, s2{0, 0};
-    // phase 2 layout: TPC threads per column, each with DCH / TPC crosses
-    const int tpc = N >= NT ? 1 : (N * 2 > NT ? 1 : (N * 4 > NT ? 2 : (N * 8 > NT ? 4 : 8)));
-    for (int c0 = 0; c0 < nc; c0 += DCH) {
-        const int np = min(DCH, nc - c0);
-        __syncthreads();  // the previous chunk is done with fg, xs, zs
-        if (tid < DCH) offs[tid] = tid < np ? rec[(size_t)blk * Cmax + c0 + tid].off : 0;
-        __syncthreads();
-        for (int e = tid; e < DCH * Ku; e += NT) {
-            const int p = e / Ku, k = e - p * Ku;
-            fg[e] = p < np ? ldcx(pool + offs[p] + MN + k) : Cx<T>{0, 0};
-        }
-        __syncthreads();
-        for (int j0 = 0; j0 < N; j0 += NT / tpc) {
-            const int jl = tid / tpc, h = tid - jl * tpc;
-            const int j = j0 + jl;
-            if (j < N) {
-                const int pp = DCH / tpc;   // crosses of this thread: h * pp ...
-                Cx<T> x[DCH], z[DCH];
+    Cx<T> acc[MQ];
 #pragma unroll
-                for (int u = 0; u < DCH; ++u) x[u] = z[u] = Cx<T>{0, 0};
+    for (int q = 0; q < MQ; ++q) acc[q] = Cx<T>{0, 0};
+    for (int g0 = 0; g0 < nc; g0 += PG) {
+        const int np = min(PG, nc - g0);
+        __syncwarp();
+        for (int e = lane; e < PG * Ku; e += 32) {
+            const int p = e / Ku, k = e - p * Ku;
+            Cx<T> v{0, 0};
+            if (p < np) v = ldcx(pool + rec[(size_t)blk * Cmax + g0 + p].off + (long long)M * N + k);
+            fg[e] = v;
+        }
+        __syncwarp();
+        for (int j0 = 0; j0 < N; j0 += 32) {
+            const int j = j0 + lane;
+            Cx<T> x[PG], z[PG];
+#pragma unroll
+            for (int p = 0; p < PG; ++p) x[p] = z[p] = Cx<T>{0, 0};
+            if (j < N) {
                 const Cx<T>* wf = Wf + br.cb + j;
                 const Cx<T>* wc = Wc + br.cb + j;
-#pragma unroll 2
+#pragma unroll 4
                 for (int k = 0; k < Ku; ++k) {
                     const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
 #pragma unroll
-                    for (int u = 0; u < DCH; ++u) {
-                        if (u < pp) {
-                            const Cx<T> f = fg[(h * pp + u) * Ku + k];
-                            cfma(x[u], f, a);
-                            cfmac(z[u], f, b);
-                        }
+                    for (int p = 0; p < PG; ++p) {
+                        const Cx<T> f = fg[p * Ku + k];
+                        cfma(x[p], f, a);
+                        cfmac(z[p], f, b);
                     }
                 }
+            }
 #pragma unroll
-                for (int u = 0; u < DCH; ++u)
-                    if (u < pp) {
-                        xs[(h * pp + u) * N + j] = x[u];
-                        zs[(h * pp + u) * N + j] = z[u];
-                    }
+            for (int p = 0; p < PG; ++p) {
+                xs[p * 32 + lane] = x[p];
+                zs[p * 32 + lane] = z[p];
             }
-        }
-        __syncthreads();
-        // phase 3: stream the chunk's faces
-        for (int i0 = 0; i0 < M; i0 += NT) {  // rows beyond NT (M > NT): one thread per row, more passes
-            const int ii = M <= NT ? i : i0 + tid;
-            const bool act = M <= NT ? row_active : ii < M;
-            const int step = M <= NT ? tpr : 1;
-            const int cstart = M <= NT ? q : 0;
-            if (act) {
-                Cx<T> t1{0, 0}, t2{0, 0};
-                const int ncol = np * N;
-                // flattened (cross, column) index c = p N + j, advanced without division
-                int p = cstart / N, j = cstart - (cstart / N) * N;
+            __syncwarp();
+            const int jn = min(32, N - j0);
+            for (int p = 0; p < np; ++p) {
+                const Cx<T>* H = pool + rec[(size_t)blk * Cmax + g0 + p].off + (long long)j0 * M;
+#pragma unroll
+                for (int q = 0; q < MQ; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i < M) {
+                        Cx<T> s1{0, 0}, s2{0, 0};
 #pragma unroll 8
-                for (int c = cstart; c < ncol; c += step) {
-                    const Cx<T> hv = ldcx(pool + offs[p] + (long long)j * M + ii);
-                    cfma(t1, hv, xs[p * N + j]);
-                    cfma(t2, hv, zs[p * N + j]);
-                    j += step;
-                    while (j >= N) {
-                        j -= N;
-                        ++p;
+                        for (int jj = 0; jj < jn; ++jj) {
+                            const Cx<T> h = ldcx(H + i + (long long)jj * M);
+                            cfma(s1, h, xs[p * 32 + jj]);
+                            cfma(s2, h, zs[p * 32 + jj]);
+                        }
+                        acc[q].x += s1.x + s2.x;  // s1 + conj(s2)
+                        acc[q].y += s1.y - s2.y;
                     }
                 }
-                if (M <= NT) {
-                    s1.x += t1.x;
-                    s1.y += t1.y;
-                    s2.x += t2.x;
-                    s2.y += t2.y;
-                } else {
-                    atomicAdd(&y[br.rb + ii].x, t1.x + t2.x);
-                    atomicAdd(&y[br.rb + ii].y, t1.y - t2.y);
-                }
             }
-            if (M <= NT) break;
+            __syncwarp();
         }
     }
-    if (M > NT) return;
-    // phase 4: rows' partial sums (s1 + conj(s2)) added over the TPR threads of a row
-    red[tid] = row_active ? Cx<T>{s1.x + s2.x, s1.y - s2.y} : Cx<T>{0, 0};
-    __syncthreads();
-    if (tid < M) {
-        Cx<T> acc{0, 0};
-        for (int qq = 0; qq < tpr; ++qq) {
-            const Cx<T> v = red[qq * M + tid];
-            acc.x += v.x;
-            acc.y += v.y;
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int i = lane + 32 * q;
+        if (i < M) {
+            atomicAdd(&y[br.rb + i].x, acc[q].x);
+            atomicAdd(&y[br.rb + i].y, acc[q].y);
         }
-        atomicAdd(&y[br.rb + tid].x, acc.x);
-        atomicAdd(&y[br.rb + tid].y, acc.y);
     }
 }
 
@@ -443,7 +406,7 @@ static g3_status launch_apply_near(g3_ctx* ctx, cudaStream_t stream, const g3_tr
 }
 
 // Far-field work lists, built on the host when the compression ends and
-// uploaded with the block ranges: the dense-face blocks (one CTA each,
+// uploaded with the block ranges: the dense-face blocks (one warp each,
 // longest first), padded to a multiple of 4 ints, then the low-rank items (block, group of
 // FAR_PG crosses) of blocks with at most FAR_NT / 2 columns (two threads per
 // column in the x formation), then those of wider blocks; each list longest
@@ -522,18 +485,33 @@ static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, Cx<T>* d_ab
     const int* d_list = fa->d_plan.as<int>();
     const BlockRange* d_ranges = fa->d_franges.as<BlockRange>();
     if (nd > 0) {
-        // dense-face blocks: one CTA per block; shared memory for the chunk's
-        // fibers, x and zc of the widest block, and the row partial sums
-        const int nmax = fa->plan_nmax_dense;
-        const size_t smem = ((size_t)DCH * Ku + 2 * (size_t)DCH * nmax + FAR_NT) * sizeof(Cx<T>);
-        if (smem > ctx->smem_optin)
-            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks with %d columns exceed the apply kernel's "
-                        "shared memory", nmax);
-        G3_CUDA(cudaFuncSetAttribute(k_far_dense<T, FAR_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_far_dense<T, FAR_NT><<<nd, FAR_NT, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
-                                                                 fa->d_r3.as<int>(), d_ranges, d_list, fa->Cmax, Ku, E,
-                                                                 Wf, Wc, y);
-        ctx->count("k_far_dense");
+        const int mmax_dense = fa->plan_mmax_dense;
+        constexpr int NW = 8, PGW = 4;
+        const size_t smem = (size_t)NW * (PGW * Ku + 2 * PGW * 32) * sizeof(Cx<T>);
+        if (smem > ctx->smem_optin || mmax_dense > 256)
+            return fail(G3_EUNSUPPORTED, "apply_gcq: dense-face blocks with %d rows exceed the apply kernel's limit",
+                        mmax_dense);
+        const int grid = (nd + NW - 1) / NW;
+        auto go = [&](auto kfn) -> g3_status {
+            G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kfn<<<grid, NW * 32, smem, ctx->stream>>>(fa->pool->as<Cx<T>>(), fa->d_rec.as<CrossRec>(),
+                                                      fa->d_r3.as<int>(), d_ranges, d_list, nd, fa->Cmax, Ku, E,
+                                                      Wf, Wc, y);
+            return G3_OK;
+        };
+        g3_status st;
+        if (mmax_dense <= 32)
+            st = go(k_apply_far_dense<T, NW, PGW, 1>);
+        else if (mmax_dense <= 64)
+            st = go(k_apply_far_dense<T, NW, PGW, 2>);
+        else if (mmax_dense <= 96)
+            st = go(k_apply_far_dense<T, NW, PGW, 3>);
+        else if (mmax_dense <= 128)
+            st = go(k_apply_far_dense<T, NW, PGW, 4>);
+        else
+            st = go(k_apply_far_dense<T, NW, PGW, 8>);
+        if (st != G3_OK) return st;
+        ctx->count("k_apply_far_dense");
         G3_CUDA(cudaGetLastError());
     }
     const int4* it1 = reinterpret_cast<const int4*>(d_list + (nd + 3) / 4 * 4);

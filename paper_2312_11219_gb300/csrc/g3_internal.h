@@ -215,6 +215,7 @@ struct g3_freqs {
     std::vector<int32_t> uniq;  // [Ku]
     std::vector<int32_t> partner;  // [K]
     int k_maxabs = 0;           // unique index of the largest |s|
+    g3::DevBuf d_s_all, d_w_all; // [K] double2: all frequencies and contour weights
     g3::DevBuf d_sd;            // [Ku] double2 (unique set)
     g3::DevBuf d_sf;            // [Ku] float2
     g3::DevBuf d_uniq, d_partner;

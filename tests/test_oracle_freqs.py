@@ -139,3 +139,50 @@ def test_pair_conjugates_arbitrary_order_and_unpaired():
     assert p[16] == 16 and p[17] == 17
     for l in u:                                                # the lower index of each pair is unique
         assert p[l] >= l
+
+
+# ---------------------------------------------------------------- the gCQ time-stepping consumer
+
+def test_gcq_history_reproduces_implicit_euler():
+    """For the transfer function F(s) = 1/(s + a) the implicit-Euler gCQ is
+    the implicit-Euler solution of y' = -a y + theta on the same (graded)
+    steps: y_n = (y_{n-1} + dt_n theta_n) / (1 + a dt_n).  The compact
+    algorithm with the contour of Appendix A must reproduce it to the
+    quadrature's accuracy (the contour runs from near s = 0 around
+    [1/dt_max, 1/dt_min], so the pole -a of F is kept well away from it:
+    a >= 20); a wrong sign of the contour weights flips the history term, a
+    wrong update index shifts it by a step."""
+    from oracle import gcq
+    from inputs import workloads
+    dts = workloads.graded_steps(64)
+    s, omega = freqs.gcq(256, float(dts.min()), float(dts.max()))
+    rng = np.random.default_rng(5)
+    theta = 1.0 + 0.5 * np.sin(np.arange(dts.size) / 5.0) + 0.1 * rng.standard_normal(dts.size)
+    for a in (20.0, 50.0, 200.0):
+        g = gcq.convolution(lambda z: 1.0 / (z + a), theta, dts, s, omega)
+        y = np.zeros(dts.size)
+        prev = 0.0
+        for n in range(dts.size):
+            prev = (prev + dts[n] * theta[n]) / (1.0 + a * dts[n])
+            y[n] = prev
+        assert np.max(np.abs(g - y)) <= 1e-10 * np.max(np.abs(y)), a
+        # the opposite orientation of the weights fails by O(1)
+        g_bad = gcq.convolution(lambda z: 1.0 / (z + a), theta, dts, s, -omega)
+        assert np.max(np.abs(g_bad - y)) > 0.1 * np.max(np.abs(y))
+
+
+def test_gcq_history_weights_sign_and_first_step():
+    """x_0 = 0 gives W = 0 at the first step; one step of a unit density gives
+    x_1(s) = dt / (1 - dt s), whose weighted sum with F = 1 is the quadrature
+    of (1/2 pi i) times the clockwise contour integral of dt / ((1 - dt s)(1 - dt' s)):
+    the residues at s = 1/dt and 1/dt' give dt / (1 - dt'/dt) * (-1/dt) * ... =
+    0 for the sum of both (the integrand decays as s^-2), so the weights of
+    the two enclosed poles cancel: sum_l W_l = 0."""
+    from oracle import gcq
+    s, omega = freqs.gcq(128, 0.005, 0.015)
+    X = np.zeros((3, s.size), complex)
+    assert np.all(gcq.history_weights(X, s, omega, 0.01) == 0)
+    X = gcq.history_step(X, np.ones(3), s, 0.012)
+    assert np.allclose(X[0], 0.012 / (1 - 0.012 * s))
+    W = gcq.history_weights(X, s, omega, 0.008)
+    assert abs(W[0].sum()) <= 1e-10 * np.abs(W[0]).sum()
