@@ -145,6 +145,13 @@ typedef struct {
                              instead of the dense expansion's O(M N r).  Single layer
                              only: G3_DLP keeps the dense expansion, the paper's
                              fallback.  0 (default) = dense expansion                   */
+    int graph;            /* 1 = the compression's launch sequence (queue resets and both
+                             persistent launches) is captured into a CUDA graph on the
+                             context's stream and launched as one graph; blocks that spill
+                             rerun as plain launches.  The low-rank / dense split of the
+                             device time is not available then (ms_lowrank = ms).  Not
+                             with unbatched.  The context's stream must not be capturing
+                             already.  0 (default) = plain launches                      */
 } g3_opts;
 
 /* Statistics of one compression. */
@@ -469,10 +476,11 @@ g3_status g3_factors_labels(g3_ctx* ctx, const g3_factors* fa, float* out);
  * mem = G3_HOST:   W, Y are host pointers; the library copies W in and Y out
  *                  on the context's stream and synchronises before return.
  * Frequencies outside the unique set use A(conj s) = conj A(s).
- * G3_APPLY_SUM: with both parts present the near field runs on a second
- * stream owned by the context, forked from and joined back into the
- * context's stream, so work the caller orders after this call on that stream
- * sees y complete.  G3_APPLY_PERFREQ runs on the context's stream only; its
+ * G3_APPLY_SUM: with both parts present the far-field kernels run on a
+ * second, high-priority stream owned by the context (forked from and joined
+ * back into the context's stream, next to the near field on the context's
+ * stream), so work the caller orders after this call on the context's
+ * stream sees y complete.  G3_APPLY_PERFREQ runs on the context's stream only; its
  * scratch holds 4 Ku M complex values (context-owned, grown on demand), and
  * face ranks above 64 return G3_EUNSUPPORTED.  The call synchronises the
  * context's stream before it returns (the device time is recorded for

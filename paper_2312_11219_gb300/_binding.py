@@ -42,7 +42,8 @@ class Opts(C.Structure):
                 ("k1", _i32p), ("cost", C.POINTER(C.c_float)), ("pool_factor", C.c_double),
                 ("eps_face", C.c_double), ("max_blocks", C.c_int), ("dense_face_max", C.c_int),
                 ("literal_stop", C.c_int), ("mlp", C.c_void_p), ("mlp_use", C.c_int),
-                ("face_floor_scale", C.c_double), ("trunc_floor_scale", C.c_double), ("pivot_index", C.c_int)]
+                ("face_floor_scale", C.c_double), ("trunc_floor_scale", C.c_double), ("pivot_index", C.c_int),
+                ("graph", C.c_int)]
 
 
 class TrainOpts(C.Structure):

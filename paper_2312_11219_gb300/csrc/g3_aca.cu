@@ -299,11 +299,19 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     unsigned long long ctr = 0;
     const g3_tree* t0 = jobs[0].t;
     const g3_freqs* f0 = jobs[0].f;
-    for (;;) {
+    for (int round = 0;; ++round) {
+        // the first round can run as one captured CUDA graph (opts->graph):
+        // the queue resets and both persistent launches become one graph launch
+        const bool graph = o.graph && round == 0 && !o.unbatched;
+        cudaGraph_t cg = nullptr;
+        if (graph) G3_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         G3_CUDA(cudaMemsetAsync(d_head.p, 0, 2 * sizeof(int), ctx->stream));
         G3_CUDA(cudaMemsetAsync(d_spill_n.p, 0, sizeof(int), ctx->stream));
         G3_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
-        G3_CUDA(cudaMemcpyAsync(d_ctr.p, &base, sizeof(base), cudaMemcpyHostToDevice, ctx->stream));
+        if (graph)  // base = 0 in the first round
+            G3_CUDA(cudaMemsetAsync(d_ctr.p, 0, sizeof(base), ctx->stream));
+        else
+            G3_CUDA(cudaMemcpyAsync(d_ctr.p, &base, sizeof(base), cudaMemcpyHostToDevice, ctx->stream));
         AcaArgs<T> A{};
         A.geos = batched ? d_geos.as<GeoDesc>() : nullptr;
         A.bgeo = batched ? d_bgeo.as<int>() : nullptr;
@@ -345,10 +353,10 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         A.ws_stride = stride;
         A.Mmax = Mmax;
         A.Nmax = Nmax;
-        G3_CUDA(cudaEventRecord(e0, ctx->stream));
+        if (!graph) G3_CUDA(cudaEventRecord(e0, ctx->stream));
         g3_status st = G3_OK;
         for (int cls = 0; cls < 2 && st == G3_OK; ++cls) {
-            if (cls == 1) G3_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
+            if (cls == 1 && !graph) G3_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
             const int cnt = cls == 0 ? n_lo : n_de;
             if (cnt == 0) continue;
             AcaArgs<T> B = A;
@@ -369,6 +377,24 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
                 else
                     st = launch_kind<T, NT, false>(ctx, kernel, B, g, smem);
             }
+        }
+        if (graph) {
+            cudaError_t ce = cudaStreamEndCapture(ctx->stream, &cg);
+            if (st != G3_OK) {
+                if (cg) cudaGraphDestroy(cg);
+                return st;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "aca3_compress: stream capture of the compression");
+            cudaGraphExec_t ge = nullptr;
+            ce = cudaGraphInstantiate(&ge, cg, 0);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaGraphLaunch(ge, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], ctx->stream);  // no split inside the graph
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+            if (ge) cudaGraphExecDestroy(ge);
+            cudaGraphDestroy(cg);
+            if (ce != cudaSuccess) return cuda_fail(ce, "aca3_compress: graph launch of the compression");
+            ctx->count("graph_launch");
         }
         if (st != G3_OK) return st;
         G3_CUDA(cudaEventRecord(e1, ctx->stream));

@@ -96,7 +96,12 @@ g3_status g3_create(int device, void* cuda_stream, g3_ctx** out) {
     }
     e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    // the apply's far-field kernels run on this stream at the highest priority,
+    // next to the near-field stream on the context's stream: pending far-field
+    // CTAs are dispatched first, near-field CTAs fill the rest of the GPU
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_greatest);
     if (e != cudaSuccess) {
         g3_destroy(c);
         return cuda_fail(e, "side stream / events");

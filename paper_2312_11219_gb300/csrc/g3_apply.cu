@@ -533,11 +533,13 @@ static g3_status launch_apply_far(g3_ctx* ctx, const g3_factors* fa, Cx<T>* d_ab
     return G3_OK;
 }
 
-// Near field and far field of one apply.  With both present the near field
-// (an HBM stream) runs on the context's side stream next to the far-field
-// kernels (bound by latency and L2 traffic rather than HBM), forked from and
-// joined back into the main stream; both add into y atomically.  ev_side
-// brackets the near field (its device time).
+// Near field and far field of one apply.  With both present the far-field
+// kernels (bound by latency: short dependent chains per item) run on the
+// context's high-priority side stream and the near field (an HBM stream) on
+// the context's stream, forked and joined through events, so that pending
+// far-field CTAs are dispatched first and near-field CTAs take the rest of
+// the SMs; both add into y atomically.  ev_side brackets the near field
+// (its device time).
 template <class T>
 static g3_status apply_near_far(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, int Ku,
                                 int E, const Cx<T>* Wf, const Cx<T>* Wc, Cx<T>* y, Cx<T>* abuf) {
@@ -545,11 +547,16 @@ static g3_status apply_near_far(g3_ctx* ctx, const g3_tree* t, const g3_near* nf
     if (has_near && has_far) {
         G3_CUDA(cudaEventRecord(ctx->fork, ctx->stream));
         G3_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
-        G3_CUDA(cudaEventRecord(ctx->ev_side[0], ctx->side));
-        G3_TRY_NA(launch_apply_near<T>(ctx, ctx->side, t, nf, Ku, E, Wf, Wc, y));
-        G3_CUDA(cudaEventRecord(ctx->ev_side[1], ctx->side));
+        // swap the streams for the far-field launches
+        cudaStream_t main = ctx->stream;
+        ctx->stream = ctx->side;
+        const g3_status sf = launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y);
+        ctx->stream = main;
+        G3_TRY_NA(sf);
         G3_CUDA(cudaEventRecord(ctx->join, ctx->side));
-        G3_TRY_NA(launch_apply_far<T>(ctx, fa, abuf, Ku, E, Wf, Wc, y));
+        G3_CUDA(cudaEventRecord(ctx->ev_side[0], ctx->stream));
+        G3_TRY_NA(launch_apply_near<T>(ctx, ctx->stream, t, nf, Ku, E, Wf, Wc, y));
+        G3_CUDA(cudaEventRecord(ctx->ev_side[1], ctx->stream));
         G3_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->join, 0));
         return G3_OK;
     }

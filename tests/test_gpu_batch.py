@@ -99,3 +99,25 @@ def test_batch_rejects_bad_input(g3, ctx):
         g3.aca3_compress_batch(ctx, [T, T], [F, F], "slp", k1=np.zeros(10, dtype=np.int32))
     with pytest.raises(g3.G3Error):
         g3.aca3_compress_batch(ctx, [T], [F], "slp", unbatched=1)
+
+
+def test_compression_as_captured_graph_matches_plain_launches(g3):
+    """opts.graph: the queue resets and both persistent launches captured into
+    one CUDA graph give the same compression, block for block, as the plain
+    launches (and the same apply)."""
+    import torch
+    ctx = g3.Context(0)
+    w = workloads.get("lshape3072")
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+    F = g3.freqs_from_spec(ctx, w.freq)
+    Wd = torch.from_numpy(workloads.densities(w.E, w.freq.K, 3)).to("cuda")
+    for ker in ("slp", "dlp"):
+        fa = g3.aca3_compress(ctx, T, F, ker, prec="mixed", eps3=w.eps3)
+        fg = g3.aca3_compress(ctx, T, F, ker, prec="mixed", eps3=w.eps3, graph=1)
+        assert np.array_equal(fa.ranks(), fg.ranks())
+        sa, sg = fa.stats(), fg.stats()
+        assert sa["entries"] == sg["entries"] and sa["factor_bytes"] == sg["factor_bytes"]
+        assert ctx.kernel_launches().get("graph_launch", 0) >= 1
+        ya = g3.apply_gcq(ctx, T, None, fa, Wd)
+        yg = g3.apply_gcq(ctx, T, None, fg, Wd)
+        assert torch.linalg.norm(ya - yg) <= 1e-6 * torch.linalg.norm(ya)
