@@ -150,8 +150,9 @@ typedef struct {
                              context's stream and launched as one graph; blocks that spill
                              rerun as plain launches.  The low-rank / dense split of the
                              device time is not available then (ms_lowrank = ms).  Not
-                             with unbatched.  The context's stream must not be capturing
-                             already.  0 (default) = plain launches                      */
+                             with unbatched.  The graph is captured and launched on the
+                             context's side stream, ordered after and joined back into the
+                             context's stream.  0 (default) = plain launches              */
 } g3_opts;
 
 /* Statistics of one compression. */

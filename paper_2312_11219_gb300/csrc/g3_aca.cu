@@ -304,7 +304,20 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         // the queue resets and both persistent launches become one graph launch
         const bool graph = o.graph && round == 0 && !o.unbatched;
         cudaGraph_t cg = nullptr;
-        if (graph) G3_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        cudaStream_t main_stream = ctx->stream;
+        if (graph) {
+            // captured on the context's side stream (the context's stream may be
+            // the legacy default stream, which cannot be captured), ordered
+            // after the work already on the context's stream
+            G3_CUDA(cudaEventRecord(ctx->fork, main_stream));
+            G3_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+            ctx->stream = ctx->side;
+            const cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+            if (ce != cudaSuccess) {
+                ctx->stream = main_stream;
+                return cuda_fail(ce, "aca3_compress: cudaStreamBeginCapture");
+            }
+        }
         G3_CUDA(cudaMemsetAsync(d_head.p, 0, 2 * sizeof(int), ctx->stream));
         G3_CUDA(cudaMemsetAsync(d_spill_n.p, 0, sizeof(int), ctx->stream));
         G3_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
@@ -380,16 +393,20 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         }
         if (graph) {
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &cg);
-            if (st != G3_OK) {
+            if (st != G3_OK || ce != cudaSuccess) {
+                ctx->stream = main_stream;
                 if (cg) cudaGraphDestroy(cg);
-                return st;
+                if (st != G3_OK) return st;
+                return cuda_fail(ce, "aca3_compress: stream capture of the compression");
             }
-            if (ce != cudaSuccess) return cuda_fail(ce, "aca3_compress: stream capture of the compression");
             cudaGraphExec_t ge = nullptr;
             ce = cudaGraphInstantiate(&ge, cg, 0);
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, ctx->stream);
             if (ce == cudaSuccess) ce = cudaGraphLaunch(ge, ctx->stream);
             if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], ctx->stream);  // no split inside the graph
+            if (ce == cudaSuccess) ce = cudaEventRecord(ctx->join, ctx->stream);
+            ctx->stream = main_stream;
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->stream, ctx->join, 0);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
             if (ge) cudaGraphExecDestroy(ge);
             cudaGraphDestroy(cg);

@@ -1075,43 +1075,6 @@ __device__ int recompress(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, in
         R[a * ld + b].y *= sc;
     }
     __syncthreads();
-    if (r <= 32) {
-        // one warp per matrix (warp 0: R_U, warp 1: R_V), synchronised by the
-        // warp alone: step k, lane j > k scales R[k][j], then lane j updates
-        // its column R[i][j] -= conj(R[k][i]) R[k][j] for k < i <= j
-        if (wid < 2) {
-            Cx<double>* R = wid == 0 ? RU : RV;
-            double* rdg = wid == 0 ? S.rdU : S.rdV;
-            bool bad = false;
-            const int j = lane;
-            for (int k = 0; k < r; ++k) {
-                const double dkk = R[k * ld + k].x;
-                const bool ok = dkk > 1e-24;
-                bad |= !ok;
-                const double irkk = ok ? rsqrt_pivot(dkk) : 0.0;
-                if (j > k && j < r) {
-                    R[k * ld + j].x *= irkk;
-                    R[k * ld + j].y *= irkk;
-                }
-                __syncwarp();
-                if (j > k && j < r) {
-                    const Cx<double> rkj = R[k * ld + j];
-                    for (int i = k + 1; i <= j; ++i) {
-                        const Cx<double> rki = R[k * ld + i];
-                        R[i * ld + j].x -= rki.x * rkj.x + rki.y * rkj.y;  // conj(R[k][i]) R[k][j]
-                        R[i * ld + j].y -= rki.x * rkj.y - rki.y * rkj.x;
-                    }
-                }
-                if (lane == 0) {
-                    R[k * ld + k] = Cx<double>{dkk * irkk, 0.0};  // sqrt(dkk)
-                    rdg[k] = irkk;                                 // its reciprocal
-                }
-                __syncwarp();
-            }
-            if (lane == 0 && bad) S.flag = 1;
-        }
-        __syncthreads();
-    } else
     for (int k = 0; k < r; ++k) {
         const int tail = r - k - 1;
         // row k of both matrices (the diagonal itself is written after the sync)
