@@ -192,6 +192,7 @@ g3_status g3_freqs_bdf2(g3_ctx* ctx, int K, double lambda, double dt, g3_freqs**
     g3_freqs* f = new (std::nothrow) g3_freqs();
     if (!f) return fail(G3_ENOMEM, "g3_freqs_bdf2: out of host memory");
     f->ctx = ctx;
+    f->device = ctx->device;
     f->kind = 0;
     f->K = K;
     f->Ku = K / 2 + 1;
@@ -244,6 +245,7 @@ g3_status g3_freqs_gcq(g3_ctx* ctx, int NQ, double dt_min, double dt_max, g3_fre
     g3_freqs* f = new (std::nothrow) g3_freqs();
     if (!f) return fail(G3_ENOMEM, "g3_freqs_gcq: out of host memory");
     f->ctx = ctx;
+    f->device = ctx->device;
     f->kind = 1;
     f->K = NQ;
     f->Ku = NQ / 2;
@@ -322,6 +324,7 @@ g3_status g3_freqs_from_array(g3_ctx* ctx, const double* s_re_im, int K, g3_freq
     g3_freqs* f = new (std::nothrow) g3_freqs();
     if (!f) return fail(G3_ENOMEM, "g3_freqs_from_array: out of host memory");
     f->ctx = ctx;
+    f->device = ctx->device;
     f->kind = 2;
     f->K = K;
     f->Ku = (int)uniq.size();
@@ -361,7 +364,7 @@ g3_status g3_freqs_get(const g3_freqs* f, double* s, double* omega, int32_t* uni
 
 g3_status g3_freqs_free(g3_freqs* f) {
     if (f) {
-        cudaSetDevice(f->ctx->device);
+        cudaSetDevice(f->device);
         delete f;
     }
     return G3_OK;
@@ -390,6 +393,7 @@ g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, co
     g3_tree* t = new (std::nothrow) g3_tree();
     if (!t) return fail(G3_ENOMEM, "build_cluster_tree: out of host memory");
     t->ctx = ctx;
+    t->device = ctx->device;
     t->ne = ne;
     t->nv = nv;
     t->leaf = leaf;
@@ -429,6 +433,7 @@ g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, in
     g3_tree* s = new (std::nothrow) g3_tree();
     if (!s) return fail(G3_ENOMEM, "g3_tree_subset: out of host memory");
     s->ctx = ctx;
+    s->device = ctx->device;
     s->ne = t->ne;
     s->nv = t->nv;
     s->leaf = t->leaf;
@@ -489,7 +494,7 @@ g3_status g3_tree_get(const g3_tree* t, int32_t* perm, int32_t* nodes, double* b
 
 g3_status g3_tree_free(g3_tree* t) {
     if (t) {
-        cudaSetDevice(t->ctx->device);
+        cudaSetDevice(t->device);
         delete t;
     }
     return G3_OK;
@@ -566,6 +571,7 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     g3_near* nf = new (std::nothrow) g3_near();
     if (!nf) return fail(G3_ENOMEM, "assemble_near: out of host memory");
     nf->ctx = ctx;
+    nf->device = ctx->device;
     nf->tree = t;
     nf->freqs = f;
     nf->prec = prec;
@@ -714,7 +720,7 @@ g3_status g3_near_get_block(const g3_near* nf, int block, double* out) {
 
 g3_status g3_near_free(g3_near* nf) {
     if (nf) {
-        cudaSetDevice(nf->ctx->device);
+        cudaSetDevice(nf->device);
         delete nf;
     }
     return G3_OK;
@@ -746,6 +752,7 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     g3_factors* fa = new (std::nothrow) g3_factors();
     if (!fa) return fail(G3_ENOMEM, "aca3_compress: out of host memory");
     fa->ctx = ctx;
+    fa->device = ctx->device;
     fa->tree = t;
     fa->freqs = f;
     fa->prec = prec;
@@ -840,6 +847,7 @@ g3_status aca3_compress_batch(g3_ctx* ctx, const g3_tree* const* trees, const g3
             return fail(G3_ENOMEM, "aca3_compress_batch: out of host memory");
         }
         fa->ctx = ctx;
+        fa->device = ctx->device;
         fa->tree = trees[j];
         fa->freqs = freqs[j];
         fa->prec = prec;
@@ -869,6 +877,7 @@ g3_status aca3_compress_separable(g3_ctx* ctx, const double* a, const double* b,
     g3_factors* fa = new (std::nothrow) g3_factors();
     if (!fa) return fail(G3_ENOMEM, "aca3_compress_separable: out of host memory");
     fa->ctx = ctx;
+    fa->device = ctx->device;
     fa->prec = prec;
     fa->kernel = G3_SEPARABLE;
     fa->Ku = Ku;
@@ -959,7 +968,7 @@ g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t
 
 g3_status g3_factors_free(g3_factors* fa) {
     if (fa) {
-        cudaSetDevice(fa->ctx->device);
+        cudaSetDevice(fa->device);
         delete fa;
     }
     return G3_OK;
@@ -1032,6 +1041,7 @@ static g3_status mlp_alloc(g3_ctx* ctx, const float* params, const float* mean, 
         m->inv_std[i] = inv_std ? inv_std[i] : 1.f;
     }
     m->ctx = ctx;
+    m->device = ctx->device;
     auto up = [&](g3::DevBuf& d, const void* src, size_t bytes) -> cudaError_t {
         cudaError_t e = d.alloc(bytes);
         if (e != cudaSuccess) return e;
@@ -1193,7 +1203,7 @@ g3_status g3_mlp_get(const g3_mlp* m, float* params, float* adam_m, float* adam_
 
 g3_status g3_mlp_free(g3_mlp* m) {
     if (!m) return G3_OK;
-    if (m->ctx) cudaSetDevice(m->ctx->device);
+    if (m->ctx) cudaSetDevice(m->device);
     delete m;
     return G3_OK;
 }

@@ -208,6 +208,7 @@ struct g3_ctx {
 
 struct g3_freqs {
     g3_ctx* ctx = nullptr;
+    int device = 0;                // the context's device (freeing needs no context)
     int kind = 0;  // 0 = bdf2, 1 = gcq, 2 = given by the caller
     int K = 0, Ku = 0;
     std::vector<double> s;      // [2K]
@@ -223,6 +224,7 @@ struct g3_freqs {
 
 struct g3_tree {
     g3_ctx* ctx = nullptr;
+    int device = 0;                // the context's device (freeing needs no context)
     int ne = 0, nv = 0, leaf = 0;
     int max_block = 0;             // cap of the larger side of a far block (0 = none)
     bool subset = false;           // a rank's share of another tree's blocks (g3_tree_subset)
@@ -245,6 +247,7 @@ struct g3_tree {
 
 struct g3_near {
     g3_ctx* ctx = nullptr;
+    int device = 0;                // the context's device (freeing needs no context)
     const g3_tree* tree = nullptr;
     int prec = 0, kernel = 0, Ku = 0, K = 0;
     std::vector<int32_t> order;       // near blocks (tree block ids) sorted by (row, col)
@@ -267,6 +270,7 @@ struct g3_near {
 
 struct g3_factors {
     g3_ctx* ctx = nullptr;
+    int device = 0;                // the context's device (freeing needs no context)
     const g3_tree* tree = nullptr;
     int prec = 0, kernel = 0, Ku = 0, K = 0, n_far = 0, Cmax = 0;
     int M_sep = 0, N_sep = 0;          // separable mode: one block
@@ -297,6 +301,7 @@ struct g3_factors {
 
 struct g3_mlp {
     g3_ctx* ctx = nullptr;
+    int device = 0;                // the context's device (freeing needs no context)
     g3::DevBuf d_params, d_m, d_v;     // float [G3_MLP_NP]: master weights, Adam moments
     g3::DevBuf d_t;                    // long long: Adam steps taken
     g3::DevBuf d_mean, d_inv_std;      // float [G3_MLP_NF]
