@@ -153,6 +153,16 @@ typedef struct {
                              with unbatched.  The graph is captured and launched on the
                              context's side stream, ordered after and joined back into the
                              context's stream.  0 (default) = plain launches              */
+    int whole_matrix;     /* 1 = the three-way ACA of the H-matrix as a whole (Section 4,
+                             first implementation remark): all admissible blocks share the
+                             frequency sequence and one fiber per cross; a face is every
+                             block's residual face (face ACA + recompression), the pivot the
+                             largest entry over all blocks, eq. (norm) summed over the blocks
+                             and the stopping test taken once for all (rank l - 1, no
+                             sampled confirmation); every block keeps the same number of
+                             crosses.  Low-rank faces only, one launch per cross; not with
+                             unbatched, the batch or the separable test tensor.
+                             0 (default) = block by block                                */
 } g3_opts;
 
 /* Statistics of one compression. */

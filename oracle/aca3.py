@@ -391,3 +391,126 @@ def aca3(op: BlockEntries, eps3: float, eps_face: float | None = None,
         fm = f.real * f.real + f.imag * f.imag if resid is None else resid
         fm = np.where(used, -1.0, fm)
         k = int(np.argmax(fm))
+
+
+class WholeResult:
+    """Three-way ACA of several blocks as one H-matrix: per block the faces
+    H_p^b = U_p^b (V_p^b)^H, and one fiber f_p shared by all blocks."""
+
+    def __init__(self, faces, fibers, pivots, computed, norm2_history):
+        self.faces = faces                 # faces[b][p] = (U, V)
+        self.fibers = fibers               # fibers[p] = f_p  [Ku]
+        self.pivots = pivots               # pivots[p] = (block, i, j, k)
+        self.computed = computed
+        self.norm2_history = norm2_history
+
+    @property
+    def rank(self) -> int:
+        return len(self.fibers)
+
+    def dense(self, b: int, M: int, N: int, Ku: int) -> np.ndarray:
+        out = np.zeros((M, N, Ku), dtype=np.complex128)
+        for (U, V), f in zip(self.faces[b], self.fibers):
+            out += (U @ V.conj().T)[:, :, None] * f[None, None, :]
+        return out
+
+
+def aca3_whole(ops: list, eps3: float, eps_face: float | None = None, s_abs: np.ndarray | None = None,
+               max_face_rank: int | None = None, k1: int = 0) -> WholeResult:
+    """The other choice of Section 4's first implementation remark: the
+    three-way ACA applied to the H-matrix as a whole.  The tensor is the
+    admissible part of the matrix over the (unique) frequencies; a face is
+    the H-matrix at k_l (every block's residual face compressed by ACA and
+    recompressed, as in `aca3`), the pivot is the largest entry of that face
+    over all blocks, and one fiber per cross serves every block:
+
+      H_l^b ~ ENTRY_b(:, :, k_l) - sum_{p<l} f_p[k_l] H_p^b
+      (b*, i, j) = argmax_b,i,j |H_l^b[i, j]|
+      f_l[k] = (ENTRY_b*(i, j, k) - sum_{p<l} H_p^b*[i, j] f_p[k]) / H_l^b*[i, j]
+      ||C^(l)||^2 = sum_b (eq. (norm) of block b)       ("evaluated for each
+                                                           block and summed up")
+      stop when ||H_l||_F ||f_l||_2 <= eps3 ||C^(l)||_F (||H_l||^2 = sum_b ||H_l^b||^2),
+      rank l - 1 as in Algorithm 1; k_{l+1} = argmax over unused k of |f_l[k]|.
+
+    A face that is zero in every block triggers the same extra frequency
+    tests as `aca3`.  The literal stopping test (no sampled confirmation)."""
+    if eps_face is None:
+        eps_face = eps3 / 100.0
+    nb = len(ops)
+    Ku = ops[0].Ku
+    faces: list[list] = [[] for _ in range(nb)]
+    dense_faces: list[list] = [[] for _ in range(nb)]
+    fibers: list[np.ndarray] = []
+    pivots: list[tuple] = []
+    used = np.zeros(Ku, dtype=bool)
+    norm2 = 0.0
+    hist: list[float] = []
+    k = k1
+    ell = 0
+
+    def block_face(b: int, kk: int):
+        op = ops[b]
+
+        def row_fn(i):
+            r = op.row(i, kk)
+            for (U, V), f in zip(faces[b], fibers):
+                r = r - f[kk] * (U[i, :] @ V.conj().T)
+            return r
+
+        def col_fn(j):
+            c = op.col(j, kk)
+            for (U, V), f in zip(faces[b], fibers):
+                c = c - f[kk] * (U @ V[j, :].conj())
+            return c
+
+        U, V = aca2(row_fn, col_fn, op.M, op.N, eps_face, max_face_rank)
+        return recompress(U, V, eps_face)
+
+    while True:
+        ell += 1
+        cand = [k] + [kk for kk in (Ku - 1, Ku // 2, int(np.argmax(s_abs)) if s_abs is not None else Ku - 1)]
+        new = None
+        for c_i, kk in enumerate(cand):
+            if c_i > 0 and (used[kk] or kk in cand[:c_i]):
+                continue
+            used[kk] = True
+            fl = [block_face(b, kk) for b in range(nb)]
+            if any(U.shape[1] > 0 for U, _ in fl):
+                new, k = fl, kk
+                break
+            if c_i == 0 and len(fibers) == 0:
+                pass
+        if new is None:
+            return WholeResult(faces, fibers, pivots, ell - 1, hist)
+        Hs = [U @ V.conj().T for U, V in new]
+        best, bp = -1.0, None
+        for b, H in enumerate(Hs):
+            mag = H.real * H.real + H.imag * H.imag
+            m = int(np.argmax(mag))
+            if mag.flat[m] > best:
+                best, bp = float(mag.flat[m]), (b, *divmod(m, ops[b].N))
+        b, ip, jp = bp
+        fib = ops[b].fiber(ip, jp)
+        for Hd, f in zip(dense_faces[b], fibers):
+            fib = fib - Hd[ip, jp] * f
+        f = fib / Hs[b][ip, jp]
+        add = 0.0
+        nH2 = 0.0
+        for bb in range(nb):
+            for Hd, fd in zip(dense_faces[bb], fibers):
+                add += 2.0 * (np.vdot(Hd, Hs[bb]) * np.vdot(fd, f)).real
+            nH2 += float(np.vdot(Hs[bb], Hs[bb]).real)
+        nf2 = float(np.vdot(f, f).real)
+        norm2 += add + nH2 * nf2
+        hist.append(norm2)
+        if np.sqrt(nH2 * nf2) <= eps3 * np.sqrt(norm2):
+            return WholeResult(faces, fibers, pivots, ell, hist)
+        for bb in range(nb):
+            faces[bb].append(new[bb])
+            dense_faces[bb].append(Hs[bb])
+        fibers.append(f)
+        pivots.append((b, ip, jp, k))
+        if used.all():
+            return WholeResult(faces, fibers, pivots, ell, hist)
+        fm = np.where(used, -1.0, f.real * f.real + f.imag * f.imag)
+        k = int(np.argmax(fm))

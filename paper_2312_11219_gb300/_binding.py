@@ -43,7 +43,7 @@ class Opts(C.Structure):
                 ("eps_face", C.c_double), ("max_blocks", C.c_int), ("dense_face_max", C.c_int),
                 ("literal_stop", C.c_int), ("mlp", C.c_void_p), ("mlp_use", C.c_int),
                 ("face_floor_scale", C.c_double), ("trunc_floor_scale", C.c_double), ("pivot_index", C.c_int),
-                ("graph", C.c_int)]
+                ("graph", C.c_int), ("whole_matrix", C.c_int)]
 
 
 class TrainOpts(C.Structure):

@@ -1,5 +1,7 @@
 // Host driver of the three-way ACA (kernel and device routines: g3_aca_dev.cuh;
 // kernel instantiations: g3_aca_slp.cu, g3_aca_dlp.cu, g3_aca_sep.cu).
+#include <cmath>
+
 #include "g3_aca_dev.cuh"
 
 namespace g3 {
@@ -19,6 +21,19 @@ G3_ACA_EXTERN_KIND(G3_SLP)
 G3_ACA_EXTERN_KIND(G3_DLP)
 G3_ACA_EXTERN_KIND(G3_SEPARABLE)
 G3_ACA_EXTERN_KIND(G3_GAL_SLP)
+
+#define G3_WHOLE_EXTERN(KER, T)                                                                              \
+    extern template g3_status launch_whole_t<KER, T>(g3_ctx*, AcaArgs<T>&, int, size_t, int, int, const double*, \
+                                                     WholeCand*, Cx<double>*, double*);                         \
+    extern template g3_status launch_whole_fiber_t<KER, T>(g3_ctx*, AcaArgs<T>&, int, int, int, int, Cx<double>*, \
+                                                           Cx<double>*, double*, int, const Cx<double>*,          \
+                                                           const double*, double*, double*);
+G3_WHOLE_EXTERN(G3_SLP, float)
+G3_WHOLE_EXTERN(G3_SLP, double)
+G3_WHOLE_EXTERN(G3_DLP, float)
+G3_WHOLE_EXTERN(G3_DLP, double)
+G3_WHOLE_EXTERN(G3_GAL_SLP, float)
+G3_WHOLE_EXTERN(G3_GAL_SLP, double)
 
 template <class T, int NT, bool DENSE>
 static g3_status launch_kind(g3_ctx* ctx, int kernel, AcaArgs<T>& A, int grid, size_t smem) {
@@ -568,8 +583,271 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     return G3_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Three-way ACA of the H-matrix as a whole (Section 4, first implementation
+// remark; kernels in g3_aca_dev.cuh): the host runs Algorithm 1's loop over
+// crosses with one face launch over all admissible blocks per cross, the
+// global pivot, one shared fiber and eq. (norm) summed over the blocks; the
+// literal stopping test (rank l - 1).  Low-rank faces for every block.
+// ---------------------------------------------------------------------------
+template <class T>
+static g3_status run_aca_whole_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel,
+                                 double eps3, const g3_opts& o) {
+    const int RF = o.face_rank_max > 0 ? std::min(o.face_rank_max, RF_MAX) : 48;
+    const double eps_face = o.eps_face > 0 ? o.eps_face : (sizeof(T) == 4 ? std::max(eps3 / 100.0, 1e-5) : eps3 / 100.0);
+    std::vector<BlockRange> ranges;
+    for (int b : t->far_index) {
+        const int32_t* r = &t->blocks[5 * (size_t)b];
+        ranges.push_back(BlockRange{r[0], r[1], r[2], r[3]});
+    }
+    const int n_far = (int)ranges.size();
+    const int Ku = fa->Ku, Cmax = Ku;
+    fa->n_far = n_far;
+    fa->ranges = ranges;
+    fa->r3.assign(n_far, 0);
+    fa->Cmax = Cmax;
+    if (n_far == 0) return far_plan_build(fa);
+    int Mmax = 0, Nmax = 0;
+    long long worst = 0;  // pool elements one cross can take
+    for (auto& r : ranges) {
+        const int M = r.re - r.rb, N = r.ce - r.cb;
+        Mmax = std::max(Mmax, M);
+        Nmax = std::max(Nmax, N);
+        worst += (long long)std::min(RF, std::min(M, N)) * (M + N) + Ku;
+    }
+    std::vector<int> queue(n_far);
+    std::iota(queue.begin(), queue.end(), 0);
+    std::stable_sort(queue.begin(), queue.end(), [&](int a, int b) {
+        return (long long)(ranges[a].re - ranges[a].rb) * (ranges[a].ce - ranges[a].cb) >
+               (long long)(ranges[b].re - ranges[b].rb) * (ranges[b].ce - ranges[b].cb);
+    });
+    constexpr int NT = 256;
+    const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
+                                std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>)) +
+                                (sizeof(T) == 4 ? 2 * (size_t)RS * RS * sizeof(Cx<T>) : 0);
+    const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>);
+    const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
+                             (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
+    const size_t smem = std::max(std::max(recomp_bytes, gram_bytes), tab_bytes);
+    const int grid = std::max(1, std::min(n_far, 2 * ctx->n_sm));
+    const size_t stride = al256(ws_bytes<T>(RF, Mmax, Nmax, Cmax, Ku));
+    DevBuf d_ws, d_ranges, d_queue, d_head, d_counters, d_ctr, d_rec, d_r3, d_normb, d_cand, d_hh, d_hself, d_fib,
+        d_ff, d_scal, d_tot;
+    G3_CUDA(d_ws.alloc(stride * grid));
+    G3_CUDA(d_ranges.alloc(n_far * sizeof(BlockRange)));
+    G3_CUDA(d_queue.alloc(n_far * sizeof(int)));
+    G3_CUDA(d_head.alloc(sizeof(int)));
+    G3_CUDA(d_counters.alloc(32 * sizeof(unsigned long long)));
+    G3_CUDA(d_ctr.alloc(sizeof(unsigned long long)));
+    G3_CUDA(d_rec.alloc((size_t)n_far * Cmax * sizeof(CrossRec)));
+    G3_CUDA(d_r3.alloc(n_far * sizeof(int)));
+    G3_CUDA(d_normb.alloc(n_far * sizeof(double)));
+    G3_CUDA(d_cand.alloc(n_far * sizeof(WholeCand)));
+    G3_CUDA(d_hh.alloc((size_t)n_far * Cmax * sizeof(Cx<double>)));
+    G3_CUDA(d_hself.alloc(n_far * sizeof(double)));
+    G3_CUDA(d_fib.alloc((size_t)Cmax * Ku * sizeof(Cx<double>)));
+    G3_CUDA(d_ff.alloc((size_t)(Cmax + 1) * sizeof(Cx<double>)));
+    G3_CUDA(d_scal.alloc(2 * sizeof(double)));
+    G3_CUDA(d_tot.alloc(2 * sizeof(double)));
+    G3_CUDA(cudaMemcpy(d_ranges.p, ranges.data(), n_far * sizeof(BlockRange), cudaMemcpyHostToDevice));
+    G3_CUDA(cudaMemcpy(d_queue.p, queue.data(), n_far * sizeof(int), cudaMemcpyHostToDevice));
+    G3_CUDA(cudaMemset(d_counters.p, 0, 32 * sizeof(unsigned long long)));
+    G3_CUDA(cudaMemset(d_ctr.p, 0, sizeof(unsigned long long)));
+    G3_CUDA(cudaMemset(d_normb.p, 0, n_far * sizeof(double)));
+    G3_CUDA(cudaMemset(d_r3.p, 0, n_far * sizeof(int)));
+    auto pool = std::make_shared<DevBuf>();
+    long long cap = 4 * worst;
+    G3_CUDA(pool->alloc((size_t)cap * sizeof(Cx<T>)));
+    AcaArgs<T> A{};
+    A.gf = t->gf;
+    A.gd = t->gd;
+    A.sd = f->d_sd.as<double2>();
+    A.sf = f->d_sf.as<float2>();
+    A.Ku = Ku;
+    A.k_maxabs = f->k_maxabs;
+    A.ranges = d_ranges.as<BlockRange>();
+    A.n_far = n_far;
+    A.queue = d_queue.as<int>();
+    A.queue_head = d_head.as<int>();
+    A.single = -1;
+    A.Cmax = Cmax;
+    A.RF = RF;
+    A.dense_max = -1;
+    A.sample_check = 0;
+    A.eps3 = eps3;
+    A.eps_face = eps_face;
+    A.face_floor = sizeof(T) == 4 ? eps_face * (o.face_floor_scale > 0 ? o.face_floor_scale : 1.0) : 0.0;
+    A.trunc_floor = sizeof(T) == 4 ? eps_face * (o.trunc_floor_scale > 0 ? o.trunc_floor_scale : 1.0) : 0.0;
+    A.no_recompress = o.no_recompress;
+    A.pool_ctr = d_ctr.as<unsigned long long>();
+    A.rec = d_rec.as<CrossRec>();
+    A.r3 = d_r3.as<int>();
+    A.counters = d_counters.as<unsigned long long>();
+    A.status = ctx->status.as<unsigned>();
+    A.ws = d_ws.as<char>();
+    A.ws_stride = stride;
+    A.Mmax = Mmax;
+    A.Nmax = Nmax;
+    auto face = [&](int kf, int nc) -> g3_status {
+        if (kernel == G3_SLP)
+            return launch_whole_t<G3_SLP, T>(ctx, A, grid, smem, kf, nc, d_normb.as<double>(), d_cand.as<WholeCand>(),
+                                             d_hh.as<Cx<double>>(), d_hself.as<double>());
+        if (kernel == G3_DLP)
+            return launch_whole_t<G3_DLP, T>(ctx, A, grid, smem, kf, nc, d_normb.as<double>(), d_cand.as<WholeCand>(),
+                                             d_hh.as<Cx<double>>(), d_hself.as<double>());
+        return launch_whole_t<G3_GAL_SLP, T>(ctx, A, grid, smem, kf, nc, d_normb.as<double>(), d_cand.as<WholeCand>(),
+                                             d_hh.as<Cx<double>>(), d_hself.as<double>());
+    };
+    auto fiber = [&](int pb, int pi, int pj, int nc) -> g3_status {
+        if (kernel == G3_SLP)
+            return launch_whole_fiber_t<G3_SLP, T>(ctx, A, pb, pi, pj, nc, d_fib.as<Cx<double>>(), d_ff.as<Cx<double>>(),
+                                                   d_scal.as<double>(), n_far, d_hh.as<Cx<double>>(),
+                                                   d_hself.as<double>(), d_normb.as<double>(), d_tot.as<double>());
+        if (kernel == G3_DLP)
+            return launch_whole_fiber_t<G3_DLP, T>(ctx, A, pb, pi, pj, nc, d_fib.as<Cx<double>>(), d_ff.as<Cx<double>>(),
+                                                   d_scal.as<double>(), n_far, d_hh.as<Cx<double>>(),
+                                                   d_hself.as<double>(), d_normb.as<double>(), d_tot.as<double>());
+        return launch_whole_fiber_t<G3_GAL_SLP, T>(ctx, A, pb, pi, pj, nc, d_fib.as<Cx<double>>(),
+                                                   d_ff.as<Cx<double>>(), d_scal.as<double>(), n_far,
+                                                   d_hh.as<Cx<double>>(), d_hself.as<double>(), d_normb.as<double>(),
+                                                   d_tot.as<double>());
+    };
+    std::vector<char> used(Ku, 0);
+    std::vector<WholeCand> cand(n_far);
+    std::vector<Cx<double>> fib((size_t)Ku);
+    double norm2 = 0.0;
+    int k = 0, R = 0, computed = 0;
+    unsigned status_all = 0;
+    cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
+    G3_CUDA(cudaEventRecord(e0, ctx->stream));
+    for (int ell = 0; ell < Ku; ++ell) {
+        // the face at k, else up to three more unused frequencies (zero faces everywhere)
+        const int tries[4] = {k, Ku - 1, Ku / 2, f->k_maxabs};
+        int pb = -1;
+        for (int c = 0; c < 4 && pb < 0; ++c) {
+            const int kk = tries[c];
+            bool dup = c > 0 && used[kk];
+            for (int d = 1; d < c; ++d) dup |= tries[d] == kk;
+            if (dup) continue;
+            // pool room for one more cross of every block
+            unsigned long long ctr = 0;
+            G3_CUDA(cudaMemcpy(&ctr, d_ctr.p, sizeof(ctr), cudaMemcpyDeviceToHost));
+            if ((long long)ctr + worst > cap) {
+                const long long ncap = std::max((long long)ctr + 4 * worst, cap + cap / 2);
+                DevBuf grown;
+                G3_CUDA(grown.alloc((size_t)ncap * sizeof(Cx<T>)));
+                G3_CUDA(cudaMemcpy(grown.p, pool->p, (size_t)ctr * sizeof(Cx<T>), cudaMemcpyDeviceToDevice));
+                take(*pool, grown);
+                cap = ncap;
+            }
+            A.pool = pool->as<Cx<T>>();
+            A.pool_cap = cap;
+            G3_CUDA(cudaMemsetAsync(d_head.p, 0, sizeof(int), ctx->stream));
+            G3_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
+            { const g3_status st_ = face(kk, ell); if (st_ != G3_OK) return st_; }
+            unsigned status = 0;
+            G3_CUDA(cudaMemcpyAsync(cand.data(), d_cand.p, n_far * sizeof(WholeCand), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+            G3_CUDA(cudaMemcpyAsync(&status, ctx->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+            G3_CUDA(cudaStreamSynchronize(ctx->stream));
+            status_all |= status;
+            if (status & ST_POOL_OVERFLOW) return fail(G3_EOVERFLOW, "aca3_compress: whole-matrix factor pool overflow");
+            used[kk] = 1;
+            ++computed;
+            double best = sizeof(T) == 4 ? 1.1754944e-38 : 2.2250738585072014e-308;
+            for (int b = 0; b < n_far; ++b)
+                if (cand[b].v > best) {
+                    best = cand[b].v;
+                    pb = b;
+                }
+            if (pb >= 0) k = kk;
+        }
+        if (pb < 0) break;  // zero faces at every tested frequency: the rank is ell
+        G3_CUDA(cudaMemsetAsync(d_tot.p, 0, 2 * sizeof(double), ctx->stream));
+        { const g3_status st_ = fiber(pb, cand[pb].i, cand[pb].j, ell); if (st_ != G3_OK) return st_; }
+        double scal[2], tot[2];
+        G3_CUDA(cudaMemcpyAsync(scal, d_scal.p, sizeof(scal), cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaMemcpyAsync(tot, d_tot.p, sizeof(tot), cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaMemcpyAsync(fib.data(), d_fib.as<Cx<double>>() + (size_t)ell * Ku, Ku * sizeof(Cx<double>),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaStreamSynchronize(ctx->stream));
+        norm2 += tot[0];
+        const double nH2 = tot[1], nf2 = scal[0];
+        if (std::sqrt(std::max(nH2 * nf2, 0.0)) <= eps3 * std::sqrt(std::max(norm2, 0.0))) break;  // rank ell
+        R = ell + 1;
+        bool all = true;
+        for (int q = 0; q < Ku; ++q) all &= used[q] != 0;
+        if (all) break;
+        double bv = -1.0;
+        int bk = -1;
+        for (int q = 0; q < Ku; ++q)
+            if (!used[q]) {
+                const double v = fib[q].x * fib[q].x + fib[q].y * fib[q].y;
+                if (v > bv) {
+                    bv = v;
+                    bk = q;
+                }
+            }
+        if (bk < 0) break;
+        k = bk;
+    }
+    G3_CUDA(cudaEventRecord(e1, ctx->stream));
+    G3_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    G3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    // every block keeps the R crosses before the dropped one
+    fa->r3.assign(n_far, R);
+    G3_CUDA(cudaMemcpy(d_r3.p, fa->r3.data(), n_far * sizeof(int), cudaMemcpyHostToDevice));
+    fa->rec.resize((size_t)n_far * Cmax);
+    G3_CUDA(cudaMemcpy(fa->rec.data(), d_rec.p, fa->rec.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
+    unsigned long long cnt[32];
+    G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
+    unsigned long long ctr = 0;
+    G3_CUDA(cudaMemcpy(&ctr, d_ctr.p, sizeof(ctr), cudaMemcpyDeviceToHost));
+    fa->pool = pool;
+    fa->pool_cap = cap;
+    take(fa->d_rec, d_rec);
+    take(fa->d_r3, d_r3);
+    fa->phases.assign((size_t)n_far * NPH, 0);
+    fa->cycles.assign(n_far, 0);
+    g3_stats& S = fa->stats;
+    S = g3_stats{};
+    S.n_far = n_far;
+    S.blocks_run = n_far;
+    S.entries = (int64_t)cnt[0];
+    S.crosses_computed = (int64_t)computed * n_far;
+    S.status_bits = (int32_t)(status_all & ~ST_POOL_OVERFLOW);
+    S.ms = ms;
+    S.ms_lowrank = ms;
+    S.ctas = grid;
+    for (int b = 0; b < n_far; ++b) {
+        const int M = ranges[b].re - ranges[b].rb, N = ranges[b].ce - ranges[b].cb;
+        S.crosses += R;
+        S.r3_max = std::max(S.r3_max, R);
+        S.dense_bytes += (int64_t)M * N * Ku * (int64_t)sizeof(Cx<T>);
+        for (int p = 0; p < R; ++p) {
+            const CrossRec& c = fa->rec[(size_t)b * Cmax + p];
+            S.face_rank_sum += c.r;
+            S.face_rank_max = std::max(S.face_rank_max, c.r);
+            S.factor_bytes += ((int64_t)c.r * (M + N) + Ku) * (int64_t)sizeof(Cx<T>);
+        }
+    }
+    (void)ctr;
+    return far_plan_build(fa);
+}
+
 g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel, int scheme,
                   double eps3, const g3_opts& o, const void* sep_a, const void* sep_b, const void* sep_c, int sep_R) {
+    if (o.whole_matrix) {
+        if (kernel == G3_SEPARABLE || o.unbatched)
+            return fail(G3_EUNSUPPORTED, "aca3_compress: whole_matrix applies to boundary element operators, not unbatched");
+        if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+            return fail(G3_EUNSUPPORTED, "aca3_compress: the Galerkin scheme is implemented for G3_SLP");
+        if (fa->Ku > KU_MAX) return fail(G3_EINVAL, "aca3_compress: %d unique frequencies exceed %d", fa->Ku, KU_MAX);
+        const int kk = scheme == G3_GALERKIN4x4 ? G3_GAL_SLP : kernel;
+        if (fa->prec == G3_MIXED) return run_aca_whole_t<float>(ctx, t, f, fa, kk, eps3, o);
+        return run_aca_whole_t<double>(ctx, t, f, fa, kk, eps3, o);
+    }
     if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
         return fail(G3_EUNSUPPORTED, "aca3_compress: the Galerkin scheme is implemented for G3_SLP");
     if (scheme == G3_GALERKIN4x4) kernel = G3_GAL_SLP;

@@ -2051,6 +2051,274 @@ __global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3(const AcaArgs<T
 }
 
 // ============================================================================
+// Three-way ACA of the H-matrix as a whole (Section 4, first implementation
+// remark): all admissible blocks share the frequency sequence k_l and one
+// fiber per cross; the pivot is the largest entry of the whole face and the
+// stopping test sums eq. (norm) over the blocks.  The host runs the loop
+// over crosses; per cross:
+//   k_aca3_face   one CTA per block (persistent queue): the block's residual
+//                 face at k_l (face ACA with the shared fibers of the earlier
+//                 crosses, already copied into each block's cross slots),
+//                 recompression, U' and V' in the pool, the block's largest
+//                 face entry (dense expansion), and the block's terms of
+//                 eq. (norm): <H_l^b, H_d^b> for d < l and ||H_l^b||^2;
+//   k_whole_fiber the shared fiber at the global pivot (block b*, i, j):
+//                 f_l[k] = (ENTRY - sum_p H_p^b*[i, j] f_p[k]) / H_l^b*[i, j],
+//                 and <f_l, f_d>, ||f_l||^2;
+//   k_whole_norm  copies f_l into every block's slot of cross l and adds the
+//                 blocks' eq. (norm) terms (per block and in total).
+// ============================================================================
+
+struct WholeCand {
+    double v;   // |H_l^b[i, j]|^2 of the block's largest entry (-1: zero face)
+    int i, j;
+};
+
+template <int KER, class T, int NT>
+__global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3_face(const AcaArgs<T> P, int kf, int nc,
+                                                                      const double* __restrict__ normb,
+                                                                      WholeCand* __restrict__ cand,
+                                                                      Cx<double>* __restrict__ hh_out,
+                                                                      double* __restrict__ hself_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockSh<T> S;
+    __shared__ int s_q;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const AcaArgs<T>& A = P;
+    const int RF = A.RF;
+    Cx<double>* shB = reinterpret_cast<Cx<double>*>(smem_raw);
+    const Ws<T> w = ws_carve<T>(A.ws + (size_t)blockIdx.x * A.ws_stride, RF, A.Mmax, A.Nmax, A.Cmax, A.Ku);
+    for (;;) {
+        if (tid == 0) {
+            const int q = atomicAdd(A.queue_head, 1);
+            s_q = q < A.n_far ? q : -1;
+        }
+        __syncthreads();
+        const int qi = s_q;
+        __syncthreads();
+        if (qi < 0) break;
+        const int blk = A.queue[qi];
+        if (tid == 0) {
+            const BlockRange br = A.ranges[blk];
+            S.rb = br.rb;
+            S.cb = br.cb;
+            S.M = br.re - br.rb;
+            S.N = br.ce - br.cb;
+            S.blk = blk;
+            S.ncross = nc;
+            S.pre[0] = 0;
+            for (int p = 0; p < nc; ++p) {
+                const CrossRec cr = A.rec[(size_t)blk * A.Cmax + p];
+                S.off[p] = cr.off;
+                S.r[p] = cr.r;
+                S.pre[p + 1] = S.pre[p] + cr.r;
+            }
+            S.norm2 = normb[blk];
+            S.entries = 0;
+            S.raw = 0;
+            for (int i = 0; i < NSUB; ++i) S.sub[i] = 0;
+            S.k = kf;
+        }
+        __syncthreads();
+        const int M = S.M, N = S.N;
+        bool ok = M <= A.Mmax && N <= A.Nmax;
+        int r = ok ? face_aca<KER, T, NT>(A, w, S, kf, smem_raw) : 0;
+        int rn = 0;
+        const Cx<T>* tU = nullptr;
+        const Cx<T>* tV = nullptr;
+        int ldT = 0;
+        bool raw = false;
+        if (r > 0) {
+            rn = A.no_recompress ? -1 : recompress<T, NT>(A, w, S, r, shB, &tU, &tV, &ldT);
+            raw = rn < 0;
+            if (raw) rn = r;
+        }
+        // the cross slot: U' (M x rn), V' (N x rn), then the shared fiber (Ku)
+        if (tid == 0) {
+            const long long need = (long long)rn * (M + N) + A.Ku;
+            const unsigned long long o = atomicAdd(A.pool_ctr, (unsigned long long)need);
+            if ((long long)o + need > A.pool_cap) {
+                atomicOr(A.status, ST_POOL_OVERFLOW);
+                S.new_off = -1;
+            } else {
+                S.new_off = (long long)o;
+            }
+        }
+        __syncthreads();
+        const long long off = S.new_off;
+        if (off < 0) {
+            if (tid == 0) {
+                cand[blk] = WholeCand{-1.0, 0, 0};
+                A.rec[(size_t)blk * A.Cmax + nc] = CrossRec{-1, 0, 0, 0, kf};  // no slot (overflow status set)
+            }
+            for (int d = tid; d < nc; d += NT) hh_out[(size_t)blk * A.Cmax + d] = Cx<double>{0, 0};
+            if (tid == 0) hself_out[blk] = 0.0;
+            __syncthreads();
+            continue;
+        }
+        Cx<T>* Un = A.pool + off;
+        Cx<T>* Vn = A.pool + off + (long long)rn * M;
+        if (rn > 0) {
+            if (raw) {
+                for (int e = tid; e < rn * M; e += NT) Un[e] = w.uw[(size_t)(e / M) * A.Mmax + e % M];
+                for (int e = tid; e < rn * N; e += NT) Vn[e] = w.vw[(size_t)(e / N) * A.Nmax + e % N];
+            } else {
+                for (int e = tid; e < (M + N) * rn; e += NT) {
+                    const int row = e % (M + N), b = e / (M + N);
+                    const bool isU = row < M;
+                    const int i = isU ? row : row - M;
+                    const Cx<T>* src = isU ? w.uw + i : w.vw + i;
+                    const size_t ld = isU ? A.Mmax : A.Nmax;
+                    const Cx<T>* Tm = isU ? tU : tV;
+                    Cx<T> acc{0, 0};
+                    for (int a = 0; a < r; ++a) cfma(acc, src[(size_t)a * ld], Tm[a * ldT + b]);
+                    (isU ? Un + i : Vn + i)[(long long)b * (isU ? M : N)] = acc;
+                }
+            }
+        }
+        __syncthreads();
+        // the block's largest face entry: dense expansion of U' V'^H, one
+        // entry per thread and pass (ties to the smallest row-major index)
+        ArgMaxT<T> best = amax_none<T>();
+        if (rn > 0)
+            for (long long e = tid; e < (long long)M * N; e += NT) {
+                const int i = (int)(e / N), j = (int)(e - (long long)i * N);
+                Cx<T> h{0, 0};
+                for (int b = 0; b < rn; ++b) cfmac(h, ldcx(Un + (long long)b * M + i), ldcx(Vn + (long long)b * N + j));
+                best = amax_better(best, ArgMaxT<T>{cabs2(h), (int)e});
+            }
+        best = block_argmax<NT>(best, S.am);
+        // eq. (norm) terms of the block: <H_l^b, H_d^b> (d < nc) and ||H_l^b||^2
+        for (int d = tid; d < nc; d += NT) S.hh[d] = Cx<double>{0, 0};
+        if (tid == 0) S.hself = 0.0;
+        __syncthreads();
+        if (rn > 0) norm_grams<T, NT>(A, S, Un, Vn, rn, reinterpret_cast<Cx<T>*>(smem_raw));
+        __syncthreads();
+        for (int d = tid; d < nc; d += NT) hh_out[(size_t)blk * A.Cmax + d] = S.hh[d];
+        if (tid == 0) {
+            hself_out[blk] = S.hself;
+            const bool have = rn > 0 && best.v >= 0 && best.i >= 0 && best.i < M * N;
+            cand[blk] = have ? WholeCand{(double)best.v, best.i / N, best.i % N} : WholeCand{-1.0, 0, 0};
+            A.rec[(size_t)blk * A.Cmax + nc] = CrossRec{off, rn, have ? best.i / N : 0, have ? best.i % N : 0, kf};
+            A.r3[blk] = nc + 1;
+            atomicAdd(&A.counters[0], (unsigned long long)S.entries);
+        }
+        __syncthreads();
+    }
+}
+
+// the shared fiber of cross nc at the pivot (block pb, local i, j): one CTA
+template <int KER, class T, int NT>
+__global__ void __launch_bounds__(NT) k_whole_fiber(const AcaArgs<T> A, int pb, int pi, int pj, int nc,
+                                                    Cx<double>* __restrict__ fib,   // [Cmax][Ku] shared fibers
+                                                    Cx<double>* __restrict__ ff,    // [Cmax]: <f_nc, f_d>, then ||f||^2
+                                                    double* __restrict__ scal) {    // [0] ||f||^2 [1] |H_pivot|^2
+    __shared__ Cx<double> hp[KU_MAX];
+    __shared__ Cx<double> hpiv;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const BlockRange br = A.ranges[pb];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    // H_p^pb[i, j] for the earlier crosses and the new one
+    for (int p = tid; p <= nc; p += NT) {
+        const CrossRec cr = A.rec[(size_t)pb * A.Cmax + p];
+        const Cx<T>* U = A.pool + cr.off;
+        const Cx<T>* V = U + (long long)cr.r * M;
+        Cx<T> h{0, 0};
+        for (int t = 0; t < cr.r; ++t) cfmac(h, U[(long long)t * M + pi], V[(long long)t * N + pj]);
+        if (p < nc) hp[p] = ccast<double>(h);
+        else hpiv = ccast<double>(h);
+    }
+    __syncthreads();
+    const Cx<double> hv = hpiv;
+    const double h2 = hv.x * hv.x + hv.y * hv.y;
+    Cx<double>* fn = fib + (size_t)nc * A.Ku;
+    for (int k = tid; k < A.Ku; k += NT) {
+        Cx<double> e = ccast<double>(ent<KER, T>(A, br.rb + pi, br.cb + pj, k));
+        for (int p = 0; p < nc; ++p) {
+            const Cx<double> hf = cmul(hp[p], fib[(size_t)p * A.Ku + k]);
+            e.x -= hf.x;
+            e.y -= hf.y;
+        }
+        fn[k] = h2 > 0 ? cdiv(e, hv) : Cx<double>{0, 0};
+    }
+    __syncthreads();
+    // <f_nc, f_d> = sum_k f_nc[k] conj(f_d[k]) for d < nc, and ||f_nc||^2
+    for (int d = wid; d <= nc; d += NT / 32) {
+        const Cx<double>* fd = fib + (size_t)d * A.Ku;
+        Cx<double> acc{0, 0};
+        for (int k = lane; k < A.Ku; k += 32) cfmac(acc, fn[k], fd[k]);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        if (lane == 0) ff[d] = acc;
+    }
+    if (tid == 0) scal[1] = h2;
+    __syncthreads();
+    if (tid == 0) scal[0] = ff[nc].x;
+    if (tid == 0 && threadIdx.x == 0) atomicAdd(&A.counters[0], (unsigned long long)A.Ku);
+}
+
+// copy the shared fiber of cross nc into every block's slot; add the blocks'
+// eq. (norm) terms: per block 2 Re sum_d <H_nc^b, H_d^b><f_nc, f_d> + ||H_nc^b||^2 ||f||^2
+// (into normb), in total (tot[0]) and sum_b ||H_nc^b||^2 (tot[1])
+template <class T>
+__global__ void k_whole_norm(const AcaArgs<T> A, int nc, const Cx<double>* __restrict__ fib,
+                             const Cx<double>* __restrict__ ff, const Cx<double>* __restrict__ hh,
+                             const double* __restrict__ hself, double* __restrict__ normb,
+                             double* __restrict__ tot) {
+    const int blk = blockIdx.x;
+    const BlockRange br = A.ranges[blk];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const CrossRec cr = A.rec[(size_t)blk * A.Cmax + nc];
+    const Cx<double>* fn = fib + (size_t)nc * A.Ku;
+    if (cr.off >= 0) {
+        Cx<T>* fs = A.pool + cr.off + (long long)cr.r * (M + N);
+        for (int k = threadIdx.x; k < A.Ku; k += blockDim.x) fs[k] = ccast<T>(fn[k]);
+    }
+    double add = 0.0;
+    for (int d = threadIdx.x; d < nc; d += blockDim.x) {
+        const Cx<double> a = hh[(size_t)blk * A.Cmax + d], b = ff[d];
+        add += 2.0 * (a.x * b.x - a.y * b.y);
+    }
+    add = warp_sum(add);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = add;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += part[q];
+        const double own = hself[blk] * ff[nc].x;
+        normb[blk] += s + own;
+        atomicAdd(&tot[0], s + own);
+        atomicAdd(&tot[1], hself[blk]);
+    }
+}
+
+template <int KER, class T>
+g3_status launch_whole_t(g3_ctx* ctx, AcaArgs<T>& A, int grid, size_t smem, int kf, int nc, const double* normb,
+                         WholeCand* cand, Cx<double>* hh, double* hself) {
+    constexpr int NT = 256;
+    auto kfn = k_aca3_face<KER, T, NT>;
+    G3_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kfn<<<grid, NT, smem, ctx->stream>>>(A, kf, nc, normb, cand, hh, hself);
+    ctx->count("k_aca3_face");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+template <int KER, class T>
+g3_status launch_whole_fiber_t(g3_ctx* ctx, AcaArgs<T>& A, int pb, int pi, int pj, int nc, Cx<double>* fib,
+                               Cx<double>* ff, double* scal, int n_far, const Cx<double>* hh, const double* hself,
+                               double* normb, double* tot) {
+    k_whole_fiber<KER, T, 256><<<1, 256, 0, ctx->stream>>>(A, pb, pi, pj, nc, fib, ff, scal);
+    ctx->count("k_whole_fiber");
+    G3_CUDA(cudaGetLastError());
+    k_whole_norm<T><<<n_far, 128, 0, ctx->stream>>>(A, nc, fib, ff, hh, hself, normb, tot);
+    ctx->count("k_whole_norm");
+    G3_CUDA(cudaGetLastError());
+    return G3_OK;
+}
+
+// ============================================================================
 // launch helpers (instantiated once per kernel kind, in g3_aca_slp.cu,
 // g3_aca_dlp.cu and g3_aca_sep.cu, so that the kinds compile in parallel)
 // ============================================================================

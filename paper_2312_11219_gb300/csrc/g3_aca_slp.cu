@@ -23,6 +23,18 @@ G3_ACA_INST(double, 256, true)
 #endif
 #if !defined(G3_ACA_PART) || G3_ACA_PART == 3
 G3_ACA_INST(float, 384, false)
+template g3_status launch_whole_t<G3_SLP, float>(g3_ctx*, AcaArgs<float>&, int, size_t, int, int, const double*,
+                                               WholeCand*, Cx<double>*, double*);
+template g3_status launch_whole_fiber_t<G3_SLP, float>(g3_ctx*, AcaArgs<float>&, int, int, int, int, Cx<double>*,
+                                                     Cx<double>*, double*, int, const Cx<double>*, const double*,
+                                                     double*, double*);
+#endif
+#if !defined(G3_ACA_PART) || G3_ACA_PART == 2
+template g3_status launch_whole_t<G3_SLP, double>(g3_ctx*, AcaArgs<double>&, int, size_t, int, int, const double*,
+                                                WholeCand*, Cx<double>*, double*);
+template g3_status launch_whole_fiber_t<G3_SLP, double>(g3_ctx*, AcaArgs<double>&, int, int, int, int, Cx<double>*,
+                                                      Cx<double>*, double*, int, const Cx<double>*, const double*,
+                                                      double*, double*);
 #endif
 
 }  // namespace g3

@@ -423,3 +423,69 @@ def test_index_pivot_single_layer_block_meets_tolerance():
     res = aca3.aca3(op, eps3, s_abs=np.abs(s_u), dense_max=-1, pivot="index")
     C = res.dense(*D.shape)
     assert np.linalg.norm(D - C) <= 10 * eps3 * np.linalg.norm(D)
+
+
+# ---------------------------------------------------------------- 3D-ACA on the H-matrix as a whole
+
+def test_whole_matrix_rank_is_set_by_all_blocks():
+    """Two blocks, each a rank-1 separable tensor: per block the ACA needs one
+    cross each; on the matrix as a whole the fibers are shared, so two
+    blocks with different frequency dependence need two crosses (the
+    combined tensor has rank 2), and one when they share it."""
+    rng = np.random.default_rng(51)
+    a1, b1, a2, b2 = _rand(rng, 1, 12), _rand(rng, 1, 10), _rand(rng, 1, 9), _rand(rng, 1, 11)
+    c1, c2 = _rand(rng, 1, 8), _rand(rng, 1, 8)
+    for ca, cb, want in ((c1, c2, 2), (c1, 0.5 * c1, 1)):
+        ops = [aca3.SeparableBlock(a1, b1, ca), aca3.SeparableBlock(a2, b2, cb)]
+        res = aca3.aca3_whole(ops, 1e-8)
+        assert res.rank == want
+        for b, (op, M, N) in enumerate(((ops[0], 12, 10), (ops[1], 9, 11))):
+            D = op.dense()
+            assert np.linalg.norm(res.dense(b, M, N, 8) - D) <= 1e-12 * np.linalg.norm(D)
+        per_block = [aca3.aca3(aca3.SeparableBlock(a1, b1, ca), 1e-8).rank,
+                     aca3.aca3(aca3.SeparableBlock(a2, b2, cb), 1e-8).rank]
+        assert per_block == [1, 1] and res.rank >= max(per_block)
+
+
+def test_whole_matrix_norm_is_the_sum_of_block_norms():
+    """eq. (norm) evaluated per block and summed: the recursive norm equals
+    the Frobenius norm of all blocks' approximants together."""
+    rng = np.random.default_rng(52)
+    R = 3
+    ops = [aca3.SeparableBlock(_rand(rng, R, 14), _rand(rng, R, 12), _rand(rng, R, 9) * (0.3 ** np.arange(R))[:, None]),
+           aca3.SeparableBlock(_rand(rng, R, 10), _rand(rng, R, 13), _rand(rng, R, 9) * (0.3 ** np.arange(R))[:, None])]
+    res = aca3.aca3_whole(ops, 1e-10)
+    tot = sum(np.linalg.norm(res.dense(b, op.M, op.N, 9)) ** 2 for b, op in enumerate(ops))
+    assert abs(res.norm2_history[res.rank - 1] - tot) <= 1e-10 * tot
+    # the shared fiber is exact at its pivot entry (cross interpolation)
+    b, i, j, k = res.pivots[-1]
+    D = ops[b].dense()
+    C = res.dense(b, ops[b].M, ops[b].N, 9)
+    assert np.max(np.abs(C[i, j, :] - D[i, j, :])) <= 1e-10 * np.abs(D).max()
+
+
+def test_whole_matrix_bem_blocks_meet_tolerance():
+    """Eight admissible single-layer blocks of the cube compressed as one
+    H-matrix meet the tolerance on all blocks together, with a rank no
+    smaller than the largest per-block rank."""
+    w = workloads.get("cube768")
+    g = Q.Geometry(w.verts, w.tris)
+    T = tree.build(w.verts, w.tris, w.leaf, w.eta)
+    fs = freqs.frequency_set(w.freq)
+    s_u = fs["s"][fs["uniq"]]
+    ef = lambda I, J, s: Q.entries(g, "slp", I, J, s)
+    far = [b for b in range(T.blocks.shape[0]) if T.blocks[b, 4] == 1]
+    rng = np.random.default_rng(53)
+    pick = rng.choice(len(far), 8, replace=False)
+    ops, Ds = [], []
+    for p in pick:
+        rb, re, cb, ce, _ = T.blocks[far[p]]
+        ops.append(aca3.BemBlock(ef, T.perm[rb:re], T.perm[cb:ce], s_u))
+        Ds.append(Q.dense(g, "slp", s_u, rows=T.perm[rb:re], cols=T.perm[cb:ce]))
+    res = aca3.aca3_whole(ops, 1e-4, s_abs=np.abs(s_u))
+    err = sum(np.linalg.norm(res.dense(b, *D.shape) - D) ** 2 for b, D in enumerate(Ds)) ** 0.5
+    ref = sum(np.linalg.norm(D) ** 2 for D in Ds) ** 0.5
+    assert err <= 10 * 1e-4 * ref
+    per_block = [aca3.aca3(aca3.BemBlock(ef, op.rows, op.cols, s_u), 1e-4, s_abs=np.abs(s_u), dense_max=-1,
+                           sample_check=False).rank for op in ops]
+    assert res.rank >= max(per_block)
