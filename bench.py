@@ -421,6 +421,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                "apply_near_ms": 0.0, "apply_bytes": 0, "apply_near_bytes": 0, "factor_bytes": 0,
                "dense_bytes": 0, "crosses": 0, "stats": {}}
         for ker in kernels:
+            keep.pop(ker, None)   # the previous step's operator first: two at once do not fit the largest workloads
             nfs = [g3.assemble_near(ctx, T, F, ker, scheme=scheme, prec=prec) for T, F in zip(trees, freqs)]
             shape = {k: tune[ker][k] for k in ("threads", "dense_face_max")} if ker in tune else {}
             if batch:

@@ -86,18 +86,6 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
             const bool act = i < Mrow;
             T ax = 0, ay = 0;
             int j = 0;
-            // sixteen, then eight loads of the block's columns in flight per lane
-            for (; j + 16 <= N; j += 16) {
-                Cx<T> a[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) a[q] = act ? ldcx(Ak + (long long)(j + q) * Mrow + i) : Cx<T>{0, 0};
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const Cx<T> f = ldcx(wf + j + q), c = ldcx(wc + j + q);
-                    ax += a[q].x * (f.x + c.x) - a[q].y * (f.y - c.y);
-                    ay += a[q].x * (f.y + c.y) + a[q].y * (f.x - c.x);
-                }
-            }
             for (; j + 8 <= N; j += 8) {
                 Cx<T> a[8];
 #pragma unroll
