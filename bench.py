@@ -502,18 +502,24 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     near_gbs = r0["apply_near_bytes"] / (near_ms / 1e3) / 1e9 if near_ms > 0 else None
     # each part of the apply alone (the near field and the far field on the
     # context's stream, one after the other; in the timed apply they overlap)
-    parts = {"near_ms": 0.0, "near_bytes": 0, "far_ms": 0.0, "far_bytes": 0}
-    for ker in kernels:
-        trees, freqs, nfs, fas, _ = keep[ker]
-        for g, (T, nf, fa) in enumerate(zip(trees, nfs, fas)):
-            for part, a, b in (("near", nf, None), ("far", None, fa)):
-                best = None
-                for _ in range(3):
-                    g3.apply_gcq(ctx, T, a, b, Wds[g])
-                    la = ctx.last_apply()
-                    best = la if best is None or la["ms"] < best["ms"] else best
-                parts[part + "_ms"] += best["ms"]
-                parts[part + "_bytes"] += best["bytes"]
+    def measure_parts():
+        """Best of three for each part; a function so that no operator
+        outlives it (the A/B steps below need the memory)."""
+        parts = {"near_ms": 0.0, "near_bytes": 0, "far_ms": 0.0, "far_bytes": 0}
+        for ker in kernels:
+            trees, freqs, nfs, fas, _ = keep[ker]
+            for g, (T, nf, fa) in enumerate(zip(trees, nfs, fas)):
+                for part, a, b in (("near", nf, None), ("far", None, fa)):
+                    best = None
+                    for _ in range(3):
+                        g3.apply_gcq(ctx, T, a, b, Wds[g])
+                        la = ctx.last_apply()
+                        best = la if best is None or la["ms"] < best["ms"] else best
+                    parts[part + "_ms"] += best["ms"]
+                    parts[part + "_bytes"] += best["bytes"]
+        return parts
+
+    parts = measure_parts()
     apply_parts = {k: {"ms": parts[k + "_ms"], "bytes": parts[k + "_bytes"],
                        "gbs": parts[k + "_bytes"] / (parts[k + "_ms"] / 1e3) / 1e9 if parts[k + "_ms"] > 0 else None}
                    for k in ("near", "far")}

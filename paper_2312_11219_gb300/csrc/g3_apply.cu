@@ -191,8 +191,25 @@ __global__ void __launch_bounds__(NT) k_far_lr(const Cx<T>* __restrict__ pool, c
                 const Cx<T>* wf = Wf + br.cb + c0 + jl;
                 const Cx<T>* wc = Wc + br.cb + c0 + jl;
                 const Cx<T>* f0 = fg + h * PPT * Ku;
-#pragma unroll 4
-                for (int k = 0; k < Ku; ++k) {
+                // sixteen W loads (eight frequencies) in flight, then their FMAs
+                int k = 0;
+                for (; k + 8 <= Ku; k += 8) {
+                    Cx<T> a[8], b[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        a[q] = ldcx(wf + (long long)(k + q) * E);
+                        b[q] = ldcx(wc + (long long)(k + q) * E);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+#pragma unroll
+                        for (int u = 0; u < PPT; ++u) {
+                            const Cx<T> f = f0[u * Ku + k + q];
+                            cfma(x[u], f, a[q]);
+                            cfmac(z[u], f, b[q]);
+                        }
+                }
+                for (; k < Ku; ++k) {
                     const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
 #pragma unroll
                     for (int u = 0; u < PPT; ++u) {
@@ -323,8 +340,25 @@ __global__ void __launch_bounds__(NW * 32, 3) k_apply_far_dense(const Cx<T>* __r
             if (j < N) {
                 const Cx<T>* wf = Wf + br.cb + j;
                 const Cx<T>* wc = Wc + br.cb + j;
-#pragma unroll 4
-                for (int k = 0; k < Ku; ++k) {
+                // sixteen W loads (eight frequencies) in flight, then their FMAs
+                int k = 0;
+                for (; k + 8 <= Ku; k += 8) {
+                    Cx<T> a[8], b[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        a[q] = ldcx(wf + (long long)(k + q) * E);
+                        b[q] = ldcx(wc + (long long)(k + q) * E);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+#pragma unroll
+                        for (int p = 0; p < PG; ++p) {
+                            const Cx<T> f = fg[p * Ku + k + q];
+                            cfma(x[p], f, a[q]);
+                            cfmac(z[p], f, b[q]);
+                        }
+                }
+                for (; k < Ku; ++k) {
                     const Cx<T> a = ldcx(wf + (long long)k * E), b = ldcx(wc + (long long)k * E);
 #pragma unroll
                     for (int p = 0; p < PG; ++p) {

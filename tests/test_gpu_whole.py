@@ -1,7 +1,7 @@
 """GPU parity of the three-way ACA of the H-matrix as a whole (Section 4,
 first implementation remark; ``whole_matrix=1``) through the C ABI:
 
-* against the oracle's `aca3_whole` on the 192-triangle cube: the same
+* against the oracle's `aca3_whole` on the 768-triangle cube: the same
   number of crosses (within 2) and, in float64, the same first frequencies;
 * every block keeps the same number of crosses, at least the largest rank
   the block-wise compression needs (the literal stopping test in both);
@@ -22,14 +22,15 @@ def ctx(g3):
     return g3.Context(0)
 
 
-def test_whole_matrix_matches_oracle_cube192(g3, ctx):
-    w = workloads.get("cube192")
+def test_whole_matrix_matches_oracle_cube768(g3, ctx):
+    w = workloads.get("cube768")
     geo = O_q.Geometry(w.verts, w.tris)
     OT = O_tree.build(w.verts, w.tris, w.leaf, w.eta)
     fs = O_freqs.frequency_set(w.freq)
     su = fs["s"][fs["uniq"]]
     ef = lambda I, J, s: O_q.entries(geo, "slp", I, J, s)
     far = [b for b in range(OT.blocks.shape[0]) if OT.blocks[b, 4] == 1]
+    assert len(far) > 100
     ops = [O_aca.BemBlock(ef, OT.perm[OT.blocks[b, 0]:OT.blocks[b, 1]], OT.perm[OT.blocks[b, 2]:OT.blocks[b, 3]], su)
            for b in far]
     ref = O_aca.aca3_whole(ops, w.eps3, s_abs=np.abs(su))
