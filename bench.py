@@ -607,6 +607,33 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                                    mlp_use=args.mlp_use, pivot_index=pi, **shape).stats()
             pivot_ab[label] = {"aca_ms": stp["ms"], "crosses": stp["crosses"], "entries": stp["entries"],
                                "factor_bytes": stp["factor_bytes"]}
+    # where a step's wall time goes: the same calls as one step, each followed
+    # by a synchronize (untimed by the bench line; host work shows up here)
+    breakdown = None
+    if world == 1 and not batch:
+        keep.clear()
+        wall = {"tree": 0.0, "freqs": 0.0, "assemble_near": 0.0, "aca3_compress": 0.0, "apply_gcq": 0.0}
+
+        def lap(key, fn):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize(dev)
+            wall[key] += (time.perf_counter() - t0) * 1e3
+            return r
+
+        Tb = lap("tree", lambda: make_tree(ws[0]))
+        Fb = lap("freqs", lambda: g3.freqs_from_spec(ctx, ws[0].freq))
+        for ker in kernels:
+            shape = {k: tune[ker][k] for k in ("threads", "dense_face_max")} if ker in tune else {}
+            nfb = lap("assemble_near", lambda: g3.assemble_near(ctx, Tb, Fb, ker, scheme=scheme, prec=prec))
+            fab = lap("aca3_compress", lambda: g3.aca3_compress(ctx, Tb, Fb, ker, scheme=scheme, prec=prec,
+                                                                eps3=ws[0].eps3, mlp=net, mlp_use=args.mlp_use,
+                                                                **shape))
+            lap("apply_gcq", lambda: g3.apply_gcq(ctx, Tb, nfb, fab, Wds[0]))
+            del nfb, fab
+        breakdown = {k: round(v, 3) for k, v in wall.items()}
+        breakdown["note"] = "wall ms of one step's calls, each followed by a synchronize"
     if rank != 0:
         return None
     ms_step = t_max / args.steps
@@ -664,6 +691,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "peaks_source": peaks["source"],
         "learned": learned,
         "pivot_index_ab": pivot_ab,
+        "step_breakdown_ms": breakdown,
         "gcq_history": gcq_hist,
         "autotune": tune or None,
         "compression_entries_per_s": aca_eps,
