@@ -553,6 +553,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
             ab[label] = {"aca_ms": r["aca_ms"], "crosses": r["crosses"], "factor_bytes": r["factor_bytes"],
                          "spilled_blocks": sum(st["spilled_blocks"] for st in r["stats"].values()),
                          "pool_regrows": sum(st["pool_regrows"] for st in r["stats"].values())}
+        # the operators are not needed any more (their trees are): free them
+        # before the fresh contexts allocate theirs
+        for k in list(keep):
+            keep[k] = keep[k][:2] + (None, None, None)
         fresh = {}
         for label, (m, u) in {"plain_estimate": (None, 0), "predicted_pool": (net, 2)}.items():
             c2 = g3.Context(local_rank, stream.cuda_stream)
@@ -613,6 +617,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     if world == 1 and not batch:
         keep.clear()
         wall = {"tree": 0.0, "freqs": 0.0, "assemble_near": 0.0, "aca3_compress": 0.0, "apply_gcq": 0.0}
+        host = {}
 
         def lap(key, fn):
             torch.cuda.synchronize(dev)
@@ -631,9 +636,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                                                                 eps3=ws[0].eps3, mlp=net, mlp_use=args.mlp_use,
                                                                 **shape))
             lap("apply_gcq", lambda: g3.apply_gcq(ctx, Tb, nfb, fab, Wds[0]))
+            sb = fab.stats()
+            for k, v in sb["ms_host"].items():
+                host[k] = host.get(k, 0.0) + v
+            host["device_ms"] = host.get("device_ms", 0.0) + sb["ms"]
             del nfb, fab
         breakdown = {k: round(v, 3) for k, v in wall.items()}
-        breakdown["note"] = "wall ms of one step's calls, each followed by a synchronize"
+        breakdown["aca3_compress_parts"] = {k: round(v, 3) for k, v in host.items()}
+        breakdown["note"] = ("wall ms of one step's calls, each followed by a synchronize; the compression's "
+                             "own host timers (set-up, launch rounds, read-back, apply plan) and device time")
     if rank != 0:
         return None
     ms_step = t_max / args.steps

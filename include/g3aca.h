@@ -200,6 +200,10 @@ typedef struct {
                                  rest; face ACA table set-up, residual rows, residual
                                  columns, approximant norm, sample checks; of the residual
                                  rows and columns: the entries; 0 (reserved)              */
+    double ms_host[4];        /* host wall time of the call: set-up before the first launch
+                                 (predictor, queue, allocations, uploads), the launch rounds
+                                 up to the last synchronize, the read-back of records and
+                                 statistics, the apply's work lists                       */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */

@@ -61,7 +61,7 @@ class Stats(C.Structure):
                 ("dense_crosses", C.c_int64), ("ms_lowrank", C.c_double), ("ms_dense", C.c_double),
                 ("spilled_blocks", C.c_int32), ("mlp_used", C.c_int32), ("ms_mlp", C.c_double),
                 ("face_check_restarts", C.c_int64), ("stop_check_overrides", C.c_int64),
-                ("sub_cycles", C.c_int64 * 12)]
+                ("sub_cycles", C.c_int64 * 12), ("ms_host", C.c_double * 4)]
 
 
 def _sig(name, res, *args):
@@ -365,6 +365,7 @@ class Factors(_Handle):
         out["sub_cycles"] = dict(zip(["rc_gram", "rc_cholesky", "rc_core", "rc_jacobi", "rc_rest", "face_table",
                                       "face_rows", "face_columns", "face_norm", "face_samples", "line_entries"],
                                      list(s.sub_cycles)))
+        out["ms_host"] = dict(zip(["setup", "rounds", "readback", "apply_plan"], list(s.ms_host)))
         return out
 
     def ranks(self) -> np.ndarray:

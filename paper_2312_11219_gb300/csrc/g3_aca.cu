@@ -1,5 +1,6 @@
 // Host driver of the three-way ACA (kernel and device routines: g3_aca_dev.cuh;
 // kernel instantiations: g3_aca_slp.cu, g3_aca_dlp.cu, g3_aca_sep.cu).
+#include <chrono>
 #include <cmath>
 
 #include "g3_aca_dev.cuh"
@@ -72,6 +73,10 @@ static void take(DevBuf& dst, DevBuf& src) {
 template <class T>
 static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, double eps3, const g3_opts& o,
                            const void* sep_a, const void* sep_b, const void* sep_c, int sep_R) {
+    const auto th0 = std::chrono::steady_clock::now();
+    auto ms_since = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+    };
     const bool sep = kernel == G3_SEPARABLE;
     const int n_jobs = (int)jobs.size();
     const bool batched = n_jobs > 1;
@@ -314,6 +319,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     unsigned long long ctr = 0;
     const g3_tree* t0 = jobs[0].t;
     const g3_freqs* f0 = jobs[0].f;
+    const double ms_setup = ms_since(th0);
+    const auto th1 = std::chrono::steady_clock::now();
     for (int round = 0;; ++round) {
         // the first round can run as one captured CUDA graph (opts->graph):
         // the queue resets and both persistent launches become one graph launch
@@ -483,6 +490,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         cap += add;
         G3_CUDA(cudaMemcpy(d_queue.p, nq.data(), n_spill * sizeof(int), cudaMemcpyHostToDevice));
     }
+    const double ms_rounds = ms_since(th1);
+    const auto th2 = std::chrono::steady_clock::now();
     if (est > 0) scale = std::max(scale, 1.15 * (double)ctr / est);
     // give back what the estimate over-reserved: a pool much larger than its
     // use is moved into an exact-size buffer (its offsets stay valid)
@@ -577,8 +586,13 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
                 }
             }
         }
+        S.ms_host[0] = ms_setup;
+        S.ms_host[1] = ms_rounds;
+        S.ms_host[2] = ms_since(th2);
+        const auto th3 = std::chrono::steady_clock::now();
         const g3_status pst = far_plan_build(fa);
         if (pst != G3_OK) return pst;
+        S.ms_host[3] = ms_since(th3);
     }
     return G3_OK;
 }
@@ -621,7 +635,6 @@ static g3_status run_aca_whole_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* 
         return (long long)(ranges[a].re - ranges[a].rb) * (ranges[a].ce - ranges[a].cb) >
                (long long)(ranges[b].re - ranges[b].rb) * (ranges[b].ce - ranges[b].cb);
     });
-    constexpr int NT = 256;
     const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
                                 std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>)) +
                                 (sizeof(T) == 4 ? 2 * (size_t)RS * RS * sizeof(Cx<T>) : 0);
