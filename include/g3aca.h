@@ -308,6 +308,15 @@ g3_status g3_shard_rows(const int32_t* nodes, int n_nodes, const int32_t* blocks
  * and apply_gcq on it handle only those blocks; the apply's y then holds the
  * rank's rows, zero elsewhere, and the ranks' y add up to t's. */
 g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, int rank, g3_tree** out);
+/* The host half of build_cluster_tree_capped alone, with no context and no
+ * device: the same permutation (perm [ne], may be NULL) and block list
+ * (blocks [n_blocks*5] as from g3_tree_get, may be NULL; blocks_cap = its
+ * capacity in blocks, G3_EINVAL if smaller than the count) for host-side use
+ * and checks; n_blocks (may be NULL) gets the count.  Errors as
+ * build_cluster_tree. */
+g3_status g3_tree_partition_host(const double* verts, int nv, const int32_t* tris, int ne, int leaf, double eta,
+                                 int max_block, int32_t* perm, int32_t* blocks, int64_t blocks_cap,
+                                 int64_t* n_blocks);
 g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near);
 /* Copy to host (any output may be NULL):
  *   perm [ne]            cluster position -> original element index

@@ -14,5 +14,5 @@ first-frequency predictions size the factor pool, order the queue and seed k1.
 from ._binding import (  # noqa: F401
     EXPORTED, LIB_PATH, Context, Factors, Freqs, G3Error, Near, Tree, aca3_compress, aca3_compress_batch, autotune,
     aca3_compress_separable, apply_gcq, apply_gcq_noalloc, gcq_history, assemble_near, build_cluster_tree, freqs_from_spec,
-    g3_entries, shard_rows, tree_subset, g3_freqs_bdf2, g3_freqs_gcq, g3_freqs_from_array, MLP_NF, MLP_NP, Mlp, block_features, mlp_create, mlp_train,
+    g3_entries, shard_rows, tree_subset, tree_partition_host, g3_freqs_bdf2, g3_freqs_gcq, g3_freqs_from_array, MLP_NF, MLP_NP, Mlp, block_features, mlp_create, mlp_train,
 )

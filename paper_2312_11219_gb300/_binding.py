@@ -89,6 +89,8 @@ _sig("build_cluster_tree", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _pp)
 _sig("build_cluster_tree_capped", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _ci, _pp)
 _sig("g3_tree_info", _ci, _p, *(C.POINTER(_ci),) * 5)
 _sig("g3_shard_rows", _ci, _i32p, _ci, _i32p, _ci, _dp, _ci, _i32p, _dp, C.POINTER(_ci))
+_sig("g3_tree_partition_host", _ci, _dp, _ci, _i32p, _ci, _ci, C.c_double, _ci, _i32p, _i32p, C.c_int64,
+     C.POINTER(C.c_int64))
 _sig("g3_tree_subset", _ci, _p, _p, _i32p, _ci, _pp)
 _sig("g3_tree_get", _ci, _p, _i32p, _i32p, _dp, _i32p, _i32p)
 _sig("g3_tree_free", _ci, _p)
@@ -125,7 +127,7 @@ _sig("g3_factors_labels", _ci, _p, _p, _fp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_from_array", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
-            "build_cluster_tree", "build_cluster_tree_capped", "g3_shard_rows", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
+            "build_cluster_tree", "build_cluster_tree_capped", "g3_shard_rows", "g3_tree_partition_host", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
             "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_gcq_history", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
@@ -291,6 +293,22 @@ def build_cluster_tree(ctx: Context, verts, tris, leaf: int = 32, eta: float = 1
     _check(_lib.build_cluster_tree_capped(ctx.h, _ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0],
                                           leaf, eta, max_block, C.byref(h)), "build_cluster_tree")
     return Tree(h, (ctx,))
+
+
+def tree_partition_host(verts, tris, leaf: int, eta: float, max_block: int = 0) -> dict:
+    """The cluster tree's permutation and block list from the host builder
+    alone (no context or device): the same arrays as `Tree.get()`."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    nb = C.c_int64(0)
+    _check(_lib.g3_tree_partition_host(_ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0], leaf, eta,
+                                       max_block, None, None, 0, C.byref(nb)), "g3_tree_partition_host")
+    perm = np.empty(t.shape[0], dtype=np.int32)
+    blocks = np.empty((nb.value, 5), dtype=np.int32)
+    _check(_lib.g3_tree_partition_host(_ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0], leaf, eta,
+                                       max_block, _ptr(perm, C.c_int32), _ptr(blocks, C.c_int32), nb.value,
+                                       C.byref(nb)), "g3_tree_partition_host")
+    return {"perm": perm, "blocks": blocks}
 
 
 def shard_rows(nodes, blocks, n_ranks: int, cost=None) -> dict:

@@ -61,6 +61,47 @@ struct AcaJob {
     int first = 0, n = 0, Ku = 0;
 };
 
+// the kept records of every block, packed: block b's r3[b] records go to
+// out[off[b]], ...  (the device keeps the [n_far][Cmax] layout; the host
+// copy is compact)
+__global__ void __launch_bounds__(256) k_rec_pack(const CrossRec* __restrict__ rec, const int* __restrict__ r3,
+                                                  const long long* __restrict__ off, int Cmax, long long n,
+                                                  CrossRec* __restrict__ out) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / Cmax), p = (int)(idx % Cmax);
+        if (p < r3[b]) out[off[b] + p] = rec[idx];
+    }
+}
+
+// pinned host staging of the context (grown, never shrunk)
+static g3_status stage_ensure(g3_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->h_stage_bytes) return G3_OK;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    const cudaError_t e = cudaMallocHost(&ctx->h_stage, want);
+    if (e != cudaSuccess) {
+        ctx->h_stage = nullptr;
+        return cuda_fail(e, "pinned staging buffer");
+    }
+    ctx->h_stage_bytes = want;
+    return G3_OK;
+}
+
+// host copies of the records in compact form from a [n][Cmax] host array
+static void compact_records(g3_factors* fa, const std::vector<CrossRec>& full, int Cmax) {
+    const int n = (int)fa->r3.size();
+    fa->rec_off.assign((size_t)n + 1, 0);
+    for (int b = 0; b < n; ++b) fa->rec_off[b + 1] = fa->rec_off[b] + std::max(0, fa->r3[b]);
+    fa->rec.resize((size_t)fa->rec_off[n]);
+    for (int b = 0; b < n; ++b) {
+        const auto src = full.begin() + (size_t)b * Cmax;
+        std::copy(src, src + (fa->rec_off[b + 1] - fa->rec_off[b]), fa->rec.begin() + fa->rec_off[b]);
+    }
+}
+
 // move a device buffer's ownership
 static void take(DevBuf& dst, DevBuf& src) {
     dst.release();
@@ -507,14 +548,43 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
             cudaGetLastError();  // keep the large pool
         }
     }
+    // read-back: counters and ranks, then the kept records packed on the
+    // device and the per-block cycles, through the pinned staging buffer
     unsigned long long cnt[32];
     G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
     std::vector<int32_t> r3(n_far);
     G3_CUDA(cudaMemcpy(r3.data(), g_r3.p, n_far * sizeof(int), cudaMemcpyDeviceToHost));
-    std::vector<long long> phases((size_t)n_far * NPH);
-    G3_CUDA(cudaMemcpy(phases.data(), g_cyc.p, phases.size() * sizeof(long long), cudaMemcpyDeviceToHost));
-    std::vector<CrossRec> rec((size_t)n_far * Cmax);
-    G3_CUDA(cudaMemcpy(rec.data(), g_rec.p, rec.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
+    std::vector<long long> roff((size_t)n_far + 1, 0);
+    for (int b = 0; b < n_far; ++b) {
+        if (r3[b] < 0 || r3[b] > Cmax) return fail(G3_ECUDA, "aca3_compress: block %d has %d crosses", b, r3[b]);
+        roff[b + 1] = roff[b] + r3[b];
+    }
+    const size_t rec_bytes = (size_t)roff[n_far] * sizeof(CrossRec);
+    const size_t ph_bytes = (size_t)n_far * NPH * sizeof(long long);
+    {
+        const g3_status sst = stage_ensure(ctx, al256(rec_bytes) + ph_bytes);
+        if (sst != G3_OK) return sst;
+    }
+    CrossRec* h_rec = static_cast<CrossRec*>(ctx->h_stage);
+    long long* h_ph = reinterpret_cast<long long*>(static_cast<char*>(ctx->h_stage) + al256(rec_bytes));
+    {
+        DevBuf d_off, d_pack;
+        G3_CUDA(d_off.alloc(roff.size() * sizeof(long long)));
+        G3_CUDA(d_pack.alloc(std::max(rec_bytes, (size_t)16)));
+        G3_CUDA(cudaMemcpyAsync(d_off.p, roff.data(), roff.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        const long long n_all = (long long)n_far * Cmax;
+        const int g_pack = (int)std::min<long long>((n_all + 255) / 256, (long long)ctx->n_sm * 8);
+        k_rec_pack<<<std::max(g_pack, 1), 256, 0, ctx->stream>>>(g_rec.as<CrossRec>(), g_r3.as<int>(),
+                                                                 d_off.as<long long>(), Cmax, n_all,
+                                                                 d_pack.as<CrossRec>());
+        G3_CUDA(cudaGetLastError());
+        ctx->count("k_rec_pack");
+        if (rec_bytes > 0)
+            G3_CUDA(cudaMemcpyAsync(h_rec, d_pack.p, rec_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaMemcpyAsync(h_ph, g_cyc.p, ph_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        G3_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
     // per mesh: device slices (the whole buffers for a single mesh), host
     // copies and statistics; the pool is shared
     for (int j = 0; j < n_jobs; ++j) {
@@ -540,11 +610,13 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
             }
         }
         fa->r3.assign(r3.begin() + J.first, r3.begin() + J.first + J.n);
-        fa->phases.assign(phases.begin() + (size_t)J.first * NPH, phases.begin() + (size_t)(J.first + J.n) * NPH);
+        fa->phases.assign(h_ph + (size_t)J.first * NPH, h_ph + (size_t)(J.first + J.n) * NPH);
         fa->cycles.assign(J.n, 0);
         for (int b = 0; b < J.n; ++b)
             for (int i = 0; i < 7; ++i) fa->cycles[b] += fa->phases[(size_t)b * NPH + i];
-        fa->rec.assign(rec.begin() + (size_t)J.first * Cmax, rec.begin() + (size_t)(J.first + J.n) * Cmax);
+        fa->rec.assign(h_rec + roff[J.first], h_rec + roff[J.first + J.n]);
+        fa->rec_off.resize((size_t)J.n + 1);
+        for (int b = 0; b <= J.n; ++b) fa->rec_off[b] = roff[J.first + b] - roff[J.first];
         // batch-wide counters and times (a batched compression is one launch)
         g3_stats& S = fa->stats;
         S = g3_stats{};
@@ -575,7 +647,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
             S.r3_max = std::max(S.r3_max, fa->r3[b]);
             S.dense_bytes += (int64_t)M * N * J.Ku * (int64_t)sizeof(Cx<T>);
             for (int p = 0; p < fa->r3[b]; ++p) {
-                const CrossRec& c = fa->rec[(size_t)b * Cmax + p];
+                const CrossRec& c = fa->crec(b, p);
                 if (c.r < 0) {  // dense face
                     S.dense_crosses += 1;
                     S.factor_bytes += ((int64_t)M * N + J.Ku) * (int64_t)sizeof(Cx<T>);
@@ -811,8 +883,11 @@ static g3_status run_aca_whole_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* 
     // every block keeps the R crosses before the dropped one
     fa->r3.assign(n_far, R);
     G3_CUDA(cudaMemcpy(d_r3.p, fa->r3.data(), n_far * sizeof(int), cudaMemcpyHostToDevice));
-    fa->rec.resize((size_t)n_far * Cmax);
-    G3_CUDA(cudaMemcpy(fa->rec.data(), d_rec.p, fa->rec.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
+    {
+        std::vector<CrossRec> full((size_t)n_far * Cmax);
+        G3_CUDA(cudaMemcpy(full.data(), d_rec.p, full.size() * sizeof(CrossRec), cudaMemcpyDeviceToHost));
+        compact_records(fa, full, Cmax);
+    }
     unsigned long long cnt[32];
     G3_CUDA(cudaMemcpy(cnt, d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost));
     unsigned long long ctr = 0;
@@ -839,7 +914,7 @@ static g3_status run_aca_whole_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* 
         S.r3_max = std::max(S.r3_max, R);
         S.dense_bytes += (int64_t)M * N * Ku * (int64_t)sizeof(Cx<T>);
         for (int p = 0; p < R; ++p) {
-            const CrossRec& c = fa->rec[(size_t)b * Cmax + p];
+            const CrossRec& c = fa->crec(b, p);
             S.face_rank_sum += c.r;
             S.face_rank_max = std::max(S.face_rank_max, c.r);
             S.factor_bytes += ((int64_t)c.r * (M + N) + Ku) * (int64_t)sizeof(Cx<T>);

@@ -399,12 +399,24 @@ __device__ __forceinline__ Cx<T> shfl_xor_c(Cx<T> v, int o) {
     return Cx<T>{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
 }
 
-// gang size: the largest power of two <= 32 with L * G <= 2 NT
+// gang size G (a power of two <= 32) of a line of L outputs whose every
+// output sums W terms (quadrature points, then the earlier columns): the G
+// that minimises one thread's serial work, passes(G) * ceil(W / G) plus a
+// per-pass overhead of two terms, where passes(G) = ceil(L G / NT); ties go
+// to the smaller G (fewer passes)
 template <int NT>
-__device__ __forceinline__ int gang_size(int L) {
-    int G = 1;
-    while (G < 32 && L * (G * 2) <= 2 * NT) G *= 2;
-    return G;
+__device__ __forceinline__ int gang_size(int L, int W) {
+    int best = 1;
+    long long best_cost = -1;
+    for (int G = 1; G <= 32; G *= 2) {
+        const long long passes = ((long long)L * G + NT - 1) / NT;
+        const long long cost = passes * ((W + G - 1) / G + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = G;
+        }
+    }
+    return best;
 }
 
 // Per-face tables of the earlier crosses' columns, flattened over (p, t):
@@ -493,7 +505,7 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N;
     const int L = ROW ? N : M;
-    const int G = gang_size<NT>(L);
+    const int G = gang_size<NT>(L, F.ncol + m + (KER == G3_GAL_SLP ? 16 : 7));
     const int per = NT / G;
     const int part = tid % G;
     const long long* col = ROW ? F.colV : F.colU;

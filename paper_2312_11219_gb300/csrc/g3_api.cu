@@ -136,6 +136,7 @@ g3_status g3_destroy(g3_ctx* ctx) {
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->join) cudaEventDestroy(ctx->join);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     delete ctx;
     return G3_OK;
 }
@@ -928,7 +929,7 @@ g3_status g3_factors_get_block(const g3_factors* fa, int i, int32_t* r3, int32_t
     G3_TRY(use_device(fa->ctx));
     size_t ou = 0, ov = 0;
     for (int p = 0; p < nc; ++p) {
-        const CrossRec& c = fa->rec[(size_t)i * fa->Cmax + p];
+        const CrossRec& c = fa->crec(i, p);
         const bool dense = c.r < 0;
         const int rr = dense ? N : c.r;
         if (face_ranks) face_ranks[p] = rr;

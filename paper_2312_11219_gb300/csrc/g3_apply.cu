@@ -460,7 +460,7 @@ g3_status far_plan_build(g3_factors* fa) {
     for (int b = 0; b < fa->n_far; ++b) {
         const int r = fa->r3[b];
         if (r <= 0) continue;
-        if (fa->rec[(size_t)b * fa->Cmax].r < 0) {
+        if (fa->crec(b, 0).r < 0) {
             const int M = fa->ranges[b].re - fa->ranges[b].rb, N = fa->ranges[b].ce - fa->ranges[b].cb;
             dense.push_back(Item{(long long)r * M * N, b, 0});
             mmax = std::max(mmax, M);
@@ -470,13 +470,13 @@ g3_status far_plan_build(g3_factors* fa) {
         const int M = fa->ranges[b].re - fa->ranges[b].rb;
         const int N = fa->ranges[b].ce - fa->ranges[b].cb;
         for (int p = 0; p < r; ++p)
-            if (fa->rec[(size_t)b * fa->Cmax + p].r > RF_TS)
+            if (fa->crec(b, p).r > RF_TS)
                 return fail(G3_EUNSUPPORTED, "aca3_compress: face rank %d above the apply's limit %d",
-                            fa->rec[(size_t)b * fa->Cmax + p].r, RF_TS);
+                            fa->crec(b, p).r, RF_TS);
         for (int g = 0; g * FAR_PG < r; ++g) {
             long long c = 0;
             for (int p = g * FAR_PG; p < std::min(r, (g + 1) * FAR_PG); ++p)
-                c += (long long)fa->rec[(size_t)b * fa->Cmax + p].r * (M + N) + fa->Ku;
+                c += (long long)fa->crec(b, p).r * (M + N) + fa->Ku;
             (N <= FAR_NT / 2 ? narrow : wide).push_back(Item{c, b, g});
         }
     }
@@ -855,9 +855,9 @@ static g3_status run_apply_perfreq_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
             for (int c0 = 0; c0 < 2 * Ku; c0 += PF_NC)
                 for (int i0 = 0; i0 < M; i0 += PF_NI) items.insert(items.end(), {b, c0, i0, 0});
             for (int p = 0; p < fa->r3[b]; ++p)
-                if (fa->rec[(size_t)b * fa->Cmax + p].r > RF_TS)
+                if (fa->crec(b, p).r > RF_TS)
                     return fail(G3_EUNSUPPORTED, "apply_gcq: face rank %d above %d in the per-frequency apply",
-                                fa->rec[(size_t)b * fa->Cmax + p].r, RF_TS);
+                                fa->crec(b, p).r, RF_TS);
         }
     }
     const size_t n_items = items.size() / 4;

@@ -189,6 +189,8 @@ struct g3_ctx {
     g3::DevBuf scratch;      // apply scratch (cluster-order densities, partial y)
     g3::DevBuf status;       // device status word(s)
     g3::DevBuf stage_w, stage_y;  // device staging of host W / Y in apply_gcq
+    void* h_stage = nullptr;      // pinned host staging of read-backs (grown, never shrunk)
+    size_t h_stage_bytes = 0;
     cudaEvent_t ev[6] = {};
     // a second stream on which the apply runs its near field next to the far
     // field (fork / join through events; ev_side times the near field there)
@@ -283,7 +285,9 @@ struct g3_factors {
     std::vector<long long> cycles;     // per-block cycle totals
     std::vector<long long> phases;     // [n_far][8]: cycles per phase, then face ACA steps
     std::vector<int32_t> r3;
-    std::vector<g3::CrossRec> rec;     // host copy
+    std::vector<g3::CrossRec> rec;     // host copy, compact: block b's r3[b] records from rec_off[b]
+    std::vector<long long> rec_off;    // [n_far + 1]
+    const g3::CrossRec& crec(int b, int p) const { return rec[(size_t)rec_off[b] + p]; }
     std::vector<g3::BlockRange> ranges;
     g3_stats stats{};
     // far-field apply work lists, built when the compression ends and kept

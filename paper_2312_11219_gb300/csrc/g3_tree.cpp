@@ -86,13 +86,19 @@ struct Builder {
             for (int d = 1; d < 3; ++d)
                 if (ext[d] > ext[axis]) axis = d;
             const double* c = cen.data();
-            std::sort(idx.begin(), idx.end(), [c, axis](int32_t x, int32_t y) {
+            auto before = [c, axis](int32_t x, int32_t y) {
                 double cx = c[3 * (size_t)x + axis], cy = c[3 * (size_t)y + axis];
                 if (cx < cy) return true;
                 if (cy < cx) return false;
                 return x < y;
-            });
+            };
+            // the keys are unique (index tie-break), so a selection of the
+            // first h gives the same halves as a full sort; a child that is a
+            // leaf keeps the sorted order of its elements
             const int h = n / 2;
+            std::nth_element(idx.begin(), idx.begin() + h, idx.end(), before);
+            if (h <= leaf) std::sort(idx.begin(), idx.begin() + h, before);
+            if (n - h <= leaf) std::sort(idx.begin() + h, idx.end(), before);
             std::vector<int32_t> L(idx.begin(), idx.begin() + h), R(idx.begin() + h, idx.end());
             std::vector<int32_t>().swap(idx);
             int l = node(L, start);
@@ -314,4 +320,36 @@ void tree_index_blocks(g3_tree* t) {
 extern "C" g3_status g3_shard_rows(const int32_t* nodes, int n_nodes, const int32_t* blocks, int n_blocks,
                                    const double* cost, int n_ranks, int32_t* owner, double* load, int* n_units) {
     return g3::shard_rows_host(nodes, n_nodes, blocks, n_blocks, cost, n_ranks, owner, load, n_units);
+}
+
+// the host part of build_cluster_tree_capped alone (no context, no device):
+// the permutation and the block list, for host-side use and checks
+extern "C" g3_status g3_tree_partition_host(const double* verts, int nv, const int32_t* tris, int ne, int leaf,
+                                            double eta, int max_block, int32_t* perm, int32_t* blocks,
+                                            int64_t blocks_cap, int64_t* n_blocks) {
+    if (!verts || !tris || nv < 3 || ne < 1 || leaf < 1 || max_block < 0 || !(eta > 0) || !std::isfinite(eta))
+        return g3::fail(G3_EINVAL, "g3_tree_partition_host: bad argument");
+    for (long long i = 0; i < 3LL * nv; ++i)
+        if (!std::isfinite(verts[i]))
+            return g3::fail(G3_EINVAL, "g3_tree_partition_host: non-finite vertex coordinate at %lld", i);
+    g3_tree t;
+    t.ne = ne;
+    t.nv = nv;
+    t.leaf = leaf;
+    t.max_block = max_block;
+    t.eta = eta;
+    t.verts.assign(verts, verts + 3 * (size_t)nv);
+    t.tris.assign(tris, tris + 3 * (size_t)ne);
+    const g3_status st = g3::build_tree_host(&t);
+    if (st != G3_OK) return st;
+    const int64_t nb = (int64_t)(t.blocks.size() / 5);
+    if (n_blocks) *n_blocks = nb;
+    if (perm) std::copy(t.perm.begin(), t.perm.end(), perm);
+    if (blocks) {
+        if (blocks_cap < nb)
+            return g3::fail(G3_EINVAL, "g3_tree_partition_host: %lld blocks do not fit in %lld", (long long)nb,
+                            (long long)blocks_cap);
+        std::copy(t.blocks.begin(), t.blocks.end(), blocks);
+    }
+    return G3_OK;
 }

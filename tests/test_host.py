@@ -292,3 +292,35 @@ def test_shard_rows_partition_properties(built_lib):
         load = np.array([cost[o == k].sum() for k in range(n)])
         assert np.allclose(load, sh["load"])
         assert load.max() - load.min() <= ucost.max() + 1e-9
+
+
+@pytest.mark.parametrize("name,cap", [("cube48", 0), ("cube768", 0), ("cube768", 96), ("lshape768", 0),
+                                      ("sphere1280", 0), ("lshape3072", 0), ("lshape3072", 192)])
+def test_host_tree_partition_bit_exact(built_lib, name, cap):
+    """The library's host tree builder (the half of build_cluster_tree that
+    needs no device) gives the oracle's permutation and block list exactly,
+    with and without the far-block cap."""
+    sys.path.insert(0, ROOT)
+    import paper_2312_11219_gb300 as g3
+    from oracle import tree as O_tree
+    w = workloads.get(name)
+    got = g3.tree_partition_host(w.verts, w.tris, w.leaf, w.eta, cap)
+    ref = O_tree.build(w.verts, w.tris, w.leaf, w.eta, cap)
+    assert np.array_equal(got["perm"], ref.perm)
+    assert np.array_equal(got["blocks"], ref.blocks)
+
+
+def test_host_tree_partition_rejects_bad_input(built_lib):
+    sys.path.insert(0, ROOT)
+    import paper_2312_11219_gb300 as g3
+    w = workloads.get("cube48")
+    bad = w.tris.copy()
+    bad[3] = [0, 0, 1]                      # degenerate
+    with pytest.raises(g3.G3Error):
+        g3.tree_partition_host(w.verts, bad, w.leaf, w.eta)
+    bad = w.tris.copy()
+    bad[0, 0] = w.verts.shape[0]            # vertex index out of range
+    with pytest.raises(g3.G3Error):
+        g3.tree_partition_host(w.verts, bad, w.leaf, w.eta)
+    with pytest.raises(g3.G3Error):
+        g3.tree_partition_host(w.verts, w.tris, 0, w.eta)
