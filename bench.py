@@ -500,16 +500,17 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     near_ms = sum(r["apply_near_ms"] for r in recs) / len(recs)
     apply_gbs = r0["apply_bytes"] / (apply_ms / 1e3) / 1e9
     near_gbs = r0["apply_near_bytes"] / (near_ms / 1e3) / 1e9 if near_ms > 0 else None
-    # each part of the apply alone (the near field and the far field on the
-    # context's stream, one after the other; in the timed apply they overlap)
+    # each part of the apply alone (the near field, the far field) and both
+    # together as in the timed apply (the two overlap on two streams), each
+    # best of three on the operators of the last timed step
     def measure_parts():
         """Best of three for each part; a function so that no operator
         outlives it (the A/B steps below need the memory)."""
-        parts = {"near_ms": 0.0, "near_bytes": 0, "far_ms": 0.0, "far_bytes": 0}
+        parts = {"near_ms": 0.0, "near_bytes": 0, "far_ms": 0.0, "far_bytes": 0, "both_ms": 0.0, "both_bytes": 0}
         for ker in kernels:
             trees, freqs, nfs, fas, _ = keep[ker]
             for g, (T, nf, fa) in enumerate(zip(trees, nfs, fas)):
-                for part, a, b in (("near", nf, None), ("far", None, fa)):
+                for part, a, b in (("near", nf, None), ("far", None, fa), ("both", nf, fa)):
                     best = None
                     for _ in range(3):
                         g3.apply_gcq(ctx, T, a, b, Wds[g])
@@ -522,7 +523,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     parts = measure_parts()
     apply_parts = {k: {"ms": parts[k + "_ms"], "bytes": parts[k + "_bytes"],
                        "gbs": parts[k + "_bytes"] / (parts[k + "_ms"] / 1e3) / 1e9 if parts[k + "_ms"] > 0 else None}
-                   for k in ("near", "far")}
+                   for k in ("near", "far", "both")}
     # learned + batched vs plain at equal accuracy: one seeded block sample,
     # both arms (single meshes only; the plain arm is one block per launch)
     vs_plain = None

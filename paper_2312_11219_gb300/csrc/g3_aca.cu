@@ -278,12 +278,12 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     // matrices of the recompression (+ Gram staging; float32: + the working-
     // precision copies of the two Cholesky factors), the pivot-search
     // tiles (2 RF TM complex T, TM = 64 float / 32 double) and the eq. (norm)
-    // staging ((NORM_RC + 1) (32 + RF) + 32 RF complex T)
+    // staging ((NORM_RC + 1) (32 + RF) + 32 RF complex T, then 64 column pointers)
     const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
                                 std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>)) +
                                 (sizeof(T) == 4 ? 2 * (size_t)RS * RS * sizeof(Cx<T>) : 0);
     const size_t tile_bytes = 2 * (size_t)RF * (sizeof(T) == 4 ? 64 : 32) * sizeof(Cx<T>);
-    const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>);
+    const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>) + 64 * sizeof(void*);
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
     const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
@@ -710,7 +710,7 @@ static g3_status run_aca_whole_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* 
     const size_t recomp_bytes = 2 * (size_t)RS * RS * sizeof(Cx<double>) +
                                 std::max(2 * (size_t)RS * RS * sizeof(Cx<T>), 33 * (size_t)RF * sizeof(Cx<T>)) +
                                 (sizeof(T) == 4 ? 2 * (size_t)RS * RS * sizeof(Cx<T>) : 0);
-    const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>);
+    const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>) + 64 * sizeof(void*);
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
     const size_t smem = std::max(std::max(recomp_bytes, gram_bytes), tab_bytes);

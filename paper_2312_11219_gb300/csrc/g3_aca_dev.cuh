@@ -399,24 +399,14 @@ __device__ __forceinline__ Cx<T> shfl_xor_c(Cx<T> v, int o) {
     return Cx<T>{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
 }
 
-// gang size G (a power of two <= 32) of a line of L outputs whose every
-// output sums W terms (quadrature points, then the earlier columns): the G
-// that minimises one thread's serial work, passes(G) * ceil(W / G) plus a
-// per-pass overhead of two terms, where passes(G) = ceil(L G / NT); ties go
-// to the smaller G (fewer passes)
+// gang size: the largest power of two <= 32 with L * G <= 2 NT (at most two
+// passes over the line; a serial-work model that allowed more passes with
+// larger gangs measured slower)
 template <int NT>
-__device__ __forceinline__ int gang_size(int L, int W) {
-    int best = 1;
-    long long best_cost = -1;
-    for (int G = 1; G <= 32; G *= 2) {
-        const long long passes = ((long long)L * G + NT - 1) / NT;
-        const long long cost = passes * ((W + G - 1) / G + 2);
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best = G;
-        }
-    }
-    return best;
+__device__ __forceinline__ int gang_size(int L) {
+    int G = 1;
+    while (G < 32 && L * (G * 2) <= 2 * NT) G *= 2;
+    return G;
 }
 
 // Per-face tables of the earlier crosses' columns, flattened over (p, t):
@@ -495,17 +485,19 @@ __device__ void line_coeffs(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, 
 //   ENTRY - sum_p f_p[kf] (U_p V_p^H) - sum_{t<m} u_t v_t^H
 //   ROW:  out[j] = ENTRY(fix, j) - sum_c coef[c] conj(X_c[j]),  X_c = V_p[:, t] | v_t
 //   !ROW: out[i] = ENTRY(i, fix) - sum_c X_c[i] coef[c],        X_c = U_p[:, t] | u_t
-// G threads per output element share the sum (eight loads in flight, four
+// G threads per output element share the sum (sixteen loads in flight, four
 // independent partial sums) and the quadrature points.  Returns the
 // block-wide argmax of |out|^2 (ROW: over all columns; !ROW: over the rows
 // not yet used).
+constexpr int LIF = 16;  // loads in flight per thread in the residual lines' sums
+
 template <int KER, class T, int NT, bool ROW>
 __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
                                     int fix, int kf, int m, Cx<T>* out) {
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N;
     const int L = ROW ? N : M;
-    const int G = gang_size<NT>(L, F.ncol + m + (KER == G3_GAL_SLP ? 16 : 7));
+    const int G = gang_size<NT>(L);
     const int per = NT / G;
     const int part = tid % G;
     const long long* col = ROW ? F.colV : F.colU;
@@ -523,7 +515,18 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
             if (tid == 0) S.sub[10] += clock64() - te;
             Cx<T> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
             int c = part;
-            // 8 loads in flight per thread (the sums wait on memory, not on arithmetic)
+            // LIF loads in flight per thread (the sums wait on memory, not on arithmetic)
+            for (; c + (LIF - 1) * G < nt; c += LIF * G) {
+                Cx<T> x[LIF];
+#pragma unroll
+                for (int u = 0; u < LIF; ++u) x[u] = ldcx(A.pool + col[c + u * G] + v);
+#pragma unroll
+                for (int u = 0; u < LIF; ++u) {
+                    Cx<T>& acc_u = (u & 3) == 0 ? s0 : (u & 3) == 1 ? s1 : (u & 3) == 2 ? s2 : s3;
+                    if (ROW) cfmac(acc_u, F.coef[c + u * G], x[u]);
+                    else cfma(acc_u, x[u], F.coef[c + u * G]);
+                }
+            }
             for (; c + 7 * G < nt; c += 8 * G) {
                 Cx<T> x[8];
 #pragma unroll
@@ -1273,37 +1276,61 @@ __device__ void norm_grams(const AcaArgs<T>& A, BlockSh<T>& S, const Cx<T>* Un, 
     const int na = S.pre[nc] + rn;
     Cx<T>* sa = sh;                  // [32][RC + 1]
     Cx<T>* sb = sh + 32 * (RC + 1);  // [rn][RC + 1]
+    // column starts of the chunk's 32 columns, U then V (after sb and the
+    // combine buffer pr)
+    const Cx<T>** cbase = reinterpret_cast<const Cx<T>**>(sb + rn * (RC + 1) + 32 * rn);
     for (int a0 = 0; a0 < na; a0 += 32) {
         const int acnt = min(32, na - a0);
         Cx<T> zu[QMAX], zv[QMAX];
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) zu[q] = zv[q] = Cx<T>{0, 0};
+        if (tid < acnt) {
+            const int col = a0 + tid;
+            if (col < S.pre[nc]) {
+                int d = 0;
+                while (S.pre[d + 1] <= col) ++d;
+                const int t = col - S.pre[d];
+                cbase[tid] = A.pool + S.off[d] + (long long)t * M;
+                cbase[32 + tid] = A.pool + S.off[d] + (long long)S.r[d] * M + (long long)t * N;
+            } else {
+                const int t = col - S.pre[nc];
+                cbase[tid] = Un + (long long)t * M;
+                cbase[32 + tid] = Vn + (long long)t * N;
+            }
+        }
+        __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {  // 0: U (rows M), 1: V (rows N)
             const int L = pass == 0 ? M : N;
+            const Cx<T>* const* cb = cbase + 32 * pass;
             for (int i0 = 0; i0 < L; i0 += RC) {
-                for (int e = tid; e < acnt * RC; e += NT) {
-                    const int c = e / RC, ii = e - c * RC, col = a0 + c;
-                    Cx<T> v{0, 0};
-                    if (i0 + ii < L) {
-                        const Cx<T>* base;
-                        if (col < S.pre[nc]) {
-                            int d = 0;
-                            while (S.pre[d + 1] <= col) ++d;
-                            const int t = col - S.pre[d];
-                            base = pass == 0 ? A.pool + S.off[d] + (long long)t * M
-                                             : A.pool + S.off[d] + (long long)S.r[d] * M + (long long)t * N;
-                        } else {
-                            const int t = col - S.pre[nc];
-                            base = pass == 0 ? Un + (long long)t * M : Vn + (long long)t * N;
+                // staging: eight independent loads in flight per thread
+                const int na_e = acnt * RC, nb_e = rn * RC;
+                for (int e0 = 0; e0 < na_e + nb_e; e0 += 8 * NT) {
+                    Cx<T> x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = e0 + tid + u * NT;
+                        x[u] = Cx<T>{0, 0};
+                        if (e < na_e) {
+                            const int c = e / RC, ii = e - c * RC;
+                            if (i0 + ii < L) x[u] = ldcx(cb[c] + i0 + ii);
+                        } else if (e < na_e + nb_e) {
+                            const int b = (e - na_e) / RC, ii = (e - na_e) - b * RC;
+                            const Cx<T>* base = pass == 0 ? Un + (long long)b * M : Vn + (long long)b * N;
+                            if (i0 + ii < L) x[u] = ldcx(base + i0 + ii);
                         }
-                        v = ldcx(base + i0 + ii);
                     }
-                    sa[c * (RC + 1) + ii] = v;
-                }
-                for (int e = tid; e < rn * RC; e += NT) {
-                    const int b = e / RC, ii = e - b * RC;
-                    const Cx<T>* base = pass == 0 ? Un + (long long)b * M : Vn + (long long)b * N;
-                    sb[b * (RC + 1) + ii] = (i0 + ii < L) ? ldcx(base + i0 + ii) : Cx<T>{0, 0};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = e0 + tid + u * NT;
+                        if (e < na_e) {
+                            const int c = e / RC, ii = e - c * RC;
+                            sa[c * (RC + 1) + ii] = x[u];
+                        } else if (e < na_e + nb_e) {
+                            const int b = (e - na_e) / RC, ii = (e - na_e) - b * RC;
+                            sb[b * (RC + 1) + ii] = x[u];
+                        }
+                    }
                 }
                 __syncthreads();
 #pragma unroll
