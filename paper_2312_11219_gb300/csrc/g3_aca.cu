@@ -307,8 +307,9 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     const int grid_dense = o.unbatched ? 1 : std::max(1, std::min(n_dense, ctx->n_sm * per_dense));
     const int grid = std::max(grid_low, grid_dense);
     const size_t stride = al256(ws_bytes<T>(RF, Mmax, Nmax, Cmax, Ku));
-    DevBuf d_ws;
-    G3_CUDA(d_ws.alloc(stride * grid));
+    // per-CTA workspace, kept by the context between compressions
+    G3_CUDA(ctx->aca_ws.ensure(stride * grid));
+    DevBuf& d_ws = ctx->aca_ws;
     // outputs of all meshes (sliced per mesh at the end)
     DevBuf g_rec, g_r3, g_cyc;
     G3_CUDA(g_rec.alloc((size_t)n_far * Cmax * sizeof(CrossRec)));
@@ -333,7 +334,9 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         }
         return (is_dense(r) ? 12.0 * m * n : 256.0 * (m + n)) + 24.0 * ku;
     };
-    double& scale = pool_mlp ? ctx->pool_scale_mlp : ctx->pool_scale;
+    // learned per kernel kind and precision: operators alternating on one
+    // context (single and double layer) need different pool sizes per estimate
+    double& scale = ctx->pool_scale[pool_mlp ? 1 : 0][(kernel >= 0 && kernel < 4) ? kernel : 4][sizeof(T) == 4 ? 1 : 0];
     double est = 0.0;
     for (int q = 0; q < n_run; ++q) est += block_est(queue[q]);
     long long cap = (long long)(pf * scale * est);

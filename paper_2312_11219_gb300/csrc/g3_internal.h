@@ -187,6 +187,7 @@ struct g3_ctx {
     std::vector<std::string> names_cache;
     g3::DevBuf gl;           // Gauss-Legendre table for self terms
     g3::DevBuf scratch;      // apply scratch (cluster-order densities, partial y)
+    g3::DevBuf aca_ws;       // per-CTA workspace of the compression (grown, never shrunk)
     g3::DevBuf status;       // device status word(s)
     g3::DevBuf stage_w, stage_y;  // device staging of host W / Y in apply_gcq
     void* h_stage = nullptr;      // pinned host staging of read-backs (grown, never shrunk)
@@ -198,8 +199,11 @@ struct g3_ctx {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaEvent_t ev_side[2] = {};
     double last_apply_ms = 0, last_near_ms = 0;
-    double pool_scale = 1.0;  // factor-pool size / estimate needed by earlier compressions
-    double pool_scale_mlp = 1.0;  // the same for the predictor-based estimate
+    // factor-pool size / estimate needed by earlier compressions, per kernel
+    // kind (slot 4: anything else) and working precision, [0] plain estimate,
+    // [1] the predictor-based one
+    double pool_scale[2][5][2] = {{{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}},
+                                  {{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}}};
     std::map<long long, std::pair<int, int>> tune_cache;  // autotuner: key -> (threads, dense_face_max)
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
     void count(const char* name, int64_t n = 1) {
