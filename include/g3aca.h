@@ -163,6 +163,15 @@ typedef struct {
                              crosses.  Low-rank faces only, one launch per cross; not with
                              unbatched, the batch or the separable test tensor.
                              0 (default) = block by block                                */
+    int residual_face_max; /* G3_MIXED, low-rank faces: blocks with M_b N_b <= this evaluate
+                             each face's residual ENTRY(i, j, k_l) - sum_p f_p[k_l]
+                             (U_p V_p^H)[i, j] for the whole face in one parallel pass into
+                             a per-CTA working buffer before the face ACA, which then reads
+                             its rows and columns there (same pivots, same stored factors;
+                             only the order of float32 sums differs).  No counterpart in
+                             the paper (an evaluation order).  0 (default) = never: rows
+                             and columns evaluated on demand (on the 12,288-triangle
+                             L-shape the dense pass costs what it saves in the lines)    */
 } g3_opts;
 
 /* Statistics of one compression. */
@@ -199,11 +208,15 @@ typedef struct {
                                  recompression Gram, Cholesky, core, core factorisation,
                                  rest; face ACA table set-up, residual rows, residual
                                  columns, approximant norm, sample checks; of the residual
-                                 rows and columns: the entries; 0 (reserved)              */
+                                 rows and columns: the entries; dense residual faces      */
     double ms_host[4];        /* host wall time of the call: set-up before the first launch
                                  (predictor, queue, allocations, uploads), the launch rounds
                                  up to the last synchronize, the read-back of records and
                                  statistics, the apply's work lists                       */
+    int64_t entries_face_dense; /* ENTRY evaluations into dense residual working faces
+                                 (opts->residual_face_max); not part of `entries`, which
+                                 counts the rows, columns, samples and fibers Algorithm 1
+                                 takes                                                   */
 } g3_stats;
 
 /* ---- context ----------------------------------------------------------- */
@@ -213,6 +226,13 @@ typedef struct {
  * work on it. */
 g3_status g3_create(int device, void* cuda_stream, g3_ctx** out);
 g3_status g3_set_stream(g3_ctx* ctx, void* cuda_stream);
+/* Where the float32 (complex64) apply forms the far-field vectors
+ * x_p = sum_k f_p[k] w_k of eq. (product): on = 1 (default) on the tensor cores
+ * (mma.sync m16n8k8 TF32 in a three-term split, float32 accumulation, about
+ * float32 accuracy), on = 0 on the CUDA cores (float32 fused multiply-adds).
+ * Applies to apply_gcq (SUM) and apply_gcq_noalloc; float64 applies always
+ * use the CUDA cores. */
+g3_status g3_set_apply_tensor_cores(g3_ctx* ctx, int on);
 g3_status g3_destroy(g3_ctx* ctx);
 const char* g3_last_error(void);
 int g3_version(void);
@@ -500,11 +520,11 @@ g3_status g3_factors_labels(g3_ctx* ctx, const g3_factors* fa, float* out);
  * mem = G3_HOST:   W, Y are host pointers; the library copies W in and Y out
  *                  on the context's stream and synchronises before return.
  * Frequencies outside the unique set use A(conj s) = conj A(s).
- * G3_APPLY_SUM: with both parts present the far-field kernels run on a
+ * G3_APPLY_SUM: with both parts present the near-field kernel runs on a
  * second, high-priority stream owned by the context (forked from and joined
- * back into the context's stream, next to the near field on the context's
- * stream), so work the caller orders after this call on the context's
- * stream sees y complete.  G3_APPLY_PERFREQ runs on the context's stream only; its
+ * back into the context's stream, next to the far-field kernels on the
+ * context's stream), so work the caller orders after this call on the
+ * context's stream sees y complete.  G3_APPLY_PERFREQ runs on the context's stream only; its
  * scratch holds 4 Ku M complex values (context-owned, grown on demand), and
  * face ranks above 64 return G3_EUNSUPPORTED.  The call synchronises the
  * context's stream before it returns (the device time is recorded for

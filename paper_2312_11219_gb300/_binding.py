@@ -43,7 +43,7 @@ class Opts(C.Structure):
                 ("eps_face", C.c_double), ("max_blocks", C.c_int), ("dense_face_max", C.c_int),
                 ("literal_stop", C.c_int), ("mlp", C.c_void_p), ("mlp_use", C.c_int),
                 ("face_floor_scale", C.c_double), ("trunc_floor_scale", C.c_double), ("pivot_index", C.c_int),
-                ("graph", C.c_int), ("whole_matrix", C.c_int)]
+                ("graph", C.c_int), ("whole_matrix", C.c_int), ("residual_face_max", C.c_int)]
 
 
 class TrainOpts(C.Structure):
@@ -61,7 +61,7 @@ class Stats(C.Structure):
                 ("dense_crosses", C.c_int64), ("ms_lowrank", C.c_double), ("ms_dense", C.c_double),
                 ("spilled_blocks", C.c_int32), ("mlp_used", C.c_int32), ("ms_mlp", C.c_double),
                 ("face_check_restarts", C.c_int64), ("stop_check_overrides", C.c_int64),
-                ("sub_cycles", C.c_int64 * 12), ("ms_host", C.c_double * 4)]
+                ("sub_cycles", C.c_int64 * 12), ("ms_host", C.c_double * 4), ("entries_face_dense", C.c_int64)]
 
 
 def _sig(name, res, *args):
@@ -74,6 +74,7 @@ def _sig(name, res, *args):
 _ci = C.c_int
 _sig("g3_create", _ci, _ci, _p, _pp)
 _sig("g3_set_stream", _ci, _p, _p)
+_sig("g3_set_apply_tensor_cores", _ci, _p, _ci)
 _sig("g3_destroy", _ci, _p)
 _sig("g3_last_error", C.c_char_p)
 _sig("g3_version", _ci)
@@ -125,7 +126,7 @@ _sig("g3_mlp_free", _ci, _p)
 _sig("g3_block_features", _ci, _p, _p, _p, _ci, C.c_double, _fp)
 _sig("g3_factors_labels", _ci, _p, _p, _fp)
 
-EXPORTED = ["g3_create", "g3_set_stream", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
+EXPORTED = ["g3_create", "g3_set_stream", "g3_set_apply_tensor_cores", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_from_array", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
             "build_cluster_tree", "build_cluster_tree_capped", "g3_shard_rows", "g3_tree_partition_host", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
@@ -190,6 +191,10 @@ class Context(_Handle):
 
     def set_stream(self, stream) -> None:
         _check(_lib.g3_set_stream(self.h, C.c_void_p(stream)), "g3_set_stream")
+
+    def set_apply_tensor_cores(self, on: bool) -> None:
+        """Far-field x formation of float32 applies on the tensor cores (default) or the CUDA cores."""
+        _check(_lib.g3_set_apply_tensor_cores(self.h, 1 if on else 0), "g3_set_apply_tensor_cores")
 
     def launch_count(self) -> int:
         return int(_lib.g3_launch_count(self.h))
@@ -381,7 +386,7 @@ class Factors(_Handle):
         out["phase_cycles"] = dict(zip(["face", "recompress", "formation", "pivot", "fiber", "norm", "next_k"],
                                        list(s.phase_cycles)))
         out["sub_cycles"] = dict(zip(["rc_gram", "rc_cholesky", "rc_core", "rc_jacobi", "rc_rest", "face_table",
-                                      "face_rows", "face_columns", "face_norm", "face_samples", "line_entries"],
+                                      "face_rows", "face_columns", "face_norm", "face_samples", "line_entries", "dense_residual_faces"],
                                      list(s.sub_cycles)))
         out["ms_host"] = dict(zip(["setup", "rounds", "readback", "apply_plan"], list(s.ms_host)))
         return out

@@ -286,7 +286,23 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     const size_t gram_bytes = ((NORM_RC<T> + 1) * (size_t)(32 + RF) + 32 * (size_t)RF) * sizeof(Cx<T>) + 64 * sizeof(void*);
     const size_t tab_bytes = 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) +
                              (TABMAX + RF_MAX) * sizeof(Cx<T>) + ROWMAX * sizeof(Cx<T>) + 64;
-    const size_t smem = std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes);
+    // dense residual working faces (float32 low-rank faces of blocks with M N <= drf):
+    // a per-CTA buffer of the largest such face and shared-memory staging after
+    // the face tables (sized for the widest launch shape)
+    long long drf_elems = 0;
+    int drf = -1;
+    if (sizeof(T) == 4 && kernel != G3_SEPARABLE) {
+        drf = o.residual_face_max > 0 ? o.residual_face_max : -1;
+        for (int q = 0; q < n_run && drf > 0; ++q) {
+            const BlockRange& r = ranges[queue[q]];
+            const long long mn = (long long)(r.re - r.rb) * (r.ce - r.cb);
+            if (!is_dense(r) && mn <= drf) drf_elems = std::max(drf_elems, mn);
+        }
+        if (drf_elems == 0) drf = -1;
+    }
+    const size_t drf_smem = drf > 0 ? drf_stage_offset<T>() + drf_stage_bytes<T, 512>() : 0;
+    const size_t smem =
+        std::max(std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes), drf_smem);
     // low-rank class: 128, 256, 384 or 512 threads per CTA (float32 path); more
     // threads shorten each block, which matters for the largest blocks at the
     // end, fewer keep more blocks in flight per SM
@@ -306,7 +322,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     const int grid_low = o.unbatched ? 1 : std::max(1, std::min(n_low, ctx->n_sm * per_low));
     const int grid_dense = o.unbatched ? 1 : std::max(1, std::min(n_dense, ctx->n_sm * per_dense));
     const int grid = std::max(grid_low, grid_dense);
-    const size_t stride = al256(ws_bytes<T>(RF, Mmax, Nmax, Cmax, Ku));
+    const size_t drf_off = al256(ws_bytes<T>(RF, Mmax, Nmax, Cmax, Ku));
+    const size_t stride = drf_off + al256((size_t)drf_elems * sizeof(Cx<T>));
     // per-CTA workspace, kept by the context between compressions
     G3_CUDA(ctx->aca_ws.ensure(stride * grid));
     DevBuf& d_ws = ctx->aca_ws;
@@ -432,6 +449,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         A.ws_stride = stride;
         A.Mmax = Mmax;
         A.Nmax = Nmax;
+        A.drf_max = drf > 0 ? drf : 0;
+        A.drf_off = drf > 0 ? drf_off : 0;
         if (!graph) G3_CUDA(cudaEventRecord(e0, ctx->stream));
         g3_status st = G3_OK;
         for (int cls = 0; cls < 2 && st == G3_OK; ++cls) {
@@ -636,6 +655,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         S.ms_lowrank = ms_low_total;
         S.ms_dense = ms_dense_total;
         S.spilled_blocks = spilled_total;
+        S.entries_face_dense = (int64_t)cnt[7];
         S.face_check_restarts = (int64_t)cnt[5];
         S.stop_check_overrides = (int64_t)cnt[6];
         S.mlp_used = mlp_use;

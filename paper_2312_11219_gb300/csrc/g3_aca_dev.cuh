@@ -48,7 +48,7 @@ namespace g3 {
 constexpr int KU_MAX = 256;   // largest unique-frequency count
 constexpr int SAMPLES = 32;   // sample entries of the convergence checks
 constexpr int NPH = 10;       // per-block diagnostics: 7 phases, steps, start, end
-constexpr int NSUB = 11;      // sub-step cycle counters (diagnostics)
+constexpr int NSUB = 12;      // sub-step cycle counters (diagnostics)
 // rows staged per pass of the eq. (norm) Gram products
 template <class T>
 constexpr int NORM_RC = sizeof(T) == 4 ? 64 : 32;
@@ -120,6 +120,9 @@ struct AcaArgs {
     char* ws;
     size_t ws_stride;
     int Mmax, Nmax;
+    int drf_max;             // float32 low-rank faces of blocks with M N <= drf_max are evaluated
+                             // densely into a working buffer before their ACA (0 = never)
+    size_t drf_off;          // byte offset of that buffer in each CTA's workspace slice
 };
 
 template <class T>
@@ -139,6 +142,7 @@ struct Ws {
     short* colP;
     Cx<double>* hs;       // [SAMPLES][Cmax] H_p at the stop-check samples
     double* rk;           // [Ku] sampled residual per frequency
+    Cx<T>* dres;          // [drf_max] dense residual working face (row-major, ld N), or null
 };
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -163,8 +167,9 @@ __host__ __device__ inline size_t ws_bytes(int RF, int Mmax, int Nmax, int Cmax,
 }
 
 template <class T>
-__device__ inline Ws<T> ws_carve(char* base, int RF, int Mmax, int Nmax, int Cmax, int Ku) {
+__device__ inline Ws<T> ws_carve(char* base, int RF, int Mmax, int Nmax, int Cmax, int Ku, size_t drf_off = 0) {
     Ws<T> w;
+    w.dres = drf_off ? reinterpret_cast<Cx<T>*>(base + drf_off) : nullptr;
     size_t o = 0;
     auto take = [&](size_t n) {
         char* p = base + o;
@@ -428,7 +433,7 @@ struct FaceTab {
 };
 
 template <class T>
-__device__ __forceinline__ size_t facetab_smem_bytes() {
+__host__ __device__ constexpr size_t facetab_smem_bytes() {
     return 2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) + (TABMAX + RF_MAX) * sizeof(Cx<T>) +
            ROWMAX * sizeof(Cx<T>) + 64;
 }
@@ -493,7 +498,7 @@ constexpr int LIF = 16;  // loads in flight per thread in the residual lines' su
 
 template <int KER, class T, int NT, bool ROW>
 __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
-                                    int fix, int kf, int m, Cx<T>* out) {
+                                    int fix, int kf, int m, Cx<T>* out, const Cx<T>* D) {
     const int tid = threadIdx.x;
     const int M = S.M, N = S.N;
     const int L = ROW ? N : M;
@@ -509,10 +514,15 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
         const int v = base + tid / G;
         Cx<T> acc{0, 0};
         if (v < L) {
-            const int gi = S.rb + (ROW ? fix : v), gj = S.cb + (ROW ? v : fix);
-            const long long te = tid == 0 ? clock64() : 0;
-            acc = ent_part<KER, T>(A, gi, gj, kf, part, G);
-            if (tid == 0) S.sub[10] += clock64() - te;
+            if (D) {
+                // the dense residual working face holds ENTRY minus the earlier crosses
+                if (part == 0) acc = ldcx(D + (ROW ? (size_t)fix * N + v : (size_t)v * N + fix));
+            } else {
+                const int gi = S.rb + (ROW ? fix : v), gj = S.cb + (ROW ? v : fix);
+                const long long te = tid == 0 ? clock64() : 0;
+                acc = ent_part<KER, T>(A, gi, gj, kf, part, G);
+                if (tid == 0) S.sub[10] += clock64() - te;
+            }
             Cx<T> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
             int c = part;
             // LIF loads in flight per thread (the sums wait on memory, not on arithmetic)
@@ -597,7 +607,7 @@ __device__ ArgMaxT<T> residual_line(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
 // columns of the earlier crosses.  Writes |R_s|^2 to S.samp.
 template <int KER, class T, int NT>
 __device__ void face_samples(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F, int kf,
-                             int m) {
+                             int m, const Cx<T>* D) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int M = S.M, N = S.N;
     for (int sm = wid; sm < SAMPLES; sm += NT / 32) {
@@ -611,11 +621,98 @@ __device__ void face_samples(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S,
         acc.x = warp_sum(acc.x);
         acc.y = warp_sum(acc.y);
         if (lane == 0) {
-            const Cx<T> e = ent<KER, T>(A, S.rb + i, S.cb + j, kf);
+            const Cx<T> e = D ? D[(size_t)i * N + j] : ent<KER, T>(A, S.rb + i, S.cb + j, kf);
             S.samp[sm] = cabs2d(Cx<T>{e.x - acc.x, e.y - acc.y});
         }
     }
     if (threadIdx.x == 0) S.entries += SAMPLES;
+    __syncthreads();
+}
+
+// ---- dense residual working face ------------------------------------------------------
+// D[i][j] = ENTRY(i, j, kf) - sum_p f_p[kf] (U_p V_p^H)[i, j]  (row-major, ld N) for all
+// i < M, j < N, in one parallel pass before the face ACA: the ACA then reads its rows
+// and columns from D and sums only the current face's crosses.  The partial-pivot
+// ACA takes the same rows and columns as with on-demand lines; only the order of
+// the float32 sums over the earlier crosses differs.  Tiles of 64 x (NT / 4)
+// outputs, a 4 x 4 micro-tile per thread; the earlier crosses' columns (scaled
+// by f_p[kf]) staged DRF_KC at a time in shared memory.  Float32 only.
+constexpr int DRF_KC = 16;
+// shared-memory staging of the dense residual face, placed after the face tables
+template <class T>
+constexpr size_t drf_stage_offset() { return (facetab_smem_bytes<T>() + 255) & ~size_t(255); }
+template <class T, int NT>
+constexpr size_t drf_stage_bytes() { return (size_t)DRF_KC * (64 + NT / 4) * sizeof(Cx<T>); }
+
+template <int KER, class T, int NT>
+__device__ void face_dense_residual(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
+                                    int kf, unsigned char* arena) {
+    static_assert(sizeof(T) == 4, "dense residual faces are a float32 path");
+    constexpr int TI = 64, TJ = NT / 4, TXN = TJ / 4;
+    const int tid = threadIdx.x;
+    const int M = S.M, N = S.N, nc = F.ncol;
+    const int tx = tid % TXN, ty = tid / TXN;  // ty < 16
+    Cx<T>* su = reinterpret_cast<Cx<T>*>(arena + drf_stage_offset<T>());  // [DRF_KC][TI]
+    Cx<T>* sv = su + DRF_KC * TI;                                          // [DRF_KC][TJ]
+    Cx<T>* D = w.dres;
+    // the entries, one thread per entry (consecutive threads take consecutive columns)
+    const int MN = M * N;
+    long long te = clock64();
+    for (int e = tid; e < MN; e += NT) {
+        const int i = e / N, j = e - i * N;
+        D[e] = ent<KER, T>(A, S.rb + i, S.cb + j, kf);
+    }
+    __syncthreads();
+    sublap(S, 10, te);  // the residual lines evaluate no entries when this runs
+    for (int i0 = 0; i0 < M; i0 += TI) {
+        for (int j0 = 0; j0 < N; j0 += TJ) {
+            Cx<T> acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int gi = i0 + ty * 4 + a, gj = j0 + tx * 4 + b;
+                    acc[a][b] = (gi < M && gj < N) ? ldcx(D + (size_t)gi * N + gj) : Cx<T>{0, 0};
+                }
+            for (int c0 = 0; c0 < nc; c0 += DRF_KC) {
+                __syncthreads();  // the previous chunk is consumed
+                for (int e = tid; e < DRF_KC * TI; e += NT) {
+                    const int kk = e / TI, ii = e - kk * TI, c = c0 + kk;
+                    su[e] = (c < nc && i0 + ii < M) ? cmul(S.fk[F.colP[c]], ldcx(A.pool + F.colU[c] + i0 + ii))
+                                                    : Cx<T>{0, 0};
+                }
+                for (int e = tid; e < DRF_KC * TJ; e += NT) {
+                    const int kk = e / TJ, jj = e - kk * TJ, c = c0 + kk;
+                    sv[e] = (c < nc && j0 + jj < N) ? ldcx(A.pool + F.colV[c] + j0 + jj) : Cx<T>{0, 0};
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int kk = 0; kk < DRF_KC; ++kk) {
+                    Cx<T> u[4], v[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) u[a] = su[kk * TI + ty * 4 + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) v[b] = sv[kk * TJ + tx * 4 + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            // acc -= u conj(v)
+                            acc[a][b].x -= u[a].x * v[b].x + u[a].y * v[b].y;
+                            acc[a][b].y -= u[a].y * v[b].x - u[a].x * v[b].y;
+                        }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int gi = i0 + ty * 4 + a, gj = j0 + tx * 4 + b;
+                    if (gi < M && gj < N) D[(size_t)gi * N + gj] = acc[a][b];
+                }
+        }
+    }
+    if (tid == 0) atomicAdd(&A.counters[7], (unsigned long long)M * N);
     __syncthreads();
 }
 
@@ -633,9 +730,21 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
     // f_p[kf] of earlier crosses, the column tables, used-row flags
     for (int p = tid; p < nc; p += NT) S.fk[p] = Fp(A, S, p)[kf];
     long long tf = clock64();
-    const FaceTab<T> F = facetab_build<T, NT>(A, w, S, arena);
+    FaceTab<T> F = facetab_build<T, NT>(A, w, S, arena);
     for (int i = tid; i < M; i += NT) w.used[i] = 0;
     __syncthreads();
+    // dense residual working face (float32, blocks up to drf_max entries): ENTRY
+    // minus the earlier crosses evaluated for the whole face at once; the lines
+    // below then subtract only the current face's crosses
+    const Cx<T>* D = nullptr;
+    if constexpr (sizeof(T) == 4 && KER != G3_SEPARABLE) {
+        if (w.dres && (long long)M * N <= A.drf_max) {
+            face_dense_residual<KER, T, NT>(A, w, S, F, kf, arena);
+            D = w.dres;
+            F.ncol = 0;
+            sublap(S, 11, tf);
+        }
+    }
     if (tid == 0) S.fsn2 = 0.0;
     int m = 0;
     int irow = 0;
@@ -651,7 +760,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             sublap(S, 5, tf);
             line_coeffs<T, NT, true>(A, w, S, F, irow, m);
             __syncthreads();
-            ArgMaxT<T> am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row);
+            ArgMaxT<T> am = residual_line<KER, T, NT, true>(A, w, S, F, irow, kf, m, F.row, D);
             if (tid == 0) w.used[irow] = 1;
             // a row counts as nonzero when |delta|^2 is a normal number of the
             // working precision (below that the entries are far under any tolerance)
@@ -689,7 +798,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
         // residual column jp = u_m; the argmax over unused rows of |u_m| is the next row
         Cx<T>* um = w.uw + (size_t)m * A.Mmax;
         sublap(S, 6, tf);
-        ArgMaxT<T> nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um);
+        ArgMaxT<T> nx = residual_line<KER, T, NT, false>(A, w, S, F, jp, kf, m, um, D);
         sublap(S, 7, tf);
         // recursive Frobenius norm of the face approximant:
         // ||S_m||^2 = ||S_{m-1}||^2 + 2 Re sum_t (u_t^H u_m)(v_m^H v_t) + ||u_m||^2 ||v_m||^2
@@ -736,7 +845,7 @@ __device__ int face_aca(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, int 
             }
             // confirm on the sample entries: partial pivoting can miss a block
             // of the face that no visited row or column reaches
-            face_samples<KER, T, NT>(A, w, S, F, kf, m);
+            face_samples<KER, T, NT>(A, w, S, F, kf, m, D);
             sublap(S, 9, tf);
             static_assert(SAMPLES == 32, "one sample per lane");
             if (wid == 0) {
@@ -1671,7 +1780,8 @@ __global__ void __launch_bounds__(NT, aca_min_ctas<NT>()) k_aca3(const AcaArgs<T
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const int RF = P.RF;
     Cx<double>* shB = reinterpret_cast<Cx<double>*>(smem_raw);  // arena base
-    const Ws<T> w = ws_carve<T>(P.ws + (size_t)blockIdx.x * P.ws_stride, RF, P.Mmax, P.Nmax, P.Cmax, P.Ku);
+    const Ws<T> w = ws_carve<T>(P.ws + (size_t)blockIdx.x * P.ws_stride, RF, P.Mmax, P.Nmax, P.Cmax, P.Ku,
+                                P.drf_max > 0 ? P.drf_off : 0);
     __shared__ int s_q;
     for (int iter = 0;; ++iter) {
         if (tid == 0) {

@@ -96,9 +96,9 @@ g3_status g3_create(int device, void* cuda_stream, g3_ctx** out) {
     }
     e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
-    // the apply's far-field kernels run on this stream at the highest priority,
-    // next to the near-field stream on the context's stream: pending far-field
-    // CTAs are dispatched first, near-field CTAs fill the rest of the GPU
+    // the apply's near-field kernel runs on this stream at the highest priority,
+    // next to the far-field kernels on the context's stream: pending near-field
+    // CTAs are dispatched first, far-field CTAs fill the rest of each SM
     int prio_least = 0, prio_greatest = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_greatest);
@@ -123,6 +123,12 @@ g3_status g3_create(int device, void* cuda_stream, g3_ctx** out) {
 g3_status g3_set_stream(g3_ctx* ctx, void* cuda_stream) {
     G3_CHECK(ctx != nullptr, "g3_set_stream: ctx is NULL");
     ctx->stream = (cudaStream_t)cuda_stream;
+    return G3_OK;
+}
+
+g3_status g3_set_apply_tensor_cores(g3_ctx* ctx, int on) {
+    G3_CHECK(ctx != nullptr, "g3_set_apply_tensor_cores: ctx is NULL");
+    ctx->apply_tensor_cores = on ? 1 : 0;
     return G3_OK;
 }
 

@@ -180,6 +180,7 @@ struct CrossRec {
 struct g3_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    int apply_tensor_cores = 1;  // float32 far-field x formation on the tensor cores
     int n_sm = 0;
     size_t smem_optin = 0;
     std::map<std::string, int64_t> launches;

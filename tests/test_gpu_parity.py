@@ -309,6 +309,50 @@ def test_compression_launch_shapes(g3, ctx, threads):
     assert n_piv > 0
 
 
+@pytest.mark.parametrize("kernel", ["slp", "dlp"])
+@pytest.mark.parametrize("threads", [256, 512])
+def test_dense_residual_faces(g3, ctx, kernel, threads):
+    """Low-rank faces evaluated through the dense residual working face
+    (opts residual_face_max) compute Algorithm 1 as the on-demand rows and
+    columns do: blocks within 10 eps3 of the oracle's dense blocks, block ranks
+    within 2 of the on-demand run, and every stored pivot the largest entry of
+    its face approximant H_l."""
+    w = workloads.get("lshape3072")
+    eps3 = 1e-4
+    geo, OT, fs, su, ef = _oracle_blocks(w, kernel, eps3)
+    T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
+    F = g3.freqs_from_spec(ctx, w.freq)
+    ref = g3.aca3_compress(ctx, T, F, kernel, prec="mixed", eps3=eps3, dense_face_max=-1, threads=threads)
+    fa = g3.aca3_compress(ctx, T, F, kernel, prec="mixed", eps3=eps3, dense_face_max=-1, threads=threads,
+                          residual_face_max=256 * 256)
+    st, st0 = fa.stats(), ref.stats()
+    assert st["status_bits"] & 1 == 0 and st["dense_crosses"] == 0
+    assert st["entries_face_dense"] > 0 and st0["entries_face_dense"] == 0
+    far = [b for b in range(OT.blocks.shape[0]) if OT.blocks[b, 4] == 1]
+    rows = np.array([OT.blocks[b, 1] - OT.blocks[b, 0] for b in far])
+    cols = np.array([OT.blocks[b, 3] - OT.blocks[b, 2] for b in far])
+    r3, r30 = fa.ranks(), ref.ranks()
+    assert np.abs(r3 - r30).max() <= 2
+    assert abs(r3.mean() - r30.mean()) <= 0.1 * r30.mean()
+    inside = np.flatnonzero(rows * cols <= 256 * 256)
+    assert inside.size > 0
+    rng = np.random.default_rng(21)
+    order = np.argsort(-(rows * cols)[inside], kind="stable")
+    check = sorted(set(inside[order[:2]].tolist()) | set(rng.choice(inside, min(3, inside.size), replace=False).tolist()))
+    for i in check:
+        rb, re, cb, ce, _ = OT.blocks[far[i]]
+        M, N = re - rb, ce - cb
+        blk = fa.block(i, M, N, su.size)
+        for U, V, piv in zip(blk["U"], blk["V"], blk["piv"]):
+            H = np.abs(U @ V.conj().T)
+            assert H[piv[0], piv[1]] >= (1 - 1e-3) * H.max(), (i, piv, H.max())
+        D = O_q.dense(geo, kernel, su, rows=OT.perm[rb:re], cols=OT.perm[cb:ce])
+        A = np.zeros_like(D)
+        for U, V, f in zip(blk["U"], blk["V"], blk["f"]):
+            A += (U @ V.conj().T)[:, :, None] * f[None, None, :]
+        assert np.linalg.norm(A - D) <= 10 * eps3 * np.linalg.norm(D), i
+
+
 @pytest.mark.parametrize("dense", [0, -1])
 def test_apply_cube768_against_oracle(g3, ctx, dense):
     import torch
