@@ -12,6 +12,8 @@ Modules
   freqs       multistep-CQ and gCQ frequencies (Appendix A)
   quadrature  collocation entries of V and K (eq. (bie_semi_diri))
   galerkin    Galerkin entries of V (eq. (bie_semi_indirect))
+  galerkin_p1 Galerkin D and K' with linear continuous elements
+              (eq. (bie_semi_neum)), element-local 3 x 3 blocks
   tree        balanced cluster tree and geometric block partition
   aca3        the three-way ACA of Algorithm 1 with face ACA and
               QR+SVD recompression

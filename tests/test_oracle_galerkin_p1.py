@@ -1,0 +1,141 @@
+"""Pins of the oracle for the Galerkin hypersingular operator D and the adjoint
+double layer K' with linear continuous elements (eq. (bie_semi_neum)).
+
+* Unit sphere: the spherical harmonics of degree n are eigenfunctions,
+      D Y_n = -s^3 i_n'(s) k_n'(s) Y_n,   K' Y_n = (s^2 i_n'(s) k_n(s) - 1/2) Y_n,
+  with the modified spherical Bessel functions i_0 = sinh z / z,
+  k_0 = exp(-z) / z, i_1 = (z cosh z - sinh z) / z^2, k_1 = exp(-z) (1 + z) / z^2
+  (their derivatives are checked here against central differences).  The
+  Galerkin residual sum_j A[i, j] u_j - lambda (M u)_i for u = 1 (n = 0) and
+  u = z (n = 1) on icospheres converges at second order in h: a dropped term,
+  a wrong sign of either part of D, or a wrong normal or sign in K' leaves
+  an O(1) residual.
+* Static limit: sum_b curl phi_b = curl 1 = 0 on every triangle, so the curl
+  part of D annihilates constants exactly; with s = 1e-6 the row sums of D
+  vanish to rounding (a wrong orientation of one curl breaks it).
+* The 4-point rule is symmetric in the two panels: the local blocks of a
+  regular pair satisfy D(tau, sigma)[a, b] = D(sigma, tau)[b, a].
+* The single layer's row sums of oracle.galerkin agree with the same
+  Sauter-Schwab maps applied to the constant local functions (sum of the
+  local P1 blocks of the s^2 part is s^2 (n . n) times the P0 integral).
+"""
+import numpy as np
+import pytest
+
+from inputs import meshes
+from oracle import galerkin as G, galerkin_p1 as P1
+
+S = np.array([1.0 + 0.0j, 2.0 + 3.0j])
+
+
+def _i0(z):
+    return np.sinh(z) / z
+
+
+def _k0(z):
+    return np.exp(-z) / z
+
+
+def _i1(z):
+    return (z * np.cosh(z) - np.sinh(z)) / z ** 2
+
+
+def _k1(z):
+    return np.exp(-z) * (1.0 + z) / z ** 2
+
+
+def _i0p(z):
+    return (z * np.cosh(z) - np.sinh(z)) / z ** 2
+
+
+def _k0p(z):
+    return -np.exp(-z) * (z + 1.0) / z ** 2
+
+
+def _i1p(z):
+    return np.sinh(z) / z - 2.0 * (z * np.cosh(z) - np.sinh(z)) / z ** 3
+
+
+def _k1p(z):
+    return -np.exp(-z) * (z * z + 2.0 * z + 2.0) / z ** 3
+
+
+def test_bessel_derivatives_by_differences():
+    h = 1e-6
+    for z in (0.7 + 0.0j, 2.0 + 3.0j):
+        for f, fp in ((_i0, _i0p), (_k0, _k0p), (_i1, _i1p), (_k1, _k1p)):
+            assert abs((f(z + h) - f(z - h)) / (2 * h) - fp(z)) <= 1e-8 * max(1.0, abs(fp(z)))
+        # Wronskian i_n k_n' - i_n' k_n = -1 / z^2
+        assert abs(_i0(z) * _k0p(z) - _i0p(z) * _k0(z) + 1 / z ** 2) < 1e-12
+        assert abs(_i1(z) * _k1p(z) - _i1p(z) * _k1(z) + 1 / z ** 2) < 1e-12
+
+
+def _eig(op, n):
+    if op == "d":
+        return -S ** 3 * (_i0p(S) * _k0p(S) if n == 0 else _i1p(S) * _k1p(S))
+    return S ** 2 * (_i0p(S) * _k0(S) if n == 0 else _i1p(S) * _k1(S)) - 0.5
+
+
+@pytest.fixture(scope="module")
+def sphere_ops():
+    out = {}
+    for lev in (1, 2):
+        v, t = meshes.icosphere(lev)
+        out[lev] = (v, P1.mass_p1(v, t), P1.dense_nodal(v, t, S, "d"), P1.dense_nodal(v, t, S, "kp"))
+    return out
+
+
+@pytest.mark.parametrize("op", ["d", "kp"])
+@pytest.mark.parametrize("n", [0, 1])
+def test_unit_sphere_eigenvalues_second_order(sphere_ops, op, n):
+    err = {}
+    for lev, (v, Mm, D, Kp) in sphere_ops.items():
+        A = D if op == "d" else Kp
+        u = np.ones(v.shape[0]) if n == 0 else v[:, 2].copy()
+        e = []
+        for m in range(S.size):
+            ref = _eig(op, n)[m] * (Mm @ u)
+            e.append(np.linalg.norm(A[:, :, m] @ u - ref) / np.linalg.norm(ref))
+        err[lev] = np.array(e)
+    assert (err[2] < 0.03).all(), err
+    assert (err[2] < err[1] / 2.2).all(), err
+
+
+def test_static_curl_part_annihilates_constants():
+    v, t = meshes.icosphere(1)
+    s = np.array([1e-6 + 0j])
+    D = P1.dense_nodal(v, t, s, "d")[:, :, 0]
+    assert np.abs(D.sum(axis=1)).max() <= 1e-10 * np.abs(D).max()
+    # and the curl part is what makes D large: at s = 1e-6 the matrix is O(1)
+    assert np.abs(D).max() > 1e-2
+
+
+def test_regular_pair_blocks_symmetric():
+    v, t = meshes.icosphere(1)
+    rng = np.random.default_rng(4)
+    done = 0
+    while done < 6:
+        a, b = rng.integers(0, t.shape[0], 2)
+        if G.classify(t, int(a), int(b))[0] != "regular":
+            continue
+        D1 = P1.local_block(v, t, int(a), int(b), S, "d")
+        D2 = P1.local_block(v, t, int(b), int(a), S, "d")
+        assert np.abs(D1 - D2.transpose(1, 0, 2)).max() <= 1e-13 * np.abs(D1).max()
+        done += 1
+
+
+@pytest.mark.parametrize("case", ["identical", "edge", "vertex"])
+def test_singular_p1_blocks_sum_to_p0_integrals(case):
+    """sum over a, b of the local P1 integrals of U is the P0 integral of
+    oracle.galerkin (the barycentric coordinates sum to one): checked through
+    the s^2 part of D with the curl part removed."""
+    v, t = meshes.icosphere(1)
+    pairs = [(a, b) for a in range(t.shape[0]) for b in range(t.shape[0]) if G.classify(t, a, b)[0] == case]
+    a, b = pairs[0]
+    D = P1.local_block(v, t, a, b, S, "d")
+    Px, nx, ax = P1.panel(v, t[a])
+    Py, ny, ay = P1.panel(v, t[b])
+    cx, cy = P1.surface_curls(Px, nx, ax), P1.surface_curls(Py, ny, ay)
+    i0 = G.entries(v, t, [a], [b], S)[0]
+    s2part = D - (cx @ cy.T)[:, :, None] * i0[None, None, :]
+    assert np.allclose(s2part.sum(axis=(0, 1)), S ** 2 * float(nx @ ny) * i0, rtol=1e-12, atol=0)
