@@ -63,7 +63,15 @@ typedef enum {
 typedef enum {
     G3_SLP = 0,          /* V: exp(-s r)/(4 pi r)                                  */
     G3_DLP = 1,          /* K: exp(-s r)(1 + s r)((x - y).n_y)/(4 pi r^3)          */
-    G3_SEPARABLE = 2     /* synthetic sum_t a_t[i] b_t[j] c_t[k] (test tensors)     */
+    G3_SEPARABLE = 2,    /* synthetic sum_t a_t[i] b_t[j] c_t[k] (test tensors)     */
+    /* Galerkin with linear continuous elements (eq. (bie_semi_neum), the Neumann
+     * problem), on a tree of build_p1_tree and with G3_GALERKIN4x4: rows and
+     * columns are element-local shape functions, the nodal matrix is
+     * P^T A P (P: element-local function -> its vertex). */
+    G3_HYPERSINGULAR = 4, /* D in the integration-by-parts (Maue) form:
+                             (curl phi_i . curl phi_j) int int U + s^2 (n_x . n_y) int int U phi_i phi_j */
+    G3_ADJOINT_DLP = 5    /* K': int int phi_i(x) dU/dn_x phi_j(y),
+                             dU/dn_x = -exp(-s r)(1 + s r)((x - y).n_x)/(4 pi r^3)          */
 } g3_kernel;
 
 /* Spatial scheme (paper Section 3, eq. (bie_semi_diri), eq. (bie_semi_indirect)). */
@@ -337,6 +345,20 @@ g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, in
 g3_status g3_tree_partition_host(const double* verts, int nv, const int32_t* tris, int ne, int leaf, double eta,
                                  int max_block, int32_t* perm, int32_t* blocks, int64_t blocks_cap,
                                  int64_t* n_blocks);
+/* Tree of element-local linear shape functions (linear continuous elements,
+ * eq. (bie_semi_neum)) over an element tree `elem` of build_cluster_tree (no
+ * counterpart beyond the paper's choice of shape functions): row 3 e + a is the
+ * shape function of local vertex a (the element's vertex order) of element e;
+ * cluster position 3 p + a; the nodes and blocks are those of `elem` with
+ * tripled index ranges, so the block partition is the element partition.  The
+ * tree owns copies of everything it needs (`elem` may be freed).  Use with
+ * G3_HYPERSINGULAR / G3_ADJOINT_DLP and G3_GALERKIN4x4 in assemble_near,
+ * aca3_compress (G3_MIXED or G3_FP64, block by block; not batched, whole-matrix
+ * or with a predictor) and apply_gcq (G3_APPLY_SUM; W and Y are NODAL, nv rows:
+ * the apply gathers w at each shape function's vertex and adds the rows of
+ * y into their vertices).  Errors: G3_EINVAL for a NULL argument or a tree that
+ * is not an element tree. */
+g3_status build_p1_tree(g3_ctx* ctx, const g3_tree* elem, g3_tree** out);
 g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near);
 /* Copy to host (any output may be NULL):
  *   perm [ne]            cluster position -> original element index

@@ -210,6 +210,25 @@ def dense_nodal(verts, tris, s, op: str, n: int = 6) -> np.ndarray:
     return out
 
 
+def nodal_rows(verts, tris, rows, s, op: str, n: int = 6) -> np.ndarray:
+    """Rows [len(rows), nv, m] of the nodal Galerkin matrix of D ("d") or K'
+    ("kp"): for each row vertex, the sum over the elements that contain it of
+    their local blocks with every element."""
+    verts = np.asarray(verts, dtype=np.float64)
+    tris = np.asarray(tris)
+    s = np.atleast_1d(np.asarray(s, dtype=np.complex128))
+    nv, E = verts.shape[0], tris.shape[0]
+    out = np.zeros((len(rows), nv, s.size), complex)
+    for r, i in enumerate(rows):
+        for t in np.flatnonzero((tris == i).any(axis=1)):
+            a = list(tris[t]).index(i)
+            for u in range(E):
+                blk = local_block(verts, tris, int(t), u, s, op, n)
+                for b in range(3):
+                    out[r, tris[u][b]] += blk[a, b]
+    return out
+
+
 def mass_p1(verts, tris) -> np.ndarray:
     """Nodal mass matrix int phi_i phi_j (exact: area / 12 (1 + delta_ab))."""
     verts = np.asarray(verts, dtype=np.float64)

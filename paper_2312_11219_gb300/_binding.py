@@ -23,7 +23,9 @@ if not os.path.exists(LIB_PATH):
 
 _lib = C.CDLL(LIB_PATH)
 
-KERNELS = {"slp": 0, "dlp": 1}
+# "hyp": hypersingular operator D, "adj": adjoint double layer K' (Galerkin,
+# linear continuous elements, on a tree of build_p1_tree)
+KERNELS = {"slp": 0, "dlp": 1, "hyp": 4, "adj": 5}
 SCHEMES = {"colloc7": 0, "galerkin4x4": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "G3_OK", -1: "G3_EINVAL", -2: "G3_ENOMEM", -3: "G3_ECUDA", -4: "G3_ETIMEOUT",
@@ -88,6 +90,7 @@ _sig("g3_freqs_get", _ci, _p, _dp, _dp, _i32p, _i32p)
 _sig("g3_freqs_free", _ci, _p)
 _sig("build_cluster_tree", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _pp)
 _sig("build_cluster_tree_capped", _ci, _p, _dp, _ci, _i32p, _ci, _ci, C.c_double, _ci, _pp)
+_sig("build_p1_tree", _ci, _p, _p, _pp)
 _sig("g3_tree_info", _ci, _p, *(C.POINTER(_ci),) * 5)
 _sig("g3_shard_rows", _ci, _i32p, _ci, _i32p, _ci, _dp, _ci, _i32p, _dp, C.POINTER(_ci))
 _sig("g3_tree_partition_host", _ci, _dp, _ci, _i32p, _ci, _ci, C.c_double, _ci, _i32p, _i32p, C.c_int64,
@@ -128,7 +131,7 @@ _sig("g3_factors_labels", _ci, _p, _p, _fp)
 
 EXPORTED = ["g3_create", "g3_set_stream", "g3_set_apply_tensor_cores", "g3_destroy", "g3_last_error", "g3_version", "g3_launch_count",
             "g3_kernel_name", "g3_freqs_bdf2", "g3_freqs_gcq", "g3_freqs_from_array", "g3_freqs_info", "g3_freqs_get", "g3_freqs_free",
-            "build_cluster_tree", "build_cluster_tree_capped", "g3_shard_rows", "g3_tree_partition_host", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
+            "build_cluster_tree", "build_cluster_tree_capped", "build_p1_tree", "g3_shard_rows", "g3_tree_partition_host", "g3_tree_subset", "g3_tree_info", "g3_tree_get", "g3_tree_free", "g3_entries", "assemble_near",
             "g3_near_info", "g3_near_get_block", "g3_near_free", "aca3_compress", "aca3_compress_batch", "g3_autotune", "aca3_compress_separable",
             "g3_factors_stats", "g3_factors_ranks", "g3_factors_block_cycles", "g3_factors_block_phases", "g3_factors_get_block", "g3_factors_free", "apply_gcq",
             "g3_apply_last", "g3_peak", "apply_gcq_noalloc", "g3_gcq_history", "g3_mlp_create", "g3_mlp_train", "g3_mlp_fit",
@@ -297,6 +300,16 @@ def build_cluster_tree(ctx: Context, verts, tris, leaf: int = 32, eta: float = 1
     h = C.c_void_p()
     _check(_lib.build_cluster_tree_capped(ctx.h, _ptr(v, C.c_double), v.shape[0], _ptr(t, C.c_int32), t.shape[0],
                                           leaf, eta, max_block, C.byref(h)), "build_cluster_tree")
+    return Tree(h, (ctx,))
+
+
+def build_p1_tree(ctx: Context, tree: Tree) -> Tree:
+    """Tree of element-local linear shape functions over an element tree:
+    row 3 e + a is local vertex a of element e (cluster position 3 p + a);
+    the operators "hyp" and "adj" with scheme "galerkin4x4" run on it, and
+    apply_gcq on it takes nodal densities (nv rows) and returns nodal y."""
+    h = C.c_void_p()
+    _check(_lib.build_p1_tree(ctx.h, tree.h, C.byref(h)), "build_p1_tree")
     return Tree(h, (ctx,))
 
 

@@ -22,12 +22,13 @@ LIB = os.path.join(LIBDIR, "libg3aca.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_aca_sep.cu", "g3_aca_gal.cu", "g3_apply.cu",
+CU_SOURCES = ["g3_prep.cu", "g3_aca.cu", "g3_aca_slp.cu", "g3_aca_dlp.cu", "g3_aca_sep.cu", "g3_aca_gal.cu",
+              "g3_aca_p1.cu", "g3_apply.cu",
               "g3_api.cu",
               "g3_probe.cu", "g3_mlp.cu", "g3_gcq.cu"]
 # the compression-kernel instantiations of each kernel kind are compiled in
 # this many parts (-DG3_ACA_PART=0..), one nvcc process each
-ACA_PARTS = {"g3_aca_slp.cu": 4, "g3_aca_dlp.cu": 4, "g3_aca_sep.cu": 4, "g3_aca_gal.cu": 4}
+ACA_PARTS = {"g3_aca_slp.cu": 4, "g3_aca_dlp.cu": 4, "g3_aca_sep.cu": 4, "g3_aca_gal.cu": 4, "g3_aca_p1.cu": 4}
 CPP_SOURCES = ["g3_tree.cpp"]
 
 

@@ -22,6 +22,15 @@ G3_ACA_EXTERN_KIND(G3_SLP)
 G3_ACA_EXTERN_KIND(G3_DLP)
 G3_ACA_EXTERN_KIND(G3_SEPARABLE)
 G3_ACA_EXTERN_KIND(G3_GAL_SLP)
+// linear-element operators: the 256-thread launches only
+G3_ACA_EXTERN(G3_GAL_P1D, float, 256, false)
+G3_ACA_EXTERN(G3_GAL_P1D, float, 256, true)
+G3_ACA_EXTERN(G3_GAL_P1D, double, 256, false)
+G3_ACA_EXTERN(G3_GAL_P1D, double, 256, true)
+G3_ACA_EXTERN(G3_GAL_P1KP, float, 256, false)
+G3_ACA_EXTERN(G3_GAL_P1KP, float, 256, true)
+G3_ACA_EXTERN(G3_GAL_P1KP, double, 256, false)
+G3_ACA_EXTERN(G3_GAL_P1KP, double, 256, true)
 
 #define G3_WHOLE_EXTERN(KER, T)                                                                              \
     extern template g3_status launch_whole_t<KER, T>(g3_ctx*, AcaArgs<T>&, int, size_t, int, int, const double*, \
@@ -41,6 +50,12 @@ static g3_status launch_kind(g3_ctx* ctx, int kernel, AcaArgs<T>& A, int grid, s
     if (kernel == G3_SLP) return launch_aca_t<G3_SLP, T, NT, DENSE>(ctx, A, grid, smem);
     if (kernel == G3_DLP) return launch_aca_t<G3_DLP, T, NT, DENSE>(ctx, A, grid, smem);
     if (kernel == G3_GAL_SLP) return launch_aca_t<G3_GAL_SLP, T, NT, DENSE>(ctx, A, grid, smem);
+    if (kernel == G3_GAL_P1D || kernel == G3_GAL_P1KP) {
+        if constexpr (NT == 256)
+            return kernel == G3_GAL_P1D ? launch_aca_t<G3_GAL_P1D, T, NT, DENSE>(ctx, A, grid, smem)
+                                        : launch_aca_t<G3_GAL_P1KP, T, NT, DENSE>(ctx, A, grid, smem);
+        return fail(G3_EUNSUPPORTED, "aca3_compress: linear-element operators run with 256 threads per CTA");
+    }
     return launch_aca_t<G3_SEPARABLE, T, NT, DENSE>(ctx, A, grid, smem);
 }
 
@@ -49,6 +64,12 @@ static int occupancy_kind(int kernel, size_t smem) {
     if (kernel == G3_SLP) return occupancy<G3_SLP, T, NT, DENSE>(smem);
     if (kernel == G3_DLP) return occupancy<G3_DLP, T, NT, DENSE>(smem);
     if (kernel == G3_GAL_SLP) return occupancy<G3_GAL_SLP, T, NT, DENSE>(smem);
+    if (kernel == G3_GAL_P1D || kernel == G3_GAL_P1KP) {
+        if constexpr (NT == 256)
+            return kernel == G3_GAL_P1D ? occupancy<G3_GAL_P1D, T, NT, DENSE>(smem)
+                                        : occupancy<G3_GAL_P1KP, T, NT, DENSE>(smem);
+        return 1;
+    }
     return occupancy<G3_SEPARABLE, T, NT, DENSE>(smem);
 }
 
@@ -950,6 +971,8 @@ static g3_status run_aca_whole_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* 
 g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* fa, int kernel, int scheme,
                   double eps3, const g3_opts& o, const void* sep_a, const void* sep_b, const void* sep_c, int sep_R) {
     if (o.whole_matrix) {
+        if (kernel == G3_GAL_P1D || kernel == G3_GAL_P1KP)
+            return fail(G3_EUNSUPPORTED, "aca3_compress: whole_matrix is not implemented for linear elements");
         if (kernel == G3_SEPARABLE || o.unbatched)
             return fail(G3_EUNSUPPORTED, "aca3_compress: whole_matrix applies to boundary element operators, not unbatched");
         if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
@@ -959,9 +982,10 @@ g3_status run_aca(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_factors* 
         if (fa->prec == G3_MIXED) return run_aca_whole_t<float>(ctx, t, f, fa, kk, eps3, o);
         return run_aca_whole_t<double>(ctx, t, f, fa, kk, eps3, o);
     }
-    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+    const bool p1 = kernel == G3_GAL_P1D || kernel == G3_GAL_P1KP;
+    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP && !p1)
         return fail(G3_EUNSUPPORTED, "aca3_compress: the Galerkin scheme is implemented for G3_SLP");
-    if (scheme == G3_GALERKIN4x4) kernel = G3_GAL_SLP;
+    if (scheme == G3_GALERKIN4x4 && !p1) kernel = G3_GAL_SLP;
     if (fa->Ku > KU_MAX) return fail(G3_EINVAL, "aca3_compress: %d unique frequencies exceed %d", fa->Ku, KU_MAX);
     std::vector<AcaJob> jobs(1);
     jobs[0].t = t;

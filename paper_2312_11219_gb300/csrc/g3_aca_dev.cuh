@@ -289,6 +289,15 @@ __device__ __forceinline__ Cx<T> ent(const AcaArgs<T>& A, int gi, int gj, int k)
             const double2 s = A.sd[k];
             return gal_regular<T>(A.gf, A.gd, gi, gj, s.x, s.y);
         }
+    } else if constexpr (KER == G3_GAL_P1D || KER == G3_GAL_P1KP) {
+        // linear elements, element-local functions: regular pairs only (as above)
+        if constexpr (sizeof(T) == 4) {
+            const float2 s = A.sf[k];
+            return p1_entry<KER, T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        } else {
+            const double2 s = A.sd[k];
+            return p1_entry<KER, T>(A.gf, A.gd, gi, gj, s.x, s.y);
+        }
     } else {
         if constexpr (sizeof(T) == 4) {
             const float2 s = A.sf[k];
@@ -347,7 +356,7 @@ __device__ __forceinline__ Cx<T> colloc_q(const G& g, int i, int j, int q, T sre
 // entry (admissible blocks hold no self entries).
 template <int KER, class T>
 __device__ __forceinline__ Cx<T> ent_part(const AcaArgs<T>& A, int gi, int gj, int k, int part, int G) {
-    if constexpr (KER == G3_SEPARABLE) {
+    if constexpr (KER == G3_SEPARABLE || KER == G3_GAL_P1D || KER == G3_GAL_P1KP) {
         return part == 0 ? ent<KER, T>(A, gi, gj, k) : Cx<T>{0, 0};
     } else if constexpr (KER == G3_GAL_SLP) {
         // 16 terms dealt round-robin to the gang's parts
@@ -2479,6 +2488,8 @@ g3_status launch_aca_t(g3_ctx* ctx, AcaArgs<T>& A, int grid, size_t smem) {
     kfn<<<grid, NT, smem, ctx->stream>>>(A);
     ctx->count(KER == G3_SEPARABLE   ? (DENSE ? "k_aca3_dense_separable" : "k_aca3_separable")
                : KER == G3_GAL_SLP ? (DENSE ? "k_aca3_dense_galerkin" : "k_aca3_galerkin")
+               : KER == G3_GAL_P1D ? (DENSE ? "k_aca3_dense_hypersingular" : "k_aca3_hypersingular")
+               : KER == G3_GAL_P1KP ? (DENSE ? "k_aca3_dense_adjoint_dlp" : "k_aca3_adjoint_dlp")
                                    : (DENSE ? "k_aca3_dense" : "k_aca3"));
     G3_CUDA(cudaGetLastError());
     return G3_OK;

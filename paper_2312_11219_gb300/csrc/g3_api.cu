@@ -435,6 +435,7 @@ g3_status build_cluster_tree_capped(g3_ctx* ctx, const double* verts, int nv, co
 
 g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, int rank, g3_tree** out) {
     G3_CHECK(ctx && t && owner && out, "g3_tree_subset: NULL argument");
+    G3_CHECK(!t->p1, "g3_tree_subset: the input must be an element tree");
     *out = nullptr;
     G3_TRY(use_device(ctx));
     g3_tree* s = new (std::nothrow) g3_tree();
@@ -478,6 +479,112 @@ g3_status g3_tree_subset(g3_ctx* ctx, const g3_tree* t, const int32_t* owner, in
     return G3_OK;
 }
 
+// tree of element-local linear shape functions (linear continuous elements):
+// position 3 p + a is local vertex a of the element at cluster position p;
+// nodes and blocks are the element tree's with tripled ranges; the geometry
+// stays per element, with the surface curls of the shape functions added
+g3_status build_p1_tree(g3_ctx* ctx, const g3_tree* t, g3_tree** out) {
+    G3_CHECK(ctx && t && out, "build_p1_tree: NULL argument");
+    *out = nullptr;
+    G3_CHECK(!t->p1 && !t->subset, "build_p1_tree: the input must be an element tree of build_cluster_tree");
+    G3_TRY(use_device(ctx));
+    g3_tree* s = new (std::nothrow) g3_tree();
+    if (!s) return fail(G3_ENOMEM, "build_p1_tree: out of host memory");
+    const int E = t->ne;
+    s->ctx = ctx;
+    s->device = ctx->device;
+    s->ne = E;  // element count while the geometry is set up (below: 3 E)
+    s->nv = t->nv;
+    s->leaf = t->leaf;
+    s->max_block = t->max_block;
+    s->eta = t->eta;
+    s->verts = t->verts;
+    s->tris = t->tris;
+    s->p1 = true;
+    s->ne_elem = E;
+    s->perm_elem = t->perm;
+    s->boxes = t->boxes;
+    s->nodes = t->nodes;
+    for (size_t n = 0; n < s->nodes.size() / 4; ++n) {
+        s->nodes[4 * n] *= 3;
+        s->nodes[4 * n + 1] *= 3;
+    }
+    s->blocks = t->blocks;
+    for (size_t b = 0; b < s->blocks.size() / 5; ++b)
+        for (int k = 0; k < 4; ++k) s->blocks[5 * b + k] *= 3;
+    tree_index_blocks(s);
+    g3_status st = G3_OK;
+    auto chk = [&](cudaError_t e, const char* w) {
+        if (st == G3_OK && e != cudaSuccess) st = cuda_fail(e, w);
+    };
+    // element geometry (cluster order of the elements)
+    chk(s->d_perm.alloc(E * sizeof(int)), "build_p1_tree: perm");
+    if (st == G3_OK) chk(cudaMemcpy(s->d_perm.p, t->perm.data(), E * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    std::vector<int> tv(3 * (size_t)E);
+    for (int p = 0; p < E; ++p)
+        for (int k = 0; k < 3; ++k) tv[3 * (size_t)p + k] = t->tris[3 * (size_t)t->perm[p] + k];
+    chk(s->d_tv.alloc(tv.size() * sizeof(int)), "build_p1_tree: vertex ids");
+    if (st == G3_OK) chk(cudaMemcpy(s->d_tv.p, tv.data(), tv.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    if (st == G3_OK) st = launch_geometry(ctx, s);
+    // surface curls of the barycentric coordinates, float64 on the host:
+    // curl lambda_a = n x grad lambda_a, grad lambda_a = n x (v_{a+2} - v_{a+1}) / (2 area)
+    std::vector<double> cd(9 * (size_t)E);
+    std::vector<float> cf(9 * (size_t)E);
+    for (int p = 0; p < E && st == G3_OK; ++p) {
+        double v[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) v[a][k] = t->verts[3 * (size_t)tv[3 * (size_t)p + a] + k];
+        double u[3], w[3];
+        for (int k = 0; k < 3; ++k) {
+            u[k] = v[1][k] - v[0][k];
+            w[k] = v[2][k] - v[0][k];
+        }
+        double c[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double a2 = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        const double n[3] = {c[0] / a2, c[1] / a2, c[2] / a2};
+        for (int a = 0; a < 3; ++a) {
+            const double* p2 = v[(a + 2) % 3];
+            const double* p1 = v[(a + 1) % 3];
+            const double e[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+            const double g[3] = {(n[1] * e[2] - n[2] * e[1]) / a2, (n[2] * e[0] - n[0] * e[2]) / a2,
+                                 (n[0] * e[1] - n[1] * e[0]) / a2};
+            const double cu[3] = {n[1] * g[2] - n[2] * g[1], n[2] * g[0] - n[0] * g[2], n[0] * g[1] - n[1] * g[0]};
+            for (int k = 0; k < 3; ++k) {
+                cd[(a * 3 + k) * (size_t)E + p] = cu[k];
+                cf[(a * 3 + k) * (size_t)E + p] = (float)cu[k];
+            }
+        }
+    }
+    chk(s->d_curl_d.alloc(cd.size() * sizeof(double)), "build_p1_tree: curls");
+    chk(s->d_curl_f.alloc(cf.size() * sizeof(float)), "build_p1_tree: curls");
+    if (st == G3_OK) chk(cudaMemcpy(s->d_curl_d.p, cd.data(), cd.size() * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    if (st == G3_OK) chk(cudaMemcpy(s->d_curl_f.p, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice), "copy");
+    // positions of the degrees of freedom: original index 3 e + a and vertex
+    std::vector<int32_t> perm3(3 * (size_t)E), src(3 * (size_t)E);
+    for (int p = 0; p < E; ++p)
+        for (int a = 0; a < 3; ++a) {
+            perm3[3 * (size_t)p + a] = 3 * t->perm[p] + a;
+            src[3 * (size_t)p + a] = tv[3 * (size_t)p + a];
+        }
+    if (st == G3_OK) {
+        s->gf.curl = s->d_curl_f.as<float>();
+        s->gd.curl = s->d_curl_d.as<double>();
+        s->perm = perm3;
+        s->ne = 3 * E;
+        chk(s->d_perm.alloc(perm3.size() * sizeof(int)), "build_p1_tree: perm");
+        if (st == G3_OK)
+            chk(cudaMemcpy(s->d_perm.p, perm3.data(), perm3.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
+        chk(s->d_src.alloc(src.size() * sizeof(int)), "build_p1_tree: vertices");
+        if (st == G3_OK) chk(cudaMemcpy(s->d_src.p, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    }
+    if (st != G3_OK) {
+        delete s;
+        return st;
+    }
+    *out = s;
+    return G3_OK;
+}
+
 g3_status g3_tree_info(const g3_tree* t, int* ne, int* n_nodes, int* n_blocks, int* n_far, int* n_near) {
     G3_CHECK(t != nullptr, "g3_tree_info: NULL handle");
     if (ne) *ne = t->ne;
@@ -512,6 +619,12 @@ g3_status g3_tree_free(g3_tree* t) {
 // ---------------------------------------------------------------------------
 
 static bool valid_kernel(int k) { return k == G3_SLP || k == G3_DLP; }
+// kernel for a tree and scheme: the operators of linear elements need a tree
+// of build_p1_tree and the Galerkin scheme, the others an element tree
+static bool kernel_fits_tree(int k, int scheme, const g3_tree* t) {
+    if (t->p1) return (k == G3_HYPERSINGULAR || k == G3_ADJOINT_DLP) && scheme == G3_GALERKIN4x4;
+    return valid_kernel(k);
+}
 static bool valid_prec(int p) { return p == G3_FP64 || p == G3_MIXED; }
 
 g3_status g3_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
@@ -521,7 +634,21 @@ g3_status g3_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel
     G3_CHECK(n >= 0 && nk >= 0, "g3_entries: negative size");
     G3_CHECK(n == 0 || (rows && cols), "g3_entries: rows/cols NULL");
     G3_CHECK(nk == 0 || kidx, "g3_entries: kidx NULL");
-    G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "g3_entries: bad kernel or precision");
+    G3_CHECK(valid_prec(prec), "g3_entries: bad precision");
+    G3_CHECK(kernel_fits_tree(kernel, scheme, t), "g3_entries: kernel %d with scheme %d does not fit this tree",
+             (int)kernel, (int)scheme);
+    if (t->p1)  // linear elements: the regular rule only (pairs of elements without a common vertex)
+        for (int i = 0; i < n; ++i) {
+            G3_CHECK(rows[i] >= 0 && rows[i] < t->ne && cols[i] >= 0 && cols[i] < t->ne,
+                     "g3_entries: pair %d = (%d, %d) outside [0, %d)", i, rows[i], cols[i], t->ne);
+            const int* a = &t->tris[3 * (size_t)(rows[i] / 3)];
+            const int* b = &t->tris[3 * (size_t)(cols[i] / 3)];
+            bool shared = false;
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) shared |= a[x] == b[y];
+            if (shared)
+                return fail(G3_EUNSUPPORTED, "g3_entries: pair %d of linear elements shares a vertex (near field only)", i);
+        }
     if (n == 0 || nk == 0) return G3_OK;
     G3_TRY(use_device(ctx));
     std::vector<int> inv(t->ne);
@@ -570,10 +697,13 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
                         g3_precision prec, g3_near** out) {
     G3_CHECK(ctx && t && f && out, "assemble_near: NULL argument");
     *out = nullptr;
-    G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "assemble_near: bad kernel or precision");
+    G3_CHECK(valid_prec(prec), "assemble_near: bad precision");
     G3_CHECK(scheme == G3_COLLOC7 || scheme == G3_GALERKIN4x4, "assemble_near: bad scheme");
-    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
-        return fail(G3_EUNSUPPORTED, "assemble_near: the Galerkin scheme is implemented for G3_SLP");
+    G3_CHECK(kernel_fits_tree(kernel, scheme, t),
+             "assemble_near: kernel %d with scheme %d does not fit this tree (linear-element operators need a "
+             "tree of build_p1_tree and G3_GALERKIN4x4)", (int)kernel, (int)scheme);
+    if (!t->p1 && scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+        return fail(G3_EUNSUPPORTED, "assemble_near: the Galerkin scheme with piecewise-constant elements is implemented for G3_SLP");
     G3_TRY(use_device(ctx));
     g3_near* nf = new (std::nothrow) g3_near();
     if (!nf) return fail(G3_ENOMEM, "assemble_near: out of host memory");
@@ -624,7 +754,31 @@ g3_status assemble_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
     // Galerkin: the pairs with a common vertex (Sauter-Schwab); they all lie
     // in near blocks (a far block's clusters have disjoint boxes)
     std::vector<SsPair> ss;
-    if (scheme == G3_GALERKIN4x4) {
+    if (t->p1) {
+        // element pairs with a common vertex inside each near block; the local
+        // entries (a, b) of the pair sit at off + a + b M (frequency stride M N)
+        const int E = t->ne_elem;
+        std::vector<int> tv(3 * (size_t)E);
+        for (int p = 0; p < E; ++p)
+            for (int k = 0; k < 3; ++k) tv[3 * (size_t)p + k] = t->tris[3 * (size_t)t->perm_elem[p] + k];
+        for (size_t b = 0; b < rg.size(); ++b) {
+            const BlockRange& r = rg[b];
+            const int M = r.re - r.rb, N = r.ce - r.cb;
+            for (int je = r.cb / 3; je < r.ce / 3; ++je)
+                for (int ie = r.rb / 3; ie < r.re / 3; ++ie) {
+                    SsPair q{};
+                    q.cas = ss_classify(&tv[3 * (size_t)ie], &tv[3 * (size_t)je], ie == je, q.px, q.py);
+                    if (q.cas == SS_REGULAR) continue;
+                    q.i = ie;
+                    q.j = je;
+                    q.stride = M * N;
+                    q.ldm = M;
+                    q.off = nf->offs[b] + (long long)(3 * je - r.cb) * M + (3 * ie - r.rb);
+                    ss.push_back(q);
+                }
+        }
+        nf->n_ss = (int)ss.size();
+    } else if (scheme == G3_GALERKIN4x4) {
         std::vector<int> tv(3 * (size_t)t->ne);
         for (int p = 0; p < t->ne; ++p)
             for (int k = 0; k < 3; ++k) tv[3 * (size_t)p + k] = t->tris[3 * (size_t)t->perm[p] + k];
@@ -747,10 +901,18 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
                         g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out) {
     G3_CHECK(ctx && t && f && out, "aca3_compress: NULL argument");
     *out = nullptr;
-    G3_CHECK(valid_kernel(kernel) && valid_prec(prec), "aca3_compress: bad kernel or precision");
+    G3_CHECK(valid_prec(prec), "aca3_compress: bad precision");
     G3_CHECK(scheme == G3_COLLOC7 || scheme == G3_GALERKIN4x4, "aca3_compress: bad scheme");
+    G3_CHECK(kernel_fits_tree(kernel, scheme, t),
+             "aca3_compress: kernel %d with scheme %d does not fit this tree (linear-element operators need a "
+             "tree of build_p1_tree and G3_GALERKIN4x4)", (int)kernel, (int)scheme);
     G3_CHECK(eps3 > 0 && eps3 < 1, "aca3_compress: eps3 = %g outside (0, 1)", eps3);
     g3_opts o = defaults(opts);
+    if (t->p1) {
+        G3_CHECK(o.threads == 0 || o.threads == 256, "aca3_compress: linear-element operators run with 256 threads");
+        G3_CHECK(o.mlp == nullptr && !o.whole_matrix && !o.unbatched,
+                 "aca3_compress: linear-element operators take no predictor, whole-matrix or unbatched run");
+    }
     G3_CHECK(o.face_rank_max >= 0 && o.face_rank_max <= 64, "aca3_compress: face_rank_max = %d outside [0, 64]", o.face_rank_max);
     G3_CHECK(o.threads == 0 || o.threads == 128 || o.threads == 256 || o.threads == 384 || o.threads == 512,
              "aca3_compress: threads must be 0, 128, 256, 384 or 512");
@@ -994,11 +1156,13 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
     G3_CHECK(mem == G3_DEVICE || mem == G3_HOST, "apply_gcq: bad memory kind");
     G3_CHECK(!nf || nf->tree == t, "apply_gcq: near field built on another tree");
     G3_CHECK(!fa || fa->tree == t, "apply_gcq: factors built on another tree");
+    G3_CHECK(!t->p1 || mode == G3_APPLY_SUM, "apply_gcq: linear-element trees take G3_APPLY_SUM");
     G3_TRY(use_device(ctx));
     const g3_freqs* f = nf ? nf->freqs : fa->freqs;
     const size_t esz = dtype == G3_C128 ? 16 : 8;
-    const size_t wbytes = (size_t)t->ne * f->K * esz;
-    const size_t ybytes = (size_t)t->ne * (mode == G3_APPLY_SUM ? 1 : f->K) * esz;
+    const size_t rows = t->p1 ? (size_t)t->nv : (size_t)t->ne;  // linear elements: nodal W and Y
+    const size_t wbytes = rows * f->K * esz;
+    const size_t ybytes = rows * (mode == G3_APPLY_SUM ? 1 : f->K) * esz;
     if (mem == G3_DEVICE) return run_apply(ctx, t, nf, fa, W, Y, dtype, mode);
     // host buffers: staged through context-owned device buffers (kept for reuse)
     G3_CUDA(ctx->stage_w.ensure(wbytes));

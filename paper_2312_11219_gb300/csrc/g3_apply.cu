@@ -31,20 +31,22 @@ constexpr int RF_TS = 64;
 // W (original order, column l = w_l, M x K column-major, complex TI) ->
 // Wf[k][p] = w_{uniq[k]}[perm[p]],  Wc[k][p] = w_{partner(uniq[k])}[perm[p]] or 0
 // (cluster order, frequency-major), and y := 0.
+// ldw: rows of W (E, or the vertex count for linear-element trees, where perm is
+// the vertex of each position: the gather w_loc = P w of the nodal densities)
 template <class TI, class T>
 __global__ void k_apply_prep(int E, int K, int Ku, const int* __restrict__ perm, const int* __restrict__ uniq,
                              const int* __restrict__ partner, const Cx<TI>* __restrict__ W, Cx<T>* __restrict__ Wf,
-                             Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y) {
+                             Cx<T>* __restrict__ Wc, Cx<T>* __restrict__ y, int ldw) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx < E) y[idx] = Cx<T>{0, 0};
     if (idx >= (long long)Ku * E) return;
     const int k = (int)(idx / E), p = (int)(idx % E);
     const int e = perm[p];
     const int l = uniq[k], lp = partner[l];
-    Cx<TI> a = W[(long long)l * E + e];
+    Cx<TI> a = W[(long long)l * ldw + e];
     Wf[idx] = Cx<T>{(T)a.x, (T)a.y};
     if (lp != l) {
-        Cx<TI> b = W[(long long)lp * E + e];
+        Cx<TI> b = W[(long long)lp * ldw + e];
         Wc[idx] = Cx<T>{(T)b.x, (T)b.y};
     } else {
         Wc[idx] = Cx<T>{0, 0};
@@ -558,6 +560,17 @@ __global__ void k_apply_finish(int E, const int* __restrict__ perm, const Cx<T>*
     Cx<T> v = y[p];
     Y[perm[p]] = Cx<TO>{(TO)v.x, (TO)v.y};
 }
+// linear elements: y = P^T y_loc, each position's row added into its vertex
+// (Y cleared before)
+template <class T, class TO>
+__global__ void k_apply_finish_add(int E, const int* __restrict__ src, const Cx<T>* __restrict__ y,
+                                   Cx<TO>* __restrict__ Y) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= E) return;
+    Cx<T> v = y[p];
+    atomicAdd(&Y[src[p]].x, (TO)v.x);
+    atomicAdd(&Y[src[p]].y, (TO)v.y);
+}
 
 
 // near-field launch: grid (row clusters) x (frequency chunks), about 16 CTAs
@@ -766,26 +779,38 @@ static g3_status run_apply_t(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, c
     Cx<T>* abuf = reinterpret_cast<Cx<T>*>((reinterpret_cast<uintptr_t>(y + E) + 255) & ~uintptr_t(255));
     cudaEvent_t e0 = ctx->ev[2], e3 = ctx->ev[5];
     G3_CUDA(cudaEventRecord(e0, ctx->stream));
+    // linear-element trees: nodal W and Y (nv rows), gathered per position at its vertex
+    const int* rowsrc = t->p1 ? t->d_src.as<int>() : t->d_perm.as<int>();
+    const int ldw = t->p1 ? t->nv : E;
     {
         long long tot = (long long)Ku * E;
         int blocks = (int)((tot + 255) / 256);
         if (dtype == G3_C128)
-            k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
-                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, y);
+            k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, rowsrc, f->d_uniq.as<int>(),
+                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, y, ldw);
         else
-            k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
-                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, y);
+            k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, rowsrc, f->d_uniq.as<int>(),
+                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, y, ldw);
         ctx->count("k_apply_prep");
         G3_CUDA(cudaGetLastError());
     }
     G3_TRY_NA(apply_near_far<T>(ctx, t, nf, fa, Ku, E, Wf, Wc, y, abuf));
     {
         int blocks = (E + 255) / 256;
-        if (dtype == G3_C128)
-            k_apply_finish<T, double><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<double>*)Y);
-        else
-            k_apply_finish<T, float><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<float>*)Y);
-        ctx->count("k_apply_finish");
+        if (t->p1) {
+            G3_CUDA(cudaMemsetAsync(Y, 0, (size_t)t->nv * (dtype == G3_C128 ? 16 : 8), ctx->stream));
+            if (dtype == G3_C128)
+                k_apply_finish_add<T, double><<<blocks, 256, 0, ctx->stream>>>(E, rowsrc, y, (Cx<double>*)Y);
+            else
+                k_apply_finish_add<T, float><<<blocks, 256, 0, ctx->stream>>>(E, rowsrc, y, (Cx<float>*)Y);
+            ctx->count("k_apply_finish_add");
+        } else {
+            if (dtype == G3_C128)
+                k_apply_finish<T, double><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<double>*)Y);
+            else
+                k_apply_finish<T, float><<<blocks, 256, 0, ctx->stream>>>(E, t->d_perm.as<int>(), y, (Cx<float>*)Y);
+            ctx->count("k_apply_finish");
+        }
         G3_CUDA(cudaGetLastError());
     }
     G3_CUDA(cudaEventRecord(e3, ctx->stream));
@@ -1028,10 +1053,10 @@ static g3_status run_apply_perfreq_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         // k_apply_prep also clears its y argument: point it at yf (cleared anyway)
         if (dtype == G3_C128)
             k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
-                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, yf);
+                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, yf, E);
         else
             k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
-                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, yf);
+                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, yf, E);
         ctx->count("k_apply_prep");
         G3_CUDA(cudaGetLastError());
     }
@@ -1143,10 +1168,10 @@ static g3_status run_apply_noalloc_t(g3_ctx* ctx, const g3_tree* t, const g3_nea
         int blocks = (int)((tot + 255) / 256);
         if (dtype == G3_C128)
             k_apply_prep<double, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
-                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, y);
+                                                                   f->d_partner.as<int>(), (const Cx<double>*)W, Wf, Wc, y, E);
         else
             k_apply_prep<float, T><<<blocks, 256, 0, ctx->stream>>>(E, K, Ku, t->d_perm.as<int>(), f->d_uniq.as<int>(),
-                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, y);
+                                                                  f->d_partner.as<int>(), (const Cx<float>*)W, Wf, Wc, y, E);
         ctx->count("k_apply_prep");
         G3_CUDA(cudaGetLastError());
     }
@@ -1183,6 +1208,7 @@ extern "C" g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_n
                                        const void* W, void* Y, g3_dtype dtype) {
     using namespace g3;
     if (!ctx || !t || !W || !Y) return fail(G3_EINVAL, "apply_gcq_noalloc: NULL argument");
+    if (t->p1) return fail(G3_EUNSUPPORTED, "apply_gcq_noalloc: linear-element trees use apply_gcq");
     if (!nf && !fa) return fail(G3_EINVAL, "apply_gcq_noalloc: near field and factors are both NULL");
     if (dtype != G3_C64 && dtype != G3_C128) return fail(G3_EINVAL, "apply_gcq_noalloc: bad dtype");
     if ((nf && nf->tree != t) || (fa && fa->tree != t))

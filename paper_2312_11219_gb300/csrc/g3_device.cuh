@@ -338,6 +338,80 @@ __device__ __forceinline__ Cx<T> gal_regular(const GeomF& gf, const GeomD& gd, i
     return gal_eval(p, sre, sim);
 }
 
+// ---- Galerkin, linear continuous elements (element-local degrees of freedom) ------
+// Local function a of element p is the barycentric coordinate lambda_a of its
+// vertex a (the element's vertex order).  OP = G3_GAL_P1D: the hypersingular
+// operator in the Maue form
+//   (curl lambda_a . curl lambda_b) int int U + s^2 (n_p . n_q) int int U lambda_a lambda_b;
+// OP = G3_GAL_P1KP: the adjoint double layer int int lambda_a lambda_b dU/dn_x with
+//   dU/dn_x = -exp(-s r) (1 + s r) ((x - y) . n_x) / (4 pi r^3).
+// Pairs without a common vertex: the 4-point rule on both triangles, whose
+// points have the barycentric coordinates below (the rule of the geometry setup).
+__device__ __forceinline__ double p1_bary4(int q, int a) {
+    const double r6 = sqrt(6.0), r3 = sqrt(3.0);
+    const int ia = q >> 1, ib = q & 1;
+    const double u = ia == 0 ? (4.0 - r6) / 10.0 : (4.0 + r6) / 10.0;
+    const double v = ib == 0 ? 0.5 - 0.5 / r3 : 0.5 + 0.5 / r3;
+    const double l1 = u, l2 = v * (1.0 - u);
+    return a == 0 ? 1.0 - l1 - l2 : (a == 1 ? l1 : l2);
+}
+
+template <int OP, class G, class T>
+__device__ __noinline__ Cx<T> p1_regular(const G& g, int p, int a, int q, int b, T sre, T sim) {
+    T d[3];
+    cdiff(g, p, q, d);
+    Cx<T> i0{0, 0}, iab{0, 0};
+    const T np0 = (T)nrm(g, 0, p), np1 = (T)nrm(g, 1, p), np2 = (T)nrm(g, 2, p);
+#pragma unroll
+    for (int qa = 0; qa < 4; ++qa) {
+        const T la = (T)p1_bary4(qa, a);
+        const T xa0 = d[0] + q4off(g, qa, 0, p), xa1 = d[1] + q4off(g, qa, 1, p), xa2 = d[2] + q4off(g, qa, 2, p);
+        const T wa = q4wt(g, qa, p) * (T)G3_INV4PI;
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) {
+            const T lb = (T)p1_bary4(qb, b);
+            const T rx = xa0 - q4off(g, qb, 0, q), ry = xa1 - q4off(g, qb, 1, q), rz = xa2 - q4off(g, qb, 2, q);
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            const T ri = krsqrt(r2);
+            const T r = r2 * ri;
+            const T m = wa * q4wt(g, qb, q) * ri * kexp(-sre * r);   // w w' exp(-Re s r) / (4 pi r)
+            T sn, cs;
+            ksincos(sim * r, &sn, &cs);
+            if (OP == G3_GAL_P1D) {
+                const Cx<T> u{m * cs, -m * sn};
+                i0.x += u.x;
+                i0.y += u.y;
+                iab.x += la * lb * u.x;
+                iab.y += la * lb * u.y;
+            } else {
+                // -(1 + s r) exp(-s r) ((x - y) . n_x) / r^2 times the weight above
+                const T f = -m * (rx * np0 + ry * np1 + rz * np2) * ri * ri * la * lb;
+                const T fr = (T)1 + sre * r, fi = sim * r;
+                iab.x += f * (fr * cs + fi * sn);
+                iab.y += f * (fi * cs - fr * sn);
+            }
+        }
+    }
+    if (OP == G3_GAL_P1KP) return iab;
+    T cab = 0, nn = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        cab += (T)g.curl[(a * 3 + k) * g.E + p] * (T)g.curl[(b * 3 + k) * g.E + q];
+        nn += (T)nrm(g, k, p) * (T)nrm(g, k, q);
+    }
+    const T s2r = sre * sre - sim * sim, s2i = 2 * sre * sim;
+    return {cab * i0.x + nn * (s2r * iab.x - s2i * iab.y), cab * i0.y + nn * (s2r * iab.y + s2i * iab.x)};
+}
+
+// both geometries: the working precision's copy
+template <int OP, class T>
+__device__ __forceinline__ Cx<T> p1_entry(const GeomF& gf, const GeomD& gd, int gi, int gj, T sre, T sim) {
+    if constexpr (sizeof(T) == 4)
+        return p1_regular<OP>(gf, gi / 3, gi % 3, gj / 3, gj % 3, sre, sim);
+    else
+        return p1_regular<OP>(gd, gi / 3, gi % 3, gj / 3, gj % 3, sre, sim);
+}
+
 // Pairs with a common vertex, a common edge or identical panels: the
 // Sauter-Schwab transformations (Sauter and Schwab, Boundary Element Methods,
 // Section 5.2).  Reference triangle {0 <= x2 <= x1 <= 1}; panel map

@@ -72,6 +72,7 @@ struct GeomF {
     const float* n;    // [3][E] unit normal
     const float* q4;   // [4][3][E] 4-point (Galerkin) rule offsets
     const float* w4;   // [4][E]
+    const float* curl; // [3 local][3][E] surface curls of the linear shape functions (linear-element trees)
 };
 struct GeomD {
     int E;
@@ -83,6 +84,7 @@ struct GeomD {
     const double* q4;  // [4][3][E]
     const double* w4;  // [4][E]
     const double* gl;  // 24-point Gauss-Legendre nodes [24] then weights [24] on [-1, 1]
+    const double* curl; // [3 local][3][E] surface curls of the linear shape functions (linear-element trees)
 };
 
 #ifdef __CUDACC__
@@ -94,6 +96,11 @@ struct GeomD {
 // internal kernel kind of the Galerkin single layer (the C ABI passes G3_SLP
 // with G3_GALERKIN4x4)
 constexpr int G3_GAL_SLP = 3;
+// kernel kinds of the Galerkin operators with linear continuous elements (the
+// same values as their public g3_kernel names): hypersingular operator D and
+// adjoint double layer K', on element-local degrees of freedom
+constexpr int G3_GAL_P1D = 4;
+constexpr int G3_GAL_P1KP = 5;
 
 // Galerkin pairs with a common vertex: classification and vertex order for
 // the Sauter-Schwab rules (shared vertices first, in the same order in both
@@ -149,8 +156,10 @@ struct SsPair {
     int i, j;          // cluster positions of tau_x, tau_y
     int cas;           // SS_VERTEX, SS_EDGE or SS_IDENTICAL
     int stride;        // M_b N_b: distance between frequencies in the block
-    long long off;     // near-field offset of the entry at the first frequency
+    long long off;     // near-field offset of the entry at the first frequency (linear
+                       // elements: of the entry of local functions (0, 0))
     int8_t px[3], py[3];
+    int ldm;           // linear elements: rows M_b of the block (column stride of the local entries)
 };
 
 // synthetic separable tensor sum_t a[t][i] b[t][j] c[t][k] (complex, interleaved)
@@ -232,7 +241,15 @@ struct g3_freqs {
 struct g3_tree {
     g3_ctx* ctx = nullptr;
     int device = 0;                // the context's device (freeing needs no context)
-    int ne = 0, nv = 0, leaf = 0;
+    int ne = 0, nv = 0, leaf = 0;  // ne: rows (elements; linear-element trees: 3 per element)
+    // linear-element tree (build_p1_tree): degree of freedom 3 e + a is the shape
+    // function of local vertex a of element e; cluster position 3 p + a; blocks
+    // are the element tree's with tripled ranges.  Geometry arrays stay per element.
+    bool p1 = false;
+    int ne_elem = 0;               // elements (p1)
+    std::vector<int32_t> perm_elem;  // element of each element cluster position (p1)
+    g3::DevBuf d_src;              // int32 [ne]: vertex (row of nodal W and Y) of each position (p1)
+    g3::DevBuf d_curl_f, d_curl_d; // surface curls [3][3][E] (p1)
     int max_block = 0;             // cap of the larger side of a far block (0 = none)
     bool subset = false;           // a rank's share of another tree's blocks (g3_tree_subset)
     double eta = 0;

@@ -332,7 +332,9 @@ __global__ void k_entries(GeomF gf, GeomD gd, const int* __restrict__ tv, SsRule
     int i = rows[pr], j = cols[pr];
     double2 s = sd[ku[m]];
     Cx<T> v;
-    if constexpr (KER == G3_GAL_SLP) {
+    if constexpr (KER == G3_GAL_P1D || KER == G3_GAL_P1KP) {
+        v = p1_entry<KER, T>(gf, gd, i, j, (T)s.x, (T)s.y);  // regular pairs (checked on the host)
+    } else if constexpr (KER == G3_GAL_SLP) {
         int8_t px[3], py[3];
         const int cas = ss_classify(tv + 3 * (size_t)i, tv + 3 * (size_t)j, i == j, px, py);
         if (cas == 0) {
@@ -374,7 +376,7 @@ __global__ void k_entries(GeomF gf, GeomD gd, const int* __restrict__ tv, SsRule
 g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int kernel, int scheme, int prec,
                          const int* d_rows, const int* d_cols, int n, const int* d_ku, const int* d_conj, int nk,
                          double* d_out) {
-    if (scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
+    if (!t->p1 && scheme == G3_GALERKIN4x4 && kernel != G3_SLP)
         return fail(G3_EUNSUPPORTED, "g3_entries: the Galerkin scheme is implemented for G3_SLP");
     long long tot = (long long)n * nk;
     int blocks = (int)((tot + 127) / 128);
@@ -386,7 +388,11 @@ g3_status launch_entries(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, int k
     const int* tv = t->d_tv.as<int>();
 #define G3_ENT(K, T) \
     k_entries<K, T><<<blocks, 128, 0, ctx->stream>>>(t->gf, t->gd, tv, gr, sd, d_rows, d_cols, n, d_ku, d_conj, nk, out)
-    if (scheme == G3_GALERKIN4x4 && prec == G3_MIXED) G3_ENT(G3_GAL_SLP, float);
+    if (t->p1 && kernel == G3_GAL_P1D && prec == G3_MIXED) G3_ENT(G3_GAL_P1D, float);
+    else if (t->p1 && kernel == G3_GAL_P1D) G3_ENT(G3_GAL_P1D, double);
+    else if (t->p1 && prec == G3_MIXED) G3_ENT(G3_GAL_P1KP, float);
+    else if (t->p1) G3_ENT(G3_GAL_P1KP, double);
+    else if (scheme == G3_GALERKIN4x4 && prec == G3_MIXED) G3_ENT(G3_GAL_SLP, float);
     else if (scheme == G3_GALERKIN4x4) G3_ENT(G3_GAL_SLP, double);
     else if (kernel == G3_SLP && prec == G3_MIXED) G3_ENT(G3_SLP, float);
     else if (kernel == G3_SLP) G3_ENT(G3_SLP, double);
@@ -514,6 +520,184 @@ __global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPai
     }
 }
 
+// Linear continuous elements (element-local degrees of freedom): near-field
+// entries of element pairs without a common vertex by the 4-point rule on both
+// panels; the entries of pairs with a common vertex are written by
+// k_near_ss_p1.  One CTA per (near block, chunk of KCH unique frequencies),
+// threads over the block's M_b N_b entries, layout [k][j][i] as k_near.
+template <int OP, class T, int KCH>
+__global__ void __launch_bounds__(256) k_near_p1(GeomF gf, GeomD gd, const int* __restrict__ tv,
+                                                 const double2* __restrict__ sd, const BlockRange* __restrict__ ranges,
+                                                 const long long* __restrict__ offs, int Ku, Cx<T>* __restrict__ out) {
+    const int b = blockIdx.x;
+    const int k0 = blockIdx.y * KCH;
+    const BlockRange br = ranges[b];
+    const int M = br.re - br.rb, N = br.ce - br.cb;
+    const int MN = M * N;
+    const long long base = offs[b];
+    const int kn = min(KCH, Ku - k0);
+    for (int e = threadIdx.x; e < MN; e += blockDim.x) {
+        const int i = br.rb + e % M, j = br.cb + e / M;
+        const int pe = i / 3, qe = j / 3;
+        bool shared = false;
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) shared |= tv[3 * pe + x] == tv[3 * qe + y];
+        if (shared) continue;
+        for (int kk = 0; kk < kn; ++kk) {
+            const double2 s = sd[k0 + kk];
+            out[base + (long long)(k0 + kk) * MN + e] = p1_entry<OP, T>(gf, gd, i, j, (T)s.x, (T)s.y);
+        }
+    }
+}
+
+// Linear elements, element pairs with a common vertex, a common edge or
+// identical panels: the Sauter-Schwab maps (as k_near_ss) with the products
+// lambda_a(x) lambda_b(y) of the local functions in the integrand; one CTA per
+// element pair writes its 3 x 3 local entries at every frequency.  The points
+// of one region (SS_N^4) are set up in float64 and kept in shared memory (their
+// reference coordinates, distance and weight, and for the adjoint double layer
+// -((x - y) . n_x) / r^2); each frequency's ten sums (the plain integral and
+// the nine weighted ones) are reduced over the CTA and added into acc.
+template <int OP, class T, int NT>
+__global__ void __launch_bounds__(NT) k_near_ss_p1(GeomD gd, SsRule gr, const SsPair* __restrict__ pairs,
+                                                   const double2* __restrict__ sd, int Ku, Cx<T>* __restrict__ out) {
+    constexpr int NQ = SS_N * SS_N * SS_N * SS_N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* pt = reinterpret_cast<T*>(smem_raw);                    // [7][NQ]: x1, x2, y1, y2, r, w, g
+    Cx<T>* acc = reinterpret_cast<Cx<T>*>(pt + 7 * NQ);         // [Ku][10]
+    __shared__ SsPanels P;
+    __shared__ Cx<T> red[NT / 32][10];
+    const SsPair pr = pairs[blockIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) ss_panels(gd, pr.i, pr.j, pr.px, pr.py, P);
+    for (int e = threadIdx.x; e < Ku * 10; e += NT) acc[e] = Cx<T>{0, 0};
+    double n[3];
+    for (int k = 0; k < 3; ++k) n[k] = gd.n[k * gd.E + pr.i];
+    __syncthreads();
+    const int nreg = ss_regions(pr.cas);
+    for (int mreg = 0; mreg < nreg; ++mreg) {
+        for (int q = threadIdx.x; q < NQ; q += NT) {
+            int rem = q;
+            double g4[4], gw = 1.0;
+            for (int a = 3; a >= 0; --a) {
+                g4[a] = gr.x[rem % SS_N];
+                gw *= gr.w[rem % SS_N];
+                rem /= SS_N;
+            }
+            double xh[2], yh[2];
+            const double f = ss_map(pr.cas, mreg, g4[0], g4[1], g4[2], g4[3], xh, yh);
+            double z[3], d2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double x = P.P[0][k] + xh[0] * (P.P[1][k] - P.P[0][k]) + xh[1] * (P.P[2][k] - P.P[1][k]);
+                const double y = P.Q[0][k] + yh[0] * (P.Q[1][k] - P.Q[0][k]) + yh[1] * (P.Q[2][k] - P.Q[1][k]);
+                z[k] = x - y;
+                d2 += z[k] * z[k];
+            }
+            const double r = sqrt(d2);
+            pt[0 * NQ + q] = (T)xh[0];
+            pt[1 * NQ + q] = (T)xh[1];
+            pt[2 * NQ + q] = (T)yh[0];
+            pt[3 * NQ + q] = (T)yh[1];
+            pt[4 * NQ + q] = (T)r;
+            pt[5 * NQ + q] = r > 0.0 ? (T)(gw * f * P.jac / r) : (T)0;
+            pt[6 * NQ + q] = r > 0.0 ? (T)(-(z[0] * n[0] + z[1] * n[1] + z[2] * n[2]) / d2) : (T)0;
+        }
+        __syncthreads();
+        for (int k = 0; k < Ku; ++k) {
+            const double2 s = sd[k];
+            const T sre = (T)s.x, sim = (T)s.y;
+            Cx<T> v[10];
+#pragma unroll
+            for (int u = 0; u < 10; ++u) v[u] = Cx<T>{0, 0};
+            for (int q = threadIdx.x; q < NQ; q += NT) {
+                const T r = pt[4 * NQ + q];
+                const T m = pt[5 * NQ + q] * kexp(-sre * r);
+                T sn, cs;
+                ksincos(sim * r, &sn, &cs);
+                Cx<T> E{m * cs, -m * sn};
+                if (OP == G3_GAL_P1KP) {
+                    const T g = pt[6 * NQ + q], fr = (T)1 + sre * r, fi = sim * r;
+                    E = Cx<T>{g * m * (fr * cs + fi * sn), g * m * (fi * cs - fr * sn)};
+                }
+                const T x1 = pt[q], x2 = pt[NQ + q], y1 = pt[2 * NQ + q], y2 = pt[3 * NQ + q];
+                const T lx[3] = {(T)1 - x1, x1 - x2, x2}, ly[3] = {(T)1 - y1, y1 - y2, y2};
+                v[9].x += E.x;
+                v[9].y += E.y;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        v[a * 3 + b].x += lx[a] * ly[b] * E.x;
+                        v[a * 3 + b].y += lx[a] * ly[b] * E.y;
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < 10; ++u) {
+                v[u].x = warp_sum(v[u].x);
+                v[u].y = warp_sum(v[u].y);
+            }
+            if (lane == 0)
+                for (int u = 0; u < 10; ++u) red[wid][u] = v[u];
+            __syncthreads();
+            if (threadIdx.x < 10) {
+                Cx<T> t{0, 0};
+                for (int w = 0; w < NT / 32; ++w) {
+                    t.x += red[w][threadIdx.x].x;
+                    t.y += red[w][threadIdx.x].y;
+                }
+                acc[k * 10 + threadIdx.x].x += t.x;
+                acc[k * 10 + threadIdx.x].y += t.y;
+            }
+            __syncthreads();
+        }
+    }
+    // local entries (Sauter-Schwab vertex order c, d = local vertices px[c], py[d])
+    for (int e = threadIdx.x; e < Ku * 9; e += NT) {
+        const int k = e / 9, c = (e % 9) / 3, dd = e % 3;
+        const int a = pr.px[c], b = pr.py[dd];
+        Cx<T> val = acc[k * 10 + c * 3 + dd];
+        if (OP == G3_GAL_P1D) {
+            const double2 s = sd[k];
+            const T s2r = (T)(s.x * s.x - s.y * s.y), s2i = (T)(2.0 * s.x * s.y);
+            T cab = 0, nn = 0;
+            for (int kk = 0; kk < 3; ++kk) {
+                cab += (T)(gd.curl[(a * 3 + kk) * gd.E + pr.i] * gd.curl[(b * 3 + kk) * gd.E + pr.j]);
+                nn += (T)(gd.n[kk * gd.E + pr.i] * gd.n[kk * gd.E + pr.j]);
+            }
+            const Cx<T> i0 = acc[k * 10 + 9];
+            val = Cx<T>{cab * i0.x + nn * (s2r * val.x - s2i * val.y), cab * i0.y + nn * (s2r * val.y + s2i * val.x)};
+        }
+        out[pr.off + (long long)k * pr.stride + a + (long long)b * pr.ldm] = val;
+    }
+}
+
+template <int OP, class T>
+static g3_status launch_near_p1_t(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf) {
+    const int nb = (int)nf->order.size();
+    constexpr int KCH = 16;
+    dim3 grid(nb, (f->Ku + KCH - 1) / KCH);
+    Cx<T>* o = reinterpret_cast<Cx<T>*>(nf->data.p);
+    k_near_p1<OP, T, KCH><<<grid, 256, 0, ctx->stream>>>(t->gf, t->gd, t->d_tv.as<int>(), f->d_sd.as<double2>(),
+                                                          nf->d_ranges.as<BlockRange>(), nf->d_offs.as<long long>(),
+                                                          f->Ku, o);
+    ctx->count("k_near_p1");
+    G3_CUDA(cudaGetLastError());
+    if (nf->n_ss > 0) {
+        SsRule gr;
+        gauss_legendre01(SS_N, gr.x, gr.w);
+        constexpr int NT = 256;
+        const size_t smem = 7 * (size_t)SS_N * SS_N * SS_N * SS_N * sizeof(T) + 10 * (size_t)f->Ku * sizeof(Cx<T>);
+        if (smem > ctx->smem_optin)
+            return fail(G3_EUNSUPPORTED, "assemble_near: %zu bytes of shared memory for the singular pairs", smem);
+        G3_CUDA(cudaFuncSetAttribute(k_near_ss_p1<OP, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_near_ss_p1<OP, T, NT><<<nf->n_ss, NT, smem, ctx->stream>>>(t->gd, gr, nf->d_ss.as<SsPair>(),
+                                                                      f->d_sd.as<double2>(), f->Ku, o);
+        ctx->count("k_near_ss_p1");
+        G3_CUDA(cudaGetLastError());
+    }
+    return G3_OK;
+}
+
 // Self entries of the near field, float64: one thread per (element p, unique
 // frequency k); the entry (p, p) of the diagonal leaf block sits at
 // diag_base[p] + k * diag_mn[p] (diag_base[p] < 0: not in this tree's blocks).
@@ -564,6 +748,13 @@ static g3_status launch_near_galerkin(g3_ctx* ctx, const g3_tree* t, const g3_fr
 g3_status launch_near(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_near* nf, int kernel, int scheme) {
     const int nb = (int)nf->order.size();
     if (nb == 0) return G3_OK;
+    if (t->p1) {
+        if (kernel == G3_GAL_P1D)
+            return nf->prec == G3_MIXED ? launch_near_p1_t<G3_GAL_P1D, float>(ctx, t, f, nf)
+                                        : launch_near_p1_t<G3_GAL_P1D, double>(ctx, t, f, nf);
+        return nf->prec == G3_MIXED ? launch_near_p1_t<G3_GAL_P1KP, float>(ctx, t, f, nf)
+                                    : launch_near_p1_t<G3_GAL_P1KP, double>(ctx, t, f, nf);
+    }
     if (scheme == G3_GALERKIN4x4) {
         if (kernel != G3_SLP) return fail(G3_EUNSUPPORTED, "assemble_near: the Galerkin scheme is implemented for G3_SLP");
         return nf->prec == G3_MIXED ? launch_near_galerkin<float>(ctx, t, f, nf)
