@@ -177,9 +177,10 @@ typedef struct {
                              a per-CTA working buffer before the face ACA, which then reads
                              its rows and columns there (same pivots, same stored factors;
                              only the order of float32 sums differs).  No counterpart in
-                             the paper (an evaluation order).  0 (default) = never: rows
-                             and columns evaluated on demand (on the 12,288-triangle
-                             L-shape the dense pass costs what it saves in the lines)    */
+                             the paper (an evaluation order; the sum over the earlier
+                             crosses is a dense product, formed on the tensor cores).
+                             0 = 192 * 192 (default), < 0 = never (rows and columns
+                             evaluated on demand)                                         */
 } g3_opts;
 
 /* Statistics of one compression. */

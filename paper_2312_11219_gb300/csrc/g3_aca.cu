@@ -313,7 +313,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     long long drf_elems = 0;
     int drf = -1;
     if (sizeof(T) == 4 && kernel != G3_SEPARABLE) {
-        drf = o.residual_face_max > 0 ? o.residual_face_max : -1;
+        drf = o.residual_face_max > 0 ? o.residual_face_max : (o.residual_face_max == 0 ? 192 * 192 : -1);
         for (int q = 0; q < n_run && drf > 0; ++q) {
             const BlockRange& r = ranges[queue[q]];
             const long long mn = (long long)(r.re - r.rb) * (r.ce - r.cb);
@@ -321,7 +321,8 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         }
         if (drf_elems == 0) drf = -1;
     }
-    const size_t drf_smem = drf > 0 ? drf_stage_offset<T>() + drf_stage_bytes<T, 512>() : 0;
+    const size_t drf_smem =
+        drf > 0 ? drf_stage_offset<T>() + std::max(drf_stage_bytes<T, 256>(), drf_stage_bytes<T, 512>()) : 0;
     const size_t smem =
         std::max(std::max(std::max(std::max(recomp_bytes, tile_bytes), gram_bytes), tab_bytes), drf_smem);
     // low-rank class: 128, 256, 384 or 512 threads per CTA (float32 path); more

@@ -644,14 +644,23 @@ __device__ void face_samples(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S,
 // and columns from D and sums only the current face's crosses.  The partial-pivot
 // ACA takes the same rows and columns as with on-demand lines; only the order of
 // the float32 sums over the earlier crosses differs.  Tiles of 64 x (NT / 4)
-// outputs, a 4 x 4 micro-tile per thread; the earlier crosses' columns (scaled
-// by f_p[kf]) staged DRF_KC at a time in shared memory.  Float32 only.
-constexpr int DRF_KC = 16;
-// shared-memory staging of the dense residual face, placed after the face tables
+// outputs; the earlier crosses' columns (scaled by f_p[kf]) staged DRF_KC at a
+// time in shared memory.  The sum over them is a dense complex product, on the
+// tensor cores at 256 threads (the TF32 three-term split, float32 accuracy),
+// else on the CUDA cores (a 4 x 4 micro-tile per thread).  Float32 only.
+constexpr int DRF_KC = 16;     // columns per staged chunk, CUDA-core path
+constexpr int DRF_KC_TC = 16;  // columns per staged chunk, tensor-core path (256 threads, two buffers)
+// shared-memory staging of the dense residual face, placed after the face's
+// column tables (the coefficient and row buffers that follow them are not in
+// use while the dense face is formed)
 template <class T>
-constexpr size_t drf_stage_offset() { return (facetab_smem_bytes<T>() + 255) & ~size_t(255); }
+constexpr size_t drf_stage_offset() {
+    return (2 * TABMAX * sizeof(long long) + TABMAX * sizeof(short) + 255) & ~size_t(255);
+}
 template <class T, int NT>
-constexpr size_t drf_stage_bytes() { return (size_t)DRF_KC * (64 + NT / 4) * sizeof(Cx<T>); }
+constexpr size_t drf_stage_bytes() {
+    return (size_t)(NT == 256 ? 2 * DRF_KC_TC : DRF_KC) * (64 + NT / 4) * sizeof(Cx<T>);
+}
 
 template <int KER, class T, int NT>
 __device__ void face_dense_residual(const AcaArgs<T>& A, const Ws<T>& w, BlockSh<T>& S, const FaceTab<T>& F,
@@ -673,6 +682,107 @@ __device__ void face_dense_residual(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
     }
     __syncthreads();
     sublap(S, 10, te);  // the residual lines evaluate no entries when this runs
+    if constexpr (NT == 256) {
+        // tensor cores: per 64 x 64 tile, warp w takes rows 16 (w % 4) and columns
+        // 32 (w / 4) (four 16 x 8 output tiles); sum_c u_ic conj(v_jc) as the real
+        // products Re = ur vr + ui vi, Im = ui vr - ur vi (mma_tf32x3 each)
+        const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+        const int rw = (warp & 3) * 16, cw = (warp >> 2) * 32;
+        constexpr int KC = DRF_KC_TC;
+        // two staging buffers of KC columns each, filled by cp.async (8 bytes per
+        // element, zero-filled outside the face and past the last column) while the
+        // tensor cores work on the other; f_p[kf] is applied to the A fragments
+        Cx<T>* bu[2] = {su, su + KC * (TI + TJ)};
+        auto issue = [&](int buf, int i0, int j0, int c0) {
+            Cx<T>* du = bu[buf];
+            Cx<T>* dv = du + KC * TI;
+            for (int e = tid; e < KC * TI; e += NT) {
+                const int kk = e / TI, ii = e - kk * TI, c = c0 + kk;
+                const bool in = c < nc && i0 + ii < M;
+                cp_async8(du + e, in ? A.pool + F.colU[c] + i0 + ii : A.pool, in);
+            }
+            for (int e = tid; e < KC * TJ; e += NT) {
+                const int kk = e / TJ, jj = e - kk * TJ, c = c0 + kk;
+                const bool in = c < nc && j0 + jj < N;
+                cp_async8(dv + e, in ? A.pool + F.colV[c] + j0 + jj : A.pool, in);
+            }
+            cp_async_commit();
+        };
+        for (int i0 = 0; i0 < M; i0 += TI) {
+            for (int j0 = 0; j0 < N; j0 += TJ) {
+                float are[4][4], aim[4][4];
+#pragma unroll
+                for (int n8 = 0; n8 < 4; ++n8)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) are[n8][q] = aim[n8][q] = 0.f;
+                __syncthreads();  // the previous tile's buffers are consumed
+                if (nc > 0) issue(0, i0, j0, 0);
+                for (int c0 = 0, b = 0; c0 < nc; c0 += KC, b ^= 1) {
+                    if (c0 + KC < nc) {
+                        issue(b ^ 1, i0, j0, c0 + KC);
+                        cp_async_wait<1>();
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    __syncthreads();  // chunk c0 is in buffer b for every thread
+                    const Cx<T>* cu = bu[b];
+                    const Cx<T>* cv = cu + KC * TI;
+#pragma unroll
+                    for (int ks = 0; ks < KC; ks += 8) {
+                        // A fragment (row i, column c): (g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4)
+                        unsigned urh[4], url[4], uih[4], uil[4], nrh[4], nrl[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = c0 + ks + t + (q >> 1) * 4;
+                            const Cx<T> u = c < nc ? cmul(S.fk[F.colP[c]], cu[(ks + t + (q >> 1) * 4) * TI + rw + g + (q & 1) * 8])
+                                                   : Cx<T>{0, 0};
+                            const Tf32Pair pr = tf32_split(u.x), pi = tf32_split(u.y);
+                            urh[q] = pr.hi;
+                            url[q] = pr.lo;
+                            uih[q] = pi.hi;
+                            uil[q] = pi.lo;
+                        }
+                        tf32_neg4(urh, nrh);
+                        tf32_neg4(url, nrl);
+#pragma unroll
+                        for (int n8 = 0; n8 < 4; ++n8) {
+                            // B fragment (row c, column j): (t, g), (t + 4, g)
+                            unsigned vrh[2], vrl[2], vih[2], vil[2];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const Cx<T> v = cv[(ks + t + q * 4) * TJ + cw + n8 * 8 + g];
+                                const Tf32Pair pr = tf32_split(v.x), pi = tf32_split(v.y);
+                                vrh[q] = pr.hi;
+                                vrl[q] = pr.lo;
+                                vih[q] = pi.hi;
+                                vil[q] = pi.lo;
+                            }
+                            mma_tf32x3(are[n8], urh, url, vrh, vrl);
+                            mma_tf32x3(are[n8], uih, uil, vih, vil);
+                            mma_tf32x3(aim[n8], uih, uil, vrh, vrl);
+                            mma_tf32x3(aim[n8], nrh, nrl, vih, vil);
+                        }
+                    }
+                    __syncthreads();  // buffer b is consumed before the next chunk refills it
+                }
+                // C fragment (row, column): (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1)
+#pragma unroll
+                for (int n8 = 0; n8 < 4; ++n8)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int gi = i0 + rw + g + (q >> 1) * 8, gj = j0 + cw + n8 * 8 + 2 * t + (q & 1);
+                        if (gi < M && gj < N) {
+                            Cx<T>* dp = D + (size_t)gi * N + gj;
+                            const Cx<T> e = *dp;
+                            *dp = Cx<T>{e.x - are[n8][q], e.y - aim[n8][q]};
+                        }
+                    }
+            }
+        }
+        if (tid == 0) atomicAdd(&A.counters[7], (unsigned long long)M * N);
+        __syncthreads();
+        return;
+    }
     for (int i0 = 0; i0 < M; i0 += TI) {
         for (int j0 = 0; j0 < N; j0 += TJ) {
             Cx<T> acc[4][4];

@@ -127,42 +127,8 @@ __global__ void __launch_bounds__(NT) k_apply_near(const Cx<T>* __restrict__ A, 
 // ---- tensor-core x formation (float32 path) --------------------------------------------
 // x_p = sum_k f_p[k] w_k for 16 columns x 8 crosses at a time is the real-matrix product
 // of W_sigma^T (columns x frequencies) and F (frequencies x crosses), split into four real
-// products per complex product.  Each real product runs on the tensor cores as
-// mma.sync m16n8k8 with TF32 inputs and float32 accumulation, in the three-term split
-// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = a rounded to TF32, a_lo = the rounded
-// remainder), which keeps the float32 accuracy of the CUDA-core sums (about 2^-21
-// relative per product instead of TF32's 2^-11).
-__device__ __forceinline__ unsigned tf32_rna(float x) {
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-struct Tf32Pair {
-    unsigned hi, lo;
-};
-__device__ __forceinline__ Tf32Pair tf32_split(float x) {
-    const unsigned h = tf32_rna(x);
-    return Tf32Pair{h, tf32_rna(x - __uint_as_float(h))};
-}
-// d += a b for one 16 x 8 x 8 tile (fragment layouts of the PTX m16n8k8 .tf32 shape)
-__device__ __forceinline__ void mma_tf32(float* d, const unsigned* a, const unsigned* b) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-// d += a b in the three-term split (the small terms first)
-__device__ __forceinline__ void mma_tf32x3(float* d, const unsigned* ah, const unsigned* al, const unsigned* bh,
-                                           const unsigned* bl) {
-    mma_tf32(d, ah, bl);
-    mma_tf32(d, al, bh);
-    mma_tf32(d, ah, bh);
-}
-// sign flip of TF32 bit patterns (exact)
-__device__ __forceinline__ void tf32_neg4(const unsigned* a, unsigned* o) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) o[q] = a[q] ^ 0x80000000u;
-}
+// products per complex product, each on the tensor cores in the three-term TF32 split
+// of g3_device.cuh (mma_tf32x3).
 // row stride (floats) of the split fibers in shared memory: >= the padded frequency
 // count and 4 mod 8, so the eight rows of a B fragment fall in distinct banks
 __host__ __device__ constexpr int tc_fiber_stride(int Ku) { return (Ku + 7) / 8 * 8 + 4; }

@@ -493,6 +493,52 @@ __device__ inline void ss_point(const SsPanels& S, int cas, int m, const double 
     w = r > 0.0 ? gw * f * S.jac / r : 0.0;
 }
 
+// ---- tensor cores: TF32 products at float32 accuracy ------------------------------
+// A real product on the tensor cores as mma.sync m16n8k8 with TF32 inputs and float32
+// accumulation, in the three-term split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi =
+// a rounded to TF32, a_lo = the rounded remainder), which keeps float32 accuracy (about
+// 2^-21 relative per product instead of TF32's 2^-11).
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+struct Tf32Pair {
+    unsigned hi, lo;
+};
+__device__ __forceinline__ Tf32Pair tf32_split(float x) {
+    const unsigned h = tf32_rna(x);
+    return Tf32Pair{h, tf32_rna(x - __uint_as_float(h))};
+}
+// d += a b for one 16 x 8 x 8 tile (fragment layouts of the PTX m16n8k8 .tf32 shape)
+__device__ __forceinline__ void mma_tf32(float* d, const unsigned* a, const unsigned* b) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// d += a b in the three-term split (the small terms first)
+__device__ __forceinline__ void mma_tf32x3(float* d, const unsigned* ah, const unsigned* al, const unsigned* bh,
+                                           const unsigned* bl) {
+    mma_tf32(d, ah, bl);
+    mma_tf32(d, al, bh);
+    mma_tf32(d, ah, bh);
+}
+// sign flip of TF32 bit patterns (exact)
+__device__ __forceinline__ void tf32_neg4(const unsigned* a, unsigned* o) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = a[q] ^ 0x80000000u;
+}
+// ---- asynchronous copies global -> shared (8 bytes; zero-filled when !in) ---------
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool in) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(in ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 // ---- block reductions ------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -313,8 +313,9 @@ def test_compression_launch_shapes(g3, ctx, threads):
 @pytest.mark.parametrize("threads", [256, 512])
 def test_dense_residual_faces(g3, ctx, kernel, threads):
     """Low-rank faces evaluated through the dense residual working face
-    (opts residual_face_max) compute Algorithm 1 as the on-demand rows and
-    columns do: blocks within 10 eps3 of the oracle's dense blocks, block ranks
+    (opts residual_face_max; the default up to 192 x 192 entries, the sum over
+    the earlier crosses on the tensor cores at 256 threads, on the CUDA cores
+    at 512) compute Algorithm 1 as the on-demand rows and columns do: blocks within 10 eps3 of the oracle's dense blocks, block ranks
     within 2 of the on-demand run, and every stored pivot the largest entry of
     its face approximant H_l."""
     w = workloads.get("lshape3072")
@@ -322,7 +323,8 @@ def test_dense_residual_faces(g3, ctx, kernel, threads):
     geo, OT, fs, su, ef = _oracle_blocks(w, kernel, eps3)
     T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta)
     F = g3.freqs_from_spec(ctx, w.freq)
-    ref = g3.aca3_compress(ctx, T, F, kernel, prec="mixed", eps3=eps3, dense_face_max=-1, threads=threads)
+    ref = g3.aca3_compress(ctx, T, F, kernel, prec="mixed", eps3=eps3, dense_face_max=-1, threads=threads,
+                           residual_face_max=-1)
     fa = g3.aca3_compress(ctx, T, F, kernel, prec="mixed", eps3=eps3, dense_face_max=-1, threads=threads,
                           residual_face_max=256 * 256)
     st, st0 = fa.stats(), ref.stats()
