@@ -785,9 +785,15 @@ def plain_arm_errors(g3, ctx, w, ker, pv, seed: int, Wd, n_rows: int, cores: int
 
 def run_reference(args) -> dict:
     """The CPU oracle as it stands, on the host cores, same workload and metric."""
+    from inputs import workloads as _wl
+    p1 = args.workload != "batch64" and _wl.get(args.workload).extra.get("p1")
     res = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(args.workload, args.ref_seconds, 100 + i, os.cpu_count() or 1)
+        if p1:
+            w1 = _wl.get(args.workload)
+            r = p1_oracle_sample(w1, list(w1.kernels), args.ref_seconds, 100 + i)
+        else:
+            r = oracle_sample(args.workload, args.ref_seconds, 100 + i, os.cpu_count() or 1)
         if i >= args.warmup:
             res.append(r)
     ent = sum(r["entries"] for r in res)
@@ -836,6 +842,194 @@ def run_profile_case(args) -> dict:
             "apply_bytes": la["bytes"], "near_ms": la["near_ms"], "near_bytes": la["near_bytes"]}
 
 
+# ---------------------------------------------------------------------------
+# the Neumann problem: Galerkin operators of linear continuous elements
+# ---------------------------------------------------------------------------
+
+def _p1_entry_fn(w, op):
+    """The oracle's ENTRY of element-local shape functions (original indices
+    3 e + a), through its local 3 x 3 blocks."""
+    import numpy as np
+    from oracle import galerkin_p1 as P1
+
+    def f(I, J, s):
+        out = np.zeros((len(I), np.atleast_1d(s).size), complex)
+        cache = {}
+        for t, (i, j) in enumerate(zip(I, J)):
+            key = (int(i) // 3, int(j) // 3)
+            if key not in cache:
+                cache[key] = P1.local_block(w.verts, w.tris, key[0], key[1], s, op)
+            out[t] = cache[key][int(i) % 3, int(j) % 3]
+        return out
+    return f
+
+
+def p1_oracle_sample(w, kernels, seconds: float, seed: int) -> dict:
+    """Oracle entries/s (one host thread) on seeded random blocks of the
+    linear-element operators: far blocks through the oracle's three-way ACA,
+    near blocks through its local blocks, in the far/near proportion."""
+    import time as _t
+
+    import numpy as np
+    from oracle import aca3 as O_aca, freqs as O_freqs, tree as O_tree
+    T = O_tree.build(w.verts, w.tris, w.leaf, w.eta, w.max_block)
+    fs = O_freqs.frequency_set(w.freq)
+    su = fs["s"][fs["uniq"]]
+    rng = np.random.default_rng(seed)
+    ops = {"hyp": "d", "adj": "kp"}
+    ent, nb, t0 = 0, 0, _t.perf_counter()
+    while _t.perf_counter() - t0 < seconds:
+        ker = kernels[nb % len(kernels)]
+        ef = _p1_entry_fn(w, ops[ker])
+        b = int(rng.integers(0, T.blocks.shape[0]))
+        rb, re, cb, ce, adm = T.blocks[b]
+        rows = (3 * T.perm[rb:re][:, None] + np.arange(3)[None, :]).ravel()
+        cols = (3 * T.perm[cb:ce][:, None] + np.arange(3)[None, :]).ravel()
+        if adm:
+            op = O_aca.BemBlock(ef, rows, cols, su)
+            O_aca.aca3(op, w.eps3, s_abs=np.abs(su))
+            ent += int(op.generated)
+        else:
+            ef(np.repeat(rows, cols.size), np.tile(cols, rows.size), su)
+            ent += rows.size * cols.size * su.size
+        nb += 1
+    sec = _t.perf_counter() - t0
+    return {"value": ent / sec, "unit": "entries/s", "cores": 1, "kind": "oracle",
+            "sample": f"{nb} seeded random blocks of {w.name} ({', '.join(kernels)}; far blocks through the "
+                      f"oracle's three-way ACA, near blocks densely), {sec:.1f} s wall, one host thread",
+            "entries": ent, "seconds": sec}
+
+
+def run_neumann(args, rank: int, world: int, local_rank: int) -> dict | None:
+    """The timed step on a linear-element workload: per operator (hypersingular,
+    adjoint double layer) the tree of element-local shape functions, the near
+    field, the three-way ACA and one nodal apply; one GPU."""
+    import numpy as np
+    import torch
+    import paper_2312_11219_gb300 as g3
+    from inputs import workloads
+    from oracle import freqs as O_freqs, galerkin_p1 as P1
+    if world > 1:
+        raise SystemExit(f"{args.workload}: one GPU only")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workloads.get(args.workload)
+    nv = w.verts.shape[0]
+    W = workloads.densities(nv, w.freq.K, w.density_seed)
+    Wd = torch.from_numpy(W).to(dev, torch.complex64)
+    stream = torch.cuda.current_stream(dev)
+    ctx = g3.Context(local_rank, stream.cuda_stream)
+    keep = {}
+
+    def step(host: bool):
+        T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
+        T1 = g3.build_p1_tree(ctx, T)
+        F = g3.freqs_from_spec(ctx, w.freq)
+        rec = {"entries_aca": 0, "entries_face_dense": 0, "entries_near": 0, "aca_ms": 0.0, "near_ms": 0.0,
+               "apply_ms": 0.0, "apply_bytes": 0, "crosses": 0, "factor_bytes": 0, "dense_bytes": 0}
+        for ker in w.kernels:
+            keep.pop(ker, None)
+            nf = g3.assemble_near(ctx, T1, F, ker, scheme="galerkin4x4", prec="mixed")
+            fa = g3.aca3_compress(ctx, T1, F, ker, scheme="galerkin4x4", prec="mixed", eps3=w.eps3)
+            y = g3.apply_gcq(ctx, T1, nf, fa, W if host else Wd)
+            la, st, ni = ctx.last_apply(), fa.stats(), nf.info()
+            rec["entries_aca"] += st["entries"]
+            rec["entries_face_dense"] += st["entries_face_dense"]
+            rec["entries_near"] += ni["entries"]
+            rec["aca_ms"] += st["ms"]
+            rec["near_ms"] += ni["ms"]
+            rec["apply_ms"] += la["ms"]
+            rec["apply_bytes"] += la["bytes"]
+            rec["crosses"] += st["crosses"]
+            rec["factor_bytes"] += st["factor_bytes"]
+            rec["dense_bytes"] += st["dense_bytes"]
+            keep[ker] = (T1, nf, fa, y)
+        return rec
+
+    def timed(n: int, host: bool):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        recs = [step(host) for _ in range(n)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return recs, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        step(False)
+    launches0 = ctx.launch_count()
+    with Clocks(local_rank) as clk:
+        recs, ms = timed(args.steps, False)
+    launches = ctx.launch_count() - launches0
+    ys = {ker: keep[ker][3].cpu().numpy() for ker in w.kernels}
+    e_steps = max(1, args.steps // 2)
+    _, ems = timed(e_steps, True)
+    r0 = recs[-1]
+    entries = r0["entries_aca"] + r0["entries_near"]
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    sfu_peak = SFU_PER_CLK_SM * props.multi_processor_count * sm_mhz * 1e6
+    aca_ms = sum(r["aca_ms"] for r in recs) / (len(recs) * len(w.kernels))
+    aca_entries = r0["entries_aca"] / len(w.kernels)
+    achieved = aca_entries * MUFU_PER_ENTRY_GALERKIN / (aca_ms / 1e3)
+    evaluated = (r0["entries_aca"] + r0["entries_face_dense"]) / len(w.kernels) * MUFU_PER_ENTRY_GALERKIN / (aca_ms / 1e3)
+    # steady-state apply, both operators, 10 applies each after one untimed apply
+    st_ms, st_bytes = 0.0, 0
+    for ker in w.kernels:
+        T1, nf, fa, _ = keep[ker]
+        g3.apply_gcq(ctx, T1, nf, fa, Wd)
+        for _ in range(10):
+            g3.apply_gcq(ctx, T1, nf, fa, Wd)
+            la = ctx.last_apply()
+            st_ms += la["ms"] / 10
+            st_bytes += la["bytes"] / 10
+    apply_gbs = st_bytes / (st_ms / 1e3) / 1e9
+    out = {
+        "metric": "3-way ACA entries/s & apply GB/s (1 GB300); learned+batched vs plain at 1e-4",
+        "value": whole_job_rate(entries, ms, args.steps), "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "triangles": w.E, "vertices": nv, "K": w.freq.K, "freqs": w.freq.kind,
+                   "kernels": list(w.kernels), "scheme": "galerkin4x4, linear continuous elements (element-local "
+                   "shape functions, nodal densities)", "leaf": w.leaf, "eta": w.eta, "eps3": w.eps3,
+                   "precision": "mixed", "l2": "near field %.2f GB per operator (not larger than L2 on every "
+                   "operator: no flush; the timed step builds every operator anew)" % (
+                       r0["entries_near"] / len(w.kernels) * 8 / 1e9), "parallelism": "single GPU"},
+        "gpu_launches": int(launches),
+        "entries_per_step": entries, "entries_aca": r0["entries_aca"], "entries_near": r0["entries_near"],
+        "entries_face_dense": r0["entries_face_dense"],
+        "phase_ms": {"aca3_compress": r0["aca_ms"], "assemble_near": r0["near_ms"], "apply_gcq": r0["apply_ms"]},
+        "storage_ratio": r0["factor_bytes"] / r0["dense_bytes"] if r0["dense_bytes"] else None,
+        "crosses": r0["crosses"], "apply_gbs": apply_gbs, "apply_ms_steady": st_ms,
+        "e2e": {"value": whole_job_rate(entries, ems, e_steps), "unit": "entries/s",
+                "h2d_bytes_per_step": int(W.nbytes * len(w.kernels)),
+                "d2h_bytes_per_step": int(nv * 16 * len(w.kernels))},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": sfu_peak / 1e12,
+                     "unit": "Tops/s (special-function unit)", "frac": achieved / sfu_peak, "traffic": None,
+                     "kernel": "k_aca3 (linear elements)", "frac_evaluated": evaluated / sfu_peak,
+                     "note": f"{MUFU_PER_ENTRY_GALERKIN} SFU ops per entry (16 kernel evaluations) x "
+                             f"{aca_entries:.4g} entries per launch / {aca_ms:.1f} ms"},
+        "roofline_apply": {"bound": "hbm", "achieved": apply_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": apply_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "apply_gcq (all kernels)",
+                           "peak_source": peaks["source"]},
+        "clocks": clk.summary(), "peaks_source": peaks["source"],
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = p1_oracle_sample(w, list(w.kernels), args.cpu_seconds, 7)
+        fs = O_freqs.frequency_set(w.freq)
+        rows = np.sort(np.random.default_rng(3).choice(nv, 2, replace=False))
+        errs = {}
+        for ker, op in (("hyp", "d"), ("adj", "kp")):
+            R = P1.nodal_rows(w.verts, w.tris, rows, fs["s"], op)
+            ref = np.einsum("rjk,jk->r", R, W)
+            errs[ker] = {"rel_err": float(np.linalg.norm(ys[ker][rows] - ref) / np.linalg.norm(ref)),
+                         "rows": int(rows.size)}
+        out["apply_error_vs_oracle"] = errs
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -866,6 +1060,12 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    from inputs import workloads as _wl
+    if args.workload not in ("batch64",) and _wl.get(args.workload).extra.get("p1"):
+        out = run_neumann(args, rank, world, local_rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
         return
     if world > 1:
         import torch

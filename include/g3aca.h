@@ -571,7 +571,8 @@ g3_status apply_gcq(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_f
  * scratch than 32 MiB (2 Ku M + M complex values, each part rounded up to
  * 256 bytes) return G3_EINVAL.  All calls
  * share the array: calls whose work overlaps on the GPU (other streams,
- * other threads) race and must be serialised by the caller. */
+ * other threads) race and must be serialised by the caller.  Element trees
+ * only (a tree of build_p1_tree returns G3_EUNSUPPORTED). */
 g3_status apply_gcq_noalloc(g3_ctx* ctx, const g3_tree* t, const g3_near* nf, const g3_factors* fa, const void* W,
                             void* Y, g3_dtype dtype);
 /* The gCQ time-stepping consumer of the apply (eq. (gCQ_xn) and the weight

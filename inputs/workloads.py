@@ -18,6 +18,10 @@ Workloads (all synthetic; the paper's meshes and load data are not used):
 * ``batch64``     64 seeded cubes/icospheres (about 500-8,000 triangles each).
 * ``sphere81920`` icosphere level 6 (81,920 triangles), collocation, single
                   layer, the gCQ set of ``sphere20480``.
+* ``sphere5120n`` icosphere level 4 (5,120 triangles, 2,562 vertices),
+                  Galerkin with linear continuous elements: hypersingular
+                  operator and adjoint double layer (the Neumann problem),
+                  N_Q = 64 gCQ frequencies, nodal densities.
 
 Small variants (``cube48``, ``cube192``, ``lshape768``, ``sphere1280``...) serve
 the tests.  The large workloads cap far blocks at 192 elements per side
@@ -140,6 +144,12 @@ def get(name: str) -> Workload:
     if name == "sphere1280g":
         v, t = meshes.icosphere(3)
         return Workload(name, v, t, gcq_spec(64, 0.005, 0.015), scheme="galerkin4x4", density_seed=17)
+    if name == "sphere5120n":
+        # the Neumann problem (Galerkin, linear continuous elements): the
+        # hypersingular operator and the adjoint double layer on nodal densities
+        v, t = meshes.icosphere(4)
+        return Workload(name, v, t, gcq_spec(64, 0.005, 0.015), kernels=("hyp", "adj"), scheme="galerkin4x4",
+                        density_seed=19, extra={"p1": True})
     if name == "sphere320g":
         v, t = meshes.icosphere(2)
         return Workload(name, v, t, gcq_spec(64, 0.005, 0.015), scheme="galerkin4x4", density_seed=16)
