@@ -403,6 +403,85 @@ __device__ __noinline__ Cx<T> p1_regular(const G& g, int p, int a, int q, int b,
     return {cab * i0.x + nn * (s2r * iab.x - s2i * iab.y), cab * i0.y + nn * (s2r * iab.y + s2i * iab.x)};
 }
 
+// all nine local entries of a regular pair: the pair's 16 distances r, weights
+// m = w w' / (4 pi r), for the adjoint double layer g = -((x - y) . n_x) / r^2,
+// and (hypersingular operator) the curl products and n_p . n_q, formed once ...
+template <int OP, class G, class T>
+__device__ __forceinline__ void p1_pair_setup(const G& g, int p, int q, T r[16], T m[16], T gz[16], T cab[9], T& nn) {
+    T d[3];
+    cdiff(g, p, q, d);
+    const T np0 = (T)nrm(g, 0, p), np1 = (T)nrm(g, 1, p), np2 = (T)nrm(g, 2, p);
+#pragma unroll
+    for (int qa = 0; qa < 4; ++qa) {
+        const T xa0 = d[0] + q4off(g, qa, 0, p), xa1 = d[1] + q4off(g, qa, 1, p), xa2 = d[2] + q4off(g, qa, 2, p);
+        const T wa = q4wt(g, qa, p) * (T)G3_INV4PI;
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) {
+            const T rx = xa0 - q4off(g, qb, 0, q), ry = xa1 - q4off(g, qb, 1, q), rz = xa2 - q4off(g, qb, 2, q);
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            const T ri = krsqrt(r2);
+            r[qa * 4 + qb] = r2 * ri;
+            m[qa * 4 + qb] = wa * q4wt(g, qb, q) * ri;
+            gz[qa * 4 + qb] = OP == G3_GAL_P1KP ? -(rx * np0 + ry * np1 + rz * np2) * ri * ri : (T)0;
+        }
+    }
+    nn = 0;
+    if (OP == G3_GAL_P1D) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                T c = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) c += (T)g.curl[(a * 3 + k) * g.E + p] * (T)g.curl[(b * 3 + k) * g.E + q];
+                cab[a * 3 + b] = c;
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nn += (T)nrm(g, k, p) * (T)nrm(g, k, q);
+    }
+}
+// ... and evaluated at one frequency: v[a * 3 + b] (local vertex a of p, b of q)
+template <int OP, class T>
+__device__ __forceinline__ void p1_pair_eval(const T r[16], const T m[16], const T gz[16], const T cab[9], T nn,
+                                             T sre, T sim, Cx<T> v[9]) {
+    Cx<T> i0{0, 0};
+#pragma unroll
+    for (int u = 0; u < 9; ++u) v[u] = Cx<T>{0, 0};
+#pragma unroll
+    for (int qa = 0; qa < 4; ++qa) {
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) {
+            const int q = qa * 4 + qb;
+            const T e = m[q] * kexp(-sre * r[q]);
+            T sn, cs;
+            ksincos(sim * r[q], &sn, &cs);
+            Cx<T> u{e * cs, -e * sn};
+            if (OP == G3_GAL_P1KP) {
+                const T fr = (T)1 + sre * r[q], fi = sim * r[q];
+                u = Cx<T>{gz[q] * e * (fr * cs + fi * sn), gz[q] * e * (fi * cs - fr * sn)};
+            }
+            i0.x += u.x;
+            i0.y += u.y;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const T l = (T)(p1_bary4(qa, a) * p1_bary4(qb, b));
+                    v[a * 3 + b].x += l * u.x;
+                    v[a * 3 + b].y += l * u.y;
+                }
+        }
+    }
+    if (OP == G3_GAL_P1D) {
+        const T s2r = sre * sre - sim * sim, s2i = 2 * sre * sim;
+#pragma unroll
+        for (int u = 0; u < 9; ++u) {
+            const Cx<T> w = v[u];
+            v[u] = Cx<T>{cab[u] * i0.x + nn * (s2r * w.x - s2i * w.y), cab[u] * i0.y + nn * (s2r * w.y + s2i * w.x)};
+        }
+    }
+}
+
 // both geometries: the working precision's copy
 template <int OP, class T>
 __device__ __forceinline__ Cx<T> p1_entry(const GeomF& gf, const GeomD& gd, int gi, int gj, T sre, T sim) {

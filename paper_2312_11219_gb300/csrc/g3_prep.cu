@@ -522,9 +522,10 @@ __global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPai
 
 // Linear continuous elements (element-local degrees of freedom): near-field
 // entries of element pairs without a common vertex by the 4-point rule on both
-// panels; the entries of pairs with a common vertex are written by
-// k_near_ss_p1.  One CTA per (near block, chunk of KCH unique frequencies),
-// threads over the block's M_b N_b entries, layout [k][j][i] as k_near.
+// panels, one thread per element pair: the 16 point distances and weights are
+// formed once and every frequency gives the pair's nine local entries; the
+// pairs with a common vertex are written by k_near_ss_p1.  One CTA per (near
+// block, chunk of KCH unique frequencies), layout [k][j][i] as k_near.
 template <int OP, class T, int KCH>
 __global__ void __launch_bounds__(256) k_near_p1(GeomF gf, GeomD gd, const int* __restrict__ tv,
                                                  const double2* __restrict__ sd, const BlockRange* __restrict__ ranges,
@@ -533,19 +534,31 @@ __global__ void __launch_bounds__(256) k_near_p1(GeomF gf, GeomD gd, const int* 
     const int k0 = blockIdx.y * KCH;
     const BlockRange br = ranges[b];
     const int M = br.re - br.rb, N = br.ce - br.cb;
-    const int MN = M * N;
+    const int Me = M / 3, Ne = N / 3;
     const long long base = offs[b];
     const int kn = min(KCH, Ku - k0);
-    for (int e = threadIdx.x; e < MN; e += blockDim.x) {
-        const int i = br.rb + e % M, j = br.cb + e / M;
-        const int pe = i / 3, qe = j / 3;
+    for (int e = threadIdx.x; e < Me * Ne; e += blockDim.x) {
+        const int pe = br.rb / 3 + e % Me, qe = br.cb / 3 + e / Me;
         bool shared = false;
         for (int x = 0; x < 3; ++x)
             for (int y = 0; y < 3; ++y) shared |= tv[3 * pe + x] == tv[3 * qe + y];
         if (shared) continue;
+        T r[16], m[16], gz[16];
+        T cab[9], nn = 0;
+        if constexpr (sizeof(T) == 4)
+            p1_pair_setup<OP>(gf, pe, qe, r, m, gz, cab, nn);
+        else
+            p1_pair_setup<OP>(gd, pe, qe, r, m, gz, cab, nn);
+        const long long e0 = base + (long long)(3 * (qe - br.cb / 3)) * M + 3 * (pe - br.rb / 3);
         for (int kk = 0; kk < kn; ++kk) {
             const double2 s = sd[k0 + kk];
-            out[base + (long long)(k0 + kk) * MN + e] = p1_entry<OP, T>(gf, gd, i, j, (T)s.x, (T)s.y);
+            Cx<T> v[9];
+            p1_pair_eval<OP, T>(r, m, gz, cab, nn, (T)s.x, (T)s.y, v);
+            Cx<T>* o = out + (long long)(k0 + kk) * M * N + e0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[a + (long long)c * M] = v[a * 3 + c];
         }
     }
 }
