@@ -37,6 +37,11 @@ METRIC = "3-way ACA entries/s & apply GB/s (1 GB300); learned+batched vs plain a
 
 # special-function-unit operations per collocation entry: 7 quadrature points,
 # each one rsqrt, one ex2, one sin and one cos (Galerkin: 16 points)
+# DRAM bytes (read + write) per low-rank k_aca3 launch of the 12,288-triangle
+# L-shape, mean of the single and double layer, from one ncu capture of each
+# operator's launch (dram__bytes_read.sum + dram__bytes_write.sum: 36.8 GB and
+# 41.8 GB) of the current kernel; other workloads have no capture (null)
+ACA_TRAFFIC_BYTES = {"lshape12288": 0.5 * (19234748160 + 17581539072 + 23269448960 + 18566676224)}
 MUFU_PER_ENTRY = 28
 MUFU_PER_ENTRY_GALERKIN = 64
 # special-function-unit results per clock per SM for rsqrt / sin / cos
@@ -423,7 +428,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         for ker in kernels:
             keep.pop(ker, None)   # the previous step's operator first: two at once do not fit the largest workloads
             nfs = [g3.assemble_near(ctx, T, F, ker, scheme=scheme, prec=prec) for T, F in zip(trees, freqs)]
-            shape = {k: tune[ker][k] for k in ("threads", "dense_face_max")} if ker in tune else {}
+            shape = {k: tune[ker][k] for k in ("threads", "dense_face_max", "residual_face_max")} if ker in tune else {}
             if batch:
                 fas = g3.aca3_compress_batch(ctx, trees, freqs, ker, scheme=scheme, prec=prec, eps3=ws[0].eps3,
                                              mlp=mlp, mlp_use=mlp_use)
@@ -658,7 +663,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         Tb = lap("tree", lambda: make_tree(ws[0]))
         Fb = lap("freqs", lambda: g3.freqs_from_spec(ctx, ws[0].freq))
         for ker in kernels:
-            shape = {k: tune[ker][k] for k in ("threads", "dense_face_max")} if ker in tune else {}
+            shape = {k: tune[ker][k] for k in ("threads", "dense_face_max", "residual_face_max")} if ker in tune else {}
             nfb = lap("assemble_near", lambda: g3.assemble_near(ctx, Tb, Fb, ker, scheme=scheme, prec=prec))
             fab = lap("aca3_compress", lambda: g3.aca3_compress(ctx, Tb, Fb, ker, scheme=scheme, prec=prec,
                                                                 eps3=ws[0].eps3, mlp=net, mlp_use=args.mlp_use,
@@ -719,7 +724,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         "e2e": {"value": whole_job_rate(entries_all, e_max, e_steps), "unit": "entries/s",
                 "h2d_bytes_per_step": int(h2d * world), "d2h_bytes_per_step": int(d2h * world)},
         "roofline": {"bound": "alu", "achieved": achieved_sfu / 1e12, "peak": sfu_peak / 1e12,
-                     "unit": "Tops/s (special-function unit)", "frac": achieved_sfu / sfu_peak, "traffic": None,
+                     "unit": "Tops/s (special-function unit)", "frac": achieved_sfu / sfu_peak,
+                     "traffic": ACA_TRAFFIC_BYTES.get(args.workload) if world == 1 else None,
+                     "traffic_unit": "bytes per launch",
                      "kernel": "k_aca3",
                      "frac_evaluated": evaluated_sfu / sfu_peak,
                      "note": f"{mufu} SFU ops per entry x {aca_entries:.4g} entries per launch (Algorithm 1's "

@@ -409,7 +409,8 @@ g3_status g3_near_free(g3_near* nf);
  *   (rank l - 1) or when all unique frequencies are used (rank l);
  *   k_{l+1} = argmax of |f_l| over unused frequencies.
  * All blocks run in one persistent launch unless opts->unbatched.
- * kernel: G3_SLP or G3_DLP.  eps3 in (0, 1). */
+ * kernel: G3_SLP or G3_DLP on an element tree, G3_HYPERSINGULAR or
+ * G3_ADJOINT_DLP (G3_GALERKIN4x4) on a tree of build_p1_tree.  eps3 in (0, 1). */
 g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,
                         g3_precision prec, double eps3, const g3_opts* opts, g3_factors** out);
 
@@ -417,8 +418,10 @@ g3_status aca3_compress(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_ker
  * Times aca3_compress on (t, f) for each candidate -- threads per CTA of the
  * low-rank launch 128, 256, 384 or 512 (all but 256: G3_MIXED only) and the dense-face
  * threshold M_b N_b <= 24^2, 48^2 or 64^2 -- and writes the fastest into
- * opts->threads and opts->dense_face_max (the other fields of *opts are used
- * as given).  The choice is cached in ctx by (K_u bucket, largest far-block
+ * opts->threads and opts->dense_face_max; in G3_MIXED it then times the
+ * fastest shape once more without the dense residual working faces and sets
+ * opts->residual_face_max to -1 when that is faster (the other fields of
+ * *opts are used as given).  The choice is cached in ctx by (K_u bucket, largest far-block
  * bucket, kernel, scheme, precision) and reused without timing.  best_ms
  * (may be NULL): the fastest time, 0 on a cache hit. */
 g3_status g3_autotune(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kernel kernel, g3_scheme scheme,

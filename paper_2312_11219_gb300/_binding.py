@@ -577,12 +577,14 @@ def aca3_compress(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", s
 def autotune(ctx: Context, tree: Tree, freqs: Freqs, kernel: str = "slp", scheme: str = "colloc7",
              prec: str = "mixed", eps3: float = 1e-4, **opts) -> dict:
     """Fastest launch shape of aca3_compress on this problem (cached per
-    problem class in the context): {"threads", "dense_face_max", "ms"}."""
+    problem class in the context): {"threads", "dense_face_max",
+    "residual_face_max", "ms"}."""
     o = _opts(**opts)
     ms = C.c_double()
     _check(_lib.g3_autotune(ctx.h, tree.h, freqs.h, KERNELS[kernel], SCHEMES[scheme], PRECISIONS[prec], eps3,
                             C.byref(o), C.byref(ms)), "g3_autotune")
-    return {"threads": o.threads, "dense_face_max": o.dense_face_max, "ms": ms.value}
+    return {"threads": o.threads, "dense_face_max": o.dense_face_max, "residual_face_max": o.residual_face_max,
+            "ms": ms.value}
 
 
 def aca3_compress_batch(ctx: Context, trees, freqs, kernel: str = "slp", scheme: str = "colloc7",

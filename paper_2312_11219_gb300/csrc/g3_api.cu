@@ -955,8 +955,9 @@ g3_status g3_autotune(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kerne
     if (best_ms) *best_ms = 0.0;
     auto hit = ctx->tune_cache.find(key);
     if (hit != ctx->tune_cache.end()) {
-        opts->threads = hit->second.first;
-        opts->dense_face_max = hit->second.second;
+        opts->threads = hit->second[0];
+        opts->dense_face_max = hit->second[1];
+        opts->residual_face_max = hit->second[2];
         return G3_OK;
     }
     G3_TRY(use_device(ctx));
@@ -979,9 +980,28 @@ g3_status g3_autotune(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3_kerne
                 bd = dmax[b];
             }
         }
-    ctx->tune_cache[key] = {bt, bd};
+    // the dense residual working faces (on by default in float32) against
+    // rows and columns evaluated on demand, at the fastest shape: which wins
+    // depends on how many ACA steps a face takes against its M_b N_b entries
+    int br = opts->residual_face_max;
+    if (prec == G3_MIXED && br >= 0) {
+        g3_opts o = *opts;
+        o.threads = bt;
+        o.dense_face_max = bd;
+        o.residual_face_max = -1;
+        g3_factors* fa = nullptr;
+        G3_TRY(aca3_compress(ctx, t, f, kernel, scheme, prec, eps3, &o, &fa));
+        const double ms = fa->stats.ms;
+        g3_factors_free(fa);
+        if (ms < best) {
+            best = ms;
+            br = -1;
+        }
+    }
+    ctx->tune_cache[key] = {bt, bd, br};
     opts->threads = bt;
     opts->dense_face_max = bd;
+    opts->residual_face_max = br;
     if (best_ms) *best_ms = best;
     return G3_OK;
 }

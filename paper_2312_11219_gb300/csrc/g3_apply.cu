@@ -608,8 +608,17 @@ g3_status far_plan_build(g3_factors* fa) {
         if (x.cost != y.cost) return x.cost > y.cost;
         return x.b != y.b ? x.b < y.b : x.g < y.g;
     };
-    std::sort(narrow.begin(), narrow.end(), by_cost);
-    std::sort(wide.begin(), wide.end(), by_cost);
+    // low-rank items grouped by column cluster (longest first within a
+    // cluster): CTAs that run at the same time read the same slice of W, which
+    // stays in L2 even when W as a whole does not (81,920 elements x 128
+    // unique frequencies: 168 MB; far field 34.8 against 39.0 ms longest first)
+    auto by_col = [&](const Item& x, const Item& y) {
+        const int cx = fa->ranges[x.b].cb, cy = fa->ranges[y.b].cb;
+        if (cx != cy) return cx < cy;
+        return by_cost(x, y);
+    };
+    std::sort(narrow.begin(), narrow.end(), by_col);
+    std::sort(wide.begin(), wide.end(), by_col);
     std::sort(dense.begin(), dense.end(), by_cost);
     for (const Item& it : dense) L.push_back(it.b);
     fa->plan_nd = (int)L.size();

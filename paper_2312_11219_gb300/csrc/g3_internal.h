@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <map>
 #include <memory>
 #include <string>
@@ -214,7 +215,8 @@ struct g3_ctx {
     // [1] the predictor-based one
     double pool_scale[2][5][2] = {{{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}},
                                   {{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}}};
-    std::map<long long, std::pair<int, int>> tune_cache;  // autotuner: key -> (threads, dense_face_max)
+    std::map<long long, std::array<int, 3>> tune_cache;  // autotuner: key -> (threads, dense_face_max,
+                                                         // residual_face_max)
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
     void count(const char* name, int64_t n = 1) {
         launches[name] += n;
