@@ -673,12 +673,30 @@ __device__ void face_dense_residual(const AcaArgs<T>& A, const Ws<T>& w, BlockSh
     Cx<T>* su = reinterpret_cast<Cx<T>*>(arena + drf_stage_offset<T>());  // [DRF_KC][TI]
     Cx<T>* sv = su + DRF_KC * TI;                                          // [DRF_KC][TJ]
     Cx<T>* D = w.dres;
-    // the entries, one thread per entry (consecutive threads take consecutive columns)
+    // the entries, one thread per entry (consecutive threads take consecutive
+    // columns); linear elements: one thread per element pair, whose nine local
+    // entries share the pair's quadrature points
     const int MN = M * N;
     long long te = clock64();
-    for (int e = tid; e < MN; e += NT) {
-        const int i = e / N, j = e - i * N;
-        D[e] = ent<KER, T>(A, S.rb + i, S.cb + j, kf);
+    if constexpr (KER == G3_GAL_P1D || KER == G3_GAL_P1KP) {
+        const float2 s = A.sf[kf];
+        const int Me = M / 3, Ne = N / 3;
+        for (int e = tid; e < Me * Ne; e += NT) {
+            const int pe = e / Ne, qe = e - pe * Ne;
+            T r[16], m[16], gz[16], cab[9], nn;
+            p1_pair_setup<KER>(A.gf, S.rb / 3 + pe, S.cb / 3 + qe, r, m, gz, cab, nn);
+            Cx<T> v[9];
+            p1_pair_eval<KER, T>(r, m, gz, cab, nn, s.x, s.y, v);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) D[(size_t)(3 * pe + a) * N + 3 * qe + b] = v[a * 3 + b];
+        }
+    } else {
+        for (int e = tid; e < MN; e += NT) {
+            const int i = e / N, j = e - i * N;
+            D[e] = ent<KER, T>(A, S.rb + i, S.cb + j, kf);
+        }
     }
     __syncthreads();
     sublap(S, 10, te);  // the residual lines evaluate no entries when this runs
