@@ -577,7 +577,15 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     }
     const double ms_rounds = ms_since(th1);
     const auto th2 = std::chrono::steady_clock::now();
-    if (est > 0) scale = std::max(scale, 1.15 * (double)ctr / est);
+    // the pool's scale against the estimate, learned from what this run
+    // needed (+15 %): it grows at once and shrinks by at most half per run,
+    // so that an over-reserving estimate stops costing the trim copy below on
+    // every compression while a problem that needs more than the last one
+    // rarely spills
+    if (est > 0) {
+        const double need = 1.15 * (double)ctr / est;
+        scale = need >= scale ? need : std::max(need, 0.5 * scale);
+    }
     // give back what the estimate over-reserved: a pool much larger than its
     // use is moved into an exact-size buffer (its offsets stay valid)
     if (ctr > 0 && (double)cap > 1.25 * (double)ctr && ((long long)cap - (long long)ctr) * (long long)sizeof(Cx<T>) > (256LL << 20)) {
