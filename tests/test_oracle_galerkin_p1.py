@@ -139,3 +139,14 @@ def test_singular_p1_blocks_sum_to_p0_integrals(case):
     i0 = G.entries(v, t, [a], [b], S)[0]
     s2part = D - (cx @ cy.T)[:, :, None] * i0[None, None, :]
     assert np.allclose(s2part.sum(axis=(0, 1)), S ** 2 * float(nx @ ny) * i0, rtol=1e-12, atol=0)
+
+
+def test_nodal_rows_match_dense_assembly():
+    """The row-by-row assembly the GPU tests and the bench use equals the
+    dense assembly (both operators)."""
+    v, t = meshes.icosphere(1)
+    rows = np.array([0, 7, 33])
+    for op in ("d", "kp"):
+        dense = P1.dense_nodal(v, t, S, op)
+        part = P1.nodal_rows(v, t, rows, S, op)
+        assert np.max(np.abs(part - dense[rows])) <= 1e-12 * np.max(np.abs(dense))
