@@ -375,7 +375,7 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     };
     // learned per kernel kind and precision: operators alternating on one
     // context (single and double layer) need different pool sizes per estimate
-    double& scale = ctx->pool_scale[pool_mlp ? 1 : 0][(kernel >= 0 && kernel < 4) ? kernel : 4][sizeof(T) == 4 ? 1 : 0];
+    double& scale = ctx->pool_scale[pool_mlp ? 1 : 0][(kernel >= 0 && kernel < 6) ? kernel : 2][sizeof(T) == 4 ? 1 : 0];
     double est = 0.0;
     for (int q = 0; q < n_run; ++q) est += block_est(queue[q]);
     long long cap = (long long)(pf * scale * est);
@@ -556,7 +556,9 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
         for (int b : sp) n_lo += !is_dense(ranges[b]);
         n_de = n_spill - n_lo;
         // enlarged pool: the used part [0, cap) is kept at the same offsets
-        long long add = (long long)(1.5 * scale * est2);
+        // at least 1.5 times the spilled blocks' plain estimate (which
+        // over-reserves): one round, even after the learned scale has shrunk
+        long long add = (long long)(1.5 * std::max(scale, 1.0) * est2);
         add = std::max(add, (long long)(ctr - std::min<unsigned long long>(ctr, (unsigned long long)cap)));
         add = std::max(add, (long long)1 << 16);
         // the enlarged pool and the copy of the old one must fit together

@@ -213,8 +213,11 @@ struct g3_ctx {
     // factor-pool size / estimate needed by earlier compressions, per kernel
     // kind (slot 4: anything else) and working precision, [0] plain estimate,
     // [1] the predictor-based one
-    double pool_scale[2][5][2] = {{{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}},
-                                  {{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}}};
+    // factor-pool scale against the plain estimate, per predictor use, kernel
+    // kind (single, double layer, separable, Galerkin single layer,
+    // hypersingular, adjoint double layer) and precision
+    double pool_scale[2][6][2] = {{{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}},
+                                  {{1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}, {1.0, 1.0}}};
     std::map<long long, std::array<int, 3>> tune_cache;  // autotuner: key -> (threads, dense_face_max,
                                                          // residual_face_max)
     int64_t last_apply_bytes = 0, last_near_bytes = 0;
