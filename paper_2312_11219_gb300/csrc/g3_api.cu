@@ -1403,6 +1403,7 @@ g3_status g3_block_features(g3_ctx* ctx, const g3_tree* t, const g3_freqs* f, g3
                             float* out) {
     G3_CHECK(ctx && t && f && out, "g3_block_features: NULL argument");
     G3_CHECK(kernel == G3_SLP || kernel == G3_DLP, "g3_block_features: kernel must be G3_SLP or G3_DLP");
+    G3_CHECK(!t->p1, "g3_block_features: the tree must be an element tree (features are per element block)");
     G3_CHECK(eps3 > 0 && eps3 < 1, "g3_block_features: eps3 = %g outside (0, 1)", eps3);
     const int n_far = (int)t->far_index.size();
     if (n_far == 0) return G3_OK;
