@@ -320,17 +320,17 @@ def whole_job_rate(units_all_ranks: float, ms_max: float, steps: int) -> float:
 
 
 def train_predictor(g3, ctx, kernels, prec):
-    """Block predictor trained on the compressions of the smaller
-    configurations (the 768-triangle cube, the 3,072-triangle L-shape with
-    both operators, and the 1,280-triangle Galerkin icosphere): features and
-    labels from the library, training on the GPU."""
+    """Block predictor trained on the compressions of configurations 1-3
+    (the 768-triangle cube, the 12,288-triangle L-shape with both operators,
+    the 20,480-triangle Galerkin icosphere): features and labels from the
+    library, training on the GPU."""
     import time
 
     import numpy as np
 
     from inputs import workloads
     X, Y = [], []
-    for name in ("cube768", "lshape3072", "sphere1280g"):
+    for name in ("cube768", "lshape12288", "sphere20480"):
         w = workloads.get(name)
         T = g3.build_cluster_tree(ctx, w.verts, w.tris, w.leaf, w.eta, max_block=w.max_block)
         F = g3.freqs_from_spec(ctx, w.freq)
@@ -345,7 +345,7 @@ def train_predictor(g3, ctx, kernels, prec):
     p = net.predict(X)
     return net, {"samples": int(X.shape[0]), "epochs": 150, "seconds": secs,
                  "mae_log2_r3": float(np.abs(p[:, 0] - Y[:, 0]).mean()),
-                 "data": "cube768 + lshape3072 (slp, dlp) + sphere1280g compressions"}
+                 "data": "cube768 + lshape12288 (slp, dlp) + sphere20480 (Galerkin) compressions"}
 
 
 def plain_vs_batched(g3, ctx, w, T, F, ker, n_blocks: int, seed: int, prec: str, eps_plain: float,
