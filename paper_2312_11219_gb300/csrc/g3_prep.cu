@@ -470,7 +470,6 @@ __global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPai
     const int npts = nq * ss_regions(pr.cas);
     T* ws = rs + npts;
     __shared__ SsPanels P;
-    __shared__ T red[2][NT / 32];
     if (threadIdx.x == 0) ss_panels(gd, pr.i, pr.j, pr.px, pr.py, P);
     __syncthreads();
     for (int q = threadIdx.x; q < npts; q += NT) {
@@ -488,12 +487,14 @@ __global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPai
         ws[q] = (T)w;
     }
     __syncthreads();
+    // each warp owns every (NT / 32)-th frequency: its lanes sum over all the
+    // points and the warp reduces, with no block-wide barrier per frequency
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = 0; k < Ku; ++k) {
+    for (int k = wid; k < Ku; k += NT / 32) {
         const double2 s = sd[k];
         const T sre = (T)s.x, sim = (T)s.y;
         T ax = 0, ay = 0;
-        for (int q = threadIdx.x; q < npts; q += NT) {
+        for (int q = lane; q < npts; q += 32) {
             const T r = rs[q];
             const T m = ws[q] * kexp(-sre * r);
             T sn, cs;
@@ -503,20 +504,7 @@ __global__ void __launch_bounds__(NT) k_near_ss(GeomD gd, SsRule gr, const SsPai
         }
         ax = warp_sum(ax);
         ay = warp_sum(ay);
-        if (lane == 0) {
-            red[0][wid] = ax;
-            red[1][wid] = ay;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            T sx = 0, sy = 0;
-            for (int w = 0; w < NT / 32; ++w) {
-                sx += red[0][w];
-                sy += red[1][w];
-            }
-            out[pr.off + (long long)k * pr.stride] = Cx<T>{sx, sy};
-        }
-        __syncthreads();
+        if (lane == 0) out[pr.off + (long long)k * pr.stride] = Cx<T>{ax, ay};
     }
 }
 
@@ -579,7 +567,6 @@ __global__ void __launch_bounds__(NT) k_near_ss_p1(GeomD gd, SsRule gr, const Ss
     T* pt = reinterpret_cast<T*>(smem_raw);                    // [7][NQ]: x1, x2, y1, y2, r, w, g
     Cx<T>* acc = reinterpret_cast<Cx<T>*>(pt + 7 * NQ);         // [Ku][10]
     __shared__ SsPanels P;
-    __shared__ Cx<T> red[NT / 32][10];
     const SsPair pr = pairs[blockIdx.x];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) ss_panels(gd, pr.i, pr.j, pr.px, pr.py, P);
@@ -616,13 +603,14 @@ __global__ void __launch_bounds__(NT) k_near_ss_p1(GeomD gd, SsRule gr, const Ss
             pt[6 * NQ + q] = r > 0.0 ? (T)(-(z[0] * n[0] + z[1] * n[1] + z[2] * n[2]) / d2) : (T)0;
         }
         __syncthreads();
-        for (int k = 0; k < Ku; ++k) {
+        // each warp owns every (NT / 32)-th frequency (no block-wide barrier per frequency)
+        for (int k = wid; k < Ku; k += NT / 32) {
             const double2 s = sd[k];
             const T sre = (T)s.x, sim = (T)s.y;
             Cx<T> v[10];
 #pragma unroll
             for (int u = 0; u < 10; ++u) v[u] = Cx<T>{0, 0};
-            for (int q = threadIdx.x; q < NQ; q += NT) {
+            for (int q = lane; q < NQ; q += 32) {
                 const T r = pt[4 * NQ + q];
                 const T m = pt[5 * NQ + q] * kexp(-sre * r);
                 T sn, cs;
@@ -649,20 +637,16 @@ __global__ void __launch_bounds__(NT) k_near_ss_p1(GeomD gd, SsRule gr, const Ss
                 v[u].x = warp_sum(v[u].x);
                 v[u].y = warp_sum(v[u].y);
             }
-            if (lane == 0)
-                for (int u = 0; u < 10; ++u) red[wid][u] = v[u];
-            __syncthreads();
-            if (threadIdx.x < 10) {
+            if (lane < 10) {  // frequency k belongs to this warp alone
                 Cx<T> t{0, 0};
-                for (int w = 0; w < NT / 32; ++w) {
-                    t.x += red[w][threadIdx.x].x;
-                    t.y += red[w][threadIdx.x].y;
-                }
-                acc[k * 10 + threadIdx.x].x += t.x;
-                acc[k * 10 + threadIdx.x].y += t.y;
+#pragma unroll
+                for (int u = 0; u < 10; ++u)
+                    if (u == lane) t = v[u];
+                acc[k * 10 + lane].x += t.x;
+                acc[k * 10 + lane].y += t.y;
             }
-            __syncthreads();
         }
+        __syncthreads();  // the region's points are consumed before the next region overwrites them
     }
     // local entries (Sauter-Schwab vertex order c, d = local vertices px[c], py[d])
     for (int e = threadIdx.x; e < Ku * 9; e += NT) {
