@@ -172,7 +172,13 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     const int Cmax = Ku;
     for (auto& J : jobs) J.fa->Cmax = Cmax;
     const int n_far = (int)ranges.size();
-    if (n_far == 0) return G3_OK;
+    if (n_far == 0) {  // no admissible block: empty work lists, the apply runs the near field alone
+        for (auto& J : jobs) {
+            const g3_status pst = far_plan_build(J.fa);
+            if (pst != G3_OK) return pst;
+        }
+        return G3_OK;
+    }
     int Mmax = 0, Nmax = 0;
     for (auto& r : ranges) {
         Mmax = std::max(Mmax, r.re - r.rb);

@@ -324,3 +324,26 @@ def test_host_tree_partition_rejects_bad_input(built_lib):
         g3.tree_partition_host(w.verts, bad, w.leaf, w.eta)
     with pytest.raises(g3.G3Error):
         g3.tree_partition_host(w.verts, w.tris, 0, w.eta)
+    with pytest.raises(g3.G3Error):           # empty mesh
+        g3.tree_partition_host(w.verts, w.tris[:0], w.leaf, w.eta)
+
+
+def test_host_tree_partition_degenerate_meshes(built_lib):
+    """One triangle: a single leaf and its 1 x 1 near block.  A mesh no larger
+    than a leaf: one near block.  The 192-triangle cube: no admissible block
+    at all (every block near), as in the oracle."""
+    sys.path.insert(0, ROOT)
+    import paper_2312_11219_gb300 as g3
+    from oracle import tree as O_tree
+    v = np.array([[0.0, 0.0, 0.0], [0.9, 0.1, 0.0], [0.2, 0.7, 0.3]])
+    t = np.array([[0, 1, 2]], dtype=np.int32)
+    got = g3.tree_partition_host(v, t, 32, 1.0)
+    assert np.array_equal(got["perm"], [0]) and np.array_equal(got["blocks"], [[0, 1, 0, 1, 0]])
+    w = workloads.get("cube48")
+    got = g3.tree_partition_host(w.verts, w.tris, 48, w.eta)
+    assert np.array_equal(got["blocks"], [[0, 48, 0, 48, 0]])
+    w = workloads.get("cube192")
+    got = g3.tree_partition_host(w.verts, w.tris, w.leaf, w.eta)
+    ref = O_tree.build(w.verts, w.tris, w.leaf, w.eta)
+    assert np.array_equal(got["perm"], ref.perm) and np.array_equal(got["blocks"], ref.blocks)
+    assert got["blocks"].shape[0] == 64 and not (got["blocks"][:, 4] == 1).any()
