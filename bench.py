@@ -42,6 +42,11 @@ METRIC = "3-way ACA entries/s & apply GB/s (1 GB300); learned+batched vs plain a
 # operator's launch (dram__bytes_read.sum + dram__bytes_write.sum: 36.8 GB and
 # 41.8 GB) of the current kernel; other workloads have no capture (null)
 ACA_TRAFFIC_BYTES = {"lshape12288": 0.5 * (19234748160 + 17581539072 + 23269448960 + 18566676224)}
+# DRAM bytes (read + write) of one apply of each operator of the same workload
+# (every kernel of apply_gcq, from one ncu capture per operator: 7,131.4 MB
+# single layer, 6,899.9 MB double layer); the bench's steady-state apply bytes
+# are the same sum over both operators
+APPLY_TRAFFIC_BYTES = {"lshape12288": 7131350656 + 6899897472}
 MUFU_PER_ENTRY = 28
 MUFU_PER_ENTRY_GALERKIN = 64
 # special-function-unit results per clock per SM for rsqrt / sin / cos
@@ -740,7 +745,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                              "rates); frac_evaluated adds the entries of the dense residual working faces"},
         "roofline_apply": {"bound": "hbm", "achieved": steady_bytes / (steady_ms / 1e3) / 1e9,
                            "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": steady_bytes / (steady_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                           "frac": steady_bytes / (steady_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                           "traffic": APPLY_TRAFFIC_BYTES.get(args.workload) if world == 1 else None,
+                           "traffic_unit": "bytes per apply of every operator", "bytes": steady_bytes,
                            "kernel": "apply_gcq (all kernels)", "peak_source": peaks["source"],
                            "note": "algorithmic bytes (near field, factors, W, y) / CUDA-event time of the whole "
                                    "apply, mean of 10 applies per operator after one untimed apply (steady state: "
@@ -831,7 +838,8 @@ def run_profile_case(args) -> dict:
     operator (256 threads, dense faces up to 48^2), then the near field and two
     applies.  Launch order: the compression's low-rank launch, its dense-face
     launch, the near-field assembly, then per apply k_apply_prep,
-    k_apply_near, k_apply_far_dense, k_far_vx, k_far_uy, k_apply_finish."""
+    k_apply_near (side stream), k_apply_far_dense, k_far_lr_tc (narrow and
+    wide blocks), k_apply_finish."""
     import torch
     import paper_2312_11219_gb300 as g3
     from inputs import workloads
