@@ -21,8 +21,7 @@
 import numpy as np
 import pytest
 
-from inputs import workloads
-from inputs import meshes
+from inputs import meshes, workloads
 from oracle import aca3 as O_aca, apply as O_apply, freqs as O_freqs, quadrature as O_q, tree as O_tree
 
 pytestmark = pytest.mark.gpu
