@@ -111,7 +111,8 @@ typedef struct g3_mlp g3_mlp;
 /* Options of aca3_compress.  Zero-initialise and set what you need;
  * a NULL pointer means all defaults. */
 typedef struct {
-    int face_rank_max;    /* cap of a face ACA's rank (0 = 48; max 64)                     */
+    int face_rank_max;    /* cap of a face ACA's rank (0 = 48, 64 for G3_HYPERSINGULAR and
+                             G3_ADJOINT_DLP; max 64)                                      */
     int unbatched;        /* 1 = one block per launch sequence, host loop (plain baseline) */
     int ctas_per_sm;      /* persistent CTAs per SM (0 = from the occupancy calculator)    */
     int threads;          /* threads per CTA of the low-rank-face launch: 128, 256, 384 or

@@ -142,7 +142,11 @@ static g3_status run_aca_t(g3_ctx* ctx, std::vector<AcaJob>& jobs, int kernel, d
     const bool sep = kernel == G3_SEPARABLE;
     const int n_jobs = (int)jobs.size();
     const bool batched = n_jobs > 1;
-    const int RF = o.face_rank_max > 0 ? std::min(o.face_rank_max, RF_MAX) : 48;
+    // face rank cap: 48, and RF_MAX for the linear-element operators, whose
+    // hypersingular faces at high frequencies need ranks of 70 and more on
+    // blocks of 40 elements a side (capped at 48 they stay unresolved)
+    const bool p1_kind = kernel == G3_GAL_P1D || kernel == G3_GAL_P1KP;
+    const int RF = o.face_rank_max > 0 ? std::min(o.face_rank_max, RF_MAX) : (p1_kind ? RF_MAX : 48);
     // face tolerance: eps3 / 100 (eps = 100 eps_ACA); in float32 arithmetic not
     // below 1e-5, the relative noise level of float32 entries
     const double eps_face = o.eps_face > 0 ? o.eps_face : (sizeof(T) == 4 ? std::max(eps3 / 100.0, 1e-5) : eps3 / 100.0);

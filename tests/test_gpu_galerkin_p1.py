@@ -151,19 +151,12 @@ def test_p1_compression_and_nodal_apply(g3, ctx, setup, kernel):
 
 
 # The hypersingular operator's later faces on the 40-element blocks need face
-# ranks 68-87 (the oracle's Algorithm 1 on the same blocks); the default face
-# rank cap of 48 leaves them unresolved (capped faces are flagged in the
-# status word): the oracle itself capped at 48 gives 8.3-8.8 eps3, at 64
-# 1.4 eps3, uncapped 0.44 eps3.
-_HYP_LOWRANK_GAP = pytest.mark.xfail(
-    reason="known gap: the face rank cap of 48 is below the 68-87 the hypersingular operator's later faces "
-           "need on 40-element blocks (11.5-12.7 eps3 here; exact dense faces 0.38 eps3)", strict=False)
-
-
+# ranks 68-87 (the oracle's Algorithm 1 on the same blocks): the oracle capped
+# at 48 gives 8.3-8.8 eps3, at 64 1.4 eps3, uncapped 0.44 eps3, so the kernel
+# caps the face ranks of the linear-element operators at 64 (48 elsewhere).
 @pytest.mark.parametrize("kernel,path", [
-    pytest.param("hyp", "dense_residual", marks=_HYP_LOWRANK_GAP),
-    pytest.param("hyp", "lines", marks=_HYP_LOWRANK_GAP),
-    ("hyp", "dense_faces"), ("adj", "dense_residual"), ("adj", "lines"), ("adj", "dense_faces")])
+    ("hyp", "dense_residual"), ("hyp", "lines"), ("hyp", "dense_faces"),
+    ("adj", "dense_residual"), ("adj", "lines"), ("adj", "dense_faces")])
 def test_p1_compression_entry_paths(g3, ctx, setup, kernel, path):
     """Each way the compression forms entries of linear elements: dense
     residual working faces (the default), the residual rows and columns of
