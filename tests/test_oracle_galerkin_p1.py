@@ -18,6 +18,9 @@ double layer K' with linear continuous elements (eq. (bie_semi_neum)).
 * The single layer's row sums of oracle.galerkin agree with the same
   Sauter-Schwab maps applied to the constant local functions (sum of the
   local P1 blocks of the s^2 part is s^2 (n . n) times the P0 integral).
+* Algorithm 1 on a far block of D reaches eps3 with free face ranks; its
+  later faces need ranks above 64, a cap of 64 keeps 10 eps3 and a cap of
+  48 does not (the face rank cap the kernel uses for these operators).
 """
 import numpy as np
 import pytest
@@ -150,3 +153,53 @@ def test_nodal_rows_match_dense_assembly():
         dense = P1.dense_nodal(v, t, S, op)
         part = P1.nodal_rows(v, t, rows, S, op)
         assert np.max(np.abs(part - dense[rows])) <= 1e-12 * np.max(np.abs(dense))
+
+
+class _DenseTensor:
+    """A block's three-way array given densely (rows, columns, frequencies)."""
+
+    def __init__(self, D):
+        self.D = D
+        self.M, self.N, self.Ku = D.shape
+        self.generated = 0
+
+    def row(self, i, k):
+        return self.D[i, :, k].copy()
+
+    def col(self, j, k):
+        return self.D[:, j, k].copy()
+
+    def fiber(self, i, j):
+        return self.D[i, j, :].copy()
+
+    def face(self, k):
+        return self.D[:, :, k].copy()
+
+
+def test_hypersingular_far_block_face_ranks():
+    """Algorithm 1 on a far block of D with linear elements (40 elements a
+    side of the 1280-triangle sphere, its gCQ set with |s| up to 400): within
+    eps3 of the block with free face ranks, whose later faces need ranks
+    above 64; a face rank cap of 64 still meets 10 eps3 (the cap the kernel
+    uses for these operators), a cap of 48 does not come close."""
+    from oracle import aca3 as O_aca, freqs as O_freqs, tree as O_tree
+    from inputs import workloads
+    w = workloads.get("sphere1280g")
+    fs = O_freqs.frequency_set(w.freq)
+    su = fs["s"][fs["uniq"]]
+    OT = O_tree.build(w.verts, w.tris, w.leaf, w.eta)
+    far = np.flatnonzero(OT.blocks[:, 4] == 1)
+    b = far[np.flatnonzero(OT.blocks[far, 1] - OT.blocks[far, 0] == 40)[0]]
+    rb, re, cb, ce, _ = OT.blocks[b]
+    D = np.zeros((3 * (re - rb), 3 * (ce - cb), su.size), complex)
+    for a, e in enumerate(OT.perm[rb:re]):
+        for c, f in enumerate(OT.perm[cb:ce]):
+            D[3 * a:3 * a + 3, 3 * c:3 * c + 3] = P1.local_block(w.verts, w.tris, int(e), int(f), su, "d")
+    eps3 = 1e-4
+    err = {}
+    for cap in (None, 64, 48):
+        r = O_aca.aca3(_DenseTensor(D), eps3, s_abs=np.abs(su), max_face_rank=cap)
+        err[cap] = np.linalg.norm(r.dense(*D.shape) - D) / np.linalg.norm(D)
+        if cap is None:
+            assert max(c.face_rank for c in r.crosses) > 64
+    assert err[None] <= eps3 and err[64] <= 10 * eps3 and err[48] > 5 * eps3, err
